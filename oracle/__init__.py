@@ -1,0 +1,236 @@
+"""CPU FP64 oracle for the SPFD Poisson solve -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library
+(``paper_2010_12879_gb300``) never imports, links or runs it, and the two share
+no code; the only common module is ``spfd_inputs`` (seeded input generators,
+which hold none of the method's arithmetic).
+
+The arithmetic lives in ``spfd_oracle.c`` (plain C, FP64, OpenMP loops), which
+this wrapper compiles with gcc on first use and calls through ctypes.  Every
+function cites the paper passage it follows:
+
+* ``conductances``  -- the diagonal M_k of Eq. 3 (Sec. II), reading R1;
+* ``assemble``      -- CSR of G^T M_k G over the conducting nodes (Eq. 3,
+  Sec. III-A), readings R1, R3;
+* ``rhs``           -- -G^T M_k a (Eq. 3);
+* ``components`` / ``project`` -- the per-component constant nullspace (R4);
+* ``pcg``           -- Jacobi-preconditioned CG to a recomputed relative
+  residual (Sec. II-A premise of 1e-12; the oracle defaults to 1e-13), R5;
+* ``efield``        -- |E| from Eq. 1, voxel averaged (Sec. III-E), R6.
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py``
+(closed forms, brute force on tiny grids, invariants); none is unpinned.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spfd_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+i64 = ctypes.c_int64
+dp = ctypes.POINTER(ctypes.c_double)
+lp = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``spfd_oracle.c`` into ``oracle/_build/liboracle.so``.
+
+    FMA contraction is disabled so that x86-64 and aarch64 hosts round alike.
+    """
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (force or not os.path.exists(_LIB_PATH)
+            or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+            "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_num_threads.restype = ctypes.c_int
+            L.orc_conductances.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+            L.orc_index_nodes.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, lp]
+            L.orc_index_nodes.restype = i64
+            L.orc_assemble.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, lp, lp, lp, dp]
+            L.orc_assemble.restype = i64
+            L.orc_rhs.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_matvec.argtypes = [i64, lp, lp, dp, dp, dp]
+            L.orc_components.argtypes = [i64, lp, lp, lp]
+            L.orc_components.restype = i64
+            L.orc_project.argtypes = [i64, lp, i64, dp]
+            L.orc_project.restype = ctypes.c_int
+            L.orc_pcg.argtypes = [i64, lp, lp, dp, dp, ctypes.c_double, i64, dp, dp]
+            L.orc_pcg.restype = ctypes.c_int
+            L.orc_efield.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_double, dp]
+            _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _d(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(dp)
+
+
+def _l(a):
+    assert a.dtype == np.int64 and a.flags.c_contiguous
+    return a.ctypes.data_as(lp)
+
+
+def _dims(sigma):
+    nz, ny, nx = sigma.shape
+    return nx, ny, nz
+
+
+def conductances(sigma: np.ndarray, h: float) -> np.ndarray:
+    """Edge conductances g, shape (3, nz+1, ny+1, nx+1) (Eq. 3's M_k, R1)."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    nx, ny, nz = _dims(sigma)
+    g = np.zeros((3, nz + 1, ny + 1, nx + 1))
+    lib().orc_conductances(_d(sigma), nx, ny, nz, float(h), _d(g))
+    return g
+
+
+@dataclass
+class System:
+    """The assembled Eq. 3 operator over the conducting nodes."""
+
+    dims: tuple              # (nx, ny, nz) voxels
+    h: float
+    g: np.ndarray            # (3, nz+1, ny+1, nx+1)
+    dof: np.ndarray          # int64 node-grid map -> compact index or -1
+    nodes: np.ndarray        # int64 compact index -> flat node id
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    comp: np.ndarray         # int64 component id per compact unknown
+    ncomp: int
+
+    @property
+    def n(self) -> int:
+        return int(self.nodes.size)
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.n, self.n))
+
+    def gather(self, full: np.ndarray) -> np.ndarray:
+        return np.ascontiguousarray(full.reshape(-1)[self.nodes])
+
+    def scatter(self, x: np.ndarray) -> np.ndarray:
+        nx, ny, nz = self.dims
+        out = np.zeros((nz + 1) * (ny + 1) * (nx + 1))
+        out[self.nodes] = x
+        return out.reshape(nz + 1, ny + 1, nx + 1)
+
+
+def assemble(sigma: np.ndarray, h: float) -> System:
+    """Assemble G^T M_k G on the conducting nodes and label its components."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    nx, ny, nz = _dims(sigma)
+    L = lib()
+    g = conductances(sigma, h)
+    dof = np.empty((nz + 1) * (ny + 1) * (nx + 1), dtype=np.int64)
+    n = int(L.orc_index_nodes(_d(g), nx, ny, nz, _l(dof)))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(max(7 * n, 1), dtype=np.int64)
+    val = np.zeros(max(7 * n, 1))
+    nnz = int(L.orc_assemble(_d(g), nx, ny, nz, _l(dof), _l(rowptr), _l(col), _d(val)))
+    col, val = col[:nnz].copy(), val[:nnz].copy()
+    comp = np.empty(max(n, 1), dtype=np.int64)
+    ncomp = int(L.orc_components(n, _l(rowptr), _l(col), _l(comp)))
+    if ncomp < 0:
+        raise MemoryError("oracle component labelling")
+    nodes = np.flatnonzero(dof >= 0).astype(np.int64)
+    return System((nx, ny, nz), float(h), g, dof, nodes, rowptr, col, val,
+                  comp[:n].copy(), ncomp)
+
+
+def rhs_full(g: np.ndarray, a: np.ndarray) -> np.ndarray:
+    """b = -G^T M_k a on the whole node grid (Eq. 3)."""
+    _, nzp, nyp, nxp = g.shape
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.shape == g.shape
+    b = np.zeros((nzp, nyp, nxp))
+    lib().orc_rhs(_d(np.ascontiguousarray(g)), _d(a), nxp - 1, nyp - 1, nzp - 1, _d(b))
+    return b
+
+
+def rhs(sys: System, a: np.ndarray) -> np.ndarray:
+    """b restricted to the unknowns (not yet projected)."""
+    return sys.gather(rhs_full(sys.g, a))
+
+
+def matvec(sys: System, x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(sys.n)
+    lib().orc_matvec(sys.n, _l(sys.rowptr), _l(sys.col), _d(sys.val), _d(x), _d(y))
+    return y
+
+
+def project(sys: System, x: np.ndarray) -> np.ndarray:
+    """Remove each component's unweighted mean (R4); returns a new array."""
+    y = np.array(x, dtype=np.float64, copy=True)
+    if sys.n and lib().orc_project(sys.n, _l(sys.comp), sys.ncomp, _d(y)) != 0:
+        raise MemoryError("oracle projection")
+    return y
+
+
+def pcg(sys: System, b: np.ndarray, tol: float = 1e-13, maxit: int = 1_000_000):
+    """Jacobi-PCG from x = 0 (R5).  Returns (x, info dict)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(max(sys.n, 1))
+    info = np.zeros(3)
+    rc = lib().orc_pcg(sys.n, _l(sys.rowptr), _l(sys.col), _d(sys.val), _d(b),
+                       float(tol), int(maxit), _d(x), _d(info))
+    if rc != 0:
+        raise MemoryError("oracle pcg")
+    return x[:sys.n], {"iters": int(info[0]), "rel_res": float(info[1]),
+                       "converged": bool(info[2])}
+
+
+def solve(sigma: np.ndarray, h: float, a: np.ndarray, tol: float = 1e-13,
+          maxit: int = 1_000_000, sys: System | None = None):
+    """Psi on the node grid (zero at removed nodes, zero mean per component)
+    solving Eq. 3, plus the solver report.  Returns (psi, info, sys)."""
+    if sys is None:
+        sys = assemble(sigma, h)
+    b = project(sys, rhs(sys, a))
+    x, info = pcg(sys, b, tol, maxit)
+    x = project(sys, x)
+    return sys.scatter(x), info, sys
+
+
+def efield(sigma: np.ndarray, a: np.ndarray, psi: np.ndarray, h: float,
+           omega: float) -> np.ndarray:
+    """Voxel-averaged |E| (Eq. 1, Sec. III-E, R6), shape (nz, ny, nx)."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    nx, ny, nz = _dims(sigma)
+    assert a.shape == (3, nz + 1, ny + 1, nx + 1) and psi.shape == (nz + 1, ny + 1, nx + 1)
+    E = np.zeros((nz, ny, nx))
+    lib().orc_efield(_d(sigma), _d(a), _d(psi), nx, ny, nz, float(h), float(omega), _d(E))
+    return E

@@ -1,0 +1,361 @@
+/*
+ * CPU FP64 oracle for the Co-Sim. SPFD Poisson solve -- TEST INFRASTRUCTURE.
+ *
+ * This file is the plain, slow, obviously-correct definition of what the GPU
+ * path computes.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load it; the product library never does, and the two
+ * share no code.
+ *
+ * Method (Haussmann et al., "Towards Real-Time Magnetic Dosimetry Simulations
+ * for Inductive Charging Systems"):
+ *   Eq. 3 (Sec. II):  G^T M_k G Psi = -G^T M_k a   (discrete Poisson system)
+ *   Eq. 1 (Sec. II):  e = -j omega (a + G Psi)       (edge voltages)
+ *   Sec. III-A:       only conducting voxels carry unknowns
+ *   Sec. II-A:        double precision, relative residual below 1e-12
+ *   Sec. III-E:       voxel-averaged |E|
+ *
+ * Readings of what the paper leaves open (each used below):
+ *   R1  M_k holds one conductance per edge, g_e = h * (sum of the sigma of the
+ *       four voxels sharing the edge) / 4; voxels outside the grid are air.
+ *   R3  a node is an unknown iff one of its incident edges has g_e > 0.
+ *   R4  Psi is fixed up to one constant per connected conducting component;
+ *       the oracle reports the zero-mean representative of each component.
+ *   R5  "relative residual" = ||b - A Psi||_2 / ||b||_2 from Psi_0 = 0, with
+ *       the residual recomputed from its definition.
+ *   R6  |E| of a voxel = (omega / h) * || (mean of u over the voxel's four
+ *       x-edges, ... y-edges, ... z-edges) ||_2 with u = a + G Psi.
+ *
+ * Layout (shared with the input generators): voxels [k][j][i] (nz,ny,nx),
+ * nodes [k][j][i] (nz+1,ny+1,nx+1), edges [d][k][j][i] with d = 0,1,2 for
+ * the x,y,z edge leaving node (i,j,k) in the +d direction.
+ *
+ * Parity status: every function below is pinned by the CPU test suite
+ * (closed forms, brute force, invariants); none is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef int64_t i64;
+
+static inline i64 node_id(i64 i, i64 j, i64 k, i64 nx, i64 ny) {
+  return (k * (ny + 1) + j) * (nx + 1) + i;
+}
+
+static inline double vox(const double *s, i64 i, i64 j, i64 k, i64 nx, i64 ny,
+                         i64 nz) {
+  if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return 0.0;
+  return s[(k * ny + j) * nx + i];
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Edge conductances g (the diagonal of M_k, Eq. 3; averaging rule R1).
+ * g has 3*(nx+1)*(ny+1)*(nz+1) entries; slots without an edge are 0. */
+void orc_conductances(const double *sigma, int nx_, int ny_, int nz_, double h,
+                      double *g) {
+  i64 nx = nx_, ny = ny_, nz = nz_;
+  i64 nn = (nx + 1) * (ny + 1) * (nz + 1);
+#pragma omp parallel for schedule(static)
+  for (i64 k = 0; k <= nz; k++)
+    for (i64 j = 0; j <= ny; j++)
+      for (i64 i = 0; i <= nx; i++) {
+        i64 n = node_id(i, j, k, nx, ny);
+        double gx = 0, gy = 0, gz = 0;
+        if (i < nx) /* x edge (i,j,k)->(i+1,j,k): voxels i, j-1..j, k-1..k */
+          gx = vox(sigma, i, j - 1, k - 1, nx, ny, nz) + vox(sigma, i, j, k - 1, nx, ny, nz) +
+               vox(sigma, i, j - 1, k, nx, ny, nz) + vox(sigma, i, j, k, nx, ny, nz);
+        if (j < ny) /* y edge: voxels i-1..i, j, k-1..k */
+          gy = vox(sigma, i - 1, j, k - 1, nx, ny, nz) + vox(sigma, i, j, k - 1, nx, ny, nz) +
+               vox(sigma, i - 1, j, k, nx, ny, nz) + vox(sigma, i, j, k, nx, ny, nz);
+        if (k < nz) /* z edge: voxels i-1..i, j-1..j, k */
+          gz = vox(sigma, i - 1, j - 1, k, nx, ny, nz) + vox(sigma, i, j - 1, k, nx, ny, nz) +
+               vox(sigma, i - 1, j, k, nx, ny, nz) + vox(sigma, i, j, k, nx, ny, nz);
+        g[0 * nn + n] = h * gx / 4.0;
+        g[1 * nn + n] = h * gy / 4.0;
+        g[2 * nn + n] = h * gz / 4.0;
+      }
+}
+
+/* The up to six edges at node (i,j,k): neighbour node and conductance. */
+static int node_edges(const double *g, i64 i, i64 j, i64 k, i64 nx, i64 ny,
+                      i64 nz, i64 nb[6], double ge[6]) {
+  i64 nn = (nx + 1) * (ny + 1) * (nz + 1);
+  i64 n = node_id(i, j, k, nx, ny);
+  int c = 0;
+  if (i > 0) {
+    i64 m = node_id(i - 1, j, k, nx, ny);
+    nb[c] = m; ge[c] = g[0 * nn + m]; c++;
+  }
+  if (i < nx) {
+    nb[c] = node_id(i + 1, j, k, nx, ny); ge[c] = g[0 * nn + n]; c++;
+  }
+  if (j > 0) {
+    i64 m = node_id(i, j - 1, k, nx, ny);
+    nb[c] = m; ge[c] = g[1 * nn + m]; c++;
+  }
+  if (j < ny) {
+    nb[c] = node_id(i, j + 1, k, nx, ny); ge[c] = g[1 * nn + n]; c++;
+  }
+  if (k > 0) {
+    i64 m = node_id(i, j, k - 1, nx, ny);
+    nb[c] = m; ge[c] = g[2 * nn + m]; c++;
+  }
+  if (k < nz) {
+    nb[c] = node_id(i, j, k + 1, nx, ny); ge[c] = g[2 * nn + n]; c++;
+  }
+  return c;
+}
+
+/* Unknowns (R3): dof[n] = compact index of node n, or -1.  Returns the count. */
+i64 orc_index_nodes(const double *g, int nx_, int ny_, int nz_, i64 *dof) {
+  i64 nx = nx_, ny = ny_, nz = nz_, cnt = 0;
+  for (i64 k = 0; k <= nz; k++)
+    for (i64 j = 0; j <= ny; j++)
+      for (i64 i = 0; i <= nx; i++) {
+        i64 nb[6];
+        double ge[6];
+        int c = node_edges(g, i, j, k, nx, ny, nz, nb, ge);
+        int act = 0;
+        for (int q = 0; q < c; q++) act |= ge[q] > 0.0;
+        dof[node_id(i, j, k, nx, ny)] = act ? cnt++ : -1;
+      }
+  return cnt;
+}
+
+/* CSR of A = G^T diag(g) G restricted to the unknowns (Eq. 3):
+ * (A x)_n = sum over edges e at n of g_e (x_n - x_other).  Diagonal first in
+ * each row, then the off-diagonals -g_e in edge order (-x,+x,-y,+y,-z,+z).
+ * rowptr has n_dof+1 entries; col/val need at most 7*n_dof. */
+i64 orc_assemble(const double *g, int nx_, int ny_, int nz_, const i64 *dof,
+                 i64 *rowptr, i64 *col, double *val) {
+  i64 nx = nx_, ny = ny_, nz = nz_, nnz = 0;
+  for (i64 k = 0; k <= nz; k++)
+    for (i64 j = 0; j <= ny; j++)
+      for (i64 i = 0; i <= nx; i++) {
+        i64 n = node_id(i, j, k, nx, ny);
+        i64 r = dof[n];
+        if (r < 0) continue;
+        i64 nb[6];
+        double ge[6];
+        int c = node_edges(g, i, j, k, nx, ny, nz, nb, ge);
+        rowptr[r] = nnz;
+        i64 dpos = nnz++;
+        double diag = 0.0;
+        for (int q = 0; q < c; q++) {
+          if (ge[q] > 0.0) {
+            col[nnz] = dof[nb[q]];
+            val[nnz] = -ge[q];
+            nnz++;
+            diag += ge[q];
+          }
+        }
+        col[dpos] = r;
+        val[dpos] = diag;
+        rowptr[r + 1] = nnz;
+      }
+  return nnz;
+}
+
+/* Right-hand side of Eq. 3 on the node grid: b = -G^T diag(g) a, i.e.
+ * b_n = sum_{e leaving n} g_e a_e - sum_{e entering n} g_e a_e. */
+void orc_rhs(const double *g, const double *a, int nx_, int ny_, int nz_,
+             double *b) {
+  i64 nx = nx_, ny = ny_, nz = nz_;
+  i64 nn = (nx + 1) * (ny + 1) * (nz + 1);
+#pragma omp parallel for schedule(static)
+  for (i64 k = 0; k <= nz; k++)
+    for (i64 j = 0; j <= ny; j++)
+      for (i64 i = 0; i <= nx; i++) {
+        i64 n = node_id(i, j, k, nx, ny);
+        double s = 0.0;
+        if (i < nx) s += g[0 * nn + n] * a[0 * nn + n];
+        if (j < ny) s += g[1 * nn + n] * a[1 * nn + n];
+        if (k < nz) s += g[2 * nn + n] * a[2 * nn + n];
+        if (i > 0) { i64 m = node_id(i - 1, j, k, nx, ny); s -= g[0 * nn + m] * a[0 * nn + m]; }
+        if (j > 0) { i64 m = node_id(i, j - 1, k, nx, ny); s -= g[1 * nn + m] * a[1 * nn + m]; }
+        if (k > 0) { i64 m = node_id(i, j, k - 1, nx, ny); s -= g[2 * nn + m] * a[2 * nn + m]; }
+        b[n] = s;
+      }
+}
+
+/* y = A x (CSR). */
+void orc_matvec(i64 n, const i64 *rowptr, const i64 *col, const double *val,
+                const double *x, double *y) {
+#pragma omp parallel for schedule(static)
+  for (i64 r = 0; r < n; r++) {
+    double s = 0.0;
+    for (i64 p = rowptr[r]; p < rowptr[r + 1]; p++) s += val[p] * x[col[p]];
+    y[r] = s;
+  }
+}
+
+/* Connected components of the graph whose edges are the off-diagonal
+ * entries of A (R4), by breadth-first search.  Returns the count. */
+i64 orc_components(i64 n, const i64 *rowptr, const i64 *col, i64 *comp) {
+  i64 *queue = (i64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(i64));
+  if (!queue) return -1;
+  for (i64 r = 0; r < n; r++) comp[r] = -1;
+  i64 nc = 0;
+  for (i64 s = 0; s < n; s++) {
+    if (comp[s] >= 0) continue;
+    i64 head = 0, tail = 0;
+    queue[tail++] = s;
+    comp[s] = nc;
+    while (head < tail) {
+      i64 r = queue[head++];
+      for (i64 p = rowptr[r]; p < rowptr[r + 1]; p++) {
+        i64 c = col[p];
+        if (comp[c] < 0) { comp[c] = nc; queue[tail++] = c; }
+      }
+    }
+    nc++;
+  }
+  free(queue);
+  return nc;
+}
+
+/* x <- x - (unweighted mean of x over its component), per component (R4). */
+int orc_project(i64 n, const i64 *comp, i64 nc, double *x) {
+  double *sum = (double *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(double));
+  i64 *cnt = (i64 *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(i64));
+  if (!sum || !cnt) { free(sum); free(cnt); return -1; }
+  for (i64 r = 0; r < n; r++) { sum[comp[r]] += x[r]; cnt[comp[r]]++; }
+  for (i64 c = 0; c < nc; c++) sum[c] /= (double)cnt[c];
+  for (i64 r = 0; r < n; r++) x[r] -= sum[comp[r]];
+  free(sum);
+  free(cnt);
+  return 0;
+}
+
+static double dot(i64 n, const double *x, const double *y) {
+  double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
+  for (i64 r = 0; r < n; r++) s += x[r] * y[r];
+  return s;
+}
+
+static double true_residual(i64 n, const i64 *rowptr, const i64 *col,
+                            const double *val, const double *b,
+                            const double *x, double *rt) {
+  orc_matvec(n, rowptr, col, val, x, rt);
+  double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
+  for (i64 i = 0; i < n; i++) {
+    rt[i] = b[i] - rt[i];
+    s += rt[i] * rt[i];
+  }
+  return sqrt(s);
+}
+
+/* Jacobi-preconditioned conjugate gradients for A x = b from x = 0 (R5).
+ * Stops when the recomputed relative residual ||b - A x|| / ||b|| <= tol.
+ * The true residual is recomputed every 50 iterations and whenever the
+ * recursive one reaches tol (then it also replaces the recursive one).  If
+ * 20 consecutive checks fail to lower the best true residual by 10 %, the
+ * solve has hit its rounding floor and stops there.
+ * info[0] = iterations, info[1] = final true relative residual,
+ * info[2] = 1 if converged, 0 if stopped at the floor or at maxit.
+ * Returns 0, or -1 on allocation failure. */
+int orc_pcg(i64 n, const i64 *rowptr, const i64 *col, const double *val,
+            const double *b, double tol, i64 maxit, double *x, double *info) {
+  size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(double);
+  double *r = malloc(bytes), *z = malloc(bytes), *p = malloc(bytes);
+  double *q = malloc(bytes), *dinv = malloc(bytes), *rt = malloc(bytes);
+  if (!r || !z || !p || !q || !dinv || !rt) {
+    free(r); free(z); free(p); free(q); free(dinv); free(rt);
+    return -1;
+  }
+  for (i64 i = 0; i < n; i++) {
+    double d = 0.0;
+    for (i64 t = rowptr[i]; t < rowptr[i + 1]; t++)
+      if (col[t] == i) d += val[t];
+    dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
+    x[i] = 0.0;
+    r[i] = b[i];
+    z[i] = dinv[i] * r[i];
+    p[i] = z[i];
+  }
+  double bnorm = sqrt(dot(n, b, b));
+  i64 it = 0;
+  double rel = 0.0;
+  if (n > 0 && bnorm > 0.0) {
+    double rz = dot(n, r, z);
+    double best = INFINITY;
+    int stall = 0;
+    rel = 1.0;
+    for (it = 1; it <= maxit; it++) {
+      orc_matvec(n, rowptr, col, val, p, q);
+      double pq = dot(n, p, q);
+      if (!(pq > 0.0)) break;
+      double alpha = rz / pq;
+#pragma omp parallel for schedule(static)
+      for (i64 i = 0; i < n; i++) {
+        x[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+      }
+      double rrel = sqrt(dot(n, r, r)) / bnorm;
+      if (rrel <= tol || it % 50 == 0) {
+        rel = true_residual(n, rowptr, col, val, b, x, rt) / bnorm;
+        if (rel <= tol) break;
+        if (rel < 0.9 * best) { best = rel; stall = 0; }
+        else if (++stall >= 20) break;
+        if (rrel <= tol) memcpy(r, rt, bytes);
+      }
+#pragma omp parallel for schedule(static)
+      for (i64 i = 0; i < n; i++) z[i] = dinv[i] * r[i];
+      double rz_new = dot(n, r, z);
+      double beta = rz_new / rz;
+      rz = rz_new;
+#pragma omp parallel for schedule(static)
+      for (i64 i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+    }
+    if (it > maxit) it = maxit;
+    rel = true_residual(n, rowptr, col, val, b, x, rt) / bnorm;
+  }
+  info[0] = (double)it;
+  info[1] = rel;
+  info[2] = rel <= tol ? 1.0 : 0.0;
+  free(r); free(z); free(p); free(q); free(dinv); free(rt);
+  return 0;
+}
+
+/* Voxel-averaged |E| (Eq. 1 with reading R6): for a conducting voxel,
+ * E_d = omega / (4 h) * sum over its four d-edges of (a_e + Psi_head - Psi_tail),
+ * |E| = sqrt(E_x^2 + E_y^2 + E_z^2); air voxels get 0. psi is on the node grid. */
+void orc_efield(const double *sigma, const double *a, const double *psi,
+                int nx_, int ny_, int nz_, double h, double omega, double *E) {
+  i64 nx = nx_, ny = ny_, nz = nz_;
+  i64 nn = (nx + 1) * (ny + 1) * (nz + 1);
+#pragma omp parallel for schedule(static)
+  for (i64 k = 0; k < nz; k++)
+    for (i64 j = 0; j < ny; j++)
+      for (i64 i = 0; i < nx; i++) {
+        i64 v = (k * ny + j) * nx + i;
+        if (!(sigma[v] > 0.0)) { E[v] = 0.0; continue; }
+        double ex = 0, ey = 0, ez = 0;
+        for (int s = 0; s < 2; s++)
+          for (int t = 0; t < 2; t++) {
+            i64 nxe = node_id(i, j + s, k + t, nx, ny);   /* x edge tail */
+            ex += a[0 * nn + nxe] + psi[node_id(i + 1, j + s, k + t, nx, ny)] - psi[nxe];
+            i64 nye = node_id(i + s, j, k + t, nx, ny);   /* y edge tail */
+            ey += a[1 * nn + nye] + psi[node_id(i + s, j + 1, k + t, nx, ny)] - psi[nye];
+            i64 nze = node_id(i + s, j + t, k, nx, ny);   /* z edge tail */
+            ez += a[2 * nn + nze] + psi[node_id(i + s, j + t, k + 1, nx, ny)] - psi[nze];
+          }
+        double c = omega / (4.0 * h);
+        ex *= c; ey *= c; ez *= c;
+        E[v] = sqrt(ex * ex + ey * ey + ez * ez);
+      }
+}
