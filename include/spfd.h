@@ -1,0 +1,159 @@
+/*
+ * spfd.h -- C ABI of the GB300 SPFD Poisson solver (libspfd.so).
+ *
+ * The library solves the discrete Poisson system of the Co-Simulation Scalar
+ * Potential Finite Difference scheme (Haussmann et al., Eq. 3 in Sec. II)
+ *
+ *     G^T M_k G Psi = -G^T M_k a
+ *
+ * on the nodes of a voxel body model, by conjugate gradients preconditioned
+ * with an operator-dependent geometric multigrid V-cycle, and evaluates the
+ * voxel-averaged induced field of Eq. 1, |E| = |-j omega (a + G Psi)|
+ * (Sec. III-E).  Every array argument is a plain pointer; no framework types
+ * cross this boundary.
+ *
+ * Grid conventions
+ *   voxels  [nz][ny][nx]          (x fastest), FP64 conductivity sigma in S/m
+ *   nodes   [nz+1][ny+1][nx+1]    (voxel corners), FP64 Psi in V*s
+ *   edges   [3][nz+1][ny+1][nx+1] component d in {x,y,z} holds the edge that
+ *           leaves node (i,j,k) in +d; a in V*s (line integral of A); slots
+ *           past the last node along d are ignored.
+ *   h       voxel edge length in m; omega angular frequency in rad/s.
+ *
+ * Method choices the paper leaves open (Sec. II: "M_k ... needs to be
+ * determined"; Sec. III-A: only conducting voxels are unknowns):
+ *   - edge conductance g_e = h * (sum of sigma of the <= 4 voxels around the
+ *     edge) / 4, voxels outside the grid counting as air;
+ *   - a node is an unknown iff an incident edge has g_e > 0; other nodes of
+ *     the returned Psi are 0;
+ *   - Psi is returned with zero mean on each connected conducting component
+ *     (the system fixes it only up to one constant per component);
+ *   - the relative residual is ||b - A Psi||_2 / ||b||_2, recomputed at exit.
+ *
+ * Ownership and streams
+ *   Pointers named *_dev are caller-owned CUDA device pointers, contiguous in
+ *   the layouts above; *_host pointers are caller-owned host memory (pinned
+ *   memory gives the fastest copies).  The context owns every internal buffer
+ *   and releases them in spfd_destroy.  All device work is ordered on the
+ *   stream given to spfd_build; spfd_solve and spfd_solve_host synchronise
+ *   that stream before returning (they report iteration counts), spfd_efield
+ *   does not.
+ *
+ * Errors
+ *   Every entry point returns a status code and never aborts the process.
+ *   spfd_last_error() returns a thread-local description of the last failure.
+ *   A context on which SPFD_ECUDA was returned must only be destroyed.
+ */
+#ifndef SPFD_H
+#define SPFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPFD_OK = 0,
+  SPFD_EINVAL = 1,         /* invalid argument (null, size, NaN/negative sigma, non-finite a) */
+  SPFD_ENOMEM = 2,         /* a device or host allocation failed; nothing leaked */
+  SPFD_ECUDA = 3,          /* a CUDA call or kernel failed */
+  SPFD_ENOTCONVERGED = 4,  /* maxit reached or stagnated; Psi holds the last iterate */
+  SPFD_EINTERNAL = 5       /* a bounded device loop hit its iteration cap */
+} spfd_status;
+
+enum { SPFD_SMOOTHER_JACOBI = 0, SPFD_SMOOTHER_CHEBYSHEV = 1 };
+
+/* Arithmetic of the solve.
+ *   SPFD_FP64:  every operation (operator, V-cycle, Krylov) in FP64.
+ *   SPFD_MIXED: FP64 iterative refinement around an FP32 preconditioned CG
+ *               whose V-cycle keeps the finest-level conductances in BF16
+ *               and accumulates in FP32; residuals, CG dot products and the
+ *               coarsest-level solve stay FP64. */
+enum { SPFD_FP64 = 0, SPFD_MIXED = 1 };
+
+typedef struct {
+  double tol;        /* default relative residual target (used when spfd_solve gets tol <= 0) */
+  int maxit;         /* PCG iteration cap (default 200) */
+  int nu_pre;        /* pre-smoothing sweeps per level (default 1) */
+  int nu_post;       /* post-smoothing sweeps per level (default 1) */
+  int smoother;      /* SPFD_SMOOTHER_* (default Jacobi) */
+  int cheb_degree;   /* Chebyshev polynomial degree (default 2) */
+  int precision;     /* SPFD_FP64 or SPFD_MIXED */
+  int coarse_max;    /* stop coarsening at <= this many unknowns (default 512) */
+  int max_levels;    /* hierarchy depth cap (default 12) */
+  int verbose;       /* 0 = silent; 1 = one line per build/solve on stderr */
+} spfd_opts;
+
+typedef struct {
+  int iters;              /* PCG iterations performed (inner iterations for SPFD_MIXED) */
+  int outer_iters;        /* refinement steps (SPFD_MIXED), 0 for SPFD_FP64 */
+  int converged;          /* 1 if rel_res_true <= tol */
+  double rel_res_true;    /* ||b - A Psi|| / ||b|| recomputed in FP64 at exit */
+  double ms_build;        /* device time of spfd_build */
+  double ms_solve;        /* device time of the last solve */
+  int64_t n_dof;          /* unknowns on the finest level */
+  int n_comp;             /* connected conducting components */
+  int n_levels;           /* multigrid levels */
+  int64_t n_bricks;       /* active 8x8x8 node bricks on the finest level */
+  int64_t bytes_device;   /* device memory held by the context */
+} spfd_info;
+
+typedef struct spfd_ctx spfd_ctx;
+
+/* Fill *opts with the defaults listed above. */
+void spfd_opts_default(spfd_opts *opts);
+
+/* Build the operator of Eq. 3 and its multigrid hierarchy.
+ *   sigma_dev  [nz][ny][nx] FP64 conductivities (>= 0, finite), device.
+ *   nx,ny,nz   voxel counts, each >= 1, with (nx+1)(ny+1)(nz+1) < 2^31.
+ *   h          voxel edge length, > 0.
+ *   opts       NULL for defaults.
+ *   stream     cudaStream_t to order all work of this context on (NULL =
+ *              the legacy default stream).
+ *   out        receives the context (NULL on failure).
+ * An all-air grid is valid: it yields a context with zero unknowns. */
+spfd_status spfd_build(const double *sigma_dev, int nx, int ny, int nz,
+                       double h, const spfd_opts *opts, void *stream,
+                       spfd_ctx **out);
+
+/* Solve Eq. 3 for the edge potentials a and write Psi.
+ *   a_dev    [3][nz+1][ny+1][nx+1] FP64, device (finite on every edge that
+ *            touches a conducting voxel).
+ *   tol      relative residual target (> 0), or <= 0 for opts.tol.
+ *   psi_dev  [nz+1][ny+1][nx+1] FP64 output, device.
+ *   info     optional report (may be NULL).
+ * Returns SPFD_ENOTCONVERGED (with Psi written) if tol was not reached. */
+spfd_status spfd_solve(spfd_ctx *ctx, const double *a_dev, double tol,
+                       double *psi_dev, spfd_info *info);
+
+/* spfd_solve with host arrays: copies a to the device, solves, copies Psi
+ * back, all on the context's stream.  Device staging buffers are allocated on
+ * first use and kept by the context. */
+spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host, double tol,
+                            double *psi_host, spfd_info *info);
+
+/* Voxel-averaged |E| of Eq. 1: for each conducting voxel,
+ *   E_d = omega / (4 h) * sum over its four d-edges of (a_e + Psi_head - Psi_tail),
+ *   |E| = sqrt(E_x^2 + E_y^2 + E_z^2); air voxels get 0.
+ *   a_dev    as in spfd_solve;  psi_dev  [nz+1][ny+1][nx+1] FP64, device.
+ *   E_dev    [nz][ny][nx] FP64 output in V/m, device.
+ * Asynchronous on the context's stream. */
+spfd_status spfd_efield(spfd_ctx *ctx, const double *a_dev,
+                        const double *psi_dev, double omega, double *E_dev);
+
+/* Report of the context (sizes, last solve); does not synchronise. */
+spfd_status spfd_get_info(const spfd_ctx *ctx, spfd_info *info);
+
+/* Release every resource of the context.  NULL is a no-op. */
+void spfd_destroy(spfd_ctx *ctx);
+
+/* Thread-local message for the most recent failing call on this thread. */
+const char *spfd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPFD_H */

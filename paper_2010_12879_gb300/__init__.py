@@ -1,0 +1,237 @@
+"""GB300 SPFD Poisson solver -- Python binding of ``libspfd.so``.
+
+The binding only marshals arguments: it passes device pointers, sizes and the
+CUDA stream of PyTorch tensors to the C ABI declared in ``include/spfd.h``;
+every step of the computation runs in the library's CUDA kernels.  There is
+no fallback: if ``libspfd.so`` is missing or no GPU is present, the calls
+raise.
+
+Functions mirror the C entry points (``spfd_build``, ``spfd_solve``,
+``spfd_solve_host``, ``spfd_efield``, ``spfd_get_info``, ``spfd_destroy``,
+``spfd_last_error``, ``spfd_opts_default``); :class:`Solver` wraps them for
+``torch.float64`` tensors.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB as LIB_PATH
+
+SPFD_OK, SPFD_EINVAL, SPFD_ENOMEM, SPFD_ECUDA, SPFD_ENOTCONVERGED, SPFD_EINTERNAL = range(6)
+STATUS_NAMES = {0: "SPFD_OK", 1: "SPFD_EINVAL", 2: "SPFD_ENOMEM", 3: "SPFD_ECUDA",
+                4: "SPFD_ENOTCONVERGED", 5: "SPFD_EINTERNAL"}
+SPFD_SMOOTHER_JACOBI, SPFD_SMOOTHER_CHEBYSHEV = 0, 1
+SPFD_FP64, SPFD_MIXED = 0, 1
+
+# Names declared in include/spfd.h (checked against the library by the tests).
+EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
+           "spfd_efield", "spfd_get_info", "spfd_destroy", "spfd_last_error")
+
+
+class SpfdOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("cheb_degree", ctypes.c_int),
+                ("precision", ctypes.c_int), ("coarse_max", ctypes.c_int),
+                ("max_levels", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class SpfdInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_res_true", ctypes.c_double),
+                ("ms_build", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("n_dof", ctypes.c_int64), ("n_comp", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("n_bricks", ctypes.c_int64),
+                ("bytes_device", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class SpfdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libspfd.so (built by ``paper_2010_12879_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, dp = ctypes.c_void_p, ctypes.c_double
+            L.spfd_opts_default.argtypes = [ctypes.POINTER(SpfdOpts)]
+            L.spfd_opts_default.restype = None
+            L.spfd_build.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                     ctypes.POINTER(SpfdOpts), vp, ctypes.POINTER(vp)]
+            L.spfd_build.restype = ctypes.c_int
+            L.spfd_solve.argtypes = [vp, vp, dp, vp, ctypes.POINTER(SpfdInfo)]
+            L.spfd_solve.restype = ctypes.c_int
+            L.spfd_solve_host.argtypes = [vp, vp, dp, vp, ctypes.POINTER(SpfdInfo)]
+            L.spfd_solve_host.restype = ctypes.c_int
+            L.spfd_efield.argtypes = [vp, vp, vp, dp, vp]
+            L.spfd_efield.restype = ctypes.c_int
+            L.spfd_get_info.argtypes = [vp, ctypes.POINTER(SpfdInfo)]
+            L.spfd_get_info.restype = ctypes.c_int
+            L.spfd_destroy.argtypes = [vp]
+            L.spfd_destroy.restype = None
+            L.spfd_last_error.argtypes = []
+            L.spfd_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def spfd_last_error() -> str:
+    return lib().spfd_last_error().decode(errors="replace")
+
+
+def _check(status: int, allow=(SPFD_OK,)):
+    if status not in allow:
+        raise SpfdError(status, spfd_last_error())
+    return status
+
+
+def spfd_opts_default() -> SpfdOpts:
+    o = SpfdOpts()
+    lib().spfd_opts_default(ctypes.byref(o))
+    return o
+
+
+def spfd_build(sigma_ptr: int, nx: int, ny: int, nz: int, h: float,
+               opts: SpfdOpts | None = None, stream: int = 0) -> int:
+    """Raw entry point: returns the context handle (an int)."""
+    out = ctypes.c_void_p()
+    st = lib().spfd_build(ctypes.c_void_p(sigma_ptr), nx, ny, nz, float(h),
+                          ctypes.byref(opts) if opts is not None else None,
+                          ctypes.c_void_p(stream), ctypes.byref(out))
+    _check(st)
+    return out.value
+
+
+def spfd_solve(ctx: int, a_ptr: int, tol: float, psi_ptr: int):
+    info = SpfdInfo()
+    st = lib().spfd_solve(ctypes.c_void_p(ctx), ctypes.c_void_p(a_ptr), float(tol),
+                          ctypes.c_void_p(psi_ptr), ctypes.byref(info))
+    _check(st, allow=(SPFD_OK, SPFD_ENOTCONVERGED))
+    return st, info
+
+
+def spfd_solve_host(ctx: int, a_ptr: int, tol: float, psi_ptr: int):
+    info = SpfdInfo()
+    st = lib().spfd_solve_host(ctypes.c_void_p(ctx), ctypes.c_void_p(a_ptr),
+                               float(tol), ctypes.c_void_p(psi_ptr), ctypes.byref(info))
+    _check(st, allow=(SPFD_OK, SPFD_ENOTCONVERGED))
+    return st, info
+
+
+def spfd_efield(ctx: int, a_ptr: int, psi_ptr: int, omega: float, E_ptr: int):
+    _check(lib().spfd_efield(ctypes.c_void_p(ctx), ctypes.c_void_p(a_ptr),
+                             ctypes.c_void_p(psi_ptr), float(omega),
+                             ctypes.c_void_p(E_ptr)))
+
+
+def spfd_get_info(ctx: int) -> SpfdInfo:
+    info = SpfdInfo()
+    _check(lib().spfd_get_info(ctypes.c_void_p(ctx), ctypes.byref(info)))
+    return info
+
+
+def spfd_destroy(ctx: int):
+    lib().spfd_destroy(ctypes.c_void_p(ctx))
+
+
+class Solver:
+    """Context bound to one conductivity model.
+
+    ``sigma`` is a contiguous ``torch.float64`` CUDA tensor of shape
+    ``(nz, ny, nx)``; arrays follow the layouts documented in
+    ``include/spfd.h``.  Work is ordered on ``stream`` (default: the current
+    PyTorch stream at construction).
+    """
+
+    def __init__(self, sigma, h: float, opts: SpfdOpts | None = None,
+                 stream=None, **kw):
+        import torch
+        if not (sigma.is_cuda and sigma.dtype == torch.float64 and sigma.dim() == 3
+                and sigma.is_contiguous()):
+            raise ValueError("sigma must be a contiguous float64 CUDA tensor (nz, ny, nx)")
+        if opts is None:
+            opts = spfd_opts_default()
+        for k, v in kw.items():
+            setattr(opts, k, v)
+        self.opts = opts
+        self.stream = stream if stream is not None else torch.cuda.current_stream(sigma.device)
+        self.device = sigma.device
+        nz, ny, nx = sigma.shape
+        self.dims = (nx, ny, nz)
+        self.h = float(h)
+        with torch.cuda.device(sigma.device):
+            self.ctx = spfd_build(sigma.data_ptr(), nx, ny, nz, h, opts,
+                                  self.stream.cuda_stream)
+
+    @property
+    def node_shape(self):
+        nx, ny, nz = self.dims
+        return (nz + 1, ny + 1, nx + 1)
+
+    def _check_edges(self, a):
+        import torch
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                and tuple(a.shape) == (3,) + self.node_shape):
+            raise ValueError(f"a must be a contiguous float64 CUDA tensor of shape {(3,) + self.node_shape}")
+
+    def solve(self, a, tol: float = 0.0, psi=None):
+        """Psi for edge potentials ``a``; returns (psi, info dict, status)."""
+        import torch
+        self._check_edges(a)
+        if psi is None:
+            psi = torch.empty(self.node_shape, dtype=torch.float64, device=a.device)
+        st, info = spfd_solve(self.ctx, a.data_ptr(), tol, psi.data_ptr())
+        return psi, info.as_dict(), st
+
+    def solve_host(self, a_host, psi_host, tol: float = 0.0):
+        """Host-array variant (``a_host``/``psi_host``: contiguous CPU float64
+        tensors, ideally pinned); returns (info dict, status)."""
+        st, info = spfd_solve_host(self.ctx, a_host.data_ptr(), tol, psi_host.data_ptr())
+        return info.as_dict(), st
+
+    def efield(self, a, psi, omega: float, E=None):
+        import torch
+        self._check_edges(a)
+        nx, ny, nz = self.dims
+        if E is None:
+            E = torch.empty((nz, ny, nx), dtype=torch.float64, device=a.device)
+        spfd_efield(self.ctx, a.data_ptr(), psi.data_ptr(), omega, E.data_ptr())
+        return E
+
+    def info(self) -> dict:
+        return spfd_get_info(self.ctx).as_dict()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            spfd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,182 @@
+// Internal declarations shared by the translation units of libspfd.
+//
+// Data layout.  Every multigrid level stores its node unknowns in 8x8x8-node
+// bricks; only bricks that touch an unknown are allocated.  A level is
+// described by its node dimensions (NX, NY, NZ), its brick-grid dimensions
+// (MX, MY, MZ), a dense brick map [MZ][MY][MX] -> brick id (or -1) and the
+// brick coordinates of each active brick.  Node (lx, ly, lz) of brick b lives
+// at slot b*512 + (lz*8 + ly)*8 + lx of every per-node array.  Slots of nodes
+// that are not unknowns (air, or past the grid edge) hold zero operator rows
+// and zero vector entries, so kernels never branch on activity for
+// correctness.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace spfd {
+
+constexpr int BE = 8;     // brick edge in nodes
+constexpr int BV = 512;   // nodes per brick
+constexpr int NT = 512;   // threads per brick-kernel block (one node each)
+
+// Stencil offset index of (dx, dy, dz) in {-1,0,1}^3; 13 is the centre.
+__host__ __device__ __forceinline__ constexpr int sidx(int dx, int dy, int dz) {
+  return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+}
+
+struct Grid {
+  int NX, NY, NZ;       // nodes per axis
+  int MX, MY, MZ;       // bricks per axis
+  int nb;               // active bricks
+  const int *bmap;      // [MZ][MY][MX] brick id or -1
+  const int4 *bco;      // [nb] brick coordinates (x, y, z, 0)
+};
+
+// Brick id of node (i, j, k) or -1 (outside the grid or brick not stored).
+__device__ __forceinline__ int brick_at(const Grid &g, int i, int j, int k) {
+  if ((unsigned)i >= (unsigned)g.NX || (unsigned)j >= (unsigned)g.NY ||
+      (unsigned)k >= (unsigned)g.NZ)
+    return -1;
+  return __ldg(&g.bmap[((k >> 3) * g.MY + (j >> 3)) * g.MX + (i >> 3)]);
+}
+
+// Slot of node (i, j, k) or -1.
+__device__ __forceinline__ int slot_at(const Grid &g, int i, int j, int k) {
+  int b = brick_at(g, i, j, k);
+  if (b < 0) return -1;
+  return (b << 9) | ((k & 7) << 6) | ((j & 7) << 3) | (i & 7);
+}
+
+// Slot of the neighbour (lx+dx, ly+dy, lz+dz) of a node of brick b at brick
+// coordinates bc; inside the brick it is pure arithmetic.
+__device__ __forceinline__ int slot_nb(const Grid &g, int b, int4 bc, int lx,
+                                       int ly, int lz, int dx, int dy, int dz) {
+  int x = lx + dx, y = ly + dy, z = lz + dz;
+  if ((unsigned)(x | y | z) < 8u) return (b << 9) | (z << 6) | (y << 3) | x;
+  return slot_at(g, bc.x * 8 + x, bc.y * 8 + y, bc.z * 8 + z);
+}
+
+// Device scalars of the Krylov loop, reduction scratch and status flags.
+struct Scalars {
+  double bb;        // ||b||^2
+  double rr;        // ||r||^2
+  double rz;        // r . z
+  double rz_old;
+  double pq;        // p . A p
+  double alpha, beta;
+  double zsum;      // sum of z over the single component (projection)
+  double rsum;      // sum of r over the unknowns (projection of r)
+  double aux[8];    // misc results (power iteration, refinement)
+  unsigned int ticket[8];  // last-block counters, one per reduction site
+  int status;       // SPFD_DEV_* bits
+};
+
+enum : int {
+  DEV_BAD_SIGMA = 1,     // NaN / negative / infinite conductivity
+  DEV_BAD_A = 2,         // non-finite edge potential on a conducting edge
+  DEV_UF_CAP = 4,        // union-find loop hit its iteration cap
+};
+
+// ---------------------------------------------------------------- launchers
+// Setup (spfd_setup.cu)
+void launch_sigma_flags(const double *sigma, int nx, int ny, int nz, int MX,
+                        int MY, unsigned char *flags, unsigned char *mask,
+                        int *status, cudaStream_t st);
+void launch_build_fine(const Grid &g, const double *sigma, int nx, int ny,
+                       int nz, double h, double *gx, double *diag,
+                       double *dinv, cudaStream_t st);
+void launch_components(const Grid &g, const double *gx, int *parent,
+                       int *status, cudaStream_t st);
+void launch_root_counts(const Grid &g, const int *parent, int *counts,
+                        cudaStream_t st);
+void launch_assign_comp(const Grid &g, const int *parent, const int *offsets,
+                        int *comp, cudaStream_t st);
+void launch_comp_sizes(const Grid &g, const int *comp, int *sizes,
+                       cudaStream_t st);
+void launch_interp_weights(const Grid &gf, const double *gx, const double *st27,
+                           const double *diag, double *W, cudaStream_t st);
+void launch_galerkin(const Grid &gf, const Grid &gc, const double *gx,
+                     const double *st27f, const double *diagf, const double *W,
+                     double *stc, cudaStream_t st);
+void launch_symmetrize(const Grid &gc, double *stc, cudaStream_t st);
+void launch_pack_P(const Grid &gf, const Grid &gc, const double *W, double *P,
+                   cudaStream_t st);
+void launch_coarse_diag(const Grid &gc, const double *stc, double thresh,
+                        double *diag, double *dinv, cudaStream_t st);
+
+// V-cycle pieces (spfd_cycle.cu); T = vector type, C = 7-point coefficient type.
+template <typename T, typename C>
+void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
+                      const T *b, T *r, cudaStream_t st);
+template <typename T>
+void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
+                       T *r, cudaStream_t st);
+template <typename T>
+void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
+                         cudaStream_t st);
+// First level-0 sweep with the projection of the right-hand side fused in:
+// b <- b - (sum b)/n on the unknowns (one component), then x = wdinv * b.
+template <typename T>
+void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
+                              const Scalars *sc, double inv_ndof,
+                              cudaStream_t st);
+template <typename T, typename C>
+void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
+                    const T *xin, const T *b, T *xout, cudaStream_t st);
+template <typename T>
+void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
+                     const T *b, T *xout, cudaStream_t st);
+template <typename T>
+void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
+                     T *bc, cudaStream_t st);
+template <typename T>
+void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
+                    T *ef, cudaStream_t st);
+template <typename T>
+void launch_coarse_solve(int m, const int *idx, const double *Binv,
+                         const T *b, T *x, cudaStream_t st);
+
+// Krylov loop, RHS, scatter, |E| (spfd_krylov.cu)
+template <typename T>
+void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
+                      T *q, Scalars *sc, double *partials, cudaStream_t st);
+template <typename T>
+void launch_update_xr(int nb, T *x, T *r, const T *p, const T *q, Scalars *sc,
+                      double *partials, cudaStream_t st);
+template <typename T>
+void launch_dot_rz(int nb, const T *r, const T *z, const int *comp,
+                   Scalars *sc, double *partials, int first, cudaStream_t st);
+template <typename T>
+void launch_comp_sum(int nb, const T *v, const int *comp, double *csum,
+                     cudaStream_t st);
+template <typename T>
+void launch_pupdate(int nb, T *p, const T *z, const int *comp,
+                    const Scalars *sc, const double *csum, const int *csize,
+                    double inv_ndof, cudaStream_t st);
+template <typename T>
+void launch_sub_mean(int nb, T *v, const int *comp, const Scalars *sc,
+                     int aux_slot, const double *csum, const int *csize,
+                     double inv_ndof, cudaStream_t st);
+template <typename T>
+void launch_dot(int nb, const T *x, const T *y, const int *comp, Scalars *sc,
+                double *partials, int slot, cudaStream_t st);
+template <typename T>
+void launch_scatter(const Grid &g, const T *x, const int *comp, double *psi,
+                    cudaStream_t st);
+void launch_rhs(const Grid &g, const double *gx, const double *a, double *b,
+                int *status, cudaStream_t st);
+void launch_gather(const Grid &g, const double *psi, const int *comp, double *x,
+                   cudaStream_t st);
+void launch_efield(const unsigned char *mask, const double *a,
+                   const double *psi, int nx, int ny, int nz, double h,
+                   double omega, double *E, cudaStream_t st);
+void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st);
+void launch_power_step(int nb, const double *r, const double *dinv, double *w,
+                       Scalars *sc, double *partials, cudaStream_t st);
+void launch_scale(int nb, double *v, double f, cudaStream_t st);
+void launch_scaled_copy(int nb, const double *src, double f, double *dst,
+                        cudaStream_t st);
+
+}  // namespace spfd

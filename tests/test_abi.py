@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+entry point declared in include/spfd.h, and rejects invalid arguments before
+touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def spfd():
+    from paper_2010_12879_gb300 import build as b
+    b.build()
+    import paper_2010_12879_gb300 as m
+    m.lib()
+    return m
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(spfd_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+def test_exports_every_declared_symbol(spfd):
+    declared = _declared()
+    assert declared, "no declarations found"
+    assert declared == set(spfd.EXPORTS)
+    L = spfd.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_opts_default(spfd):
+    o = spfd.spfd_opts_default()
+    assert o.tol == 1e-8 and o.maxit == 200 and o.nu_pre == 1 and o.nu_post == 1
+    assert o.precision == spfd.SPFD_FP64 and o.coarse_max == 512
+
+
+def _raw_build(spfd, sigma, nx, ny, nz, h, out=True):
+    L = spfd.lib()
+    handle = ctypes.c_void_p()
+    st = L.spfd_build(ctypes.c_void_p(sigma), nx, ny, nz, h, None, None,
+                      ctypes.byref(handle) if out else None)
+    return st, handle.value
+
+
+@pytest.mark.parametrize("args", [
+    (0, 4, 4, 4, 2e-3),            # null sigma
+    (8, 0, 4, 4, 2e-3),            # zero dims
+    (8, 4, -1, 4, 2e-3),
+    (8, 4, 4, 4, 0.0),             # h <= 0
+    (8, 4, 4, 4, float("nan")),
+    (8, 4000, 4000, 4000, 2e-3),   # > 2^31 nodes
+])
+def test_build_rejects_invalid_arguments(spfd, args):
+    st, h = _raw_build(spfd, *args)
+    assert st == spfd.SPFD_EINVAL and h is None
+    assert spfd.spfd_last_error()
+
+
+def test_build_rejects_null_out(spfd):
+    st, _ = _raw_build(spfd, 8, 4, 4, 4, 2e-3, out=False)
+    assert st == spfd.SPFD_EINVAL
+
+
+def test_null_context_calls(spfd):
+    L = spfd.lib()
+    info = spfd.SpfdInfo()
+    assert L.spfd_solve(None, ctypes.c_void_p(8), 1e-8, ctypes.c_void_p(8), ctypes.byref(info)) == spfd.SPFD_EINVAL
+    assert L.spfd_solve_host(None, ctypes.c_void_p(8), 1e-8, ctypes.c_void_p(8), None) == spfd.SPFD_EINVAL
+    assert L.spfd_efield(None, ctypes.c_void_p(8), ctypes.c_void_p(8), 1.0, ctypes.c_void_p(8)) == spfd.SPFD_EINVAL
+    assert L.spfd_get_info(None, ctypes.byref(info)) == spfd.SPFD_EINVAL
+    L.spfd_destroy(None)  # no-op
+
+
+def test_invalid_options_rejected(spfd):
+    L = spfd.lib()
+    o = spfd.spfd_opts_default()
+    o.maxit = 0
+    handle = ctypes.c_void_p()
+    st = L.spfd_build(ctypes.c_void_p(8), 4, 4, 4, 2e-3, ctypes.byref(o), None, ctypes.byref(handle))
+    assert st == spfd.SPFD_EINVAL
+
+
+def test_without_gpu_build_reports_cuda_error(spfd):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, h = _raw_build(spfd, 8, 4, 4, 4, 2e-3)
+    assert st == spfd.SPFD_ECUDA and h is None
