@@ -1,0 +1,411 @@
+"""Benchmark: the SPFD hot path on the 2 mm, ~9.25M-unknown body phantom.
+
+One step is one pass of the whole hot path over the full-size workload
+(256 x 160 x 896 voxels, h = 2 mm, 9,250,062 conducting nodes, loop source):
+  spfd_build  -- edge conductances, unknowns, components, multigrid setup,
+  spfd_solve  -- right-hand side, multigrid-preconditioned CG to a relative
+                 residual of 1e-8, projection, Psi on the node grid,
+  spfd_efield -- voxel-averaged |E|.
+The headline line is the plain FP64 form; the mixed-precision form (FP64
+refinement around an FP32/BF16 V-cycle CG) is timed on the same inputs and
+reported beside it.  Inputs (3.7 GB working set) exceed the 129 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own phantom copy (replicas: the
+solve has no data-parallel split on one node in this design) and rank 0
+prints the line.  ``--impl reference`` times the CPU FP64 oracle on the host
+cores instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2mm phantom solve time (s) to 1e-8 rel residual; stencil HBM GB/s vs peak; mixed vs FP64"
+WORKLOAD = "body phantom 256x160x896 voxels, h=2 mm, 9,250,062 unknowns, loop source R=0.3 m, I=1000 A, 0.4 m below"
+TOL = 1e-8
+OMEGA = 2 * 3.141592653589793 * 85e3
+# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+GOLDEN = os.path.join(ROOT, "tests", "golden", "body_2mm_oracle.json")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return rank, world, local, dist
+    return 0, 1, local, None
+
+
+def _inputs():
+    from spfd_inputs import body_phantom, loop_potential
+    ph = body_phantom()
+    a = loop_potential(ph.dims, ph.h, ph.origin)
+    return ph, a
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2010_12879_gb300 as spfd
+
+    rank, world, local, dist = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ph, a = _inputs()
+    sig = torch.from_numpy(ph.sigma).to(dev)
+    ad = torch.from_numpy(a).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    nz, ny, nx = ph.sigma.shape
+    psi = torch.empty((nz + 1, ny + 1, nx + 1), dtype=torch.float64, device=dev)
+    E = torch.empty((nz, ny, nx), dtype=torch.float64, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+
+    def one_step(precision, profile):
+        opts = spfd.spfd_opts_default()
+        opts.precision = precision
+        opts.profile = 1 if profile else 0
+        t = {}
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        S = spfd.Solver(sig, ph.h, opts, stream=stream)
+        build_launches = S.info()["launches"]
+        e[1].record(stream)
+        _, info, st = S.solve(ad, TOL, psi)
+        e[2].record(stream)
+        S.efield(ad, psi, OMEGA, E)
+        e[3].record(stream)
+        torch.cuda.synchronize(dev)
+        t["build_ms"] = e[0].elapsed_time(e[1])
+        t["solve_ms"] = e[1].elapsed_time(e[2])
+        t["efield_ms"] = e[2].elapsed_time(e[3])
+        t["step_ms"] = e[0].elapsed_time(e[3])
+        # kernels of this library launched in the step: build + solve + |E|
+        t["launches"] = build_launches + info["launches"] + 1
+        binfo = dict(info)
+        stats = S.kernel_stats() if profile else []
+        S.close()
+        assert st == spfd.SPFD_OK and info["converged"], spfd.spfd_last_error()
+        return t, binfo, stats
+
+    def timed(precision, steps, warmup, profile):
+        for _ in range(warmup):
+            one_step(precision, profile)
+        barrier()
+        rec = []
+        with ClockSampler(local) as clk:
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                rec.append(one_step(precision, profile))
+            barrier()
+            wall = time.perf_counter() - t0
+        return rec, wall, clk.summary()
+
+    hbm_peak, peak_kind = _peaks()
+    K, W = args.steps, args.warmup
+    rec64, wall64, clk64 = timed(spfd.SPFD_FP64, K, W, True)
+    recmx, wallmx, clkmx = timed(spfd.SPFD_MIXED, K, max(1, W // 2), True)
+
+    def agg(rec):
+        keys = rec[0][0].keys()
+        out = {k: statistics.mean(r[0][k] for r in rec) for k in keys if rec[0][0][k] is not None}
+        out["std_step_ms"] = statistics.pstdev(r[0]["step_ms"] for r in rec)
+        info = rec[-1][1]
+        fam = {}
+        for r in rec:
+            for s in r[2]:
+                f = fam.setdefault(s["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+                for k in ("launches", "ms", "bytes", "flops"):
+                    f[k] += s[k]
+        return out, info, fam
+
+    t64, info64, fam64 = agg(rec64)
+    tmx, infomx, fammx = agg(recmx)
+
+    # max over ranks of the mean step time
+    step_ms = t64["step_ms"]
+    if dist:
+        v = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        step_ms = float(v.item())
+
+    def roofline(fam, kind):
+        solve_fams = {k: v for k, v in fam.items() if not k.startswith("setup")}
+        name, f = max(solve_fams.items(), key=lambda kv: kv[1]["ms"])
+        per = f["ms"] / f["launches"]
+        bytes_per = f["bytes"] / f["launches"]
+        flops_per = f["flops"] / f["launches"]
+        gbs = bytes_per / (per * 1e-3) / 1e9
+        tfl = flops_per / (per * 1e-3) / 1e12
+        # FP64 stencils sit above the machine balance of the FP64 pipe
+        # (flop/byte > FP64 peak / HBM peak): bound by the FP64 ALU
+        alu = name.endswith("_f64") and flops_per / max(bytes_per, 1) > FP64_PEAK_TFLOPS * 1e12 / (hbm_peak * 1e9)
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+        if os.path.exists(tf):
+            try:
+                with open(tf) as fh:
+                    traffic = json.load(fh).get(name)
+            except Exception:
+                traffic = None
+        share = f["ms"] / sum(v["ms"] for v in solve_fams.values())
+        if alu:
+            return {"kernel": name, "bound": "alu", "achieved": round(tfl, 4),
+                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                    "frac": round(tfl / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "peak_kind": "FP64 pipe, derived from unit counts and clocks",
+                    "algorithmic_GBs": round(gbs, 1), "avg_launch_ms": round(per, 4),
+                    "launches": f["launches"], "share_of_solve_kernel_time": round(share, 3)}
+        return {"kernel": name, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
+                "peak_kind": peak_kind, "avg_launch_ms": round(per, 4),
+                "launches": f["launches"], "share_of_solve_kernel_time": round(share, 3)}
+
+    roof64 = roofline(fam64, "fp64")
+    roofmx = roofline(fammx, "mixed")
+
+    # end to end through the public API with host arrays: sigma and a copied
+    # from pinned host memory, Psi and |E| copied back, all inside the region
+    e2e = None
+    if not args.no_e2e:
+        sig_h = torch.from_numpy(ph.sigma).pin_memory()
+        a_h = torch.from_numpy(a).pin_memory()
+        psi_h = torch.empty(psi.shape, dtype=torch.float64).pin_memory()
+        E_h = torch.empty(E.shape, dtype=torch.float64).pin_memory()
+        times = []
+        for i in range(W + K):
+            barrier()
+            t0 = time.perf_counter()
+            sig_d = sig_h.to(dev, non_blocking=True)
+            a_d = a_h.to(dev, non_blocking=True)
+            S = spfd.Solver(sig_d, ph.h, stream=stream)
+            S.solve(a_d, TOL, psi)
+            S.efield(a_d, psi, OMEGA, E)
+            psi_h.copy_(psi, non_blocking=True)
+            E_h.copy_(E, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            S.close()
+            if i >= W:
+                times.append(dt)
+        e2e = {"value": round(statistics.mean(times) / world, 6), "unit": "s",
+               "h2d_bytes_per_step": int(sig_h.numel() * 8 + a_h.numel() * 8),
+               "d2h_bytes_per_step": int(psi_h.numel() * 8 + E_h.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ph, a, iters=args.cpu_iters)
+
+    if rank == 0:
+        n_launch = int(round(t64["launches"] * K))
+        line = {
+            "metric": METRIC, "value": round(step_ms / 1000.0 / world, 6), "unit": "s",
+            "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(step_ms, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded ellipsoid body phantom, 40 Voronoi tissues, analytic loop potential)",
+            "config": {"workload": WORKLOAD, "tol": TOL, "precision": "fp64",
+                       "step": "spfd_build + spfd_solve + spfd_efield",
+                       "l2": "inputs larger than L2 (3.7 GB device working set vs 129 MB L2)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "breakdown_ms": {k: round(v, 3) for k, v in t64.items()},
+            "solve_s": round(t64["solve_ms"] / 1000.0, 6),
+            "iters": info64["iters"], "rel_res_true": info64["rel_res_true"],
+            "n_dof": info64["n_dof"], "n_levels": info64["n_levels"],
+            "mixed": {"ms_per_step": round(tmx["step_ms"], 3),
+                      "solve_s": round(tmx["solve_ms"] / 1000.0, 6),
+                      "breakdown_ms": {k: round(v, 3) for k, v in tmx.items()},
+                      "iters": infomx["iters"], "outer_iters": infomx["outer_iters"],
+                      "rel_res_true": infomx["rel_res_true"],
+                      "solve_speedup_vs_fp64": round(t64["solve_ms"] / tmx["solve_ms"], 3),
+                      "step_speedup_vs_fp64": round(t64["step_ms"] / tmx["step_ms"], 3),
+                      "roofline": roofmx, "clocks": clkmx},
+            "roofline": roof64,
+            "kernels_fp64": {k: {"launches": v["launches"] // K, "ms": round(v["ms"] / K, 4),
+                                 "GBs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                             for k, v in sorted(fam64.items(), key=lambda kv: -kv[1]["ms"])},
+            "kernels_mixed": {k: {"launches": v["launches"] // K, "ms": round(v["ms"] / K, 4),
+                                  "GBs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                              for k, v in sorted(fammx.items(), key=lambda kv: -kv[1]["ms"])},
+            "gpu_launches": n_launch,
+            "clocks": clk64,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "timing": "CUDA events on the launch stream; kernel families timed with per-launch events (profile mode)",
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(ph, a, iters=30, record=None):
+    """The oracle (CPU, FP64, as it stands) on a bounded sample of the same
+    workload: assembly + right-hand side, `iters` Jacobi-PCG iterations, and
+    |E|; the solve is extrapolated to the oracle's own iteration count for
+    1e-8 on this workload (tests/golden/body_2mm_oracle.json)."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    sys_ = oracle.assemble(ph.sigma, ph.h)
+    b = oracle.project(sys_, oracle.rhs(sys_, a))
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, info = oracle.pcg(sys_, b, tol=1e-300, maxit=iters)
+    t_it = (time.perf_counter() - t0) / max(info["iters"], 1)
+    psi = sys_.scatter(oracle.project(sys_, x))
+    t0 = time.perf_counter()
+    oracle.efield(ph.sigma, a, psi, ph.h, OMEGA)
+    t_e = time.perf_counter() - t0
+    n_it, src = None, None
+    try:
+        with open(GOLDEN) as f:
+            g = json.load(f)
+        n_it = int(g["tol_1e-08"]["iters"])
+        src = "tests/golden/body_2mm_oracle.json"
+    except Exception:
+        pass
+    if n_it is None:
+        return {"value": None, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": f"assembly + {info['iters']} Jacobi-PCG iterations ({t_it:.4f} s/iter); "
+                          "iteration count to 1e-8 unavailable"}
+    total = t_setup + n_it * t_it + t_e
+    return {"value": round(total, 3), "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"full-size workload: assembly+rhs {t_setup:.2f} s, {info['iters']} Jacobi-PCG "
+                       f"iterations timed ({t_it:.4f} s/iter) and extrapolated to the oracle's "
+                       f"{n_it} iterations to 1e-8 ({src}), |E| {t_e:.2f} s")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ph, a = _inputs()
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        c = cpu_baseline(ph, a, iters=args.cpu_iters)
+        if i >= args.warmup and c["value"] is not None:
+            vals.append(c["value"])
+        last = c
+    v = round(statistics.mean(vals), 3) if vals else None
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1000 if v else None,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded ellipsoid body phantom, 40 Voronoi tissues, analytic loop potential)",
+            "config": {"workload": WORKLOAD, "tol": TOL, "precision": "fp64",
+                       "step": "oracle assembly + Jacobi-PCG solve + |E|"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-iters", type=int, default=30)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

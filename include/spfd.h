@@ -84,6 +84,8 @@ typedef struct {
   int coarse_max;    /* stop coarsening at <= this many unknowns (default 512) */
   int max_levels;    /* hierarchy depth cap (default 12) */
   int verbose;       /* 0 = silent; 1 = one line per build/solve on stderr */
+  int profile;       /* 1 = time every kernel launch with CUDA events (see
+                        spfd_kernel_stats); adds ~2 us of host work per launch */
 } spfd_opts;
 
 typedef struct {
@@ -98,7 +100,17 @@ typedef struct {
   int n_levels;           /* multigrid levels */
   int64_t n_bricks;       /* active 8x8x8 node bricks on the finest level */
   int64_t bytes_device;   /* device memory held by the context */
+  int64_t launches;       /* kernels launched by the last build / solve call */
 } spfd_info;
+
+/* Per-kernel-family timing collected while opts.profile is set. */
+typedef struct {
+  const char *name;       /* family, e.g. "jacobi7_l0" (static string) */
+  int64_t launches;       /* launches timed since the last reset */
+  double ms;              /* summed device time of those launches */
+  double bytes;           /* algorithmic DRAM bytes of those launches */
+  double flops;           /* FP64 (or FP32) operations of those launches */
+} spfd_kernel_stat;
 
 typedef struct spfd_ctx spfd_ctx;
 
@@ -145,6 +157,15 @@ spfd_status spfd_efield(spfd_ctx *ctx, const double *a_dev,
 
 /* Report of the context (sizes, last solve); does not synchronise. */
 spfd_status spfd_get_info(const spfd_ctx *ctx, spfd_info *info);
+
+/* Kernel timing of a context built with opts.profile = 1.
+ *   stats  caller array of at least max entries (may be NULL when max = 0).
+ *   n      receives the number of families (may exceed max).
+ *   reset  1 = clear the accumulated times after copying them out.
+ * Synchronises the context's stream.  Algorithmic bytes count each array
+ * element a kernel must read or write once (halo re-reads not counted). */
+spfd_status spfd_kernel_stats(spfd_ctx *ctx, spfd_kernel_stat *stats, int max,
+                              int *n, int reset);
 
 /* Release every resource of the context.  NULL is a no-op. */
 void spfd_destroy(spfd_ctx *ctx);

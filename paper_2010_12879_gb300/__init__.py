@@ -28,7 +28,8 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 
 # Names declared in include/spfd.h (checked against the library by the tests).
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
-           "spfd_efield", "spfd_get_info", "spfd_destroy", "spfd_last_error")
+           "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
+           "spfd_last_error")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -36,7 +37,8 @@ class SpfdOpts(ctypes.Structure):
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("cheb_degree", ctypes.c_int),
                 ("precision", ctypes.c_int), ("coarse_max", ctypes.c_int),
-                ("max_levels", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("max_levels", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class SpfdInfo(ctypes.Structure):
@@ -45,10 +47,16 @@ class SpfdInfo(ctypes.Structure):
                 ("ms_build", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("n_dof", ctypes.c_int64), ("n_comp", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("n_bricks", ctypes.c_int64),
-                ("bytes_device", ctypes.c_int64)]
+                ("bytes_device", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class SpfdKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
 
 
 class SpfdError(RuntimeError):
@@ -85,6 +93,9 @@ def lib():
             L.spfd_efield.restype = ctypes.c_int
             L.spfd_get_info.argtypes = [vp, ctypes.POINTER(SpfdInfo)]
             L.spfd_get_info.restype = ctypes.c_int
+            L.spfd_kernel_stats.argtypes = [vp, ctypes.POINTER(SpfdKernelStat), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+            L.spfd_kernel_stats.restype = ctypes.c_int
             L.spfd_destroy.argtypes = [vp]
             L.spfd_destroy.restype = None
             L.spfd_last_error.argtypes = []
@@ -146,6 +157,17 @@ def spfd_get_info(ctx: int) -> SpfdInfo:
     info = SpfdInfo()
     _check(lib().spfd_get_info(ctypes.c_void_p(ctx), ctypes.byref(info)))
     return info
+
+
+def spfd_kernel_stats(ctx: int, reset: bool = False) -> list:
+    """Per-kernel-family timing of a context built with ``profile=1``."""
+    n = ctypes.c_int(0)
+    _check(lib().spfd_kernel_stats(ctypes.c_void_p(ctx), None, 0, ctypes.byref(n), 0))
+    arr = (SpfdKernelStat * max(n.value, 1))()
+    _check(lib().spfd_kernel_stats(ctypes.c_void_p(ctx), arr, n.value, ctypes.byref(n),
+                                   1 if reset else 0))
+    return [{"name": s.name.decode(), "launches": s.launches, "ms": s.ms,
+             "bytes": s.bytes, "flops": s.flops} for s in arr[:n.value]]
 
 
 def spfd_destroy(ctx: int):
@@ -218,6 +240,9 @@ class Solver:
 
     def info(self) -> dict:
         return spfd_get_info(self.ctx).as_dict()
+
+    def kernel_stats(self, reset: bool = False) -> list:
+        return spfd_kernel_stats(self.ctx, reset)
 
     def close(self):
         if getattr(self, "ctx", None):

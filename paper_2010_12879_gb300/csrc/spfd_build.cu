@@ -1,0 +1,483 @@
+// spfd_build: the operator of Eq. 3 and its multigrid hierarchy.
+//
+// Paper: Eq. 3 (Sec. II) defines G^T M_k G; Sec. III-A keeps only the
+// conducting nodes; Sec. III solves with AMG-preconditioned FGMRES (AmgX).
+// Here the hierarchy is geometric and operator-dependent: 2:1 vertex
+// coarsening of the brick grid, BoxMG-style interpolation collapsed from the
+// operator, Galerkin 27-point coarse operators, weighted-Jacobi smoothing
+// with omega from a power-iteration estimate of lambda_max(D^-1 A), and a
+// dense regularised inverse on the coarsest level.
+#include <cstdio>
+#include <cstring>
+
+#include "spfd_ctx.cuh"
+
+namespace spfd {
+
+// Geometry of a level from its brick activity flags.
+static spfd_status make_level(spfd_ctx *c, Level &lv, int NX, int NY, int NZ,
+                              const std::vector<unsigned char> &flags) {
+  Grid &g = lv.g;
+  g.NX = NX; g.NY = NY; g.NZ = NZ;
+  g.MX = (NX + 7) / 8; g.MY = (NY + 7) / 8; g.MZ = (NZ + 7) / 8;
+  size_t nbm = (size_t)g.MX * g.MY * g.MZ;
+  lv.hbmap.assign(nbm, -1);
+  lv.hbco.clear();
+  for (int bz = 0; bz < g.MZ; ++bz)
+    for (int by = 0; by < g.MY; ++by)
+      for (int bx = 0; bx < g.MX; ++bx) {
+        size_t q = ((size_t)bz * g.MY + by) * g.MX + bx;
+        if (flags[q]) {
+          lv.hbmap[q] = (int)lv.hbco.size();
+          lv.hbco.push_back(make_int4(bx, by, bz, 0));
+        }
+      }
+  if (lv.hbco.size() > (size_t)(INT32_MAX / BV))
+    return fail(SPFD_EINVAL, "grid too large: %zu active bricks", lv.hbco.size());
+  g.nb = (int)lv.hbco.size();
+  lv.S = (size_t)g.nb * BV;
+  int *bmap = nullptr;
+  int4 *bco = nullptr;
+  TRY(dalloc(c, &bmap, nbm));
+  TRY(dalloc(c, &bco, lv.hbco.size()));
+  CU(cudaMemcpyAsync(bmap, lv.hbmap.data(), nbm * sizeof(int),
+                     cudaMemcpyHostToDevice, c->stream));
+  if (g.nb)
+    CU(cudaMemcpyAsync(bco, lv.hbco.data(), lv.hbco.size() * sizeof(int4),
+                       cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));  // the host vectors may be reused
+  g.bmap = bmap;
+  g.bco = bco;
+  return SPFD_OK;
+}
+
+// Largest eigenvalue of D^-1 A by power iteration (for the Jacobi weight).
+static spfd_status estimate_lmax(spfd_ctx *c, int l, double *lmax) {
+  Level &lv = c->L[l];
+  const int nb = lv.g.nb;
+  cudaStream_t st = c->stream;
+  *lmax = 0.0;
+  if (nb == 0) return SPFD_OK;
+  if (nb > c->L[0].g.nb || !c->partials)
+    return fail(SPFD_EINTERNAL, "reduction scratch too small for level %d", l);
+  double *v = lv.x, *w = lv.t, *r = lv.r, *zero = lv.b;
+  CU(cudaMemsetAsync(zero, 0, lv.S * sizeof(double), st));
+  SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_power_init(nb, lv.diag, v, st));
+  // v <- D^-1 A v / |D^-1 A v|; after the first step |v| = 1 and |D^-1 A v|
+  // is the estimate.
+  double est = 0.0;
+  for (int it = 0; it < 20; ++it) {
+    if (l == 0)
+      SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+                  (launch_residual7<double, double>(lv.g, lv.gx, lv.diag, v, zero, r, st)));
+    else
+      SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+                  launch_residual27<double>(lv.g, lv.st, v, zero, r, st));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+                launch_power_step(nb, r, lv.dinv, w, c->sc, c->partials, st));
+    TRY(launch_check("power iteration"));
+    TRY(read_scalars(c));
+    double wn = std::sqrt(c->hsc->aux[4]);
+    if (!(wn > 0.0)) break;
+    if (it > 0) est = wn;
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_scaled_copy(nb, w, 1.0 / wn, v, st));
+  }
+  *lmax = est;
+  return SPFD_OK;
+}
+
+// Gauss-Jordan inverse (partial pivoting) of a dense n x n matrix, in place.
+static bool invert_dense(std::vector<double> &A, int n) {
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    double best = std::fabs(A[(size_t)col * n + col]);
+    for (int r = col + 1; r < n; ++r) {
+      double v = std::fabs(A[(size_t)r * n + col]);
+      if (v > best) { best = v; piv = r; }
+    }
+    if (!(best > 0.0)) return false;
+    if (piv != col) {
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)piv * n + k], A[(size_t)col * n + k]);
+        std::swap(I[(size_t)piv * n + k], I[(size_t)col * n + k]);
+      }
+    }
+    const double d = 1.0 / A[(size_t)col * n + col];
+    double *ac = &A[(size_t)col * n], *ic = &I[(size_t)col * n];
+    for (int k = 0; k < n; ++k) { ac[k] *= d; ic[k] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      double f = A[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      double *ar = &A[(size_t)r * n], *ir = &I[(size_t)r * n];
+      for (int k = 0; k < n; ++k) { ar[k] -= f * ac[k]; ir[k] -= f * ic[k]; }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// Coarsest level: B = A + sum_c mu_c v_c v_c^T (v_c the normalised indicator
+// of a connected component of the coarsest graph, mu_c its mean diagonal) is
+// SPD, and B^-1 r = A^+ r for r with zero mean on every component.  The
+// symmetrised inverse is applied as a dense FP64 matrix-vector product.
+static spfd_status setup_coarsest(spfd_ctx *c) {
+  Level &lv = c->L.back();
+  const size_t S = lv.S;
+  const bool single = c->L.size() == 1;
+  c->m = 0;
+  if (S == 0) return SPFD_OK;
+  std::vector<double> hst, hgx, hdiag(S);
+  CU(cudaMemcpyAsync(hdiag.data(), lv.diag, S * sizeof(double),
+                     cudaMemcpyDeviceToHost, c->stream));
+  if (single) {
+    hgx.resize(3 * S);
+    CU(cudaMemcpyAsync(hgx.data(), lv.gx, 3 * S * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    hst.resize(27 * S);
+    CU(cudaMemcpyAsync(hst.data(), lv.st, 27 * S * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+  }
+  TRY(sync_check(c, "coarsest copy"));
+  std::vector<int> row(S, -1), idx;
+  for (size_t s = 0; s < S; ++s)
+    if (hdiag[s] > 0.0) { row[s] = (int)idx.size(); idx.push_back((int)s); }
+  const int m = (int)idx.size();
+  c->m = m;
+  if (m == 0) return SPFD_OK;
+  if ((int64_t)m * m > ((int64_t)1 << 26))
+    return fail(SPFD_EINVAL, "coarsest level too large (%d unknowns); raise max_levels", m);
+  const Grid &g = lv.g;
+  auto slot_of = [&](int i, int j, int k) -> int {
+    if (i < 0 || j < 0 || k < 0 || i >= g.NX || j >= g.NY || k >= g.NZ) return -1;
+    int b = lv.hbmap[((size_t)(k >> 3) * g.MY + (j >> 3)) * g.MX + (i >> 3)];
+    if (b < 0) return -1;
+    return b * BV + ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
+  };
+  std::vector<double> A((size_t)m * m, 0.0);
+  for (int a = 0; a < m; ++a) {
+    const int s = idx[a];
+    const int4 bc = lv.hbco[s / BV];
+    const int t = s % BV;
+    const int i = bc.x * 8 + (t & 7), j = bc.y * 8 + ((t >> 3) & 7), k = bc.z * 8 + (t >> 6);
+    if (single) {  // the 7-point level-0 operator (tiny problems)
+      A[(size_t)a * m + a] = hdiag[s];
+      const int dd[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+      for (int q = 0; q < 6; ++q) {
+        int u = slot_of(i + dd[q][0], j + dd[q][1], k + dd[q][2]);
+        if (u < 0 || row[u] < 0) continue;
+        int ax = q / 2;
+        double ge = (q % 2 == 0) ? hgx[(size_t)ax * S + s] : hgx[(size_t)ax * S + u];
+        A[(size_t)a * m + row[u]] -= ge;
+      }
+    } else {
+      for (int e = 0; e < 27; ++e) {
+        int u = slot_of(i + e % 3 - 1, j + (e / 3) % 3 - 1, k + e / 9 - 1);
+        if (u < 0 || row[u] < 0) continue;
+        A[(size_t)a * m + row[u]] += hst[(size_t)e * S + s];
+      }
+    }
+  }
+  // connected components of the coarsest graph
+  std::vector<int> cc(m, -1), queue;
+  int nc = 0;
+  for (int a = 0; a < m; ++a) {
+    if (cc[a] >= 0) continue;
+    queue.assign(1, a);
+    cc[a] = nc;
+    for (size_t hd = 0; hd < queue.size(); ++hd) {
+      const int u = queue[hd];
+      for (int v = 0; v < m; ++v)
+        if (v != u && cc[v] < 0 && A[(size_t)u * m + v] != 0.0) {
+          cc[v] = nc;
+          queue.push_back(v);
+        }
+    }
+    ++nc;
+  }
+  std::vector<double> dsum(nc, 0.0);
+  std::vector<int> cnt(nc, 0);
+  for (int a = 0; a < m; ++a) { dsum[cc[a]] += A[(size_t)a * m + a]; cnt[cc[a]]++; }
+  for (int a = 0; a < m; ++a)
+    for (int b2 = 0; b2 < m; ++b2)
+      if (cc[a] == cc[b2]) {
+        const int q = cc[a];
+        A[(size_t)a * m + b2] += (dsum[q] / cnt[q]) / cnt[q];
+      }
+  if (!invert_dense(A, m))
+    return fail(SPFD_EINTERNAL, "coarsest-level matrix is singular after regularisation");
+  for (int a = 0; a < m; ++a)  // symmetrise the rounding of the inverse
+    for (int b2 = a + 1; b2 < m; ++b2) {
+      double v = 0.5 * (A[(size_t)a * m + b2] + A[(size_t)b2 * m + a]);
+      A[(size_t)a * m + b2] = A[(size_t)b2 * m + a] = v;
+    }
+  TRY(dalloc(c, &c->cidx, m));
+  TRY(dalloc(c, &c->Binv, (size_t)m * m));
+  CU(cudaMemcpyAsync(c->cidx, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaMemcpyAsync(c->Binv, A.data(), (size_t)m * m * sizeof(double),
+                     cudaMemcpyHostToDevice, c->stream));
+  return sync_check(c, "coarsest upload");
+}
+
+// Number of positive entries (and the largest) of a device diagonal.
+static spfd_status count_positive(spfd_ctx *c, const Level &lv, const double *d_dev,
+                                  int64_t *n, double *maxdiag) {
+  std::vector<double> d(lv.S);
+  if (lv.S)
+    CU(cudaMemcpyAsync(d.data(), d_dev, lv.S * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync_check(c, "count"));
+  int64_t k = 0;
+  double mx = 0.0;
+  for (double v : d) { if (v > 0.0) ++k; mx = std::max(mx, v); }
+  *n = k;
+  if (maxdiag) *maxdiag = mx;
+  return SPFD_OK;
+}
+
+// FP32 / BF16 copies of the hierarchy for the mixed-precision solve.
+static spfd_status setup_mixed(spfd_ctx *c) {
+  cudaStream_t st = c->stream;
+  for (size_t l = 0; l < c->L.size(); ++l) {
+    Level &lv = c->L[l];
+    const size_t S = lv.S;
+    TRY(dalloc(c, &lv.x32, S));
+    TRY(dalloc(c, &lv.b32, S));
+    TRY(dalloc(c, &lv.r32, S));
+    TRY(dalloc(c, &lv.t32, S));
+    CU(cudaMemsetAsync(lv.x32, 0, S * sizeof(float), st));
+    CU(cudaMemsetAsync(lv.t32, 0, S * sizeof(float), st));
+    TRY(dalloc(c, &lv.wdinv32, S));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(S, lv.wdinv, 1.0, lv.wdinv32, st));
+    if (l == 0) {
+      TRY(dalloc(c, &lv.gx32, 3 * S));
+      TRY(dalloc(c, &lv.gxbf, 3 * S));
+      TRY(dalloc(c, &lv.diag32, S));
+      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(3 * S, lv.gx, 1.0, lv.gx32, st));
+      SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+                  launch_convert<__nv_bfloat16>(3 * S, lv.gx, 1.0, lv.gxbf, st));
+      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
+    } else {
+      TRY(dalloc(c, &lv.st32, 27 * S));
+      TRY(dalloc(c, &lv.P32, 27 * S));
+      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
+      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
+    }
+  }
+  const size_t S0 = c->L[0].S;
+  TRY(dalloc(c, &c->dk32, S0));
+  TRY(dalloc(c, &c->rk32, S0));
+  TRY(dalloc(c, &c->pk32, S0));
+  TRY(dalloc(c, &c->qk32, S0));
+  return launch_check("mixed-precision copies");
+}
+
+spfd_status build_impl(spfd_ctx *c, const double *sigma) {
+  cudaStream_t st = c->stream;
+  TRY(dalloc(c, &c->sc, 1));
+  CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
+  CU(cudaMallocHost(&c->hsc, sizeof(Scalars)));
+  memset(c->hsc, 0, sizeof(Scalars));
+  CU(cudaEventCreate(&c->ev0));
+  CU(cudaEventCreate(&c->ev1));
+  CU(cudaEventRecord(c->ev0, st));
+  const int64_t launches0 = c->launch_count;
+
+  const int NX = c->nx + 1, NY = c->ny + 1, NZ = c->nz + 1;
+  const int MX = (NX + 7) / 8, MY = (NY + 7) / 8, MZ = (NZ + 7) / 8;
+  const size_t nbm = (size_t)MX * MY * MZ;
+  const size_t nvox = (size_t)c->nx * c->ny * c->nz;
+  unsigned char *flags = nullptr;
+  TRY(dalloc(c, &flags, nbm));
+  TRY(dalloc(c, &c->mask, nvox));
+  CU(cudaMemsetAsync(flags, 0, nbm, st));
+  SPFD_LAUNCH(c, "setup", false, 1, 9.0 * nvox, 0,
+              launch_sigma_flags(sigma, c->nx, c->ny, c->nz, MX, MY, flags, c->mask,
+                                 &c->sc->status, st));
+  TRY(launch_check("sigma flags"));
+  std::vector<unsigned char> hflags(nbm);
+  CU(cudaMemcpyAsync(hflags.data(), flags, nbm, cudaMemcpyDeviceToHost, st));
+  TRY(read_scalars(c));
+  dfree(c, flags);
+  if (c->hsc->status & DEV_BAD_SIGMA)
+    return fail(SPFD_EINVAL, "sigma holds a negative, NaN or infinite value");
+
+  c->L.clear();
+  c->L.emplace_back();
+  TRY(make_level(c, c->L[0], NX, NY, NZ, hflags));
+  const size_t S0 = c->L[0].S;
+  const int nb0 = c->L[0].g.nb;
+  // reduction scratch: level 0 has the most bricks of all levels and every
+  // grid reduction writes at most 2 values per block
+  TRY(dalloc(c, &c->partials, 4 * (size_t)std::max(nb0, 1)));
+  {
+    Level &l0 = c->L[0];
+    TRY(dalloc(c, &l0.gx, 3 * S0));
+    TRY(dalloc(c, &l0.diag, S0));
+    TRY(dalloc(c, &l0.dinv, S0));
+    TRY(dalloc(c, &l0.wdinv, S0));
+    SPFD_LAUNCH(c, "setup", false, 1, 40.0 * S0, 0,
+                launch_build_fine(l0.g, sigma, c->nx, c->ny, c->nz, c->h, l0.gx,
+                                  l0.diag, l0.dinv, st));
+    TRY(launch_check("build fine"));
+
+    // connected components of the conducting nodes
+    int *parent = nullptr, *counts = nullptr, *offsets = nullptr;
+    TRY(dalloc(c, &parent, S0));
+    TRY(dalloc(c, &c->comp, S0));
+    SPFD_LAUNCH(c, "setup", false, 3, 0, 0,
+                launch_components(l0.g, l0.gx, parent, &c->sc->status, st));
+    TRY(launch_check("components"));
+    TRY(dalloc(c, &counts, nb0));
+    TRY(dalloc(c, &offsets, nb0));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_root_counts(l0.g, parent, counts, st));
+    std::vector<int> hcnt(nb0), hoff(nb0);
+    if (nb0)
+      CU(cudaMemcpyAsync(hcnt.data(), counts, nb0 * sizeof(int),
+                         cudaMemcpyDeviceToHost, st));
+    TRY(read_scalars(c));
+    if (c->hsc->status & DEV_UF_CAP)
+      return fail(SPFD_EINTERNAL, "component labelling hit its iteration cap");
+    int64_t tot = 0;
+    for (int b = 0; b < nb0; ++b) { hoff[b] = (int)tot; tot += hcnt[b]; }
+    c->ncomp = (int)tot;
+    if (nb0)
+      CU(cudaMemcpyAsync(offsets, hoff.data(), nb0 * sizeof(int),
+                         cudaMemcpyHostToDevice, st));
+    SPFD_LAUNCH(c, "setup", false, 2, 0, 0, launch_assign_comp(l0.g, parent, offsets, c->comp, st));
+    TRY(dalloc(c, &c->csize, std::max(c->ncomp, 1)));
+    CU(cudaMemsetAsync(c->csize, 0, std::max(c->ncomp, 1) * sizeof(int), st));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_comp_sizes(l0.g, c->comp, c->csize, st));
+    TRY(launch_check("component sizes"));
+    std::vector<int> hsize(std::max(c->ncomp, 1));
+    CU(cudaMemcpyAsync(hsize.data(), c->csize, hsize.size() * sizeof(int),
+                       cudaMemcpyDeviceToHost, st));
+    TRY(sync_check(c, "components"));
+    dfree(c, parent);
+    dfree(c, counts);
+    dfree(c, offsets);
+    c->ndof = 0;
+    for (int q = 0; q < c->ncomp; ++q) c->ndof += hsize[q];
+    l0.n_active = c->ndof;
+    if (c->ncomp > 1) TRY(dalloc(c, &c->csum, c->ncomp));
+  }
+
+  // multigrid hierarchy
+  for (int l = 0;; ++l) {
+    {
+      Level &f = c->L[l];
+      TRY(dalloc(c, &f.x, f.S));
+      TRY(dalloc(c, &f.b, f.S));
+      TRY(dalloc(c, &f.r, f.S));
+      TRY(dalloc(c, &f.t, f.S));
+      CU(cudaMemsetAsync(f.x, 0, f.S * sizeof(double), st));
+      CU(cudaMemsetAsync(f.t, 0, f.S * sizeof(double), st));
+      const bool last = f.n_active <= c->opts.coarse_max || l + 1 >= c->opts.max_levels ||
+                        (f.g.NX <= 3 && f.g.NY <= 3 && f.g.NZ <= 3);
+      if (last) break;
+    }
+    // coarse node I <-> fine node 2I; coarse brick B covers fine bricks
+    // 2B-1 .. 2B+1 on each axis
+    const Grid fg = c->L[l].g;
+    const int CX = fg.NX / 2 + 1, CY = fg.NY / 2 + 1, CZ = fg.NZ / 2 + 1;
+    const int cMX = (CX + 7) / 8, cMY = (CY + 7) / 8, cMZ = (CZ + 7) / 8;
+    std::vector<unsigned char> cfl((size_t)cMX * cMY * cMZ, 0);
+    {
+      const Level &f = c->L[l];
+      for (int bz = 0; bz < cMZ; ++bz)
+        for (int by = 0; by < cMY; ++by)
+          for (int bx = 0; bx < cMX; ++bx) {
+            bool any = false;
+            for (int fz = std::max(0, 2 * bz - 1); fz <= std::min(fg.MZ - 1, 2 * bz + 1) && !any; ++fz)
+              for (int fy = std::max(0, 2 * by - 1); fy <= std::min(fg.MY - 1, 2 * by + 1) && !any; ++fy)
+                for (int fx = std::max(0, 2 * bx - 1); fx <= std::min(fg.MX - 1, 2 * bx + 1) && !any; ++fx)
+                  any = f.hbmap[((size_t)fz * fg.MY + fy) * fg.MX + fx] >= 0;
+            cfl[((size_t)bz * cMY + by) * cMX + bx] = any;
+          }
+    }
+    c->L.emplace_back();  // (invalidates references into c->L)
+    Level &fl = c->L[l];
+    Level &cl = c->L[l + 1];
+    TRY(make_level(c, cl, CX, CY, CZ, cfl));
+    const size_t Sc = cl.S;
+    TRY(dalloc(c, &cl.st, 27 * Sc));
+    TRY(dalloc(c, &cl.P, 27 * Sc));
+    TRY(dalloc(c, &cl.diag, Sc));
+    TRY(dalloc(c, &cl.dinv, Sc));
+    TRY(dalloc(c, &cl.wdinv, Sc));
+    double *W = nullptr;
+    TRY(dalloc(c, &W, 8 * fl.S));
+    SPFD_LAUNCH(c, "setup", false, 5, 0, 0,
+                launch_interp_weights(fl.g, fl.gx, fl.st, fl.diag, W, st));
+    TRY(launch_check("interpolation weights"));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+                launch_galerkin(fl.g, cl.g, fl.gx, fl.st, fl.diag, W, cl.st, st));
+    TRY(launch_check("galerkin"));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_symmetrize(cl.g, cl.st, st));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_pack_P(fl.g, cl.g, W, cl.P, st));
+    TRY(launch_check("pack P"));
+    TRY(sync_check(c, "coarse level"));
+    dfree(c, W);
+    int64_t nact = 0;
+    double maxdiag = 0.0;
+    TRY(count_positive(c, cl, cl.st + 13 * Sc, &nact, &maxdiag));
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+                launch_coarse_diag(cl.g, cl.st, 1e-13 * maxdiag, cl.diag, cl.dinv, st));
+    TRY(launch_check("coarse diag"));
+    TRY(count_positive(c, cl, cl.diag, &cl.n_active, nullptr));
+  }
+
+  // smoother weights (weighted Jacobi, omega = 4 / (3 * 1.05 * lambda_max(D^-1 A)))
+  for (size_t l = 0; l + 1 < c->L.size(); ++l) {
+    double lm = 0.0;
+    TRY(estimate_lmax(c, (int)l, &lm));
+    if (!(lm > 0.0)) lm = 2.0;
+    Level &lv = c->L[l];
+    lv.lmax = lm;
+    lv.omega = 4.0 / (3.0 * 1.05 * lm);
+    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+                launch_scaled_copy(lv.g.nb, lv.dinv, lv.omega, lv.wdinv, st));
+    CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), st));
+    CU(cudaMemsetAsync(lv.t, 0, lv.S * sizeof(double), st));
+  }
+  TRY(setup_coarsest(c));
+
+  // Krylov vectors
+  TRY(dalloc(c, &c->xk, S0));
+  TRY(dalloc(c, &c->rk, S0));
+  TRY(dalloc(c, &c->pk, S0));
+  TRY(dalloc(c, &c->qk, S0));
+  TRY(dalloc(c, &c->bk, S0));
+  if (c->opts.precision == SPFD_MIXED) TRY(setup_mixed(c));
+  for (auto &lv : c->L)
+    if (lv.g.nb > nb0)
+      return fail(SPFD_EINTERNAL, "a coarse level has more bricks than level 0");
+  CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
+  CU(cudaEventRecord(c->ev1, st));
+  TRY(sync_check(c, "build"));
+  TRY(prof_flush(c));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->info.ms_build = ms;
+  c->info.n_dof = c->ndof;
+  c->info.n_comp = c->ncomp;
+  c->info.n_levels = (int)c->L.size();
+  c->info.n_bricks = nb0;
+  c->info.bytes_device = c->bytes;
+  c->info.launches = c->launch_count - launches0;
+  if (c->opts.verbose) {
+    fprintf(stderr, "[spfd] build: %lld dof, %d comp, %d levels, %.2f ms, %.1f MB\n",
+            (long long)c->ndof, c->ncomp, (int)c->L.size(), ms, c->bytes / 1e6);
+    for (size_t l = 0; l < c->L.size(); ++l)
+      fprintf(stderr, "[spfd]   level %zu: nodes %dx%dx%d, bricks %d, active %lld, lmax %.3f\n",
+              l, c->L[l].g.NX, c->L[l].g.NY, c->L[l].g.NZ, c->L[l].g.nb,
+              (long long)c->L[l].n_active, c->L[l].lmax);
+  }
+  return SPFD_OK;
+}
+
+}  // namespace spfd

@@ -1,0 +1,198 @@
+// Host-side context of libspfd: levels, device buffers, profiling records.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "spfd.h"
+#include "spfd_internal.cuh"
+
+namespace spfd {
+
+spfd_status fail(spfd_status s, const char *fmt, ...);
+void set_error(const std::string &msg);
+std::string last_error_copy();
+
+#define CU(call)                                                            \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      return ::spfd::fail(SPFD_ECUDA, "%s failed: %s (%s:%d)", #call,       \
+                          cudaGetErrorString(e_), __FILE__, __LINE__);      \
+  } while (0)
+
+#define TRY(expr)                    \
+  do {                               \
+    spfd_status s_ = (expr);         \
+    if (s_ != SPFD_OK) return s_;    \
+  } while (0)
+
+struct Level {
+  Grid g{};                       // device view
+  std::vector<int> hbmap;         // host brick map
+  std::vector<int4> hbco;         // host brick coordinates
+  size_t S = 0;                   // slots = nb * 512
+  int64_t n_active = 0;
+  double omega = 0.0, lmax = 0.0;
+  // FP64 operator and transfer
+  double *gx = nullptr;           // level 0: [3][S] +edge conductances
+  double *st = nullptr;           // level >= 1: [27][S] Galerkin stencil
+  double *P = nullptr;            // level >= 1: [27][S] interpolation from here to level-1
+  double *diag = nullptr, *dinv = nullptr, *wdinv = nullptr;
+  double *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  // FP32 copies for the mixed-precision V-cycle
+  float *gx32 = nullptr;          // level 0: [3][S] (inner CG operator)
+  __nv_bfloat16 *gxbf = nullptr;  // level 0: [3][S] (V-cycle smoother)
+  float *st32 = nullptr, *P32 = nullptr, *diag32 = nullptr, *wdinv32 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
+
+  // accessors by precision
+  template <typename T> T *X();
+  template <typename T> T *B();
+  template <typename T> T *R();
+  template <typename T> T *Tt();
+  template <typename T> const T *ST() const;
+  template <typename T> const T *PP() const;
+  template <typename T> const T *DIAG() const;
+  template <typename T> const T *WDINV() const;
+};
+template <> inline double *Level::X<double>() { return x; }
+template <> inline float *Level::X<float>() { return x32; }
+template <> inline double *Level::B<double>() { return b; }
+template <> inline float *Level::B<float>() { return b32; }
+template <> inline double *Level::R<double>() { return r; }
+template <> inline float *Level::R<float>() { return r32; }
+template <> inline double *Level::Tt<double>() { return t; }
+template <> inline float *Level::Tt<float>() { return t32; }
+template <> inline const double *Level::ST<double>() const { return st; }
+template <> inline const float *Level::ST<float>() const { return st32; }
+template <> inline const double *Level::PP<double>() const { return P; }
+template <> inline const float *Level::PP<float>() const { return P32; }
+template <> inline const double *Level::DIAG<double>() const { return diag; }
+template <> inline const float *Level::DIAG<float>() const { return diag32; }
+template <> inline const double *Level::WDINV<double>() const { return wdinv; }
+template <> inline const float *Level::WDINV<float>() const { return wdinv32; }
+
+struct KernelStat {
+  std::string name;
+  int64_t launches = 0;
+  double ms = 0.0, bytes = 0.0, flops = 0.0;
+};
+struct ProfRec {
+  int stat;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+
+}  // namespace spfd
+
+struct spfd_ctx {
+  int device = 0, nsm = 0;
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, nz = 0;
+  double h = 0.0;
+  spfd_opts opts{};
+  std::vector<spfd::Level> L;
+  std::vector<void *> allocs;
+  int64_t bytes = 0;
+  int alloc_count = 0;
+  // fine-level bookkeeping
+  unsigned char *mask = nullptr;  // [nz][ny][nx] conducting voxel flags
+  int *comp = nullptr;            // [S0] component id or -1
+  int ncomp = 0;
+  int64_t ndof = 0;
+  int *csize = nullptr;           // [ncomp]
+  double *csum = nullptr;         // [ncomp] (only when ncomp > 1)
+  // Krylov vectors (FP64) and the FP32 inner-solve vectors (mixed)
+  double *xk = nullptr, *rk = nullptr, *pk = nullptr, *qk = nullptr, *bk = nullptr;
+  float *dk32 = nullptr, *rk32 = nullptr, *pk32 = nullptr, *qk32 = nullptr;
+  spfd::Scalars *sc = nullptr;    // device scalars
+  spfd::Scalars *hsc = nullptr;   // pinned host mirror
+  double *partials = nullptr;
+  // coarsest level
+  int m = 0;
+  int *cidx = nullptr;
+  double *Binv = nullptr;
+  // host-array staging; the edge potentials of the solve in progress
+  double *a_stage = nullptr, *psi_stage = nullptr;
+  const double *a_cur = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  spfd_info info{};
+  // launch accounting and profiling
+  int64_t launch_count = 0;
+  std::vector<spfd::KernelStat> stats;
+  std::vector<spfd::ProfRec> pending;
+  std::vector<cudaEvent_t> evpool;
+};
+
+namespace spfd {
+
+// Allocation with optional injected failure: SPFD_FAIL_ALLOC_AT=N makes the
+// N-th device allocation of a context fail (counted from 1), so tests can
+// check that every failure path releases what was already allocated.
+template <typename T>
+spfd_status dalloc(spfd_ctx *c, T **p, size_t count) {
+  *p = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  ++c->alloc_count;
+  const char *inj = getenv("SPFD_FAIL_ALLOC_AT");
+  if (inj && atoi(inj) == c->alloc_count)
+    return fail(SPFD_ENOMEM, "injected allocation failure #%d", c->alloc_count);
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? SPFD_ENOMEM : SPFD_ECUDA,
+                "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  c->bytes += (int64_t)bytes;
+  *p = (T *)q;
+  return SPFD_OK;
+}
+
+template <typename T>
+void dfree(spfd_ctx *c, T *&p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), (void *)p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+  p = nullptr;
+}
+
+spfd_status sync_check(spfd_ctx *c, const char *what);
+spfd_status launch_check(const char *what);
+spfd_status read_scalars(spfd_ctx *c);
+spfd_status build_impl(spfd_ctx *c, const double *sigma);
+void destroy_ctx(spfd_ctx *c);
+
+// Profiling: event pair around a launch, resolved at the next flush.
+int stat_index(spfd_ctx *c, const char *name, bool f32);
+cudaEvent_t take_event(spfd_ctx *c);
+void prof_push(spfd_ctx *c, int stat, cudaEvent_t a, cudaEvent_t b,
+               double bytes, double flops);
+spfd_status prof_flush(spfd_ctx *c);
+
+}  // namespace spfd
+
+// Launch CALL (which starts NK kernels) on c->stream; with opts.profile the
+// launch is bracketed by CUDA events and credited to family NAME with its
+// algorithmic bytes and flops.
+#define SPFD_LAUNCH(c, NAME, F32, NK, BYTES, FLOPS, CALL)                     \
+  do {                                                                       \
+    (c)->launch_count += (NK);                                               \
+    if ((c)->opts.profile) {                                                 \
+      cudaEvent_t e0_ = ::spfd::take_event(c), e1_ = ::spfd::take_event(c);  \
+      cudaEventRecord(e0_, (c)->stream);                                     \
+      CALL;                                                                  \
+      cudaEventRecord(e1_, (c)->stream);                                     \
+      ::spfd::prof_push((c), ::spfd::stat_index((c), NAME, F32), e0_, e1_,   \
+                        (double)(BYTES), (double)(FLOPS));                   \
+    } else {                                                                 \
+      CALL;                                                                  \
+    }                                                                        \
+  } while (0)

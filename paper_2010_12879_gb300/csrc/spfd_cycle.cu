@@ -24,14 +24,34 @@ template <typename T> __device__ __forceinline__ T cv(__nv_bfloat16 v) {
   const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;                \
   (void)S; (void)lx; (void)ly; (void)lz;
 
-// (A x)_s for the 7-point level-0 operator: diag*x_s - sum g x_nbr.
+// (A x)_s for the 7-point level-0 operator.  FP64: diag*x_s - sum g x_nbr
+// (fewest FP64-pipe operations).  FP32 (BF16 or FP32 g): sum g (x_s - x_nbr),
+// which is exactly zero on constants, so rounded conductances keep the
+// operator positive semidefinite.
 template <typename T, typename C>
 __device__ __forceinline__ T apply7(const Grid &g, const C *__restrict__ gx,
                                     const T *__restrict__ diag,
                                     const T *__restrict__ x, size_t S, int bk,
                                     int4 bc, int s, int lx, int ly, int lz) {
-  T acc = diag[s] * x[s];
   int m;
+  if constexpr (sizeof(T) == 4) {
+    const T xs = x[s];
+    T acc = 0;
+    m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
+    if (m >= 0) acc += cv<T>(gx[s]) * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
+    if (m >= 0) acc += cv<T>(gx[m]) * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 1, 0);
+    if (m >= 0) acc += cv<T>(gx[S + s]) * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, -1, 0);
+    if (m >= 0) acc += cv<T>(gx[S + m]) * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, 1);
+    if (m >= 0) acc += cv<T>(gx[2 * S + s]) * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, -1);
+    if (m >= 0) acc += cv<T>(gx[2 * S + m]) * (xs - x[m]);
+    return acc;
+  }
+  T acc = diag[s] * x[s];
   m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
   if (m >= 0) acc -= cv<T>(gx[s]) * x[m];
   m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);

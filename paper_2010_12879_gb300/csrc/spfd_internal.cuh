@@ -172,6 +172,13 @@ void launch_gather(const Grid &g, const double *psi, const int *comp, double *x,
 void launch_efield(const unsigned char *mask, const double *a,
                    const double *psi, int nx, int ny, int nz, double h,
                    double omega, double *E, cudaStream_t st);
+template <typename T>
+void launch_convert(size_t n, const double *src, double f, T *dst,
+                    cudaStream_t st);
+void launch_axpy_mixed(int nb, double *x, const float *d, double f,
+                       cudaStream_t st);
+void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
+                         Scalars *sc, double *partials, cudaStream_t st);
 void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st);
 void launch_power_step(int nb, const double *r, const double *dinv, double *w,
                        Scalars *sc, double *partials, cudaStream_t st);

@@ -78,8 +78,25 @@ __device__ __forceinline__ T apply7k(const Grid &g, const T *__restrict__ gx,
                                      const T *__restrict__ diag,
                                      const T *__restrict__ x, size_t S, int bk,
                                      int4 bc, int s, int lx, int ly, int lz) {
-  T acc = diag[s] * x[s];
   int m;
+  if constexpr (sizeof(T) == 4) {  // difference form: exactly zero on constants
+    const T xs = x[s];
+    T acc = 0;
+    m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
+    if (m >= 0) acc += gx[s] * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
+    if (m >= 0) acc += gx[m] * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 1, 0);
+    if (m >= 0) acc += gx[S + s] * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, -1, 0);
+    if (m >= 0) acc += gx[S + m] * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, 1);
+    if (m >= 0) acc += gx[2 * S + s] * (xs - x[m]);
+    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, -1);
+    if (m >= 0) acc += gx[2 * S + m] * (xs - x[m]);
+    return acc;
+  }
+  T acc = diag[s] * x[s];
   m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
   if (m >= 0) acc -= gx[s] * x[m];
   m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
@@ -333,7 +350,63 @@ k_scaled_copy(const double *__restrict__ src, double f, double *__restrict__ dst
   dst[s] = f * src[s];
 }
 
+// ------------------------------------------------ precision conversions
+// dst = (T) (f * src) elementwise over n values.
+template <typename T>
+__global__ void k_convert(size_t n, const double *__restrict__ src, double f,
+                          T *__restrict__ dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (T)(f * src[i]);
+}
+template <>
+__global__ void k_convert<__nv_bfloat16>(size_t n, const double *__restrict__ src,
+                                         double f, __nv_bfloat16 *__restrict__ dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __double2bfloat16(f * src[i]);
+}
+
+// x += f * d (FP64 accumulation of an FP32 correction) on level-0 slots.
+__global__ void __launch_bounds__(NT)
+k_axpy_mixed(double *__restrict__ x, const float *__restrict__ d, double f) {
+  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  x[s] += f * (double)d[s];
+}
+
+// r32 = (float)(f * r64); the sum of r32 lands in sc->rsum for the fused
+// projection of the first V-cycle sweep.
+__global__ void __launch_bounds__(NT)
+k_scale_to_f32(const double *__restrict__ r, double f, float *__restrict__ r32,
+               Scalars *sc, double *partials) {
+  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  const float v = (float)(f * r[s]);
+  r32[s] = v;
+  double t[1] = {(double)v};
+  double tot[1];
+  if (grid_sum<1>(t, partials, &sc->ticket[5], tot)) sc->rsum = tot[0];
+}
+
 // ------------------------------------------------------------ launchers
+template <typename T>
+void launch_convert(size_t n, const double *src, double f, T *dst,
+                    cudaStream_t st) {
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks == 0) return;
+  k_convert<T><<<(int)blocks, 256, 0, st>>>(n, src, f, dst);
+}
+template void launch_convert<float>(size_t, const double *, double, float *, cudaStream_t);
+template void launch_convert<__nv_bfloat16>(size_t, const double *, double,
+                                            __nv_bfloat16 *, cudaStream_t);
+void launch_axpy_mixed(int nb, double *x, const float *d, double f,
+                       cudaStream_t st) {
+  if (nb) k_axpy_mixed<<<nb, NT, 0, st>>>(x, d, f);
+}
+void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
+                         Scalars *sc, double *partials, cudaStream_t st) {
+  if (nb) k_scale_to_f32<<<nb, NT, 0, st>>>(r, f, r32, sc, partials);
+}
 void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st) {
   if (nb) k_power_init<<<nb, NT, 0, st>>>(diag, v);
 }
