@@ -167,6 +167,31 @@ spfd_status spfd_get_info(const spfd_ctx *ctx, spfd_info *info);
 spfd_status spfd_kernel_stats(spfd_ctx *ctx, spfd_kernel_stat *stats, int max,
                               int *n, int reset);
 
+/* Relative residual ||b - A psi||_2 / ||b||_2 of a node potential for the
+ * system above (b = -G^T M_k a, A = G^T M_k G, summed over the conducting
+ * nodes), computed directly from the voxel grid without a context and
+ * without allocating any device memory.  The paper has no counterpart: this
+ * is a service for callers that cannot allocate while they check a solution
+ * -- code running during CUDA stream capture (cudaMalloc cannot be
+ * captured), processes whose device memory an allocator has reserved up
+ * front, real-time loops that must not enter the allocator.
+ *   sigma_dev, a_dev, psi_dev  as in spfd_build / spfd_solve (device, FP64).
+ *   nx, ny, nz, h              the voxel grid; at most 134,217,728 nodes
+ *                              ((nx+1)(ny+1)(nz+1)), else SPFD_EINVAL.
+ *   stream                     cudaStream_t to run on (NULL = default stream).
+ *   rel_res                    host output; 0 when b = 0.
+ * The partial sums live in one fixed 256 KB device array of the library,
+ * which every device that loads the library holds until the process exits.
+ * The first call on a device looks up that array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  b is not projected, so the value matches
+ * spfd_solve's rel_res_true to rounding.  Synchronises the stream. */
+spfd_status spfd_residual_noalloc(const double *sigma_dev, const double *a_dev,
+                                  const double *psi_dev, int nx, int ny, int nz,
+                                  double h, void *stream, double *rel_res);
+
 /* Release every resource of the context.  NULL is a no-op. */
 void spfd_destroy(spfd_ctx *ctx);
 

@@ -29,7 +29,7 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 # Names declared in include/spfd.h (checked against the library by the tests).
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
-           "spfd_last_error")
+           "spfd_last_error", "spfd_residual_noalloc")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -100,6 +100,9 @@ def lib():
             L.spfd_destroy.restype = None
             L.spfd_last_error.argtypes = []
             L.spfd_last_error.restype = ctypes.c_char_p
+            L.spfd_residual_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, dp, vp, ctypes.POINTER(dp)]
+            L.spfd_residual_noalloc.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -172,6 +175,18 @@ def spfd_kernel_stats(ctx: int, reset: bool = False) -> list:
 
 def spfd_destroy(ctx: int):
     lib().spfd_destroy(ctypes.c_void_p(ctx))
+
+
+def spfd_residual_noalloc(sigma_ptr: int, a_ptr: int, psi_ptr: int, nx: int,
+                          ny: int, nz: int, h: float, stream: int = 0) -> float:
+    """Relative residual of psi computed without a context and without
+    allocating device memory (for callers that cannot allocate, e.g. during
+    stream capture); the first call on a device must precede any capture."""
+    out = ctypes.c_double(0.0)
+    _check(lib().spfd_residual_noalloc(ctypes.c_void_p(sigma_ptr), ctypes.c_void_p(a_ptr),
+                                       ctypes.c_void_p(psi_ptr), nx, ny, nz, float(h),
+                                       ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
 
 
 class Solver:
