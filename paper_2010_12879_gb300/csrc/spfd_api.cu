@@ -268,13 +268,22 @@ static T *vcycle(spfd_ctx *c, int l, T *bl, bool proj) {
               launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st));
   T *ec = vcycle<T>(c, l + 1, cl.B<T>(), false);
   SPFD_LAUNCH(c, l == 0 ? "prolong_l0" : "prolong_coarse", f32, 1,
-              28 * w * Sc + 2 * w * S, 7 * S,
-              launch_prolong<T>(lv.g, cl.g, cl.PP<T>(), ec, cur, st));
+              (27.0 / 8.0 + 2.0) * w * S + w * Sc, 7 * S,
+              launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st));
   for (int s = 0; s < c->opts.nu_post; ++s) { sweep(cur, oth); std::swap(cur, oth); }
   return cur;
 }
 
 // ------------------------------------------------------------------ Krylov
+// The residual about to enter the V-cycle already has zero mean: clear the
+// sum and the means the fused projection reads.
+static spfd_status zero_rsum(spfd_ctx *c) {
+  CU(cudaMemsetAsync(&c->sc->rsum, 0, sizeof(double), c->stream));
+  CU(cudaMemsetAsync(&c->sc->rmean, 0, sizeof(double), c->stream));
+  CU(cudaMemsetAsync(&c->sc->rmean_f, 0, sizeof(float), c->stream));
+  return SPFD_OK;
+}
+
 static spfd_status true_residual(spfd_ctx *c, double bb, double *rel) {
   Level &l0 = c->L[0];
   const double S = (double)l0.S;
@@ -337,6 +346,9 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
   for (it = 1; it <= maxit; ++it) {
     SPFD_LAUNCH(c, "apply_dot", f32, 1, (f32 ? 5 : 6) * w * S, (f32 ? 20 : 15) * S,
                 launch_apply_dot<T>(l0.g, opgx, opdiag, p, q, c->sc, c->partials, st));
+    SPFD_LAUNCH(c, "finish_pq", false, 1, 8.0 * nb, nb,
+                launch_finish_pq(apply_dot_partials<T>(nb), c->partials,
+                                 c->partials + (size_t)16 * nb, c->sc, st));
     SPFD_LAUNCH(c, "update_xr", f32, 1, 6 * w * S, 7 * S,
                 launch_update_xr<T>(nb, x, r, p, q, c->sc, c->partials, st));
     TRY(launch_check("CG update"));
@@ -355,7 +367,7 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
       else if (++stall >= 3) break;
       CU(cudaMemcpyAsync(r, l0.r, S0 * sizeof(T), cudaMemcpyDeviceToDevice, st));
       TRY(project<T>(c, r));
-      CU(cudaMemsetAsync(&c->sc->rsum, 0, sizeof(double), st));
+      TRY(zero_rsum(c));
       restart = true;
     }
     TRY(precondition(restart ? 1 : 0));
@@ -395,7 +407,7 @@ static spfd_status solve_fp64(spfd_ctx *c, double tol, spfd_info *out) {
     res.conv = true;
   } else {
     CU(cudaMemcpyAsync(c->rk, c->bk, S0 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    CU(cudaMemsetAsync(&c->sc->rsum, 0, sizeof(double), c->stream));  // b is projected
+    TRY(zero_rsum(c));  // b is projected
     TRY(pcg<double>(c, c->xk, c->rk, c->pk, c->qk, l0.gx, l0.diag, bb, tol,
                     c->opts.maxit, &res));
     TRY(project<double>(c, c->xk));

@@ -7,6 +7,7 @@
 // operator, Galerkin 27-point coarse operators, weighted-Jacobi smoothing
 // with omega from a power-iteration estimate of lambda_max(D^-1 A), and a
 // dense regularised inverse on the coarsest level.
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 
@@ -45,9 +46,62 @@ static spfd_status make_level(spfd_ctx *c, Level &lv, int NX, int NY, int NZ,
   if (g.nb)
     CU(cudaMemcpyAsync(bco, lv.hbco.data(), lv.hbco.size() * sizeof(int4),
                        cudaMemcpyHostToDevice, c->stream));
+  // 27-neighbour brick table
+  std::vector<int> hn((size_t)std::max(g.nb, 1) * 27, -1);
+  for (int b = 0; b < g.nb; ++b) {
+    const int4 bc = lv.hbco[b];
+    for (int e = 0; e < 27; ++e) {
+      const int x = bc.x + e % 3 - 1, y = bc.y + (e / 3) % 3 - 1, z = bc.z + e / 9 - 1;
+      if (x < 0 || y < 0 || z < 0 || x >= g.MX || y >= g.MY || z >= g.MZ) continue;
+      hn[(size_t)b * 27 + e] = lv.hbmap[((size_t)z * g.MY + y) * g.MX + x];
+    }
+  }
+  int *nbr = nullptr;
+  TRY(dalloc(c, &nbr, hn.size()));
+  CU(cudaMemcpyAsync(nbr, hn.data(), hn.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
   CU(cudaStreamSynchronize(c->stream));  // the host vectors may be reused
   g.bmap = bmap;
   g.bco = bco;
+  g.nbr = nbr;
+  g.kid = nullptr;
+  g.par = nullptr;
+  return SPFD_OK;
+}
+
+// Transfer tables between a fine level f and its coarse level cl: for each
+// coarse brick the 27 fine bricks its 17^3 fine support touches, and for
+// each fine brick the 8 coarse bricks that hold its parents.
+static spfd_status make_transfer_tables(spfd_ctx *c, Level &f, Level &cl) {
+  const Grid &fg = f.g, &cg = cl.g;
+  std::vector<int> kid((size_t)std::max(cg.nb, 1) * 27, -1);
+  for (int b = 0; b < cg.nb; ++b) {
+    const int4 bc = cl.hbco[b];
+    for (int o = 0; o < 27; ++o) {
+      const int x = 2 * bc.x + o % 3 - 1, y = 2 * bc.y + (o / 3) % 3 - 1, z = 2 * bc.z + o / 9 - 1;
+      if (x < 0 || y < 0 || z < 0 || x >= fg.MX || y >= fg.MY || z >= fg.MZ) continue;
+      kid[(size_t)b * 27 + o] = f.hbmap[((size_t)z * fg.MY + y) * fg.MX + x];
+    }
+  }
+  std::vector<int> par((size_t)std::max(fg.nb, 1) * 8, -1);
+  for (int b = 0; b < fg.nb; ++b) {
+    const int4 bc = f.hbco[b];
+    for (int o = 0; o < 8; ++o) {
+      const int x = (bc.x >> 1) + (o & 1), y = (bc.y >> 1) + ((o >> 1) & 1), z = (bc.z >> 1) + (o >> 2);
+      if (x >= cg.MX || y >= cg.MY || z >= cg.MZ) continue;
+      par[(size_t)b * 8 + o] = cl.hbmap[((size_t)z * cg.MY + y) * cg.MX + x];
+    }
+  }
+  int *dkid = nullptr, *dpar = nullptr;
+  TRY(dalloc(c, &dkid, kid.size()));
+  TRY(dalloc(c, &dpar, par.size()));
+  CU(cudaMemcpyAsync(dkid, kid.data(), kid.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaMemcpyAsync(dpar, par.data(), par.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  cl.g.kid = dkid;
+  f.g.par = dpar;
   return SPFD_OK;
 }
 
@@ -62,60 +116,66 @@ static spfd_status estimate_lmax(spfd_ctx *c, int l, double *lmax) {
     return fail(SPFD_EINTERNAL, "reduction scratch too small for level %d", l);
   double *v = lv.x, *w = lv.t, *r = lv.r, *zero = lv.b;
   CU(cudaMemsetAsync(zero, 0, lv.S * sizeof(double), st));
-  SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_power_init(nb, lv.diag, v, st));
-  // v <- D^-1 A v / |D^-1 A v|; after the first step |v| = 1 and |D^-1 A v|
-  // is the estimate.
-  double est = 0.0;
-  for (int it = 0; it < 20; ++it) {
+  SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0, launch_power_init(nb, lv.diag, v, st));
+  // v <- D^-1 A v / |D^-1 A v| entirely on the device (the normalisation
+  // reads |w|^2 from the device scalars); after the first step |v| = 1, so
+  // the last |D^-1 A v| is the estimate and only it is read back.
+  const int iters = 15;
+  for (int it = 0; it < iters; ++it) {
     if (l == 0)
-      SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+      SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
                   (launch_residual7<double, double>(lv.g, lv.gx, lv.diag, v, zero, r, st)));
     else
-      SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+      SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
                   launch_residual27<double>(lv.g, lv.st, v, zero, r, st));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+    SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
                 launch_power_step(nb, r, lv.dinv, w, c->sc, c->partials, st));
-    TRY(launch_check("power iteration"));
-    TRY(read_scalars(c));
-    double wn = std::sqrt(c->hsc->aux[4]);
-    if (!(wn > 0.0)) break;
-    if (it > 0) est = wn;
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_scaled_copy(nb, w, 1.0 / wn, v, st));
+    if (it + 1 < iters)
+      SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0, launch_normalize(nb, w, v, c->sc, st));
   }
-  *lmax = est;
+  TRY(launch_check("power iteration"));
+  TRY(read_scalars(c));
+  const double wn = std::sqrt(c->hsc->aux[4]);
+  *lmax = std::isfinite(wn) ? wn : 0.0;
   return SPFD_OK;
 }
 
-// Gauss-Jordan inverse (partial pivoting) of a dense n x n matrix, in place.
-static bool invert_dense(std::vector<double> &A, int n) {
-  std::vector<double> I((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
-  for (int col = 0; col < n; ++col) {
-    int piv = col;
-    double best = std::fabs(A[(size_t)col * n + col]);
-    for (int r = col + 1; r < n; ++r) {
-      double v = std::fabs(A[(size_t)r * n + col]);
-      if (v > best) { best = v; piv = r; }
-    }
-    if (!(best > 0.0)) return false;
-    if (piv != col) {
-      for (int k = 0; k < n; ++k) {
-        std::swap(A[(size_t)piv * n + k], A[(size_t)col * n + k]);
-        std::swap(I[(size_t)piv * n + k], I[(size_t)col * n + k]);
-      }
-    }
-    const double d = 1.0 / A[(size_t)col * n + col];
-    double *ac = &A[(size_t)col * n], *ic = &I[(size_t)col * n];
-    for (int k = 0; k < n; ++k) { ac[k] *= d; ic[k] *= d; }
-    for (int r = 0; r < n; ++r) {
-      if (r == col) continue;
-      double f = A[(size_t)r * n + col];
-      if (f == 0.0) continue;
-      double *ar = &A[(size_t)r * n], *ir = &I[(size_t)r * n];
-      for (int k = 0; k < n; ++k) { ar[k] -= f * ac[k]; ir[k] -= f * ic[k]; }
+// Inverse of a dense SPD n x n matrix (row-major), in place: Cholesky
+// A = L L^T, then L^-1 by forward substitution, then A^-1 = L^-T L^-1.
+// Returns false if a pivot is not positive.
+static bool invert_spd(std::vector<double> &A, int n) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    const double *lj = &L[(size_t)j * n];
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= lj[k] * lj[k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      const double *li = &L[(size_t)i * n];
+      double s = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= li[k] * lj[k];
+      L[(size_t)i * n + j] = s / ljj;
     }
   }
-  A.swap(I);
+  // Linv (lower triangular), row-major
+  std::vector<double> Li((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    Li[(size_t)i * n + i] = 1.0 / L[(size_t)i * n + i];
+    for (int j = 0; j < i; ++j) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += L[(size_t)i * n + k] * Li[(size_t)k * n + j];
+      Li[(size_t)i * n + j] = -s / L[(size_t)i * n + i];
+    }
+  }
+  // A^-1 = Linv^T Linv: (i,j) = sum_{k >= max(i,j)} Li[k][i] Li[k][j]
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = 0.0;
+      for (int k = i; k < n; ++k) s += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = s;
+    }
   return true;
 }
 
@@ -207,20 +267,34 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
         const int q = cc[a];
         A[(size_t)a * m + b2] += (dsum[q] / cnt[q]) / cnt[q];
       }
-  if (!invert_dense(A, m))
-    return fail(SPFD_EINTERNAL, "coarsest-level matrix is singular after regularisation");
-  for (int a = 0; a < m; ++a)  // symmetrise the rounding of the inverse
-    for (int b2 = a + 1; b2 < m; ++b2) {
-      double v = 0.5 * (A[(size_t)a * m + b2] + A[(size_t)b2 * m + a]);
-      A[(size_t)a * m + b2] = A[(size_t)b2 * m + a] = v;
-    }
   TRY(dalloc(c, &c->cidx, m));
-  TRY(dalloc(c, &c->Binv, (size_t)m * m));
   CU(cudaMemcpyAsync(c->cidx, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice,
                      c->stream));
-  CU(cudaMemcpyAsync(c->Binv, A.data(), (size_t)m * m * sizeof(double),
+  if (m <= 64) {  // small: invert on the host
+    if (!invert_spd(A, m))
+      return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
+    TRY(dalloc(c, &c->Binv, (size_t)m * m));
+    CU(cudaMemcpyAsync(c->Binv, A.data(), (size_t)m * m * sizeof(double),
+                       cudaMemcpyHostToDevice, c->stream));
+    return sync_check(c, "coarsest upload");
+  }
+  // larger: Gauss-Jordan sweeps on the device (ping-pong between two buffers)
+  double *b0 = nullptr, *b1 = nullptr;
+  TRY(dalloc(c, &b0, (size_t)m * m));
+  TRY(dalloc(c, &b1, (size_t)m * m));
+  CU(cudaMemcpyAsync(b0, A.data(), (size_t)m * m * sizeof(double),
                      cudaMemcpyHostToDevice, c->stream));
-  return sync_check(c, "coarsest upload");
+  CU(cudaMemsetAsync(&c->sc->status, 0, sizeof(int), c->stream));
+  double *inv = nullptr;
+  SPFD_LAUNCH(c, "setup_coarsest", false, m, 0, 2.0 * m * m * m,
+              inv = launch_dense_inverse(b0, b1, m, &c->sc->status, c->stream));
+  TRY(launch_check("coarsest inverse"));
+  TRY(read_scalars(c));
+  if (c->hsc->status & DEV_BAD_PIVOT)
+    return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
+  c->Binv = inv;
+  if (inv == b0) dfree(c, b1); else dfree(c, b0);
+  return SPFD_OK;
 }
 
 // Number of positive entries (and the largest) of a device diagonal.
@@ -252,20 +326,25 @@ static spfd_status setup_mixed(spfd_ctx *c) {
     CU(cudaMemsetAsync(lv.x32, 0, S * sizeof(float), st));
     CU(cudaMemsetAsync(lv.t32, 0, S * sizeof(float), st));
     TRY(dalloc(c, &lv.wdinv32, S));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(S, lv.wdinv, 1.0, lv.wdinv32, st));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.wdinv, 1.0, lv.wdinv32, st));
+    if (lv.Pc) {
+      TRY(dalloc(c, &lv.Pc32, 27 * (S / 8)));
+      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
+                  launch_convert<float>(27 * (S / 8), lv.Pc, 1.0, lv.Pc32, st));
+    }
     if (l == 0) {
       TRY(dalloc(c, &lv.gx32, 3 * S));
       TRY(dalloc(c, &lv.gxbf, 3 * S));
       TRY(dalloc(c, &lv.diag32, S));
-      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(3 * S, lv.gx, 1.0, lv.gx32, st));
-      SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(3 * S, lv.gx, 1.0, lv.gx32, st));
+      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
                   launch_convert<__nv_bfloat16>(3 * S, lv.gx, 1.0, lv.gxbf, st));
-      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
+      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
     } else {
       TRY(dalloc(c, &lv.st32, 27 * S));
       TRY(dalloc(c, &lv.P32, 27 * S));
-      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
-      SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
+      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
+      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
     }
   }
   const size_t S0 = c->L[0].S;
@@ -276,8 +355,23 @@ static spfd_status setup_mixed(spfd_ctx *c) {
   return launch_check("mixed-precision copies");
 }
 
+// Wall-clock phase marks of the build (printed with opts.verbose >= 2).
+struct PhaseClock {
+  spfd_ctx *c;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  void mark(const char *what) {
+    if (c->opts.verbose < 2) return;
+    cudaStreamSynchronize(c->stream);
+    auto t1 = std::chrono::steady_clock::now();
+    fprintf(stderr, "[spfd]   build phase %-18s %8.3f ms\n", what,
+            std::chrono::duration<double, std::milli>(t1 - t0).count());
+    t0 = t1;
+  }
+};
+
 spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   cudaStream_t st = c->stream;
+  PhaseClock clk{c};
   TRY(dalloc(c, &c->sc, 1));
   CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
   CU(cudaMallocHost(&c->hsc, sizeof(Scalars)));
@@ -295,7 +389,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   TRY(dalloc(c, &flags, nbm));
   TRY(dalloc(c, &c->mask, nvox));
   CU(cudaMemsetAsync(flags, 0, nbm, st));
-  SPFD_LAUNCH(c, "setup", false, 1, 9.0 * nvox, 0,
+  SPFD_LAUNCH(c, "setup_flags", false, 1, 9.0 * nvox, 0,
               launch_sigma_flags(sigma, c->nx, c->ny, c->nz, MX, MY, flags, c->mask,
                                  &c->sc->status, st));
   TRY(launch_check("sigma flags"));
@@ -306,21 +400,23 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   if (c->hsc->status & DEV_BAD_SIGMA)
     return fail(SPFD_EINVAL, "sigma holds a negative, NaN or infinite value");
 
+  clk.mark("flags");
   c->L.clear();
   c->L.emplace_back();
   TRY(make_level(c, c->L[0], NX, NY, NZ, hflags));
   const size_t S0 = c->L[0].S;
   const int nb0 = c->L[0].g.nb;
-  // reduction scratch: level 0 has the most bricks of all levels and every
-  // grid reduction writes at most 2 values per block
-  TRY(dalloc(c, &c->partials, 4 * (size_t)std::max(nb0, 1)));
+  // reduction scratch: level 0 has the most bricks of all levels; the CG
+  // operator writes up to 16 partials per brick, followed by the finishing
+  // reduction's block sums; other grid reductions write 2 values per block
+  TRY(dalloc(c, &c->partials, 16 * (size_t)std::max(nb0, 1) + 1024));
   {
     Level &l0 = c->L[0];
     TRY(dalloc(c, &l0.gx, 3 * S0));
     TRY(dalloc(c, &l0.diag, S0));
     TRY(dalloc(c, &l0.dinv, S0));
     TRY(dalloc(c, &l0.wdinv, S0));
-    SPFD_LAUNCH(c, "setup", false, 1, 40.0 * S0, 0,
+    SPFD_LAUNCH(c, "setup_fine", false, 1, 40.0 * S0, 0,
                 launch_build_fine(l0.g, sigma, c->nx, c->ny, c->nz, c->h, l0.gx,
                                   l0.diag, l0.dinv, st));
     TRY(launch_check("build fine"));
@@ -329,12 +425,12 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     int *parent = nullptr, *counts = nullptr, *offsets = nullptr;
     TRY(dalloc(c, &parent, S0));
     TRY(dalloc(c, &c->comp, S0));
-    SPFD_LAUNCH(c, "setup", false, 3, 0, 0,
+    SPFD_LAUNCH(c, "setup_components", false, 3, 0, 0,
                 launch_components(l0.g, l0.gx, parent, &c->sc->status, st));
     TRY(launch_check("components"));
     TRY(dalloc(c, &counts, nb0));
     TRY(dalloc(c, &offsets, nb0));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_root_counts(l0.g, parent, counts, st));
+    SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0, launch_root_counts(l0.g, parent, counts, st));
     std::vector<int> hcnt(nb0), hoff(nb0);
     if (nb0)
       CU(cudaMemcpyAsync(hcnt.data(), counts, nb0 * sizeof(int),
@@ -348,10 +444,10 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     if (nb0)
       CU(cudaMemcpyAsync(offsets, hoff.data(), nb0 * sizeof(int),
                          cudaMemcpyHostToDevice, st));
-    SPFD_LAUNCH(c, "setup", false, 2, 0, 0, launch_assign_comp(l0.g, parent, offsets, c->comp, st));
+    SPFD_LAUNCH(c, "setup_components", false, 2, 0, 0, launch_assign_comp(l0.g, parent, offsets, c->comp, st));
     TRY(dalloc(c, &c->csize, std::max(c->ncomp, 1)));
     CU(cudaMemsetAsync(c->csize, 0, std::max(c->ncomp, 1) * sizeof(int), st));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_comp_sizes(l0.g, c->comp, c->csize, st));
+    SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0, launch_comp_sizes(l0.g, c->comp, c->csize, st));
     TRY(launch_check("component sizes"));
     std::vector<int> hsize(std::max(c->ncomp, 1));
     CU(cudaMemcpyAsync(hsize.data(), c->csize, hsize.size() * sizeof(int),
@@ -366,6 +462,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     if (c->ncomp > 1) TRY(dalloc(c, &c->csum, c->ncomp));
   }
 
+  clk.mark("fine+components");
   // multigrid hierarchy
   for (int l = 0;; ++l) {
     {
@@ -403,6 +500,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     Level &fl = c->L[l];
     Level &cl = c->L[l + 1];
     TRY(make_level(c, cl, CX, CY, CZ, cfl));
+    TRY(make_transfer_tables(c, fl, cl));
     const size_t Sc = cl.S;
     TRY(dalloc(c, &cl.st, 27 * Sc));
     TRY(dalloc(c, &cl.P, 27 * Sc));
@@ -411,24 +509,27 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     TRY(dalloc(c, &cl.wdinv, Sc));
     double *W = nullptr;
     TRY(dalloc(c, &W, 8 * fl.S));
-    SPFD_LAUNCH(c, "setup", false, 5, 0, 0,
+    SPFD_LAUNCH(c, "setup_interp", false, 5, 0, 0,
                 launch_interp_weights(fl.g, fl.gx, fl.st, fl.diag, W, st));
     TRY(launch_check("interpolation weights"));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+    SPFD_LAUNCH(c, "setup_galerkin", false, 1, 0, 0,
                 launch_galerkin(fl.g, cl.g, fl.gx, fl.st, fl.diag, W, cl.st, st));
     TRY(launch_check("galerkin"));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_symmetrize(cl.g, cl.st, st));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0, launch_pack_P(fl.g, cl.g, W, cl.P, st));
+    SPFD_LAUNCH(c, "setup_galerkin", false, 1, 0, 0, launch_symmetrize(cl.g, cl.st, st));
+    SPFD_LAUNCH(c, "setup_pack", false, 1, 0, 0, launch_pack_P(fl.g, cl.g, W, cl.P, st));
+    TRY(dalloc(c, &fl.Pc, 27 * (fl.S / 8)));
+    SPFD_LAUNCH(c, "setup_pack", false, 1, 0, 0, launch_pack_Pc(fl.g, W, fl.Pc, st));
     TRY(launch_check("pack P"));
     TRY(sync_check(c, "coarse level"));
     dfree(c, W);
     int64_t nact = 0;
     double maxdiag = 0.0;
     TRY(count_positive(c, cl, cl.st + 13 * Sc, &nact, &maxdiag));
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+    SPFD_LAUNCH(c, "setup_pack", false, 1, 0, 0,
                 launch_coarse_diag(cl.g, cl.st, 1e-13 * maxdiag, cl.diag, cl.dinv, st));
     TRY(launch_check("coarse diag"));
     TRY(count_positive(c, cl, cl.diag, &cl.n_active, nullptr));
+    clk.mark("coarse level");
   }
 
   // smoother weights (weighted Jacobi, omega = 4 / (3 * 1.05 * lambda_max(D^-1 A)))
@@ -439,12 +540,14 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     Level &lv = c->L[l];
     lv.lmax = lm;
     lv.omega = 4.0 / (3.0 * 1.05 * lm);
-    SPFD_LAUNCH(c, "setup", false, 1, 0, 0,
+    SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
                 launch_scaled_copy(lv.g.nb, lv.dinv, lv.omega, lv.wdinv, st));
     CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), st));
     CU(cudaMemsetAsync(lv.t, 0, lv.S * sizeof(double), st));
   }
+  clk.mark("smoother weights");
   TRY(setup_coarsest(c));
+  clk.mark("coarsest inverse");
 
   // Krylov vectors
   TRY(dalloc(c, &c->xk, S0));
@@ -453,10 +556,13 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   TRY(dalloc(c, &c->qk, S0));
   TRY(dalloc(c, &c->bk, S0));
   if (c->opts.precision == SPFD_MIXED) TRY(setup_mixed(c));
+  clk.mark("vectors+mixed");
   for (auto &lv : c->L)
     if (lv.g.nb > nb0)
       return fail(SPFD_EINTERNAL, "a coarse level has more bricks than level 0");
   CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
+  const double inv_ndof = c->ndof ? 1.0 / (double)c->ndof : 0.0;
+  CU(cudaMemcpyAsync(&c->sc->inv_ndof, &inv_ndof, sizeof(double), cudaMemcpyHostToDevice, st));
   CU(cudaEventRecord(c->ev1, st));
   TRY(sync_check(c, "build"));
   TRY(prof_flush(c));

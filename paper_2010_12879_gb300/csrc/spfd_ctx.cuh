@@ -42,12 +42,15 @@ struct Level {
   double *gx = nullptr;           // level 0: [3][S] +edge conductances
   double *st = nullptr;           // level >= 1: [27][S] Galerkin stencil
   double *P = nullptr;            // level >= 1: [27][S] interpolation from here to level-1
+  double *Pc = nullptr;           // levels with a coarser level: [27][S/8] the same
+                                  //   weights per fine cell (prolongation layout)
   double *diag = nullptr, *dinv = nullptr, *wdinv = nullptr;
   double *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   // FP32 copies for the mixed-precision V-cycle
   float *gx32 = nullptr;          // level 0: [3][S] (inner CG operator)
   __nv_bfloat16 *gxbf = nullptr;  // level 0: [3][S] (V-cycle smoother)
-  float *st32 = nullptr, *P32 = nullptr, *diag32 = nullptr, *wdinv32 = nullptr;
+  float *st32 = nullptr, *P32 = nullptr, *Pc32 = nullptr, *diag32 = nullptr,
+        *wdinv32 = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
 
   // accessors by precision
@@ -57,6 +60,7 @@ struct Level {
   template <typename T> T *Tt();
   template <typename T> const T *ST() const;
   template <typename T> const T *PP() const;
+  template <typename T> const T *PC() const;
   template <typename T> const T *DIAG() const;
   template <typename T> const T *WDINV() const;
 };
@@ -72,6 +76,8 @@ template <> inline const double *Level::ST<double>() const { return st; }
 template <> inline const float *Level::ST<float>() const { return st32; }
 template <> inline const double *Level::PP<double>() const { return P; }
 template <> inline const float *Level::PP<float>() const { return P32; }
+template <> inline const double *Level::PC<double>() const { return Pc; }
+template <> inline const float *Level::PC<float>() const { return Pc32; }
 template <> inline const double *Level::DIAG<double>() const { return diag; }
 template <> inline const float *Level::DIAG<float>() const { return diag32; }
 template <> inline const double *Level::WDINV<double>() const { return wdinv; }

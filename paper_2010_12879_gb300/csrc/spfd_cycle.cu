@@ -1,124 +1,40 @@
-// Solve-path kernels: multigrid V-cycle pieces, fused Krylov updates with
-// deterministic grid reductions, right-hand side, Psi scatter and |E|.
+// V-cycle kernels: smoothers, residuals, restriction, prolongation and the
+// coarsest-level solve.
 //
-// Paper: Eq. 3 (Sec. II) is the system; Sec. II-A fixes double precision and
-// a relative-residual stopping rule; Eq. 1 with the voxel averaging of
-// Sec. III-E gives |E|.  Every kernel here is bandwidth- or FP64-pipe bound;
-// none is a dense contraction, so no tensor-core path is used.
+// Paper: Eq. 3 (Sec. II) is the system; the paper's own preconditioner is
+// AmgX's algebraic multigrid (Sec. III).  These kernels implement the
+// geometric operator-dependent V-cycle that replaces it.  All are
+// bandwidth-bound stencil or transfer sweeps (the FP64 forms approach the
+// FP64 pipe's rate); none is a dense contraction, so no tensor-core path is
+// used.  One block handles one 8x8x8 brick (one thread per node) and stages
+// the vector it reads in shared memory (spfd_tile.cuh).
 #include "spfd_internal.cuh"
+#include "spfd_tile.cuh"
 
 namespace spfd {
 
-// --------------------------------------------------------------- conversions
-template <typename T> __device__ __forceinline__ T cv(double v) { return (T)v; }
-template <typename T> __device__ __forceinline__ T cv(float v) { return (T)v; }
-template <typename T> __device__ __forceinline__ T cv(__nv_bfloat16 v) {
-  return (T)__bfloat162float(v);
-}
-
-#define BRICK_PROLOGUE(g)                                              \
-  const size_t S = (size_t)(g).nb * BV;                                \
-  const int bk = blockIdx.x, t = threadIdx.x;                          \
-  const int s = bk * BV + t;                                           \
-  const int4 bc = (g).bco[bk];                                         \
-  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;                \
-  (void)S; (void)lx; (void)ly; (void)lz;
-
-// (A x)_s for the 7-point level-0 operator.  FP64: diag*x_s - sum g x_nbr
-// (fewest FP64-pipe operations).  FP32 (BF16 or FP32 g): sum g (x_s - x_nbr),
-// which is exactly zero on constants, so rounded conductances keep the
-// operator positive semidefinite.
-template <typename T, typename C>
-__device__ __forceinline__ T apply7(const Grid &g, const C *__restrict__ gx,
-                                    const T *__restrict__ diag,
-                                    const T *__restrict__ x, size_t S, int bk,
-                                    int4 bc, int s, int lx, int ly, int lz) {
-  int m;
-  if constexpr (sizeof(T) == 4) {
-    const T xs = x[s];
-    T acc = 0;
-    m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
-    if (m >= 0) acc += cv<T>(gx[s]) * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
-    if (m >= 0) acc += cv<T>(gx[m]) * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 1, 0);
-    if (m >= 0) acc += cv<T>(gx[S + s]) * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, -1, 0);
-    if (m >= 0) acc += cv<T>(gx[S + m]) * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, 1);
-    if (m >= 0) acc += cv<T>(gx[2 * S + s]) * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, -1);
-    if (m >= 0) acc += cv<T>(gx[2 * S + m]) * (xs - x[m]);
-    return acc;
-  }
-  T acc = diag[s] * x[s];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
-  if (m >= 0) acc -= cv<T>(gx[s]) * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
-  if (m >= 0) acc -= cv<T>(gx[m]) * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, 1, 0);
-  if (m >= 0) acc -= cv<T>(gx[S + s]) * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, -1, 0);
-  if (m >= 0) acc -= cv<T>(gx[S + m]) * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, 1);
-  if (m >= 0) acc -= cv<T>(gx[2 * S + s]) * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, -1);
-  if (m >= 0) acc -= cv<T>(gx[2 * S + m]) * x[m];
-  return acc;
-}
-
-template <typename T>
-__device__ __forceinline__ T apply27(const Grid &g, const T *__restrict__ st,
-                                     const T *__restrict__ x, size_t S, int bk,
-                                     int4 bc, int s, int lx, int ly, int lz) {
-  T acc = 0;
-#pragma unroll
-  for (int e = 0; e < 27; ++e) {
-    const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
-    int m = slot_nb(g, bk, bc, lx, ly, lz, dx, dy, dz);
-    if (m >= 0) acc += st[(size_t)e * S + s] * x[m];
-  }
-  return acc;
-}
-
 // ------------------------------------------------------------ smoothers
+// The 7-point kernels issue every load that does not need the neighbour
+// bricks (own x, b, conductances, ...) before the first barrier, then the
+// face halo and the low-face conductances, then compute from the tile.
 template <typename T, typename C>
 __global__ void __launch_bounds__(NT)
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r) {
-  BRICK_PROLOGUE(g);
-  r[s] = b[s] - apply7<T, C>(g, gx, diag, x, S, bk, bc, s, lx, ly, lz);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT)
-k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
-             const T *__restrict__ b, T *__restrict__ r) {
-  BRICK_PROLOGUE(g);
-  r[s] = b[s] - apply27<T>(g, st, x, S, bk, bc, s, lx, ly, lz);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT)
-k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
-               T *__restrict__ x) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  x[s] = wdinv[s] * b[s];
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT)
-k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
-                    T *__restrict__ x, const Scalars *sc, double inv_ndof) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  const T w = wdinv[s];
-  if (w > (T)0) {  // an unknown of level 0
-    const T bv = (T)((double)b[s] - sc->rsum * inv_ndof);
-    b[s] = bv;
-    x[s] = w * bv;
-  } else {
-    x[s] = (T)0;
-  }
+  __shared__ T tl[10][10][10];
+  __shared__ int sn[27];
+  const int bk = blockIdx.x, t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  load_nbr(g, bk, sn);
+  const T xc = x[s], bv = b[s];
+  Stencil7<T, C> A;
+  A.prefetch(gx, diag, S, s, lx, ly, lz);
+  tl[lz + 1][ly + 1][lx + 1] = xc;
+  __syncthreads();
+  tile_face_halo<T>(tl, x, sn);
+  A.resolve(gx, S, t, lx, ly, lz, sn);
+  __syncthreads();
+  r[s] = bv - A.apply(tl, lx, ly, lz);
 }
 
 template <typename T, typename C>
@@ -126,9 +42,35 @@ __global__ void __launch_bounds__(NT)
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
           const T *__restrict__ b, T *__restrict__ xout) {
-  BRICK_PROLOGUE(g);
-  T r = b[s] - apply7<T, C>(g, gx, diag, xin, S, bk, bc, s, lx, ly, lz);
-  xout[s] = xin[s] + wdinv[s] * r;
+  __shared__ T tl[10][10][10];
+  __shared__ int sn[27];
+  const int bk = blockIdx.x, t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  load_nbr(g, bk, sn);
+  const T xc = xin[s], bv = b[s], wv = wdinv[s];
+  Stencil7<T, C> A;
+  A.prefetch(gx, diag, S, s, lx, ly, lz);
+  tl[lz + 1][ly + 1][lx + 1] = xc;
+  __syncthreads();
+  tile_face_halo<T>(tl, xin, sn);
+  A.resolve(gx, S, t, lx, ly, lz, sn);
+  __syncthreads();
+  xout[s] = xc + wv * (bv - A.apply(tl, lx, ly, lz));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT)
+k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
+             const T *__restrict__ b, T *__restrict__ r) {
+  __shared__ T tl[10][10][10];
+  __shared__ int sn[27];
+  const int bk = blockIdx.x;
+  load_nbr(g, bk, sn);
+  __syncthreads();
+  tile_full<T>(tl, x, bk, sn);
+  __syncthreads();
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + threadIdx.x;
+  r[s] = b[s] - apply27_tile<T>(tl, st, S, s);
 }
 
 template <typename T>
@@ -136,52 +78,142 @@ __global__ void __launch_bounds__(NT)
 k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
            const T *__restrict__ xin, const T *__restrict__ b,
            T *__restrict__ xout) {
-  BRICK_PROLOGUE(g);
-  T r = b[s] - apply27<T>(g, st, xin, S, bk, bc, s, lx, ly, lz);
-  xout[s] = xin[s] + wdinv[s] * r;
+  __shared__ T tl[10][10][10];
+  __shared__ int sn[27];
+  const int bk = blockIdx.x;
+  load_nbr(g, bk, sn);
+  __syncthreads();
+  tile_full<T>(tl, xin, bk, sn);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  const T r = b[s] - apply27_tile<T>(tl, st, S, s);
+  xout[s] = tl[(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wdinv[s] * r;
+}
+
+// First sweep from a zero guess, x = omega D^-1 b: a streaming kernel, one
+// brick per block, 16 bytes per thread access.
+template <typename T>
+__global__ void __launch_bounds__(NT)
+k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
+               T *__restrict__ x) {
+  constexpr int N = V16<T>::N;
+  const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
+  const V16<T> w = ld16(wdinv + s0), bv = ld16(b + s0);
+  V16<T> xv;
+#pragma unroll
+  for (int i = 0; i < N; ++i) xv.v[i] = w.v[i] * bv.v[i];
+  st16(x + s0, xv);
+}
+
+// The same with the projection of b fused in: b <- b - mean(b) on the
+// unknowns (mean formed by the preceding reduction), in place.
+template <typename T>
+__global__ void __launch_bounds__(NT)
+k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
+                    T *__restrict__ x, const Scalars *sc, double) {
+  constexpr int N = V16<T>::N;
+  const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
+  T mean;
+  if constexpr (sizeof(T) == 4) mean = sc->rmean_f; else mean = sc->rmean;
+  const V16<T> w = ld16(wdinv + s0);
+  V16<T> bv = ld16(b + s0), xv;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (w.v[i] > (T)0) {  // an unknown of level 0
+      bv.v[i] -= mean;
+      xv.v[i] = w.v[i] * bv.v[i];
+    } else {
+      xv.v[i] = (T)0;
+    }
+  }
+  st16(b + s0, bv);
+  st16(x + s0, xv);
 }
 
 // ------------------------------------------------------------ transfers
-// Restriction r_c(I) = sum_d P[d][I] r_f(2I + d)  (P^T, the adjoint of the
-// prolongation below).
+// Restriction r_c(I) = sum_d P[d][I] r_f(2I + d) (P^T, the adjoint of the
+// prolongation below).  A coarse brick B reads the 17^3 fine nodes
+// 16B-1 .. 16B+15 (per axis) from the 27 fine bricks 2B-1 .. 2B+1.
 template <typename T>
 __global__ void __launch_bounds__(NT)
-k_restrict(Grid gf, Grid gc, const T *__restrict__ P, const T *__restrict__ rf,
+k_restrict(Grid gc, const T *__restrict__ P, const T *__restrict__ rf,
            T *__restrict__ bcoarse) {
-  BRICK_PROLOGUE(gc);
-  const int I = bc.x * 8 + lx, J = bc.y * 8 + ly, K = bc.z * 8 + lz;
+  __shared__ T fs[17][17][17];
+  __shared__ int sk[27];
+  const int bk = blockIdx.x, t = threadIdx.x;
+  if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
+  __syncthreads();
+  for (int q = t; q < 17 * 17 * 17; q += NT) {
+    const int fz = q / 289, fy = (q / 17) % 17, fx = q % 17;
+    const int nb = sk[((fz + 7) >> 3) * 9 + ((fy + 7) >> 3) * 3 + ((fx + 7) >> 3)];
+    fs[fz][fy][fx] = nb >= 0
+        ? rf[(size_t)nb * BV + (((fz - 1) & 7) * 8 + ((fy - 1) & 7)) * 8 + ((fx - 1) & 7)]
+        : T(0);
+  }
+  __syncthreads();
+  const size_t Sc = (size_t)gc.nb * BV, s = (size_t)bk * BV + t;
+  const int cx = 2 * (t & 7) + 1, cy = 2 * ((t >> 3) & 7) + 1, cz = 2 * (t >> 6) + 1;
   T acc = 0;
 #pragma unroll
   for (int d = 0; d < 27; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-    int n = slot_at(gf, 2 * I + dx, 2 * J + dy, 2 * K + dz);
-    if (n >= 0) acc += P[(size_t)d * S + s] * rf[n];
+    acc += P[(size_t)d * Sc + s] * fs[cz + dz][cy + dy][cx + dx];
   }
   bcoarse[s] = acc;
 }
 
-// Prolongation + correction e_f(n) += sum over the <= 8 coarse parents I of n
-// of P[n - 2I][I] e_c(I).
+// Prolongation + correction e_f(n) += sum over the <= 8 parents I of n of
+// P(n, I) e_c(I).  Threads are grouped by the parity class of their node
+// (two warps per class), so a warp shares one parent pattern, and the
+// per-cell weights Pc (k_pack_Pc) of a warp are consecutive: they are loaded
+// coalesced before the first barrier.  The brick's parents are the coarse
+// nodes 4F .. 4F+4, held by the coarse bricks (F >> 1) + {0,1}; their
+// values are staged in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(NT)
-k_prolong(Grid gf, Grid gc, const T *__restrict__ P, const T *__restrict__ ec,
+k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
           T *__restrict__ ef) {
-  BRICK_PROLOGUE(gf);
-  const size_t Sc = (size_t)gc.nb * BV;
-  const int i = bc.x * 8 + lx, j = bc.y * 8 + ly, k = bc.z * 8 + lz;
-  const int ox = i & 1, oy = j & 1, oz = k & 1;
+  __shared__ T es[125];
+  __shared__ int sp[8];
+  const int bk = blockIdx.x, t = threadIdx.x;
+  if (t < 8) sp[t] = gf.par[(size_t)bk * 8 + t];
+  const int q = t >> 6, cell = t & 63;
+  const int ux = q & 1, uy = (q >> 1) & 1, uz = q >> 2;
+  const int ccx = cell & 3, ccy = (cell >> 2) & 3, ccz = cell >> 4;
+  const int lx = 2 * ccx + ux, ly = 2 * ccy + uy, lz = 2 * ccz + uz;
+  const size_t s = (size_t)bk * BV + (lz * 8 + ly) * 8 + lx;
+  const size_t NC = (size_t)gf.nb * 64, cid = (size_t)bk * 64 + cell;
+  const int4 bc = gf.bco[bk];
+  const T efv = ef[s];
+  // weight of parent c + o (o <= u) sits at compact index
+  // j = (oz (uy+1) + oy) (ux+1) + ox, the (oz, oy, ox) order of k_pack_Pc
+  const int off = pc_off(q);
+  T w[8];
+#pragma unroll
+  for (int c8 = 0; c8 < 8; ++c8) {
+    const int ox = c8 & 1, oy = (c8 >> 1) & 1, oz = c8 >> 2;
+    const int j = (oz * (uy + 1) + oy) * (ux + 1) + ox;
+    w[c8] = (ox <= ux && oy <= uy && oz <= uz) ? Pc[(size_t)(off + j) * NC + cid] : T(0);
+  }
+  __syncthreads();
+  if (t < 125) {
+    const int cx = t % 5, cy = (t / 5) % 5, cz = t / 25;
+    const int gx_ = 4 * bc.x + cx, gy_ = 4 * bc.y + cy, gz_ = 4 * bc.z + cz;
+    const int o = (((gz_ >> 3) - (bc.z >> 1)) << 2) | (((gy_ >> 3) - (bc.y >> 1)) << 1) |
+                  ((gx_ >> 3) - (bc.x >> 1));
+    const int nb = sp[o];
+    es[t] = nb >= 0 ? ec[(size_t)nb * BV + ((gz_ & 7) * 8 + (gy_ & 7)) * 8 + (gx_ & 7)] : T(0);
+  }
+  __syncthreads();
   T acc = 0;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-    if ((cx && !ox) || (cy && !oy) || (cz && !oz)) continue;
-    // parent index and offset d = n - 2I on each axis
-    const int I = (i >> 1) + cx, J = (j >> 1) + cy, K = (k >> 1) + cz;
-    const int dx = i - 2 * I, dy = j - 2 * J, dz = k - 2 * K;
-    int sc = slot_at(gc, I, J, K);
-    if (sc >= 0) acc += P[(size_t)sidx(dx, dy, dz) * Sc + sc] * ec[sc];
+  for (int c8 = 0; c8 < 8; ++c8) {
+    const int ox = c8 & 1, oy = (c8 >> 1) & 1, oz = c8 >> 2;
+    if (ox <= ux && oy <= uy && oz <= uz)
+      acc += w[c8] * es[((ccz + oz) * 5 + (ccy + oy)) * 5 + (ccx + ox)];
   }
-  ef[s] += acc;
+  ef[s] = efv + acc;
 }
 
 // Coarsest level: x = B^{-1} b on the m listed unknowns (dense, FP64); one
@@ -215,13 +247,14 @@ void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
 template <typename T>
 void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
                          cudaStream_t st) {
-  if (g.nb) k_jacobi_first<T><<<g.nb, NT, 0, st>>>(wdinv, b, x);
+  if (g.nb) k_jacobi_first<T><<<g.nb, NT / V16<T>::N, 0, st>>>(wdinv, b, x);
 }
 template <typename T>
 void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
                               const Scalars *sc, double inv_ndof,
                               cudaStream_t st) {
-  if (g.nb) k_jacobi_first_proj<T><<<g.nb, NT, 0, st>>>(wdinv, b, x, sc, inv_ndof);
+  if (g.nb)
+    k_jacobi_first_proj<T><<<g.nb, NT / V16<T>::N, 0, st>>>(wdinv, b, x, sc, inv_ndof);
 }
 template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
@@ -234,9 +267,9 @@ void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
   if (g.nb) k_jacobi27<T><<<g.nb, NT, 0, st>>>(g, stc, wdinv, xin, b, xout);
 }
 template <typename T>
-void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
+void launch_restrict(const Grid &, const Grid &gc, const T *P, const T *rf,
                      T *bcoarse, cudaStream_t st) {
-  if (gc.nb) k_restrict<T><<<gc.nb, NT, 0, st>>>(gf, gc, P, rf, bcoarse);
+  if (gc.nb) k_restrict<T><<<gc.nb, NT, 0, st>>>(gc, P, rf, bcoarse);
 }
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,

@@ -26,12 +26,24 @@ __host__ __device__ __forceinline__ constexpr int sidx(int dx, int dy, int dz) {
   return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
 }
 
+// First per-cell prolongation weight of parity class q (node 2c + u of a
+// 2x2x2 cell, q = uz*4 + uy*2 + ux): sum over q' < q of 2^popcount(q').
+__host__ __device__ __forceinline__ constexpr int pc_off(int q) {
+  return q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 3 : q == 3 ? 5 : q == 4 ? 9
+       : q == 5 ? 11 : q == 6 ? 15 : 19;
+}
+
 struct Grid {
   int NX, NY, NZ;       // nodes per axis
   int MX, MY, MZ;       // bricks per axis
   int nb;               // active bricks
   const int *bmap;      // [MZ][MY][MX] brick id or -1
   const int4 *bco;      // [nb] brick coordinates (x, y, z, 0)
+  const int *nbr;       // [nb][27] ids of the bricks at offset sidx(dx,dy,dz), or -1
+  const int *kid;       // coarse levels: [nb][27] ids of the finer-level bricks
+                        //   2B + (o - 1), o in {0,1,2}^3 (index o.z*9+o.y*3+o.x), or -1
+  const int *par;       // levels with a coarser level: [nb][8] ids of the coarser
+                        //   bricks (B >> 1) + o, o in {0,1}^3 (index o.z*4+o.y*2+o.x), or -1
 };
 
 // Brick id of node (i, j, k) or -1 (outside the grid or brick not stored).
@@ -68,6 +80,9 @@ struct Scalars {
   double alpha, beta;
   double zsum;      // sum of z over the single component (projection)
   double rsum;      // sum of r over the unknowns (projection of r)
+  double inv_ndof;  // 1 / (number of unknowns), set by the build
+  double zmean, rmean;  // zsum / n, rsum / n (formed once by the last block)
+  float alpha_f, beta_f, zmean_f, rmean_f;  // FP32 copies for FP32 kernels
   double aux[8];    // misc results (power iteration, refinement)
   unsigned int ticket[8];  // last-block counters, one per reduction site
   int status;       // SPFD_DEV_* bits
@@ -77,6 +92,7 @@ enum : int {
   DEV_BAD_SIGMA = 1,     // NaN / negative / infinite conductivity
   DEV_BAD_A = 2,         // non-finite edge potential on a conducting edge
   DEV_UF_CAP = 4,        // union-find loop hit its iteration cap
+  DEV_BAD_PIVOT = 8,     // coarsest dense inverse met a non-positive pivot
 };
 
 // ---------------------------------------------------------------- launchers
@@ -103,8 +119,11 @@ void launch_galerkin(const Grid &gf, const Grid &gc, const double *gx,
 void launch_symmetrize(const Grid &gc, double *stc, cudaStream_t st);
 void launch_pack_P(const Grid &gf, const Grid &gc, const double *W, double *P,
                    cudaStream_t st);
+void launch_pack_Pc(const Grid &gf, const double *W, double *Pc, cudaStream_t st);
 void launch_coarse_diag(const Grid &gc, const double *stc, double thresh,
                         double *diag, double *dinv, cudaStream_t st);
+double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
+                             cudaStream_t st);
 
 // V-cycle pieces (spfd_cycle.cu); T = vector type, C = 7-point coefficient type.
 template <typename T, typename C>
@@ -142,6 +161,12 @@ void launch_coarse_solve(int m, const int *idx, const double *Binv,
 template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st);
+// Number of partial sums launch_apply_dot writes for nb bricks (16 per brick
+// for float, 1 for double); launch_finish_pq adds n of them (scratch: at
+// least 152 doubles, not overlapping) and sets alpha = rz / pq.
+template <typename T> int apply_dot_partials(int nb);
+void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
+                      cudaStream_t st);
 template <typename T>
 void launch_update_xr(int nb, T *x, T *r, const T *p, const T *q, Scalars *sc,
                       double *partials, cudaStream_t st);
@@ -183,6 +208,8 @@ void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st);
 void launch_power_step(int nb, const double *r, const double *dinv, double *w,
                        Scalars *sc, double *partials, cudaStream_t st);
 void launch_scale(int nb, double *v, double f, cudaStream_t st);
+void launch_normalize(int nb, const double *w, double *v, const Scalars *sc,
+                      cudaStream_t st);
 void launch_scaled_copy(int nb, const double *src, double f, double *dst,
                         cudaStream_t st);
 

@@ -1,13 +1,42 @@
-// Krylov-loop kernels with fused, deterministic grid reductions; the
-// right-hand side of Eq. 3, the Psi scatter and the |E| of Eq. 1.
+// Krylov-loop kernels with fused, deterministic reductions; the right-hand
+// side of Eq. 3, the Psi scatter and the |E| of Eq. 1.
 //
-// Every reduction here finishes on the device: each block writes its partial
-// sums, and the last block to arrive (ticket counter) adds the partials in a
-// fixed order and updates the Krylov scalars in place, so the loop needs no
-// host round trip except the convergence test.
+// Reductions finish on the device: blocks write partial sums, and either the
+// last block to arrive (ticket counter) or a one-block finishing kernel adds
+// them in a fixed order and updates the Krylov scalars in place, so the loop
+// needs no host round trip except the convergence test.
+//
+// GB300's FP64 pipe retires about one FP64 operation per 11 bytes of HBM
+// traffic, so FP32 kernels here keep every per-element operation in FP32:
+// scalars arrive pre-converted (alpha_f, beta_f, ...) and dot products sum
+// per thread in compensated (Kahan) FP32 before the FP64 tree across threads
+// and blocks.
+#include <algorithm>
+
 #include "spfd_internal.cuh"
+#include "spfd_tile.cuh"
 
 namespace spfd {
+
+// ------------------------------------------------------------ accumulators
+// Per-thread running sum: FP64 for double kernels, compensated FP32 for float
+// kernels (about FP64 accuracy over the few dozen terms a thread adds).
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
 
 // ------------------------------------------------------------ reductions
 template <int NV>
@@ -65,105 +94,157 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket,
   return true;
 }
 
-#define BRICK_PROLOGUE(g)                                              \
-  const size_t S = (size_t)(g).nb * BV;                                \
-  const int bk = blockIdx.x, t = threadIdx.x;                          \
-  const int s = bk * BV + t;                                           \
-  const int4 bc = (g).bco[bk];                                         \
-  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;                \
-  (void)S; (void)lx; (void)ly; (void)lz; (void)bc;
+// Grid-stride reduction kernels use at most RED_GRID blocks, so the ticket
+// sees few same-address atomics.
+constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SMs
 
-template <typename T>
-__device__ __forceinline__ T apply7k(const Grid &g, const T *__restrict__ gx,
-                                     const T *__restrict__ diag,
-                                     const T *__restrict__ x, size_t S, int bk,
-                                     int4 bc, int s, int lx, int ly, int lz) {
-  int m;
-  if constexpr (sizeof(T) == 4) {  // difference form: exactly zero on constants
-    const T xs = x[s];
-    T acc = 0;
-    m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
-    if (m >= 0) acc += gx[s] * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
-    if (m >= 0) acc += gx[m] * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 1, 0);
-    if (m >= 0) acc += gx[S + s] * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, -1, 0);
-    if (m >= 0) acc += gx[S + m] * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, 1);
-    if (m >= 0) acc += gx[2 * S + s] * (xs - x[m]);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, -1);
-    if (m >= 0) acc += gx[2 * S + m] * (xs - x[m]);
-    return acc;
-  }
-  T acc = diag[s] * x[s];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 1, 0, 0);
-  if (m >= 0) acc -= gx[s] * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
-  if (m >= 0) acc -= gx[m] * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, 1, 0);
-  if (m >= 0) acc -= gx[S + s] * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, -1, 0);
-  if (m >= 0) acc -= gx[S + m] * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, 1);
-  if (m >= 0) acc -= gx[2 * S + s] * x[m];
-  m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, -1);
-  if (m >= 0) acc -= gx[2 * S + m] * x[m];
-  return acc;
-}
-
-// q = A p and p.q; the last block sets alpha = rz / pq.
+// ------------------------------------------------------------ CG operator
+// q = A p on one brick per block, with p staged in a shared tile; each block
+// writes its part of p.q, and k_finish_pq adds them.
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
-            const T *__restrict__ p, T *__restrict__ q, Scalars *sc,
-            double *partials) {
-  BRICK_PROLOGUE(g);
-  T qs = apply7k<T>(g, gx, diag, p, S, bk, bc, s, lx, ly, lz);
+            const T *__restrict__ p, T *__restrict__ q, double *partials) {
+  __shared__ T tl[10][10][10];
+  __shared__ int sn[27];
+  const int bk = blockIdx.x, t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  load_nbr(g, bk, sn);
+  const T pc = p[s];
+  Stencil7<T, T> A;
+  A.prefetch(gx, diag, S, s, lx, ly, lz);
+  tl[lz + 1][ly + 1][lx + 1] = pc;
+  __syncthreads();
+  tile_face_halo<T>(tl, p, sn);
+  A.resolve(gx, S, t, lx, ly, lz, sn);
+  __syncthreads();
+  const T qs = A.apply(tl, lx, ly, lz);
   q[s] = qs;
-  double v[1] = {(double)p[s] * (double)qs};
-  double tot[1];
-  if (grid_sum<1>(v, partials, &sc->ticket[0], tot)) {
-    sc->pq = tot[0];
-    sc->alpha = tot[0] > 0.0 ? sc->rz / tot[0] : 0.0;
+  const T pq = pc * qs;
+  if constexpr (sizeof(T) == 4) {
+    // warp sums in error-free FP32 (TwoSum pairs); one FP64 partial per warp,
+    // no block barrier
+    float hi = pq, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      const float sh = hi + oh, bb = sh - hi;
+      const float e = (hi - (sh - bb)) + (oh - bb);
+      hi = sh;
+      lo = lo + ol + e;
+    }
+    if ((t & 31) == 0) partials[(size_t)bk * (NT / 32) + (t >> 5)] = (double)hi + (double)lo;
+  } else {
+    // shared-memory tree: warp 0 adds 16 values per lane, then 5 shuffles,
+    // about one FP64 addition per node instead of five
+    __shared__ double red[NT];
+    red[t] = pq;
+    __syncthreads();
+    if (t < 32) {
+      double a = 0.0;
+#pragma unroll
+      for (int k = 0; k < NT / 32; ++k) a += red[k * 32 + t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (t == 0) partials[bk] = a;
+    }
   }
 }
 
-// x += alpha p; r -= alpha q; rr = r.r
+// Number of partials k_apply_dot writes for nb bricks.
+template <typename T>
+int apply_dot_partials(int nb) { return sizeof(T) == 4 ? nb * (NT / 32) : nb; }
+
+// pq = sum of the n partials of k_apply_dot (blocks add contiguous chunks,
+// the last block adds the block sums, fixed order); alpha = rz / pq.
+// scratch must not overlap the partials.
+__global__ void __launch_bounds__(NT)
+k_finish_pq(const double *__restrict__ partials, int n, double *scratch, Scalars *sc) {
+  double a = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    a += partials[i];
+  double v[1] = {a};
+  double tot[1];
+  if (grid_sum<1>(v, scratch, &sc->ticket[6], tot)) {
+    sc->pq = tot[0];
+    const double al = tot[0] > 0.0 ? sc->rz / tot[0] : 0.0;
+    sc->alpha = al;
+    sc->alpha_f = (float)al;
+  }
+}
+
+// x += alpha p; r -= alpha q; rr = r.r and rsum = sum r (removed nodes hold
+// r = 0); the last block also forms rmean = rsum / n.
 template <typename T>
 __global__ void __launch_bounds__(NT)
-k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-            const T *__restrict__ q, Scalars *sc, double *partials) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  const T alpha = (T)sc->alpha;
-  x[s] += alpha * p[s];
-  T rs = r[s] - alpha * q[s];
-  r[s] = rs;
-  // removed nodes hold r = 0, so the plain sum is the sum over the unknowns
-  double v[2] = {(double)rs * (double)rs, (double)rs};
+k_update_xr(int nb, T *__restrict__ x, T *__restrict__ r,
+            const T *__restrict__ p, const T *__restrict__ q, Scalars *sc,
+            double *partials) {
+  constexpr int N = V16<T>::N;
+  T alpha;
+  if constexpr (sizeof(T) == 4) alpha = sc->alpha_f; else alpha = sc->alpha;
+  Acc<T> rr, rs_sum;
+  const size_t nv = (size_t)nb * BV / N;
+  for (size_t vi = blockIdx.x * (size_t)blockDim.x + threadIdx.x; vi < nv;
+       vi += (size_t)gridDim.x * blockDim.x) {
+    const size_t s0 = vi * N;
+    V16<T> xv = ld16(x + s0), rv = ld16(r + s0);
+    const V16<T> pv = ld16(p + s0), qv = ld16(q + s0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      xv.v[i] += alpha * pv.v[i];
+      rv.v[i] -= alpha * qv.v[i];
+      rr.add(rv.v[i] * rv.v[i]);
+      rs_sum.add(rv.v[i]);
+    }
+    st16(x + s0, xv);
+    st16(r + s0, rv);
+  }
+  double v[2] = {rr.get(), rs_sum.get()};
   double tot[2];
   if (grid_sum<2>(v, partials, &sc->ticket[1], tot)) {
     sc->rr = tot[0];
     sc->rsum = tot[1];
+    sc->rmean = tot[1] * sc->inv_ndof;
+    sc->rmean_f = (float)sc->rmean;
   }
 }
 
-// rz = r.z (new), beta = rz/rz_old, zsum = sum of z over the unknowns.
+// rz = r.z (new), beta = rz / rz_old, zsum = sum of z over the unknowns and
+// zmean = zsum / n.
 template <typename T>
 __global__ void __launch_bounds__(NT)
-k_dot_rz(const T *__restrict__ r, const T *__restrict__ z,
+k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
          const int *__restrict__ comp, Scalars *sc, double *partials,
          int first) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  const double zs = (double)z[s];
-  double v[2] = {(double)r[s] * zs, comp[s] >= 0 ? zs : 0.0};
+  constexpr int N = V16<T>::N;
+  Acc<T> rz, zsum;
+  const size_t nv = (size_t)nb * BV / N;
+  for (size_t vi = blockIdx.x * (size_t)blockDim.x + threadIdx.x; vi < nv;
+       vi += (size_t)gridDim.x * blockDim.x) {
+    const size_t s0 = vi * N;
+    const V16<T> rv = ld16(r + s0), zv = ld16(z + s0);
+    int c[N];
+    ld_ints<N>(comp + s0, c);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      rz.add(rv.v[i] * zv.v[i]);
+      if (c[i] >= 0) zsum.add(zv.v[i]);
+    }
+  }
+  double v[2] = {rz.get(), zsum.get()};
   double tot[2];
   if (grid_sum<2>(v, partials, &sc->ticket[2], tot)) {
-    double old = sc->rz;
+    const double old = sc->rz;
     sc->rz_old = old;
     sc->rz = tot[0];
-    sc->beta = (first || old == 0.0) ? 0.0 : tot[0] / old;
+    const double beta = (first || old == 0.0) ? 0.0 : tot[0] / old;
+    sc->beta = beta;
+    sc->beta_f = (float)beta;
     sc->zsum = tot[1];
+    sc->zmean = tot[1] * sc->inv_ndof;
+    sc->zmean_f = (float)sc->zmean;
   }
 }
 
@@ -176,10 +257,9 @@ k_comp_sum(const T *__restrict__ v, const int *__restrict__ comp, double *csum) 
   const int c = comp[s];
   const unsigned grp = __match_any_sync(0xffffffffu, c);
   double x = c >= 0 ? (double)v[s] : 0.0;
-  // sum within the group: walk the set bits (at most 32)
   double tot = 0.0;
   unsigned m = grp;
-  while (m) {
+  while (m) {  // sum within the group: walk the set bits (at most 32)
     int src = __ffs(m) - 1;
     tot += __shfl_sync(grp, x, src);
     m &= m - 1;
@@ -187,41 +267,56 @@ k_comp_sum(const T *__restrict__ v, const int *__restrict__ comp, double *csum) 
   if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&csum[c], tot);
 }
 
-// p = (z - mean_c(z)) + beta p on the unknowns.  With one component the mean
-// comes from sc->zsum; otherwise from csum[c] / csize[c].
+// p = (z - mean_c(z)) + beta p on the unknowns.  One component: the mean is
+// sc->zmean; several: csum[c] / csize[c].
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_pupdate(T *__restrict__ p, const T *__restrict__ z,
           const int *__restrict__ comp, const Scalars *sc,
-          const double *__restrict__ csum, const int *__restrict__ csize,
-          double inv_ndof) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  const int c = comp[s];
-  if (c < 0) { p[s] = (T)0; return; }
-  const double mean = csum ? csum[c] / (double)csize[c] : sc->zsum * inv_ndof;
-  p[s] = (T)((double)z[s] - mean) + (T)sc->beta * p[s];
+          const double *__restrict__ csum, const int *__restrict__ csize) {
+  constexpr int N = V16<T>::N;
+  const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
+  T mean1, beta;
+  if constexpr (sizeof(T) == 4) { mean1 = sc->zmean_f; beta = sc->beta_f; }
+  else { mean1 = sc->zmean; beta = sc->beta; }
+  int c[N];
+  ld_ints<N>(comp + s0, c);
+  const V16<T> zv = ld16(z + s0);
+  V16<T> pv = ld16(p + s0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (c[i] < 0) { pv.v[i] = (T)0; continue; }
+    const T mean = csum ? (T)(csum[c[i]] / (double)csize[c[i]]) : mean1;
+    pv.v[i] = (zv.v[i] - mean) + beta * pv.v[i];
+  }
+  st16(p + s0, pv);
 }
 
-// v -= mean_c(v) on the unknowns (single component: mean = sc->aux[slot]/n).
+// v -= mean_c(v) on the unknowns (single component: mean = aux[slot] / n).
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_sub_mean(T *__restrict__ v, const int *__restrict__ comp, const Scalars *sc,
            int aux_slot, const double *__restrict__ csum,
-           const int *__restrict__ csize, double inv_ndof) {
+           const int *__restrict__ csize) {
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
   const int c = comp[s];
   if (c < 0) { v[s] = (T)0; return; }
-  const double mean = csum ? csum[c] / (double)csize[c] : sc->aux[aux_slot] * inv_ndof;
-  v[s] = (T)((double)v[s] - mean);
+  const T mean = csum ? (T)(csum[c] / (double)csize[c])
+                      : (T)(sc->aux[aux_slot] * sc->inv_ndof);
+  v[s] = v[s] - mean;
 }
 
 // aux[slot] = sum over unknowns of x*y (y = null: plain sum of x).
 template <typename T>
 __global__ void __launch_bounds__(NT)
-k_dot(const T *__restrict__ x, const T *__restrict__ y,
+k_dot(int nb, const T *__restrict__ x, const T *__restrict__ y,
       const int *__restrict__ comp, Scalars *sc, double *partials, int slot) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  double v[1] = {comp[s] >= 0 ? (double)x[s] * (y ? (double)y[s] : 1.0) : 0.0};
+  Acc<T> acc;
+  for (int bk = blockIdx.x; bk < nb; bk += gridDim.x) {
+    const size_t s = (size_t)bk * BV + threadIdx.x;
+    if (comp[s] >= 0) acc.add(y ? x[s] * y[s] : x[s]);
+  }
+  double v[1] = {acc.get()};
   double tot[1];
   if (grid_sum<1>(v, partials, &sc->ticket[3], tot)) sc->aux[slot] = tot[0];
 }
@@ -233,7 +328,13 @@ k_dot(const T *__restrict__ x, const T *__restrict__ y,
 __global__ void __launch_bounds__(NT)
 k_rhs(Grid g, const double *__restrict__ gx, const double *__restrict__ a,
       double *__restrict__ b, int *status) {
-  BRICK_PROLOGUE(g);
+  __shared__ int sn[27];
+  const int bk = blockIdx.x, t = threadIdx.x;
+  load_nbr(g, bk, sn);
+  __syncthreads();
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  const int4 bc = g.bco[bk];
+  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
   const int i = bc.x * 8 + lx, j = bc.y * 8 + ly, k = bc.z * 8 + lz;
   double acc = 0.0;
   bool bad = false;
@@ -242,7 +343,7 @@ k_rhs(Grid g, const double *__restrict__ gx, const double *__restrict__ a,
     const size_t n = ((size_t)k * g.NY + j) * g.NX + i;
     auto term = [&](double ge, size_t idx, double sign) {
       if (ge > 0.0) {
-        double av = a[idx];
+        const double av = a[idx];
         if (!isfinite(av)) bad = true;
         acc += sign * ge * av;
       }
@@ -250,13 +351,16 @@ k_rhs(Grid g, const double *__restrict__ gx, const double *__restrict__ a,
     term(gx[s], n, 1.0);
     term(gx[S + s], NN + n, 1.0);
     term(gx[2 * S + s], 2 * NN + n, 1.0);
-    int m;
-    m = slot_nb(g, bk, bc, lx, ly, lz, -1, 0, 0);
-    if (m >= 0) term(gx[m], n - 1, -1.0);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, -1, 0);
-    if (m >= 0) term(gx[S + m], NN + n - g.NX, -1.0);
-    m = slot_nb(g, bk, bc, lx, ly, lz, 0, 0, -1);
-    if (m >= 0) term(gx[2 * S + m], 2 * NN + n - (size_t)g.NX * g.NY, -1.0);
+    // -edges: the +edge conductance of the neighbour node
+    int nb;
+    if (lx > 0) term(gx[s - 1], n - 1, -1.0);
+    else if ((nb = sn[sidx(-1, 0, 0)]) >= 0) term(gx[(size_t)nb * BV + t + 7], n - 1, -1.0);
+    if (ly > 0) term(gx[S + s - 8], NN + n - g.NX, -1.0);
+    else if ((nb = sn[sidx(0, -1, 0)]) >= 0)
+      term(gx[S + (size_t)nb * BV + t + 56], NN + n - g.NX, -1.0);
+    if (lz > 0) term(gx[2 * S + s - 64], 2 * NN + n - (size_t)g.NX * g.NY, -1.0);
+    else if ((nb = sn[sidx(0, 0, -1)]) >= 0)
+      term(gx[2 * S + (size_t)nb * BV + t + 448], 2 * NN + n - (size_t)g.NX * g.NY, -1.0);
   }
   b[s] = bad ? 0.0 : acc;
   if (bad) atomicOr(status, DEV_BAD_A);
@@ -269,9 +373,9 @@ __global__ void k_scatter(Grid g, const T *__restrict__ x,
   const size_t NN = (size_t)g.NX * g.NY * g.NZ;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < NN;
        n += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(n % g.NX), j = (int)((n / g.NX) % g.NY),
-        k = (int)(n / ((size_t)g.NX * g.NY));
-    int s = slot_at(g, i, j, k);
+    const int i = (int)(n % g.NX), j = (int)((n / g.NX) % g.NY),
+              k = (int)(n / ((size_t)g.NX * g.NY));
+    const int s = slot_at(g, i, j, k);
     psi[n] = (s >= 0 && comp[s] >= 0) ? (double)x[s] : 0.0;
   }
 }
@@ -280,8 +384,10 @@ __global__ void k_scatter(Grid g, const T *__restrict__ x,
 __global__ void __launch_bounds__(NT)
 k_gather(Grid g, const double *__restrict__ psi, const int *__restrict__ comp,
          double *__restrict__ x) {
-  BRICK_PROLOGUE(g);
-  const int i = bc.x * 8 + lx, j = bc.y * 8 + ly, k = bc.z * 8 + lz;
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const size_t s = (size_t)bk * BV + t;
+  const int4 bc = g.bco[bk];
+  const int i = bc.x * 8 + (t & 7), j = bc.y * 8 + ((t >> 3) & 7), k = bc.z * 8 + (t >> 6);
   double v = 0.0;
   if (comp[s] >= 0) v = psi[((size_t)k * g.NY + j) * g.NX + i];
   x[s] = v;
@@ -298,18 +404,18 @@ __global__ void k_efield(const unsigned char *__restrict__ mask,
   for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < NV_;
        v += (size_t)gridDim.x * blockDim.x) {
     if (!mask[v]) { E[v] = 0.0; continue; }
-    size_t i = v % nx, j = (v / nx) % ny, k = v / ((size_t)nx * ny);
-    size_t n000 = (k * NY + j) * NX + i;
+    const size_t i = v % nx, j = (v / nx) % ny, k = v / ((size_t)nx * ny);
+    const size_t n000 = (k * NY + j) * NX + i;
     double ex = 0.0, ey = 0.0, ez = 0.0;
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        size_t tx = n000 + (q * NY + r) * NX;       // x edge at (i, j+r, k+q)
+        const size_t tx = n000 + (q * NY + r) * NX;  // x edge at (i, j+r, k+q)
         ex += a[tx] + psi[tx + 1] - psi[tx];
-        size_t ty = n000 + q * NY * NX + r;         // y edge at (i+r, j, k+q)
+        const size_t ty = n000 + q * NY * NX + r;    // y edge at (i+r, j, k+q)
         ey += a[NN + ty] + psi[ty + NX] - psi[ty];
-        size_t tz = n000 + q * NX + r;              // z edge at (i+r, j+q, k)
+        const size_t tz = n000 + q * NX + r;         // z edge at (i+r, j+q, k)
         ez += a[2 * NN + tz] + psi[tz + NX * NY] - psi[tz];
       }
     ex *= c; ey *= c; ez *= c;
@@ -329,14 +435,26 @@ k_power_init(const double *__restrict__ diag, double *__restrict__ v) {
 
 // w = D^{-1} A v given r = -A v; aux[4] = |w|^2.
 __global__ void __launch_bounds__(NT)
-k_power_step(const double *__restrict__ r, const double *__restrict__ dinv,
+k_power_step(int nb, const double *__restrict__ r, const double *__restrict__ dinv,
              double *__restrict__ w, Scalars *sc, double *partials) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  double ws = -dinv[s] * r[s];
-  w[s] = ws;
-  double v[1] = {ws * ws};
+  double acc = 0.0;
+  for (int bk = blockIdx.x; bk < nb; bk += gridDim.x) {
+    const size_t s = (size_t)bk * BV + threadIdx.x;
+    const double ws = -dinv[s] * r[s];
+    w[s] = ws;
+    acc += ws * ws;
+  }
+  double v[1] = {acc};
   double tot[1];
   if (grid_sum<1>(v, partials, &sc->ticket[4], tot)) sc->aux[4] = tot[0];
+}
+
+// v = w / |w| with |w|^2 from sc->aux[4] (power iteration without a host trip).
+__global__ void __launch_bounds__(NT)
+k_normalize(const double *__restrict__ w, double *__restrict__ v, const Scalars *sc) {
+  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  const double n2 = sc->aux[4];
+  v[s] = n2 > 0.0 ? w[s] * rsqrt(n2) : 0.0;
 }
 
 __global__ void __launch_bounds__(NT) k_scale(double *__restrict__ v, double f) {
@@ -374,17 +492,25 @@ k_axpy_mixed(double *__restrict__ x, const float *__restrict__ d, double f) {
   x[s] += f * (double)d[s];
 }
 
-// r32 = (float)(f * r64); the sum of r32 lands in sc->rsum for the fused
-// projection of the first V-cycle sweep.
+// r32 = (float)(f * r64); sum(r32) and its mean land in sc->rsum / rmean_f
+// for the fused projection of the first V-cycle sweep.
 __global__ void __launch_bounds__(NT)
-k_scale_to_f32(const double *__restrict__ r, double f, float *__restrict__ r32,
-               Scalars *sc, double *partials) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  const float v = (float)(f * r[s]);
-  r32[s] = v;
-  double t[1] = {(double)v};
+k_scale_to_f32(int nb, const double *__restrict__ r, double f,
+               float *__restrict__ r32, Scalars *sc, double *partials) {
+  Acc<float> acc;
+  for (int bk = blockIdx.x; bk < nb; bk += gridDim.x) {
+    const size_t s = (size_t)bk * BV + threadIdx.x;
+    const float v = (float)(f * r[s]);
+    r32[s] = v;
+    acc.add(v);
+  }
+  double t[1] = {acc.get()};
   double tot[1];
-  if (grid_sum<1>(t, partials, &sc->ticket[5], tot)) sc->rsum = tot[0];
+  if (grid_sum<1>(t, partials, &sc->ticket[5], tot)) {
+    sc->rsum = tot[0];
+    sc->rmean = tot[0] * sc->inv_ndof;
+    sc->rmean_f = (float)sc->rmean;
+  }
 }
 
 // ------------------------------------------------------------ launchers
@@ -405,14 +531,18 @@ void launch_axpy_mixed(int nb, double *x, const float *d, double f,
 }
 void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
                          Scalars *sc, double *partials, cudaStream_t st) {
-  if (nb) k_scale_to_f32<<<nb, NT, 0, st>>>(r, f, r32, sc, partials);
+  if (nb) k_scale_to_f32<<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, f, r32, sc, partials);
 }
 void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st) {
   if (nb) k_power_init<<<nb, NT, 0, st>>>(diag, v);
 }
 void launch_power_step(int nb, const double *r, const double *dinv, double *w,
                        Scalars *sc, double *partials, cudaStream_t st) {
-  if (nb) k_power_step<<<nb, NT, 0, st>>>(r, dinv, w, sc, partials);
+  if (nb) k_power_step<<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, dinv, w, sc, partials);
+}
+void launch_normalize(int nb, const double *w, double *v, const Scalars *sc,
+                      cudaStream_t st) {
+  if (nb) k_normalize<<<nb, NT, 0, st>>>(w, v, sc);
 }
 void launch_scale(int nb, double *v, double f, cudaStream_t st) {
   if (nb) k_scale<<<nb, NT, 0, st>>>(v, f);
@@ -424,17 +554,24 @@ void launch_scaled_copy(int nb, const double *src, double f, double *dst,
 template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st) {
-  if (g.nb) k_apply_dot<T><<<g.nb, NT, 0, st>>>(g, gx, diag, p, q, sc, partials);
+  if (!g.nb) return;
+  k_apply_dot<T><<<g.nb, NT, 0, st>>>(g, gx, diag, p, q, partials);
+}
+void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
+                      cudaStream_t st) {
+  if (n <= 0) return;
+  const int blocks = std::min(152, (n + NT - 1) / NT);
+  k_finish_pq<<<blocks, NT, 0, st>>>(partials, n, scratch, sc);
 }
 template <typename T>
 void launch_update_xr(int nb, T *x, T *r, const T *p, const T *q, Scalars *sc,
                       double *partials, cudaStream_t st) {
-  if (nb) k_update_xr<T><<<nb, NT, 0, st>>>(x, r, p, q, sc, partials);
+  if (nb) k_update_xr<T><<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, x, r, p, q, sc, partials);
 }
 template <typename T>
 void launch_dot_rz(int nb, const T *r, const T *z, const int *comp,
                    Scalars *sc, double *partials, int first, cudaStream_t st) {
-  if (nb) k_dot_rz<T><<<nb, NT, 0, st>>>(r, z, comp, sc, partials, first);
+  if (nb) k_dot_rz<T><<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, z, comp, sc, partials, first);
 }
 template <typename T>
 void launch_comp_sum(int nb, const T *v, const int *comp, double *csum,
@@ -444,20 +581,19 @@ void launch_comp_sum(int nb, const T *v, const int *comp, double *csum,
 template <typename T>
 void launch_pupdate(int nb, T *p, const T *z, const int *comp,
                     const Scalars *sc, const double *csum, const int *csize,
-                    double inv_ndof, cudaStream_t st) {
-  if (nb) k_pupdate<T><<<nb, NT, 0, st>>>(p, z, comp, sc, csum, csize, inv_ndof);
+                    double, cudaStream_t st) {
+  if (nb) k_pupdate<T><<<nb, NT / V16<T>::N, 0, st>>>(p, z, comp, sc, csum, csize);
 }
 template <typename T>
 void launch_sub_mean(int nb, T *v, const int *comp, const Scalars *sc,
                      int aux_slot, const double *csum, const int *csize,
-                     double inv_ndof, cudaStream_t st) {
-  if (nb)
-    k_sub_mean<T><<<nb, NT, 0, st>>>(v, comp, sc, aux_slot, csum, csize, inv_ndof);
+                     double, cudaStream_t st) {
+  if (nb) k_sub_mean<T><<<nb, NT, 0, st>>>(v, comp, sc, aux_slot, csum, csize);
 }
 template <typename T>
 void launch_dot(int nb, const T *x, const T *y, const int *comp, Scalars *sc,
                 double *partials, int slot, cudaStream_t st) {
-  if (nb) k_dot<T><<<nb, NT, 0, st>>>(x, y, comp, sc, partials, slot);
+  if (nb) k_dot<T><<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, x, y, comp, sc, partials, slot);
 }
 void launch_rhs(const Grid &g, const double *gx, const double *a, double *b,
                 int *status, cudaStream_t st) {
@@ -483,8 +619,7 @@ void launch_efield(const unsigned char *mask, const double *a,
   size_t blocks = (n + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks == 0) blocks = 1;
-  k_efield<<<(int)blocks, 256, 0, st>>>(mask, a, psi, nx, ny, nz,
-                                        omega / (4.0 * h), E);
+  k_efield<<<(int)blocks, 256, 0, st>>>(mask, a, psi, nx, ny, nz, omega / (4.0 * h), E);
 }
 
 #define INST_K(T)                                                              \
@@ -507,6 +642,8 @@ void launch_efield(const unsigned char *mask, const double *a,
                               Scalars *, double *, int, cudaStream_t);         \
   template void launch_scatter<T>(const Grid &, const T *, const int *,        \
                                   double *, cudaStream_t);
+template int apply_dot_partials<double>(int);
+template int apply_dot_partials<float>(int);
 INST_K(double)
 INST_K(float)
 

@@ -524,4 +524,66 @@ void launch_coarse_diag(const Grid &gc, const double *stc, double thresh,
   k_coarse_diag<<<gc.nb, NT, 0, st>>>(stc, (size_t)gc.nb * BV, thresh, diag, dinv);
 }
 
+// Prolongation weights per fine cell.  A fine brick holds 64 cells of 2x2x2
+// nodes; node 2c + u of cell c (u in {0,1}^3, parity class q = uz*4+uy*2+ux)
+// has 2^(ux+uy+uz) parents c + o (o <= u componentwise).  Pc[pc_off(q) + j]
+// [cell] is the weight of its j-th parent in (oz, oy, ox) loop order, so the
+// threads of one parity class read consecutive entries.
+__global__ void __launch_bounds__(NT)
+k_pack_Pc(Grid gf, const double *__restrict__ W, double *__restrict__ Pc) {
+  const size_t S = (size_t)gf.nb * BV, NC = S / 8;
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const int q = t >> 6, cell = t & 63;
+  const int ux = q & 1, uy = (q >> 1) & 1, uz = q >> 2;
+  const int lx = 2 * (cell & 3) + ux, ly = 2 * ((cell >> 2) & 3) + uy, lz = 2 * (cell >> 4) + uz;
+  const size_t s = (size_t)bk * BV + (lz * 8 + ly) * 8 + lx;
+  const size_t cid = (size_t)bk * 64 + cell;
+  int j = pc_off(q);
+  for (int oz = 0; oz <= uz; ++oz)
+    for (int oy = 0; oy <= uy; ++oy)
+      for (int ox = 0; ox <= ux; ++ox)
+        Pc[(size_t)(j++) * NC + cid] = W[(size_t)(oz * 4 + oy * 2 + ox) * S + s];
+}
+
+void launch_pack_Pc(const Grid &gf, const double *W, double *Pc, cudaStream_t st) {
+  if (gf.nb) k_pack_Pc<<<gf.nb, NT, 0, st>>>(gf, W, Pc);
+}
+
+// ------------------------------------------------ coarsest dense inverse
+// One Gauss-Jordan sweep of an SPD matrix on pivot k, read from A into B
+// (m x m, row-major):  B[k][k] = 1/p,  B[k][j] = A[k][j]/p,
+// B[i][k] = -A[i][k]/p,  B[i][j] = A[i][j] - A[i][k] A[k][j] / p  with
+// p = A[k][k].  After sweeping every pivot once, B = A^-1.  Positive
+// definiteness keeps every pivot (a Schur complement) positive, so no
+// pivoting is needed; a non-positive pivot raises DEV_BAD_PIVOT.
+__global__ void k_gj_sweep(const double *__restrict__ A, double *__restrict__ B,
+                           int m, int k, int *status) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)m * m) return;
+  const int i = (int)(idx / m), j = (int)(idx % m);
+  const double p = A[(size_t)k * m + k];
+  if (idx == 0 && !(p > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
+  const double inv = 1.0 / p;
+  double v;
+  if (i == k && j == k) v = inv;
+  else if (i == k) v = A[(size_t)k * m + j] * inv;
+  else if (j == k) v = -A[(size_t)i * m + k] * inv;
+  else v = A[idx] - A[(size_t)i * m + k] * A[(size_t)k * m + j] * inv;
+  B[idx] = v;
+}
+
+// Inverts the SPD matrix in buf0 (m x m); returns the buffer holding A^-1.
+double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
+                             cudaStream_t st) {
+  const size_t n = (size_t)m * m;
+  const int threads = 256;
+  const int blocks = (int)((n + threads - 1) / threads);
+  double *a = buf0, *b = buf1;
+  for (int k = 0; k < m; ++k) {
+    k_gj_sweep<<<blocks, threads, 0, st>>>(a, b, m, k, status);
+    double *tmp = a; a = b; b = tmp;
+  }
+  return a;
+}
+
 }  // namespace spfd
