@@ -391,6 +391,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ncu_step(args):
+    """One step (build + solve + |E|) of the full-size workload, nothing else:
+    the target of the ncu launch lists and captures summarised in profiles/."""
+    import torch
+
+    import paper_2010_12879_gb300 as spfd
+
+    if args.ncu_small:
+        # the same body and source at 4 mm: 128 x 80 x 448 voxels, ~1.2M
+        # unknowns, stencil arrays still larger than L2
+        from spfd_inputs import body_phantom, loop_potential
+        ph = body_phantom(128, 80, 448, h=4e-3)
+        a = loop_potential(ph.dims, ph.h, ph.origin)
+    else:
+        ph, a = _inputs()
+    sig = torch.from_numpy(ph.sigma).cuda()
+    ad = torch.from_numpy(a).cuda()
+    prec = spfd.SPFD_FP64 if args.ncu_step == "fp64" else spfd.SPFD_MIXED
+    with spfd.Solver(sig, ph.h, precision=prec) as S:
+        psi, info, st = S.solve(ad, TOL)
+        E = S.efield(ad, psi, OMEGA)
+        torch.cuda.synchronize()
+        assert st == spfd.SPFD_OK and info["converged"], spfd.spfd_last_error()
+    print(json.dumps({"ncu_step": args.ncu_step, "iters": info["iters"],
+                      "outer_iters": info["outer_iters"],
+                      "rel_res_true": info["rel_res_true"],
+                      "launches": info["launches"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,8 +429,14 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=30)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-step", choices=["fp64", "mixed"], default=None,
+                    help="run one untimed step only (profiling target)")
+    ap.add_argument("--ncu-small", action="store_true",
+                    help="with --ncu-step: the 4 mm body (128x80x448) instead")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ncu_step:
+        run_ncu_step(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -64,6 +64,7 @@ void destroy_ctx(spfd_ctx *c) {
   cudaStreamSynchronize(c->stream);
   for (void *p : c->allocs) cudaFree(p);
   c->allocs.clear();
+  c->alloc_bytes.clear();
   for (auto &r : c->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->hsc) cudaFreeHost(c->hsc);

@@ -112,8 +112,8 @@ static spfd_status estimate_lmax(spfd_ctx *c, int l, double *lmax) {
   cudaStream_t st = c->stream;
   *lmax = 0.0;
   if (nb == 0) return SPFD_OK;
-  if (nb > c->L[0].g.nb || !c->partials)
-    return fail(SPFD_EINTERNAL, "reduction scratch too small for level %d", l);
+  if (!c->partials)
+    return fail(SPFD_EINTERNAL, "reduction scratch missing for level %d", l);
   double *v = lv.x, *w = lv.t, *r = lv.r, *zero = lv.b;
   CU(cudaMemsetAsync(zero, 0, lv.S * sizeof(double), st));
   SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0, launch_power_init(nb, lv.diag, v, st));
@@ -286,8 +286,9 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
                      cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemsetAsync(&c->sc->status, 0, sizeof(int), c->stream));
   double *inv = nullptr;
-  SPFD_LAUNCH(c, "setup_coarsest", false, m, 0, 2.0 * m * m * m,
-              inv = launch_dense_inverse(b0, b1, m, &c->sc->status, c->stream));
+  SPFD_LAUNCH(c, "setup_coarsest", false, m + 1, 0, 2.0 * m * m * m,
+              inv = launch_dense_inverse(b0, b1, m, &c->sc->aux[6], &c->sc->status,
+                                         c->stream));
   TRY(launch_check("coarsest inverse"));
   TRY(read_scalars(c));
   if (c->hsc->status & DEV_BAD_PIVOT)
@@ -300,16 +301,18 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
 // Number of positive entries (and the largest) of a device diagonal.
 static spfd_status count_positive(spfd_ctx *c, const Level &lv, const double *d_dev,
                                   int64_t *n, double *maxdiag) {
-  std::vector<double> d(lv.S);
-  if (lv.S)
-    CU(cudaMemcpyAsync(d.data(), d_dev, lv.S * sizeof(double),
-                       cudaMemcpyDeviceToHost, c->stream));
-  TRY(sync_check(c, "count"));
-  int64_t k = 0;
-  double mx = 0.0;
-  for (double v : d) { if (v > 0.0) ++k; mx = std::max(mx, v); }
-  *n = k;
-  if (maxdiag) *maxdiag = mx;
+  CU(cudaMemsetAsync(c->sc->ustat, 0, sizeof(c->sc->ustat), c->stream));
+  SPFD_LAUNCH(c, "setup_pack", false, 1, 8.0 * lv.S, 0,
+              launch_diag_stats(d_dev, lv.S, c->sc->ustat, c->stream));
+  TRY(launch_check("diagonal statistics"));
+  TRY(read_scalars(c));
+  *n = (int64_t)c->hsc->ustat[0];
+  if (maxdiag) {
+    const unsigned long long bits = c->hsc->ustat[1];
+    double mx = 0.0;
+    memcpy(&mx, &bits, sizeof mx);
+    *maxdiag = mx;
+  }
   return SPFD_OK;
 }
 
@@ -406,10 +409,11 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   TRY(make_level(c, c->L[0], NX, NY, NZ, hflags));
   const size_t S0 = c->L[0].S;
   const int nb0 = c->L[0].g.nb;
-  // reduction scratch: level 0 has the most bricks of all levels; the CG
-  // operator writes up to 16 partials per brick, followed by the finishing
-  // reduction's block sums; other grid reductions write 2 values per block
-  TRY(dalloc(c, &c->partials, 16 * (size_t)std::max(nb0, 1) + 1024));
+  // reduction scratch: the level-0 CG operator writes up to 16 partials per
+  // brick, followed by the finishing reduction's block sums (152); the
+  // grid-stride reductions of every level write 2 values per block, on at
+  // most 608 blocks
+  TRY(dalloc(c, &c->partials, 16 * (size_t)std::max(nb0, 1) + 2048));
   {
     Level &l0 = c->L[0];
     TRY(dalloc(c, &l0.gx, 3 * S0));
@@ -463,7 +467,11 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   }
 
   clk.mark("fine+components");
-  // multigrid hierarchy
+  // multigrid hierarchy (Ttmp: the product A P of one level, scratch grown to
+  // the largest fine level: a coarse level can hold more bricks than the
+  // level above it, up to 8 per odd-indexed fine brick)
+  double *Ttmp = nullptr;
+  size_t Tcap = 0;
   for (int l = 0;; ++l) {
     {
       Level &f = c->L[l];
@@ -507,21 +515,21 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     TRY(dalloc(c, &cl.diag, Sc));
     TRY(dalloc(c, &cl.dinv, Sc));
     TRY(dalloc(c, &cl.wdinv, Sc));
-    double *W = nullptr;
-    TRY(dalloc(c, &W, 8 * fl.S));
-    SPFD_LAUNCH(c, "setup_interp", false, 5, 0, 0,
-                launch_interp_weights(fl.g, fl.gx, fl.st, fl.diag, W, st));
-    TRY(launch_check("interpolation weights"));
-    SPFD_LAUNCH(c, "setup_galerkin", false, 1, 0, 0,
-                launch_galerkin(fl.g, cl.g, fl.gx, fl.st, fl.diag, W, cl.st, st));
-    TRY(launch_check("galerkin"));
-    SPFD_LAUNCH(c, "setup_galerkin", false, 1, 0, 0, launch_symmetrize(cl.g, cl.st, st));
-    SPFD_LAUNCH(c, "setup_pack", false, 1, 0, 0, launch_pack_P(fl.g, cl.g, W, cl.P, st));
     TRY(dalloc(c, &fl.Pc, 27 * (fl.S / 8)));
-    SPFD_LAUNCH(c, "setup_pack", false, 1, 0, 0, launch_pack_Pc(fl.g, W, fl.Pc, st));
-    TRY(launch_check("pack P"));
+    if (fl.S > Tcap) {
+      dfree(c, Ttmp);
+      Ttmp = nullptr;
+      TRY(dalloc(c, &Ttmp, (size_t)ap_rows_per_cell() * (fl.S / 8)));
+      Tcap = fl.S;
+    }
+    SPFD_LAUNCH(c, "setup_interp", false, 3, 0, 0,
+                launch_interp_weights(fl.g, fl.gx, fl.st, fl.diag, fl.Pc, st));
+    TRY(launch_check("interpolation weights"));
+    SPFD_LAUNCH(c, "setup_galerkin", false, 3, 0, 0,
+                launch_galerkin(fl.g, cl.g, fl.gx, fl.st, fl.diag, fl.Pc, Ttmp, cl.st,
+                                cl.P, st));
+    TRY(launch_check("galerkin"));
     TRY(sync_check(c, "coarse level"));
-    dfree(c, W);
     int64_t nact = 0;
     double maxdiag = 0.0;
     TRY(count_positive(c, cl, cl.st + 13 * Sc, &nact, &maxdiag));
@@ -533,13 +541,21 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   }
 
   // smoother weights (weighted Jacobi, omega = 4 / (3 * 1.05 * lambda_max(D^-1 A)))
+  dfree(c, Ttmp);
+  // Level 0: D^-1 A is the normalised Laplacian of the (bipartite) node
+  // graph, so lambda_max = 2 exactly (the checkerboard mode) and omega = 2/3.
+  // Coarser Galerkin operators are estimated by power iteration, with a 5 %
+  // margin.
   for (size_t l = 0; l + 1 < c->L.size(); ++l) {
-    double lm = 0.0;
-    TRY(estimate_lmax(c, (int)l, &lm));
-    if (!(lm > 0.0)) lm = 2.0;
+    double lm = 2.0, margin = 1.0;
+    if (l > 0) {
+      TRY(estimate_lmax(c, (int)l, &lm));
+      if (!(lm > 0.0)) lm = 2.0;
+      margin = 1.05;
+    }
     Level &lv = c->L[l];
     lv.lmax = lm;
-    lv.omega = 4.0 / (3.0 * 1.05 * lm);
+    lv.omega = 4.0 / (3.0 * margin * lm);
     SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
                 launch_scaled_copy(lv.g.nb, lv.dinv, lv.omega, lv.wdinv, st));
     CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), st));
@@ -557,9 +573,6 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   TRY(dalloc(c, &c->bk, S0));
   if (c->opts.precision == SPFD_MIXED) TRY(setup_mixed(c));
   clk.mark("vectors+mixed");
-  for (auto &lv : c->L)
-    if (lv.g.nb > nb0)
-      return fail(SPFD_EINTERNAL, "a coarse level has more bricks than level 0");
   CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
   const double inv_ndof = c->ndof ? 1.0 / (double)c->ndof : 0.0;
   CU(cudaMemcpyAsync(&c->sc->inv_ndof, &inv_ndof, sizeof(double), cudaMemcpyHostToDevice, st));

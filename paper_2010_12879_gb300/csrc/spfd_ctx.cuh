@@ -104,6 +104,7 @@ struct spfd_ctx {
   spfd_opts opts{};
   std::vector<spfd::Level> L;
   std::vector<void *> allocs;
+  std::vector<size_t> alloc_bytes;  // size of each entry of allocs
   int64_t bytes = 0;
   int alloc_count = 0;
   // fine-level bookkeeping
@@ -156,6 +157,7 @@ spfd_status dalloc(spfd_ctx *c, T **p, size_t count) {
                 "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
   }
   c->allocs.push_back(q);
+  c->alloc_bytes.push_back(bytes);
   c->bytes += (int64_t)bytes;
   *p = (T *)q;
   return SPFD_OK;
@@ -165,7 +167,12 @@ template <typename T>
 void dfree(spfd_ctx *c, T *&p) {
   if (!p) return;
   auto it = std::find(c->allocs.begin(), c->allocs.end(), (void *)p);
-  if (it != c->allocs.end()) c->allocs.erase(it);
+  if (it != c->allocs.end()) {
+    const size_t k = (size_t)(it - c->allocs.begin());
+    c->bytes -= (int64_t)c->alloc_bytes[k];
+    c->alloc_bytes.erase(c->alloc_bytes.begin() + k);
+    c->allocs.erase(it);
+  }
   cudaFree(p);
   p = nullptr;
 }

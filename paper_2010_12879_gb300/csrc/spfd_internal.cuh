@@ -84,6 +84,7 @@ struct Scalars {
   double zmean, rmean;  // zsum / n, rsum / n (formed once by the last block)
   float alpha_f, beta_f, zmean_f, rmean_f;  // FP32 copies for FP32 kernels
   double aux[8];    // misc results (power iteration, refinement)
+  unsigned long long ustat[2];  // count of positive entries, max entry (bits)
   unsigned int ticket[8];  // last-block counters, one per reduction site
   int status;       // SPFD_DEV_* bits
 };
@@ -111,19 +112,25 @@ void launch_assign_comp(const Grid &g, const int *parent, const int *offsets,
                         int *comp, cudaStream_t st);
 void launch_comp_sizes(const Grid &g, const int *comp, int *sizes,
                        cudaStream_t st);
+// Multigrid hierarchy (spfd_hierarchy.cu).  Pc: the fine level's compact
+// per-cell interpolation weights, [27][S/8] (row pc_off(q) + j, column
+// brick*64 + cell).  T: scratch for the product A P, [ap_rows_per_cell()][S/8].
+// stc / P: the coarse level's 27 Galerkin coefficients and 27 per-coarse-node
+// transfer weights ([d][I] = P(2I + d, I)), [27][Sc] each.
+int ap_rows_per_cell();
 void launch_interp_weights(const Grid &gf, const double *gx, const double *st27,
-                           const double *diag, double *W, cudaStream_t st);
+                           const double *diag, double *Pc, cudaStream_t st);
 void launch_galerkin(const Grid &gf, const Grid &gc, const double *gx,
-                     const double *st27f, const double *diagf, const double *W,
-                     double *stc, cudaStream_t st);
-void launch_symmetrize(const Grid &gc, double *stc, cudaStream_t st);
-void launch_pack_P(const Grid &gf, const Grid &gc, const double *W, double *P,
-                   cudaStream_t st);
-void launch_pack_Pc(const Grid &gf, const double *W, double *Pc, cudaStream_t st);
+                     const double *st27f, const double *diagf, const double *Pc,
+                     double *T, double *stc, double *P, cudaStream_t st);
+// ustat[0] += number of entries > 0 of d[0..n), ustat[1] = max(ustat[1], bits
+// of the largest entry) (non-negative doubles order like their bit patterns).
+void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
+                       cudaStream_t st);
 void launch_coarse_diag(const Grid &gc, const double *stc, double thresh,
                         double *diag, double *dinv, cudaStream_t st);
-double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
-                             cudaStream_t st);
+double *launch_dense_inverse(double *buf0, double *buf1, int m, double *pinv,
+                             int *status, cudaStream_t st);
 
 // V-cycle pieces (spfd_cycle.cu); T = vector type, C = 7-point coefficient type.
 template <typename T, typename C>

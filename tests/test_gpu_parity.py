@@ -2,8 +2,11 @@
 
 Tolerances (readings of Sec. II-A and the parity bar):
 * Psi: ||Psi_gpu - Psi_oracle||_2 / ||Psi_oracle||_2 <= 1e-9 after
-  per-component mean removal, the GPU solving to 1e-12 and the oracle to
-  1e-13 (relative residual);
+  per-component mean removal, the oracle solving to 1e-13 relative residual
+  and the GPU to the same 1e-13 on the small grids (1e-12 on the 8 mm body):
+  where |E| sits at the floor below, the bar is an absolute 1e-13 of the
+  field scale, which a 1e-12 solve meets only by chance of its iteration
+  path;
 * |E|: max over conducting voxels of |dE| / max(E_oracle, 1e-6 max E_oracle)
   <= 1e-7, where the 1e-6 floor is taken of the larger of max E_oracle and
   the source field scale omega/h max|a| (so that fields which vanish
@@ -85,8 +88,8 @@ def test_sphere_parity(torch_cuda, spfd, oracle_mod, gauge):
     ph = sphere_phantom()
     f = uniform_b_symmetric if gauge == "symmetric" else uniform_b_landau
     a = f(ph.dims, ph.h, ph.origin, 27e-6)
-    psi, E, info, st = _gpu_solve(torch_cuda, spfd, ph, a)
-    assert st == spfd.SPFD_OK and info["converged"] and info["rel_res_true"] <= 1e-12
+    psi, E, info, st = _gpu_solve(torch_cuda, spfd, ph, a, tol=1e-13)
+    assert st == spfd.SPFD_OK and info["converged"] and info["rel_res_true"] <= 1e-13
     assert info["n_dof"] == 13469 and info["n_comp"] == 1
     _compare(oracle_mod, ph, a, psi, E)
 
@@ -102,10 +105,32 @@ def test_random_phantom_parity(torch_cuda, spfd, oracle_mod, seed, dims, air):
     ph = random_phantom(*dims, rng, air_fraction=air)
     nx, ny, nz = dims
     a = rng.normal(size=(3, nz + 1, ny + 1, nx + 1)) * 1e-9
-    psi, E, info, st = _gpu_solve(torch_cuda, spfd, ph, a)
-    assert st == spfd.SPFD_OK and info["rel_res_true"] <= 1e-12
+    psi, E, info, st = _gpu_solve(torch_cuda, spfd, ph, a, tol=1e-13)
+    assert st == spfd.SPFD_OK and info["rel_res_true"] <= 1e-13
     sys = oracle_mod.assemble(ph.sigma, ph.h)
     assert info["n_dof"] == sys.n and info["n_comp"] == sys.ncomp
+    _compare(oracle_mod, ph, a, psi, E)
+
+
+def test_coarse_level_with_more_bricks_than_fine(torch_cuda, spfd, oracle_mod):
+    """64 separate 6^3-voxel blobs, one inside each odd-indexed 8^3-node
+    brick of a 64^3 grid: each such brick has two coarse parent bricks per
+    axis, so level 1 holds 125 bricks against level 0's 64 and is coarsened
+    once more (64 components, ~22k unknowns)."""
+    from types import SimpleNamespace
+    n = 64
+    rng = np.random.default_rng(5)
+    sigma = np.zeros((n, n, n))
+    for bz in (1, 3, 5, 7):
+        for by in (1, 3, 5, 7):
+            for bx in (1, 3, 5, 7):
+                sigma[8 * bz + 1:8 * bz + 7, 8 * by + 1:8 * by + 7, 8 * bx + 1:8 * bx + 7] = \
+                    rng.uniform(0.05, 1.0, size=(6, 6, 6))
+    ph = SimpleNamespace(sigma=sigma, h=2e-3)
+    a = rng.normal(size=(3, n + 1, n + 1, n + 1)) * 1e-9
+    psi, E, info, st = _gpu_solve(torch_cuda, spfd, ph, a, tol=1e-13)
+    assert st == spfd.SPFD_OK and info["rel_res_true"] <= 1e-13
+    assert info["n_comp"] == 64 and info["n_levels"] >= 3
     _compare(oracle_mod, ph, a, psi, E)
 
 
@@ -274,3 +299,25 @@ def test_body_full_size_properties(torch_cuda, spfd, oracle_mod, body_2mm):
     floor = 1e-6 * max(E_r[m].max(), OMEGA / ph.h * np.abs(a).max())
     assert (np.abs(E - E_r)[m] / np.maximum(E_r[m], floor)).max() <= 1e-12
     assert np.all(E[~m] == 0.0)
+
+
+def test_body_full_size_matches_oracle_samples(torch_cuda, spfd, body_2mm):
+    """Full-size parity against the oracle's own solve of the same workload:
+    tests/golden/body_2mm_oracle.json holds Psi (zero mean) of the oracle's
+    Jacobi-PCG at its 1.4e-12 rounding floor at 4096 seeded unknowns, written
+    by tests/golden/make_body_oracle_golden.py.  The GPU solve to 1e-12 must
+    match those samples to 1e-9 relative (L2 over the samples)."""
+    import json
+    import os
+    torch = torch_cuda
+    ph, a = body_2mm
+    with open(os.path.join(os.path.dirname(__file__), "golden", "body_2mm_oracle.json")) as f:
+        gold = json.load(f)
+    with spfd.Solver(_dev(torch, ph.sigma), ph.h) as S:
+        psi, info, st = S.solve(_dev(torch, a), 1e-12)
+    assert st == spfd.SPFD_OK and info["n_dof"] == gold["n_dof"]
+    nodes = np.array(gold["psi_sample_nodes"], dtype=np.int64)
+    want = np.array(gold["psi_sample_values"])
+    got = psi.reshape(-1)[torch.from_numpy(nodes).cuda()].cpu().numpy()
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 1e-9, f"sampled psi rel error {err:.3e}"
