@@ -6,56 +6,42 @@
 // geometric operator-dependent V-cycle that replaces it.  All are
 // bandwidth-bound stencil or transfer sweeps (the FP64 forms approach the
 // FP64 pipe's rate); none is a dense contraction, so no tensor-core path is
-// used.  One block handles one 8x8x8 brick (one thread per node) and stages
-// the vector it reads in shared memory (spfd_tile.cuh).
+// used.  One block handles one 8x8x8 brick: four nodes per thread without
+// shared memory on level 0, one node per thread with a shared tile on the
+// 27-point levels (spfd_tile.cuh).
 #include "spfd_internal.cuh"
 #include "spfd_tile.cuh"
 
 namespace spfd {
 
 // ------------------------------------------------------------ smoothers
-// The 7-point kernels issue every load that does not need the neighbour
-// bricks (own x, b, conductances, ...) before the first barrier, then the
-// face halo and the low-face conductances, then compute from the tile.
+// Level 0 (7-point): r = b - A x, and the weighted-Jacobi sweep
+// x_out = x + omega D^-1 (b - A x), on the row mapping.
 template <typename T, typename C>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(RT)
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r) {
-  __shared__ T tl[10][10][10];
-  __shared__ int sn[27];
-  const int bk = blockIdx.x, t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
-  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
-  load_nbr(g, bk, sn);
-  const T xc = x[s], bv = b[s];
-  Stencil7<T, C> A;
-  A.prefetch(gx, diag, S, s, lx, ly, lz);
-  tl[lz + 1][ly + 1][lx + 1] = xc;
-  __syncthreads();
-  tile_face_halo<T>(tl, x, sn);
-  A.resolve(gx, S, t, lx, ly, lz, sn);
-  __syncthreads();
-  r[s] = bv - A.apply(tl, lx, ly, lz);
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  const Q4<T> bv = ldq<T>(b + s0);
+  Q4<T> xc, rv;
+  apply7_row<T, C, true>(g, gx, diag, x, S, bk, t, bv, xc, rv);
+  stq(r + s0, rv);
 }
 
 template <typename T, typename C>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(RT)
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
           const T *__restrict__ b, T *__restrict__ xout) {
-  __shared__ T tl[10][10][10];
-  __shared__ int sn[27];
-  const int bk = blockIdx.x, t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
-  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
-  load_nbr(g, bk, sn);
-  const T xc = xin[s], bv = b[s], wv = wdinv[s];
-  Stencil7<T, C> A;
-  A.prefetch(gx, diag, S, s, lx, ly, lz);
-  tl[lz + 1][ly + 1][lx + 1] = xc;
-  __syncthreads();
-  tile_face_halo<T>(tl, xin, sn);
-  A.resolve(gx, S, t, lx, ly, lz, sn);
-  __syncthreads();
-  xout[s] = xc + wv * (bv - A.apply(tl, lx, ly, lz));
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  const Q4<T> bv = ldq<T>(b + s0), wv = ldq<T>(wdinv + s0);
+  Q4<T> xc, rv;
+  apply7_row<T, C, true>(g, gx, diag, xin, S, bk, t, bv, xc, rv);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) xc.v[i] += wv.v[i] * rv.v[i];
+  stq(xout + s0, xc);
 }
 
 template <typename T>
@@ -237,7 +223,7 @@ __global__ void k_coarse_solve(int m, const int *__restrict__ idx,
 template <typename T, typename C>
 void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
                       const T *b, T *r, cudaStream_t st) {
-  if (g.nb) k_residual7<T, C><<<g.nb, NT, 0, st>>>(g, gx, diag, x, b, r);
+  if (g.nb) k_residual7<T, C><<<g.nb, RT, 0, st>>>(g, gx, diag, x, b, r);
 }
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
@@ -259,7 +245,7 @@ void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
 template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
                     const T *xin, const T *b, T *xout, cudaStream_t st) {
-  if (g.nb) k_jacobi7<T, C><<<g.nb, NT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout);
+  if (g.nb) k_jacobi7<T, C><<<g.nb, RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout);
 }
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,

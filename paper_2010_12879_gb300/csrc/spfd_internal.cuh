@@ -168,8 +168,8 @@ void launch_coarse_solve(int m, const int *idx, const double *Binv,
 template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st);
-// Number of partial sums launch_apply_dot writes for nb bricks (16 per brick
-// for float, 1 for double); launch_finish_pq adds n of them (scratch: at
+// Number of partial sums launch_apply_dot writes for nb bricks (one per warp,
+// 4 per brick); launch_finish_pq adds n of them (scratch: at
 // least 152 doubles, not overlapping) and sets alpha = rz / pq.
 template <typename T> int apply_dot_partials(int nb);
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,

@@ -99,32 +99,29 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket,
 constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SMs
 
 // ------------------------------------------------------------ CG operator
-// q = A p on one brick per block, with p staged in a shared tile; each block
-// writes its part of p.q, and k_finish_pq adds them.
+// q = A p on one brick per block (row mapping, four nodes per thread); each
+// warp writes its part of p.q, and k_finish_pq adds them.
 template <typename T>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(RT)
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ p, T *__restrict__ q, double *partials) {
-  __shared__ T tl[10][10][10];
-  __shared__ int sn[27];
-  const int bk = blockIdx.x, t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
-  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
-  load_nbr(g, bk, sn);
-  const T pc = p[s];
-  Stencil7<T, T> A;
-  A.prefetch(gx, diag, S, s, lx, ly, lz);
-  tl[lz + 1][ly + 1][lx + 1] = pc;
-  __syncthreads();
-  tile_face_halo<T>(tl, p, sn);
-  A.resolve(gx, S, t, lx, ly, lz, sn);
-  __syncthreads();
-  const T qs = A.apply(tl, lx, ly, lz);
-  q[s] = qs;
-  const T pq = pc * qs;
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  Q4<T> pc, qv;
+  apply7_row<T, T, false>(g, gx, diag, p, S, bk, t, zq<T>(), pc, qv);
+  stq(q + s0, qv);
+  double part;
   if constexpr (sizeof(T) == 4) {
-    // warp sums in error-free FP32 (TwoSum pairs); one FP64 partial per warp,
-    // no block barrier
-    float hi = pq, lo = 0.f;
+    // FP32 products, summed without rounding error in (hi, lo) pairs
+    // (TwoSum) over the thread's four nodes and the warp; FP64 per warp
+    float hi = pc.v[0] * qv.v[0], lo = 0.f;
+#pragma unroll
+    for (int i = 1; i < 4; ++i) {
+      const float v = pc.v[i] * qv.v[i];
+      const float sh = hi + v, bb = sh - hi;
+      lo += (hi - (sh - bb)) + (v - bb);
+      hi = sh;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -134,27 +131,21 @@ k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
       hi = sh;
       lo = lo + ol + e;
     }
-    if ((t & 31) == 0) partials[(size_t)bk * (NT / 32) + (t >> 5)] = (double)hi + (double)lo;
+    part = (double)hi + (double)lo;
   } else {
-    // shared-memory tree: warp 0 adds 16 values per lane, then 5 shuffles,
-    // about one FP64 addition per node instead of five
-    __shared__ double red[NT];
-    red[t] = pq;
-    __syncthreads();
-    if (t < 32) {
-      double a = 0.0;
+    double a = pc.v[0] * qv.v[0];
 #pragma unroll
-      for (int k = 0; k < NT / 32; ++k) a += red[k * 32 + t];
+    for (int i = 1; i < 4; ++i) a += pc.v[i] * qv.v[i];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (t == 0) partials[bk] = a;
-    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    part = a;
   }
+  if ((t & 31) == 0) partials[(size_t)bk * (RT / 32) + (t >> 5)] = part;
 }
 
 // Number of partials k_apply_dot writes for nb bricks.
 template <typename T>
-int apply_dot_partials(int nb) { return sizeof(T) == 4 ? nb * (NT / 32) : nb; }
+int apply_dot_partials(int nb) { return nb * (RT / 32); }
 
 // pq = sum of the n partials of k_apply_dot (blocks add contiguous chunks,
 // the last block adds the block sums, fixed order); alpha = rz / pq.
@@ -555,7 +546,7 @@ template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st) {
   if (!g.nb) return;
-  k_apply_dot<T><<<g.nb, NT, 0, st>>>(g, gx, diag, p, q, partials);
+  k_apply_dot<T><<<g.nb, RT, 0, st>>>(g, gx, diag, p, q, partials);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
                       cudaStream_t st) {
