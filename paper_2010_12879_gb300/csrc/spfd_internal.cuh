@@ -129,8 +129,10 @@ void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
                        cudaStream_t st);
 void launch_coarse_diag(const Grid &gc, const double *stc, double thresh,
                         double *diag, double *dinv, cudaStream_t st);
-double *launch_dense_inverse(double *buf0, double *buf1, int m, double *pinv,
-                             int *status, cudaStream_t st);
+// Inverse of the SPD matrix in buf0 (m x m, row-major) by blocked
+// Gauss-Jordan sweeps; returns buf0 or buf1, whichever holds the result.
+double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
+                             cudaStream_t st);
 
 // V-cycle pieces (spfd_cycle.cu); T = vector type, C = 7-point coefficient type.
 template <typename T, typename C>

@@ -385,32 +385,77 @@ k_gather(Grid g, const double *__restrict__ psi, const int *__restrict__ comp,
 }
 
 // ------------------------------------------------------------ Eq. 1 |E|
-__global__ void k_efield(const unsigned char *__restrict__ mask,
-                         const double *__restrict__ a,
-                         const double *__restrict__ psi, int nx, int ny, int nz,
-                         double c, double *__restrict__ E) {
-  const size_t NV_ = (size_t)nx * ny * nz;
-  const size_t NX = nx + 1, NY = ny + 1;
-  const size_t NN = NX * NY * (size_t)(nz + 1);
-  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < NV_;
-       v += (size_t)gridDim.x * blockDim.x) {
-    if (!mask[v]) { E[v] = 0.0; continue; }
-    const size_t i = v % nx, j = (v / nx) % ny, k = v / ((size_t)nx * ny);
-    const size_t n000 = (k * NY + j) * NX + i;
-    double ex = 0.0, ey = 0.0, ez = 0.0;
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const size_t tx = n000 + (q * NY + r) * NX;  // x edge at (i, j+r, k+q)
-        ex += a[tx] + psi[tx + 1] - psi[tx];
-        const size_t ty = n000 + q * NY * NX + r;    // y edge at (i+r, j, k+q)
-        ey += a[NN + ty] + psi[ty + NX] - psi[ty];
-        const size_t tz = n000 + q * NX + r;         // z edge at (i+r, j+q, k)
-        ez += a[2 * NN + tz] + psi[tz + NX * NY] - psi[tz];
-      }
-    ex *= c; ey *= c; ez *= c;
-    E[v] = sqrt(ex * ex + ey * ey + ez * ez);
+// E_d of voxel (i, j, k) = c * sum over its four d-edges of
+// (a_e + Psi_head - Psi_tail), c = omega / (4h); |E| = |(E_x, E_y, E_z)|.
+// Each edge term is formed as (a_e + Psi_head) - Psi_tail and the four terms
+// of an axis are added in the order (s, t) = (0,0), (0,1), (1,0), (1,1) of
+// the edge offsets, with no contracted multiply-add, so the result is the
+// correctly rounded evaluation of that fixed expression.
+// Thread i of row (j, k) loads node column i (nodes (i, j..j+1, k..k+1)):
+// its four Psi values, its two y-edge terms (at k and k+1) and its two
+// z-edge terms (at j and j+1).  Voxel i also needs column i+1, which comes
+// from the next lane (the last lane loads it itself).
+struct EfCol {
+  double p00, p10, p01, p11;  // Psi(i, j+s, k+t) as p_st
+  double y0, y1, z0, z1;      // y-edge terms at k, k+1; z-edge terms at j, j+1
+};
+
+__device__ __forceinline__ EfCol ef_column(const double *__restrict__ a,
+                                           const double *__restrict__ psi, size_t n00,
+                                           size_t NX, size_t NXY, size_t NN) {
+  EfCol c;
+  c.p00 = psi[n00];
+  c.p10 = psi[n00 + NX];
+  c.p01 = psi[n00 + NXY];
+  c.p11 = psi[n00 + NXY + NX];
+  c.y0 = __dadd_rn(__dadd_rn(a[NN + n00], c.p10), -c.p00);
+  c.y1 = __dadd_rn(__dadd_rn(a[NN + n00 + NXY], c.p11), -c.p01);
+  c.z0 = __dadd_rn(__dadd_rn(a[2 * NN + n00], c.p01), -c.p00);
+  c.z1 = __dadd_rn(__dadd_rn(a[2 * NN + n00 + NX], c.p11), -c.p10);
+  return c;
+}
+
+__device__ __forceinline__ double shfl_next(double v) {
+  return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+__global__ void __launch_bounds__(128)
+k_efield(const unsigned char *__restrict__ mask, const double *__restrict__ a,
+         const double *__restrict__ psi, int nx, int ny, int nz, double c,
+         double *__restrict__ E) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  const size_t NX = (size_t)nx + 1, NXY = NX * ((size_t)ny + 1);
+  const size_t NN = NXY * ((size_t)nz + 1);
+  for (int k = blockIdx.z; k < nz; k += gridDim.z) {
+    const size_t n00 = (size_t)k * NXY + (size_t)j * NX + i;
+    EfCol h{0, 0, 0, 0, 0, 0, 0, 0};
+    if (i <= nx) h = ef_column(a, psi, n00, NX, NXY, NN);
+    EfCol n;
+    n.p00 = shfl_next(h.p00);
+    n.p10 = shfl_next(h.p10);
+    n.p01 = shfl_next(h.p01);
+    n.p11 = shfl_next(h.p11);
+    n.y0 = shfl_next(h.y0);
+    n.y1 = shfl_next(h.y1);
+    n.z0 = shfl_next(h.z0);
+    n.z1 = shfl_next(h.z1);
+    if (i >= nx) continue;
+    const size_t v = ((size_t)k * ny + j) * nx + i;
+    if (!mask[v]) {
+      E[v] = 0.0;
+      continue;
+    }
+    if (lane == 31) n = ef_column(a, psi, n00 + 1, NX, NXY, NN);
+    // x-edge terms at (i, j+s, k+t)
+    const double x00 = __dadd_rn(__dadd_rn(a[n00], n.p00), -h.p00);
+    const double x01 = __dadd_rn(__dadd_rn(a[n00 + NXY], n.p01), -h.p01);
+    const double x10 = __dadd_rn(__dadd_rn(a[n00 + NX], n.p10), -h.p10);
+    const double x11 = __dadd_rn(__dadd_rn(a[n00 + NXY + NX], n.p11), -h.p11);
+    const double ex = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(x00, x01), x10), x11), c);
+    const double ey = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(h.y0, h.y1), n.y0), n.y1), c);
+    const double ez = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(h.z0, h.z1), n.z0), n.z1), c);
+    E[v] = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
   }
 }
 
@@ -606,11 +651,9 @@ void launch_gather(const Grid &g, const double *psi, const int *comp, double *x,
 void launch_efield(const unsigned char *mask, const double *a,
                    const double *psi, int nx, int ny, int nz, double h,
                    double omega, double *E, cudaStream_t st) {
-  size_t n = (size_t)nx * ny * nz;
-  size_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  if (blocks == 0) blocks = 1;
-  k_efield<<<(int)blocks, 256, 0, st>>>(mask, a, psi, nx, ny, nz, omega / (4.0 * h), E);
+  if ((size_t)nx * ny * nz == 0) return;
+  const dim3 grid((nx + 127) / 128, ny, nz < 65535 ? nz : 65535);
+  k_efield<<<grid, 128, 0, st>>>(mask, a, psi, nx, ny, nz, omega / (4.0 * h), E);
 }
 
 #define INST_K(T)                                                              \

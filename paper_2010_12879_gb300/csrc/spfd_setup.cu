@@ -328,50 +328,101 @@ void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
 }
 
 // ------------------------------------------------ coarsest dense inverse
-// One Gauss-Jordan sweep of an SPD matrix on pivot k, read from A into B
-// (m x m, row-major):  B[k][k] = 1/p,  B[k][j] = A[k][j]/p,
-// B[i][k] = -A[i][k]/p,  B[i][j] = A[i][j] - A[i][k] A[k][j] / p  with
-// p = A[k][k].  After sweeping every pivot once, B = A^-1.  Positive
-// definiteness keeps every pivot (a Schur complement) positive, so no
-// pivoting is needed; a non-positive pivot raises DEV_BAD_PIVOT.
-// The reciprocal of the pivot comes from pinv[k & 1]: the thread that forms
-// the next pivot B[k+1][k+1] also writes its reciprocal to pinv[(k+1) & 1],
-// so the FP64 division happens once per sweep, not once per element.
-__global__ void k_gj_sweep(const double *__restrict__ A, double *__restrict__ B,
-                           int m, int k, double *pinv, int *status) {
-  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (idx >= (size_t)m * m) return;
-  const int i = (int)(idx / m), j = (int)(idx % m);
-  const double inv = pinv[k & 1];
-  double v;
-  if (i == k && j == k) v = inv;
-  else if (i == k) v = A[(size_t)k * m + j] * inv;
-  else if (j == k) v = -A[(size_t)i * m + k] * inv;
-  else v = A[idx] - A[(size_t)i * m + k] * A[(size_t)k * m + j] * inv;
-  B[idx] = v;
-  if (i == k + 1 && j == k + 1) {
-    if (!(v > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
-    pinv[(k + 1) & 1] = 1.0 / v;
+// Blocked Gauss-Jordan inversion of an SPD matrix (m x m, row-major).  One
+// launch sweeps the pivot set K = k0 .. k0+r-1 (r <= GJ_B) at once, reading
+// the current matrix M from A and writing B (a principal pivot transform):
+//   B[K,K] = D^-1,  B[K,j] = D^-1 M[K,j],  B[i,K] = -M[i,K] D^-1,
+//   B[i,j] = M[i,j] - M[i,K] D^-1 M[K,j]   (i, j not in K),  D = M[K,K].
+// After every pivot set has been swept once, B = A^-1.  Every block inverts
+// D itself (scalar Gauss-Jordan in shared memory): its pivots are Schur
+// complements of the SPD matrix, hence positive; a non-positive one raises
+// DEV_BAD_PIVOT.  A block then forms D^-1 M[K, its columns] once and updates
+// its GJ_T x GJ_T tile.
+constexpr int GJ_B = 16;   // pivots per launch
+constexpr int GJ_T = 32;   // tile edge
+constexpr int GJ_NT = 256; // threads per block (GJ_B * GJ_B)
+
+__global__ void __launch_bounds__(GJ_NT)
+k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, int r,
+           int *status) {
+  __shared__ double D[GJ_B][GJ_B + 1];
+  __shared__ double W[GJ_B][GJ_T];
+  __shared__ double U[GJ_T][GJ_B + 1];
+  __shared__ double C[GJ_B][GJ_T];
+  __shared__ double pinv;
+  const int t = threadIdx.x;
+  const int i0 = blockIdx.y * GJ_T, j0 = blockIdx.x * GJ_T;
+  {
+    const int a = t / GJ_B, b = t % GJ_B;
+    D[a][b] = (a < r && b < r) ? A[(size_t)(k0 + a) * m + k0 + b] : (a == b ? 1.0 : 0.0);
+  }
+  for (int q = t; q < GJ_T * GJ_B; q += GJ_NT) {
+    const int ii = q / GJ_B, l = q % GJ_B;
+    U[ii][l] = (l < r && i0 + ii < m) ? A[(size_t)(i0 + ii) * m + k0 + l] : 0.0;
+    const int l2 = q / GJ_T, jj = q % GJ_T;
+    C[l2][jj] = (l2 < r && j0 + jj < m) ? A[(size_t)(k0 + l2) * m + j0 + jj] : 0.0;
+  }
+  __syncthreads();
+  // D <- D^-1, one pivot at a time
+  for (int p = 0; p < GJ_B; ++p) {
+    if (t == 0) {
+      const double d = D[p][p];
+      if (!(d > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
+      pinv = d > 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    const int a = t / GJ_B, b = t % GJ_B;
+    const double iv = pinv;
+    double v;
+    if (a == p && b == p) v = iv;
+    else if (a == p) v = D[p][b] * iv;
+    else if (b == p) v = -D[a][p] * iv;
+    else v = D[a][b] - D[a][p] * D[p][b] * iv;
+    __syncthreads();
+    D[a][b] = v;
+    __syncthreads();
+  }
+  // W = D^-1 M[K, tile columns]
+  for (int q = t; q < GJ_B * GJ_T; q += GJ_NT) {
+    const int l = q / GJ_T, jj = q % GJ_T;
+    double w = 0.0;
+#pragma unroll
+    for (int l2 = 0; l2 < GJ_B; ++l2) w += D[l][l2] * C[l2][jj];
+    W[l][jj] = w;
+  }
+  __syncthreads();
+  for (int q = t; q < GJ_T * GJ_T; q += GJ_NT) {
+    const int ii = q / GJ_T, jj = q % GJ_T;
+    const int i = i0 + ii, j = j0 + jj;
+    if (i >= m || j >= m) continue;
+    const bool ki = i >= k0 && i < k0 + r, kj = j >= k0 && j < k0 + r;
+    double v;
+    if (ki && kj) {
+      v = D[i - k0][j - k0];
+    } else if (ki) {
+      v = W[i - k0][jj];
+    } else if (kj) {
+      v = 0.0;
+#pragma unroll
+      for (int l = 0; l < GJ_B; ++l) v -= U[ii][l] * D[l][j - k0];
+    } else {
+      v = A[(size_t)i * m + j];
+#pragma unroll
+      for (int l = 0; l < GJ_B; ++l) v -= U[ii][l] * W[l][jj];
+    }
+    B[(size_t)i * m + j] = v;
   }
 }
 
-__global__ void k_gj_first(const double *__restrict__ A, double *pinv, int *status) {
-  const double p = A[0];
-  if (!(p > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
-  pinv[0] = 1.0 / p;
-}
-
-// Inverts the SPD matrix in buf0 (m x m); returns the buffer holding A^-1.
-// pinv: 2 doubles of device scratch.
-double *launch_dense_inverse(double *buf0, double *buf1, int m, double *pinv,
-                             int *status, cudaStream_t st) {
-  const size_t n = (size_t)m * m;
-  const int threads = 256;
-  const int blocks = (int)((n + threads - 1) / threads);
+// Inverts the SPD matrix in buf0 (m x m); returns the buffer holding A^-1
+// (buf0 or buf1, which serve as ping-pong buffers).
+double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
+                             cudaStream_t st) {
   double *a = buf0, *b = buf1;
-  k_gj_first<<<1, 1, 0, st>>>(a, pinv, status);
-  for (int k = 0; k < m; ++k) {
-    k_gj_sweep<<<blocks, threads, 0, st>>>(a, b, m, k, pinv, status);
+  const int nt = (m + GJ_T - 1) / GJ_T;
+  for (int k0 = 0; k0 < m; k0 += GJ_B) {
+    k_gj_block<<<dim3(nt, nt), GJ_NT, 0, st>>>(a, b, m, k0, m - k0 < GJ_B ? m - k0 : GJ_B,
+                                              status);
     double *tmp = a; a = b; b = tmp;
   }
   return a;
