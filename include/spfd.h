@@ -192,8 +192,18 @@ spfd_status spfd_residual_noalloc(const double *sigma_dev, const double *a_dev,
                                   const double *psi_dev, int nx, int ny, int nz,
                                   double h, void *stream, double *rel_res);
 
-/* Release every resource of the context.  NULL is a no-op. */
+/* Release every resource of the context.  NULL is a no-op.  The context's
+ * device buffers are idle once its stream has been synchronised; they go to
+ * a process-wide cache (per device) from which later spfd_build calls take
+ * blocks of matching size instead of calling cudaMalloc again. */
 void spfd_destroy(spfd_ctx *ctx);
+
+/* Give every cached device block back to the driver (cudaFree); the bytes
+ * released go to *released if it is not NULL.  Safe at any time: contexts
+ * alive keep their own buffers.  A cudaMalloc that fails for lack of memory
+ * does the same once before it retries.  Not part of the paper's method:
+ * memory management of this library. */
+spfd_status spfd_release_cached_memory(size_t *released);
 
 /* Thread-local message for the most recent failing call on this thread. */
 const char *spfd_last_error(void);

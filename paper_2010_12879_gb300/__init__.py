@@ -29,7 +29,7 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 # Names declared in include/spfd.h (checked against the library by the tests).
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
-           "spfd_last_error", "spfd_residual_noalloc")
+           "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -103,6 +103,8 @@ def lib():
             L.spfd_residual_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, dp, vp, ctypes.POINTER(dp)]
             L.spfd_residual_noalloc.restype = ctypes.c_int
+            L.spfd_release_cached_memory.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
+            L.spfd_release_cached_memory.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -175,6 +177,14 @@ def spfd_kernel_stats(ctx: int, reset: bool = False) -> list:
 
 def spfd_destroy(ctx: int):
     lib().spfd_destroy(ctypes.c_void_p(ctx))
+
+
+def spfd_release_cached_memory() -> int:
+    """Give the library's cached idle device blocks back to the driver;
+    returns the bytes released."""
+    out = ctypes.c_size_t(0)
+    _check(lib().spfd_release_cached_memory(ctypes.byref(out)))
+    return out.value
 
 
 def spfd_residual_noalloc(sigma_ptr: int, a_ptr: int, psi_ptr: int, nx: int,

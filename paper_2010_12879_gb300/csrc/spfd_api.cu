@@ -61,10 +61,14 @@ spfd_status read_scalars(spfd_ctx *c) {
 
 void destroy_ctx(spfd_ctx *c) {
   if (!c) return;
+  // idle after the synchronisation: every block goes to the process cache
   cudaStreamSynchronize(c->stream);
-  for (void *p : c->allocs) cudaFree(p);
+  for (size_t k = 0; k < c->allocs.size(); ++k)
+    spfd::mem_put(c->device, c->allocs[k], c->alloc_bytes[k]);
+  for (auto &b : c->spare) spfd::mem_put(c->device, b.first, b.second);
   c->allocs.clear();
   c->alloc_bytes.clear();
+  c->spare.clear();
   for (auto &r : c->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->hsc) cudaFreeHost(c->hsc);
@@ -118,6 +122,12 @@ spfd_status prof_flush(spfd_ctx *c) {
 }  // namespace spfd
 
 extern "C" const char *spfd_last_error(void) { return g_err.c_str(); }
+
+extern "C" spfd_status spfd_release_cached_memory(size_t *released) {
+  const size_t n = spfd::mem_release_all();
+  if (released) *released = n;
+  return SPFD_OK;
+}
 
 extern "C" void spfd_destroy(spfd_ctx *ctx) { destroy_ctx(ctx); }
 

@@ -369,13 +369,15 @@ static spfd_status setup_mixed(spfd_ctx *c) {
 struct PhaseClock {
   spfd_ctx *c;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double alloc0 = 0.0;
   void mark(const char *what) {
     if (c->opts.verbose < 2) return;
     cudaStreamSynchronize(c->stream);
     auto t1 = std::chrono::steady_clock::now();
-    fprintf(stderr, "[spfd]   build phase %-18s %8.3f ms\n", what,
-            std::chrono::duration<double, std::milli>(t1 - t0).count());
+    fprintf(stderr, "[spfd]   build phase %-18s %8.3f ms (cudaMalloc %.3f ms)\n", what,
+            std::chrono::duration<double, std::milli>(t1 - t0).count(), c->alloc_ms - alloc0);
     t0 = t1;
+    alloc0 = c->alloc_ms;
   }
 };
 
@@ -563,6 +565,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     Level &lv = c->L[l];
     lv.lmax = lm;
     lv.omega = 4.0 / (3.0 * margin * lm);
+    if (c->opts.verbose >= 2) fprintf(stderr, "[spfd]   level %zu lambda_max %.4f omega %.4f\n", l, lm, lv.omega);
     SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
                 launch_scaled_copy(lv.g.nb, lv.dinv, lv.omega, lv.wdinv, st));
     CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), st));

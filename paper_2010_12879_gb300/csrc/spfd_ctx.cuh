@@ -4,12 +4,14 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <chrono>
 #include <cstdlib>
 #include <string>
 #include <vector>
 
 #include "spfd.h"
 #include "spfd_internal.cuh"
+#include "spfd_mem.cuh"
 
 namespace spfd {
 
@@ -104,9 +106,13 @@ struct spfd_ctx {
   spfd_opts opts{};
   std::vector<spfd::Level> L;
   std::vector<void *> allocs;
-  std::vector<size_t> alloc_bytes;  // size of each entry of allocs
+  std::vector<size_t> alloc_bytes;  // block size of each entry of allocs
+  // blocks released while the context lives: reused by its later requests
+  // (ordered on its own stream), returned to the process cache at destroy
+  std::vector<std::pair<void *, size_t>> spare;
   int64_t bytes = 0;
   int alloc_count = 0;
+  double alloc_ms = 0.0;  // host time spent in cudaMalloc (verbose reports)
   // fine-level bookkeeping
   unsigned char *mask = nullptr;  // [nz][ny][nx] conducting voxel flags
   int *comp = nullptr;            // [S0] component id or -1
@@ -150,19 +156,38 @@ spfd_status dalloc(spfd_ctx *c, T **p, size_t count) {
   if (inj && atoi(inj) == c->alloc_count)
     return fail(SPFD_ENOMEM, "injected allocation failure #%d", c->alloc_count);
   void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(e == cudaErrorMemoryAllocation ? SPFD_ENOMEM : SPFD_ECUDA,
-                "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  size_t block = 0;
+  // the context's own released blocks first (best fit, at most 25 % larger)
+  int best = -1;
+  for (size_t k = 0; k < c->spare.size(); ++k) {
+    const size_t b = c->spare[k].second;
+    if (b >= bytes && b <= bytes + bytes / 4 + 4096 &&
+        (best < 0 || b < c->spare[best].second))
+      best = (int)k;
+  }
+  if (best >= 0) {
+    q = c->spare[best].first;
+    block = c->spare[best].second;
+    c->spare.erase(c->spare.begin() + best);
+  } else {
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t e = spfd::mem_get(c->device, bytes, &q, &block);
+    c->alloc_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? SPFD_ENOMEM : SPFD_ECUDA,
+                  "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
   }
   c->allocs.push_back(q);
-  c->alloc_bytes.push_back(bytes);
-  c->bytes += (int64_t)bytes;
+  c->alloc_bytes.push_back(block);
+  c->bytes += (int64_t)block;
   *p = (T *)q;
   return SPFD_OK;
 }
 
+// Releases a buffer of the context to its spare list (no synchronisation:
+// only this context's stream-ordered work can reuse it before destroy).
 template <typename T>
 void dfree(spfd_ctx *c, T *&p) {
   if (!p) return;
@@ -170,10 +195,10 @@ void dfree(spfd_ctx *c, T *&p) {
   if (it != c->allocs.end()) {
     const size_t k = (size_t)(it - c->allocs.begin());
     c->bytes -= (int64_t)c->alloc_bytes[k];
+    c->spare.emplace_back(*it, c->alloc_bytes[k]);
     c->alloc_bytes.erase(c->alloc_bytes.begin() + k);
     c->allocs.erase(it);
   }
-  cudaFree(p);
   p = nullptr;
 }
 

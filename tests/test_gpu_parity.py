@@ -225,6 +225,7 @@ def test_injected_allocation_failure_leaks_nothing(torch_cuda, spfd, monkeypatch
     ph = sphere_phantom()
     sig = _dev(torch, ph.sigma)
     torch.cuda.synchronize()
+    spfd.spfd_release_cached_memory()
     free0, _ = torch.cuda.mem_get_info()
     for k in (1, 3, 7, 15, 40):
         monkeypatch.setenv("SPFD_FAIL_ALLOC_AT", str(k))
@@ -233,6 +234,8 @@ def test_injected_allocation_failure_leaks_nothing(torch_cuda, spfd, monkeypatch
         assert e.value.status == spfd.SPFD_ENOMEM
     monkeypatch.delenv("SPFD_FAIL_ALLOC_AT")
     torch.cuda.synchronize()
+    # blocks of the failed builds went to the library's cache: hand them back
+    assert spfd.spfd_release_cached_memory() > 0
     free1, _ = torch.cuda.mem_get_info()
     assert free0 - free1 < 8 << 20
     with spfd.Solver(sig, ph.h) as S:
@@ -250,6 +253,26 @@ def test_host_array_entry_point(torch_cuda, spfd, oracle_mod):
         psi_d, _, _ = S.solve(_dev(torch, a), 1e-12)
     assert st == spfd.SPFD_OK
     np.testing.assert_array_equal(psi_h.numpy(), psi_d.cpu().numpy())
+
+
+def test_cached_blocks_are_reused(torch_cuda, spfd):
+    """A second build of the same model takes its device buffers from the
+    library's cache: no net device memory is taken from the driver, and
+    releasing the cache gives all of it back."""
+    torch = torch_cuda
+    ph = sphere_phantom()
+    sig = _dev(torch, ph.sigma)
+    torch.cuda.synchronize()
+    spfd.spfd_release_cached_memory()
+    with spfd.Solver(sig, ph.h) as S:
+        held = S.info()["bytes_device"]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    with spfd.Solver(sig, ph.h) as S:
+        assert S.info()["bytes_device"] == held
+        free2, _ = torch.cuda.mem_get_info()
+    assert free1 - free2 < (4 << 20)  # driver-internal allocations only
+    assert spfd.spfd_release_cached_memory() >= held
 
 
 def test_repeat_solves_are_deterministic(torch_cuda, spfd):
