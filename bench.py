@@ -192,7 +192,7 @@ def run_ours(args):
     hbm_peak, peak_kind = _peaks()
     K, W = args.steps, args.warmup
     rec64, wall64, clk64 = timed(spfd.SPFD_FP64, K, W, True)
-    recmx, wallmx, clkmx = timed(spfd.SPFD_MIXED, K, max(1, W // 2), True)
+    recmx, wallmx, clkmx = timed(spfd.SPFD_MIXED, K, W, True)
 
     def agg(rec):
         keys = rec[0][0].keys()
@@ -423,7 +423,7 @@ def run_ncu_step(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-iters", type=int, default=30)

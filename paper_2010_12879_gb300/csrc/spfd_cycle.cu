@@ -18,7 +18,7 @@ namespace spfd {
 // Level 0 (7-point): r = b - A x, and the weighted-Jacobi sweep
 // x_out = x + omega D^-1 (b - A x), on the row mapping.
 template <typename T, typename C>
-__global__ void __launch_bounds__(RT)
+__global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r) {
   const int bk = blockIdx.x, t = threadIdx.x;
@@ -30,7 +30,7 @@ k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
 }
 
 template <typename T, typename C>
-__global__ void __launch_bounds__(RT)
+__global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
           const T *__restrict__ b, T *__restrict__ xout) {

@@ -214,11 +214,11 @@ void launch_axpy_mixed(int nb, double *x, const float *d, double f,
 void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
                          Scalars *sc, double *partials, cudaStream_t st);
 void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st);
-void launch_power_step(int nb, const double *r, const double *dinv, double *w,
-                       Scalars *sc, double *partials, cudaStream_t st);
+// w = D^-1 A v on a 27-point level; sc->aux[4] = v.(A v), sc->aux[5] = v.(D v).
+void launch_power27(const Grid &g, const double *st27, const double *diag,
+                    const double *dinv, const double *v, double *w, Scalars *sc,
+                    double *partials, cudaStream_t st);
 void launch_scale(int nb, double *v, double f, cudaStream_t st);
-void launch_normalize(int nb, const double *w, double *v, const Scalars *sc,
-                      cudaStream_t st);
 void launch_scaled_copy(int nb, const double *src, double f, double *dst,
                         cudaStream_t st);
 

@@ -102,7 +102,7 @@ constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SM
 // q = A p on one brick per block (row mapping, four nodes per thread); each
 // warp writes its part of p.q, and k_finish_pq adds them.
 template <typename T>
-__global__ void __launch_bounds__(RT)
+__global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ p, T *__restrict__ q, double *partials) {
   const int bk = blockIdx.x, t = threadIdx.x;
@@ -429,8 +429,12 @@ k_efield(const unsigned char *__restrict__ mask, const double *__restrict__ a,
   const size_t NN = NXY * ((size_t)nz + 1);
   for (int k = blockIdx.z; k < nz; k += gridDim.z) {
     const size_t n00 = (size_t)k * NXY + (size_t)j * NX + i;
+    const size_t v = ((size_t)k * ny + j) * nx + i;
+    // column i serves voxels i (own) and i-1 (through the shuffle)
+    const bool cond = i < nx && mask[v];
+    const bool need = cond || (i > 0 && i <= nx && mask[v - 1]);
     EfCol h{0, 0, 0, 0, 0, 0, 0, 0};
-    if (i <= nx) h = ef_column(a, psi, n00, NX, NXY, NN);
+    if (need) h = ef_column(a, psi, n00, NX, NXY, NN);
     EfCol n;
     n.p00 = shfl_next(h.p00);
     n.p10 = shfl_next(h.p10);
@@ -441,8 +445,7 @@ k_efield(const unsigned char *__restrict__ mask, const double *__restrict__ a,
     n.z0 = shfl_next(h.z0);
     n.z1 = shfl_next(h.z1);
     if (i >= nx) continue;
-    const size_t v = ((size_t)k * ny + j) * nx + i;
-    if (!mask[v]) {
+    if (!cond) {
       E[v] = 0.0;
       continue;
     }
@@ -469,28 +472,38 @@ k_power_init(const double *__restrict__ diag, double *__restrict__ v) {
   v[s] = diag[s] > 0.0 ? 0.5 + (double)(h & 0xffff) / 65536.0 : 0.0;
 }
 
-// w = D^{-1} A v given r = -A v; aux[4] = |w|^2.
+// One power-iteration step for the Jacobi weight of a 27-point level:
+// w = D^-1 A v, with the generalized Rayleigh quotient terms v.(A v) and
+// v.(D v) added into sc->aux[4] and sc->aux[5] (last-block reduction).
+// Bricks are grid-strided over at most RED_GRID blocks; v is staged in a
+// full-halo tile per brick.
 __global__ void __launch_bounds__(NT)
-k_power_step(int nb, const double *__restrict__ r, const double *__restrict__ dinv,
-             double *__restrict__ w, Scalars *sc, double *partials) {
-  double acc = 0.0;
-  for (int bk = blockIdx.x; bk < nb; bk += gridDim.x) {
-    const size_t s = (size_t)bk * BV + threadIdx.x;
-    const double ws = -dinv[s] * r[s];
-    w[s] = ws;
-    acc += ws * ws;
+k_power27(Grid g, const double *__restrict__ st, const double *__restrict__ diag,
+          const double *__restrict__ dinv, const double *__restrict__ v,
+          double *__restrict__ w, Scalars *sc, double *partials) {
+  __shared__ double tl[10][10][10];
+  __shared__ int sn[27];
+  const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  const size_t S = (size_t)g.nb * BV;
+  double vav = 0.0, vdv = 0.0;
+  for (int bk = blockIdx.x; bk < g.nb; bk += gridDim.x) {
+    __syncthreads();  // the previous brick's tile is no longer read
+    load_nbr(g, bk, sn);
+    __syncthreads();
+    tile_full<double>(tl, v, bk, sn);
+    __syncthreads();
+    const size_t s = (size_t)bk * BV + t;
+    const double av = apply27_tile<double>(tl, st, S, s);
+    const double vs = tl[lz + 1][ly + 1][lx + 1];
+    w[s] = dinv[s] * av;
+    vav += vs * av;
+    vdv += vs * vs * diag[s];
   }
-  double v[1] = {acc};
-  double tot[1];
-  if (grid_sum<1>(v, partials, &sc->ticket[4], tot)) sc->aux[4] = tot[0];
-}
-
-// v = w / |w| with |w|^2 from sc->aux[4] (power iteration without a host trip).
-__global__ void __launch_bounds__(NT)
-k_normalize(const double *__restrict__ w, double *__restrict__ v, const Scalars *sc) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  const double n2 = sc->aux[4];
-  v[s] = n2 > 0.0 ? w[s] * rsqrt(n2) : 0.0;
+  double vals[2] = {vav, vdv}, tot[2];
+  if (grid_sum<2>(vals, partials, &sc->ticket[4], tot)) {
+    sc->aux[4] = tot[0];
+    sc->aux[5] = tot[1];
+  }
 }
 
 __global__ void __launch_bounds__(NT) k_scale(double *__restrict__ v, double f) {
@@ -572,13 +585,11 @@ void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
 void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st) {
   if (nb) k_power_init<<<nb, NT, 0, st>>>(diag, v);
 }
-void launch_power_step(int nb, const double *r, const double *dinv, double *w,
-                       Scalars *sc, double *partials, cudaStream_t st) {
-  if (nb) k_power_step<<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, dinv, w, sc, partials);
-}
-void launch_normalize(int nb, const double *w, double *v, const Scalars *sc,
-                      cudaStream_t st) {
-  if (nb) k_normalize<<<nb, NT, 0, st>>>(w, v, sc);
+void launch_power27(const Grid &g, const double *st27, const double *diag,
+                    const double *dinv, const double *v, double *w, Scalars *sc,
+                    double *partials, cudaStream_t st) {
+  if (g.nb) k_power27<<<std::min(g.nb, RED_GRID), NT, 0, st>>>(g, st27, diag, dinv, v, w, sc,
+                                                                partials);
 }
 void launch_scale(int nb, double *v, double f, cudaStream_t st) {
   if (nb) k_scale<<<nb, NT, 0, st>>>(v, f);

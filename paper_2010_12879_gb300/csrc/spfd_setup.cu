@@ -147,48 +147,90 @@ __device__ void uf_unite(int *parent, int a, int b, int *capped) {
   *capped = 1;
 }
 
+// Brick-local pass: the block links the edges inside its brick with the
+// same lock-free union-find on a shared-memory forest, then writes each
+// unknown's local root (the smallest slot of its local component) as its
+// global parent.  A node is an unknown iff an incident edge conducts (its
+// own +edges or the -edges that are its neighbours' +edges).
+__device__ int uf_find_sh(int *p, int x, int *capped) {
+  volatile int *q = p;
+  for (int it = 0; it < UF_FIND_CAP; ++it) {
+    const int px = q[x];
+    if (px == x) return x;
+    const int gp = q[px];
+    if (gp != px) q[x] = gp;
+    x = gp;
+  }
+  *capped = 1;
+  return x;
+}
+
+__device__ void uf_unite_sh(int *p, int a, int b, int *capped) {
+  for (int it = 0; it < UF_UNITE_CAP; ++it) {
+    a = uf_find_sh(p, a, capped);
+    b = uf_find_sh(p, b, capped);
+    if (a == b || *capped) return;
+    if (a < b) { const int t = a; a = b; b = t; }
+    if (atomicCAS(&p[a], a, b) == a) return;
+  }
+  *capped = 1;
+}
+
 __global__ void __launch_bounds__(NT)
-k_uf_init(Grid g, const double *__restrict__ gx, int *parent) {
+k_uf_local(Grid g, const double *__restrict__ gx, int *parent, int *status) {
+  __shared__ int lp[BV];
   const size_t S = (size_t)g.nb * BV;
   const int b = blockIdx.x, t = threadIdx.x;
   const size_t s = (size_t)b * BV + t;
   const int4 bc = g.bco[b];
   const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
-  // active iff an incident edge conducts: own +edges or the neighbours' +edges
-  bool act = gx[s] > 0 || gx[S + s] > 0 || gx[2 * S + s] > 0;
+  const bool ex = gx[s] > 0, ey = gx[S + s] > 0, ez = gx[2 * S + s] > 0;
+  bool act = ex || ey || ez;
   if (!act) {
-    int m = slot_nb(g, b, bc, lx, ly, lz, -1, 0, 0);
+    const int m = slot_nb(g, b, bc, lx, ly, lz, -1, 0, 0);
     act = m >= 0 && gx[m] > 0;
   }
   if (!act) {
-    int m = slot_nb(g, b, bc, lx, ly, lz, 0, -1, 0);
+    const int m = slot_nb(g, b, bc, lx, ly, lz, 0, -1, 0);
     act = m >= 0 && gx[S + m] > 0;
   }
   if (!act) {
-    int m = slot_nb(g, b, bc, lx, ly, lz, 0, 0, -1);
+    const int m = slot_nb(g, b, bc, lx, ly, lz, 0, 0, -1);
     act = m >= 0 && gx[2 * S + m] > 0;
   }
-  parent[s] = act ? (int)s : -1;
+  lp[t] = act ? t : -1;
+  __syncthreads();
+  int capped = 0;
+  if (ex && lx < 7) uf_unite_sh(lp, t, t + 1, &capped);
+  if (ey && ly < 7) uf_unite_sh(lp, t, t + 8, &capped);
+  if (ez && lz < 7) uf_unite_sh(lp, t, t + 64, &capped);
+  __syncthreads();
+  int r = -1;
+  if (act) r = uf_find_sh(lp, t, &capped);
+  parent[s] = act ? b * BV + r : -1;
+  if (capped) atomicOr(status, DEV_UF_CAP);
 }
 
+// Links across the brick's +x/+y/+z faces (the edges the local pass left).
 __global__ void __launch_bounds__(NT)
 k_uf_union(Grid g, const double *__restrict__ gx, int *parent, int *status) {
   const size_t S = (size_t)g.nb * BV;
   const int b = blockIdx.x, t = threadIdx.x;
+  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  if (lx != 7 && ly != 7 && lz != 7) return;
   const int s = b * BV + t;
   const int4 bc = g.bco[b];
-  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
   int capped = 0;
-  if (gx[s] > 0) {
-    int m = slot_nb(g, b, bc, lx, ly, lz, 1, 0, 0);
+  if (lx == 7 && gx[s] > 0) {
+    const int m = slot_nb(g, b, bc, lx, ly, lz, 1, 0, 0);
     if (m >= 0) uf_unite(parent, s, m, &capped);
   }
-  if (gx[S + s] > 0) {
-    int m = slot_nb(g, b, bc, lx, ly, lz, 0, 1, 0);
+  if (ly == 7 && gx[S + s] > 0) {
+    const int m = slot_nb(g, b, bc, lx, ly, lz, 0, 1, 0);
     if (m >= 0) uf_unite(parent, s, m, &capped);
   }
-  if (gx[2 * S + s] > 0) {
-    int m = slot_nb(g, b, bc, lx, ly, lz, 0, 0, 1);
+  if (lz == 7 && gx[2 * S + s] > 0) {
+    const int m = slot_nb(g, b, bc, lx, ly, lz, 0, 0, 1);
     if (m >= 0) uf_unite(parent, s, m, &capped);
   }
   if (capped) atomicOr(status, DEV_UF_CAP);
@@ -205,7 +247,7 @@ k_uf_compress(Grid g, int *parent, int *status) {
 void launch_components(const Grid &g, const double *gx, int *parent,
                        int *status, cudaStream_t st) {
   if (g.nb == 0) return;
-  k_uf_init<<<g.nb, NT, 0, st>>>(g, gx, parent);
+  k_uf_local<<<g.nb, NT, 0, st>>>(g, gx, parent, status);
   k_uf_union<<<g.nb, NT, 0, st>>>(g, gx, parent, status);
   k_uf_compress<<<g.nb, NT, 0, st>>>(g, parent, status);
 }
@@ -257,10 +299,21 @@ void launch_assign_comp(const Grid &g, const int *parent, const int *offsets,
 
 __global__ void __launch_bounds__(NT)
 k_comp_sizes(const int *__restrict__ comp, int *sizes) {
+  __shared__ int c0;
   const int s = blockIdx.x * BV + threadIdx.x;
   const int c = comp[s];
-  // group lanes holding the same component; the lowest lane adds the count
-  unsigned grp = __match_any_sync(0xffffffffu, c);
+  // a brick inside one component (the common case) adds its count once
+  if (threadIdx.x == 0) c0 = -1;
+  __syncthreads();
+  if (c >= 0) atomicMax(&c0, c);
+  __syncthreads();
+  const int n = __syncthreads_count(c >= 0);
+  if (__syncthreads_and(c < 0 || c == c0)) {
+    if (threadIdx.x == 0 && n > 0) atomicAdd(&sizes[c0], n);
+    return;
+  }
+  // otherwise group the lanes holding the same component; the lowest lane adds
+  const unsigned grp = __match_any_sync(0xffffffffu, c);
   if (c >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1)
     atomicAdd(&sizes[c], __popc(grp));
 }

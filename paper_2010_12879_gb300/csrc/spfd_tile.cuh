@@ -79,6 +79,12 @@ __device__ __forceinline__ void tile_full(T (*tl)[10][10], const T *__restrict__
 // the brick), the +-x neighbours of the row ends from the other half-row by
 // shuffle or from the x-neighbour brick.  No shared memory, no barrier.
 constexpr int RT = 128;  // threads per brick in the row mapping
+// Resident blocks per SM asked of the compiler for row kernels: FP32 kernels
+// wait on memory and want many warps in flight (12 blocks = 48 warps caps
+// them at 40 registers); FP64 kernels are bound by the FP64 pipe and keep
+// their registers.
+template <typename T>
+constexpr int row_min_blocks() { return sizeof(T) == 4 ? 10 : 4; }
 
 template <typename T>
 struct Q4 {
