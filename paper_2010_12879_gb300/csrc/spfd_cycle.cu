@@ -150,56 +150,57 @@ k_restrict(Grid gc, const T *__restrict__ P, const T *__restrict__ rf,
 }
 
 // Prolongation + correction e_f(n) += sum over the <= 8 parents I of n of
-// P(n, I) e_c(I).  Threads are grouped by the parity class of their node
-// (two warps per class), so a warp shares one parent pattern, and the
-// per-cell weights Pc (k_pack_Pc) of a warp are consecutive: they are loaded
-// coalesced before the first barrier.  The brick's parents are the coarse
-// nodes 4F .. 4F+4, held by the coarse bricks (F >> 1) + {0,1}; their
-// values are staged in shared memory.
+// P(n, I) e_c(I).  One thread per 2x2x2 cell of a fine brick (two bricks per
+// 128-thread block): it loads the cell's 27 weights (row j of Pc at column
+// brick*64 + cell, coalesced across the warp), the 8 coarse corner values
+// c + o (o in {0,1}^3; coarse bricks from the brick's parent table) and its
+// 8 fine values as 2-vectors along x, then writes the 8 corrected values.
+// No shared memory and no barrier: every load is independent.
 template <typename T>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(128)
 k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
           T *__restrict__ ef) {
-  __shared__ T es[125];
-  __shared__ int sp[8];
-  const int bk = blockIdx.x, t = threadIdx.x;
-  if (t < 8) sp[t] = gf.par[(size_t)bk * 8 + t];
-  const int q = t >> 6, cell = t & 63;
-  const int ux = q & 1, uy = (q >> 1) & 1, uz = q >> 2;
+  const int bk = blockIdx.x * 2 + (threadIdx.x >> 6);
+  if (bk >= gf.nb) return;
+  const int cell = threadIdx.x & 63;
   const int ccx = cell & 3, ccy = (cell >> 2) & 3, ccz = cell >> 4;
-  const int lx = 2 * ccx + ux, ly = 2 * ccy + uy, lz = 2 * ccz + uz;
-  const size_t s = (size_t)bk * BV + (lz * 8 + ly) * 8 + lx;
   const size_t NC = (size_t)gf.nb * 64, cid = (size_t)bk * 64 + cell;
+  T w[27];
+#pragma unroll
+  for (int j = 0; j < 27; ++j) w[j] = Pc[(size_t)j * NC + cid];
   const int4 bc = gf.bco[bk];
-  const T efv = ef[s];
-  // weight of parent c + o (o <= u) sits at compact index
-  // j = (oz (uy+1) + oy) (ux+1) + ox, the (oz, oy, ox) order of k_pack_Pc
-  const int off = pc_off(q);
-  T w[8];
+  T e[8];
 #pragma unroll
-  for (int c8 = 0; c8 < 8; ++c8) {
-    const int ox = c8 & 1, oy = (c8 >> 1) & 1, oz = c8 >> 2;
-    const int j = (oz * (uy + 1) + oy) * (ux + 1) + ox;
-    w[c8] = (ox <= ux && oy <= uy && oz <= uz) ? Pc[(size_t)(off + j) * NC + cid] : T(0);
+  for (int o = 0; o < 8; ++o) {
+    const int gx_ = 4 * bc.x + ccx + (o & 1), gy_ = 4 * bc.y + ccy + ((o >> 1) & 1),
+              gz_ = 4 * bc.z + ccz + (o >> 2);
+    const int pb = (((gz_ >> 3) - (bc.z >> 1)) << 2) | (((gy_ >> 3) - (bc.y >> 1)) << 1) |
+                   ((gx_ >> 3) - (bc.x >> 1));
+    const int nb = __ldg(&gf.par[(size_t)bk * 8 + pb]);
+    e[o] = nb >= 0 ? ec[(size_t)nb * BV + ((gz_ & 7) * 8 + (gy_ & 7)) * 8 + (gx_ & 7)] : T(0);
   }
-  __syncthreads();
-  if (t < 125) {
-    const int cx = t % 5, cy = (t / 5) % 5, cz = t / 25;
-    const int gx_ = 4 * bc.x + cx, gy_ = 4 * bc.y + cy, gz_ = 4 * bc.z + cz;
-    const int o = (((gz_ >> 3) - (bc.z >> 1)) << 2) | (((gy_ >> 3) - (bc.y >> 1)) << 1) |
-                  ((gx_ >> 3) - (bc.x >> 1));
-    const int nb = sp[o];
-    es[t] = nb >= 0 ? ec[(size_t)nb * BV + ((gz_ & 7) * 8 + (gy_ & 7)) * 8 + (gx_ & 7)] : T(0);
-  }
-  __syncthreads();
-  T acc = 0;
 #pragma unroll
-  for (int c8 = 0; c8 < 8; ++c8) {
-    const int ox = c8 & 1, oy = (c8 >> 1) & 1, oz = c8 >> 2;
-    if (ox <= ux && oy <= uy && oz <= uz)
-      acc += w[c8] * es[((ccz + oz) * 5 + (ccy + oy)) * 5 + (ccx + ox)];
+  for (int r = 0; r < 4; ++r) {  // r = uz*2 + uy: one 2-vector (ux = 0, 1) per row
+    const int uy = r & 1, uz = r >> 1;
+    T *row = ef + (size_t)bk * BV + ((2 * ccz + uz) * 8 + 2 * ccy + uy) * 8 + 2 * ccx;
+    T v[2];
+    if constexpr (sizeof(T) == 4) {
+      const float2 u = *reinterpret_cast<const float2 *>(row);
+      v[0] = u.x; v[1] = u.y;
+    } else {
+      const double2 u = *reinterpret_cast<const double2 *>(row);
+      v[0] = u.x; v[1] = u.y;
+    }
+#pragma unroll
+    for (int ux = 0; ux < 2; ++ux) {
+      const int q = uz * 4 + uy * 2 + ux;
+#pragma unroll
+      for (int o = 0; o < 8; ++o)
+        if ((o & ~q) == 0) v[ux] += w[pc_off(q) + crank(q, o)] * e[o];
+    }
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(row) = make_float2(v[0], v[1]);
+    else *reinterpret_cast<double2 *>(row) = make_double2(v[0], v[1]);
   }
-  ef[s] = efv + acc;
 }
 
 // Coarsest level: x = B^{-1} b on the m listed unknowns (dense, FP64); one
@@ -260,7 +261,7 @@ void launch_restrict(const Grid &, const Grid &gc, const T *P, const T *rf,
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
                     T *ef, cudaStream_t st) {
-  if (gf.nb) k_prolong<T><<<gf.nb, NT, 0, st>>>(gf, gc, P, ec, ef);
+  if (gf.nb) k_prolong<T><<<(gf.nb + 1) / 2, 128, 0, st>>>(gf, gc, P, ec, ef);
 }
 template <typename T>
 void launch_coarse_solve(int m, const int *idx, const double *Binv, const T *b,

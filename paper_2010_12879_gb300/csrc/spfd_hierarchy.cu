@@ -28,12 +28,6 @@ namespace spfd {
 
 namespace {
 
-// Position of parent o among the parents o' <= u in ascending order.
-__host__ __device__ constexpr int crank(int u, int o) {
-  int r = 0;
-  for (int c = 0; c < o; ++c) r += (c & ~u) == 0;
-  return r;
-}
 __host__ __device__ constexpr int popc3(int q) {
   return (q & 1) + ((q >> 1) & 1) + ((q >> 2) & 1);
 }

@@ -33,6 +33,15 @@ __host__ __device__ __forceinline__ constexpr int pc_off(int q) {
        : q == 5 ? 11 : q == 6 ? 15 : 19;
 }
 
+// Position of parent o among the parents o' <= u (bit sets) in ascending
+// order: parent o of a class-u node is weight pc_off(u) + crank(u, o) of its
+// cell.
+__host__ __device__ __forceinline__ constexpr int crank(int u, int o) {
+  int r = 0;
+  for (int c = 0; c < o; ++c) r += (c & ~u) == 0;
+  return r;
+}
+
 struct Grid {
   int NX, NY, NZ;       // nodes per axis
   int MX, MY, MZ;       // bricks per axis

@@ -389,8 +389,9 @@ void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
 // After every pivot set has been swept once, B = A^-1.  Every block inverts
 // D itself (scalar Gauss-Jordan in shared memory): its pivots are Schur
 // complements of the SPD matrix, hence positive; a non-positive one raises
-// DEV_BAD_PIVOT.  A block then forms D^-1 M[K, its columns] once and updates
-// its GJ_T x GJ_T tile.
+// DEV_BAD_PIVOT.  One warp inverts D while the others stage the block's
+// rows and columns of M; the block then forms D^-1 M[K, its columns] once
+// and updates its GJ_T x GJ_T tile.
 constexpr int GJ_B = 16;   // pivots per launch
 constexpr int GJ_T = 32;   // tile edge
 constexpr int GJ_NT = 256; // threads per block (GJ_B * GJ_B)
@@ -402,39 +403,48 @@ k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, 
   __shared__ double W[GJ_B][GJ_T];
   __shared__ double U[GJ_T][GJ_B + 1];
   __shared__ double C[GJ_B][GJ_T];
-  __shared__ double pinv;
   const int t = threadIdx.x;
   const int i0 = blockIdx.y * GJ_T, j0 = blockIdx.x * GJ_T;
-  {
-    const int a = t / GJ_B, b = t % GJ_B;
-    D[a][b] = (a < r && b < r) ? A[(size_t)(k0 + a) * m + k0 + b] : (a == b ? 1.0 : 0.0);
-  }
-  for (int q = t; q < GJ_T * GJ_B; q += GJ_NT) {
-    const int ii = q / GJ_B, l = q % GJ_B;
-    U[ii][l] = (l < r && i0 + ii < m) ? A[(size_t)(i0 + ii) * m + k0 + l] : 0.0;
-    const int l2 = q / GJ_T, jj = q % GJ_T;
-    C[l2][jj] = (l2 < r && j0 + jj < m) ? A[(size_t)(k0 + l2) * m + j0 + jj] : 0.0;
+  if (t < 32) {
+    // warp 0: D <- D^-1, one pivot at a time (8 entries per lane,
+    // warp-synchronous)
+#pragma unroll
+    for (int q = 0; q < GJ_B * GJ_B / 32; ++q) {
+      const int e = q * 32 + t, a = e / GJ_B, b = e % GJ_B;
+      D[a][b] = (a < r && b < r) ? A[(size_t)(k0 + a) * m + k0 + b] : (a == b ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    for (int p = 0; p < GJ_B; ++p) {
+      const double d = D[p][p];
+      if (t == 0 && !(d > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
+      const double iv = d > 0.0 ? 1.0 / d : 0.0;
+      double v[GJ_B * GJ_B / 32];
+#pragma unroll
+      for (int q = 0; q < GJ_B * GJ_B / 32; ++q) {
+        const int e = q * 32 + t, a = e / GJ_B, b = e % GJ_B;
+        if (a == p && b == p) v[q] = iv;
+        else if (a == p) v[q] = D[p][b] * iv;
+        else if (b == p) v[q] = -D[a][p] * iv;
+        else v[q] = D[a][b] - D[a][p] * D[p][b] * iv;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < GJ_B * GJ_B / 32; ++q) {
+        const int e = q * 32 + t;
+        D[e / GJ_B][e % GJ_B] = v[q];
+      }
+      __syncwarp();
+    }
+  } else {
+    // warps 1..7: the block's rows M[tile rows, K] and columns M[K, tile cols]
+    for (int q = t - 32; q < GJ_T * GJ_B; q += GJ_NT - 32) {
+      const int ii = q / GJ_B, l = q % GJ_B;
+      U[ii][l] = (l < r && i0 + ii < m) ? A[(size_t)(i0 + ii) * m + k0 + l] : 0.0;
+      const int l2 = q / GJ_T, jj = q % GJ_T;
+      C[l2][jj] = (l2 < r && j0 + jj < m) ? A[(size_t)(k0 + l2) * m + j0 + jj] : 0.0;
+    }
   }
   __syncthreads();
-  // D <- D^-1, one pivot at a time
-  for (int p = 0; p < GJ_B; ++p) {
-    if (t == 0) {
-      const double d = D[p][p];
-      if (!(d > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
-      pinv = d > 0.0 ? 1.0 / d : 0.0;
-    }
-    __syncthreads();
-    const int a = t / GJ_B, b = t % GJ_B;
-    const double iv = pinv;
-    double v;
-    if (a == p && b == p) v = iv;
-    else if (a == p) v = D[p][b] * iv;
-    else if (b == p) v = -D[a][p] * iv;
-    else v = D[a][b] - D[a][p] * D[p][b] * iv;
-    __syncthreads();
-    D[a][b] = v;
-    __syncthreads();
-  }
   // W = D^-1 M[K, tile columns]
   for (int q = t; q < GJ_B * GJ_T; q += GJ_NT) {
     const int l = q / GJ_T, jj = q % GJ_T;
