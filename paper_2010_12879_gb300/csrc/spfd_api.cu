@@ -69,9 +69,10 @@ void destroy_ctx(spfd_ctx *c) {
   c->allocs.clear();
   c->alloc_bytes.clear();
   c->spare.clear();
+  for (auto &b : c->hblocks) spfd::host_put(b.first, b.second);
+  c->hblocks.clear();
   for (auto &r : c->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
-  if (c->hsc) cudaFreeHost(c->hsc);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;

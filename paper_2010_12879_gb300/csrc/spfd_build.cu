@@ -15,19 +15,21 @@
 
 namespace spfd {
 
-// Geometry of a level from its brick activity flags.
-static spfd_status make_level(spfd_ctx *c, Level &lv, int NX, int NY, int NZ,
+// Geometry of a level from its brick activity flags (host only): brick map,
+// brick coordinates and the 27-neighbour brick table.
+static spfd_status host_level(Level &lv, int NX, int NY, int NZ,
                               const std::vector<unsigned char> &flags) {
   Grid &g = lv.g;
+  g = Grid{};
   g.NX = NX; g.NY = NY; g.NZ = NZ;
   g.MX = (NX + 7) / 8; g.MY = (NY + 7) / 8; g.MZ = (NZ + 7) / 8;
-  size_t nbm = (size_t)g.MX * g.MY * g.MZ;
+  const size_t nbm = (size_t)g.MX * g.MY * g.MZ;
   lv.hbmap.assign(nbm, -1);
   lv.hbco.clear();
   for (int bz = 0; bz < g.MZ; ++bz)
     for (int by = 0; by < g.MY; ++by)
       for (int bx = 0; bx < g.MX; ++bx) {
-        size_t q = ((size_t)bz * g.MY + by) * g.MX + bx;
+        const size_t q = ((size_t)bz * g.MY + by) * g.MX + bx;
         if (flags[q]) {
           lv.hbmap[q] = (int)lv.hbco.size();
           lv.hbco.push_back(make_int4(bx, by, bz, 0));
@@ -37,85 +39,106 @@ static spfd_status make_level(spfd_ctx *c, Level &lv, int NX, int NY, int NZ,
     return fail(SPFD_EINVAL, "grid too large: %zu active bricks", lv.hbco.size());
   g.nb = (int)lv.hbco.size();
   lv.S = (size_t)g.nb * BV;
-  int *bmap = nullptr;
-  int4 *bco = nullptr;
-  TRY(dalloc(c, &bmap, nbm));
-  TRY(dalloc(c, &bco, lv.hbco.size()));
-  CU(cudaMemcpyAsync(bmap, lv.hbmap.data(), nbm * sizeof(int),
-                     cudaMemcpyHostToDevice, c->stream));
-  if (g.nb)
-    CU(cudaMemcpyAsync(bco, lv.hbco.data(), lv.hbco.size() * sizeof(int4),
-                       cudaMemcpyHostToDevice, c->stream));
-  // 27-neighbour brick table
-  std::vector<int> hn((size_t)std::max(g.nb, 1) * 27, -1);
+  lv.hnbr.assign((size_t)std::max(g.nb, 1) * 27, -1);
   for (int b = 0; b < g.nb; ++b) {
     const int4 bc = lv.hbco[b];
     for (int e = 0; e < 27; ++e) {
       const int x = bc.x + e % 3 - 1, y = bc.y + (e / 3) % 3 - 1, z = bc.z + e / 9 - 1;
       if (x < 0 || y < 0 || z < 0 || x >= g.MX || y >= g.MY || z >= g.MZ) continue;
-      hn[(size_t)b * 27 + e] = lv.hbmap[((size_t)z * g.MY + y) * g.MX + x];
+      lv.hnbr[(size_t)b * 27 + e] = lv.hbmap[((size_t)z * g.MY + y) * g.MX + x];
     }
   }
-  int *nbr = nullptr;
-  TRY(dalloc(c, &nbr, hn.size()));
-  CU(cudaMemcpyAsync(nbr, hn.data(), hn.size() * sizeof(int), cudaMemcpyHostToDevice,
-                     c->stream));
-  CU(cudaStreamSynchronize(c->stream));  // the host vectors may be reused
-  g.bmap = bmap;
-  g.bco = bco;
-  g.nbr = nbr;
-  g.kid = nullptr;
-  g.par = nullptr;
   return SPFD_OK;
 }
 
-// Transfer tables between a fine level f and its coarse level cl: for each
-// coarse brick the 27 fine bricks its 17^3 fine support touches, and for
-// each fine brick the 8 coarse bricks that hold its parents.
-static spfd_status make_transfer_tables(spfd_ctx *c, Level &f, Level &cl) {
+// Brick activity of the level below fine level f: coarse node I sits on fine
+// node 2I, and coarse brick B covers fine bricks 2B-1 .. 2B+1 on each axis.
+static void coarse_flags(const Level &f, int *CX, int *CY, int *CZ,
+                         std::vector<unsigned char> *cfl) {
+  const Grid &fg = f.g;
+  *CX = fg.NX / 2 + 1; *CY = fg.NY / 2 + 1; *CZ = fg.NZ / 2 + 1;
+  const int cMX = (*CX + 7) / 8, cMY = (*CY + 7) / 8, cMZ = (*CZ + 7) / 8;
+  cfl->assign((size_t)cMX * cMY * cMZ, 0);
+  for (int bz = 0; bz < cMZ; ++bz)
+    for (int by = 0; by < cMY; ++by)
+      for (int bx = 0; bx < cMX; ++bx) {
+        bool any = false;
+        for (int fz = std::max(0, 2 * bz - 1); fz <= std::min(fg.MZ - 1, 2 * bz + 1) && !any; ++fz)
+          for (int fy = std::max(0, 2 * by - 1); fy <= std::min(fg.MY - 1, 2 * by + 1) && !any; ++fy)
+            for (int fx = std::max(0, 2 * bx - 1); fx <= std::min(fg.MX - 1, 2 * bx + 1) && !any; ++fx)
+              any = f.hbmap[((size_t)fz * fg.MY + fy) * fg.MX + fx] >= 0;
+        (*cfl)[((size_t)bz * cMY + by) * cMX + bx] = any;
+      }
+}
+
+// Transfer tables between fine level f and its coarse level cl (host only):
+// for each coarse brick the 27 fine bricks its 17^3 fine support touches,
+// and for each fine brick the 8 coarse bricks that hold its parents.
+static void host_transfer(Level &f, Level &cl) {
   const Grid &fg = f.g, &cg = cl.g;
-  std::vector<int> kid((size_t)std::max(cg.nb, 1) * 27, -1);
+  cl.hkid.assign((size_t)std::max(cg.nb, 1) * 27, -1);
   for (int b = 0; b < cg.nb; ++b) {
     const int4 bc = cl.hbco[b];
     for (int o = 0; o < 27; ++o) {
       const int x = 2 * bc.x + o % 3 - 1, y = 2 * bc.y + (o / 3) % 3 - 1, z = 2 * bc.z + o / 9 - 1;
       if (x < 0 || y < 0 || z < 0 || x >= fg.MX || y >= fg.MY || z >= fg.MZ) continue;
-      kid[(size_t)b * 27 + o] = f.hbmap[((size_t)z * fg.MY + y) * fg.MX + x];
+      cl.hkid[(size_t)b * 27 + o] = f.hbmap[((size_t)z * fg.MY + y) * fg.MX + x];
     }
   }
-  std::vector<int> par((size_t)std::max(fg.nb, 1) * 8, -1);
+  f.hpar.assign((size_t)std::max(fg.nb, 1) * 8, -1);
   for (int b = 0; b < fg.nb; ++b) {
     const int4 bc = f.hbco[b];
     for (int o = 0; o < 8; ++o) {
       const int x = (bc.x >> 1) + (o & 1), y = (bc.y >> 1) + ((o >> 1) & 1), z = (bc.z >> 1) + (o >> 2);
       if (x >= cg.MX || y >= cg.MY || z >= cg.MZ) continue;
-      par[(size_t)b * 8 + o] = cl.hbmap[((size_t)z * cg.MY + y) * cg.MX + x];
+      f.hpar[(size_t)b * 8 + o] = cl.hbmap[((size_t)z * cg.MY + y) * cg.MX + x];
     }
   }
-  int *dkid = nullptr, *dpar = nullptr;
-  TRY(dalloc(c, &dkid, kid.size()));
-  TRY(dalloc(c, &dpar, par.size()));
-  CU(cudaMemcpyAsync(dkid, kid.data(), kid.size() * sizeof(int), cudaMemcpyHostToDevice,
-                     c->stream));
-  CU(cudaMemcpyAsync(dpar, par.data(), par.size() * sizeof(int), cudaMemcpyHostToDevice,
-                     c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  cl.g.kid = dkid;
-  f.g.par = dpar;
-  return SPFD_OK;
 }
 
-// Largest eigenvalue of D^-1 A of a 27-point level (for the Jacobi weight):
-// power iteration v <- D^-1 A v from a fixed positive start vector, with the
-// generalized Rayleigh quotient v.(A v) / v.(D v) of the last iterate as the
-// estimate.  The quotient of the symmetric pencil (A, D) converges twice as
-// fast as the ratio of norms, so 8 steps match 16 of the latter.  The
-// iterates are not normalised: they grow by at most 4^8.
-static spfd_status estimate_lmax(spfd_ctx *c, int l, double *lmax) {
+// One asynchronous upload of host tables: each (host vector, device slot)
+// pair is packed into a pinned block, copied into one device block, and the
+// slot pointed at its part.  The pinned block stays with the context.
+struct TableUpload {
+  struct Item {
+    const void *src;
+    size_t bytes;
+    const void **dst;
+  };
+  std::vector<Item> items;
+  template <typename T>
+  void add(const std::vector<T> &v, const T **dst) {
+    items.push_back({v.data(), v.size() * sizeof(T), (const void **)dst});
+  }
+  spfd_status run(spfd_ctx *c) {
+    size_t total = 0;
+    for (auto &it : items) total += (it.bytes + 255) / 256 * 256;
+    if (total == 0) return SPFD_OK;
+    unsigned char *h = nullptr, *d = nullptr;
+    TRY(halloc(c, &h, total));
+    TRY(dalloc(c, &d, total));
+    size_t off = 0;
+    for (auto &it : items) {
+      memcpy(h + off, it.src, it.bytes);
+      *it.dst = d + off;
+      off += (it.bytes + 255) / 256 * 256;
+    }
+    CU(cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, c->stream));
+    return SPFD_OK;
+  }
+};
+
+// Jacobi weights of a 27-point level, omega = 4 / (3 * 1.05 * lambda_max),
+// with lambda_max of D^-1 A from a power iteration v <- D^-1 A v from a fixed
+// positive start vector: the generalized Rayleigh quotient v.(A v) / v.(D v)
+// of the last iterate.  The quotient of the symmetric pencil (A, D) converges
+// twice as fast as the ratio of norms, so 8 steps match 16 of the latter.
+// The iterates are not normalised (they grow by at most 4^8), and nothing is
+// read back: the weights are formed on the device, lambda goes to *lam_dev.
+static spfd_status smoother_weights(spfd_ctx *c, int l, double *lam_dev) {
   Level &lv = c->L[l];
   const int nb = lv.g.nb;
   cudaStream_t st = c->stream;
-  *lmax = 0.0;
   if (nb == 0) return SPFD_OK;
   if (!c->partials || !lv.st)
     return fail(SPFD_EINTERNAL, "power iteration needs a 27-point level (%d)", l);
@@ -127,11 +150,9 @@ static spfd_status estimate_lmax(spfd_ctx *c, int l, double *lmax) {
                 launch_power27(lv.g, lv.st, lv.diag, lv.dinv, v, w, c->sc, c->partials, st));
     std::swap(v, w);
   }
-  TRY(launch_check("power iteration"));
-  TRY(read_scalars(c));
-  const double q = c->hsc->aux[4] / c->hsc->aux[5];
-  *lmax = std::isfinite(q) ? q : 0.0;
-  return SPFD_OK;
+  SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
+              launch_jacobi_weights(nb, lv.dinv, c->sc, 1.05, lv.wdinv, lam_dev, st));
+  return launch_check("power iteration");
 }
 
 // Inverse of a dense SPD n x n matrix (row-major), in place: Cholesky
@@ -286,34 +307,13 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
   TRY(dalloc(c, &b1, (size_t)m * m));
   CU(cudaMemcpyAsync(b0, A.data(), (size_t)m * m * sizeof(double),
                      cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemsetAsync(&c->sc->status, 0, sizeof(int), c->stream));
   double *inv = nullptr;
   SPFD_LAUNCH(c, "setup_coarsest", false, (m + 15) / 16, 0, 2.0 * m * m * m,
               inv = launch_dense_inverse(b0, b1, m, &c->sc->status, c->stream));
   TRY(launch_check("coarsest inverse"));
-  TRY(read_scalars(c));
-  if (c->hsc->status & DEV_BAD_PIVOT)
-    return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
+  // a non-positive pivot raises DEV_BAD_PIVOT, read at the end of the build
   c->Binv = inv;
   if (inv == b0) dfree(c, b1); else dfree(c, b0);
-  return SPFD_OK;
-}
-
-// Number of positive entries (and the largest) of a device diagonal.
-static spfd_status count_positive(spfd_ctx *c, const Level &lv, const double *d_dev,
-                                  int64_t *n, double *maxdiag) {
-  CU(cudaMemsetAsync(c->sc->ustat, 0, sizeof(c->sc->ustat), c->stream));
-  SPFD_LAUNCH(c, "setup_pack", false, 1, 8.0 * lv.S, 0,
-              launch_diag_stats(d_dev, lv.S, c->sc->ustat, c->stream));
-  TRY(launch_check("diagonal statistics"));
-  TRY(read_scalars(c));
-  *n = (int64_t)c->hsc->ustat[0];
-  if (maxdiag) {
-    const unsigned long long bits = c->hsc->ustat[1];
-    double mx = 0.0;
-    memcpy(&mx, &bits, sizeof mx);
-    *maxdiag = mx;
-  }
   return SPFD_OK;
 }
 
@@ -380,7 +380,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   PhaseClock clk{c};
   TRY(dalloc(c, &c->sc, 1));
   CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
-  CU(cudaMallocHost(&c->hsc, sizeof(Scalars)));
+  TRY(halloc(c, &c->hsc, 1));
   memset(c->hsc, 0, sizeof(Scalars));
   CU(cudaEventCreate(&c->ev0));
   CU(cudaEventCreate(&c->ev1));
@@ -391,16 +391,16 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   const int MX = (NX + 7) / 8, MY = (NY + 7) / 8, MZ = (NZ + 7) / 8;
   const size_t nbm = (size_t)MX * MY * MZ;
   const size_t nvox = (size_t)c->nx * c->ny * c->nz;
-  unsigned char *flags = nullptr;
+  unsigned char *flags = nullptr, *hflags_p = nullptr;
   TRY(dalloc(c, &flags, nbm));
   TRY(dalloc(c, &c->mask, nvox));
+  TRY(halloc(c, &hflags_p, nbm));
   CU(cudaMemsetAsync(flags, 0, nbm, st));
   SPFD_LAUNCH(c, "setup_flags", false, 1, 9.0 * nvox, 0,
               launch_sigma_flags(sigma, c->nx, c->ny, c->nz, MX, MY, flags, c->mask,
                                  &c->sc->status, st));
   TRY(launch_check("sigma flags"));
-  std::vector<unsigned char> hflags(nbm);
-  CU(cudaMemcpyAsync(hflags.data(), flags, nbm, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(hflags_p, flags, nbm, cudaMemcpyDeviceToHost, st));
   TRY(read_scalars(c));
   dfree(c, flags);
   if (c->hsc->status & DEV_BAD_SIGMA)
@@ -409,7 +409,16 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   clk.mark("flags");
   c->L.clear();
   c->L.emplace_back();
-  TRY(make_level(c, c->L[0], NX, NY, NZ, hflags));
+  {
+    const std::vector<unsigned char> hflags(hflags_p, hflags_p + nbm);
+    TRY(host_level(c->L[0], NX, NY, NZ, hflags));
+    TableUpload up;
+    Level &l0 = c->L[0];
+    up.add(l0.hbmap, &l0.g.bmap);
+    up.add(l0.hbco, &l0.g.bco);
+    up.add(l0.hnbr, &l0.g.nbr);
+    TRY(up.run(c));
+  }
   const size_t S0 = c->L[0].S;
   const int nb0 = c->L[0].g.nb;
   // reduction scratch: the level-0 CG operator writes 4 partials per brick
@@ -417,6 +426,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   // grid-stride reductions of every level write 2 values per block, on at
   // most 608 blocks
   TRY(dalloc(c, &c->partials, 16 * (size_t)std::max(nb0, 1) + 2048));
+  int *parent = nullptr, *counts = nullptr, *offsets = nullptr;
   {
     Level &l0 = c->L[0];
     TRY(dalloc(c, &l0.gx, 3 * S0));
@@ -427,9 +437,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
                 launch_build_fine(l0.g, sigma, c->nx, c->ny, c->nz, c->h, l0.gx,
                                   l0.diag, l0.dinv, st));
     TRY(launch_check("build fine"));
-
     // connected components of the conducting nodes
-    int *parent = nullptr, *counts = nullptr, *offsets = nullptr;
     TRY(dalloc(c, &parent, S0));
     TRY(dalloc(c, &c->comp, S0));
     SPFD_LAUNCH(c, "setup_components", false, 3, 0, 0,
@@ -438,130 +446,165 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     TRY(dalloc(c, &counts, nb0));
     TRY(dalloc(c, &offsets, nb0));
     SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0, launch_root_counts(l0.g, parent, counts, st));
-    std::vector<int> hcnt(nb0), hoff(nb0);
+  }
+
+  // The brick structure of every coarser level follows from the brick maps
+  // alone, so it is built on the host while the device labels components.
+  // Levels are added until one could hold no more than coarse_max unknowns
+  // (its slot count bounds them) or the grid is exhausted; the levels past
+  // the first one whose actual unknowns fit coarse_max are dropped below.
+  for (int l = 0;; ++l) {
+    const Level &f = c->L[l];
+    if ((int64_t)f.S <= c->opts.coarse_max || l + 1 >= c->opts.max_levels ||
+        (f.g.NX <= 3 && f.g.NY <= 3 && f.g.NZ <= 3))
+      break;
+    int CX, CY, CZ;
+    std::vector<unsigned char> cfl;
+    coarse_flags(f, &CX, &CY, &CZ, &cfl);
+    c->L.emplace_back();  // (invalidates references into c->L)
+    TRY(host_level(c->L[l + 1], CX, CY, CZ, cfl));
+    host_transfer(c->L[l], c->L[l + 1]);
+  }
+  const int LB = (int)c->L.size();
+  {
+    TableUpload up;
+    for (int l = 0; l < LB; ++l) {
+      Level &lv = c->L[l];
+      if (l > 0) {
+        up.add(lv.hbmap, &lv.g.bmap);
+        up.add(lv.hbco, &lv.g.bco);
+        up.add(lv.hnbr, &lv.g.nbr);
+        up.add(lv.hkid, &lv.g.kid);
+      }
+      if (l + 1 < LB) up.add(lv.hpar, &lv.g.par);
+    }
+    TRY(up.run(c));
+  }
+
+  // component numbering (one read-back: the root count per brick)
+  {
+    Level &l0 = c->L[0];
+    int *hcnt = nullptr;
+    TRY(halloc(c, &hcnt, nb0));
     if (nb0)
-      CU(cudaMemcpyAsync(hcnt.data(), counts, nb0 * sizeof(int),
-                         cudaMemcpyDeviceToHost, st));
+      CU(cudaMemcpyAsync(hcnt, counts, nb0 * sizeof(int), cudaMemcpyDeviceToHost, st));
     TRY(read_scalars(c));
     if (c->hsc->status & DEV_UF_CAP)
       return fail(SPFD_EINTERNAL, "component labelling hit its iteration cap");
+    int *hoff = nullptr;
+    TRY(halloc(c, &hoff, nb0));
     int64_t tot = 0;
     for (int b = 0; b < nb0; ++b) { hoff[b] = (int)tot; tot += hcnt[b]; }
     c->ncomp = (int)tot;
     if (nb0)
-      CU(cudaMemcpyAsync(offsets, hoff.data(), nb0 * sizeof(int),
-                         cudaMemcpyHostToDevice, st));
+      CU(cudaMemcpyAsync(offsets, hoff, nb0 * sizeof(int), cudaMemcpyHostToDevice, st));
     SPFD_LAUNCH(c, "setup_components", false, 2, 0, 0, launch_assign_comp(l0.g, parent, offsets, c->comp, st));
     TRY(dalloc(c, &c->csize, std::max(c->ncomp, 1)));
     CU(cudaMemsetAsync(c->csize, 0, std::max(c->ncomp, 1) * sizeof(int), st));
     SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0, launch_comp_sizes(l0.g, c->comp, c->csize, st));
     TRY(launch_check("component sizes"));
-    std::vector<int> hsize(std::max(c->ncomp, 1));
-    CU(cudaMemcpyAsync(hsize.data(), c->csize, hsize.size() * sizeof(int),
-                       cudaMemcpyDeviceToHost, st));
-    TRY(sync_check(c, "components"));
     dfree(c, parent);
     dfree(c, counts);
     dfree(c, offsets);
-    c->ndof = 0;
-    for (int q = 0; q < c->ncomp; ++q) c->ndof += hsize[q];
-    l0.n_active = c->ndof;
     if (c->ncomp > 1) TRY(dalloc(c, &c->csum, c->ncomp));
   }
-
   clk.mark("fine+components");
-  // multigrid hierarchy (Ttmp: the product A P of one level, scratch grown to
-  // the largest fine level: a coarse level can hold more bricks than the
-  // level above it, up to 8 per odd-indexed fine brick)
+
+  // Multigrid hierarchy, enqueued without host round trips.  lstat[4l..4l+3]:
+  // level l's count and largest entry of the Galerkin diagonal, then the
+  // same after the activity threshold (count = unknowns of the level).
+  // Ttmp: the product A P of one level, scratch grown to the largest fine
+  // level (a coarse level can hold more bricks than the level above it, up
+  // to 8 per odd-indexed fine brick).
+  unsigned long long *lstat = nullptr;
+  double *lam = nullptr;
+  TRY(dalloc(c, &lstat, 4 * (size_t)LB));
+  TRY(dalloc(c, &lam, LB));
+  CU(cudaMemsetAsync(lstat, 0, 4 * LB * sizeof(unsigned long long), st));
+  CU(cudaMemsetAsync(lam, 0, LB * sizeof(double), st));
   double *Ttmp = nullptr;
   size_t Tcap = 0;
-  for (int l = 0;; ++l) {
-    {
-      Level &f = c->L[l];
-      TRY(dalloc(c, &f.x, f.S));
-      TRY(dalloc(c, &f.b, f.S));
-      TRY(dalloc(c, &f.r, f.S));
-      TRY(dalloc(c, &f.t, f.S));
-      CU(cudaMemsetAsync(f.x, 0, f.S * sizeof(double), st));
-      CU(cudaMemsetAsync(f.t, 0, f.S * sizeof(double), st));
-      const bool last = f.n_active <= c->opts.coarse_max || l + 1 >= c->opts.max_levels ||
-                        (f.g.NX <= 3 && f.g.NY <= 3 && f.g.NZ <= 3);
-      if (last) break;
-    }
-    // coarse node I <-> fine node 2I; coarse brick B covers fine bricks
-    // 2B-1 .. 2B+1 on each axis
-    const Grid fg = c->L[l].g;
-    const int CX = fg.NX / 2 + 1, CY = fg.NY / 2 + 1, CZ = fg.NZ / 2 + 1;
-    const int cMX = (CX + 7) / 8, cMY = (CY + 7) / 8, cMZ = (CZ + 7) / 8;
-    std::vector<unsigned char> cfl((size_t)cMX * cMY * cMZ, 0);
-    {
-      const Level &f = c->L[l];
-      for (int bz = 0; bz < cMZ; ++bz)
-        for (int by = 0; by < cMY; ++by)
-          for (int bx = 0; bx < cMX; ++bx) {
-            bool any = false;
-            for (int fz = std::max(0, 2 * bz - 1); fz <= std::min(fg.MZ - 1, 2 * bz + 1) && !any; ++fz)
-              for (int fy = std::max(0, 2 * by - 1); fy <= std::min(fg.MY - 1, 2 * by + 1) && !any; ++fy)
-                for (int fx = std::max(0, 2 * bx - 1); fx <= std::min(fg.MX - 1, 2 * bx + 1) && !any; ++fx)
-                  any = f.hbmap[((size_t)fz * fg.MY + fy) * fg.MX + fx] >= 0;
-            cfl[((size_t)bz * cMY + by) * cMX + bx] = any;
-          }
-    }
-    c->L.emplace_back();  // (invalidates references into c->L)
-    Level &fl = c->L[l];
+  for (int l = 0; l < LB; ++l) {
+    Level &f = c->L[l];
+    TRY(dalloc(c, &f.x, f.S));
+    TRY(dalloc(c, &f.b, f.S));
+    TRY(dalloc(c, &f.r, f.S));
+    TRY(dalloc(c, &f.t, f.S));
+    CU(cudaMemsetAsync(f.x, 0, f.S * sizeof(double), st));
+    CU(cudaMemsetAsync(f.t, 0, f.S * sizeof(double), st));
+    if (l + 1 == LB) break;
     Level &cl = c->L[l + 1];
-    TRY(make_level(c, cl, CX, CY, CZ, cfl));
-    TRY(make_transfer_tables(c, fl, cl));
     const size_t Sc = cl.S;
     TRY(dalloc(c, &cl.st, 27 * Sc));
     TRY(dalloc(c, &cl.P, 27 * Sc));
     TRY(dalloc(c, &cl.diag, Sc));
     TRY(dalloc(c, &cl.dinv, Sc));
     TRY(dalloc(c, &cl.wdinv, Sc));
-    TRY(dalloc(c, &fl.Pc, 27 * (fl.S / 8)));
-    if (fl.S > Tcap) {
+    TRY(dalloc(c, &f.Pc, 27 * (f.S / 8)));
+    if (f.S > Tcap) {
       dfree(c, Ttmp);
-      Ttmp = nullptr;
-      TRY(dalloc(c, &Ttmp, (size_t)ap_rows_per_cell() * (fl.S / 8)));
-      Tcap = fl.S;
+      TRY(dalloc(c, &Ttmp, (size_t)ap_rows_per_cell() * (f.S / 8)));
+      Tcap = f.S;
     }
     SPFD_LAUNCH(c, "setup_interp", false, 3, 0, 0,
-                launch_interp_weights(fl.g, fl.gx, fl.st, fl.diag, fl.Pc, st));
-    TRY(launch_check("interpolation weights"));
+                launch_interp_weights(f.g, f.gx, f.st, f.diag, f.Pc, st));
     SPFD_LAUNCH(c, "setup_galerkin", false, 3, 0, 0,
-                launch_galerkin(fl.g, cl.g, fl.gx, fl.st, fl.diag, fl.Pc, Ttmp, cl.st,
-                                cl.P, st));
-    TRY(launch_check("galerkin"));
-    TRY(sync_check(c, "coarse level"));
-    int64_t nact = 0;
-    double maxdiag = 0.0;
-    TRY(count_positive(c, cl, cl.st + 13 * Sc, &nact, &maxdiag));
+                launch_galerkin(f.g, cl.g, f.gx, f.st, f.diag, f.Pc, Ttmp, cl.st, cl.P, st));
+    // Rows below 1e-13 of the level's largest diagonal are not unknowns:
+    // they come only from basis functions constant on a tiny component.
+    unsigned long long *ls = lstat + 4 * (l + 1);
+    SPFD_LAUNCH(c, "setup_pack", false, 1, 8.0 * Sc, 0,
+                launch_diag_stats(cl.st + 13 * Sc, Sc, ls, st));
     SPFD_LAUNCH(c, "setup_pack", false, 1, 0, 0,
-                launch_coarse_diag(cl.g, cl.st, 1e-13 * maxdiag, cl.diag, cl.dinv, st));
-    TRY(launch_check("coarse diag"));
-    TRY(count_positive(c, cl, cl.diag, &cl.n_active, nullptr));
-    clk.mark("coarse level");
+                launch_coarse_diag(cl.g, cl.st, ls + 1, 1e-13, cl.diag, cl.dinv, st));
+    SPFD_LAUNCH(c, "setup_pack", false, 1, 8.0 * Sc, 0,
+                launch_diag_stats(cl.diag, Sc, ls + 2, st));
+    TRY(launch_check("coarse level"));
   }
-
-  // smoother weights (weighted Jacobi, omega = 4 / (3 * 1.05 * lambda_max(D^-1 A)))
   dfree(c, Ttmp);
-  // Level 0: D^-1 A is the normalised Laplacian of the (bipartite) node
-  // graph, so lambda_max = 2 exactly (the checkerboard mode) and omega = 2/3.
-  // Coarser Galerkin operators are estimated by power iteration, with a 5 %
-  // margin.
+  {
+    // the one read-back of the hierarchy: component sizes and the unknowns
+    // of every level
+    unsigned long long *hl = nullptr;
+    int *hsize = nullptr;
+    TRY(halloc(c, &hl, 4 * (size_t)LB));
+    TRY(halloc(c, &hsize, std::max(c->ncomp, 1)));
+    CU(cudaMemcpyAsync(hl, lstat, 4 * LB * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(hsize, c->csize, std::max(c->ncomp, 1) * sizeof(int),
+                       cudaMemcpyDeviceToHost, st));
+    TRY(sync_check(c, "hierarchy"));
+    c->ndof = 0;
+    for (int q = 0; q < c->ncomp; ++q) c->ndof += hsize[q];
+    c->L[0].n_active = c->ndof;
+    for (int l = 1; l < LB; ++l) c->L[l].n_active = (int64_t)hl[4 * l + 2];
+  }
+  // the coarsest level: the first whose unknowns fit coarse_max
+  int LU = LB;
+  for (int l = 0; l < LB; ++l)
+    if (c->L[l].n_active <= c->opts.coarse_max) { LU = l + 1; break; }
+  while ((int)c->L.size() > LU) {
+    Level &lv = c->L.back();
+    for (double **p : {&lv.st, &lv.P, &lv.diag, &lv.dinv, &lv.wdinv, &lv.x, &lv.b, &lv.r,
+                       &lv.t, &lv.Pc})
+      dfree(c, *p);
+    c->L.pop_back();
+  }
+  dfree(c, c->L.back().Pc);
+  clk.mark("coarse levels");
+
+  // smoother weights (weighted Jacobi): level 0 has D^-1 A the random-walk
+  // Laplacian of a bipartite node graph, so lambda_max = 2 exactly and
+  // omega = 2/3; coarser levels estimate it on the device
   for (size_t l = 0; l + 1 < c->L.size(); ++l) {
-    double lm = 2.0, margin = 1.0;
-    if (l > 0) {
-      TRY(estimate_lmax(c, (int)l, &lm));
-      if (!(lm > 0.0)) lm = 2.0;
-      margin = 1.05;
-    }
     Level &lv = c->L[l];
-    lv.lmax = lm;
-    lv.omega = 4.0 / (3.0 * margin * lm);
-    if (c->opts.verbose >= 2) fprintf(stderr, "[spfd]   level %zu lambda_max %.4f omega %.4f\n", l, lm, lv.omega);
-    SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
-                launch_scaled_copy(lv.g.nb, lv.dinv, lv.omega, lv.wdinv, st));
+    if (l == 0) {
+      lv.lmax = 2.0;
+      lv.omega = 2.0 / 3.0;
+      SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
+                  launch_scaled_copy(lv.g.nb, lv.dinv, lv.omega, lv.wdinv, st));
+    } else {
+      TRY(smoother_weights(c, (int)l, lam + l));
+    }
     CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), st));
     CU(cudaMemsetAsync(lv.t, 0, lv.S * sizeof(double), st));
   }
@@ -577,11 +620,25 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   TRY(dalloc(c, &c->bk, S0));
   if (c->opts.precision == SPFD_MIXED) TRY(setup_mixed(c));
   clk.mark("vectors+mixed");
+  // read back the device status and the smoother estimates, then clear the
+  // scalars for the solves
+  double *hlam = nullptr;
+  TRY(halloc(c, &hlam, LB));
+  CU(cudaMemcpyAsync(hlam, lam, LB * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
   CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
   const double inv_ndof = c->ndof ? 1.0 / (double)c->ndof : 0.0;
   CU(cudaMemcpyAsync(&c->sc->inv_ndof, &inv_ndof, sizeof(double), cudaMemcpyHostToDevice, st));
   CU(cudaEventRecord(c->ev1, st));
   TRY(sync_check(c, "build"));
+  if (c->hsc->status & DEV_BAD_PIVOT)
+    return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
+  for (size_t l = 1; l + 1 < c->L.size(); ++l) {
+    c->L[l].lmax = hlam[l];
+    c->L[l].omega = 4.0 / (3.0 * 1.05 * hlam[l]);
+  }
+  dfree(c, lstat);
+  dfree(c, lam);
   TRY(prof_flush(c));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);

@@ -37,6 +37,7 @@ struct Level {
   Grid g{};                       // device view
   std::vector<int> hbmap;         // host brick map
   std::vector<int4> hbco;         // host brick coordinates
+  std::vector<int> hnbr, hkid, hpar;  // host copies of the brick tables
   size_t S = 0;                   // slots = nb * 512
   int64_t n_active = 0;
   double omega = 0.0, lmax = 0.0;
@@ -110,6 +111,9 @@ struct spfd_ctx {
   // blocks released while the context lives: reused by its later requests
   // (ordered on its own stream), returned to the process cache at destroy
   std::vector<std::pair<void *, size_t>> spare;
+  // pinned host blocks (staging, scalar mirror): returned to the process
+  // cache at destroy, once no queued copy reads them
+  std::vector<std::pair<void *, size_t>> hblocks;
   int64_t bytes = 0;
   int alloc_count = 0;
   double alloc_ms = 0.0;  // host time spent in cudaMalloc (verbose reports)
@@ -182,6 +186,22 @@ spfd_status dalloc(spfd_ctx *c, T **p, size_t count) {
   c->allocs.push_back(q);
   c->alloc_bytes.push_back(block);
   c->bytes += (int64_t)block;
+  *p = (T *)q;
+  return SPFD_OK;
+}
+
+// Pinned host block held by the context until destroy.
+template <typename T>
+spfd_status halloc(spfd_ctx *c, T **p, size_t count) {
+  *p = nullptr;
+  void *q = nullptr;
+  size_t block = 0;
+  cudaError_t e = spfd::host_get(std::max<size_t>(count, 1) * sizeof(T), &q, &block);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SPFD_ENOMEM, "pinned host allocation failed: %s", cudaGetErrorString(e));
+  }
+  c->hblocks.emplace_back(q, block);
   *p = (T *)q;
   return SPFD_OK;
 }

@@ -136,8 +136,10 @@ void launch_galerkin(const Grid &gf, const Grid &gc, const double *gx,
 // of the largest entry) (non-negative doubles order like their bit patterns).
 void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
                        cudaStream_t st);
-void launch_coarse_diag(const Grid &gc, const double *stc, double thresh,
-                        double *diag, double *dinv, cudaStream_t st);
+// diag = stc's centre coefficient where it exceeds rel * (the double whose
+// bits are *maxbits, as written by launch_diag_stats), else 0; dinv = 1/diag.
+void launch_coarse_diag(const Grid &gc, const double *stc, const unsigned long long *maxbits,
+                        double rel, double *diag, double *dinv, cudaStream_t st);
 // Inverse of the SPD matrix in buf0 (m x m, row-major) by blocked
 // Gauss-Jordan sweeps; returns buf0 or buf1, whichever holds the result.
 double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
@@ -228,6 +230,11 @@ void launch_power27(const Grid &g, const double *st27, const double *diag,
                     const double *dinv, const double *v, double *w, Scalars *sc,
                     double *partials, cudaStream_t st);
 void launch_scale(int nb, double *v, double f, cudaStream_t st);
+// Jacobi weights of a 27-point level from its power iteration: lambda =
+// sc->aux[4] / sc->aux[5] (2 if not a positive number), omega = 4 / (3 margin
+// lambda), wdinv = omega * dinv; *lam_out = lambda.
+void launch_jacobi_weights(int nb, const double *dinv, const Scalars *sc, double margin,
+                           double *wdinv, double *lam_out, cudaStream_t st);
 void launch_scaled_copy(int nb, const double *src, double f, double *dst,
                         cudaStream_t st);
 

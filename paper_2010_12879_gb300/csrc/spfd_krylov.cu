@@ -517,6 +517,21 @@ k_scaled_copy(const double *__restrict__ src, double f, double *__restrict__ dst
   dst[s] = f * src[s];
 }
 
+__global__ void __launch_bounds__(NT)
+k_jacobi_weights(const double *__restrict__ dinv, const Scalars *sc, double margin,
+                 double *__restrict__ wdinv, double *lam_out) {
+  __shared__ double om;
+  if (threadIdx.x == 0) {
+    double lam = sc->aux[4] / sc->aux[5];
+    if (!(lam > 0.0) || !isfinite(lam)) lam = 2.0;
+    om = 4.0 / (3.0 * margin * lam);
+    if (blockIdx.x == 0) *lam_out = lam;
+  }
+  __syncthreads();
+  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  wdinv[s] = om * dinv[s];
+}
+
 // ------------------------------------------------ precision conversions
 // dst = (T) (f * src) elementwise over n values.
 template <typename T>
@@ -593,6 +608,10 @@ void launch_power27(const Grid &g, const double *st27, const double *diag,
 }
 void launch_scale(int nb, double *v, double f, cudaStream_t st) {
   if (nb) k_scale<<<nb, NT, 0, st>>>(v, f);
+}
+void launch_jacobi_weights(int nb, const double *dinv, const Scalars *sc, double margin,
+                           double *wdinv, double *lam_out, cudaStream_t st) {
+  if (nb) k_jacobi_weights<<<nb, NT, 0, st>>>(dinv, sc, margin, wdinv, lam_out);
 }
 void launch_scaled_copy(int nb, const double *src, double f, double *dst,
                         cudaStream_t st) {

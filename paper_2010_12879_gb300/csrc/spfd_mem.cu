@@ -1,4 +1,4 @@
-// Device memory cache.
+// Device (and pinned host) memory cache.
 //
 // A context allocates a few dozen device buffers (4.6 GB for the 2 mm body
 // with the mixed-precision copies), and cudaMalloc/cudaFree of that much
@@ -24,6 +24,7 @@ namespace {
 struct Cache {
   std::mutex mu;
   std::vector<std::multimap<size_t, void *>> free_by_device;  // block size -> block
+  std::multimap<size_t, void *> free_host;                    // pinned host blocks
   size_t held = 0;                                            // bytes in the cache
 };
 
@@ -83,10 +84,46 @@ void mem_put(int device, void *p, size_t block) {
   c.held += block;
 }
 
+cudaError_t host_get(size_t bytes, void **p, size_t *block) {
+  const size_t want = round_up(bytes < 1 ? 1 : bytes);
+  Cache &c = cache();
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.free_host.lower_bound(want);
+    if (it != c.free_host.end() && it->first <= 2 * want + (1u << 20)) {
+      *p = it->second;
+      *block = it->first;
+      c.held -= it->first;
+      c.free_host.erase(it);
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaMallocHost(p, want);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  *block = want;
+  return cudaSuccess;
+}
+
+void host_put(void *p, size_t block) {
+  if (!p) return;
+  Cache &c = cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  c.free_host.emplace(block, p);
+  c.held += block;
+}
+
 size_t mem_release_all() {
   Cache &c = cache();
   std::lock_guard<std::mutex> lk(c.mu);
   size_t freed = 0;
+  for (auto &kv : c.free_host) {
+    cudaFreeHost(kv.second);
+    freed += kv.first;
+  }
+  c.free_host.clear();
   int cur = 0;
   cudaGetDevice(&cur);
   for (size_t d = 0; d < c.free_by_device.size(); ++d) {

@@ -13,7 +13,11 @@ namespace spfd {
 cudaError_t mem_get(int device, size_t bytes, void **p, size_t *block);
 // Returns an idle block (no queued work may still use it) to the cache.
 void mem_put(int device, void *p, size_t block);
-// Frees every cached block; returns the bytes released.
+// Pinned host blocks (staging for asynchronous uploads), cached the same way;
+// a block may be put back only once no queued copy reads it.
+cudaError_t host_get(size_t bytes, void **p, size_t *block);
+void host_put(void *p, size_t block);
+// Frees every cached block (device and pinned host); returns the bytes.
 size_t mem_release_all();
 size_t mem_cached_bytes();
 

@@ -329,19 +329,20 @@ void launch_comp_sizes(const Grid &g, const int *comp, int *sizes,
 // being unknowns (dinv = 0): they arise only from basis functions that are
 // constant on a whole tiny component and carry no information.
 __global__ void __launch_bounds__(NT)
-k_coarse_diag(const double *__restrict__ stc, size_t S, double thresh,
-              double *__restrict__ diag, double *__restrict__ dinv) {
+k_coarse_diag(const double *__restrict__ stc, size_t S, const unsigned long long *maxbits,
+              double rel, double *__restrict__ diag, double *__restrict__ dinv) {
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  double d = stc[13 * S + s];
-  bool act = d > thresh;
+  const double thresh = rel * __longlong_as_double((long long)*maxbits);
+  const double d = stc[13 * S + s];
+  const bool act = d > thresh;
   diag[s] = act ? d : 0.0;
   dinv[s] = act ? 1.0 / d : 0.0;
 }
 
-void launch_coarse_diag(const Grid &gc, const double *stc, double thresh,
-                        double *diag, double *dinv, cudaStream_t st) {
+void launch_coarse_diag(const Grid &gc, const double *stc, const unsigned long long *maxbits,
+                        double rel, double *diag, double *dinv, cudaStream_t st) {
   if (gc.nb == 0) return;
-  k_coarse_diag<<<gc.nb, NT, 0, st>>>(stc, (size_t)gc.nb * BV, thresh, diag, dinv);
+  k_coarse_diag<<<gc.nb, NT, 0, st>>>(stc, (size_t)gc.nb * BV, maxbits, rel, diag, dinv);
 }
 
 __global__ void __launch_bounds__(NT)
