@@ -17,7 +17,11 @@ function cites the paper passage it follows:
 * ``components`` / ``project`` -- the per-component constant nullspace (R4);
 * ``pcg``           -- Jacobi-preconditioned CG to a recomputed relative
   residual (Sec. II-A premise of 1e-12; the oracle defaults to 1e-13), R5;
-* ``efield``        -- |E| from Eq. 1, voxel averaged (Sec. III-E), R6.
+* ``efield``        -- |E| from Eq. 1, voxel averaged (Sec. III-E), R6;
+* ``energy`` / ``div`` / ``energy_gradient`` -- the adjoint gradient of
+  J = mean over conducting voxels of |E|^2 with respect to a and sigma: one
+  extra Eq. 3 solve A lambda = G^T dJ/du (same operator), then
+  dJ/da = dJ/du - M G lambda and dJ/dsigma from dJ/dg = -(G lambda) u (R1).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 (closed forms, brute force on tiny grids, invariants); none is unpinned.
@@ -81,6 +85,12 @@ def lib():
             L.orc_pcg.restype = ctypes.c_int
             L.orc_efield.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_double, dp]
+            L.orc_energy.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_double, dp]
+            L.orc_energy.restype = ctypes.c_double
+            L.orc_div.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_energy_grads.argtypes = [dp, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_double, dp, dp]
             _lib = L
     return _lib
 
@@ -234,3 +244,49 @@ def efield(sigma: np.ndarray, a: np.ndarray, psi: np.ndarray, h: float,
     E = np.zeros((nz, ny, nx))
     lib().orc_efield(_d(sigma), _d(a), _d(psi), nx, ny, nz, float(h), float(omega), _d(E))
     return E
+
+
+def energy(sigma: np.ndarray, a: np.ndarray, psi: np.ndarray, h: float,
+           omega: float):
+    """J = mean over conducting voxels of |E|^2 (Eq. 1, R6) and its gradient
+    gJ = dJ/du on the edges (u = a + G Psi).  Returns (J, gJ)."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    nx, ny, nz = _dims(sigma)
+    gJ = np.zeros((3, nz + 1, ny + 1, nx + 1))
+    J = float(lib().orc_energy(_d(sigma), _d(a), _d(psi), nx, ny, nz, float(h),
+                               float(omega), _d(gJ)))
+    return J, gJ
+
+
+def div(v: np.ndarray) -> np.ndarray:
+    """G^T v on the node grid for an edge field v of shape (3, nz+1, ny+1, nx+1)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    _, nzp, nyp, nxp = v.shape
+    out = np.zeros((nzp, nyp, nxp))
+    lib().orc_div(_d(v), nxp - 1, nyp - 1, nzp - 1, _d(out))
+    return out
+
+
+def energy_gradient(sigma: np.ndarray, h: float, a: np.ndarray, omega: float,
+                    tol: float = 1e-13, sys: System | None = None):
+    """J and its gradients by the adjoint method (module docstring).
+
+    Returns a dict with J, dJda (edges), dJdsigma (voxels, zero in air),
+    psi and lam (node grids) and the two solver reports."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    psi, info, sys = solve(sigma, h, a, tol, sys=sys)
+    J, gJ = energy(sigma, a, psi, h, omega)
+    badj = project(sys, sys.gather(div(gJ)))
+    lam, info_adj = pcg(sys, badj, tol)
+    lam_full = sys.scatter(project(sys, lam))
+    nx, ny, nz = _dims(sigma)
+    dJda = np.zeros_like(a)
+    dJds = np.zeros_like(sigma)
+    lib().orc_energy_grads(_d(sigma), _d(a), _d(psi), _d(lam_full), _d(gJ),
+                           _d(np.ascontiguousarray(sys.g)), nx, ny, nz, float(h),
+                           _d(dJda), _d(dJds))
+    return {"J": J, "dJda": dJda, "dJdsigma": dJds, "psi": psi, "lam": lam_full,
+            "info": info, "info_adj": info_adj}

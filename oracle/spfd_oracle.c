@@ -359,3 +359,123 @@ void orc_efield(const double *sigma, const double *a, const double *psi,
         E[v] = sqrt(ex * ex + ey * ey + ez * ez);
       }
 }
+
+/* ---------------------------------------------------------------------------
+ * Adjoint gradient of the field energy.
+ *
+ * Objective (a smooth exposure measure built on Eq. 1 and reading R6):
+ *   J = (1 / Nc) * sum over conducting voxels v of |E_v|^2,
+ *   E_v,d = c * sum over the four d-edges e of v of u_e,  c = omega / (4 h),
+ *   u = a + G Psi,  Psi solving Eq. 3:  A Psi = -G^T M a,  A = G^T M G.
+ * Gradients (one extra solve with the same operator, A lambda = G^T gJ):
+ *   gJ_e     = dJ/du_e = (1 / Nc) * sum over conducting v at e of 2 c E_v,d(e)
+ *   dJ/da_e  = gJ_e - g_e (G lambda)_e
+ *   dJ/dg_e  = -(G lambda)_e u_e
+ *   dJ/dsigma_v = (h / 4) * sum over the 12 edges e of v of dJ/dg_e
+ *                 (g_e = h/4 * sum of the sigma of the 4 voxels at e, R1),
+ * for conducting v (the set of conducting voxels is held fixed).  Edges are
+ * laid out like a, nodes like Psi, voxels like sigma.  Serial loops keep the
+ * summation order fixed.
+ * ------------------------------------------------------------------------- */
+
+/* J and gJ.  Returns J; gJ (3 * node count) is overwritten. */
+double orc_energy(const double *sigma, const double *a, const double *psi,
+                  int nx_, int ny_, int nz_, double h, double omega, double *gJ) {
+  i64 nx = nx_, ny = ny_, nz = nz_;
+  i64 nn = (nx + 1) * (ny + 1) * (nz + 1);
+  double c = omega / (4.0 * h);
+  i64 nc = 0;
+  for (i64 v = 0; v < nx * ny * nz; v++) nc += sigma[v] > 0.0;
+  for (i64 e = 0; e < 3 * nn; e++) gJ[e] = 0.0;
+  if (nc == 0) return 0.0;
+  double J = 0.0;
+  for (i64 k = 0; k < nz; k++)
+    for (i64 j = 0; j < ny; j++)
+      for (i64 i = 0; i < nx; i++) {
+        i64 v = (k * ny + j) * nx + i;
+        if (!(sigma[v] > 0.0)) continue;
+        i64 tail[3][4];   /* tail node of the four d-edges of v */
+        double E[3] = {0.0, 0.0, 0.0};
+        int q = 0;
+        for (int s = 0; s < 2; s++)
+          for (int t = 0; t < 2; t++, q++) {
+            tail[0][q] = node_id(i, j + s, k + t, nx, ny);
+            tail[1][q] = node_id(i + s, j, k + t, nx, ny);
+            tail[2][q] = node_id(i + s, j + t, k, nx, ny);
+            i64 hx = node_id(i + 1, j + s, k + t, nx, ny);
+            i64 hy = node_id(i + s, j + 1, k + t, nx, ny);
+            i64 hz = node_id(i + s, j + t, k + 1, nx, ny);
+            E[0] += a[0 * nn + tail[0][q]] + psi[hx] - psi[tail[0][q]];
+            E[1] += a[1 * nn + tail[1][q]] + psi[hy] - psi[tail[1][q]];
+            E[2] += a[2 * nn + tail[2][q]] + psi[hz] - psi[tail[2][q]];
+          }
+        for (int d = 0; d < 3; d++) {
+          E[d] *= c;
+          J += E[d] * E[d];
+          for (q = 0; q < 4; q++) gJ[d * nn + tail[d][q]] += 2.0 * c * E[d] / (double)nc;
+        }
+      }
+  return J / (double)nc;
+}
+
+/* out = G^T v on the node grid: (G^T v)_n = sum_{e entering n} v_e -
+ * sum_{e leaving n} v_e (G maps node values to head minus tail). */
+void orc_div(const double *v, int nx_, int ny_, int nz_, double *out) {
+  i64 nx = nx_, ny = ny_, nz = nz_;
+  i64 nn = (nx + 1) * (ny + 1) * (nz + 1);
+  for (i64 k = 0; k <= nz; k++)
+    for (i64 j = 0; j <= ny; j++)
+      for (i64 i = 0; i <= nx; i++) {
+        i64 n = node_id(i, j, k, nx, ny);
+        double s = 0.0;
+        if (i > 0) s += v[0 * nn + node_id(i - 1, j, k, nx, ny)];
+        if (j > 0) s += v[1 * nn + node_id(i, j - 1, k, nx, ny)];
+        if (k > 0) s += v[2 * nn + node_id(i, j, k - 1, nx, ny)];
+        if (i < nx) s -= v[0 * nn + n];
+        if (j < ny) s -= v[1 * nn + n];
+        if (k < nz) s -= v[2 * nn + n];
+        out[n] = s;
+      }
+}
+
+/* dJ/da (3 * node count) and dJ/dsigma (voxel count) from lambda (node
+ * grid, zero off the unknowns), gJ, g, a and Psi. */
+void orc_energy_grads(const double *sigma, const double *a, const double *psi,
+                      const double *lambda, const double *gJ, const double *g,
+                      int nx_, int ny_, int nz_, double h, double *dJda,
+                      double *dJdsigma) {
+  i64 nx = nx_, ny = ny_, nz = nz_;
+  i64 nn = (nx + 1) * (ny + 1) * (nz + 1);
+  for (i64 k = 0; k <= nz; k++)
+    for (i64 j = 0; j <= ny; j++)
+      for (i64 i = 0; i <= nx; i++) {
+        i64 n = node_id(i, j, k, nx, ny);
+        i64 head[3] = {i < nx ? node_id(i + 1, j, k, nx, ny) : -1,
+                       j < ny ? node_id(i, j + 1, k, nx, ny) : -1,
+                       k < nz ? node_id(i, j, k + 1, nx, ny) : -1};
+        for (int d = 0; d < 3; d++) {
+          double gl = head[d] >= 0 ? lambda[head[d]] - lambda[n] : 0.0;
+          dJda[d * nn + n] = gJ[d * nn + n] - g[d * nn + n] * gl;
+        }
+      }
+  for (i64 k = 0; k < nz; k++)
+    for (i64 j = 0; j < ny; j++)
+      for (i64 i = 0; i < nx; i++) {
+        i64 v = (k * ny + j) * nx + i;
+        if (!(sigma[v] > 0.0)) { dJdsigma[v] = 0.0; continue; }
+        double s = 0.0;
+        for (int p = 0; p < 2; p++)
+          for (int q = 0; q < 2; q++) {
+            i64 t[3] = {node_id(i, j + p, k + q, nx, ny), node_id(i + p, j, k + q, nx, ny),
+                        node_id(i + p, j + q, k, nx, ny)};
+            i64 hd[3] = {node_id(i + 1, j + p, k + q, nx, ny), node_id(i + p, j + 1, k + q, nx, ny),
+                         node_id(i + p, j + q, k + 1, nx, ny)};
+            for (int d = 0; d < 3; d++) {
+              double u = a[d * nn + t[d]] + psi[hd[d]] - psi[t[d]];
+              double gl = lambda[hd[d]] - lambda[t[d]];
+              s += -gl * u;   /* dJ/dg_e */
+            }
+          }
+        dJdsigma[v] = 0.25 * h * s;
+      }
+}
