@@ -198,6 +198,30 @@ spfd_status spfd_residual_noalloc(const double *sigma_dev, const double *a_dev,
  * blocks of matching size instead of calling cudaMalloc again. */
 void spfd_destroy(spfd_ctx *ctx);
 
+/* Gradient of the field energy
+ *   J = (1 / Nc) * sum over the Nc conducting voxels v of |E_v|^2,
+ *   E_v,d = omega / (4h) * sum over the four d-edges e of v of u_e,
+ *   u = a + G Psi
+ * (Eq. 1 voxel-averaged as in spfd_efield, without the sqrt), where psi_dev
+ * solves Eq. 3 for a_dev (from spfd_solve).  One adjoint solve
+ * A lambda = G^T dJ/du with the context's operator, preconditioner and
+ * precision gives
+ *   dJda_dev[e]      = dJ/du_e - g_e (lambda_head - lambda_tail)   (edges,
+ *                      layout of a_dev),
+ *   dJdsigma_dev[v]  = h/4 * sum over the 12 edges of v of
+ *                      -(lambda_head - lambda_tail) u_e             (voxels,
+ *                      layout of sigma; 0 in air),
+ * the derivative with respect to the conductivity of each conducting voxel
+ * (the set of conducting voxels held fixed).  J_out is host memory;
+ * dJda_dev and dJdsigma_dev are caller-owned device arrays.  tol applies to
+ * the adjoint solve.  Allocates scratch on first use (3 voxel-grid and 4
+ * node-grid arrays) and synchronises the stream.  Returns SPFD_ENOTCONVERGED
+ * (with the gradients of the current iterate) when the adjoint solve stops
+ * above tol.  Not in the paper: the adjoint of its Eq. 3 / Eq. 1 pipeline. */
+spfd_status spfd_energy_grad(spfd_ctx *ctx, const double *a_dev, const double *psi_dev,
+                             double omega, double tol, double *J_out, double *dJda_dev,
+                             double *dJdsigma_dev, spfd_info *info);
+
 /* Give every cached device block back to the driver (cudaFree); the bytes
  * released go to *released if it is not NULL.  Safe at any time: contexts
  * alive keep their own buffers.  A cudaMalloc that fails for lack of memory

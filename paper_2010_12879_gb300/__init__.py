@@ -29,7 +29,8 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 # Names declared in include/spfd.h (checked against the library by the tests).
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
-           "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory")
+           "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
+           "spfd_energy_grad")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -103,6 +104,9 @@ def lib():
             L.spfd_residual_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, dp, vp, ctypes.POINTER(dp)]
             L.spfd_residual_noalloc.restype = ctypes.c_int
+            L.spfd_energy_grad.argtypes = [vp, vp, vp, dp, dp, ctypes.POINTER(dp), vp, vp,
+                                           ctypes.POINTER(SpfdInfo)]
+            L.spfd_energy_grad.restype = ctypes.c_int
             L.spfd_release_cached_memory.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
             L.spfd_release_cached_memory.restype = ctypes.c_int
             _lib = L
@@ -177,6 +181,20 @@ def spfd_kernel_stats(ctx: int, reset: bool = False) -> list:
 
 def spfd_destroy(ctx: int):
     lib().spfd_destroy(ctypes.c_void_p(ctx))
+
+
+def spfd_energy_grad(ctx: int, a_ptr: int, psi_ptr: int, omega: float, tol: float,
+                     dJda_ptr: int, dJds_ptr: int):
+    """J and its gradients into the given device arrays; returns
+    (status, J, SpfdInfo of the adjoint solve)."""
+    J = ctypes.c_double(0.0)
+    info = SpfdInfo()
+    st = _check(lib().spfd_energy_grad(ctypes.c_void_p(ctx), ctypes.c_void_p(a_ptr),
+                                       ctypes.c_void_p(psi_ptr), float(omega), float(tol),
+                                       ctypes.byref(J), ctypes.c_void_p(dJda_ptr),
+                                       ctypes.c_void_p(dJds_ptr), ctypes.byref(info)),
+                allow=(SPFD_OK, SPFD_ENOTCONVERGED))
+    return st, J.value, info
 
 
 def spfd_release_cached_memory() -> int:
@@ -262,6 +280,19 @@ class Solver:
             E = torch.empty((nz, ny, nx), dtype=torch.float64, device=a.device)
         spfd_efield(self.ctx, a.data_ptr(), psi.data_ptr(), omega, E.data_ptr())
         return E
+
+    def energy_grad(self, a, psi, omega: float, tol: float = 0.0):
+        """J = mean over conducting voxels of |E|^2 and its gradients with
+        respect to ``a`` (edges) and the voxel conductivities (adjoint solve,
+        include/spfd.h).  Returns (J, dJda, dJdsigma, info dict, status)."""
+        import torch
+        self._check_edges(a)
+        nx, ny, nz = self.dims
+        dJda = torch.empty_like(a)
+        dJds = torch.empty((nz, ny, nx), dtype=torch.float64, device=a.device)
+        st, J, info = spfd_energy_grad(self.ctx, a.data_ptr(), psi.data_ptr(), omega, tol,
+                                       dJda.data_ptr(), dJds.data_ptr())
+        return J, dJda, dJds, info.as_dict(), st
 
     def info(self) -> dict:
         return spfd_get_info(self.ctx).as_dict()

@@ -393,8 +393,12 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
 static spfd_status prepare_rhs(spfd_ctx *c, const double *a_dev, double *bb) {
   Level &l0 = c->L[0];
   const double S = (double)l0.S;
-  SPFD_LAUNCH(c, "rhs", false, 1, 56 * S, 12 * S,
-              launch_rhs(l0.g, l0.gx, a_dev, c->bk, &c->sc->status, c->stream));
+  if (c->gJ_cur)
+    SPFD_LAUNCH(c, "rhs", false, 1, 56 * S, 6 * S,
+                launch_div_brick(l0.g, l0.diag, c->gJ_cur, c->bk, c->stream));
+  else
+    SPFD_LAUNCH(c, "rhs", false, 1, 56 * S, 12 * S,
+                launch_rhs(l0.g, l0.gx, a_dev, c->bk, &c->sc->status, c->stream));
   TRY(launch_check("rhs"));
   TRY(project<double>(c, c->bk));
   SPFD_LAUNCH(c, "project", false, 1, 20 * S, 2 * S,
@@ -534,6 +538,58 @@ static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
     return fail(SPFD_ENOTCONVERGED, "not converged: rel residual %.3e after %d iterations",
                 res.rel_res_true, res.iters);
   return SPFD_OK;
+}
+
+// Gradient of J = mean over conducting voxels of |E|^2 (Eq. 1, voxel
+// averaged) with respect to a and the voxel conductivities, by one adjoint
+// solve A lambda = G^T gJ with the context's operator and preconditioner.
+extern "C" spfd_status spfd_energy_grad(spfd_ctx *ctx, const double *a_dev,
+                                        const double *psi_dev, double omega, double tol,
+                                        double *J_out, double *dJda_dev,
+                                        double *dJdsigma_dev, spfd_info *info) {
+  if (!ctx) return fail(SPFD_EINVAL, "ctx is NULL");
+  if (!a_dev || !psi_dev || !J_out || !dJda_dev || !dJdsigma_dev)
+    return fail(SPFD_EINVAL, "a NULL argument");
+  if (std::isnan(tol) || !std::isfinite(omega)) return fail(SPFD_EINVAL, "tol or omega invalid");
+  spfd_ctx *c = ctx;
+  cudaStream_t st = c->stream;
+  Level &l0 = c->L[0];
+  const size_t nv = (size_t)c->nx * c->ny * c->nz;
+  const size_t NN = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  if (!c->ev_stage) TRY(dalloc(c, &c->ev_stage, 3 * nv));
+  if (!c->gj_stage) TRY(dalloc(c, &c->gj_stage, 3 * NN));
+  if (!c->lam_stage) TRY(dalloc(c, &c->lam_stage, NN));
+  const double cf = omega / (4.0 * c->h);
+  SPFD_LAUNCH(c, "energy", false, 1, 0, 0,
+              launch_energy(c->mask, a_dev, psi_dev, c->nx, c->ny, c->nz, cf, c->ev_stage,
+                            c->sc, c->partials, st));
+  SPFD_LAUNCH(c, "energy", false, 1, 0, 0,
+              launch_energy_gJ(c->mask, c->ev_stage, c->nx, c->ny, c->nz, cf, c->sc,
+                               c->gj_stage, st));
+  TRY(launch_check("energy"));
+  CU(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+  TRY(sync_check(c, "energy"));
+  const double Jsum = c->hsc->aux[6], nc = c->hsc->aux[7];
+  *J_out = nc > 0.0 ? Jsum / nc : 0.0;
+  spfd_info res = c->info;
+  spfd_status s = SPFD_OK;
+  if (c->ndof == 0 || !(nc > 0.0)) {
+    CU(cudaMemsetAsync(c->lam_stage, 0, NN * sizeof(double), st));
+  } else {
+    // the adjoint solve: same path as spfd_solve, right-hand side G^T gJ
+    c->gJ_cur = c->gj_stage;
+    s = solve_device(c, a_dev, tol, c->lam_stage, &res);
+    c->gJ_cur = nullptr;
+    if (s != SPFD_OK && s != SPFD_ENOTCONVERGED) return s;
+  }
+  SPFD_LAUNCH(c, "energy", false, 2, 0, 0,
+              launch_energy_grads(l0.g, l0.gx, c->mask, a_dev, psi_dev, c->lam_stage,
+                                  c->gj_stage, c->nx, c->ny, c->nz, c->h, dJda_dev,
+                                  dJdsigma_dev, st));
+  TRY(launch_check("energy gradients"));
+  TRY(sync_check(c, "energy gradients"));
+  if (info) *info = res;
+  return s;
 }
 
 extern "C" spfd_status spfd_solve(spfd_ctx *ctx, const double *a_dev,

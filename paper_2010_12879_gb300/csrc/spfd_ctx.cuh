@@ -137,6 +137,10 @@ struct spfd_ctx {
   // host-array staging; the edge potentials of the solve in progress
   double *a_stage = nullptr, *psi_stage = nullptr;
   const double *a_cur = nullptr;
+  // adjoint solve: when set, the right-hand side is G^T gJ_cur instead of
+  // -G^T M a_cur; scratch of spfd_energy_grad (allocated on first use)
+  const double *gJ_cur = nullptr;
+  double *ev_stage = nullptr, *gj_stage = nullptr, *lam_stage = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   spfd_info info{};
   // launch accounting and profiling

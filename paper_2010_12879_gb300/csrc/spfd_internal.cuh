@@ -214,6 +214,19 @@ void launch_rhs(const Grid &g, const double *gx, const double *a, double *b,
                 int *status, cudaStream_t st);
 void launch_gather(const Grid &g, const double *psi, const int *comp, double *x,
                    cudaStream_t st);
+// Adjoint of J = mean over conducting voxels of |E|^2 (spfd_krylov.cu).
+// Ev: [3][nx*ny*nz] scratch; gJ, dJda: [3][NN]; lam: node grid; dJds: voxels.
+void launch_energy(const unsigned char *mask, const double *a, const double *psi, int nx,
+                   int ny, int nz, double c, double *Ev, Scalars *sc, double *partials,
+                   cudaStream_t st);
+void launch_energy_gJ(const unsigned char *mask, const double *Ev, int nx, int ny, int nz,
+                      double c, const Scalars *sc, double *gJ, cudaStream_t st);
+void launch_div_brick(const Grid &g, const double *diag, const double *gJ, double *b,
+                      cudaStream_t st);
+void launch_energy_grads(const Grid &g, const double *gx, const unsigned char *mask,
+                         const double *a, const double *psi, const double *lam,
+                         const double *gJ, int nx, int ny, int nz, double h, double *dJda,
+                         double *dJds, cudaStream_t st);
 void launch_efield(const unsigned char *mask, const double *a,
                    const double *psi, int nx, int ny, int nz, double h,
                    double omega, double *E, cudaStream_t st);

@@ -462,6 +462,176 @@ k_efield(const unsigned char *__restrict__ mask, const double *__restrict__ a,
   }
 }
 
+// ------------------------------------------------ adjoint of the field energy
+// J = (1/Nc) sum over conducting voxels of |E_v|^2, E_v,d = c * sum over the
+// voxel's four d-edges of u_e, u = a + G Psi, c = omega / (4h) (Eq. 1,
+// voxel averaged).  Its gradient needs one extra solve A lambda = G^T gJ,
+// gJ = dJ/du; then dJ/da = gJ - g (G lambda) and dJ/dg = -(G lambda) u,
+// which the edge-conductance rule (g_e = h/4 * sum of the 4 voxels' sigma)
+// turns into dJ/dsigma_v = h/4 * sum over the voxel's 12 edges of dJ/dg.
+
+__device__ __forceinline__ void voxel_ijk(size_t v, int nx, int ny, int *i, int *j, int *k) {
+  const size_t r = v / (size_t)nx;
+  *i = (int)(v - r * nx);
+  *j = (int)(r % (size_t)ny);
+  *k = (int)(r / (size_t)ny);
+}
+
+// Ev[d][v] = E_v,d (0 in air); sc->aux[6] = sum |E_v|^2, sc->aux[7] = Nc.
+__global__ void __launch_bounds__(NT)
+k_energy(const unsigned char *__restrict__ mask, const double *__restrict__ a,
+         const double *__restrict__ psi, int nx, int ny, int nz, double c,
+         double *__restrict__ Ev, Scalars *sc, double *partials) {
+  const size_t nv = (size_t)nx * ny * nz;
+  const size_t NX = (size_t)nx + 1, NXY = NX * ((size_t)ny + 1), NN = NXY * ((size_t)nz + 1);
+  double sum = 0.0, cnt = 0.0;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv;
+       v += (size_t)gridDim.x * blockDim.x) {
+    double E[3] = {0.0, 0.0, 0.0};
+    if (mask[v]) {
+      int i, j, k;
+      voxel_ijk(v, nx, ny, &i, &j, &k);
+      const size_t n = (size_t)k * NXY + (size_t)j * NX + i;
+#pragma unroll
+      for (int st = 0; st < 4; ++st) {  // (s, t) = (0,0), (0,1), (1,0), (1,1)
+        const int s_ = st >> 1, t_ = st & 1;
+        const size_t tx = n + s_ * NX + t_ * NXY;   // x edge at (i, j+s, k+t)
+        const size_t ty = n + s_ + t_ * NXY;        // y edge at (i+s, j, k+t)
+        const size_t tz = n + s_ + t_ * NX;         // z edge at (i+s, j+t, k)
+        E[0] += (a[tx] + psi[tx + 1]) - psi[tx];
+        E[1] += (a[NN + ty] + psi[ty + NX]) - psi[ty];
+        E[2] += (a[2 * NN + tz] + psi[tz + NXY]) - psi[tz];
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        E[d] *= c;
+        sum += E[d] * E[d];
+      }
+      cnt += 1.0;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Ev[d * nv + v] = E[d];
+  }
+  double vals[2] = {sum, cnt}, tot[2];
+  if (grid_sum<2>(vals, partials, &sc->ticket[7], tot)) {
+    sc->aux[6] = tot[0];
+    sc->aux[7] = tot[1];
+  }
+}
+
+// gJ_e = sum over the conducting voxels v at edge e of 2 c E_v,d(e) / Nc,
+// in increasing voxel order; one thread per node and direction.
+__global__ void __launch_bounds__(NT)
+k_energy_gJ(const unsigned char *__restrict__ mask, const double *__restrict__ Ev,
+            int nx, int ny, int nz, double c, const Scalars *sc, double *__restrict__ gJ) {
+  const size_t nv = (size_t)nx * ny * nz;
+  const size_t NX = (size_t)nx + 1, NY = (size_t)ny + 1, NN = NX * NY * ((size_t)nz + 1);
+  const double nc = sc->aux[7];
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 3 * NN;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int d = (int)(q / NN);
+    const size_t n = q - (size_t)d * NN;
+    const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
+    double acc = 0.0;
+    // the up to 4 voxels at the edge, lowest voxel index first: offsets on
+    // the two axes other than d, (-1,-1), (0,-1), (-1,0), (0,0)
+    const bool on = (d == 0 ? i < nx : d == 1 ? j < ny : k < nz);
+    if (on && nc > 0.0) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int p1 = (w & 1) - 1, p2 = (w >> 1) - 1;  // offsets -1/0
+        int vi = i, vj = j, vk = k;
+        if (d == 0) { vj += p1; vk += p2; }
+        else if (d == 1) { vi += p1; vk += p2; }
+        else { vi += p1; vj += p2; }
+        if (vi < 0 || vj < 0 || vk < 0 || vi >= nx || vj >= ny || vk >= nz) continue;
+        const size_t v = ((size_t)vk * ny + vj) * nx + vi;
+        if (mask[v]) acc += 2.0 * c * Ev[d * nv + v] / nc;
+      }
+    }
+    gJ[q] = acc;
+  }
+}
+
+// b = G^T gJ on the level-0 unknowns (0 elsewhere):
+// sum of the entering edges' gJ minus the leaving edges'.
+__global__ void __launch_bounds__(NT)
+k_div_brick(Grid g, const double *__restrict__ diag, const double *__restrict__ gJ,
+            double *__restrict__ b) {
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const size_t s = (size_t)bk * BV + t;
+  const int4 bc = g.bco[bk];
+  const int i = bc.x * 8 + (t & 7), j = bc.y * 8 + ((t >> 3) & 7), k = bc.z * 8 + (t >> 6);
+  double acc = 0.0;
+  if (i < g.NX && j < g.NY && k < g.NZ && diag[s] > 0.0) {
+    const size_t NN = (size_t)g.NX * g.NY * g.NZ;
+    const size_t n = ((size_t)k * g.NY + j) * g.NX + i;
+    if (i > 0) acc += gJ[n - 1];
+    if (j > 0) acc += gJ[NN + n - g.NX];
+    if (k > 0) acc += gJ[2 * NN + n - (size_t)g.NX * g.NY];
+    if (i + 1 < g.NX) acc -= gJ[n];
+    if (j + 1 < g.NY) acc -= gJ[NN + n];
+    if (k + 1 < g.NZ) acc -= gJ[2 * NN + n];
+  }
+  b[s] = acc;
+}
+
+// dJ/da_e = gJ_e - g_e (lambda_head - lambda_tail); g_e from the level-0
+// conductances (0 where the brick is not stored).
+__global__ void __launch_bounds__(NT)
+k_energy_grad_a(Grid g, const double *__restrict__ gx, const double *__restrict__ lam,
+                const double *__restrict__ gJ, double *__restrict__ dJda) {
+  const size_t NX = g.NX, NY = g.NY, NN = NX * NY * (size_t)g.NZ;
+  const size_t S = (size_t)g.nb * BV;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < NN;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
+    const int s = slot_at(g, i, j, k);
+    const size_t head[3] = {n + 1, n + NX, n + NX * NY};
+    const bool has[3] = {i + 1 < g.NX, j + 1 < g.NY, k + 1 < g.NZ};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double gl = has[d] ? lam[head[d]] - lam[n] : 0.0;
+      const double ge = s >= 0 ? gx[(size_t)d * S + s] : 0.0;
+      dJda[d * NN + n] = gJ[d * NN + n] - ge * gl;
+    }
+  }
+}
+
+// dJ/dsigma_v = h/4 * sum over the 12 edges e of conducting voxel v of
+// -(lambda_head - lambda_tail) u_e (0 in air).
+__global__ void __launch_bounds__(NT)
+k_energy_grad_sigma(const unsigned char *__restrict__ mask, const double *__restrict__ a,
+                    const double *__restrict__ psi, const double *__restrict__ lam,
+                    int nx, int ny, int nz, double h, double *__restrict__ dJds) {
+  const size_t nv = (size_t)nx * ny * nz;
+  const size_t NX = (size_t)nx + 1, NXY = NX * ((size_t)ny + 1), NN = NXY * ((size_t)nz + 1);
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv;
+       v += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    if (mask[v]) {
+      int i, j, k;
+      voxel_ijk(v, nx, ny, &i, &j, &k);
+      const size_t n = (size_t)k * NXY + (size_t)j * NX + i;
+#pragma unroll
+      for (int pq = 0; pq < 4; ++pq) {
+        const int p = pq >> 1, q = pq & 1;
+        const size_t t3[3] = {n + p * NX + q * NXY, n + p + q * NXY, n + p + q * NX};
+        const size_t off[3] = {1, NX, NXY};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const size_t tl = t3[d], hd = tl + off[d];
+          const double u = (a[d * NN + tl] + psi[hd]) - psi[tl];
+          const double gl = lam[hd] - lam[tl];
+          acc += -gl * u;
+        }
+      }
+      acc *= 0.25 * h;
+    }
+    dJds[v] = acc;
+  }
+}
+
 // ------------------------------------------------ smoother eigenvalue estimate
 // Deterministic start vector on the unknowns for the power iteration.
 __global__ void __launch_bounds__(NT)
@@ -684,6 +854,38 @@ void launch_efield(const unsigned char *mask, const double *a,
   if ((size_t)nx * ny * nz == 0) return;
   const dim3 grid((nx + 127) / 128, ny, nz < 65535 ? nz : 65535);
   k_efield<<<grid, 128, 0, st>>>(mask, a, psi, nx, ny, nz, omega / (4.0 * h), E);
+}
+
+static int grid_for(size_t n) {
+  size_t b = (n + NT - 1) / NT;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, RED_GRID));
+}
+void launch_energy(const unsigned char *mask, const double *a, const double *psi, int nx,
+                   int ny, int nz, double c, double *Ev, Scalars *sc, double *partials,
+                   cudaStream_t st) {
+  const size_t nv = (size_t)nx * ny * nz;
+  k_energy<<<grid_for(nv), NT, 0, st>>>(mask, a, psi, nx, ny, nz, c, Ev, sc, partials);
+}
+void launch_energy_gJ(const unsigned char *mask, const double *Ev, int nx, int ny, int nz,
+                      double c, const Scalars *sc, double *gJ, cudaStream_t st) {
+  const size_t NN = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  k_energy_gJ<<<(int)std::min<size_t>((3 * NN + NT - 1) / NT, 152 * 64), NT, 0, st>>>(
+      mask, Ev, nx, ny, nz, c, sc, gJ);
+}
+void launch_div_brick(const Grid &g, const double *diag, const double *gJ, double *b,
+                      cudaStream_t st) {
+  if (g.nb) k_div_brick<<<g.nb, NT, 0, st>>>(g, diag, gJ, b);
+}
+void launch_energy_grads(const Grid &g, const double *gx, const unsigned char *mask,
+                         const double *a, const double *psi, const double *lam,
+                         const double *gJ, int nx, int ny, int nz, double h, double *dJda,
+                         double *dJds, cudaStream_t st) {
+  const size_t NN = (size_t)g.NX * g.NY * g.NZ, nv = (size_t)nx * ny * nz;
+  k_energy_grad_a<<<(int)std::min<size_t>((NN + NT - 1) / NT, 152 * 64), NT, 0, st>>>(
+      g, gx, lam, gJ, dJda);
+  if (nv)
+    k_energy_grad_sigma<<<(int)std::min<size_t>((nv + NT - 1) / NT, 152 * 64), NT, 0, st>>>(
+        mask, a, psi, lam, nx, ny, nz, h, dJds);
 }
 
 #define INST_K(T)                                                              \

@@ -22,6 +22,7 @@ from .phantoms import (
     Phantom,
     body_phantom,
     random_phantom,
+    scaled_body_phantom,
     sphere_phantom,
 )
 from .sources import (
@@ -39,6 +40,7 @@ __all__ = [
     "Phantom",
     "body_phantom",
     "random_phantom",
+    "scaled_body_phantom",
     "sphere_phantom",
     "MU0",
     "edge_potential",
