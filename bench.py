@@ -8,7 +8,9 @@ One step is one pass of the whole hot path over the full-size workload
   spfd_efield -- voxel-averaged |E|.
 The headline line is the plain FP64 form; the mixed-precision form (FP64
 refinement around an FP32/BF16 V-cycle CG) is timed on the same inputs and
-reported beside it.  Inputs (3.7 GB working set) exceed the 129 MB L2.
+reported beside it, and the adjoint gradient of J = mean |E|^2 (build +
+solve + gradient on the 128 x 96 x 448 config-5 body) in the "adjoint"
+sub-object.  Inputs (3.7 GB working set) exceed the 129 MB L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -252,6 +254,40 @@ def run_ours(args):
     roof64 = roofline(fam64, "fp64")
     roofmx = roofline(fammx, "mixed")
 
+    # adjoint gradient (config 5): 128 x 96 x 448 voxels at 2 mm, the C2
+    # ellipsoids scaled to the box, loop source; build + solve + gradient of
+    # J = mean |E|^2 over conducting voxels, both solves to TOL
+    adjoint = None
+    if not args.no_adjoint:
+        from spfd_inputs import loop_potential, scaled_body_phantom
+        ph5 = scaled_body_phantom(128, 96, 448)
+        a5 = torch.from_numpy(loop_potential(ph5.dims, ph5.h, ph5.origin)).to(dev)
+        sig5 = torch.from_numpy(ph5.sigma).to(dev)
+        recs = []
+        for i in range(W + K):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            S5 = spfd.Solver(sig5, ph5.h, stream=stream)
+            e[1].record(stream)
+            psi5, info5, st5 = S5.solve(a5, TOL)
+            e[2].record(stream)
+            J5, _, _, infoa, sta = S5.energy_grad(a5, psi5, OMEGA, TOL)
+            e[3].record(stream)
+            torch.cuda.synchronize(dev)
+            S5.close()
+            assert st5 == spfd.SPFD_OK and sta == spfd.SPFD_OK
+            if i >= W:
+                recs.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]),
+                             e[2].elapsed_time(e[3]), e[0].elapsed_time(e[3])))
+        mean = [statistics.mean(r[q] for r in recs) for q in range(4)]
+        adjoint = {"workload": "body phantom scaled to 128x96x448 voxels, h=2 mm, "
+                               f"{info5['n_dof']} unknowns, loop source",
+                   "objective": "J = mean over conducting voxels of |E|^2; dJ/dsigma per voxel, dJ/da per edge",
+                   "tol": TOL, "ms_per_step": round(mean[3], 3),
+                   "breakdown_ms": {"build_ms": round(mean[0], 3), "solve_ms": round(mean[1], 3),
+                                    "grad_ms": round(mean[2], 3)},
+                   "iters": info5["iters"], "adjoint_iters": infoa["iters"], "J": J5}
+
     # end to end through the public API with host arrays: sigma and a copied
     # from pinned host memory, Psi and |E| copied back, all inside the region
     e2e = None
@@ -309,6 +345,7 @@ def run_ours(args):
                       "step_speedup_vs_fp64": round(t64["step_ms"] / tmx["step_ms"], 3),
                       "roofline": roofmx, "clocks": clkmx},
             "roofline": roof64,
+            "adjoint": adjoint,
             "kernels_fp64": {k: {"launches": v["launches"] // K, "ms": round(v["ms"] / K, 4),
                                  "GBs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
                              for k, v in sorted(fam64.items(), key=lambda kv: -kv[1]["ms"])},
@@ -429,6 +466,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=30)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--ncu-step", choices=["fp64", "mixed"], default=None,
                     help="run one untimed step only (profiling target)")
     ap.add_argument("--ncu-small", action="store_true",

@@ -451,11 +451,12 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   // The brick structure of every coarser level follows from the brick maps
   // alone, so it is built on the host while the device labels components.
   // Levels are added until one could hold no more than coarse_max unknowns
-  // (its slot count bounds them) or the grid is exhausted; the levels past
+  // (its slot and node counts bound them) or the grid is exhausted; the levels past
   // the first one whose actual unknowns fit coarse_max are dropped below.
   for (int l = 0;; ++l) {
     const Level &f = c->L[l];
-    if ((int64_t)f.S <= c->opts.coarse_max || l + 1 >= c->opts.max_levels ||
+    const int64_t bound = std::min<int64_t>((int64_t)f.S, (int64_t)f.g.NX * f.g.NY * f.g.NZ);
+    if (bound <= c->opts.coarse_max || l + 1 >= c->opts.max_levels ||
         (f.g.NX <= 3 && f.g.NY <= 3 && f.g.NZ <= 3))
       break;
     int CX, CY, CZ;

@@ -390,9 +390,8 @@ void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
 // After every pivot set has been swept once, B = A^-1.  Every block inverts
 // D itself (scalar Gauss-Jordan in shared memory): its pivots are Schur
 // complements of the SPD matrix, hence positive; a non-positive one raises
-// DEV_BAD_PIVOT.  One warp inverts D while the others stage the block's
-// rows and columns of M; the block then forms D^-1 M[K, its columns] once
-// and updates its GJ_T x GJ_T tile.
+// DEV_BAD_PIVOT.  The block then forms D^-1 M[K, its columns] once and
+// updates its GJ_T x GJ_T tile.
 constexpr int GJ_B = 16;   // pivots per launch
 constexpr int GJ_T = 32;   // tile edge
 constexpr int GJ_NT = 256; // threads per block (GJ_B * GJ_B)
@@ -400,58 +399,52 @@ constexpr int GJ_NT = 256; // threads per block (GJ_B * GJ_B)
 __global__ void __launch_bounds__(GJ_NT)
 k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, int r,
            int *status) {
-  __shared__ double D[GJ_B][GJ_B + 1];
+  __shared__ double D[2][GJ_B][GJ_B + 1];
   __shared__ double W[GJ_B][GJ_T];
   __shared__ double U[GJ_T][GJ_B + 1];
   __shared__ double C[GJ_B][GJ_T];
+  __shared__ double pinv[2];
   const int t = threadIdx.x;
   const int i0 = blockIdx.y * GJ_T, j0 = blockIdx.x * GJ_T;
-  if (t < 32) {
-    // warp 0: D <- D^-1, one pivot at a time (8 entries per lane,
-    // warp-synchronous)
-#pragma unroll
-    for (int q = 0; q < GJ_B * GJ_B / 32; ++q) {
-      const int e = q * 32 + t, a = e / GJ_B, b = e % GJ_B;
-      D[a][b] = (a < r && b < r) ? A[(size_t)(k0 + a) * m + k0 + b] : (a == b ? 1.0 : 0.0);
-    }
-    __syncwarp();
-    for (int p = 0; p < GJ_B; ++p) {
-      const double d = D[p][p];
-      if (t == 0 && !(d > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
-      const double iv = d > 0.0 ? 1.0 / d : 0.0;
-      double v[GJ_B * GJ_B / 32];
-#pragma unroll
-      for (int q = 0; q < GJ_B * GJ_B / 32; ++q) {
-        const int e = q * 32 + t, a = e / GJ_B, b = e % GJ_B;
-        if (a == p && b == p) v[q] = iv;
-        else if (a == p) v[q] = D[p][b] * iv;
-        else if (b == p) v[q] = -D[a][p] * iv;
-        else v[q] = D[a][b] - D[a][p] * D[p][b] * iv;
-      }
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < GJ_B * GJ_B / 32; ++q) {
-        const int e = q * 32 + t;
-        D[e / GJ_B][e % GJ_B] = v[q];
-      }
-      __syncwarp();
-    }
-  } else {
-    // warps 1..7: the block's rows M[tile rows, K] and columns M[K, tile cols]
-    for (int q = t - 32; q < GJ_T * GJ_B; q += GJ_NT - 32) {
-      const int ii = q / GJ_B, l = q % GJ_B;
-      U[ii][l] = (l < r && i0 + ii < m) ? A[(size_t)(i0 + ii) * m + k0 + l] : 0.0;
-      const int l2 = q / GJ_T, jj = q % GJ_T;
-      C[l2][jj] = (l2 < r && j0 + jj < m) ? A[(size_t)(k0 + l2) * m + j0 + jj] : 0.0;
-    }
+  const int a = t / GJ_B, b = t % GJ_B;
+  const double d0 = (a < r && b < r) ? A[(size_t)(k0 + a) * m + k0 + b] : (a == b ? 1.0 : 0.0);
+  D[0][a][b] = d0;
+  if (t == 0) {
+    if (!(d0 > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
+    pinv[0] = d0 > 0.0 ? 1.0 / d0 : 0.0;
+  }
+  for (int q = t; q < GJ_T * GJ_B; q += GJ_NT) {
+    const int ii = q / GJ_B, l = q % GJ_B;
+    U[ii][l] = (l < r && i0 + ii < m) ? A[(size_t)(i0 + ii) * m + k0 + l] : 0.0;
+    const int l2 = q / GJ_T, jj = q % GJ_T;
+    C[l2][jj] = (l2 < r && j0 + jj < m) ? A[(size_t)(k0 + l2) * m + j0 + jj] : 0.0;
   }
   __syncthreads();
+  // D <- D^-1, one pivot per step, ping-pong between D[0] and D[1]: the
+  // thread that forms the next pivot also writes its reciprocal, so a step
+  // needs a single barrier
+  for (int p = 0; p < GJ_B; ++p) {
+    const double(*Dc)[GJ_B + 1] = D[p & 1];
+    const double iv = pinv[p & 1];
+    double v;
+    if (a == p && b == p) v = iv;
+    else if (a == p) v = Dc[p][b] * iv;
+    else if (b == p) v = -Dc[a][p] * iv;
+    else v = Dc[a][b] - Dc[a][p] * Dc[p][b] * iv;
+    D[(p + 1) & 1][a][b] = v;
+    if (a == p + 1 && b == p + 1) {
+      if (!(v > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
+      pinv[(p + 1) & 1] = v > 0.0 ? 1.0 / v : 0.0;
+    }
+    __syncthreads();
+  }
+  const double(*Dinv)[GJ_B + 1] = D[GJ_B & 1];
   // W = D^-1 M[K, tile columns]
   for (int q = t; q < GJ_B * GJ_T; q += GJ_NT) {
     const int l = q / GJ_T, jj = q % GJ_T;
     double w = 0.0;
 #pragma unroll
-    for (int l2 = 0; l2 < GJ_B; ++l2) w += D[l][l2] * C[l2][jj];
+    for (int l2 = 0; l2 < GJ_B; ++l2) w += Dinv[l][l2] * C[l2][jj];
     W[l][jj] = w;
   }
   __syncthreads();
@@ -462,13 +455,13 @@ k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, 
     const bool ki = i >= k0 && i < k0 + r, kj = j >= k0 && j < k0 + r;
     double v;
     if (ki && kj) {
-      v = D[i - k0][j - k0];
+      v = Dinv[i - k0][j - k0];
     } else if (ki) {
       v = W[i - k0][jj];
     } else if (kj) {
       v = 0.0;
 #pragma unroll
-      for (int l = 0; l < GJ_B; ++l) v -= U[ii][l] * D[l][j - k0];
+      for (int l = 0; l < GJ_B; ++l) v -= U[ii][l] * Dinv[l][j - k0];
     } else {
       v = A[(size_t)i * m + j];
 #pragma unroll
