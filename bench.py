@@ -288,6 +288,11 @@ def run_ours(args):
                                     "grad_ms": round(mean[2], 3)},
                    "iters": info5["iters"], "adjoint_iters": infoa["iters"], "J": J5}
 
+    batch = None
+    if not args.no_batch:
+        batch = bench_batch(spfd, torch, dev, stream, ph, sig, args.batch_rhs,
+                            max(1, min(K, 3)), W)
+
     # end to end through the public API with host arrays: sigma and a copied
     # from pinned host memory, Psi and |E| copied back, all inside the region
     e2e = None
@@ -346,6 +351,7 @@ def run_ours(args):
                       "roofline": roofmx, "clocks": clkmx},
             "roofline": roof64,
             "adjoint": adjoint,
+            "batch": batch,
             "kernels_fp64": {k: {"launches": v["launches"] // K, "ms": round(v["ms"] / K, 4),
                                  "GBs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
                              for k, v in sorted(fam64.items(), key=lambda kv: -kv[1]["ms"])},
@@ -362,6 +368,70 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def bench_batch(spfd, torch, dev, stream, ph, sig, nrhs, K, W):
+    """Many source fields on one body (batched-source workload): nrhs loops
+    at seeded positions (x, y in +-0.5 m, z in -0.6..-0.3 m) and random
+    orientations, made on the device.  One context; the solves of all fields
+    to TOL as one spfd_solve_batch call against nrhs spfd_solve calls, each
+    timed with CUDA events on the context's stream after W warm-up rounds."""
+    import numpy as np
+
+    from spfd_inputs import random_loops
+    from spfd_inputs.sources_torch import loop_potential_t
+    loops = random_loops(nrhs, np.random.default_rng(4))
+    nshape = tuple(d + 1 for d in ph.dims[::-1])
+    A = torch.empty((nrhs, 3) + nshape, dtype=torch.float64, device=dev)
+    for j, (c, n) in enumerate(loops):
+        loop_potential_t(ph.dims, ph.h, ph.origin, center=c, normal=n, device=dev, out=A[j])
+    psi = torch.empty((nrhs,) + nshape, dtype=torch.float64, device=dev)
+    S = spfd.Solver(sig, ph.h, stream=stream)
+
+    def batched():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        _, infos, st = S.solve_batch(A, TOL, psi)
+        e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        assert st == spfd.SPFD_OK, spfd.spfd_last_error()
+        return e[0].elapsed_time(e[1]), infos
+
+    def sequential():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        infos = []
+        e[0].record(stream)
+        for j in range(nrhs):
+            _, info, st = S.solve(A[j], TOL, psi[j])
+            assert st == spfd.SPFD_OK, spfd.spfd_last_error()
+            infos.append(info)
+        e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        return e[0].elapsed_time(e[1]), infos
+
+    out = {}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        for _ in range(W):
+            fn()
+        rec = [fn() for _ in range(K)]
+        ms = statistics.mean(r[0] for r in rec)
+        infos = rec[-1][1]
+        it = [i["iters"] for i in infos]
+        out[name] = {"ms": round(ms, 3), "solves_per_s": round(nrhs / (ms * 1e-3), 2),
+                     "iters_mean": round(statistics.mean(it), 2), "iters_max": max(it),
+                     "launches": int(sum(i["launches"] for i in infos)) if name == "sequential"
+                     else int(infos[0]["launches"]),
+                     "max_rel_res_true": max(i["rel_res_true"] for i in infos)}
+    bytes_dev = S.info()["bytes_device"]
+    S.close()
+    del A, psi
+    return {"workload": f"{nrhs} loop sources (R=0.3 m, I=1000 A) at seeded positions x,y in "
+                        "+-0.5 m, z in -0.6..-0.3 m, random orientations, on the "
+                        "256x160x896 body, h=2 mm",
+            "nrhs": nrhs, "tol": TOL, "precision": "fp64", "steps": K, "warmup": W,
+            "context_bytes_device": bytes_dev,
+            "speedup_batched_vs_sequential": round(out["sequential"]["ms"] / out["batched"]["ms"], 3),
+            **out}
 
 
 def cpu_baseline(ph, a, iters=30, record=None):
@@ -467,6 +537,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-rhs", type=int, default=64,
+                    help="source fields of the batched-solve sub-object")
     ap.add_argument("--ncu-step", choices=["fp64", "mixed"], default=None,
                     help="run one untimed step only (profiling target)")
     ap.add_argument("--ncu-small", action="store_true",

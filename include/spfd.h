@@ -140,6 +140,28 @@ spfd_status spfd_build(const double *sigma_dev, int nx, int ny, int nz,
 spfd_status spfd_solve(spfd_ctx *ctx, const double *a_dev, double tol,
                        double *psi_dev, spfd_info *info);
 
+/* Solve Eq. 3 for nrhs source fields on the same body (e.g. coil positions
+ * and orientations) in one call.
+ *   nrhs     number of right-hand sides, 1..65535.
+ *   a_dev    [nrhs][3][nz+1][ny+1][nx+1] FP64, device (as in spfd_solve).
+ *   tol      relative residual target of every right-hand side (> 0), or
+ *            <= 0 for opts.tol.
+ *   psi_dev  [nrhs][nz+1][ny+1][nx+1] FP64 output, device.
+ *   infos    optional array of nrhs reports (may be NULL); ms_solve and
+ *            launches are those of the whole call.
+ * With opts.precision = SPFD_FP64 the right-hand sides share every launch
+ * (each kernel covers the batch, one host synchronisation per CG iteration
+ * for all of them) while each keeps its own CG recurrence and stopping
+ * decision, so each Psi is the one spfd_solve returns for it alone.  The
+ * context grows its per-right-hand-side buffers on the first call with a
+ * larger nrhs (about 10 FP64 vectors of the finest level per right-hand
+ * side) and keeps them.  With SPFD_MIXED the right-hand sides are solved one
+ * after the other.  Returns SPFD_ENOTCONVERGED (every Psi written) if any
+ * right-hand side missed tol; a non-finite a on a conducting edge of any of
+ * them gives SPFD_EINVAL. */
+spfd_status spfd_solve_batch(spfd_ctx *ctx, int nrhs, const double *a_dev, double tol,
+                             double *psi_dev, spfd_info *infos);
+
 /* spfd_solve with host arrays: copies a to the device, solves, copies Psi
  * back, all on the context's stream.  Device staging buffers are allocated on
  * first use and kept by the context. */

@@ -30,7 +30,7 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
            "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
-           "spfd_energy_grad")
+           "spfd_energy_grad", "spfd_solve_batch")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -88,6 +88,9 @@ def lib():
             L.spfd_build.restype = ctypes.c_int
             L.spfd_solve.argtypes = [vp, vp, dp, vp, ctypes.POINTER(SpfdInfo)]
             L.spfd_solve.restype = ctypes.c_int
+            L.spfd_solve_batch.argtypes = [vp, ctypes.c_int, vp, dp, vp,
+                                           ctypes.POINTER(SpfdInfo)]
+            L.spfd_solve_batch.restype = ctypes.c_int
             L.spfd_solve_host.argtypes = [vp, vp, dp, vp, ctypes.POINTER(SpfdInfo)]
             L.spfd_solve_host.restype = ctypes.c_int
             L.spfd_efield.argtypes = [vp, vp, vp, dp, vp]
@@ -146,6 +149,14 @@ def spfd_solve(ctx: int, a_ptr: int, tol: float, psi_ptr: int):
                           ctypes.c_void_p(psi_ptr), ctypes.byref(info))
     _check(st, allow=(SPFD_OK, SPFD_ENOTCONVERGED))
     return st, info
+
+
+def spfd_solve_batch(ctx: int, nrhs: int, a_ptr: int, tol: float, psi_ptr: int):
+    infos = (SpfdInfo * max(nrhs, 1))()
+    st = lib().spfd_solve_batch(ctypes.c_void_p(ctx), int(nrhs), ctypes.c_void_p(a_ptr),
+                                float(tol), ctypes.c_void_p(psi_ptr), infos)
+    _check(st, allow=(SPFD_OK, SPFD_ENOTCONVERGED))
+    return st, [infos[j] for j in range(nrhs)]
 
 
 def spfd_solve_host(ctx: int, a_ptr: int, tol: float, psi_ptr: int):
@@ -265,6 +276,21 @@ class Solver:
             psi = torch.empty(self.node_shape, dtype=torch.float64, device=a.device)
         st, info = spfd_solve(self.ctx, a.data_ptr(), tol, psi.data_ptr())
         return psi, info.as_dict(), st
+
+    def solve_batch(self, a, tol: float = 0.0, psi=None):
+        """Psi for each of the source fields ``a`` (contiguous float64 CUDA,
+        ``(k, 3) + node_shape``) in one batched solve; returns (psi of shape
+        ``(k,) + node_shape``, list of k info dicts, status)."""
+        import torch
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                and a.dim() == 5 and tuple(a.shape[1:]) == (3,) + self.node_shape):
+            raise ValueError(f"a must be a contiguous float64 CUDA tensor of shape "
+                             f"(k, 3) + {self.node_shape}")
+        k = a.shape[0]
+        if psi is None:
+            psi = torch.empty((k,) + self.node_shape, dtype=torch.float64, device=a.device)
+        st, infos = spfd_solve_batch(self.ctx, k, a.data_ptr(), tol, psi.data_ptr())
+        return psi, [i.as_dict() for i in infos], st
 
     def solve_host(self, a_host, psi_host, tol: float = 0.0):
         """Host-array variant (``a_host``/``psi_host``: contiguous CPU float64

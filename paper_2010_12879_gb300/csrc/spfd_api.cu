@@ -52,9 +52,10 @@ spfd_status launch_check(const char *what) {
   return SPFD_OK;
 }
 
-// Device scalars into the pinned mirror (synchronises the stream).
-spfd_status read_scalars(spfd_ctx *c) {
-  CU(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
+// Device scalars of the first nk right-hand sides into the pinned mirror
+// (synchronises the stream).
+spfd_status read_scalars(spfd_ctx *c, int nk) {
+  CU(cudaMemcpyAsync(c->hsc, c->sc, (size_t)nk * sizeof(Scalars), cudaMemcpyDeviceToHost,
                      c->stream));
   return sync_check(c, "reading solver scalars");
 }
@@ -199,113 +200,143 @@ template <> struct Prec<float> {
   static const __nv_bfloat16 *gx(const Level &l) { return l.gxbf; }
 };
 
-// v -= per-component mean of v (aux slot 0 is scratch).
+// v -= per-component mean of v for nk right-hand sides (aux slot 0 of each
+// one's Scalars is scratch).  j0 selects the first right-hand side.
 template <typename T>
-static spfd_status project(spfd_ctx *c, T *v) {
+static spfd_status project(spfd_ctx *c, T *v, int nk = 1, int j0 = 0) {
   Level &l0 = c->L[0];
   cudaStream_t st = c->stream;
   const bool f32 = sizeof(T) == 4;
-  const double S = (double)l0.S, w = sizeof(T);
+  const double S = (double)l0.S * nk, w = sizeof(T);
   const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
+  Scalars *sc = c->sc + j0;
+  double *partials = c->partials + (size_t)j0 * c->pstride;
   if (c->ncomp > 1) {
-    CU(cudaMemsetAsync(c->csum, 0, c->ncomp * sizeof(double), st));
-    SPFD_LAUNCH(c, "project", f32, 1, (w + 4) * S, S,
-                launch_comp_sum<T>(l0.g.nb, v, c->comp, c->csum, st));
+    double *csum = c->csum + (size_t)j0 * c->cstride;
+    SPFD_LAUNCH(c, "project", f32, 3, 2 * (w + 4) * S, 12 * S,
+                launch_comp_sum<T>(l0.g.nb, v, c->comp, csum, c->ncomp, c->cstride, st, nk));
     SPFD_LAUNCH(c, "project", f32, 1, (2 * w + 4) * S, S,
-                launch_sub_mean<T>(l0.g.nb, v, c->comp, c->sc, 0, c->csum, c->csize, inv, st));
+                launch_sub_mean<T>(l0.g.nb, v, c->comp, sc, 0, csum, c->csize, inv, st, nk,
+                                   c->cstride));
   } else {
     SPFD_LAUNCH(c, "project", f32, 1, (w + 4) * S, S,
-                launch_dot<T>(l0.g.nb, v, nullptr, c->comp, c->sc, c->partials, 0, st));
+                launch_dot<T>(l0.g.nb, v, nullptr, c->comp, sc, partials, 0, st, nk,
+                              c->pstride));
     SPFD_LAUNCH(c, "project", f32, 1, (2 * w + 4) * S, S,
-                launch_sub_mean<T>(l0.g.nb, v, c->comp, c->sc, 0, nullptr, c->csize, inv, st));
+                launch_sub_mean<T>(l0.g.nb, v, c->comp, sc, 0, nullptr, c->csize, inv, st, nk));
   }
   return launch_check("projection");
 }
 
-// V-cycle on level l for the right-hand side bl; returns the buffer holding
-// the correction.  With proj (level 0) bl is first projected onto the range
-// of A in place (its per-component mean removed), so the preconditioner acts
-// as Pi M Pi and r.z never sees the rounding drift of r along the constant
-// nullspace; with one component this is fused into the first sweep, using
-// sum(r) left in sc->rsum by the preceding x/r update.
+// V-cycle on level l for the right-hand sides bl (nk of them, S_l apart);
+// returns the buffer holding the corrections.  With proj (level 0) bl is
+// first projected onto the range of A in place (its per-component mean
+// removed), so the preconditioner acts as Pi M Pi and r.z never sees the
+// rounding drift of r along the constant nullspace; with one component this
+// is fused into the first sweep, using sum(r) left in each right-hand side's
+// Scalars by the preceding x/r update.
 template <typename T>
-static T *vcycle(spfd_ctx *c, int l, T *bl, bool proj) {
+static T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk) {
   Level &lv = c->L[l];
   cudaStream_t st = c->stream;
   const int nl = (int)c->L.size();
   const bool f32 = sizeof(T) == 4;
-  const double w = sizeof(T), S = (double)lv.S;
+  const double w = sizeof(T), S = (double)lv.S * nk;
   const double wc = sizeof(typename Prec<T>::C7);
   const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
   if (proj && (c->ncomp > 1 || l == nl - 1)) {
-    project<T>(c, bl);
+    project<T>(c, bl, nk);
     proj = false;
   }
   if (l == nl - 1) {
     const double m = c->m;
-    cudaMemsetAsync(lv.X<T>(), 0, lv.S * sizeof(T), st);
-    SPFD_LAUNCH(c, "coarsest_solve", f32, 1, 8 * m * m + 2 * w * m, 2 * m * m,
-                launch_coarse_solve<T>(c->m, c->cidx, c->Binv, bl, lv.X<T>(), st));
+    cudaMemsetAsync(lv.X<T>(), 0, lv.S * nk * sizeof(T), st);
+    SPFD_LAUNCH(c, "coarsest_solve", f32, 1, (8 * m * m + 2 * w * m) * nk, 2 * m * m * nk,
+                launch_coarse_solve<T>(c->m, lv.S, c->cidx, c->Binv, bl, lv.X<T>(), st, nk));
     return lv.X<T>();
   }
   T *cur = lv.X<T>(), *oth = lv.Tt<T>();
   const T *wd = lv.WDINV<T>();
   if (proj)
     SPFD_LAUNCH(c, "jacobi_first_l0", f32, 1, 4 * w * S, 2 * S,
-                launch_jacobi_first_proj<T>(lv.g, wd, bl, cur, c->sc, inv, st));
+                launch_jacobi_first_proj<T>(lv.g, wd, bl, cur, c->sc, inv, st, nk));
   else
     SPFD_LAUNCH(c, l == 0 ? "jacobi_first_l0" : "jacobi_first_coarse", f32, 1,
-                3 * w * S, S, launch_jacobi_first<T>(lv.g, wd, bl, cur, st));
+                3 * w * S, S, launch_jacobi_first<T>(lv.g, wd, bl, cur, st, nk));
   auto sweep = [&](T *in, T *out) {
     if (l == 0)
       SPFD_LAUNCH(c, "jacobi7_l0", f32, 1, (5 * w + 3 * wc) * S, 16 * S,
                   (launch_jacobi7<T, typename Prec<T>::C7>(lv.g, Prec<T>::gx(lv),
-                                                           lv.DIAG<T>(), wd, in, bl, out, st)));
+                                                           lv.DIAG<T>(), wd, in, bl, out, st,
+                                                           nk)));
     else
       SPFD_LAUNCH(c, "jacobi27", f32, 1, 32 * w * S, 57 * S,
-                  launch_jacobi27<T>(lv.g, lv.ST<T>(), wd, in, bl, out, st));
+                  launch_jacobi27<T>(lv.g, lv.ST<T>(), wd, in, bl, out, st, nk));
   };
   for (int s = 1; s < c->opts.nu_pre; ++s) { sweep(cur, oth); std::swap(cur, oth); }
   if (l == 0)
     SPFD_LAUNCH(c, "residual7_l0", f32, 1, (4 * w + 3 * wc) * S, 14 * S,
                 (launch_residual7<T, typename Prec<T>::C7>(lv.g, Prec<T>::gx(lv),
-                                                           lv.DIAG<T>(), cur, bl, lv.R<T>(), st)));
+                                                           lv.DIAG<T>(), cur, bl, lv.R<T>(), st,
+                                                           nk)));
   else
     SPFD_LAUNCH(c, "residual27", f32, 1, 30 * w * S, 55 * S,
-                launch_residual27<T>(lv.g, lv.ST<T>(), cur, bl, lv.R<T>(), st));
+                launch_residual27<T>(lv.g, lv.ST<T>(), cur, bl, lv.R<T>(), st, nk));
   Level &cl = c->L[l + 1];
-  const double Sc = (double)cl.S;
+  const double Sc = (double)cl.S * nk;
   SPFD_LAUNCH(c, l == 0 ? "restrict_l0" : "restrict_coarse", f32, 1,
               28 * w * Sc + w * S, 54 * Sc,
-              launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st));
-  T *ec = vcycle<T>(c, l + 1, cl.B<T>(), false);
+              launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st, nk));
+  T *ec = vcycle<T>(c, l + 1, cl.B<T>(), false, nk);
   SPFD_LAUNCH(c, l == 0 ? "prolong_l0" : "prolong_coarse", f32, 1,
               (27.0 / 8.0 + 2.0) * w * S + w * Sc, 7 * S,
-              launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st));
+              launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st, nk));
   for (int s = 0; s < c->opts.nu_post; ++s) { sweep(cur, oth); std::swap(cur, oth); }
   return cur;
 }
 
 // ------------------------------------------------------------------ Krylov
+// Per-right-hand-side flags and sums of the Scalars array, set on the device.
+__global__ void k_batch_flags(Scalars *sc, int nk, int clear_rsum, int frozen, int restart) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nk) return;
+  if (clear_rsum) {
+    sc[j].rsum = 0.0;
+    sc[j].rmean = 0.0;
+    sc[j].rmean_f = 0.f;
+  }
+  if (frozen >= 0) sc[j].frozen = frozen;
+  if (restart >= 0) sc[j].restart = restart;
+}
+static spfd_status batch_flags(spfd_ctx *c, int j0, int nk, int clear_rsum, int frozen,
+                               int restart) {
+  if (nk <= 0) return SPFD_OK;
+  SPFD_LAUNCH(c, "flags", false, 1, 0, 0,
+              (k_batch_flags<<<(nk + 127) / 128, 128, 0, c->stream>>>(c->sc + j0, nk, clear_rsum,
+                                                                       frozen, restart)));
+  return launch_check("batch flags");
+}
 // The residual about to enter the V-cycle already has zero mean: clear the
 // sum and the means the fused projection reads.
-static spfd_status zero_rsum(spfd_ctx *c) {
-  CU(cudaMemsetAsync(&c->sc->rsum, 0, sizeof(double), c->stream));
-  CU(cudaMemsetAsync(&c->sc->rmean, 0, sizeof(double), c->stream));
-  CU(cudaMemsetAsync(&c->sc->rmean_f, 0, sizeof(float), c->stream));
-  return SPFD_OK;
+static spfd_status zero_rsum(spfd_ctx *c, int j0 = 0, int nk = 1) {
+  return batch_flags(c, j0, nk, 1, -1, -1);
 }
 
-static spfd_status true_residual(spfd_ctx *c, double bb, double *rel) {
+// True relative residuals ||b - A x|| / ||b|| of the nk right-hand sides
+// (level 0's r is the scratch).
+static spfd_status true_residual(spfd_ctx *c, const double *bb, double *rel, int nk = 1) {
   Level &l0 = c->L[0];
-  const double S = (double)l0.S;
+  const double S = (double)l0.S * nk;
   SPFD_LAUNCH(c, "true_residual", false, 1, 56 * S, 14 * S,
-              (launch_residual7<double, double>(l0.g, l0.gx, l0.diag, c->xk, c->bk, l0.r, c->stream)));
+              (launch_residual7<double, double>(l0.g, l0.gx, l0.diag, c->xk, c->bk, l0.r,
+                                                c->stream, nk)));
   SPFD_LAUNCH(c, "true_residual", false, 1, 20 * S, 2 * S,
-              launch_dot<double>(l0.g.nb, l0.r, l0.r, c->comp, c->sc, c->partials, 2, c->stream));
+              launch_dot<double>(l0.g.nb, l0.r, l0.r, c->comp, c->sc, c->partials, 2,
+                                 c->stream, nk, c->pstride));
   TRY(launch_check("true residual"));
-  TRY(read_scalars(c));
-  *rel = bb > 0.0 ? std::sqrt(c->hsc->aux[2] / bb) : 0.0;
+  TRY(read_scalars(c, nk));
+  for (int j = 0; j < nk; ++j)
+    rel[j] = bb[j] > 0.0 ? std::sqrt(c->hsc[j].aux[2] / bb[j]) : 0.0;
   return SPFD_OK;
 }
 
@@ -315,124 +346,175 @@ struct PcgResult {
   double rel_true = 0.0;
 };
 
-// Preconditioned CG on level 0 for A x = r0 (x = 0 on entry, r holds r0 with
-// zero mean on every component, sc->rsum = its sum).  T = double: the
-// operator is the FP64 one and the stopping rule recomputes the true
-// residual (restarting from it when the recursion has drifted).  T = float:
-// the inner solve of the refinement, stopped on the recursive residual.
+// Multigrid-preconditioned CG on level 0 for A x = r0, for nk right-hand
+// sides at once (x = 0 on entry; r holds each r0 with zero mean on every
+// component, and each right-hand side's Scalars hold rsum = 0).  Every
+// right-hand side keeps its own recurrence, scalars and stopping decision;
+// one that has stopped is frozen on the device (the x/r update skips it), so
+// each reaches the iterate it would reach alone.  Launches cover the
+// right-hand sides up to the last one still running.
+// T = double: the operator is the FP64 one and the stopping rule recomputes
+// the true residual (restarting from it when the recursion has drifted).
+// T = float: the inner solve of the refinement, stopped on the recursive
+// residual.  bb[j] = |r0_j|^2; a right-hand side with bb[j] = 0 is solved
+// by x = 0 and takes no iteration.
 template <typename T>
 static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
-                       const T *opdiag, double bb, double tol, int maxit,
-                       PcgResult *res) {
+                       const T *opdiag, const double *bb, double tol, int maxit,
+                       PcgResult *res, int nk = 1) {
   Level &l0 = c->L[0];
   cudaStream_t st = c->stream;
   const int nb = l0.g.nb;
   const size_t S0 = l0.S;
   const bool f32 = sizeof(T) == 4;
-  const double w = sizeof(T), S = (double)S0;
+  const double w = sizeof(T);
   const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
   const double *csum = c->ncomp > 1 ? c->csum : nullptr;
-  CU(cudaMemsetAsync(p, 0, S0 * sizeof(T), st));
-  auto precondition = [&](int first) -> spfd_status {
-    T *z = vcycle<T>(c, 0, r, true);
-    SPFD_LAUNCH(c, "dot_rz", f32, 1, (2 * w + 4) * S, 3 * S,
-                launch_dot_rz<T>(nb, r, z, c->comp, c->sc, c->partials, first, st));
-    if (c->ncomp > 1) {
-      CU(cudaMemsetAsync(c->csum, 0, c->ncomp * sizeof(double), st));
-      SPFD_LAUNCH(c, "project", f32, 1, (w + 4) * S, S,
-                  launch_comp_sum<T>(nb, z, c->comp, c->csum, st));
+  std::vector<int> done(nk, 0);
+  auto active_end = [&]() {
+    int e = 0;
+    for (int j = 0; j < nk; ++j)
+      if (!done[j]) e = j + 1;
+    return e;
+  };
+  CU(cudaMemsetAsync(p, 0, S0 * nk * sizeof(T), st));
+  TRY(batch_flags(c, 0, nk, 0, 0, 0));
+  for (int j = 0; j < nk; ++j) {
+    res[j] = PcgResult{};
+    if (!(bb[j] > 0.0)) {
+      res[j].conv = true;
+      done[j] = 2;
+      TRY(batch_flags(c, j, 1, 0, 1, -1));
     }
+  }
+  int na = active_end();
+  auto precondition = [&](int first) -> spfd_status {
+    const double S = (double)S0 * na;
+    T *z = vcycle<T>(c, 0, r, true, na);
+    SPFD_LAUNCH(c, "dot_rz", f32, 1, (2 * w + 4) * S, 3 * S,
+                launch_dot_rz<T>(nb, r, z, c->comp, c->sc, c->partials, first, st, na,
+                                 c->pstride));
+    if (c->ncomp > 1)
+      SPFD_LAUNCH(c, "project", f32, 3, 2 * (w + 4) * S, 12 * S,
+                  launch_comp_sum<T>(nb, z, c->comp, c->csum, c->ncomp, c->cstride, st, na));
     SPFD_LAUNCH(c, "pupdate", f32, 1, (3 * w + 4) * S, 3 * S,
-                launch_pupdate<T>(nb, p, z, c->comp, c->sc, csum, c->csize, inv, st));
+                launch_pupdate<T>(nb, p, z, c->comp, c->sc, csum, c->csize, inv, st, na,
+                                  c->cstride));
     return launch_check("V-cycle");
   };
+  if (na == 0) return SPFD_OK;
   TRY(precondition(1));
   // FP64 stopping: the recursive residual triggers a recomputation of the
   // true one; if that is still above tol, CG restarts from it (beta = 0).
   // Three restarts that fail to halve the best true residual mean the
   // rounding floor is reached: stop there (not converged).
-  double best_true = INFINITY, min_rrel = INFINITY;
-  int stall = 0, it;
-  bool restart = false;
-  res->conv = false;
-  for (it = 1; it <= maxit; ++it) {
+  std::vector<double> best_true(nk, INFINITY), min_rrel(nk, INFINITY), rel(nk, 0.0);
+  std::vector<int> stall(nk, 0), check, broke;
+  for (int it = 1; it <= maxit && na > 0; ++it) {
+    const double S = (double)S0 * na;
     SPFD_LAUNCH(c, "apply_dot", f32, 1, (f32 ? 5 : 6) * w * S, (f32 ? 20 : 15) * S,
-                launch_apply_dot<T>(l0.g, opgx, opdiag, p, q, c->sc, c->partials, st));
-    SPFD_LAUNCH(c, "finish_pq", false, 1, 8.0 * nb, nb,
+                launch_apply_dot<T>(l0.g, opgx, opdiag, p, q, c->sc, c->partials, st, na,
+                                    c->pstride));
+    SPFD_LAUNCH(c, "finish_pq", false, 1, 8.0 * nb * na, nb * na,
                 launch_finish_pq(apply_dot_partials<T>(nb), c->partials,
-                                 c->partials + (size_t)16 * nb, c->sc, st));
+                                 c->partials + (size_t)16 * nb, c->sc, st, na, c->pstride));
     SPFD_LAUNCH(c, "update_xr", f32, 1, 6 * w * S, 7 * S,
-                launch_update_xr<T>(nb, x, r, p, q, c->sc, c->partials, st));
+                launch_update_xr<T>(nb, x, r, p, q, c->sc, c->partials, st, na, c->pstride));
     TRY(launch_check("CG update"));
-    TRY(read_scalars(c));
-    const double rrel = std::sqrt(c->hsc->rr / bb);
-    if (!std::isfinite(rrel) || rrel > 1e8 * std::max(min_rrel, tol)) {
-      if (!f32) TRY(true_residual(c, c->hsc->bb, &res->rel_true));
-      break;  // breakdown: report the current iterate, not converged
+    TRY(read_scalars(c, na));
+    check.clear();
+    broke.clear();
+    for (int j = 0; j < na; ++j) {
+      if (done[j]) continue;
+      res[j].iters = it;
+      const double rrel = std::sqrt(c->hsc[j].rr / bb[j]);
+      if (!std::isfinite(rrel) || rrel > 1e8 * std::max(min_rrel[j], tol)) {
+        broke.push_back(j);  // breakdown: report the current iterate, not converged
+        continue;
+      }
+      min_rrel[j] = std::min(min_rrel[j], rrel);
+      if (rrel <= tol) {
+        if (f32) { res[j].conv = true; done[j] = 1; }
+        else check.push_back(j);
+      }
     }
-    min_rrel = std::min(min_rrel, rrel);
-    if (rrel <= tol) {
-      if (f32) { res->conv = true; break; }
-      TRY(true_residual(c, bb, &res->rel_true));
-      if (res->rel_true <= tol) { res->conv = true; break; }
-      if (res->rel_true < 0.5 * best_true) { best_true = res->rel_true; stall = 0; }
-      else if (++stall >= 3) break;
-      CU(cudaMemcpyAsync(r, l0.r, S0 * sizeof(T), cudaMemcpyDeviceToDevice, st));
-      TRY(project<T>(c, r));
-      TRY(zero_rsum(c));
-      restart = true;
+    if (!f32 && (!check.empty() || !broke.empty()))
+      TRY(true_residual(c, bb, rel.data(), na));
+    for (int j : broke) {
+      if (!f32) res[j].rel_true = rel[j];
+      done[j] = 1;
     }
-    TRY(precondition(restart ? 1 : 0));
-    restart = false;
+    for (int j : check) {
+      res[j].rel_true = rel[j];
+      if (rel[j] <= tol) { res[j].conv = true; done[j] = 1; continue; }
+      if (rel[j] < 0.5 * best_true[j]) { best_true[j] = rel[j]; stall[j] = 0; }
+      else if (++stall[j] >= 3) { done[j] = 1; continue; }
+      // restart from the true residual (left in level 0's r by true_residual)
+      CU(cudaMemcpyAsync(r + (size_t)j * S0, l0.r + (size_t)j * S0, S0 * sizeof(T),
+                         cudaMemcpyDeviceToDevice, st));
+      TRY(project<T>(c, r + (size_t)j * S0, 1, j));
+      TRY(batch_flags(c, j, 1, 1, -1, 1));
+    }
+    for (int j = 0; j < na; ++j)
+      if (done[j] == 1) {
+        TRY(batch_flags(c, j, 1, 0, 1, -1));
+        done[j] = 2;
+      }
+    na = active_end();
+    if (na > 0) TRY(precondition(0));
   }
-  res->iters = std::min(it, maxit);
   return SPFD_OK;
 }
 
-// Right-hand side b = -G^T M a (projected), and |b|^2 into c->hsc->aux[1].
-static spfd_status prepare_rhs(spfd_ctx *c, const double *a_dev, double *bb) {
+// Right-hand sides of the nk solves: b = -G^T M a (or G^T gJ for the
+// adjoint), projected; |b|^2 of each into bb.
+static spfd_status prepare_rhs(spfd_ctx *c, const double *a_dev, double *bb, int nk = 1) {
   Level &l0 = c->L[0];
-  const double S = (double)l0.S;
+  const double S = (double)l0.S * nk;
   if (c->gJ_cur)
     SPFD_LAUNCH(c, "rhs", false, 1, 56 * S, 6 * S,
                 launch_div_brick(l0.g, l0.diag, c->gJ_cur, c->bk, c->stream));
   else
     SPFD_LAUNCH(c, "rhs", false, 1, 56 * S, 12 * S,
-                launch_rhs(l0.g, l0.gx, a_dev, c->bk, &c->sc->status, c->stream));
+                launch_rhs(l0.g, l0.gx, a_dev, c->bk, &c->sc->status, c->stream, nk));
   TRY(launch_check("rhs"));
-  TRY(project<double>(c, c->bk));
+  TRY(project<double>(c, c->bk, nk));
   SPFD_LAUNCH(c, "project", false, 1, 20 * S, 2 * S,
-              launch_dot<double>(l0.g.nb, c->bk, c->bk, c->comp, c->sc, c->partials, 1, c->stream));
-  TRY(read_scalars(c));
-  if (c->hsc->status & DEV_BAD_A)
+              launch_dot<double>(l0.g.nb, c->bk, c->bk, c->comp, c->sc, c->partials, 1,
+                                 c->stream, nk, c->pstride));
+  TRY(read_scalars(c, nk));
+  if (c->hsc[0].status & DEV_BAD_A)  // one flag for the whole batch
     return fail(SPFD_EINVAL, "a holds a non-finite value on a conducting edge");
-  *bb = c->hsc->aux[1];
-  CU(cudaMemcpyAsync(&c->sc->bb, &c->sc->aux[1], sizeof(double),
-                     cudaMemcpyDeviceToDevice, c->stream));
+  for (int j = 0; j < nk; ++j) bb[j] = c->hsc[j].aux[1];
   return SPFD_OK;
 }
 
-static spfd_status solve_fp64(spfd_ctx *c, double tol, spfd_info *out) {
+static spfd_status solve_fp64(spfd_ctx *c, double tol, spfd_info *out, int nk = 1) {
   Level &l0 = c->L[0];
   const size_t S0 = l0.S;
-  double bb = 0.0;
-  TRY(prepare_rhs(c, c->a_cur, &bb));
-  CU(cudaMemsetAsync(c->xk, 0, S0 * sizeof(double), c->stream));
-  PcgResult res;
-  if (!(bb > 0.0)) {
-    res.conv = true;
-  } else {
-    CU(cudaMemcpyAsync(c->rk, c->bk, S0 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    TRY(zero_rsum(c));  // b is projected
-    TRY(pcg<double>(c, c->xk, c->rk, c->pk, c->qk, l0.gx, l0.diag, bb, tol,
-                    c->opts.maxit, &res));
-    TRY(project<double>(c, c->xk));
-    if (!res.conv) TRY(true_residual(c, bb, &res.rel_true));
+  std::vector<double> bb(nk, 0.0), rel(nk, 0.0);
+  std::vector<PcgResult> res(nk);
+  TRY(prepare_rhs(c, c->a_cur, bb.data(), nk));
+  CU(cudaMemsetAsync(c->xk, 0, S0 * nk * sizeof(double), c->stream));
+  CU(cudaMemcpyAsync(c->rk, c->bk, S0 * nk * sizeof(double), cudaMemcpyDeviceToDevice,
+                     c->stream));
+  TRY(zero_rsum(c, 0, nk));  // b is projected
+  TRY(pcg<double>(c, c->xk, c->rk, c->pk, c->qk, l0.gx, l0.diag, bb.data(), tol,
+                  c->opts.maxit, res.data(), nk));
+  TRY(project<double>(c, c->xk, nk));
+  bool redo = false;
+  for (int j = 0; j < nk; ++j) redo |= !res[j].conv;
+  if (redo) {
+    TRY(true_residual(c, bb.data(), rel.data(), nk));
+    for (int j = 0; j < nk; ++j)
+      if (!res[j].conv) res[j].rel_true = rel[j];
   }
-  out->iters = res.iters;
-  out->outer_iters = 0;
-  out->converged = res.conv ? 1 : 0;
-  out->rel_res_true = res.rel_true;
+  for (int j = 0; j < nk; ++j) {
+    out[j].iters = res[j].iters;
+    out[j].outer_iters = 0;
+    out[j].converged = res[j].conv ? 1 : 0;
+    out[j].rel_res_true = res[j].rel_true;
+  }
   return SPFD_OK;
 }
 
@@ -472,11 +554,11 @@ static spfd_status solve_mixed(spfd_ctx *c, double tol, spfd_info *out) {
     const double bb_in = c->hsc->aux[3];
     PcgResult in;
     TRY(pcg<float>(c, c->dk32, c->rk32, c->pk32, c->qk32, l0.gx32, l0.diag32,
-                   bb_in, eta, c->opts.maxit - total, &in));
+                   &bb_in, eta, c->opts.maxit - total, &in));
     total += in.iters;
     SPFD_LAUNCH(c, "convert", false, 1, 20 * S, 2 * S,
                 launch_axpy_mixed(nb, c->xk, c->dk32, nr, st));
-    TRY(true_residual(c, bb, &rel));
+    TRY(true_residual(c, &bb, &rel));
     if (rel <= tol) { out->converged = 1; break; }
     if (rel > 0.5 * prev) { if (++stall >= 2) break; } else stall = 0;
     prev = std::min(prev, rel);
@@ -494,31 +576,82 @@ static spfd_status solve_mixed(spfd_ctx *c, double tol, spfd_info *out) {
   return SPFD_OK;
 }
 
+// Grows the per-right-hand-side buffers to hold k right-hand sides: every
+// level's x, b, r, t, the FP64 Krylov vectors, the scalars (each with
+// inv_ndof), the reduction scratch and the component sums.  New vectors are
+// zeroed (slots that are not unknowns must read 0).  Synchronises the stream.
+static spfd_status ensure_batch(spfd_ctx *c, int k) {
+  if (k <= c->kcap) return SPFD_OK;
+  cudaStream_t st = c->stream;
+  TRY(sync_check(c, "batch buffers"));
+  auto grow = [&](double *&v, size_t n) -> spfd_status {
+    dfree(c, v);
+    TRY(dalloc(c, &v, n));
+    CU(cudaMemsetAsync(v, 0, n * sizeof(double), st));
+    return SPFD_OK;
+  };
+  for (Level &lv : c->L)
+    for (double **v : {&lv.x, &lv.b, &lv.r, &lv.t}) TRY(grow(*v, lv.S * k));
+  const size_t S0 = c->L[0].S;
+  for (double **v : {&c->xk, &c->rk, &c->pk, &c->qk, &c->bk}) TRY(grow(*v, S0 * k));
+  TRY(grow(c->partials, c->pstride * k));
+  if (c->ncomp > 1) TRY(grow(c->csum, (size_t)c->cstride * k));
+  Scalars *sc = nullptr, *hsc = nullptr;
+  TRY(dalloc(c, &sc, k));
+  TRY(halloc(c, &hsc, k));
+  memset(hsc, 0, (size_t)k * sizeof(Scalars));
+  const double inv_ndof = c->ndof ? 1.0 / (double)c->ndof : 0.0;
+  for (int j = 0; j < k; ++j) hsc[j].inv_ndof = inv_ndof;
+  CU(cudaMemcpyAsync(sc, hsc, (size_t)k * sizeof(Scalars), cudaMemcpyHostToDevice, st));
+  TRY(sync_check(c, "batch scalars"));
+  dfree(c, c->sc);
+  c->sc = sc;
+  c->hsc = hsc;
+  c->kcap = k;
+  return SPFD_OK;
+}
+
+// Solves the nk systems whose edge potentials are a_dev + j * 3 NN (NN
+// nodes) into psi_dev + j * NN.  FP64: one CG over all of them (batched
+// launches); mixed precision: one refinement after the other.
 static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
-                                double *psi_dev, spfd_info *info) {
+                                double *psi_dev, spfd_info *info, int nk = 1) {
   if (!(tol > 0.0)) tol = c->opts.tol;
   cudaStream_t st = c->stream;
   Level &l0 = c->L[0];
-  spfd_info res = c->info;
+  const size_t NNs = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  std::vector<spfd_info> res(nk, c->info);
   const int64_t launches0 = c->launch_count;
+  if (nk > 1 && c->ndof > 0 && c->opts.precision != SPFD_MIXED) TRY(ensure_batch(c, nk));
   CU(cudaEventRecord(c->ev0, st));
   CU(cudaMemsetAsync(&c->sc->status, 0, sizeof(int), st));
   if (c->ndof == 0) {
-    size_t NN = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
-    CU(cudaMemsetAsync(psi_dev, 0, NN * sizeof(double), st));
-    res.iters = 0;
-    res.outer_iters = 0;
-    res.converged = 1;
-    res.rel_res_true = 0.0;
+    CU(cudaMemsetAsync(psi_dev, 0, NNs * nk * sizeof(double), st));
+    for (auto &r : res) {
+      r.iters = 0;
+      r.outer_iters = 0;
+      r.converged = 1;
+      r.rel_res_true = 0.0;
+    }
+  } else if (c->opts.precision == SPFD_MIXED) {
+    for (int j = 0; j < nk; ++j) {
+      c->a_cur = a_dev + (size_t)j * 3 * NNs;
+      spfd_status s = solve_mixed(c, tol, &res[j]);
+      c->a_cur = nullptr;
+      TRY(s);
+      const double NN = (double)NNs;
+      SPFD_LAUNCH(c, "scatter", false, 1, 8 * NN + 12.0 * l0.S, 0,
+                  launch_scatter<double>(l0.g, c->xk, c->comp, psi_dev + (size_t)j * NNs, st));
+      TRY(launch_check("scatter"));
+    }
   } else {
     c->a_cur = a_dev;
-    spfd_status s = c->opts.precision == SPFD_MIXED ? solve_mixed(c, tol, &res)
-                                                    : solve_fp64(c, tol, &res);
+    spfd_status s = solve_fp64(c, tol, res.data(), nk);
     c->a_cur = nullptr;
     TRY(s);
-    const double NN = (double)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
-    SPFD_LAUNCH(c, "scatter", false, 1, 8 * NN + 12.0 * l0.S, 0,
-                launch_scatter<double>(l0.g, c->xk, c->comp, psi_dev, st));
+    const double NN = (double)NNs * nk;
+    SPFD_LAUNCH(c, "scatter", false, 1, 8 * NN + 12.0 * l0.S * nk, 0,
+                launch_scatter<double>(l0.g, c->xk, c->comp, psi_dev, st, nk));
     TRY(launch_check("scatter"));
   }
   CU(cudaEventRecord(c->ev1, st));
@@ -526,17 +659,23 @@ static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
   TRY(prof_flush(c));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-  res.ms_solve = ms;
-  res.bytes_device = c->bytes;
-  res.launches = c->launch_count - launches0;
-  c->info = res;
-  if (info) *info = res;
+  int bad = -1;
+  for (int j = 0; j < nk; ++j) {
+    res[j].ms_solve = ms;
+    res[j].bytes_device = c->bytes;
+    res[j].launches = c->launch_count - launches0;
+    if (info) info[j] = res[j];
+    if (!res[j].converged && bad < 0) bad = j;
+  }
+  c->info = res[nk - 1];
   if (c->opts.verbose)
-    fprintf(stderr, "[spfd] solve: %d it (%d outer), rel %.3e, %.3f ms\n", res.iters,
-            res.outer_iters, res.rel_res_true, ms);
-  if (!res.converged)
-    return fail(SPFD_ENOTCONVERGED, "not converged: rel residual %.3e after %d iterations",
-                res.rel_res_true, res.iters);
+    for (int j = 0; j < nk; ++j)
+      fprintf(stderr, "[spfd] solve %d/%d: %d it (%d outer), rel %.3e, %.3f ms\n", j + 1, nk,
+              res[j].iters, res[j].outer_iters, res[j].rel_res_true, ms);
+  if (bad >= 0)
+    return fail(SPFD_ENOTCONVERGED,
+                "not converged: right-hand side %d at rel residual %.3e after %d iterations",
+                bad, res[bad].rel_res_true, res[bad].iters);
   return SPFD_OK;
 }
 
@@ -599,6 +738,15 @@ extern "C" spfd_status spfd_solve(spfd_ctx *ctx, const double *a_dev,
   if (!a_dev || !psi_dev) return fail(SPFD_EINVAL, "a_dev / psi_dev is NULL");
   if (std::isnan(tol)) return fail(SPFD_EINVAL, "tol is NaN");
   return solve_device(ctx, a_dev, tol, psi_dev, info);
+}
+
+extern "C" spfd_status spfd_solve_batch(spfd_ctx *ctx, int nrhs, const double *a_dev,
+                                        double tol, double *psi_dev, spfd_info *infos) {
+  if (!ctx) return fail(SPFD_EINVAL, "ctx is NULL");
+  if (nrhs < 1 || nrhs > 65535) return fail(SPFD_EINVAL, "nrhs must be in 1..65535");
+  if (!a_dev || !psi_dev) return fail(SPFD_EINVAL, "a_dev / psi_dev is NULL");
+  if (std::isnan(tol)) return fail(SPFD_EINVAL, "tol is NaN");
+  return solve_device(ctx, a_dev, tol, psi_dev, infos, nrhs);
 }
 
 extern "C" spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host,

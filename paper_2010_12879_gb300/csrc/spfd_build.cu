@@ -425,7 +425,8 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   // (16 reserved), followed by the finishing reduction's block sums (152); the
   // grid-stride reductions of every level write 2 values per block, on at
   // most 608 blocks
-  TRY(dalloc(c, &c->partials, 16 * (size_t)std::max(nb0, 1) + 2048));
+  c->pstride = 16 * (size_t)std::max(nb0, 1) + 2048;
+  TRY(dalloc(c, &c->partials, c->pstride));
   int *parent = nullptr, *counts = nullptr, *offsets = nullptr;
   {
     Level &l0 = c->L[0];
@@ -507,7 +508,8 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     dfree(c, parent);
     dfree(c, counts);
     dfree(c, offsets);
-    if (c->ncomp > 1) TRY(dalloc(c, &c->csum, c->ncomp));
+    c->cstride = 3 * c->ncomp + 1;
+    if (c->ncomp > 1) TRY(dalloc(c, &c->csum, c->cstride));
   }
   clk.mark("fine+components");
 

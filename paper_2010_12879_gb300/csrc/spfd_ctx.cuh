@@ -123,13 +123,20 @@ struct spfd_ctx {
   int ncomp = 0;
   int64_t ndof = 0;
   int *csize = nullptr;           // [ncomp]
-  double *csum = nullptr;         // [ncomp] (only when ncomp > 1)
+  // per-component sum workspace [kcap][cstride], cstride = 3 ncomp + 1
+  // (only when ncomp > 1)
+  double *csum = nullptr;
+  int cstride = 0;
   // Krylov vectors (FP64) and the FP32 inner-solve vectors (mixed)
   double *xk = nullptr, *rk = nullptr, *pk = nullptr, *qk = nullptr, *bk = nullptr;
   float *dk32 = nullptr, *rk32 = nullptr, *pk32 = nullptr, *qk32 = nullptr;
-  spfd::Scalars *sc = nullptr;    // device scalars
+  spfd::Scalars *sc = nullptr;    // device scalars, one per right-hand side
   spfd::Scalars *hsc = nullptr;   // pinned host mirror
-  double *partials = nullptr;
+  double *partials = nullptr;     // reduction scratch, pstride per right-hand side
+  size_t pstride = 0;
+  // right-hand sides the per-RHS buffers hold (level vectors, Krylov
+  // vectors, scalars, partials, component sums); grown by batched solves
+  int kcap = 1;
   // coarsest level
   int m = 0;
   int *cidx = nullptr;
@@ -228,7 +235,7 @@ void dfree(spfd_ctx *c, T *&p) {
 
 spfd_status sync_check(spfd_ctx *c, const char *what);
 spfd_status launch_check(const char *what);
-spfd_status read_scalars(spfd_ctx *c);
+spfd_status read_scalars(spfd_ctx *c, int nk = 1);
 spfd_status build_impl(spfd_ctx *c, const double *sigma);
 void destroy_ctx(spfd_ctx *c);
 

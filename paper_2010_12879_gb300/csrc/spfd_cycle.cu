@@ -23,6 +23,8 @@ k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r) {
   const int bk = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  const size_t off = (size_t)blockIdx.y * S;  // right-hand side blockIdx.y
+  x += off; b += off; r += off;
   const Q4<T> bv = ldq<T>(b + s0);
   Q4<T> xc, rv;
   apply7_row<T, C, true>(g, gx, diag, x, S, bk, t, bv, xc, rv);
@@ -36,6 +38,8 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ b, T *__restrict__ xout) {
   const int bk = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  const size_t off = (size_t)blockIdx.y * S;
+  xin += off; b += off; xout += off;
   const Q4<T> bv = ldq<T>(b + s0), wv = ldq<T>(wdinv + s0);
   Q4<T> xc, rv;
   apply7_row<T, C, true>(g, gx, diag, xin, S, bk, t, bv, xc, rv);
@@ -51,6 +55,8 @@ k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
   __shared__ T tl[10][10][10];
   __shared__ int sn[27];
   const int bk = blockIdx.x;
+  const size_t off = (size_t)blockIdx.y * g.nb * BV;
+  x += off; b += off; r += off;
   load_nbr(g, bk, sn);
   __syncthreads();
   tile_full<T>(tl, x, bk, sn);
@@ -67,6 +73,8 @@ k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
   __shared__ T tl[10][10][10];
   __shared__ int sn[27];
   const int bk = blockIdx.x;
+  const size_t off = (size_t)blockIdx.y * g.nb * BV;
+  xin += off; b += off; xout += off;
   load_nbr(g, bk, sn);
   __syncthreads();
   tile_full<T>(tl, xin, bk, sn);
@@ -85,6 +93,8 @@ k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
                T *__restrict__ x) {
   constexpr int N = V16<T>::N;
   const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
+  const size_t off = (size_t)blockIdx.y * gridDim.x * BV;
+  b += off; x += off;
   const V16<T> w = ld16(wdinv + s0), bv = ld16(b + s0);
   V16<T> xv;
 #pragma unroll
@@ -100,6 +110,8 @@ k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
                     T *__restrict__ x, const Scalars *sc, double) {
   constexpr int N = V16<T>::N;
   const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
+  const size_t off = (size_t)blockIdx.y * gridDim.x * BV;
+  b += off; x += off; sc += blockIdx.y;
   T mean;
   if constexpr (sizeof(T) == 4) mean = sc->rmean_f; else mean = sc->rmean;
   const V16<T> w = ld16(wdinv + s0);
@@ -123,11 +135,13 @@ k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
 // 16B-1 .. 16B+15 (per axis) from the 27 fine bricks 2B-1 .. 2B+1.
 template <typename T>
 __global__ void __launch_bounds__(NT)
-k_restrict(Grid gc, const T *__restrict__ P, const T *__restrict__ rf,
+k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf,
            T *__restrict__ bcoarse) {
   __shared__ T fs[17][17][17];
   __shared__ int sk[27];
   const int bk = blockIdx.x, t = threadIdx.x;
+  rf += (size_t)blockIdx.y * Sf;
+  bcoarse += (size_t)blockIdx.y * gc.nb * BV;
   if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
   __syncthreads();
   for (int q = t; q < 17 * 17 * 17; q += NT) {
@@ -162,6 +176,8 @@ k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
           T *__restrict__ ef) {
   const int bk = blockIdx.x * 2 + (threadIdx.x >> 6);
   if (bk >= gf.nb) return;
+  ec += (size_t)blockIdx.y * gc.nb * BV;
+  ef += (size_t)blockIdx.y * gf.nb * BV;
   const int cell = threadIdx.x & 63;
   const int ccx = cell & 3, ccy = (cell >> 2) & 3, ccz = cell >> 4;
   const size_t NC = (size_t)gf.nb * 64, cid = (size_t)bk * 64 + cell;
@@ -206,9 +222,11 @@ k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
 // Coarsest level: x = B^{-1} b on the m listed unknowns (dense, FP64); one
 // warp per row.  Unlisted slots must be zero beforehand.
 template <typename T>
-__global__ void k_coarse_solve(int m, const int *__restrict__ idx,
+__global__ void k_coarse_solve(int m, size_t S, const int *__restrict__ idx,
                                const double *__restrict__ Binv,
                                const T *__restrict__ b, T *__restrict__ x) {
+  b += (size_t)blockIdx.y * S;
+  x += (size_t)blockIdx.y * S;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m) return;
@@ -223,80 +241,83 @@ __global__ void k_coarse_solve(int m, const int *__restrict__ idx,
 // ------------------------------------------------------------ launchers
 template <typename T, typename C>
 void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
-                      const T *b, T *r, cudaStream_t st) {
-  if (g.nb) k_residual7<T, C><<<g.nb, RT, 0, st>>>(g, gx, diag, x, b, r);
+                      const T *b, T *r, cudaStream_t st, int nk) {
+  if (g.nb) k_residual7<T, C><<<dim3(g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r);
 }
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
-                       T *r, cudaStream_t st) {
-  if (g.nb) k_residual27<T><<<g.nb, NT, 0, st>>>(g, stc, x, b, r);
+                       T *r, cudaStream_t st, int nk) {
+  if (g.nb) k_residual27<T><<<dim3(g.nb, nk), NT, 0, st>>>(g, stc, x, b, r);
 }
 template <typename T>
 void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
-                         cudaStream_t st) {
-  if (g.nb) k_jacobi_first<T><<<g.nb, NT / V16<T>::N, 0, st>>>(wdinv, b, x);
+                         cudaStream_t st, int nk) {
+  if (g.nb) k_jacobi_first<T><<<dim3(g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x);
 }
 template <typename T>
 void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
                               const Scalars *sc, double inv_ndof,
-                              cudaStream_t st) {
+                              cudaStream_t st, int nk) {
   if (g.nb)
-    k_jacobi_first_proj<T><<<g.nb, NT / V16<T>::N, 0, st>>>(wdinv, b, x, sc, inv_ndof);
+    k_jacobi_first_proj<T><<<dim3(g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, sc, inv_ndof);
 }
 template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
-                    const T *xin, const T *b, T *xout, cudaStream_t st) {
-  if (g.nb) k_jacobi7<T, C><<<g.nb, RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout);
+                    const T *xin, const T *b, T *xout, cudaStream_t st, int nk) {
+  if (g.nb) k_jacobi7<T, C><<<dim3(g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout);
 }
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
-                     const T *b, T *xout, cudaStream_t st) {
-  if (g.nb) k_jacobi27<T><<<g.nb, NT, 0, st>>>(g, stc, wdinv, xin, b, xout);
+                     const T *b, T *xout, cudaStream_t st, int nk) {
+  if (g.nb) k_jacobi27<T><<<dim3(g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout);
 }
 template <typename T>
-void launch_restrict(const Grid &, const Grid &gc, const T *P, const T *rf,
-                     T *bcoarse, cudaStream_t st) {
-  if (gc.nb) k_restrict<T><<<gc.nb, NT, 0, st>>>(gc, P, rf, bcoarse);
+void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
+                     T *bcoarse, cudaStream_t st, int nk) {
+  if (gc.nb)
+    k_restrict<T><<<dim3(gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf, bcoarse);
 }
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
-                    T *ef, cudaStream_t st) {
-  if (gf.nb) k_prolong<T><<<(gf.nb + 1) / 2, 128, 0, st>>>(gf, gc, P, ec, ef);
+                    T *ef, cudaStream_t st, int nk) {
+  if (gf.nb) k_prolong<T><<<dim3((gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef);
 }
 template <typename T>
-void launch_coarse_solve(int m, const int *idx, const double *Binv, const T *b,
-                         T *x, cudaStream_t st) {
+void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
+                         const T *b, T *x, cudaStream_t st, int nk) {
   if (m <= 0) return;
   const int warps_per_block = 8;
-  k_coarse_solve<T><<<(m + warps_per_block - 1) / warps_per_block,
-                      32 * warps_per_block, 0, st>>>(m, idx, Binv, b, x);
+  k_coarse_solve<T><<<dim3((m + warps_per_block - 1) / warps_per_block, nk),
+                      32 * warps_per_block, 0, st>>>(m, S, idx, Binv, b, x);
 }
 
 #define INST_T(T)                                                             \
   template void launch_residual27<T>(const Grid &, const T *, const T *,      \
-                                     const T *, T *, cudaStream_t);           \
+                                     const T *, T *, cudaStream_t, int);      \
   template void launch_jacobi_first<T>(const Grid &, const T *, const T *,    \
-                                       T *, cudaStream_t);                    \
+                                       T *, cudaStream_t, int);               \
   template void launch_jacobi_first_proj<T>(const Grid &, const T *, T *,     \
                                             T *, const Scalars *, double,     \
-                                            cudaStream_t);                    \
+                                            cudaStream_t, int);               \
   template void launch_jacobi27<T>(const Grid &, const T *, const T *,        \
-                                   const T *, const T *, T *, cudaStream_t);  \
+                                   const T *, const T *, T *, cudaStream_t,   \
+                                   int);                                      \
   template void launch_restrict<T>(const Grid &, const Grid &, const T *,     \
-                                   const T *, T *, cudaStream_t);             \
+                                   const T *, T *, cudaStream_t, int);        \
   template void launch_prolong<T>(const Grid &, const Grid &, const T *,      \
-                                  const T *, T *, cudaStream_t);              \
-  template void launch_coarse_solve<T>(int, const int *, const double *,      \
-                                       const T *, T *, cudaStream_t);
+                                  const T *, T *, cudaStream_t, int);         \
+  template void launch_coarse_solve<T>(int, size_t, const int *,              \
+                                       const double *, const T *, T *,        \
+                                       cudaStream_t, int);
 INST_T(double)
 INST_T(float)
 #define INST_TC(T, C)                                                         \
   template void launch_residual7<T, C>(const Grid &, const C *, const T *,    \
                                        const T *, const T *, T *,             \
-                                       cudaStream_t);                         \
+                                       cudaStream_t, int);                    \
   template void launch_jacobi7<T, C>(const Grid &, const C *, const T *,      \
                                      const T *, const T *, const T *, T *,    \
-                                     cudaStream_t);
+                                     cudaStream_t, int);
 INST_TC(double, double)
 INST_TC(float, float)
 INST_TC(float, __nv_bfloat16)

@@ -96,6 +96,8 @@ struct Scalars {
   unsigned long long ustat[2];  // count of positive entries, max entry (bits)
   unsigned int ticket[8];  // last-block counters, one per reduction site
   int status;       // SPFD_DEV_* bits
+  int frozen;       // batched solves: this right-hand side has stopped
+  int restart;      // batched solves: the next beta of this right-hand side is 0
 };
 
 enum : int {
@@ -146,72 +148,88 @@ double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
                              cudaStream_t st);
 
 // V-cycle pieces (spfd_cycle.cu); T = vector type, C = 7-point coefficient type.
+// nk right-hand sides per launch (blockIdx.y): the vectors of a level with S
+// slots are nk consecutive blocks of S values; operators are shared.
 template <typename T, typename C>
 void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
-                      const T *b, T *r, cudaStream_t st);
+                      const T *b, T *r, cudaStream_t st, int nk = 1);
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
-                       T *r, cudaStream_t st);
+                       T *r, cudaStream_t st, int nk = 1);
 template <typename T>
 void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
-                         cudaStream_t st);
+                         cudaStream_t st, int nk = 1);
 // First level-0 sweep with the projection of the right-hand side fused in:
-// b <- b - (sum b)/n on the unknowns (one component), then x = wdinv * b.
+// b <- b - (sum b)/n on the unknowns (one component), then x = wdinv * b;
+// sc holds one Scalars per right-hand side.
 template <typename T>
 void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
                               const Scalars *sc, double inv_ndof,
-                              cudaStream_t st);
+                              cudaStream_t st, int nk = 1);
 template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
-                    const T *xin, const T *b, T *xout, cudaStream_t st);
+                    const T *xin, const T *b, T *xout, cudaStream_t st, int nk = 1);
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
-                     const T *b, T *xout, cudaStream_t st);
+                     const T *b, T *xout, cudaStream_t st, int nk = 1);
 template <typename T>
 void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
-                     T *bc, cudaStream_t st);
+                     T *bc, cudaStream_t st, int nk = 1);
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
-                    T *ef, cudaStream_t st);
+                    T *ef, cudaStream_t st, int nk = 1);
+// x[idx] = Binv b[idx] on the coarsest level (S slots per right-hand side).
 template <typename T>
-void launch_coarse_solve(int m, const int *idx, const double *Binv,
-                         const T *b, T *x, cudaStream_t st);
+void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
+                         const T *b, T *x, cudaStream_t st, int nk = 1);
 
-// Krylov loop, RHS, scatter, |E| (spfd_krylov.cu)
+// Krylov loop, RHS, scatter, |E| (spfd_krylov.cu).  nk right-hand sides per
+// launch (blockIdx.y): level-0 vectors are nk blocks of S0 values, sc points
+// at nk consecutive Scalars, partials at nk regions pstride apart, csum at nk
+// blocks of ncomp sums; edge and node-grid arrays are nk blocks of 3 NN / NN.
 template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
-                      T *q, Scalars *sc, double *partials, cudaStream_t st);
+                      T *q, Scalars *sc, double *partials, cudaStream_t st, int nk = 1,
+                      size_t pstride = 0);
 // Number of partial sums launch_apply_dot writes for nb bricks (one per warp,
-// 4 per brick); launch_finish_pq adds n of them (scratch: at
-// least 152 doubles, not overlapping) and sets alpha = rz / pq.
+// 4 per brick); launch_finish_pq adds n of them (scratch: at least 152
+// doubles, not overlapping) and sets alpha = rz / pq.
 template <typename T> int apply_dot_partials(int nb);
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
-                      cudaStream_t st);
+                      cudaStream_t st, int nk = 1, size_t pstride = 0);
+// x += alpha p, r -= alpha q, r.r, sum r; right-hand sides whose Scalars are
+// frozen are left as they are.
 template <typename T>
 void launch_update_xr(int nb, T *x, T *r, const T *p, const T *q, Scalars *sc,
-                      double *partials, cudaStream_t st);
+                      double *partials, cudaStream_t st, int nk = 1, size_t pstride = 0);
+// r.z and beta (0 when first, or when the right-hand side's restart flag is
+// set; the flag is cleared).
 template <typename T>
 void launch_dot_rz(int nb, const T *r, const T *z, const int *comp,
-                   Scalars *sc, double *partials, int first, cudaStream_t st);
+                   Scalars *sc, double *partials, int first, cudaStream_t st, int nk = 1,
+                   size_t pstride = 0);
+// Per-component sums of v (several components), exact and order-independent:
+// ws is a workspace of cstride >= 3 ncomp + 1 doubles per right-hand side
+// (zeroed here), whose first ncomp entries receive the sums.  Four launches.
 template <typename T>
-void launch_comp_sum(int nb, const T *v, const int *comp, double *csum,
-                     cudaStream_t st);
+void launch_comp_sum(int nb, const T *v, const int *comp, double *ws, int ncomp,
+                     int cstride, cudaStream_t st, int nk = 1);
 template <typename T>
 void launch_pupdate(int nb, T *p, const T *z, const int *comp,
                     const Scalars *sc, const double *csum, const int *csize,
-                    double inv_ndof, cudaStream_t st);
+                    double inv_ndof, cudaStream_t st, int nk = 1, int cstride = 0);
 template <typename T>
 void launch_sub_mean(int nb, T *v, const int *comp, const Scalars *sc,
                      int aux_slot, const double *csum, const int *csize,
-                     double inv_ndof, cudaStream_t st);
+                     double inv_ndof, cudaStream_t st, int nk = 1, int cstride = 0);
 template <typename T>
 void launch_dot(int nb, const T *x, const T *y, const int *comp, Scalars *sc,
-                double *partials, int slot, cudaStream_t st);
+                double *partials, int slot, cudaStream_t st, int nk = 1, size_t pstride = 0);
 template <typename T>
 void launch_scatter(const Grid &g, const T *x, const int *comp, double *psi,
-                    cudaStream_t st);
+                    cudaStream_t st, int nk = 1);
 void launch_rhs(const Grid &g, const double *gx, const double *a, double *b,
-                int *status, cudaStream_t st);
+                int *status, cudaStream_t st, int nk = 1);
 void launch_gather(const Grid &g, const double *psi, const int *comp, double *x,
                    cudaStream_t st);
 // Adjoint of J = mean over conducting voxels of |E|^2 (spfd_krylov.cu).

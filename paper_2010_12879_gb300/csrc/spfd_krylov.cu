@@ -104,9 +104,13 @@ constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SM
 template <typename T>
 __global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
-            const T *__restrict__ p, T *__restrict__ q, double *partials) {
+            const T *__restrict__ p, T *__restrict__ q, double *partials,
+            size_t pstride) {
   const int bk = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  p += (size_t)blockIdx.y * S;  // right-hand side blockIdx.y
+  q += (size_t)blockIdx.y * S;
+  partials += (size_t)blockIdx.y * pstride;
   Q4<T> pc, qv;
   apply7_row<T, T, false>(g, gx, diag, p, S, bk, t, zq<T>(), pc, qv);
   stq(q + s0, qv);
@@ -151,7 +155,11 @@ int apply_dot_partials(int nb) { return nb * (RT / 32); }
 // the last block adds the block sums, fixed order); alpha = rz / pq.
 // scratch must not overlap the partials.
 __global__ void __launch_bounds__(NT)
-k_finish_pq(const double *__restrict__ partials, int n, double *scratch, Scalars *sc) {
+k_finish_pq(const double *__restrict__ partials, int n, double *scratch, Scalars *sc,
+            size_t pstride) {
+  partials += (size_t)blockIdx.y * pstride;
+  scratch += (size_t)blockIdx.y * pstride;
+  sc += blockIdx.y;
   double a = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     a += partials[i];
@@ -171,8 +179,15 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
 k_update_xr(int nb, T *__restrict__ x, T *__restrict__ r,
             const T *__restrict__ p, const T *__restrict__ q, Scalars *sc,
-            double *partials) {
+            double *partials, size_t pstride) {
   constexpr int N = V16<T>::N;
+  sc += blockIdx.y;
+  if (sc->frozen) return;  // this right-hand side has converged
+  {
+    const size_t off = (size_t)blockIdx.y * nb * BV;
+    x += off; r += off; p += off; q += off;
+    partials += (size_t)blockIdx.y * pstride;
+  }
   T alpha;
   if constexpr (sizeof(T) == 4) alpha = sc->alpha_f; else alpha = sc->alpha;
   Acc<T> rr, rs_sum;
@@ -208,8 +223,14 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
 k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
          const int *__restrict__ comp, Scalars *sc, double *partials,
-         int first) {
+         int first, size_t pstride) {
   constexpr int N = V16<T>::N;
+  {
+    const size_t off = (size_t)blockIdx.y * nb * BV;
+    r += off; z += off;
+    sc += blockIdx.y;
+    partials += (size_t)blockIdx.y * pstride;
+  }
   Acc<T> rz, zsum;
   const size_t nv = (size_t)nb * BV / N;
   for (size_t vi = blockIdx.x * (size_t)blockDim.x + threadIdx.x; vi < nv;
@@ -230,7 +251,8 @@ k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
     const double old = sc->rz;
     sc->rz_old = old;
     sc->rz = tot[0];
-    const double beta = (first || old == 0.0) ? 0.0 : tot[0] / old;
+    const double beta = (first || sc->restart || old == 0.0) ? 0.0 : tot[0] / old;
+    sc->restart = 0;
     sc->beta = beta;
     sc->beta_f = (float)beta;
     sc->zsum = tot[1];
@@ -239,23 +261,99 @@ k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
   }
 }
 
-// Per-component sums of v over the unknowns (several components): lanes that
-// share a component are combined before one atomic per group.
+// Per-component sums of v over the unknowns (several components), exact and
+// independent of the order of the atomics, so that repeated and batched
+// solves are bit-identical.  The workspace of one right-hand side (cstride
+// words) holds the FP64 sums [ncomp], 128-bit accumulators [ncomp][2] and the
+// bits of max |v|.  k_absmax takes max |v|; k_comp_sum scales every value by
+// the same power of two, 2^k with max |v| 2^k < 2^96, truncates it to an
+// integer and adds it to its component's 128-bit two's-complement
+// accumulator (two 64-bit words, the low word's carry-out counted by the
+// atomic that caused it); up to 2^31 values cannot overflow 2^127.
+// k_comp_finish turns the accumulators back into FP64.  Values below
+// 2^-95 max |v| are lost to truncation, far under FP64 rounding of the sum.
+__device__ __forceinline__ int sum_scale_exp(unsigned long long maxbits) {
+  return 95 - ilogb(__longlong_as_double((long long)maxbits));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT)
-k_comp_sum(const T *__restrict__ v, const int *__restrict__ comp, double *csum) {
+k_absmax(const T *__restrict__ v, const int *__restrict__ comp, double *ws, int cstride,
+         int ncomp) {
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  v += (size_t)blockIdx.y * gridDim.x * BV;
+  ws += (size_t)blockIdx.y * cstride;
+  unsigned long long m =
+      comp[s] >= 0 ? (unsigned long long)__double_as_longlong(fabs((double)v[s])) : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long q = __shfl_xor_sync(0xffffffffu, m, o);
+    m = q > m ? q : m;
+  }
+  __shared__ unsigned long long wm[NT / 32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < NT / 32; ++w) m = wm[w] > m ? wm[w] : m;
+    // non-negative doubles order like their bit patterns
+    if (m) atomicMax(reinterpret_cast<unsigned long long *>(ws + 3 * ncomp), m);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT)
+k_comp_sum(const T *__restrict__ v, const int *__restrict__ comp, double *ws, int cstride,
+           int ncomp) {
+  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  v += (size_t)blockIdx.y * gridDim.x * BV;
+  ws += (size_t)blockIdx.y * cstride;
+  unsigned long long *acc = reinterpret_cast<unsigned long long *>(ws + ncomp);
+  const unsigned long long mb = *reinterpret_cast<const unsigned long long *>(ws + 3 * ncomp);
   const int c = comp[s];
   const unsigned grp = __match_any_sync(0xffffffffu, c);
-  double x = c >= 0 ? (double)v[s] : 0.0;
-  double tot = 0.0;
+  unsigned long long lo = 0ull, hi = 0ull;
+  if (c >= 0 && mb) {
+    const double x = (double)v[s];
+    const double ax = scalbn(fabs(x), sum_scale_exp(mb));  // < 2^96, exact
+    const double hd = floor(ax * 0x1p-64);                 // exact
+    lo = (unsigned long long)(ax - hd * 0x1p64);           // exact difference, truncated
+    hi = (unsigned long long)hd;
+    if (x < 0.0) {  // two's complement negation of (hi, lo)
+      lo = ~lo + 1ull;
+      hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+  }
+  unsigned long long tl = 0ull, th = 0ull;
   unsigned m = grp;
-  while (m) {  // sum within the group: walk the set bits (at most 32)
-    int src = __ffs(m) - 1;
-    tot += __shfl_sync(grp, x, src);
+  while (m) {  // exact sum within the group: walk the set bits (at most 32)
+    const int src = __ffs(m) - 1;
+    const unsigned long long ol = __shfl_sync(grp, lo, src), oh = __shfl_sync(grp, hi, src);
+    const unsigned long long nl = tl + ol;
+    th += oh + (nl < tl ? 1ull : 0ull);
+    tl = nl;
     m &= m - 1;
   }
-  if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&csum[c], tot);
+  if (c >= 0 && mb && (int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+    const unsigned long long old = atomicAdd(&acc[2 * c], tl);
+    atomicAdd(&acc[2 * c + 1], th + (old + tl < old ? 1ull : 0ull));
+  }
+}
+
+__global__ void k_comp_finish(double *ws, int cstride, int ncomp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  ws += (size_t)blockIdx.y * cstride;
+  if (c >= ncomp) return;
+  const unsigned long long mb = *reinterpret_cast<const unsigned long long *>(ws + 3 * ncomp);
+  const unsigned long long *acc = reinterpret_cast<const unsigned long long *>(ws + ncomp);
+  unsigned long long lo = acc[2 * c], hi = acc[2 * c + 1];
+  if (!mb) { ws[c] = 0.0; return; }
+  const bool neg = (long long)hi < 0;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  const double mag = (double)hi * 0x1p64 + (double)lo;
+  ws[c] = scalbn(neg ? -mag : mag, -sum_scale_exp(mb));
 }
 
 // p = (z - mean_c(z)) + beta p on the unknowns.  One component: the mean is
@@ -264,9 +362,15 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
 k_pupdate(T *__restrict__ p, const T *__restrict__ z,
           const int *__restrict__ comp, const Scalars *sc,
-          const double *__restrict__ csum, const int *__restrict__ csize) {
+          const double *__restrict__ csum, const int *__restrict__ csize, int cstride) {
   constexpr int N = V16<T>::N;
   const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
+  {
+    const size_t off = (size_t)blockIdx.y * gridDim.x * BV;
+    p += off; z += off;
+    sc += blockIdx.y;
+    if (csum) csum += (size_t)blockIdx.y * cstride;
+  }
   T mean1, beta;
   if constexpr (sizeof(T) == 4) { mean1 = sc->zmean_f; beta = sc->beta_f; }
   else { mean1 = sc->zmean; beta = sc->beta; }
@@ -288,8 +392,11 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
 k_sub_mean(T *__restrict__ v, const int *__restrict__ comp, const Scalars *sc,
            int aux_slot, const double *__restrict__ csum,
-           const int *__restrict__ csize) {
+           const int *__restrict__ csize, int cstride) {
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  v += (size_t)blockIdx.y * gridDim.x * BV;
+  sc += blockIdx.y;
+  if (csum) csum += (size_t)blockIdx.y * cstride;
   const int c = comp[s];
   if (c < 0) { v[s] = (T)0; return; }
   const T mean = csum ? (T)(csum[c] / (double)csize[c])
@@ -301,7 +408,15 @@ k_sub_mean(T *__restrict__ v, const int *__restrict__ comp, const Scalars *sc,
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_dot(int nb, const T *__restrict__ x, const T *__restrict__ y,
-      const int *__restrict__ comp, Scalars *sc, double *partials, int slot) {
+      const int *__restrict__ comp, Scalars *sc, double *partials, int slot,
+      size_t pstride) {
+  {
+    const size_t off = (size_t)blockIdx.y * nb * BV;
+    x += off;
+    if (y) y += off;
+    sc += blockIdx.y;
+    partials += (size_t)blockIdx.y * pstride;
+  }
   Acc<T> acc;
   for (int bk = blockIdx.x; bk < nb; bk += gridDim.x) {
     const size_t s = (size_t)bk * BV + threadIdx.x;
@@ -324,6 +439,8 @@ k_rhs(Grid g, const double *__restrict__ gx, const double *__restrict__ a,
   load_nbr(g, bk, sn);
   __syncthreads();
   const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  a += (size_t)blockIdx.y * 3 * ((size_t)g.NX * g.NY * g.NZ);
+  b += (size_t)blockIdx.y * S;
   const int4 bc = g.bco[bk];
   const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
   const int i = bc.x * 8 + lx, j = bc.y * 8 + ly, k = bc.z * 8 + lz;
@@ -362,6 +479,8 @@ template <typename T>
 __global__ void k_scatter(Grid g, const T *__restrict__ x,
                           const int *__restrict__ comp, double *__restrict__ psi) {
   const size_t NN = (size_t)g.NX * g.NY * g.NZ;
+  x += (size_t)blockIdx.y * g.nb * BV;
+  psi += (size_t)blockIdx.y * NN;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < NN;
        n += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(n % g.NX), j = (int)((n / g.NX) % g.NY),
@@ -789,60 +908,72 @@ void launch_scaled_copy(int nb, const double *src, double f, double *dst,
 }
 template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
-                      T *q, Scalars *sc, double *partials, cudaStream_t st) {
+                      T *q, Scalars *sc, double *partials, cudaStream_t st, int nk,
+                      size_t pstride) {
   if (!g.nb) return;
-  k_apply_dot<T><<<g.nb, RT, 0, st>>>(g, gx, diag, p, q, partials);
+  k_apply_dot<T><<<dim3(g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
-                      cudaStream_t st) {
+                      cudaStream_t st, int nk, size_t pstride) {
   if (n <= 0) return;
   const int blocks = std::min(152, (n + NT - 1) / NT);
-  k_finish_pq<<<blocks, NT, 0, st>>>(partials, n, scratch, sc);
+  k_finish_pq<<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, pstride);
 }
 template <typename T>
 void launch_update_xr(int nb, T *x, T *r, const T *p, const T *q, Scalars *sc,
-                      double *partials, cudaStream_t st) {
-  if (nb) k_update_xr<T><<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, x, r, p, q, sc, partials);
+                      double *partials, cudaStream_t st, int nk, size_t pstride) {
+  if (nb)
+    k_update_xr<T><<<dim3(std::min(nb, RED_GRID), nk), NT, 0, st>>>(nb, x, r, p, q, sc,
+                                                                    partials, pstride);
 }
 template <typename T>
 void launch_dot_rz(int nb, const T *r, const T *z, const int *comp,
-                   Scalars *sc, double *partials, int first, cudaStream_t st) {
-  if (nb) k_dot_rz<T><<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, z, comp, sc, partials, first);
+                   Scalars *sc, double *partials, int first, cudaStream_t st, int nk,
+                   size_t pstride) {
+  if (nb)
+    k_dot_rz<T><<<dim3(std::min(nb, RED_GRID), nk), NT, 0, st>>>(nb, r, z, comp, sc, partials,
+                                                                 first, pstride);
 }
 template <typename T>
-void launch_comp_sum(int nb, const T *v, const int *comp, double *csum,
-                     cudaStream_t st) {
-  if (nb) k_comp_sum<T><<<nb, NT, 0, st>>>(v, comp, csum);
+void launch_comp_sum(int nb, const T *v, const int *comp, double *ws, int ncomp,
+                     int cstride, cudaStream_t st, int nk) {
+  cudaMemsetAsync(ws, 0, (size_t)nk * cstride * sizeof(double), st);
+  if (!nb) return;
+  k_absmax<T><<<dim3(nb, nk), NT, 0, st>>>(v, comp, ws, cstride, ncomp);
+  k_comp_sum<T><<<dim3(nb, nk), NT, 0, st>>>(v, comp, ws, cstride, ncomp);
+  k_comp_finish<<<dim3((ncomp + 255) / 256, nk), 256, 0, st>>>(ws, cstride, ncomp);
 }
 template <typename T>
 void launch_pupdate(int nb, T *p, const T *z, const int *comp,
                     const Scalars *sc, const double *csum, const int *csize,
-                    double, cudaStream_t st) {
-  if (nb) k_pupdate<T><<<nb, NT / V16<T>::N, 0, st>>>(p, z, comp, sc, csum, csize);
+                    double, cudaStream_t st, int nk, int cstride) {
+  if (nb) k_pupdate<T><<<dim3(nb, nk), NT / V16<T>::N, 0, st>>>(p, z, comp, sc, csum, csize, cstride);
 }
 template <typename T>
 void launch_sub_mean(int nb, T *v, const int *comp, const Scalars *sc,
                      int aux_slot, const double *csum, const int *csize,
-                     double, cudaStream_t st) {
-  if (nb) k_sub_mean<T><<<nb, NT, 0, st>>>(v, comp, sc, aux_slot, csum, csize);
+                     double, cudaStream_t st, int nk, int cstride) {
+  if (nb) k_sub_mean<T><<<dim3(nb, nk), NT, 0, st>>>(v, comp, sc, aux_slot, csum, csize, cstride);
 }
 template <typename T>
 void launch_dot(int nb, const T *x, const T *y, const int *comp, Scalars *sc,
-                double *partials, int slot, cudaStream_t st) {
-  if (nb) k_dot<T><<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, x, y, comp, sc, partials, slot);
+                double *partials, int slot, cudaStream_t st, int nk, size_t pstride) {
+  if (nb)
+    k_dot<T><<<dim3(std::min(nb, RED_GRID), nk), NT, 0, st>>>(nb, x, y, comp, sc, partials,
+                                                              slot, pstride);
 }
 void launch_rhs(const Grid &g, const double *gx, const double *a, double *b,
-                int *status, cudaStream_t st) {
-  if (g.nb) k_rhs<<<g.nb, NT, 0, st>>>(g, gx, a, b, status);
+                int *status, cudaStream_t st, int nk) {
+  if (g.nb) k_rhs<<<dim3(g.nb, nk), NT, 0, st>>>(g, gx, a, b, status);
 }
 template <typename T>
 void launch_scatter(const Grid &g, const T *x, const int *comp, double *psi,
-                    cudaStream_t st) {
+                    cudaStream_t st, int nk) {
   size_t NN = (size_t)g.NX * g.NY * g.NZ;
   size_t blocks = (NN + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks == 0) blocks = 1;
-  k_scatter<T><<<(int)blocks, 256, 0, st>>>(g, x, comp, psi);
+  k_scatter<T><<<dim3((int)blocks, nk), 256, 0, st>>>(g, x, comp, psi);
 }
 void launch_gather(const Grid &g, const double *psi, const int *comp, double *x,
                    cudaStream_t st) {
@@ -891,23 +1022,27 @@ void launch_energy_grads(const Grid &g, const double *gx, const unsigned char *m
 #define INST_K(T)                                                              \
   template void launch_apply_dot<T>(const Grid &, const T *, const T *,        \
                                     const T *, T *, Scalars *, double *,       \
-                                    cudaStream_t);                             \
+                                    cudaStream_t, int, size_t);                \
   template void launch_update_xr<T>(int, T *, T *, const T *, const T *,       \
-                                    Scalars *, double *, cudaStream_t);        \
+                                    Scalars *, double *, cudaStream_t, int,    \
+                                    size_t);                                   \
   template void launch_dot_rz<T>(int, const T *, const T *, const int *,       \
-                                 Scalars *, double *, int, cudaStream_t);      \
-  template void launch_comp_sum<T>(int, const T *, const int *, double *,      \
-                                   cudaStream_t);                              \
+                                 Scalars *, double *, int, cudaStream_t, int,  \
+                                 size_t);                                      \
+  template void launch_comp_sum<T>(int, const T *, const int *, double *, int, \
+                                   int, cudaStream_t, int);                    \
   template void launch_pupdate<T>(int, T *, const T *, const int *,            \
                                   const Scalars *, const double *,             \
-                                  const int *, double, cudaStream_t);          \
+                                  const int *, double, cudaStream_t, int,      \
+                                  int);                                        \
   template void launch_sub_mean<T>(int, T *, const int *, const Scalars *,     \
                                    int, const double *, const int *, double,   \
-                                   cudaStream_t);                              \
+                                   cudaStream_t, int, int);                    \
   template void launch_dot<T>(int, const T *, const T *, const int *,          \
-                              Scalars *, double *, int, cudaStream_t);         \
+                              Scalars *, double *, int, cudaStream_t, int,     \
+                              size_t);                                         \
   template void launch_scatter<T>(const Grid &, const T *, const int *,        \
-                                  double *, cudaStream_t);
+                                  double *, cudaStream_t, int);
 template int apply_dot_partials<double>(int);
 template int apply_dot_partials<float>(int);
 INST_K(double)
