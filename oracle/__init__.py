@@ -21,7 +21,10 @@ function cites the paper passage it follows:
 * ``energy`` / ``div`` / ``energy_gradient`` -- the adjoint gradient of
   J = mean over conducting voxels of |E|^2 with respect to a and sigma: one
   extra Eq. 3 solve A lambda = G^T dJ/du (same operator), then
-  dJ/da = dJ/du - M G lambda and dJ/dsigma from dJ/dg = -(G lambda) u (R1).
+  dJ/da = dJ/du - M G lambda and dJ/dsigma from dJ/dg = -(G lambda) u (R1);
+* ``nearest_rank`` / ``percentile`` -- step 6 of the pipeline (Sec. II-A,
+  Sec. III-E): the 99th percentile of the voxel-averaged |E| per tissue and
+  over the whole body, nearest-rank (reading R14).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 (closed forms, brute force on tiny grids, invariants); none is unpinned.
@@ -91,6 +94,11 @@ def lib():
             L.orc_div.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
             L.orc_energy_grads.argtypes = [dp, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_double, dp, dp]
+            L.orc_nearest_rank.argtypes = [ctypes.c_double, i64]
+            L.orc_nearest_rank.restype = i64
+            L.orc_percentile.argtypes = [dp, dp, ctypes.POINTER(ctypes.c_int32), i64,
+                                         ctypes.c_int, ctypes.c_double, dp, lp]
+            L.orc_percentile.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -290,3 +298,27 @@ def energy_gradient(sigma: np.ndarray, h: float, a: np.ndarray, omega: float,
                            _d(dJda), _d(dJds))
     return {"J": J, "dJda": dJda, "dJdsigma": dJds, "psi": psi, "lam": lam_full,
             "info": info, "info_adj": info_adj}
+
+
+def nearest_rank(p: float, n: int) -> int:
+    """Least integer k >= p * n (exact), k >= 1; 0 when n = 0 (R14)."""
+    return int(lib().orc_nearest_rank(float(p), int(n)))
+
+
+def percentile(sigma: np.ndarray, E: np.ndarray, labels: np.ndarray, n_labels: int,
+               p: float = 0.99):
+    """Nearest-rank p-quantile of |E| over the conducting voxels of each
+    tissue label 0..n_labels-1 and, last, over the whole body (step 6 of
+    Sec. II-A, Sec. III-E, R14).  Returns (values, counts), each of length
+    n_labels + 1; a group without voxels gets NaN and count 0."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    assert sigma.shape == E.shape == lab.shape
+    out = np.zeros(n_labels + 1)
+    cnt = np.zeros(n_labels + 1, dtype=np.int64)
+    rc = lib().orc_percentile(_d(sigma), _d(E), lab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              sigma.size, int(n_labels), float(p), _d(out), _l(cnt))
+    if rc != 0:
+        raise MemoryError("oracle percentile")
+    return out, cnt

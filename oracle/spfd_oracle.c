@@ -479,3 +479,55 @@ void orc_energy_grads(const double *sigma, const double *a, const double *psi,
         dJdsigma[v] = 0.25 * h * s;
       }
 }
+
+/* ---------------------------------------------------------------------------
+ * Step 6 of the pipeline (Sec. II-A, step 6; Sec. III-E): the 99th
+ * percentile of the voxel-averaged |E|, taken to discard unphysical field
+ * peaks.  Reading R14: the p-quantile of a set of n values is the nearest-
+ * rank value, the k-th smallest with k the least integer >= p * n (exact
+ * arithmetic, k >= 1), taken per tissue label over the conducting voxels
+ * (sigma > 0) that carry the label, plus once over every conducting voxel
+ * (the whole body).  A library sort gives the order statistics.
+ * ------------------------------------------------------------------------- */
+
+/* Least integer k >= p * n for p in (0, 1], computed exactly: p is the
+ * binary fraction m / 2^s with m a 53-bit integer. */
+i64 orc_nearest_rank(double p, i64 n) {
+  if (n <= 0) return 0;
+  int e;
+  double f = frexp(p, &e);                 /* p = f 2^e, f in [0.5, 1) */
+  uint64_t m = (uint64_t)ldexp(f, 53);     /* exact */
+  int s = 53 - e;                          /* p = m / 2^s */
+  unsigned __int128 x = (unsigned __int128)m * (uint64_t)n;
+  i64 k;
+  if (s >= 127) k = 1;
+  else k = (i64)((x + (((unsigned __int128)1 << s) - 1)) >> s);
+  return k < 1 ? 1 : k;
+}
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* out[t] / count[t] for labels t = 0..nlab-1, out[nlab] / count[nlab] for
+ * the whole body; groups without a voxel get NaN and 0.  Returns 0, or -1 if
+ * memory ran out. */
+int orc_percentile(const double *sigma, const double *E, const int *labels, i64 nvox,
+                   int nlab, double p, double *out, i64 *count) {
+  double *buf = (double *)malloc((size_t)(nvox > 0 ? nvox : 1) * sizeof(double));
+  if (!buf) return -1;
+  for (int t = 0; t <= nlab; t++) {
+    i64 n = 0;
+    for (i64 v = 0; v < nvox; v++) {
+      if (!(sigma[v] > 0.0)) continue;
+      if (t == nlab || labels[v] == t) buf[n++] = E[v];
+    }
+    count[t] = n;
+    if (n == 0) { out[t] = NAN; continue; }
+    qsort(buf, (size_t)n, sizeof(double), cmp_double);
+    out[t] = buf[orc_nearest_rank(p, n) - 1];
+  }
+  free(buf);
+  return 0;
+}
