@@ -20,8 +20,8 @@
  *           past the last node along d are ignored.
  *   h       voxel edge length in m; omega angular frequency in rad/s.
  *
- * Method choices the paper leaves open (Sec. II: "M_k ... needs to be
- * determined"; Sec. III-A: only conducting voxels are unknowns):
+ * Method choices the paper leaves open (Sec. II does not fix how M_k is
+ * formed from the voxels; Sec. III-A keeps only conducting voxels):
  *   - edge conductance g_e = h * (sum of sigma of the <= 4 voxels around the
  *     edge) / 4, voxels outside the grid counting as air;
  *   - a node is an unknown iff an incident edge has g_e > 0; other nodes of
@@ -176,6 +176,30 @@ spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host, double tol,
  * Asynchronous on the context's stream. */
 spfd_status spfd_efield(spfd_ctx *ctx, const double *a_dev,
                         const double *psi_dev, double omega, double *E_dev);
+
+/* Step 6 of the pipeline (Sec. II-A, step 6; Sec. III-E): the p-quantile
+ * (p = 0.99 for the 99th percentile) of the voxel-averaged |E| per tissue and
+ * over the whole body.  The quantile of n values is the nearest-rank value,
+ * the k-th smallest with k the least integer >= p * n in exact arithmetic
+ * (p read as its binary fraction; k >= 1), so no rounding decides the rank
+ * and the result is one of the inputs, bit for bit.
+ *   E_dev        [nz][ny][nx] FP64 |E| (e.g. from spfd_efield), device; only
+ *                the context's conducting voxels (sigma > 0) are read, and
+ *                there it must be finite and >= 0 (else SPFD_EINVAL).
+ *   labels_dev   [nz][ny][nx] int32 tissue labels, device; a conducting
+ *                voxel with label t in 0..n_labels-1 counts for tissue t, any
+ *                other label for the whole body only.  May be NULL when
+ *                n_labels = 0.
+ *   n_labels     0..2048.
+ *   p            in (0, 1].
+ *   values_host  host output of n_labels + 1 entries: tissues 0..n_labels-1,
+ *                then the whole body (NaN for a group without voxels).
+ *   counts_host  optional host output of n_labels + 1 voxel counts.
+ * Allocates scratch on first use (8 bytes per conducting voxel twice, 32 KB
+ * per group) and keeps it; synchronises the stream. */
+spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev, const int32_t *labels_dev,
+                            int n_labels, double p, double *values_host,
+                            int64_t *counts_host);
 
 /* Report of the context (sizes, last solve); does not synchronise. */
 spfd_status spfd_get_info(const spfd_ctx *ctx, spfd_info *info);

@@ -30,7 +30,7 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
            "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
-           "spfd_energy_grad", "spfd_solve_batch")
+           "spfd_energy_grad", "spfd_solve_batch", "spfd_percentile")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -110,6 +110,9 @@ def lib():
             L.spfd_energy_grad.argtypes = [vp, vp, vp, dp, dp, ctypes.POINTER(dp), vp, vp,
                                            ctypes.POINTER(SpfdInfo)]
             L.spfd_energy_grad.restype = ctypes.c_int
+            L.spfd_percentile.argtypes = [vp, vp, vp, ctypes.c_int, dp, ctypes.POINTER(dp),
+                                          ctypes.POINTER(ctypes.c_int64)]
+            L.spfd_percentile.restype = ctypes.c_int
             L.spfd_release_cached_memory.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
             L.spfd_release_cached_memory.restype = ctypes.c_int
             _lib = L
@@ -206,6 +209,17 @@ def spfd_energy_grad(ctx: int, a_ptr: int, psi_ptr: int, omega: float, tol: floa
                                        ctypes.c_void_p(dJds_ptr), ctypes.byref(info)),
                 allow=(SPFD_OK, SPFD_ENOTCONVERGED))
     return st, J.value, info
+
+
+def spfd_percentile(ctx: int, E_ptr: int, labels_ptr: int, n_labels: int, p: float):
+    """Nearest-rank p-quantile of |E| per tissue label and over the whole
+    body (step 6); returns (values, counts), lists of n_labels + 1."""
+    vals = (ctypes.c_double * (n_labels + 1))()
+    cnts = (ctypes.c_int64 * (n_labels + 1))()
+    _check(lib().spfd_percentile(ctypes.c_void_p(ctx), ctypes.c_void_p(E_ptr),
+                                 ctypes.c_void_p(labels_ptr), int(n_labels), float(p),
+                                 vals, cnts))
+    return list(vals), list(cnts)
 
 
 def spfd_release_cached_memory() -> int:
@@ -319,6 +333,25 @@ class Solver:
         st, J, info = spfd_energy_grad(self.ctx, a.data_ptr(), psi.data_ptr(), omega, tol,
                                        dJda.data_ptr(), dJds.data_ptr())
         return J, dJda, dJds, info.as_dict(), st
+
+    def percentile(self, E, labels=None, n_labels: int = 0, p: float = 0.99):
+        """Nearest-rank p-quantile of ``E`` (contiguous float64 CUDA, voxel
+        shape) over the conducting voxels of each label 0..n_labels-1 of
+        ``labels`` (contiguous int32 CUDA, voxel shape) and, last, over the
+        whole body.  Returns (values, counts), lists of n_labels + 1."""
+        import torch
+        nx, ny, nz = self.dims
+        if not (E.is_cuda and E.dtype == torch.float64 and E.is_contiguous()
+                and tuple(E.shape) == (nz, ny, nx)):
+            raise ValueError("E must be a contiguous float64 CUDA tensor (nz, ny, nx)")
+        lp = 0
+        if n_labels > 0:
+            if labels is None or not (labels.is_cuda and labels.dtype == torch.int32
+                                      and labels.is_contiguous()
+                                      and tuple(labels.shape) == (nz, ny, nx)):
+                raise ValueError("labels must be a contiguous int32 CUDA tensor (nz, ny, nx)")
+            lp = labels.data_ptr()
+        return spfd_percentile(self.ctx, E.data_ptr(), lp, n_labels, p)
 
     def info(self) -> dict:
         return spfd_get_info(self.ctx).as_dict()

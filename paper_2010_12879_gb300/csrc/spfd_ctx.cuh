@@ -148,6 +148,15 @@ struct spfd_ctx {
   // -G^T M a_cur; scratch of spfd_energy_grad (allocated on first use)
   const double *gJ_cur = nullptr;
   double *ev_stage = nullptr, *gj_stage = nullptr, *lam_stage = nullptr;
+  // scratch of spfd_percentile (allocated on first use, grown on demand):
+  // per-group counters, digit histograms, the key segments, the chunk table
+  // and its pinned host staging
+  unsigned long long *pct_small = nullptr, *pct_keys = nullptr;
+  unsigned *pct_hist = nullptr;
+  long long *pct_chunks = nullptr, *pct_hstage = nullptr;
+  int pct_gcap = 0, pct_chcap = 0;
+  long long pct_keycap = 0, pct_nc = 0;  // pct_nc: conducting voxels seen last call
+  size_t pct_hstage_n = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   spfd_info info{};
   // launch accounting and profiling
