@@ -201,6 +201,48 @@ spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev, const int32_t *l
                             int n_labels, double p, double *values_host,
                             int64_t *counts_host);
 
+/* Several bodies solved together by one launch of a captured CUDA graph.
+ *
+ * A group holds contexts built for different bodies (for example phantoms of
+ * different sizes) and solves Eq. 3 (Sec. II) on all of them at once.  The
+ * FP64 solve of each context (the same steps as spfd_solve) is captured as
+ * one branch of a single graph whose CG loop runs on the GPU: control
+ * kernels decide, between iterations, to check the true residual, restart or
+ * stop, through the graph's conditional nodes, so the host launches the
+ * graph once and synchronises once per group solve.  Each Psi equals what
+ * spfd_solve returns for that context, bit for bit, with the same iteration
+ * count.  The paper solves one body at a time (Sec. III); grouping is a
+ * throughput form of the same solve.
+ *
+ * spfd_group_create
+ *   ctxs    n distinct contexts (1..4096) on one device, each built with
+ *           opts.precision = SPFD_FP64 (else SPFD_EINVAL).  The group keeps
+ *           the pointers: destroy the group before any of its contexts.
+ *   stream  cudaStream_t the group launches on (NULL = legacy default
+ *           stream); work already queued on the contexts' streams runs
+ *           first.
+ * spfd_group_solve
+ *   a_devs    n device pointers, a_devs[i] laid out as in spfd_solve for
+ *             context i.
+ *   tol       relative residual target (> 0), or <= 0 for each context's
+ *             opts.tol; maxit is each context's opts.maxit.
+ *   psi_devs  n device outputs, laid out as in spfd_solve.
+ *   infos     optional array of n reports (ms_solve: the whole group).
+ *   The first call captures and instantiates the graph (milliseconds);
+ *   later calls only point its input and output nodes at the new arrays.  A
+ *   call also captures again after a context has reallocated its solve
+ *   buffers (e.g. a larger spfd_solve_batch).  Contexts must not be used on
+ *   other streams while a group solve runs.  Synchronises.  Returns
+ *   SPFD_ENOTCONVERGED (every Psi written) if any body missed tol and
+ *   SPFD_EINVAL if any a is non-finite on a conducting edge.
+ * spfd_group_destroy  releases the graph, streams and events; NULL is a
+ *   no-op. */
+typedef struct spfd_group spfd_group;
+spfd_status spfd_group_create(spfd_ctx *const *ctxs, int n, void *stream, spfd_group **out);
+spfd_status spfd_group_solve(spfd_group *group, const double *const *a_devs, double tol,
+                             double *const *psi_devs, spfd_info *infos);
+void spfd_group_destroy(spfd_group *group);
+
 /* Report of the context (sizes, last solve); does not synchronise. */
 spfd_status spfd_get_info(const spfd_ctx *ctx, spfd_info *info);
 

@@ -30,7 +30,8 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
            "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
-           "spfd_energy_grad", "spfd_solve_batch", "spfd_percentile")
+           "spfd_energy_grad", "spfd_solve_batch", "spfd_percentile",
+           "spfd_group_create", "spfd_group_solve", "spfd_group_destroy")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -113,6 +114,14 @@ def lib():
             L.spfd_percentile.argtypes = [vp, vp, vp, ctypes.c_int, dp, ctypes.POINTER(dp),
                                           ctypes.POINTER(ctypes.c_int64)]
             L.spfd_percentile.restype = ctypes.c_int
+            L.spfd_group_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp,
+                                            ctypes.POINTER(vp)]
+            L.spfd_group_create.restype = ctypes.c_int
+            L.spfd_group_solve.argtypes = [vp, ctypes.POINTER(vp), dp, ctypes.POINTER(vp),
+                                           ctypes.POINTER(SpfdInfo)]
+            L.spfd_group_solve.restype = ctypes.c_int
+            L.spfd_group_destroy.argtypes = [vp]
+            L.spfd_group_destroy.restype = None
             L.spfd_release_cached_memory.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
             L.spfd_release_cached_memory.restype = ctypes.c_int
             _lib = L
@@ -240,6 +249,74 @@ def spfd_residual_noalloc(sigma_ptr: int, a_ptr: int, psi_ptr: int, nx: int,
                                        ctypes.c_void_p(psi_ptr), nx, ny, nz, float(h),
                                        ctypes.c_void_p(stream), ctypes.byref(out)))
     return out.value
+
+
+def spfd_group_create(ctxs, stream: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    out = ctypes.c_void_p()
+    _check(lib().spfd_group_create(arr, len(ctxs), ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
+
+
+def spfd_group_solve(group: int, a_ptrs, tol: float, psi_ptrs):
+    """Returns (status, list of SpfdInfo)."""
+    n = len(a_ptrs)
+    a = (ctypes.c_void_p * n)(*a_ptrs)
+    p = (ctypes.c_void_p * n)(*psi_ptrs)
+    infos = (SpfdInfo * n)()
+    st = _check(lib().spfd_group_solve(ctypes.c_void_p(group), a, float(tol), p, infos),
+                allow=(SPFD_OK, SPFD_ENOTCONVERGED))
+    return st, list(infos)
+
+
+def spfd_group_destroy(group: int):
+    lib().spfd_group_destroy(ctypes.c_void_p(group))
+
+
+class Group:
+    """Several Solver contexts (bodies of different sizes) solved together
+    by one launch of a captured CUDA graph (``spfd_group_*`` in
+    ``include/spfd.h``).  Close the group before its solvers."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        dev = self.solvers[0].device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        with torch.cuda.device(dev):
+            self.handle = spfd_group_create([s.ctx for s in self.solvers],
+                                            self.stream.cuda_stream)
+
+    def solve(self, a_list, tol: float = 0.0, psi_list=None):
+        """Psi of every body; returns (list of psi, list of info dicts, status)."""
+        import torch
+        if len(a_list) != len(self.solvers):
+            raise ValueError("one source field per solver")
+        for S, a in zip(self.solvers, a_list):
+            S._check_edges(a)
+        if psi_list is None:
+            psi_list = [torch.empty(S.node_shape, dtype=torch.float64, device=a.device)
+                        for S, a in zip(self.solvers, a_list)]
+        st, infos = spfd_group_solve(self.handle, [a.data_ptr() for a in a_list], tol,
+                                     [p.data_ptr() for p in psi_list])
+        return psi_list, [i.as_dict() for i in infos], st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spfd_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Solver:

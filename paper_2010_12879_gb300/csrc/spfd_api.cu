@@ -203,7 +203,7 @@ template <> struct Prec<float> {
 // v -= per-component mean of v for nk right-hand sides (aux slot 0 of each
 // one's Scalars is scratch).  j0 selects the first right-hand side.
 template <typename T>
-static spfd_status project(spfd_ctx *c, T *v, int nk = 1, int j0 = 0) {
+spfd_status project(spfd_ctx *c, T *v, int nk, int j0) {
   Level &l0 = c->L[0];
   cudaStream_t st = c->stream;
   const bool f32 = sizeof(T) == 4;
@@ -236,7 +236,7 @@ static spfd_status project(spfd_ctx *c, T *v, int nk = 1, int j0 = 0) {
 // is fused into the first sweep, using sum(r) left in each right-hand side's
 // Scalars by the preceding x/r update.
 template <typename T>
-static T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk) {
+T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk) {
   Level &lv = c->L[l];
   cudaStream_t st = c->stream;
   const int nl = (int)c->L.size();
@@ -308,8 +308,8 @@ __global__ void k_batch_flags(Scalars *sc, int nk, int clear_rsum, int frozen, i
   if (frozen >= 0) sc[j].frozen = frozen;
   if (restart >= 0) sc[j].restart = restart;
 }
-static spfd_status batch_flags(spfd_ctx *c, int j0, int nk, int clear_rsum, int frozen,
-                               int restart) {
+spfd_status batch_flags(spfd_ctx *c, int j0, int nk, int clear_rsum, int frozen,
+                        int restart) {
   if (nk <= 0) return SPFD_OK;
   SPFD_LAUNCH(c, "flags", false, 1, 0, 0,
               (k_batch_flags<<<(nk + 127) / 128, 128, 0, c->stream>>>(c->sc + j0, nk, clear_rsum,
@@ -340,6 +340,34 @@ static spfd_status true_residual(spfd_ctx *c, const double *bb, double *rel, int
   return SPFD_OK;
 }
 
+// z = M r (V-cycle on the projected residual), r.z and beta, then
+// p = z + beta p, for the first nk right-hand sides; first = 1 on the first
+// iteration (beta = 0).
+template <typename T>
+spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
+  const int nb = c->L[0].g.nb;
+  const bool f32 = sizeof(T) == 4;
+  const double w = sizeof(T), S = (double)c->L[0].S * nk;
+  const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
+  const double *csum = c->ncomp > 1 ? c->csum : nullptr;
+  cudaStream_t st = c->stream;
+  T *z = vcycle<T>(c, 0, r, true, nk);
+  SPFD_LAUNCH(c, "dot_rz", f32, 1, (2 * w + 4) * S, 3 * S,
+              launch_dot_rz<T>(nb, r, z, c->comp, c->sc, c->partials, first, st, nk,
+                               c->pstride));
+  if (c->ncomp > 1)
+    SPFD_LAUNCH(c, "project", f32, 3, 2 * (w + 4) * S, 12 * S,
+                launch_comp_sum<T>(nb, z, c->comp, c->csum, c->ncomp, c->cstride, st, nk));
+  SPFD_LAUNCH(c, "pupdate", f32, 1, (3 * w + 4) * S, 3 * S,
+              launch_pupdate<T>(nb, p, z, c->comp, c->sc, csum, c->csize, inv, st, nk,
+                                c->cstride));
+  return launch_check("V-cycle");
+}
+template spfd_status precondition_step<double>(spfd_ctx *, double *, double *, int, int);
+template spfd_status precondition_step<float>(spfd_ctx *, float *, float *, int, int);
+template spfd_status project<double>(spfd_ctx *, double *, int, int);
+template double *vcycle<double>(spfd_ctx *, int, double *, bool, int);
+
 struct PcgResult {
   int iters = 0;
   bool conv = false;
@@ -368,8 +396,6 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
   const size_t S0 = l0.S;
   const bool f32 = sizeof(T) == 4;
   const double w = sizeof(T);
-  const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
-  const double *csum = c->ncomp > 1 ? c->csum : nullptr;
   std::vector<int> done(nk, 0);
   auto active_end = [&]() {
     int e = 0;
@@ -389,18 +415,7 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
   }
   int na = active_end();
   auto precondition = [&](int first) -> spfd_status {
-    const double S = (double)S0 * na;
-    T *z = vcycle<T>(c, 0, r, true, na);
-    SPFD_LAUNCH(c, "dot_rz", f32, 1, (2 * w + 4) * S, 3 * S,
-                launch_dot_rz<T>(nb, r, z, c->comp, c->sc, c->partials, first, st, na,
-                                 c->pstride));
-    if (c->ncomp > 1)
-      SPFD_LAUNCH(c, "project", f32, 3, 2 * (w + 4) * S, 12 * S,
-                  launch_comp_sum<T>(nb, z, c->comp, c->csum, c->ncomp, c->cstride, st, na));
-    SPFD_LAUNCH(c, "pupdate", f32, 1, (3 * w + 4) * S, 3 * S,
-                launch_pupdate<T>(nb, p, z, c->comp, c->sc, csum, c->csize, inv, st, na,
-                                  c->cstride));
-    return launch_check("V-cycle");
+    return precondition_step<T>(c, r, p, first, na);
   };
   if (na == 0) return SPFD_OK;
   TRY(precondition(1));
@@ -606,6 +621,7 @@ static spfd_status ensure_batch(spfd_ctx *c, int k) {
   TRY(sync_check(c, "batch scalars"));
   dfree(c, c->sc);
   c->sc = sc;
+  ++c->gen;  // solve buffers moved: captured graphs must be captured again
   c->hsc = hsc;
   c->kcap = k;
   return SPFD_OK;

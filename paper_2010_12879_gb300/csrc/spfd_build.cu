@@ -256,6 +256,15 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
       }
     }
   }
+  // diagnostics: SPFD_DUMP_COARSEST=<path> writes m (int32) and the
+  // assembled coarsest matrix (m x m FP64, row-major) before regularisation
+  if (const char *dump = getenv("SPFD_DUMP_COARSEST")) {
+    if (FILE *f = fopen(dump, "wb")) {
+      fwrite(&m, sizeof(int), 1, f);
+      fwrite(A.data(), sizeof(double), (size_t)m * m, f);
+      fclose(f);
+    }
+  }
   // connected components of the coarsest graph
   std::vector<int> cc(m, -1), queue;
   int nc = 0;
@@ -285,11 +294,20 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
   // The coarsest Galerkin operator is numerically singular beyond the
   // component constants: coarse basis functions at the conducting boundary
   // can be nearly dependent (on the 2 mm body, 46 of 481 eigenvalues lie
-  // below 1e-10 of the largest).  Any inverse is rounding noise along those
+  // below 1e-10 of the largest), and a few such "ghost" rows have diagonals
+  // near 1e-13 of the largest.  Any inverse is rounding noise along those
   // directions, and different elimination orders give different noise.  A
-  // relative diagonal shift of 1e-8 bounds that noise while changing the
-  // coarse solve of modes above 1e-5 of the spectrum by under 1e-3.
-  for (int a = 0; a < m; ++a) A[(size_t)a * m + a] *= 1.0 + 1e-8;
+  // shift of the whole diagonal by 1e-8 of the mean diagonal bounds the
+  // condition number near 1e9, so the unpivoted elimination below stays
+  // positive, while it changes the coarse solve of modes above 1e-5 of the
+  // spectrum by under 1e-3.  (A shift proportional to each row's own
+  // diagonal leaves the tiny ghost rows unregularised: on a 96x96x256 body
+  // the condition number stayed at 2e11 and elimination met a negative
+  // pivot.)
+  double dmean = 0.0;
+  for (int a = 0; a < m; ++a) dmean += hdiag[idx[a]];
+  dmean /= m;
+  for (int a = 0; a < m; ++a) A[(size_t)a * m + a] += 1e-8 * dmean;
   TRY(dalloc(c, &c->cidx, m));
   CU(cudaMemcpyAsync(c->cidx, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice,
                      c->stream));

@@ -137,6 +137,9 @@ struct spfd_ctx {
   // right-hand sides the per-RHS buffers hold (level vectors, Krylov
   // vectors, scalars, partials, component sums); grown by batched solves
   int kcap = 1;
+  // generation of the solve buffers: bumped whenever they are reallocated,
+  // so that graphs captured over them know to capture again
+  uint64_t gen = 0;
   // coarsest level
   int m = 0;
   int *cidx = nullptr;
@@ -256,6 +259,22 @@ void prof_push(spfd_ctx *c, int stat, cudaEvent_t a, cudaEvent_t b,
 spfd_status prof_flush(spfd_ctx *c);
 
 }  // namespace spfd
+
+// Solve steps shared by the host-driven solves (spfd_api.cu) and the
+// captured, device-driven ones (spfd_graph.cu).  All of them only enqueue
+// work on c->stream (no host synchronisation), so they can be captured.
+// v -= per-component mean of v for nk right-hand sides starting at j0.
+template <typename T>
+spfd_status project(spfd_ctx *c, T *v, int nk = 1, int j0 = 0);
+// V-cycle on level l for nk right-hand sides; returns the corrections.
+template <typename T>
+T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk);
+// z = M r, r.z, beta and p = z + beta p for the first nk right-hand sides.
+template <typename T>
+spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk);
+// Per-right-hand-side flags (clear_rsum: 1 clears the residual sums; frozen,
+// restart: >= 0 sets that flag) of the nk right-hand sides from j0.
+spfd_status batch_flags(spfd_ctx *c, int j0, int nk, int clear_rsum, int frozen, int restart);
 
 // Launch CALL (which starts NK kernels) on c->stream; with opts.profile the
 // launch is bracketed by CUDA events and credited to family NAME with its

@@ -123,7 +123,7 @@ def body_phantom(nx: int = 256, ny: int = 160, nz: int = 896, h: float = 2e-3,
         vk, vj, vi = np.unravel_index(idx, m.shape)
         pts = np.stack([(vi + 0.5) * h - ox, (vj + 0.5) * h - oy,
                         (vk + 0.5) * h], axis=1)
-        _, near = tree.query(pts, k=1)
+        _, near = tree.query(pts, k=1, workers=-1)
         labels.reshape(-1)[idx] = seed_label[near].astype(np.int16)
     sigma = np.where(labels >= 0, tissue_sigma[np.maximum(labels, 0)], 0.0)
     return Phantom(sigma.astype(np.float64), labels, h, (ox, oy, 0.0),
