@@ -527,9 +527,10 @@ def bench_group(spfd, torch, dev, stream, ph, sig, ad, K, W):
 def bench_batch(spfd, torch, dev, stream, ph, sig, nrhs, K, W):
     """Many source fields on one body (batched-source workload): nrhs loops
     at seeded positions (x, y in +-0.5 m, z in -0.6..-0.3 m) and random
-    orientations, made on the device.  One context; the solves of all fields
-    to TOL as one spfd_solve_batch call against nrhs spfd_solve calls, each
-    timed with CUDA events on the context's stream after W warm-up rounds."""
+    orientations, made on the device.  For each precision (plain FP64 and
+    the mixed form), one context solves all fields to TOL as one
+    spfd_solve_batch call and as nrhs spfd_solve calls, each timed with CUDA
+    events on the context's stream after W warm-up rounds."""
     import numpy as np
 
     from spfd_inputs import random_loops
@@ -540,52 +541,58 @@ def bench_batch(spfd, torch, dev, stream, ph, sig, nrhs, K, W):
     for j, (c, n) in enumerate(loops):
         loop_potential_t(ph.dims, ph.h, ph.origin, center=c, normal=n, device=dev, out=A[j])
     psi = torch.empty((nrhs,) + nshape, dtype=torch.float64, device=dev)
-    S = spfd.Solver(sig, ph.h, stream=stream)
 
-    def batched():
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        e[0].record(stream)
-        _, infos, st = S.solve_batch(A, TOL, psi)
-        e[1].record(stream)
-        torch.cuda.synchronize(dev)
-        assert st == spfd.SPFD_OK, spfd.spfd_last_error()
-        return e[0].elapsed_time(e[1]), infos
+    def run(precision):
+        S = spfd.Solver(sig, ph.h, stream=stream, precision=precision)
 
-    def sequential():
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        infos = []
-        e[0].record(stream)
-        for j in range(nrhs):
-            _, info, st = S.solve(A[j], TOL, psi[j])
+        def batched():
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            _, infos, st = S.solve_batch(A, TOL, psi)
+            e[1].record(stream)
+            torch.cuda.synchronize(dev)
             assert st == spfd.SPFD_OK, spfd.spfd_last_error()
-            infos.append(info)
-        e[1].record(stream)
-        torch.cuda.synchronize(dev)
-        return e[0].elapsed_time(e[1]), infos
+            return e[0].elapsed_time(e[1]), infos
 
-    out = {}
-    for name, fn in (("batched", batched), ("sequential", sequential)):
-        for _ in range(W):
-            fn()
-        rec = [fn() for _ in range(K)]
-        ms = statistics.mean(r[0] for r in rec)
-        infos = rec[-1][1]
-        it = [i["iters"] for i in infos]
-        out[name] = {"ms": round(ms, 3), "solves_per_s": round(nrhs / (ms * 1e-3), 2),
-                     "iters_mean": round(statistics.mean(it), 2), "iters_max": max(it),
-                     "launches": int(sum(i["launches"] for i in infos)) if name == "sequential"
-                     else int(infos[0]["launches"]),
-                     "max_rel_res_true": max(i["rel_res_true"] for i in infos)}
-    bytes_dev = S.info()["bytes_device"]
-    S.close()
+        def sequential():
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            infos = []
+            e[0].record(stream)
+            for j in range(nrhs):
+                _, info, st = S.solve(A[j], TOL, psi[j])
+                assert st == spfd.SPFD_OK, spfd.spfd_last_error()
+                infos.append(info)
+            e[1].record(stream)
+            torch.cuda.synchronize(dev)
+            return e[0].elapsed_time(e[1]), infos
+
+        out = {}
+        for name, fn in (("batched", batched), ("sequential", sequential)):
+            for _ in range(W):
+                fn()
+            rec = [fn() for _ in range(K)]
+            ms = statistics.mean(r[0] for r in rec)
+            infos = rec[-1][1]
+            it = [i["iters"] for i in infos]
+            out[name] = {"ms": round(ms, 3), "solves_per_s": round(nrhs / (ms * 1e-3), 2),
+                         "iters_mean": round(statistics.mean(it), 2), "iters_max": max(it),
+                         "launches": int(sum(i["launches"] for i in infos)) if name == "sequential"
+                         else int(infos[0]["launches"]),
+                         "max_rel_res_true": max(i["rel_res_true"] for i in infos)}
+        out["context_bytes_device"] = S.info()["bytes_device"]
+        out["speedup_batched_vs_sequential"] = round(out["sequential"]["ms"] / out["batched"]["ms"], 3)
+        S.close()
+        return out
+
+    fp64 = run(spfd.SPFD_FP64)
+    mixed = run(spfd.SPFD_MIXED)
     del A, psi
     return {"workload": f"{nrhs} loop sources (R=0.3 m, I=1000 A) at seeded positions x,y in "
                         "+-0.5 m, z in -0.6..-0.3 m, random orientations, on the "
                         "256x160x896 body, h=2 mm",
-            "nrhs": nrhs, "tol": TOL, "precision": "fp64", "steps": K, "warmup": W,
-            "context_bytes_device": bytes_dev,
-            "speedup_batched_vs_sequential": round(out["sequential"]["ms"] / out["batched"]["ms"], 3),
-            **out}
+            "nrhs": nrhs, "tol": TOL, "steps": K, "warmup": W,
+            "fp64": fp64, "mixed": mixed,
+            "mixed_batched_vs_fp64_batched": round(fp64["batched"]["ms"] / mixed["batched"]["ms"], 3)}
 
 
 def cpu_baseline(ph, a, iters=30, record=None):

@@ -155,8 +155,11 @@ spfd_status spfd_solve(spfd_ctx *ctx, const double *a_dev, double tol,
  * decision, so each Psi is the one spfd_solve returns for it alone.  The
  * context grows its per-right-hand-side buffers on the first call with a
  * larger nrhs (about 10 FP64 vectors of the finest level per right-hand
- * side) and keeps them.  With SPFD_MIXED the right-hand sides are solved one
- * after the other.  Returns SPFD_ENOTCONVERGED (every Psi written) if any
+ * side; with SPFD_MIXED also their FP32 copies) and keeps them.  With
+ * SPFD_MIXED each right-hand side keeps its own FP64 refinement (scale,
+ * inner target, stopping) while the FP32 inner CG covers all of them in
+ * shared launches; each Psi again equals its spfd_solve result.  Returns
+ * SPFD_ENOTCONVERGED (every Psi written) if any
  * right-hand side missed tol; a non-finite a on a conducting edge of any of
  * them gives SPFD_EINVAL. */
 spfd_status spfd_solve_batch(spfd_ctx *ctx, int nrhs, const double *a_dev, double tol,

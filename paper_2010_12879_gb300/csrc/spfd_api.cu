@@ -388,8 +388,8 @@ struct PcgResult {
 // by x = 0 and takes no iteration.
 template <typename T>
 static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
-                       const T *opdiag, const double *bb, double tol, int maxit,
-                       PcgResult *res, int nk = 1) {
+                       const T *opdiag, const double *bb, const double *tolv,
+                       const int *maxitv, PcgResult *res, int nk = 1) {
   Level &l0 = c->L[0];
   cudaStream_t st = c->stream;
   const int nb = l0.g.nb;
@@ -425,7 +425,21 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
   // rounding floor is reached: stop there (not converged).
   std::vector<double> best_true(nk, INFINITY), min_rrel(nk, INFINITY), rel(nk, 0.0);
   std::vector<int> stall(nk, 0), check, broke;
-  for (int it = 1; it <= maxit && na > 0; ++it) {
+  int maxit_all = 0;
+  for (int j = 0; j < nk; ++j) maxit_all = std::max(maxit_all, maxitv[j]);
+  for (int it = 1; it <= maxit_all && na > 0; ++it) {
+    // a right-hand side past its own iteration cap stops here
+    bool capped = false;
+    for (int j = 0; j < na; ++j)
+      if (!done[j] && it > maxitv[j]) {
+        TRY(batch_flags(c, j, 1, 0, 1, -1));
+        done[j] = 2;
+        capped = true;
+      }
+    if (capped) {
+      na = active_end();
+      if (na == 0) break;
+    }
     const double S = (double)S0 * na;
     SPFD_LAUNCH(c, "apply_dot", f32, 1, (f32 ? 5 : 6) * w * S, (f32 ? 20 : 15) * S,
                 launch_apply_dot<T>(l0.g, opgx, opdiag, p, q, c->sc, c->partials, st, na,
@@ -442,6 +456,7 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
     for (int j = 0; j < na; ++j) {
       if (done[j]) continue;
       res[j].iters = it;
+      const double tol = tolv[j];
       const double rrel = std::sqrt(c->hsc[j].rr / bb[j]);
       if (!std::isfinite(rrel) || rrel > 1e8 * std::max(min_rrel[j], tol)) {
         broke.push_back(j);  // breakdown: report the current iterate, not converged
@@ -461,7 +476,7 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
     }
     for (int j : check) {
       res[j].rel_true = rel[j];
-      if (rel[j] <= tol) { res[j].conv = true; done[j] = 1; continue; }
+      if (rel[j] <= tolv[j]) { res[j].conv = true; done[j] = 1; continue; }
       if (rel[j] < 0.5 * best_true[j]) { best_true[j] = rel[j]; stall[j] = 0; }
       else if (++stall[j] >= 3) { done[j] = 1; continue; }
       // restart from the true residual (left in level 0's r by true_residual)
@@ -514,8 +529,10 @@ static spfd_status solve_fp64(spfd_ctx *c, double tol, spfd_info *out, int nk = 
   CU(cudaMemcpyAsync(c->rk, c->bk, S0 * nk * sizeof(double), cudaMemcpyDeviceToDevice,
                      c->stream));
   TRY(zero_rsum(c, 0, nk));  // b is projected
-  TRY(pcg<double>(c, c->xk, c->rk, c->pk, c->qk, l0.gx, l0.diag, bb.data(), tol,
-                  c->opts.maxit, res.data(), nk));
+  std::vector<double> tolv(nk, tol);
+  std::vector<int> maxitv(nk, c->opts.maxit);
+  TRY(pcg<double>(c, c->xk, c->rk, c->pk, c->qk, l0.gx, l0.diag, bb.data(), tolv.data(),
+                  maxitv.data(), res.data(), nk));
   TRY(project<double>(c, c->xk, nk));
   bool redo = false;
   for (int j = 0; j < nk; ++j) redo |= !res[j].conv;
@@ -533,61 +550,120 @@ static spfd_status solve_fp64(spfd_ctx *c, double tol, spfd_info *out, int nk = 
   return SPFD_OK;
 }
 
-// FP64 iterative refinement around the FP32 multigrid-preconditioned CG.
-static spfd_status solve_mixed(spfd_ctx *c, double tol, spfd_info *out) {
+// FP64 iterative refinement around the FP32 multigrid-preconditioned CG,
+// for nk right-hand sides at once.  Each right-hand side keeps its own outer
+// state (scale, inner target, stall count, iteration budget) and leaves the
+// loop on its own; the inner CG covers every one still refining in shared
+// launches, each with its own recurrence, so each result is the one the
+// right-hand side reaches alone.
+static spfd_status solve_mixed(spfd_ctx *c, double tol, spfd_info *out, int nk = 1) {
   Level &l0 = c->L[0];
   cudaStream_t st = c->stream;
   const size_t S0 = l0.S;
   const double S = (double)S0;
   const int nb = l0.g.nb;
-  double bb = 0.0;
-  TRY(prepare_rhs(c, c->a_cur, &bb));
-  CU(cudaMemsetAsync(c->xk, 0, S0 * sizeof(double), st));
-  out->iters = 0;
-  out->outer_iters = 0;
-  out->converged = 0;
-  out->rel_res_true = 0.0;
-  if (!(bb > 0.0)) {
-    out->converged = 1;
-    return SPFD_OK;
-  }
-  CU(cudaMemcpyAsync(c->rk, c->bk, S0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double nrm2 = bb, rel = 1.0, prev = INFINITY;
-  int total = 0, outer, stall = 0;
   const int max_outer = 30;
-  for (outer = 1; outer <= max_outer && total < c->opts.maxit; ++outer) {
-    const double nr = std::sqrt(nrm2);
-    // inner target: what is still missing for tol, but no tighter than what
-    // an FP32 solve reliably reaches
-    const double eta = std::min(0.5, std::max(0.5 * tol * std::sqrt(bb) / nr, 1e-4));
-    SPFD_LAUNCH(c, "convert", true, 1, 12 * S, S,
-                launch_scale_to_f32(nb, c->rk, 1.0 / nr, c->rk32, c->sc, c->partials, st));
-    CU(cudaMemsetAsync(c->dk32, 0, S0 * sizeof(float), st));
-    SPFD_LAUNCH(c, "project", true, 1, 12 * S, 2 * S,
-                launch_dot<float>(nb, c->rk32, c->rk32, c->comp, c->sc, c->partials, 3, st));
-    TRY(read_scalars(c));
-    const double bb_in = c->hsc->aux[3];
-    PcgResult in;
-    TRY(pcg<float>(c, c->dk32, c->rk32, c->pk32, c->qk32, l0.gx32, l0.diag32,
-                   &bb_in, eta, c->opts.maxit - total, &in));
-    total += in.iters;
-    SPFD_LAUNCH(c, "convert", false, 1, 20 * S, 2 * S,
-                launch_axpy_mixed(nb, c->xk, c->dk32, nr, st));
-    TRY(true_residual(c, &bb, &rel));
-    if (rel <= tol) { out->converged = 1; break; }
-    if (rel > 0.5 * prev) { if (++stall >= 2) break; } else stall = 0;
-    prev = std::min(prev, rel);
-    CU(cudaMemcpyAsync(c->rk, l0.r, S0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    TRY(project<double>(c, c->rk));
-    SPFD_LAUNCH(c, "project", false, 1, 20 * S, 2 * S,
-                launch_dot<double>(nb, c->rk, c->rk, c->comp, c->sc, c->partials, 3, st));
-    TRY(read_scalars(c));
-    nrm2 = c->hsc->aux[3];
+  std::vector<double> bb(nk, 0.0), nrm2(nk), rel(nk, 1.0), prev(nk, INFINITY), nr(nk);
+  std::vector<double> rel_all(nk, 0.0), bb_in(nk), eta(nk);
+  std::vector<int> total(nk, 0), stall(nk, 0), outer_of(nk, 0), active(nk, 0), cap(nk);
+  std::vector<PcgResult> in(nk);
+  TRY(prepare_rhs(c, c->a_cur, bb.data(), nk));
+  CU(cudaMemsetAsync(c->xk, 0, S0 * nk * sizeof(double), st));
+  for (int j = 0; j < nk; ++j) {
+    out[j].iters = 0;
+    out[j].outer_iters = 0;
+    out[j].converged = 0;
+    out[j].rel_res_true = 0.0;
+    if (!(bb[j] > 0.0)) out[j].converged = 1;
+    else active[j] = 1;
+    nrm2[j] = bb[j];
   }
-  TRY(project<double>(c, c->xk));
-  out->iters = total;
-  out->outer_iters = std::min(outer, max_outer);
-  out->rel_res_true = rel;
+  CU(cudaMemcpyAsync(c->rk, c->bk, S0 * nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  for (int outer = 1;; ++outer) {
+    // right-hand sides out of outer steps or inner iterations stop here
+    int na = 0;
+    for (int j = 0; j < nk; ++j) {
+      if (!active[j]) continue;
+      if (outer > max_outer || total[j] >= c->opts.maxit) {
+        active[j] = 0;
+        outer_of[j] = std::min(outer, max_outer);
+        continue;
+      }
+      na = j + 1;
+    }
+    if (na == 0) break;
+    CU(cudaMemsetAsync(c->dk32, 0, S0 * na * sizeof(float), st));
+    for (int j = 0; j < na; ++j) {
+      if (!active[j]) continue;
+      nr[j] = std::sqrt(nrm2[j]);
+      // inner target: what is still missing for tol, but no tighter than
+      // what an FP32 solve reliably reaches
+      eta[j] = std::min(0.5, std::max(0.5 * tol * std::sqrt(bb[j]) / nr[j], 1e-4));
+      SPFD_LAUNCH(c, "convert", true, 1, 12 * S, S,
+                  launch_scale_to_f32(nb, c->rk + (size_t)j * S0, 1.0 / nr[j],
+                                      c->rk32 + (size_t)j * S0, c->sc + j,
+                                      c->partials + (size_t)j * c->pstride, st));
+    }
+    SPFD_LAUNCH(c, "project", true, 1, 12 * S * na, 2 * S * na,
+                launch_dot<float>(nb, c->rk32, c->rk32, c->comp, c->sc, c->partials, 3, st,
+                                  na, c->pstride));
+    TRY(read_scalars(c, na));
+    for (int j = 0; j < na; ++j) {
+      bb_in[j] = active[j] ? c->hsc[j].aux[3] : 0.0;  // 0: the inner CG skips it
+      cap[j] = c->opts.maxit - total[j];
+    }
+    TRY(pcg<float>(c, c->dk32, c->rk32, c->pk32, c->qk32, l0.gx32, l0.diag32, bb_in.data(),
+                   eta.data(), cap.data(), in.data(), na));
+    for (int j = 0; j < na; ++j) {
+      if (!active[j]) continue;
+      total[j] += in[j].iters;
+      SPFD_LAUNCH(c, "convert", false, 1, 20 * S, 2 * S,
+                  launch_axpy_mixed(nb, c->xk + (size_t)j * S0, c->dk32 + (size_t)j * S0,
+                                    nr[j], st));
+    }
+    TRY(true_residual(c, bb.data(), rel_all.data(), na));
+    bool more = false;
+    for (int j = 0; j < na; ++j) {
+      if (!active[j]) continue;
+      rel[j] = rel_all[j];
+      bool stop = false;
+      if (rel[j] <= tol) {
+        out[j].converged = 1;
+        stop = true;
+      } else if (rel[j] > 0.5 * prev[j]) {
+        if (++stall[j] >= 2) stop = true;
+      } else {
+        stall[j] = 0;
+      }
+      if (stop) {
+        active[j] = 0;
+        outer_of[j] = outer;
+        continue;
+      }
+      prev[j] = std::min(prev[j], rel[j]);
+      // the next correction solves for the true residual (in level 0's r)
+      CU(cudaMemcpyAsync(c->rk + (size_t)j * S0, l0.r + (size_t)j * S0, S0 * sizeof(double),
+                         cudaMemcpyDeviceToDevice, st));
+      TRY(project<double>(c, c->rk + (size_t)j * S0, 1, j));
+      SPFD_LAUNCH(c, "project", false, 1, 20 * S, 2 * S,
+                  launch_dot<double>(nb, c->rk + (size_t)j * S0, c->rk + (size_t)j * S0,
+                                     c->comp, c->sc + j, c->partials + (size_t)j * c->pstride,
+                                     3, st));
+      more = true;
+    }
+    if (more) {
+      TRY(read_scalars(c, na));
+      for (int j = 0; j < na; ++j)
+        if (active[j]) nrm2[j] = c->hsc[j].aux[3];
+    }
+  }
+  TRY(project<double>(c, c->xk, nk));
+  for (int j = 0; j < nk; ++j) {
+    if (!(bb[j] > 0.0)) continue;
+    out[j].iters = total[j];
+    out[j].outer_iters = outer_of[j];
+    out[j].rel_res_true = rel[j];
+  }
   return SPFD_OK;
 }
 
@@ -605,10 +681,26 @@ static spfd_status ensure_batch(spfd_ctx *c, int k) {
     CU(cudaMemsetAsync(v, 0, n * sizeof(double), st));
     return SPFD_OK;
   };
-  for (Level &lv : c->L)
-    for (double **v : {&lv.x, &lv.b, &lv.r, &lv.t}) TRY(grow(*v, lv.S * k));
+  auto grow32 = [&](float *&v, size_t n) -> spfd_status {
+    dfree(c, v);
+    TRY(dalloc(c, &v, n));
+    CU(cudaMemsetAsync(v, 0, n * sizeof(float), st));
+    return SPFD_OK;
+  };
+  const bool mixed = c->opts.precision == SPFD_MIXED;
+  for (size_t l = 0; l < c->L.size(); ++l) {
+    Level &lv = c->L[l];
+    // the mixed solve runs its V-cycle in FP32; of the FP64 level vectors
+    // it uses level 0's r only (true residuals)
+    if (!mixed || l == 0)
+      for (double **v : {&lv.x, &lv.b, &lv.r, &lv.t}) TRY(grow(*v, lv.S * k));
+    if (mixed)
+      for (float **v : {&lv.x32, &lv.b32, &lv.r32, &lv.t32}) TRY(grow32(*v, lv.S * k));
+  }
   const size_t S0 = c->L[0].S;
   for (double **v : {&c->xk, &c->rk, &c->pk, &c->qk, &c->bk}) TRY(grow(*v, S0 * k));
+  if (mixed)
+    for (float **v : {&c->dk32, &c->rk32, &c->pk32, &c->qk32}) TRY(grow32(*v, S0 * k));
   TRY(grow(c->partials, c->pstride * k));
   if (c->ncomp > 1) TRY(grow(c->csum, (size_t)c->cstride * k));
   Scalars *sc = nullptr, *hsc = nullptr;
@@ -628,8 +720,8 @@ static spfd_status ensure_batch(spfd_ctx *c, int k) {
 }
 
 // Solves the nk systems whose edge potentials are a_dev + j * 3 NN (NN
-// nodes) into psi_dev + j * NN.  FP64: one CG over all of them (batched
-// launches); mixed precision: one refinement after the other.
+// nodes) into psi_dev + j * NN, in batched launches (FP64 CG, or the mixed
+// refinement with a batched FP32 inner CG).
 static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
                                 double *psi_dev, spfd_info *info, int nk = 1) {
   if (!(tol > 0.0)) tol = c->opts.tol;
@@ -638,7 +730,7 @@ static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
   const size_t NNs = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
   std::vector<spfd_info> res(nk, c->info);
   const int64_t launches0 = c->launch_count;
-  if (nk > 1 && c->ndof > 0 && c->opts.precision != SPFD_MIXED) TRY(ensure_batch(c, nk));
+  if (nk > 1 && c->ndof > 0) TRY(ensure_batch(c, nk));
   CU(cudaEventRecord(c->ev0, st));
   CU(cudaMemsetAsync(&c->sc->status, 0, sizeof(int), st));
   if (c->ndof == 0) {
@@ -649,20 +741,10 @@ static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
       r.converged = 1;
       r.rel_res_true = 0.0;
     }
-  } else if (c->opts.precision == SPFD_MIXED) {
-    for (int j = 0; j < nk; ++j) {
-      c->a_cur = a_dev + (size_t)j * 3 * NNs;
-      spfd_status s = solve_mixed(c, tol, &res[j]);
-      c->a_cur = nullptr;
-      TRY(s);
-      const double NN = (double)NNs;
-      SPFD_LAUNCH(c, "scatter", false, 1, 8 * NN + 12.0 * l0.S, 0,
-                  launch_scatter<double>(l0.g, c->xk, c->comp, psi_dev + (size_t)j * NNs, st));
-      TRY(launch_check("scatter"));
-    }
   } else {
     c->a_cur = a_dev;
-    spfd_status s = solve_fp64(c, tol, res.data(), nk);
+    spfd_status s = c->opts.precision == SPFD_MIXED ? solve_mixed(c, tol, res.data(), nk)
+                                                     : solve_fp64(c, tol, res.data(), nk);
     c->a_cur = nullptr;
     TRY(s);
     const double NN = (double)NNs * nk;

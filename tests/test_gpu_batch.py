@@ -109,9 +109,10 @@ def test_batch_buffers_grow_and_are_reused(torch_cuda, spfd):
             assert st == spfd.SPFD_OK
 
 
-def test_batch_mixed_precision_is_sequential(torch_cuda, spfd):
-    """With SPFD_MIXED the batch runs one refinement after the other: the
-    same results as single mixed solves."""
+def test_batch_mixed_precision_equals_single(torch_cuda, spfd):
+    """With SPFD_MIXED the batch shares the FP32 inner CG's launches while
+    each right-hand side keeps its own refinement state: the same results as
+    single mixed solves, bit for bit."""
     torch = torch_cuda
     ph = body_phantom(64, 40, 224, h=8e-3)
     loops = random_loops(3, np.random.default_rng(42))
@@ -120,6 +121,25 @@ def test_batch_mixed_precision_is_sequential(torch_cuda, spfd):
     with spfd.Solver(_dev(torch, ph.sigma), ph.h, precision=spfd.SPFD_MIXED) as S:
         _, infos, st = _check_batch(torch, S, A, 1e-10)
         assert st == spfd.SPFD_OK and all(i["outer_iters"] >= 1 for i in infos)
+
+
+@pytest.mark.parametrize("seed,air", [(48, 0.55), (49, 0.2)])
+def test_batch_mixed_random_and_zero(torch_cuda, spfd, oracle_mod, seed, air):
+    """Mixed batches on random phantoms (many components at 55 % air), with a
+    zero field and fields of very different scale; one, solved to 1e-11, is
+    held to the oracle to 1e-7."""
+    torch = torch_cuda
+    rng = np.random.default_rng(seed)
+    ph = random_phantom(15, 11, 13, rng, air_fraction=air)
+    nx, ny, nz = ph.dims
+    A = rng.normal(size=(4, 3, nz + 1, ny + 1, nx + 1))
+    A[1] = 0.0
+    A[2] *= 1e4
+    with spfd.Solver(_dev(torch, ph.sigma), ph.h, precision=spfd.SPFD_MIXED) as S:
+        psi_b, infos, st = _check_batch(torch, S, _dev(torch, A), 1e-11)
+        assert st == spfd.SPFD_OK
+        assert infos[1]["iters"] == 0 and not torch.any(psi_b[1] != 0)
+        assert _oracle_psi_err(oracle_mod, ph, A[3], psi_b[3].cpu().numpy()) <= 1e-7
 
 
 def test_batch_argument_errors(torch_cuda, spfd):
@@ -142,10 +162,11 @@ def test_batch_argument_errors(torch_cuda, spfd):
         _check_batch(torch, S, _dev(torch, A), 1e-12)
 
 
-def test_batch_full_size_body_loops(torch_cuda, spfd):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_full_size_body_loops(torch_cuda, spfd, precision):
     """The 256 x 160 x 896 body (h = 2 mm, 9.25 M unknowns) with four of the
-    batched-source loops at 1e-8: each Psi bit-identical to its single solve,
-    all converged."""
+    batched-source loops at 1e-8, in both precisions: each Psi bit-identical
+    to its single solve, all converged."""
     torch = torch_cuda
     from spfd_inputs.sources_torch import loop_potential_t
     ph = body_phantom()
@@ -154,7 +175,8 @@ def test_batch_full_size_body_loops(torch_cuda, spfd):
                     device="cuda")
     for j, (c, n) in enumerate(loops):
         loop_potential_t(ph.dims, ph.h, ph.origin, center=c, normal=n, device="cuda", out=A[j])
-    with spfd.Solver(_dev(torch, ph.sigma), ph.h) as S:
+    prec = spfd.SPFD_FP64 if precision == "fp64" else spfd.SPFD_MIXED
+    with spfd.Solver(_dev(torch, ph.sigma), ph.h, precision=prec) as S:
         _, infos, st = _check_batch(torch, S, A, 1e-8)
         assert st == spfd.SPFD_OK and all(i["converged"] for i in infos)
         assert all(i["rel_res_true"] <= 1e-8 for i in infos)
