@@ -542,8 +542,8 @@ def bench_batch(spfd, torch, dev, stream, ph, sig, nrhs, K, W):
         loop_potential_t(ph.dims, ph.h, ph.origin, center=c, normal=n, device=dev, out=A[j])
     psi = torch.empty((nrhs,) + nshape, dtype=torch.float64, device=dev)
 
-    def run(precision):
-        S = spfd.Solver(sig, ph.h, stream=stream, precision=precision)
+    def run(precision, autotune=1, sequential_too=True):
+        S = spfd.Solver(sig, ph.h, stream=stream, precision=precision, autotune=autotune)
 
         def batched():
             e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -567,7 +567,13 @@ def bench_batch(spfd, torch, dev, stream, ph, sig, nrhs, K, W):
             return e[0].elapsed_time(e[1]), infos
 
         out = {}
-        for name, fn in (("batched", batched), ("sequential", sequential)):
+        # the first batched call grows the buffers and runs the autotuner
+        t0 = time.perf_counter()
+        batched()
+        out["first_batched_call_ms"] = round((time.perf_counter() - t0) * 1e3, 1)
+        todo = (("batched", batched), ("sequential", sequential)) if sequential_too \
+            else (("batched", batched),)
+        for name, fn in todo:
             for _ in range(W):
                 fn()
             rec = [fn() for _ in range(K)]
@@ -580,12 +586,26 @@ def bench_batch(spfd, torch, dev, stream, ph, sig, nrhs, K, W):
                          else int(infos[0]["launches"]),
                          "max_rel_res_true": max(i["rel_res_true"] for i in infos)}
         out["context_bytes_device"] = S.info()["bytes_device"]
-        out["speedup_batched_vs_sequential"] = round(out["sequential"]["ms"] / out["batched"]["ms"], 3)
+        if sequential_too:
+            out["speedup_batched_vs_sequential"] = round(
+                out["sequential"]["ms"] / out["batched"]["ms"], 3)
+        rep = S.autotune_report()
+        if rep:
+            out["autotune"] = {
+                "decisions": len(rep), "order1_chosen": sum(r["order"] for r in rep),
+                "tuned_launch_ms": {f"{r['family']}_l{r['level']}":
+                                    [round(r["ms_order0"], 3), round(r["ms_order1"], 3), r["order"]]
+                                    for r in rep},
+                "note": "per family and level: [ms per launch in order 0 (right-hand sides one "
+                        "after the other), in order 1 (all right-hand sides of a brick side by "
+                        "side), order kept]"}
         S.close()
         return out
 
     fp64 = run(spfd.SPFD_FP64)
     mixed = run(spfd.SPFD_MIXED)
+    fp64["batched_fixed_order0_ms"] = run(spfd.SPFD_FP64, 0, False)["batched"]["ms"]
+    mixed["batched_fixed_order0_ms"] = run(spfd.SPFD_MIXED, 0, False)["batched"]["ms"]
     del A, psi
     return {"workload": f"{nrhs} loop sources (R=0.3 m, I=1000 A) at seeded positions x,y in "
                         "+-0.5 m, z in -0.6..-0.3 m, random orientations, on the "

@@ -86,6 +86,10 @@ typedef struct {
   int verbose;       /* 0 = silent; 1 = one line per build/solve on stderr */
   int profile;       /* 1 = time every kernel launch with CUDA events (see
                         spfd_kernel_stats); adds ~2 us of host work per launch */
+  int autotune;      /* 1 (default) = the first batched solve of each batch
+                        size times both block orders of each batched kernel
+                        family and level and keeps the faster (see
+                        spfd_autotune_report); 0 = fixed order */
 } spfd_opts;
 
 typedef struct {
@@ -312,6 +316,30 @@ void spfd_destroy(spfd_ctx *ctx);
 spfd_status spfd_energy_grad(spfd_ctx *ctx, const double *a_dev, const double *psi_dev,
                              double omega, double tol, double *J_out, double *dJda_dev,
                              double *dJdsigma_dev, spfd_info *info);
+
+/* One decision of the autotuner of batched solves (not in the paper: launch
+ * tuning of this library).  A batched launch covers nk right-hand sides
+ * over the bricks of a level in one of two block orders: 0 = the
+ * right-hand sides one after the other, 1 = the nk blocks of each brick side
+ * by side, so that they share the brick's operator entries through L2.  The
+ * first spfd_solve_batch of each batch size (with opts.autotune set) times
+ * both orders of every batched kernel family on every level and keeps the
+ * faster; results are unchanged either way. */
+typedef struct {
+  const char *family;  /* "jacobi_first", "smooth", "residual", "restrict",
+                          "prolong" (fine level) or "apply_dot" (static) */
+  int level;           /* multigrid level (0 = finest) */
+  int nrhs;            /* batch size tuned for */
+  int order;           /* the order kept (0 or 1) */
+  double ms_order0;    /* mean time of one launch in order 0 */
+  double ms_order1;    /* mean time of one launch in order 1 */
+} spfd_tune_entry;
+
+/* The autotuner's decisions for this context, oldest first.
+ *   entries  caller array of at least max entries (may be NULL when max = 0).
+ *   n        receives the number of decisions recorded (may exceed max). */
+spfd_status spfd_autotune_report(const spfd_ctx *ctx, spfd_tune_entry *entries, int max,
+                                 int *n);
 
 /* Give every cached device block back to the driver (cudaFree); the bytes
  * released go to *released if it is not NULL.  Safe at any time: contexts

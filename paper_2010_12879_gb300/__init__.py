@@ -31,7 +31,8 @@ EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
            "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
            "spfd_energy_grad", "spfd_solve_batch", "spfd_percentile",
-           "spfd_group_create", "spfd_group_solve", "spfd_group_destroy")
+           "spfd_group_create", "spfd_group_solve", "spfd_group_destroy",
+           "spfd_autotune_report")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -40,7 +41,7 @@ class SpfdOpts(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("cheb_degree", ctypes.c_int),
                 ("precision", ctypes.c_int), ("coarse_max", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class SpfdInfo(ctypes.Structure):
@@ -59,6 +60,12 @@ class SpfdKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64),
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
                 ("flops", ctypes.c_double)]
+
+
+class SpfdTuneEntry(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_char_p), ("level", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("order", ctypes.c_int), ("ms_order0", ctypes.c_double),
+                ("ms_order1", ctypes.c_double)]
 
 
 class SpfdError(RuntimeError):
@@ -122,6 +129,9 @@ def lib():
             L.spfd_group_solve.restype = ctypes.c_int
             L.spfd_group_destroy.argtypes = [vp]
             L.spfd_group_destroy.restype = None
+            L.spfd_autotune_report.argtypes = [vp, ctypes.POINTER(SpfdTuneEntry), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]
+            L.spfd_autotune_report.restype = ctypes.c_int
             L.spfd_release_cached_memory.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
             L.spfd_release_cached_memory.restype = ctypes.c_int
             _lib = L
@@ -229,6 +239,16 @@ def spfd_percentile(ctx: int, E_ptr: int, labels_ptr: int, n_labels: int, p: flo
                                  ctypes.c_void_p(labels_ptr), int(n_labels), float(p),
                                  vals, cnts))
     return list(vals), list(cnts)
+
+
+def spfd_autotune_report(ctx: int) -> list:
+    """The autotuner's block-order decisions for batched solves (dicts)."""
+    n = ctypes.c_int(0)
+    _check(lib().spfd_autotune_report(ctypes.c_void_p(ctx), None, 0, ctypes.byref(n)))
+    arr = (SpfdTuneEntry * max(n.value, 1))()
+    _check(lib().spfd_autotune_report(ctypes.c_void_p(ctx), arr, n.value, ctypes.byref(n)))
+    return [{"family": e.family.decode(), "level": e.level, "nrhs": e.nrhs, "order": e.order,
+             "ms_order0": e.ms_order0, "ms_order1": e.ms_order1} for e in arr[:n.value]]
 
 
 def spfd_release_cached_memory() -> int:
@@ -429,6 +449,9 @@ class Solver:
                 raise ValueError("labels must be a contiguous int32 CUDA tensor (nz, ny, nx)")
             lp = labels.data_ptr()
         return spfd_percentile(self.ctx, E.data_ptr(), lp, n_labels, p)
+
+    def autotune_report(self) -> list:
+        return spfd_autotune_report(self.ctx)
 
     def info(self) -> dict:
         return spfd_get_info(self.ctx).as_dict()

@@ -146,6 +146,7 @@ extern "C" void spfd_opts_default(spfd_opts *o) {
   o->max_levels = 12;
   o->verbose = 0;
   o->profile = 0;
+  o->autotune = 1;
 }
 
 extern "C" spfd_status spfd_build(const double *sigma_dev, int nx, int ny,
@@ -259,40 +260,150 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk) {
   const T *wd = lv.WDINV<T>();
   if (proj)
     SPFD_LAUNCH(c, "jacobi_first_l0", f32, 1, 4 * w * S, 2 * S,
-                launch_jacobi_first_proj<T>(lv.g, wd, bl, cur, c->sc, inv, st, nk));
+                launch_jacobi_first_proj<T>(lv.g, wd, bl, cur, c->sc, inv, st, nk,
+                                            block_order(c, TF_JFIRST, l)));
   else
     SPFD_LAUNCH(c, l == 0 ? "jacobi_first_l0" : "jacobi_first_coarse", f32, 1,
-                3 * w * S, S, launch_jacobi_first<T>(lv.g, wd, bl, cur, st, nk));
+                3 * w * S, S,
+                launch_jacobi_first<T>(lv.g, wd, bl, cur, st, nk, block_order(c, TF_JFIRST, l)));
   auto sweep = [&](T *in, T *out) {
     if (l == 0)
       SPFD_LAUNCH(c, "jacobi7_l0", f32, 1, (5 * w + 3 * wc) * S, 16 * S,
                   (launch_jacobi7<T, typename Prec<T>::C7>(lv.g, Prec<T>::gx(lv),
                                                            lv.DIAG<T>(), wd, in, bl, out, st,
-                                                           nk)));
+                                                           nk, block_order(c, TF_SMOOTH, l))));
     else
       SPFD_LAUNCH(c, "jacobi27", f32, 1, 32 * w * S, 57 * S,
-                  launch_jacobi27<T>(lv.g, lv.ST<T>(), wd, in, bl, out, st, nk));
+                  launch_jacobi27<T>(lv.g, lv.ST<T>(), wd, in, bl, out, st, nk,
+                                     block_order(c, TF_SMOOTH, l)));
   };
   for (int s = 1; s < c->opts.nu_pre; ++s) { sweep(cur, oth); std::swap(cur, oth); }
   if (l == 0)
     SPFD_LAUNCH(c, "residual7_l0", f32, 1, (4 * w + 3 * wc) * S, 14 * S,
                 (launch_residual7<T, typename Prec<T>::C7>(lv.g, Prec<T>::gx(lv),
                                                            lv.DIAG<T>(), cur, bl, lv.R<T>(), st,
-                                                           nk)));
+                                                           nk, block_order(c, TF_RESID, l))));
   else
     SPFD_LAUNCH(c, "residual27", f32, 1, 30 * w * S, 55 * S,
-                launch_residual27<T>(lv.g, lv.ST<T>(), cur, bl, lv.R<T>(), st, nk));
+                launch_residual27<T>(lv.g, lv.ST<T>(), cur, bl, lv.R<T>(), st, nk,
+                                     block_order(c, TF_RESID, l)));
   Level &cl = c->L[l + 1];
   const double Sc = (double)cl.S * nk;
   SPFD_LAUNCH(c, l == 0 ? "restrict_l0" : "restrict_coarse", f32, 1,
               28 * w * Sc + w * S, 54 * Sc,
-              launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st, nk));
+              launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st, nk,
+                                 block_order(c, TF_RESTRICT, l)));
   T *ec = vcycle<T>(c, l + 1, cl.B<T>(), false, nk);
   SPFD_LAUNCH(c, l == 0 ? "prolong_l0" : "prolong_coarse", f32, 1,
               (27.0 / 8.0 + 2.0) * w * S + w * Sc, 7 * S,
-              launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st, nk));
+              launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st, nk,
+                                block_order(c, TF_PROLONG, l)));
   for (int s = 0; s < c->opts.nu_post; ++s) { sweep(cur, oth); std::swap(cur, oth); }
   return cur;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Chooses the block order (unit_rhs) of every batched kernel family on every
+// level for nk right-hand sides: each order is timed on the context's own
+// operators and level vectors (one warm-up launch, then two timed ones,
+// CUDA events on the context's stream) and the faster is kept.  Tuning only
+// rewrites scratch vectors that every solve initialises before use, and each
+// kernel keeps zero vector entries at slots that are not unknowns, so it
+// leaves no trace in later solves.  Order 1 is skipped where units * nk
+// does not fit a one-dimensional grid.
+template <typename T>
+static spfd_status autotune_orders(spfd_ctx *c, int nk, std::vector<signed char> &tab) {
+  using C7 = typename Prec<T>::C7;
+  const int nl = (int)c->L.size();
+  tab.assign((size_t)TF_COUNT * nl, 0);
+  cudaStream_t st = c->stream;
+  cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+  struct Give {  // the events go back to the context's pool on every exit
+    spfd_ctx *c;
+    cudaEvent_t a, b;
+    ~Give() {
+      if (a) c->evpool.push_back(a);
+      if (b) c->evpool.push_back(b);
+    }
+  } give{c, e0, e1};
+  if (!e0 || !e1) return fail(SPFD_ECUDA, "autotuner events");
+  auto timed = [&](const auto &launch, int order, float *ms) -> spfd_status {
+    launch(order);
+    CU(cudaEventRecord(e0, st));
+    launch(order);
+    launch(order);
+    CU(cudaEventRecord(e1, st));
+    CU(cudaEventSynchronize(e1));
+    CU(cudaEventElapsedTime(ms, e0, e1));
+    c->launch_count += 3;
+    *ms *= 0.5f;
+    return launch_check("autotune");
+  };
+  auto pick = [&](int fam, int l, int units, const auto &launch) -> spfd_status {
+    if (units <= 0 || !order1_fits(units, nk)) return SPFD_OK;
+    float m0 = 0.f, m1 = 0.f;
+    TRY(timed(launch, 0, &m0));
+    TRY(timed(launch, 1, &m1));
+    const int best = m1 < m0 ? 1 : 0;
+    tab[(size_t)fam * nl + l] = (signed char)best;
+    c->tune_log.push_back(TuneRecord{fam, l, nk, best, (double)m0, (double)m1});
+    return SPFD_OK;
+  };
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level &lv = c->L[l], &cl = c->L[l + 1];
+    const Grid &g = lv.g;
+    const T *wd = lv.WDINV<T>();
+    T *x = lv.X<T>(), *t = lv.Tt<T>(), *b = lv.B<T>(), *r = lv.R<T>();
+    if (l == 0 && c->ncomp == 1)
+      TRY(pick(TF_JFIRST, l, g.nb, [&](int o) {
+        launch_jacobi_first_proj<T>(g, wd, b, x, c->sc, 0.0, st, nk, o);
+      }));
+    else
+      TRY(pick(TF_JFIRST, l, g.nb, [&](int o) { launch_jacobi_first<T>(g, wd, b, x, st, nk, o); }));
+    if (l == 0) {
+      TRY(pick(TF_SMOOTH, l, g.nb, [&](int o) {
+        launch_jacobi7<T, C7>(g, Prec<T>::gx(lv), lv.DIAG<T>(), wd, x, b, t, st, nk, o);
+      }));
+      TRY(pick(TF_RESID, l, g.nb, [&](int o) {
+        launch_residual7<T, C7>(g, Prec<T>::gx(lv), lv.DIAG<T>(), x, b, r, st, nk, o);
+      }));
+      const T *opgx = sizeof(T) == 4 ? (const T *)lv.gx32 : (const T *)lv.gx;
+      const T *opdiag = sizeof(T) == 4 ? (const T *)lv.diag32 : (const T *)lv.diag;
+      TRY(pick(TF_APPLY, l, g.nb, [&](int o) {
+        launch_apply_dot<T>(g, opgx, opdiag, x, r, c->sc, c->partials, st, nk, c->pstride, o);
+      }));
+    } else {
+      TRY(pick(TF_SMOOTH, l, g.nb, [&](int o) {
+        launch_jacobi27<T>(g, lv.ST<T>(), wd, x, b, t, st, nk, o);
+      }));
+      TRY(pick(TF_RESID, l, g.nb, [&](int o) {
+        launch_residual27<T>(g, lv.ST<T>(), x, b, r, st, nk, o);
+      }));
+    }
+    TRY(pick(TF_RESTRICT, l, cl.g.nb, [&](int o) {
+      launch_restrict<T>(g, cl.g, cl.PP<T>(), r, cl.B<T>(), st, nk, o);
+    }));
+    TRY(pick(TF_PROLONG, l, (g.nb + 1) / 2, [&](int o) {
+      launch_prolong<T>(g, cl.g, lv.PC<T>(), cl.X<T>(), x, st, nk, o);
+    }));
+  }
+  return SPFD_OK;
+}
+
+// The block-order table for a batch of nk right-hand sides (tuned on first
+// use when opts.autotune is set); nullptr keeps order 0.
+static spfd_status batch_orders(spfd_ctx *c, int nk, const signed char **out) {
+  *out = nullptr;
+  if (nk <= 1 || !c->opts.autotune || c->ndof == 0) return SPFD_OK;
+  auto it = c->tuned.find(nk);
+  if (it == c->tuned.end()) {
+    std::vector<signed char> tab;
+    const bool mixed = c->opts.precision == SPFD_MIXED;
+    TRY(mixed ? autotune_orders<float>(c, nk, tab) : autotune_orders<double>(c, nk, tab));
+    it = c->tuned.emplace(nk, std::move(tab)).first;
+  }
+  *out = it->second.data();
+  return SPFD_OK;
 }
 
 // ------------------------------------------------------------------ Krylov
@@ -443,7 +554,7 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
     const double S = (double)S0 * na;
     SPFD_LAUNCH(c, "apply_dot", f32, 1, (f32 ? 5 : 6) * w * S, (f32 ? 20 : 15) * S,
                 launch_apply_dot<T>(l0.g, opgx, opdiag, p, q, c->sc, c->partials, st, na,
-                                    c->pstride));
+                                    c->pstride, block_order(c, TF_APPLY, 0)));
     SPFD_LAUNCH(c, "finish_pq", false, 1, 8.0 * nb * na, nb * na,
                 launch_finish_pq(apply_dot_partials<T>(nb), c->partials,
                                  c->partials + (size_t)16 * nb, c->sc, st, na, c->pstride));
@@ -731,6 +842,8 @@ static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
   std::vector<spfd_info> res(nk, c->info);
   const int64_t launches0 = c->launch_count;
   if (nk > 1 && c->ndof > 0) TRY(ensure_batch(c, nk));
+  const signed char *orders = nullptr;
+  TRY(batch_orders(c, nk, &orders));
   CU(cudaEventRecord(c->ev0, st));
   CU(cudaMemsetAsync(&c->sc->status, 0, sizeof(int), st));
   if (c->ndof == 0) {
@@ -743,8 +856,10 @@ static spfd_status solve_device(spfd_ctx *c, const double *a_dev, double tol,
     }
   } else {
     c->a_cur = a_dev;
+    c->ord = orders;
     spfd_status s = c->opts.precision == SPFD_MIXED ? solve_mixed(c, tol, res.data(), nk)
                                                      : solve_fp64(c, tol, res.data(), nk);
+    c->ord = nullptr;
     c->a_cur = nullptr;
     TRY(s);
     const double NN = (double)NNs * nk;
@@ -879,6 +994,24 @@ extern "C" spfd_status spfd_efield(spfd_ctx *ctx, const double *a_dev,
               launch_efield(ctx->mask, a_dev, psi_dev, ctx->nx, ctx->ny, ctx->nz,
                             ctx->h, omega, E_dev, ctx->stream));
   return launch_check("efield");
+}
+
+extern "C" spfd_status spfd_autotune_report(const spfd_ctx *ctx, spfd_tune_entry *entries,
+                                            int max, int *n) {
+  if (!ctx || !n || (max > 0 && !entries)) return fail(SPFD_EINVAL, "null argument");
+  static const char *const names[TF_COUNT] = {"jacobi_first", "smooth", "residual",
+                                              "restrict", "prolong", "apply_dot"};
+  *n = (int)ctx->tune_log.size();
+  for (int i = 0; i < max && i < *n; ++i) {
+    const TuneRecord &r = ctx->tune_log[i];
+    entries[i].family = names[r.fam];
+    entries[i].level = r.level;
+    entries[i].nrhs = r.nk;
+    entries[i].order = r.order;
+    entries[i].ms_order0 = r.ms0;
+    entries[i].ms_order1 = r.ms1;
+  }
+  return SPFD_OK;
 }
 
 extern "C" spfd_status spfd_get_info(const spfd_ctx *ctx, spfd_info *info) {

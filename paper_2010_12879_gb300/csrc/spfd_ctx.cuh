@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <chrono>
+#include <map>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -86,6 +87,22 @@ template <> inline const float *Level::DIAG<float>() const { return diag32; }
 template <> inline const double *Level::WDINV<double>() const { return wdinv; }
 template <> inline const float *Level::WDINV<float>() const { return wdinv32; }
 
+// Kernel families whose block order the autotuner chooses per level
+// (restriction and prolongation are indexed by their fine level).
+enum TuneFam : int {
+  TF_JFIRST = 0,   // first smoothing sweep from a zero guess
+  TF_SMOOTH,       // weighted-Jacobi sweep (7-point on level 0, 27-point above)
+  TF_RESID,        // residual
+  TF_RESTRICT,     // restriction to the next coarser level
+  TF_PROLONG,      // prolongation and correction from the next coarser level
+  TF_APPLY,        // the CG operator with its dot product (level 0)
+  TF_COUNT
+};
+struct TuneRecord {
+  int fam, level, nk, order;
+  double ms0, ms1;  // mean time per launch in order 0 and order 1
+};
+
 struct KernelStat {
   std::string name;
   int64_t launches = 0;
@@ -160,6 +177,12 @@ struct spfd_ctx {
   int pct_gcap = 0, pct_chcap = 0;
   long long pct_keycap = 0, pct_nc = 0;  // pct_nc: conducting voxels seen last call
   size_t pct_hstage_n = 0;
+  // block orders chosen by the autotuner for batched launches: per batch
+  // size, TF_COUNT x (levels) entries of 0 or 1; ord points at the table of
+  // the batched solve in progress (nullptr: order 0 everywhere)
+  std::map<int, std::vector<signed char>> tuned;
+  const signed char *ord = nullptr;
+  std::vector<spfd::TuneRecord> tune_log;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   spfd_info info{};
   // launch accounting and profiling
@@ -259,6 +282,11 @@ void prof_push(spfd_ctx *c, int stat, cudaEvent_t a, cudaEvent_t b,
 spfd_status prof_flush(spfd_ctx *c);
 
 }  // namespace spfd
+
+// Block order of family fam on level l for the launch in progress.
+inline int block_order(const spfd_ctx *c, int fam, int l) {
+  return c->ord ? c->ord[fam * (int)c->L.size() + l] : 0;
+}
 
 // Solve steps shared by the host-driven solves (spfd_api.cu) and the
 // captured, device-driven ones (spfd_graph.cu).  All of them only enqueue

@@ -20,10 +20,13 @@ namespace spfd {
 template <typename T, typename C>
 __global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
-            const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r) {
-  const int bk = blockIdx.x, t = threadIdx.x;
+            const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r,
+            int order, int nk) {
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
-  const size_t off = (size_t)blockIdx.y * S;  // right-hand side blockIdx.y
+  const size_t off = (size_t)rhs * S;
   x += off; b += off; r += off;
   const Q4<T> bv = ldq<T>(b + s0);
   Q4<T> xc, rv;
@@ -35,10 +38,12 @@ template <typename T, typename C>
 __global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
-          const T *__restrict__ b, T *__restrict__ xout) {
-  const int bk = blockIdx.x, t = threadIdx.x;
+          const T *__restrict__ b, T *__restrict__ xout, int order, int nk) {
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
-  const size_t off = (size_t)blockIdx.y * S;
+  const size_t off = (size_t)rhs * S;
   xin += off; b += off; xout += off;
   const Q4<T> bv = ldq<T>(b + s0), wv = ldq<T>(wdinv + s0);
   Q4<T> xc, rv;
@@ -51,11 +56,12 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
-             const T *__restrict__ b, T *__restrict__ r) {
+             const T *__restrict__ b, T *__restrict__ r, int order, int nk) {
   __shared__ T tl[10][10][10];
   __shared__ int sn[27];
-  const int bk = blockIdx.x;
-  const size_t off = (size_t)blockIdx.y * g.nb * BV;
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const size_t off = (size_t)rhs * g.nb * BV;
   x += off; b += off; r += off;
   load_nbr(g, bk, sn);
   __syncthreads();
@@ -69,11 +75,12 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
 k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
            const T *__restrict__ xin, const T *__restrict__ b,
-           T *__restrict__ xout) {
+           T *__restrict__ xout, int order, int nk) {
   __shared__ T tl[10][10][10];
   __shared__ int sn[27];
-  const int bk = blockIdx.x;
-  const size_t off = (size_t)blockIdx.y * g.nb * BV;
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const size_t off = (size_t)rhs * g.nb * BV;
   xin += off; b += off; xout += off;
   load_nbr(g, bk, sn);
   __syncthreads();
@@ -90,10 +97,12 @@ k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
-               T *__restrict__ x) {
+               T *__restrict__ x, int nb, int order, int nk) {
   constexpr int N = V16<T>::N;
-  const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
-  const size_t off = (size_t)blockIdx.y * gridDim.x * BV;
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const size_t s0 = (size_t)bk * BV + threadIdx.x * N;
+  const size_t off = (size_t)rhs * nb * BV;
   b += off; x += off;
   const V16<T> w = ld16(wdinv + s0), bv = ld16(b + s0);
   V16<T> xv;
@@ -107,11 +116,13 @@ k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
-                    T *__restrict__ x, const Scalars *sc, double) {
+                    T *__restrict__ x, const Scalars *sc, int nb, int order, int nk) {
   constexpr int N = V16<T>::N;
-  const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
-  const size_t off = (size_t)blockIdx.y * gridDim.x * BV;
-  b += off; x += off; sc += blockIdx.y;
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const size_t s0 = (size_t)bk * BV + threadIdx.x * N;
+  const size_t off = (size_t)rhs * nb * BV;
+  b += off; x += off; sc += rhs;
   T mean;
   if constexpr (sizeof(T) == 4) mean = sc->rmean_f; else mean = sc->rmean;
   const V16<T> w = ld16(wdinv + s0);
@@ -136,12 +147,14 @@ k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf,
-           T *__restrict__ bcoarse) {
+           T *__restrict__ bcoarse, int order, int nk) {
   __shared__ T fs[17][17][17];
   __shared__ int sk[27];
-  const int bk = blockIdx.x, t = threadIdx.x;
-  rf += (size_t)blockIdx.y * Sf;
-  bcoarse += (size_t)blockIdx.y * gc.nb * BV;
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const int t = threadIdx.x;
+  rf += (size_t)rhs * Sf;
+  bcoarse += (size_t)rhs * gc.nb * BV;
   if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
   __syncthreads();
   for (int q = t; q < 17 * 17 * 17; q += NT) {
@@ -173,11 +186,13 @@ k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
-          T *__restrict__ ef) {
-  const int bk = blockIdx.x * 2 + (threadIdx.x >> 6);
+          T *__restrict__ ef, int order, int nk) {
+  int pair, rhs;
+  unit_rhs(order, nk, pair, rhs);
+  const int bk = pair * 2 + (threadIdx.x >> 6);
   if (bk >= gf.nb) return;
-  ec += (size_t)blockIdx.y * gc.nb * BV;
-  ef += (size_t)blockIdx.y * gf.nb * BV;
+  ec += (size_t)rhs * gc.nb * BV;
+  ef += (size_t)rhs * gf.nb * BV;
   const int cell = threadIdx.x & 63;
   const int ccx = cell & 3, ccy = (cell >> 2) & 3, ccz = cell >> 4;
   const size_t NC = (size_t)gf.nb * 64, cid = (size_t)bk * 64 + cell;
@@ -241,46 +256,58 @@ __global__ void k_coarse_solve(int m, size_t S, const int *__restrict__ idx,
 // ------------------------------------------------------------ launchers
 template <typename T, typename C>
 void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
-                      const T *b, T *r, cudaStream_t st, int nk) {
-  if (g.nb) k_residual7<T, C><<<dim3(g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r);
+                      const T *b, T *r, cudaStream_t st, int nk, int order) {
+  if (g.nb)
+    k_residual7<T, C><<<unit_grid(order, g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r, order, nk);
 }
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
-                       T *r, cudaStream_t st, int nk) {
-  if (g.nb) k_residual27<T><<<dim3(g.nb, nk), NT, 0, st>>>(g, stc, x, b, r);
+                       T *r, cudaStream_t st, int nk, int order) {
+  if (g.nb) k_residual27<T><<<unit_grid(order, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, order, nk);
 }
 template <typename T>
 void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
-                         cudaStream_t st, int nk) {
-  if (g.nb) k_jacobi_first<T><<<dim3(g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x);
+                         cudaStream_t st, int nk, int order) {
+  if (g.nb)
+    k_jacobi_first<T><<<unit_grid(order, g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, g.nb,
+                                                                            order, nk);
 }
 template <typename T>
 void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
                               const Scalars *sc, double inv_ndof,
-                              cudaStream_t st, int nk) {
+                              cudaStream_t st, int nk, int order) {
+  (void)inv_ndof;  // the mean comes from each right-hand side's Scalars
   if (g.nb)
-    k_jacobi_first_proj<T><<<dim3(g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, sc, inv_ndof);
+    k_jacobi_first_proj<T><<<unit_grid(order, g.nb, nk), NT / V16<T>::N, 0, st>>>(
+        wdinv, b, x, sc, g.nb, order, nk);
 }
 template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
-                    const T *xin, const T *b, T *xout, cudaStream_t st, int nk) {
-  if (g.nb) k_jacobi7<T, C><<<dim3(g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout);
+                    const T *xin, const T *b, T *xout, cudaStream_t st, int nk, int order) {
+  if (g.nb)
+    k_jacobi7<T, C><<<unit_grid(order, g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout,
+                                                               order, nk);
 }
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
-                     const T *b, T *xout, cudaStream_t st, int nk) {
-  if (g.nb) k_jacobi27<T><<<dim3(g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout);
+                     const T *b, T *xout, cudaStream_t st, int nk, int order) {
+  if (g.nb)
+    k_jacobi27<T><<<unit_grid(order, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, order,
+                                                             nk);
 }
 template <typename T>
 void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
-                     T *bcoarse, cudaStream_t st, int nk) {
+                     T *bcoarse, cudaStream_t st, int nk, int order) {
   if (gc.nb)
-    k_restrict<T><<<dim3(gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf, bcoarse);
+    k_restrict<T><<<unit_grid(order, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
+                                                              bcoarse, order, nk);
 }
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
-                    T *ef, cudaStream_t st, int nk) {
-  if (gf.nb) k_prolong<T><<<dim3((gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef);
+                    T *ef, cudaStream_t st, int nk, int order) {
+  if (gf.nb)
+    k_prolong<T><<<unit_grid(order, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, order,
+                                                                        nk);
 }
 template <typename T>
 void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
@@ -293,19 +320,19 @@ void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
 
 #define INST_T(T)                                                             \
   template void launch_residual27<T>(const Grid &, const T *, const T *,      \
-                                     const T *, T *, cudaStream_t, int);      \
+                                     const T *, T *, cudaStream_t, int, int); \
   template void launch_jacobi_first<T>(const Grid &, const T *, const T *,    \
-                                       T *, cudaStream_t, int);               \
+                                       T *, cudaStream_t, int, int);          \
   template void launch_jacobi_first_proj<T>(const Grid &, const T *, T *,     \
                                             T *, const Scalars *, double,     \
-                                            cudaStream_t, int);               \
+                                            cudaStream_t, int, int);          \
   template void launch_jacobi27<T>(const Grid &, const T *, const T *,        \
                                    const T *, const T *, T *, cudaStream_t,   \
-                                   int);                                      \
+                                   int, int);                                 \
   template void launch_restrict<T>(const Grid &, const Grid &, const T *,     \
-                                   const T *, T *, cudaStream_t, int);        \
+                                   const T *, T *, cudaStream_t, int, int);   \
   template void launch_prolong<T>(const Grid &, const Grid &, const T *,      \
-                                  const T *, T *, cudaStream_t, int);         \
+                                  const T *, T *, cudaStream_t, int, int);    \
   template void launch_coarse_solve<T>(int, size_t, const int *,              \
                                        const double *, const T *, T *,        \
                                        cudaStream_t, int);
@@ -314,10 +341,10 @@ INST_T(float)
 #define INST_TC(T, C)                                                         \
   template void launch_residual7<T, C>(const Grid &, const C *, const T *,    \
                                        const T *, const T *, T *,             \
-                                       cudaStream_t, int);                    \
+                                       cudaStream_t, int, int);               \
   template void launch_jacobi7<T, C>(const Grid &, const C *, const T *,      \
                                      const T *, const T *, const T *, T *,    \
-                                     cudaStream_t, int);
+                                     cudaStream_t, int, int);
 INST_TC(double, double)
 INST_TC(float, float)
 INST_TC(float, __nv_bfloat16)

@@ -42,6 +42,30 @@ __host__ __device__ __forceinline__ constexpr int crank(int u, int o) {
   return r;
 }
 
+// Block order of a batched launch (nk right-hand sides over units of one
+// or two bricks).  Order 0: blockIdx.x is the unit and blockIdx.y the
+// right-hand side, so the right-hand sides run one after the other.  Order 1
+// (a one-dimensional grid): block b covers unit b / nk of right-hand side
+// b % nk, so the nk blocks of one unit run side by side and share its
+// operator entries through L2.  The arithmetic of every block is the same
+// in both orders; the autotuner picks one per kernel family and level.
+__device__ __forceinline__ void unit_rhs(int order, int nk, int &unit, int &rhs) {
+  if (order) {
+    unit = (int)(blockIdx.x / (unsigned)nk);
+    rhs = (int)(blockIdx.x % (unsigned)nk);
+  } else {
+    unit = (int)blockIdx.x;
+    rhs = (int)blockIdx.y;
+  }
+}
+inline dim3 unit_grid(int order, int units, int nk) {
+  return order ? dim3((unsigned)units * (unsigned)nk) : dim3((unsigned)units, (unsigned)nk);
+}
+// Order 1 is available while units * nk fits a one-dimensional grid.
+inline bool order1_fits(int units, int nk) {
+  return (long long)units * nk <= 2147483647LL;
+}
+
 struct Grid {
   int NX, NY, NZ;       // nodes per axis
   int MX, MY, MZ;       // bricks per axis
@@ -152,32 +176,33 @@ double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
 // slots are nk consecutive blocks of S values; operators are shared.
 template <typename T, typename C>
 void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
-                      const T *b, T *r, cudaStream_t st, int nk = 1);
+                      const T *b, T *r, cudaStream_t st, int nk = 1, int order = 0);
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
-                       T *r, cudaStream_t st, int nk = 1);
+                       T *r, cudaStream_t st, int nk = 1, int order = 0);
 template <typename T>
 void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
-                         cudaStream_t st, int nk = 1);
+                         cudaStream_t st, int nk = 1, int order = 0);
 // First level-0 sweep with the projection of the right-hand side fused in:
 // b <- b - (sum b)/n on the unknowns (one component), then x = wdinv * b;
 // sc holds one Scalars per right-hand side.
 template <typename T>
 void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
                               const Scalars *sc, double inv_ndof,
-                              cudaStream_t st, int nk = 1);
+                              cudaStream_t st, int nk = 1, int order = 0);
 template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
-                    const T *xin, const T *b, T *xout, cudaStream_t st, int nk = 1);
+                    const T *xin, const T *b, T *xout, cudaStream_t st, int nk = 1,
+                    int order = 0);
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
-                     const T *b, T *xout, cudaStream_t st, int nk = 1);
+                     const T *b, T *xout, cudaStream_t st, int nk = 1, int order = 0);
 template <typename T>
 void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
-                     T *bc, cudaStream_t st, int nk = 1);
+                     T *bc, cudaStream_t st, int nk = 1, int order = 0);
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
-                    T *ef, cudaStream_t st, int nk = 1);
+                    T *ef, cudaStream_t st, int nk = 1, int order = 0);
 // x[idx] = Binv b[idx] on the coarsest level (S slots per right-hand side).
 template <typename T>
 void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
@@ -190,7 +215,7 @@ void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
 template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st, int nk = 1,
-                      size_t pstride = 0);
+                      size_t pstride = 0, int order = 0);
 // Number of partial sums launch_apply_dot writes for nb bricks (one per warp,
 // 4 per brick); launch_finish_pq adds n of them (scratch: at least 152
 // doubles, not overlapping) and sets alpha = rz / pq.

@@ -105,12 +105,14 @@ template <typename T>
 __global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ p, T *__restrict__ q, double *partials,
-            size_t pstride) {
-  const int bk = blockIdx.x, t = threadIdx.x;
+            size_t pstride, int order, int nk) {
+  int bk, rhs;
+  unit_rhs(order, nk, bk, rhs);
+  const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
-  p += (size_t)blockIdx.y * S;  // right-hand side blockIdx.y
-  q += (size_t)blockIdx.y * S;
-  partials += (size_t)blockIdx.y * pstride;
+  p += (size_t)rhs * S;
+  q += (size_t)rhs * S;
+  partials += (size_t)rhs * pstride;
   Q4<T> pc, qv;
   apply7_row<T, T, false>(g, gx, diag, p, S, bk, t, zq<T>(), pc, qv);
   stq(q + s0, qv);
@@ -909,9 +911,10 @@ void launch_scaled_copy(int nb, const double *src, double f, double *dst,
 template <typename T>
 void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st, int nk,
-                      size_t pstride) {
+                      size_t pstride, int order) {
   if (!g.nb) return;
-  k_apply_dot<T><<<dim3(g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride);
+  k_apply_dot<T><<<unit_grid(order, g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride,
+                                                            order, nk);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
                       cudaStream_t st, int nk, size_t pstride) {
@@ -1022,7 +1025,7 @@ void launch_energy_grads(const Grid &g, const double *gx, const unsigned char *m
 #define INST_K(T)                                                              \
   template void launch_apply_dot<T>(const Grid &, const T *, const T *,        \
                                     const T *, T *, Scalars *, double *,       \
-                                    cudaStream_t, int, size_t);                \
+                                    cudaStream_t, int, size_t, int);           \
   template void launch_update_xr<T>(int, T *, T *, const T *, const T *,       \
                                     Scalars *, double *, cudaStream_t, int,    \
                                     size_t);                                   \

@@ -142,6 +142,39 @@ def test_batch_mixed_random_and_zero(torch_cuda, spfd, oracle_mod, seed, air):
         assert _oracle_psi_err(oracle_mod, ph, A[3], psi_b[3].cpu().numpy()) <= 1e-7
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_autotuned_orders_keep_results(torch_cuda, spfd, precision):
+    """Both block orders run the same arithmetic per block: the batch solved
+    with the autotuner's orders equals, bit for bit, the same batch in the
+    fixed order 0; the autotuner records one decision per tuned family and
+    level, for this batch size only."""
+    torch = torch_cuda
+    ph = body_phantom(64, 40, 224, h=8e-3)
+    loops = random_loops(4, np.random.default_rng(50))
+    A = _dev(torch, np.stack([loop_potential(ph.dims, ph.h, ph.origin, center=c, normal=n)
+                              for c, n in loops]))
+    prec = spfd.SPFD_FP64 if precision == "fp64" else spfd.SPFD_MIXED
+    sig = _dev(torch, ph.sigma)
+    with spfd.Solver(sig, ph.h, precision=prec) as S1, \
+            spfd.Solver(sig, ph.h, precision=prec, autotune=0) as S0:
+        p1, i1, st1 = S1.solve_batch(A, 1e-10)
+        p0, i0, st0 = S0.solve_batch(A, 1e-10)
+        assert st1 == st0 == spfd.SPFD_OK
+        assert torch.equal(p1, p0)
+        assert [i["iters"] for i in i1] == [i["iters"] for i in i0]
+        rep = S1.autotune_report()
+        nl = S1.info()["n_levels"]
+        # per non-coarsest level: first sweep, smooth, residual, restrict,
+        # prolong; apply_dot on level 0
+        assert len(rep) == 5 * (nl - 1) + 1
+        assert all(r["order"] in (0, 1) and r["nrhs"] == 4 for r in rep)
+        assert all(r["ms_order0"] > 0 and r["ms_order1"] > 0 for r in rep)
+        assert S0.autotune_report() == []
+        # a second batch of the same size reuses the decisions
+        S1.solve_batch(A, 1e-10)
+        assert len(S1.autotune_report()) == len(rep)
+
+
 def test_batch_argument_errors(torch_cuda, spfd):
     torch = torch_cuda
     rng = np.random.default_rng(43)
