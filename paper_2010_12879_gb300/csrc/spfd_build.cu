@@ -135,23 +135,24 @@ struct TableUpload {
 // twice as fast as the ratio of norms, so 8 steps match 16 of the latter.
 // The iterates are not normalised (they grow by at most 4^8), and nothing is
 // read back: the weights are formed on the device, lambda goes to *lam_dev.
-static spfd_status smoother_weights(spfd_ctx *c, int l, double *lam_dev) {
+static spfd_status smoother_weights(spfd_ctx *c, int l, double *lam_dev, Scalars *sc,
+                                   double *partials) {
   Level &lv = c->L[l];
   const int nb = lv.g.nb;
   cudaStream_t st = c->stream;
   if (nb == 0) return SPFD_OK;
-  if (!c->partials || !lv.st)
+  if (!partials || !lv.st)
     return fail(SPFD_EINTERNAL, "power iteration needs a 27-point level (%d)", l);
   double *v = lv.x, *w = lv.t;
   SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0, launch_power_init(nb, lv.diag, v, st));
   const int iters = 8;
   for (int it = 0; it < iters; ++it) {
     SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
-                launch_power27(lv.g, lv.st, lv.diag, lv.dinv, v, w, c->sc, c->partials, st));
+                launch_power27(lv.g, lv.st, lv.diag, lv.dinv, v, w, sc, partials, st));
     std::swap(v, w);
   }
   SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
-              launch_jacobi_weights(nb, lv.dinv, c->sc, 1.05, lv.wdinv, lam_dev, st));
+              launch_jacobi_weights(nb, lv.dinv, sc, 1.05, lv.wdinv, lam_dev, st));
   return launch_check("power iteration");
 }
 
@@ -336,45 +337,50 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
 }
 
 // FP32 / BF16 copies of the hierarchy for the mixed-precision solve.
-static spfd_status setup_mixed(spfd_ctx *c) {
+// FP32 / BF16 copies of level l for the mixed-precision solve, on
+// c->stream (levels are independent; level l needs its smoother weights).
+static spfd_status setup_mixed_level(spfd_ctx *c, int l) {
   cudaStream_t st = c->stream;
-  for (size_t l = 0; l < c->L.size(); ++l) {
-    Level &lv = c->L[l];
-    const size_t S = lv.S;
-    TRY(dalloc(c, &lv.x32, S));
-    TRY(dalloc(c, &lv.b32, S));
-    TRY(dalloc(c, &lv.r32, S));
-    TRY(dalloc(c, &lv.t32, S));
-    CU(cudaMemsetAsync(lv.x32, 0, S * sizeof(float), st));
-    CU(cudaMemsetAsync(lv.t32, 0, S * sizeof(float), st));
-    TRY(dalloc(c, &lv.wdinv32, S));
-    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.wdinv, 1.0, lv.wdinv32, st));
-    if (lv.Pc) {
-      TRY(dalloc(c, &lv.Pc32, 27 * (S / 8)));
-      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
-                  launch_convert<float>(27 * (S / 8), lv.Pc, 1.0, lv.Pc32, st));
-    }
-    if (l == 0) {
-      TRY(dalloc(c, &lv.gx32, 3 * S));
-      TRY(dalloc(c, &lv.gxbf, 3 * S));
-      TRY(dalloc(c, &lv.diag32, S));
-      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(3 * S, lv.gx, 1.0, lv.gx32, st));
-      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
-                  launch_convert<__nv_bfloat16>(3 * S, lv.gx, 1.0, lv.gxbf, st));
-      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
-    } else {
-      TRY(dalloc(c, &lv.st32, 27 * S));
-      TRY(dalloc(c, &lv.P32, 27 * S));
-      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
-      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
-    }
+  Level &lv = c->L[l];
+  const size_t S = lv.S;
+  TRY(dalloc(c, &lv.x32, S));
+  TRY(dalloc(c, &lv.b32, S));
+  TRY(dalloc(c, &lv.r32, S));
+  TRY(dalloc(c, &lv.t32, S));
+  CU(cudaMemsetAsync(lv.x32, 0, S * sizeof(float), st));
+  CU(cudaMemsetAsync(lv.t32, 0, S * sizeof(float), st));
+  TRY(dalloc(c, &lv.wdinv32, S));
+  SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.wdinv, 1.0, lv.wdinv32, st));
+  if (lv.Pc) {
+    TRY(dalloc(c, &lv.Pc32, 27 * (S / 8)));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
+                launch_convert<float>(27 * (S / 8), lv.Pc, 1.0, lv.Pc32, st));
   }
+  if (l == 0) {
+    TRY(dalloc(c, &lv.gx32, 3 * S));
+    TRY(dalloc(c, &lv.gxbf, 3 * S));
+    TRY(dalloc(c, &lv.diag32, S));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(3 * S, lv.gx, 1.0, lv.gx32, st));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
+                launch_convert<__nv_bfloat16>(3 * S, lv.gx, 1.0, lv.gxbf, st));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
+  } else {
+    TRY(dalloc(c, &lv.st32, 27 * S));
+    TRY(dalloc(c, &lv.P32, 27 * S));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
+  }
+  return launch_check("mixed-precision copies");
+}
+
+// The FP32 inner-solve vectors of the mixed-precision solve.
+static spfd_status setup_mixed_krylov(spfd_ctx *c) {
   const size_t S0 = c->L[0].S;
   TRY(dalloc(c, &c->dk32, S0));
   TRY(dalloc(c, &c->rk32, S0));
   TRY(dalloc(c, &c->pk32, S0));
   TRY(dalloc(c, &c->qk32, S0));
-  return launch_check("mixed-precision copies");
+  return SPFD_OK;
 }
 
 // Wall-clock phase marks of the build (printed with opts.verbose >= 2).
@@ -615,23 +621,78 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
 
   // smoother weights (weighted Jacobi): level 0 has D^-1 A the random-walk
   // Laplacian of a bipartite node graph, so lambda_max = 2 exactly and
-  // omega = 2/3; coarser levels estimate it on the device
-  for (size_t l = 0; l + 1 < c->L.size(); ++l) {
-    Level &lv = c->L[l];
-    if (l == 0) {
-      lv.lmax = 2.0;
-      lv.omega = 2.0 / 3.0;
-      SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
-                  launch_scaled_copy(lv.g.nb, lv.dinv, lv.omega, lv.wdinv, st));
-    } else {
-      TRY(smoother_weights(c, (int)l, lam + l));
+  // omega = 2/3; coarser levels estimate it on the device by power
+  // iterations.  Those are independent of one another and of the coarsest
+  // inverse, so each runs on a stream of its own (with its own reduction
+  // scratch) while the main stream assembles and inverts the coarsest level.
+  {
+    Level &l0 = c->L[0];
+    l0.lmax = 2.0;
+    l0.omega = 2.0 / 3.0;
+    SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
+                launch_scaled_copy(l0.g.nb, l0.dinv, l0.omega, l0.wdinv, st));
+    if (c->L.size() > 1) {
+      CU(cudaMemsetAsync(l0.x, 0, l0.S * sizeof(double), st));
+      CU(cudaMemsetAsync(l0.t, 0, l0.S * sizeof(double), st));
     }
-    CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), st));
-    CU(cudaMemsetAsync(lv.t, 0, lv.S * sizeof(double), st));
+  }
+  const int np = std::max(0, (int)c->L.size() - 2);  // levels 1 .. coarsest - 1
+  struct SideStreams {  // streams and events are released on every exit
+    spfd_ctx *c;
+    cudaStream_t main;
+    std::vector<cudaStream_t> s;
+    std::vector<cudaEvent_t> e;
+    ~SideStreams() {
+      c->stream = main;
+      for (cudaStream_t x : s) if (x) cudaStreamDestroy(x);
+      for (cudaEvent_t x : e) if (x) cudaEventDestroy(x);
+    }
+  };
+  // one stream per power iteration, plus one for level 0's mixed-precision
+  // copies; the last event is the fork point
+  const bool mixed = c->opts.precision == SPFD_MIXED;
+  const int ns = np + (mixed ? 1 : 0);
+  SideStreams side{c, st, std::vector<cudaStream_t>(ns, nullptr),
+                   std::vector<cudaEvent_t>(ns + 1, nullptr)};
+  Scalars *psc = nullptr;
+  double *ppart = nullptr;
+  const size_t part_per_level = 2 * 1024;  // grid_sum<2> over <= 1024 blocks
+  if (ns > 0) {
+    if (np > 0) {
+      TRY(dalloc(c, &psc, np));
+      TRY(dalloc(c, &ppart, part_per_level * np));
+      CU(cudaMemsetAsync(psc, 0, np * sizeof(Scalars), st));
+    }
+    CU(cudaEventCreateWithFlags(&side.e[ns], cudaEventDisableTiming));
+    CU(cudaEventRecord(side.e[ns], st));
+    for (int i = 0; i < ns; ++i) {
+      CU(cudaStreamCreateWithFlags(&side.s[i], cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&side.e[i], cudaEventDisableTiming));
+      CU(cudaStreamWaitEvent(side.s[i], side.e[ns], 0));
+      c->stream = side.s[i];
+      if (i < np) {
+        const int l = i + 1;
+        Level &lv = c->L[l];
+        TRY(smoother_weights(c, l, lam + l, psc + i, ppart + part_per_level * i));
+        CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), side.s[i]));
+        CU(cudaMemsetAsync(lv.t, 0, lv.S * sizeof(double), side.s[i]));
+        if (mixed) TRY(setup_mixed_level(c, l));
+      } else {
+        TRY(setup_mixed_level(c, 0));
+      }
+      CU(cudaEventRecord(side.e[i], side.s[i]));
+      c->stream = st;
+    }
+  } else if (mixed) {
+    TRY(setup_mixed_level(c, 0));
   }
   clk.mark("smoother weights");
   TRY(setup_coarsest(c));
   clk.mark("coarsest inverse");
+  if (mixed && c->L.size() > 1) TRY(setup_mixed_level(c, (int)c->L.size() - 1));
+  for (int i = 0; i < ns; ++i) CU(cudaStreamWaitEvent(st, side.e[i], 0));
+  dfree(c, psc);
+  dfree(c, ppart);
 
   // Krylov vectors
   TRY(dalloc(c, &c->xk, S0));
@@ -639,7 +700,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   TRY(dalloc(c, &c->pk, S0));
   TRY(dalloc(c, &c->qk, S0));
   TRY(dalloc(c, &c->bk, S0));
-  if (c->opts.precision == SPFD_MIXED) TRY(setup_mixed(c));
+  if (mixed) TRY(setup_mixed_krylov(c));
   clk.mark("vectors+mixed");
   // read back the device status and the smoother estimates, then clear the
   // scalars for the solves
