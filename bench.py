@@ -314,6 +314,10 @@ def run_ours(args):
     if not args.no_group:
         group = bench_group(spfd, torch, dev, stream, ph, sig, ad, max(1, min(K, 5)), W)
 
+    body1 = None
+    if not args.no_1mm:
+        body1 = bench_body_1mm(spfd, torch, dev, stream, 2, 1)
+
     batch = None
     if not args.no_batch:
         batch = bench_batch(spfd, torch, dev, stream, ph, sig, args.batch_rhs,
@@ -379,6 +383,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "percentile": pct,
             "group": group,
+            "body_1mm": body1,
             "batch": batch,
             "kernels_fp64": {k: {"launches": v["launches"] // KP, "ms": round(v["ms"] / KP, 4),
                                  "GBs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
@@ -445,6 +450,64 @@ def uneven_phantom_dims(n=12):
         t = i / (n - 1)
         out.append(tuple(int(round((lo + t * (hi - lo)) / 32.0)) * 32
                          for lo, hi in ((64, 192), (64, 128), (128, 640))))
+    return out
+
+
+def bench_body_1mm(spfd, torch, dev, stream, K, W):
+    """The second workload: the same ellipsoid body at h = 1 mm (512 x 320 x
+    1792 voxels, 71.6 M conducting voxels, ~74 M unknowns), the same 40
+    seeded tissues and loop source, on one GPU.  Per precision, W + K steps
+    of build + solve to TOL + |E| + the per-tissue 99th percentile, each
+    timed with CUDA events on the stream.  The loop's edge potentials are
+    generated on the device."""
+    import numpy as np
+
+    from spfd_inputs import body_phantom
+    from spfd_inputs.sources_torch import loop_potential_t
+    t0 = time.perf_counter()
+    ph = body_phantom(512, 320, 1792, h=1e-3)
+    gen_s = time.perf_counter() - t0
+    sig = torch.from_numpy(ph.sigma).to(dev)
+    lab = torch.from_numpy(ph.labels.astype(np.int32)).to(dev)
+    nlab = int(ph.tissue_sigma.size)
+    a = loop_potential_t(ph.dims, ph.h, ph.origin, device=dev)
+    nz, ny, nx = ph.sigma.shape
+    psi = torch.empty((nz + 1, ny + 1, nx + 1), dtype=torch.float64, device=dev)
+    E = torch.empty((nz, ny, nx), dtype=torch.float64, device=dev)
+    out = {"workload": "body phantom 512x320x1792 voxels, h=1 mm, 40 tissues, loop source "
+                       "R=0.3 m, I=1000 A, 0.4 m below; FP64 / mixed to 1e-8",
+           "conducting_voxels": int((ph.sigma > 0).sum()),
+           "phantom_generation_s_host": round(gen_s, 1), "steps": K, "warmup": W}
+    for name, prec in (("fp64", spfd.SPFD_FP64), ("mixed", spfd.SPFD_MIXED)):
+        rec = []
+        for i in range(W + K):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            e[0].record(stream)
+            S = spfd.Solver(sig, ph.h, stream=stream, precision=prec)
+            e[1].record(stream)
+            _, info, st = S.solve(a, TOL, psi)
+            e[2].record(stream)
+            S.efield(a, psi, OMEGA, E)
+            e[3].record(stream)
+            vals, _ = S.percentile(E, lab, nlab, 0.99)
+            e[4].record(stream)
+            torch.cuda.synchronize(dev)
+            bi = S.info()
+            S.close()
+            assert st == spfd.SPFD_OK and info["converged"], spfd.spfd_last_error()
+            if i >= W:
+                rec.append([e[q].elapsed_time(e[q + 1]) for q in range(4)] +
+                           [e[0].elapsed_time(e[4])])
+        m = [statistics.mean(r[q] for r in rec) for q in range(5)]
+        out[name] = {"build_ms": round(m[0], 2), "solve_ms": round(m[1], 2),
+                     "efield_ms": round(m[2], 2), "percentile_ms": round(m[3], 2),
+                     "step_ms": round(m[4], 2), "iters": info["iters"],
+                     "outer_iters": info["outer_iters"], "rel_res_true": info["rel_res_true"],
+                     "n_dof": int(bi["n_dof"]), "n_levels": int(bi["n_levels"]),
+                     "context_bytes_device": int(bi["bytes_device"]),
+                     "p99_body_V_per_m": vals[nlab]}
+    del sig, lab, a, psi, E
+    torch.cuda.empty_cache()
     return out
 
 
@@ -721,6 +784,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-percentile", action="store_true")
     ap.add_argument("--no-group", action="store_true")
+    ap.add_argument("--no-1mm", action="store_true")
     ap.add_argument("--batch-rhs", type=int, default=64,
                     help="source fields of the batched-solve sub-object")
     ap.add_argument("--ncu-step", choices=["fp64", "mixed"], default=None,
