@@ -516,8 +516,9 @@ def bench_group(spfd, torch, dev, stream, ph, sig, ad, K, W):
     scaled to boxes from 64x64x128 to 192x128x640 voxels (h = 2 mm, tissues
     seeded as for the 2 mm body), one loop source each, solved to TOL
     (a) one after the other with spfd_solve and (b) together by one launch of
-    the group's captured graph (spfd_group_solve); plus the 2 mm body alone,
-    host-driven against its captured graph.  CUDA events on the stream."""
+    the group's captured graph (spfd_group_solve), in FP64 and in the mixed
+    form; plus the 2 mm body alone, host-driven against its captured graph.
+    CUDA events on the stream."""
     from spfd_inputs import loop_potential, scaled_body_phantom
     dims = uneven_phantom_dims()
     phs = [scaled_body_phantom(*d) for d in dims]
@@ -539,15 +540,14 @@ def bench_group(spfd, torch, dev, stream, ph, sig, ad, K, W):
             rec.append(e[0].elapsed_time(e[1]))
         return statistics.mean(rec), out
 
-    def sequential():
-        infos = []
-        for S, a, p in zip(solvers, A, psis):
-            _, info, st = S.solve(a, TOL, p)
-            assert st == spfd.SPFD_OK, spfd.spfd_last_error()
-            infos.append(info)
-        return infos
-
-    try:
+    def seq_and_group(solvers):
+        def sequential():
+            infos = []
+            for S, a, p in zip(solvers, A, psis):
+                _, info, st = S.solve(a, TOL, p)
+                assert st == spfd.SPFD_OK, spfd.spfd_last_error()
+                infos.append(info)
+            return infos
         ms_seq, infos_seq = timed(sequential, K, W)
         ref = [p.clone() for p in psis]
         with spfd.Group(solvers, stream=stream) as G:
@@ -560,6 +560,15 @@ def bench_group(spfd, torch, dev, stream, ph, sig, ad, K, W):
             capture_ms = (time.perf_counter() - t0) * 1e3
             ms_grp, infos_grp = timed(grouped, K, W)
             same = all(torch.equal(a, b) for a, b in zip(ref, psis))
+        return ms_seq, infos_seq, ms_grp, infos_grp, capture_ms, same
+
+    try:
+        ms_seq, infos_seq, ms_grp, infos_grp, capture_ms, same = seq_and_group(solvers)
+        for S in solvers:
+            S.close()
+        solvers = [spfd.Solver(s, p.h, stream=stream, precision=spfd.SPFD_MIXED)
+                   for s, p in zip(sigs, phs)]
+        mx = seq_and_group(solvers)
         # the 2 mm body alone: host-driven solve against its captured graph
         psi_b = torch.empty((ph.sigma.shape[0] + 1, ph.sigma.shape[1] + 1,
                              ph.sigma.shape[2] + 1), dtype=torch.float64, device=dev)
@@ -581,6 +590,13 @@ def bench_group(spfd, torch, dev, stream, ph, sig, ad, K, W):
             "graph_launches_per_group_solve": 1,
             "kernels_in_graph": int(infos_grp[0]["launches"]),
             "bit_identical_to_sequential": bool(same),
+            "mixed": {"sequential_ms": round(mx[0], 3), "group_graph_ms": round(mx[2], 3),
+                      "speedup_group_vs_sequential": round(mx[0] / mx[2], 3),
+                      "group_capture_ms": round(mx[4], 1),
+                      "iters": [int(i["iters"]) for i in mx[3]],
+                      "outer_iters": [int(i["outer_iters"]) for i in mx[3]],
+                      "bit_identical_to_sequential": bool(mx[5]),
+                      "group_mixed_vs_group_fp64": round(ms_grp / mx[2], 3)},
             "body_2mm": {"host_driven_solve_ms": round(ms_bh, 3),
                          "graph_solve_ms": round(ms_bg, 3),
                          "iters": int(ibg["iters"]), "rel_res_true": ibg["rel_res_true"]},

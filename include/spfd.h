@@ -212,8 +212,8 @@ spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev, const int32_t *l
  *
  * A group holds contexts built for different bodies (for example phantoms of
  * different sizes) and solves Eq. 3 (Sec. II) on all of them at once.  The
- * FP64 solve of each context (the same steps as spfd_solve) is captured as
- * one branch of a single graph whose CG loop runs on the GPU: control
+ * solve of each context (the same steps as spfd_solve, FP64 or mixed) is
+ * captured as one branch of a single graph whose loops run on the GPU: control
  * kernels decide, between iterations, to check the true residual, restart or
  * stop, through the graph's conditional nodes, so the host launches the
  * graph once and synchronises once per group solve.  Each Psi equals what
@@ -222,9 +222,10 @@ spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev, const int32_t *l
  * throughput form of the same solve.
  *
  * spfd_group_create
- *   ctxs    n distinct contexts (1..4096) on one device, each built with
- *           opts.precision = SPFD_FP64 (else SPFD_EINVAL).  The group keeps
- *           the pointers: destroy the group before any of its contexts.
+ *   ctxs    n distinct contexts (1..4096) on one device, of either precision
+ *           (a SPFD_MIXED context's branch runs its refinement as nested
+ *           device-driven loops).  The group keeps the pointers: destroy the
+ *           group before any of its contexts.
  *   stream  cudaStream_t the group launches on (NULL = legacy default
  *           stream); work already queued on the contexts' streams runs
  *           first.

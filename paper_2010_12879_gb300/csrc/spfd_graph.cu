@@ -1,6 +1,7 @@
-// Device-driven solves: the FP64 solve of Eq. 3 (Sec. II) captured as one
-// CUDA graph whose CG loop runs on the GPU, and groups of bodies (phantoms
-// of different sizes) solved together by one launch of such a graph.
+// Device-driven solves: the FP64 solve of Eq. 3 (Sec. II), or its
+// mixed-precision refinement, captured as one CUDA graph whose loops run on
+// the GPU, and groups of bodies (phantoms of different sizes) solved together
+// by one launch of such a graph.
 //
 // The host-driven solve (spfd_api.cu) reads the CG scalars back after every
 // iteration to decide whether to stop, check the true residual or restart.
@@ -22,6 +23,12 @@
 // decision compares the same FP64 values the host compares, so a graph solve
 // returns the same Psi, bit for bit, with the same iteration count.
 //
+// The mixed-precision form nests the same pattern: a WHILE node over the FP64
+// refinement steps (scale of the FP32 residual and inner target on the
+// device), inside it a WHILE node over the FP32 CG iterations stopped on the
+// recursive residual, then x += scale d, the true residual and the decision
+// to refine again, exactly as the host-driven refinement takes them.
+//
 // A group captures one such branch per context, side by side in one graph,
 // so the bodies' kernels share the GPU (small bodies fill what a large one
 // leaves idle) and the whole group costs one graph launch and one host
@@ -41,6 +48,19 @@ struct GraphCtl {
   double rel;       // last true relative residual
   int maxit;        // iteration cap (set per solve)
   int it, stall, done, conv, broke, bad;
+  // mixed precision: FP64 refinement state and the FP32 inner CG's
+  double nrm2;      // |r|^2 of the current FP64 residual
+  double nr, inv_nr;  // its norm and 1 / norm (scale of the FP32 copy)
+  double eta;       // inner relative target
+  double prev;      // smallest true relative residual so far
+  double bb_in;     // |r32|^2 of the scaled FP32 residual
+  double min_rrel_in;
+  int total;        // inner iterations so far
+  int outer;        // refinement step in progress
+  int outer_of;     // refinement steps taken when the solve stopped
+  int it_in;        // inner iterations of this step
+  int cap;          // inner iteration budget of this step
+  int idone;        // the inner CG has stopped
 };
 
 namespace {
@@ -116,6 +136,98 @@ __global__ void k_ctl_after(const GraphCtl *g, cudaGraphConditionalHandle final_
 __global__ void k_ctl_final(GraphCtl *g, const Scalars *sc) {
   g->rel = sqrt(sc->aux[2] / g->bb);
 }
+
+// ------------------------------------------- mixed precision (refinement)
+__global__ void k_mctl_init(GraphCtl *g, const Scalars *sc, cudaGraphConditionalHandle outer) {
+  g->bb = sc->aux[1];
+  g->bad = (sc->status & DEV_BAD_A) != 0;
+  const bool run = !g->bad && g->bb > 0.0;
+  g->done = run ? 0 : 1;
+  g->conv = (!g->bad && !(g->bb > 0.0)) ? 1 : 0;
+  g->nrm2 = g->bb;
+  g->prev = INFINITY;
+  g->rel = 0.0;
+  g->stall = 0;
+  g->total = 0;
+  g->outer = 0;
+  g->outer_of = 0;
+  cudaGraphSetConditional(outer, run ? 1u : 0u);
+}
+
+// Start of a refinement step: stop past 30 steps or the iteration budget,
+// else the scale of the FP32 copy and the inner target.
+__global__ void k_mctl_begin(GraphCtl *g, cudaGraphConditionalHandle outer,
+                             cudaGraphConditionalHandle go) {
+  g->outer += 1;
+  const bool stop = g->outer > 30 || g->total >= g->maxit;
+  if (stop) {
+    g->done = 1;
+    g->outer_of = min(g->outer, 30);
+  } else {
+    g->nr = sqrt(g->nrm2);
+    g->inv_nr = 1.0 / g->nr;
+    // what is still missing for tol, but no tighter than what an FP32 solve
+    // reliably reaches
+    g->eta = fmin(0.5, fmax(0.5 * g->tol * sqrt(g->bb) / g->nr, 1e-4));
+  }
+  cudaGraphSetConditional(outer, stop ? 0u : 1u);
+  cudaGraphSetConditional(go, stop ? 0u : 1u);
+}
+
+// Inner CG start (|r32|^2 in aux[3]).
+__global__ void k_ictl_init(GraphCtl *g, const Scalars *sc, cudaGraphConditionalHandle inner) {
+  g->bb_in = sc->aux[3];
+  g->it_in = 0;
+  g->min_rrel_in = INFINITY;
+  g->cap = g->maxit - g->total;
+  g->idone = g->bb_in > 0.0 ? 0 : 1;
+  cudaGraphSetConditional(inner, g->idone ? 0u : 1u);
+}
+
+// After an inner x / r update: stopped on the recursive residual.
+__global__ void k_ictl_iter(GraphCtl *g, Scalars *sc, cudaGraphConditionalHandle inner,
+                            cudaGraphConditionalHandle prec) {
+  g->it_in += 1;
+  const double rrel = sqrt(sc->rr / g->bb_in);
+  if (!isfinite(rrel) || rrel > 1e8 * fmax(g->min_rrel_in, g->eta)) {
+    g->idone = 1;
+  } else {
+    g->min_rrel_in = fmin(g->min_rrel_in, rrel);
+    if (rrel <= g->eta) g->idone = 1;
+  }
+  if (!g->idone && g->it_in >= g->cap) g->idone = 1;
+  if (g->idone) sc->frozen = 1;
+  cudaGraphSetConditional(prec, g->idone ? 0u : 1u);
+  cudaGraphSetConditional(inner, g->idone ? 0u : 1u);
+}
+
+__global__ void k_mctl_mid(GraphCtl *g) { g->total += g->it_in; }
+
+// After the true residual of the refined x (|b - A x|^2 in aux[2]).
+__global__ void k_mctl_check(GraphCtl *g, const Scalars *sc, cudaGraphConditionalHandle outer,
+                             cudaGraphConditionalHandle next) {
+  const double rel = sqrt(sc->aux[2] / g->bb);
+  g->rel = rel;
+  bool stop = false;
+  if (rel <= g->tol) {
+    g->conv = 1;
+    stop = true;
+  } else if (rel > 0.5 * g->prev) {
+    if (++g->stall >= 2) stop = true;
+  } else {
+    g->stall = 0;
+  }
+  if (stop) {
+    g->done = 1;
+    g->outer_of = g->outer;
+  } else {
+    g->prev = fmin(g->prev, rel);
+  }
+  cudaGraphSetConditional(outer, stop ? 0u : 1u);
+  cudaGraphSetConditional(next, stop ? 0u : 1u);
+}
+
+__global__ void k_mctl_nrm(GraphCtl *g, const Scalars *sc) { g->nrm2 = sc->aux[3]; }
 
 // ---------------------------------------------------------------- capture
 cudaGraph_t capture_graph(cudaStream_t s, const cudaGraphNode_t **deps, size_t *nd) {
@@ -313,6 +425,122 @@ spfd_status capture_solve_fp64(spfd_ctx *c, GraphCtl *ctl, const double *a, doub
   return SPFD_OK;
 }
 
+// One branch: the mixed-precision solve of context c (the steps of the
+// host-driven refinement), captured on c->stream; body[0..3] are free
+// streams for the nested conditional bodies.
+spfd_status capture_solve_mixed(spfd_ctx *c, GraphCtl *ctl, const double *a, double *psi,
+                                cudaStream_t body[4], cudaGraphNode_t *rhs_node,
+                                cudaGraphNode_t *scatter_node) {
+  Level &l0 = c->L[0];
+  const size_t S0 = l0.S;
+  const double S = (double)S0;
+  const int nb = l0.g.nb;
+  cudaStream_t s0 = c->stream;
+  CU(cudaMemsetAsync(&c->sc->status, 0, sizeof(int), s0));
+  SPFD_LAUNCH(c, "rhs", false, 1, 56 * S, 12 * S,
+              launch_rhs(l0.g, l0.gx, a, c->bk, &c->sc->status, s0, 1));
+  TRY(launch_check("rhs"));
+  TRY(last_node(s0, rhs_node));
+  TRY(project<double>(c, c->bk, 1, 0));
+  SPFD_LAUNCH(c, "project", false, 1, 20 * S, 2 * S,
+              launch_dot<double>(nb, c->bk, c->bk, c->comp, c->sc, c->partials, 1, s0, 1,
+                                 c->pstride));
+  CU(cudaMemsetAsync(c->xk, 0, S0 * sizeof(double), s0));
+  CU(cudaMemcpyAsync(c->rk, c->bk, S0 * sizeof(double), cudaMemcpyDeviceToDevice, s0));
+  cudaGraphConditionalHandle h_outer;
+  TRY(new_handle(s0, &h_outer));
+  k_mctl_init<<<1, 1, 0, s0>>>(ctl, c->sc, h_outer);
+  TRY(launch_check("control"));
+  TRY(cond_begin(s0, h_outer, cudaGraphCondTypeWhile, body[0]));
+  {
+    cudaStream_t s1 = body[0];
+    c->stream = s1;
+    cudaGraphConditionalHandle h_go;
+    TRY(new_handle(s1, &h_go));
+    k_mctl_begin<<<1, 1, 0, s1>>>(ctl, h_outer, h_go);
+    TRY(launch_check("control"));
+    TRY(cond_begin(s1, h_go, cudaGraphCondTypeIf, body[1]));
+    {
+      cudaStream_t s2 = body[1];
+      c->stream = s2;
+      CU(cudaMemsetAsync(c->dk32, 0, S0 * sizeof(float), s2));
+      SPFD_LAUNCH(c, "convert", true, 1, 12 * S, S,
+                  launch_scale_to_f32(nb, c->rk, 0.0, c->rk32, c->sc, c->partials, s2,
+                                      &ctl->inv_nr));
+      SPFD_LAUNCH(c, "project", true, 1, 12 * S, 2 * S,
+                  launch_dot<float>(nb, c->rk32, c->rk32, c->comp, c->sc, c->partials, 3, s2,
+                                    1, c->pstride));
+      // the inner FP32 CG
+      CU(cudaMemsetAsync(c->pk32, 0, S0 * sizeof(float), s2));
+      TRY(batch_flags(c, 0, 1, 0, 0, 0));
+      cudaGraphConditionalHandle h_inner, h_next;
+      TRY(new_handle(s2, &h_inner));
+      TRY(new_handle(s2, &h_next));
+      k_ictl_init<<<1, 1, 0, s2>>>(ctl, c->sc, h_inner);
+      TRY(launch_check("control"));
+      TRY(precondition_step<float>(c, c->rk32, c->pk32, 1, 1));
+      TRY(cond_begin(s2, h_inner, cudaGraphCondTypeWhile, body[2]));
+      {
+        cudaStream_t s3 = body[2];
+        c->stream = s3;
+        SPFD_LAUNCH(c, "apply_dot", true, 1, 5 * 4 * S, 20 * S,
+                    launch_apply_dot<float>(l0.g, l0.gx32, l0.diag32, c->pk32, c->qk32, c->sc,
+                                            c->partials, s3, 1, c->pstride));
+        SPFD_LAUNCH(c, "finish_pq", false, 1, 8.0 * nb, nb,
+                    launch_finish_pq(apply_dot_partials<float>(nb), c->partials,
+                                     c->partials + (size_t)16 * nb, c->sc, s3, 1, c->pstride));
+        SPFD_LAUNCH(c, "update_xr", true, 1, 6 * 4 * S, 7 * S,
+                    launch_update_xr<float>(nb, c->dk32, c->rk32, c->pk32, c->qk32, c->sc,
+                                            c->partials, s3, 1, c->pstride));
+        cudaGraphConditionalHandle h_iprec;
+        TRY(new_handle(s3, &h_iprec));
+        k_ictl_iter<<<1, 1, 0, s3>>>(ctl, c->sc, h_inner, h_iprec);
+        TRY(launch_check("control"));
+        TRY(cond_begin(s3, h_iprec, cudaGraphCondTypeIf, body[3]));
+        c->stream = body[3];
+        TRY(precondition_step<float>(c, c->rk32, c->pk32, 0, 1));
+        TRY(cond_end(body[3]));
+        c->stream = s3;
+      }
+      TRY(cond_end(body[2]));
+      c->stream = s2;
+      k_mctl_mid<<<1, 1, 0, s2>>>(ctl);
+      TRY(launch_check("control"));
+      SPFD_LAUNCH(c, "convert", false, 1, 20 * S, 2 * S,
+                  launch_axpy_mixed(nb, c->xk, c->dk32, 0.0, s2, &ctl->nr));
+      TRY(enqueue_true_residual(c));
+      k_mctl_check<<<1, 1, 0, s2>>>(ctl, c->sc, h_outer, h_next);
+      TRY(launch_check("control"));
+      TRY(cond_begin(s2, h_next, cudaGraphCondTypeIf, body[2]));
+      {
+        // the next correction solves for the true residual (in level 0's r)
+        c->stream = body[2];
+        CU(cudaMemcpyAsync(c->rk, l0.r, S0 * sizeof(double), cudaMemcpyDeviceToDevice,
+                           body[2]));
+        TRY(project<double>(c, c->rk, 1, 0));
+        SPFD_LAUNCH(c, "project", false, 1, 20 * S, 2 * S,
+                    launch_dot<double>(nb, c->rk, c->rk, c->comp, c->sc, c->partials, 3,
+                                       body[2], 1, c->pstride));
+        k_mctl_nrm<<<1, 1, 0, body[2]>>>(ctl, c->sc);
+        TRY(launch_check("control"));
+      }
+      TRY(cond_end(body[2]));
+      c->stream = s2;
+    }
+    TRY(cond_end(body[1]));
+    c->stream = s1;
+  }
+  TRY(cond_end(body[0]));
+  c->stream = s0;
+  TRY(project<double>(c, c->xk, 1, 0));
+  const double NN = (double)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  SPFD_LAUNCH(c, "scatter", false, 1, 8 * NN + 12.0 * S, 0,
+              launch_scatter<double>(l0.g, c->xk, c->comp, psi, s0, 1));
+  TRY(launch_check("scatter"));
+  TRY(last_node(s0, scatter_node));
+  return SPFD_OK;
+}
+
 }  // namespace spfd
 
 using namespace spfd;
@@ -323,7 +551,7 @@ struct spfd_group {
   std::vector<spfd_ctx *> ctx;
   std::vector<uint64_t> gen;            // buffer generation of each context at capture
   std::vector<cudaStream_t> branch;     // capture stream per context
-  cudaStream_t origin = nullptr, body[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t origin = nullptr, body[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> join;
   cudaGraph_t graph = nullptr;
@@ -368,8 +596,11 @@ spfd_status capture_group(spfd_group *g, const double *const *a, double *const *
     if (e != cudaSuccess) break;
     c->stream = g->branch[i];
     c->opts.profile = 0;  // no event nodes inside the graph
-    s = capture_solve_fp64(c, g->dctl + i, a[i], psi[i], g->body, &g->rhs_node[i],
-                           &g->scatter_node[i]);
+    s = c->opts.precision == SPFD_MIXED
+            ? capture_solve_mixed(c, g->dctl + i, a[i], psi[i], g->body, &g->rhs_node[i],
+                                  &g->scatter_node[i])
+            : capture_solve_fp64(c, g->dctl + i, a[i], psi[i], g->body, &g->rhs_node[i],
+                                 &g->scatter_node[i]);
     c->stream = saved[i];
     c->opts.profile = prof[i];
     if (s != SPFD_OK) break;
@@ -440,8 +671,6 @@ extern "C" spfd_status spfd_group_create(spfd_ctx *const *ctxs, int n, void *str
   int dev = -1;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(SPFD_EINVAL, "context %d is NULL", i);
-    if (ctxs[i]->opts.precision != SPFD_FP64)
-      return fail(SPFD_EINVAL, "context %d: group solves run the FP64 path", i);
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(SPFD_EINVAL, "context %d appears twice", i);
     if (dev < 0) dev = ctxs[i]->device;
@@ -462,7 +691,7 @@ extern "C" spfd_status spfd_group_create(spfd_ctx *const *ctxs, int n, void *str
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking)) != cudaSuccess)
     return bad(e);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 4; ++i)
     if ((e = cudaStreamCreateWithFlags(&g->body[i], cudaStreamNonBlocking)) != cudaSuccess)
       return bad(e);
   for (int i = 0; i < n; ++i) {
@@ -535,8 +764,9 @@ extern "C" spfd_status spfd_group_solve(spfd_group *g, const double *const *a_de
     const GraphCtl &h = g->hctl[i];
     spfd_info r = c->info;
     const bool empty = c->ndof == 0;
-    r.iters = empty ? 0 : h.it;
-    r.outer_iters = 0;
+    const bool mixed = c->opts.precision == SPFD_MIXED;
+    r.iters = empty ? 0 : (mixed ? h.total : h.it);
+    r.outer_iters = empty || !mixed ? 0 : h.outer_of;
     r.converged = empty ? 1 : h.conv;
     r.rel_res_true = empty ? 0.0 : h.rel;
     r.ms_solve = ms;
@@ -552,8 +782,8 @@ extern "C" spfd_status spfd_group_solve(spfd_group *g, const double *const *a_de
                 first_bad);
   if (first_nc >= 0)
     return fail(SPFD_ENOTCONVERGED,
-                "not converged: context %d at rel residual %.3e after %d iterations", first_nc,
-                g->hctl[first_nc].rel, g->hctl[first_nc].it);
+                "not converged: context %d at rel residual %.3e", first_nc,
+                g->hctl[first_nc].rel);
   return SPFD_OK;
 }
 

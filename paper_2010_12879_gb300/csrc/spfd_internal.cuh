@@ -276,10 +276,13 @@ void launch_efield(const unsigned char *mask, const double *a,
 template <typename T>
 void launch_convert(size_t n, const double *src, double f, T *dst,
                     cudaStream_t st);
+// x += f d (f from *fdev when fdev is not null: device-driven solves).
 void launch_axpy_mixed(int nb, double *x, const float *d, double f,
-                       cudaStream_t st);
+                       cudaStream_t st, const double *fdev = nullptr);
+// r32 = (float)(f r), sum(r32) into sc (f from *fdev when fdev is not null).
 void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
-                         Scalars *sc, double *partials, cudaStream_t st);
+                         Scalars *sc, double *partials, cudaStream_t st,
+                         const double *fdev = nullptr);
 void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st);
 // w = D^-1 A v on a 27-point level; sc->aux[4] = v.(A v), sc->aux[5] = v.(D v).
 void launch_power27(const Grid &g, const double *st27, const double *diag,

@@ -842,7 +842,9 @@ __global__ void k_convert<__nv_bfloat16>(size_t n, const double *__restrict__ sr
 
 // x += f * d (FP64 accumulation of an FP32 correction) on level-0 slots.
 __global__ void __launch_bounds__(NT)
-k_axpy_mixed(double *__restrict__ x, const float *__restrict__ d, double f) {
+k_axpy_mixed(double *__restrict__ x, const float *__restrict__ d, double f,
+             const double *__restrict__ fdev) {
+  if (fdev) f = *fdev;
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
   x[s] += f * (double)d[s];
 }
@@ -851,7 +853,9 @@ k_axpy_mixed(double *__restrict__ x, const float *__restrict__ d, double f) {
 // for the fused projection of the first V-cycle sweep.
 __global__ void __launch_bounds__(NT)
 k_scale_to_f32(int nb, const double *__restrict__ r, double f,
-               float *__restrict__ r32, Scalars *sc, double *partials) {
+               const double *__restrict__ fdev, float *__restrict__ r32, Scalars *sc,
+               double *partials) {
+  if (fdev) f = *fdev;
   Acc<float> acc;
   for (int bk = blockIdx.x; bk < nb; bk += gridDim.x) {
     const size_t s = (size_t)bk * BV + threadIdx.x;
@@ -881,12 +885,13 @@ template void launch_convert<float>(size_t, const double *, double, float *, cud
 template void launch_convert<__nv_bfloat16>(size_t, const double *, double,
                                             __nv_bfloat16 *, cudaStream_t);
 void launch_axpy_mixed(int nb, double *x, const float *d, double f,
-                       cudaStream_t st) {
-  if (nb) k_axpy_mixed<<<nb, NT, 0, st>>>(x, d, f);
+                       cudaStream_t st, const double *fdev) {
+  if (nb) k_axpy_mixed<<<nb, NT, 0, st>>>(x, d, f, fdev);
 }
 void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
-                         Scalars *sc, double *partials, cudaStream_t st) {
-  if (nb) k_scale_to_f32<<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, f, r32, sc, partials);
+                         Scalars *sc, double *partials, cudaStream_t st, const double *fdev) {
+  if (nb)
+    k_scale_to_f32<<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, f, fdev, r32, sc, partials);
 }
 void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st) {
   if (nb) k_power_init<<<nb, NT, 0, st>>>(diag, v);
