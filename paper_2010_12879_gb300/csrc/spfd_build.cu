@@ -39,15 +39,6 @@ static spfd_status host_level(Level &lv, int NX, int NY, int NZ,
     return fail(SPFD_EINVAL, "grid too large: %zu active bricks", lv.hbco.size());
   g.nb = (int)lv.hbco.size();
   lv.S = (size_t)g.nb * BV;
-  lv.hnbr.assign((size_t)std::max(g.nb, 1) * 27, -1);
-  for (int b = 0; b < g.nb; ++b) {
-    const int4 bc = lv.hbco[b];
-    for (int e = 0; e < 27; ++e) {
-      const int x = bc.x + e % 3 - 1, y = bc.y + (e / 3) % 3 - 1, z = bc.z + e / 9 - 1;
-      if (x < 0 || y < 0 || z < 0 || x >= g.MX || y >= g.MY || z >= g.MZ) continue;
-      lv.hnbr[(size_t)b * 27 + e] = lv.hbmap[((size_t)z * g.MY + y) * g.MX + x];
-    }
-  }
   return SPFD_OK;
 }
 
@@ -69,31 +60,6 @@ static void coarse_flags(const Level &f, int *CX, int *CY, int *CZ,
               any = f.hbmap[((size_t)fz * fg.MY + fy) * fg.MX + fx] >= 0;
         (*cfl)[((size_t)bz * cMY + by) * cMX + bx] = any;
       }
-}
-
-// Transfer tables between fine level f and its coarse level cl (host only):
-// for each coarse brick the 27 fine bricks its 17^3 fine support touches,
-// and for each fine brick the 8 coarse bricks that hold its parents.
-static void host_transfer(Level &f, Level &cl) {
-  const Grid &fg = f.g, &cg = cl.g;
-  cl.hkid.assign((size_t)std::max(cg.nb, 1) * 27, -1);
-  for (int b = 0; b < cg.nb; ++b) {
-    const int4 bc = cl.hbco[b];
-    for (int o = 0; o < 27; ++o) {
-      const int x = 2 * bc.x + o % 3 - 1, y = 2 * bc.y + (o / 3) % 3 - 1, z = 2 * bc.z + o / 9 - 1;
-      if (x < 0 || y < 0 || z < 0 || x >= fg.MX || y >= fg.MY || z >= fg.MZ) continue;
-      cl.hkid[(size_t)b * 27 + o] = f.hbmap[((size_t)z * fg.MY + y) * fg.MX + x];
-    }
-  }
-  f.hpar.assign((size_t)std::max(fg.nb, 1) * 8, -1);
-  for (int b = 0; b < fg.nb; ++b) {
-    const int4 bc = f.hbco[b];
-    for (int o = 0; o < 8; ++o) {
-      const int x = (bc.x >> 1) + (o & 1), y = (bc.y >> 1) + ((o >> 1) & 1), z = (bc.z >> 1) + (o >> 2);
-      if (x >= cg.MX || y >= cg.MY || z >= cg.MZ) continue;
-      f.hpar[(size_t)b * 8 + o] = cl.hbmap[((size_t)z * cg.MY + y) * cg.MX + x];
-    }
-  }
 }
 
 // One asynchronous upload of host tables: each (host vector, device slot)
@@ -440,9 +406,14 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     Level &l0 = c->L[0];
     up.add(l0.hbmap, &l0.g.bmap);
     up.add(l0.hbco, &l0.g.bco);
-    up.add(l0.hnbr, &l0.g.nbr);
     TRY(up.run(c));
+    int *nbr = nullptr;
+    TRY(dalloc(c, &nbr, (size_t)std::max(l0.g.nb, 1) * 27));
+    launch_brick_nbr(l0.g, nbr, st);
+    c->launch_count += l0.g.nb ? 1 : 0;
+    l0.g.nbr = nbr;
   }
+  clk.mark("level-0 tables");
   const size_t S0 = c->L[0].S;
   const int nb0 = c->L[0].g.nb;
   // reduction scratch: the level-0 CG operator writes 4 partials per brick
@@ -489,22 +460,39 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     coarse_flags(f, &CX, &CY, &CZ, &cfl);
     c->L.emplace_back();  // (invalidates references into c->L)
     TRY(host_level(c->L[l + 1], CX, CY, CZ, cfl));
-    host_transfer(c->L[l], c->L[l + 1]);
   }
   const int LB = (int)c->L.size();
+  clk.mark("coarse tables (host)");
   {
+    // brick maps and coordinates from the host; the neighbour, child and
+    // parent tables are formed on the device from them
     TableUpload up;
-    for (int l = 0; l < LB; ++l) {
-      Level &lv = c->L[l];
-      if (l > 0) {
-        up.add(lv.hbmap, &lv.g.bmap);
-        up.add(lv.hbco, &lv.g.bco);
-        up.add(lv.hnbr, &lv.g.nbr);
-        up.add(lv.hkid, &lv.g.kid);
-      }
-      if (l + 1 < LB) up.add(lv.hpar, &lv.g.par);
+    for (int l = 1; l < LB; ++l) {
+      up.add(c->L[l].hbmap, &c->L[l].g.bmap);
+      up.add(c->L[l].hbco, &c->L[l].g.bco);
     }
     TRY(up.run(c));
+    for (int l = 0; l < LB; ++l) {
+      Grid &g = c->L[l].g;
+      if (l > 0) {
+        int *nbr = nullptr, *kid = nullptr;
+        TRY(dalloc(c, &nbr, (size_t)std::max(g.nb, 1) * 27));
+        TRY(dalloc(c, &kid, (size_t)std::max(g.nb, 1) * 27));
+        launch_brick_nbr(g, nbr, st);
+        launch_brick_kid(c->L[l - 1].g, g, kid, st);
+        c->launch_count += g.nb ? 2 : 0;
+        g.nbr = nbr;
+        g.kid = kid;
+      }
+      if (l + 1 < LB) {
+        int *par = nullptr;
+        TRY(dalloc(c, &par, (size_t)std::max(g.nb, 1) * 8));
+        launch_brick_par(g, c->L[l + 1].g, par, st);
+        c->launch_count += g.nb ? 1 : 0;
+        g.par = par;
+      }
+    }
+    TRY(launch_check("brick tables"));
   }
 
   // component numbering (one read-back: the root count per brick)

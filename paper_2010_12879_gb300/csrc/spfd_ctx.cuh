@@ -38,7 +38,6 @@ struct Level {
   Grid g{};                       // device view
   std::vector<int> hbmap;         // host brick map
   std::vector<int4> hbco;         // host brick coordinates
-  std::vector<int> hnbr, hkid, hpar;  // host copies of the brick tables
   size_t S = 0;                   // slots = nb * 512
   int64_t n_active = 0;
   double omega = 0.0, lmax = 0.0;

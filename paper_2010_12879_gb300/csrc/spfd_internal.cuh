@@ -145,6 +145,12 @@ void launch_root_counts(const Grid &g, const int *parent, int *counts,
                         cudaStream_t st);
 void launch_assign_comp(const Grid &g, const int *parent, const int *offsets,
                         int *comp, cudaStream_t st);
+// Brick tables from the brick maps and coordinates already on the device:
+// nbr [nb][27] of level g; kid [gc.nb][27] of coarse level gc (fine bricks of
+// level gf); par [gf.nb][8] of fine level gf (coarse bricks of level gc).
+void launch_brick_nbr(const Grid &g, int *nbr, cudaStream_t st);
+void launch_brick_kid(const Grid &gf, const Grid &gc, int *kid, cudaStream_t st);
+void launch_brick_par(const Grid &gf, const Grid &gc, int *par, cudaStream_t st);
 void launch_comp_sizes(const Grid &g, const int *comp, int *sizes,
                        cudaStream_t st);
 // Multigrid hierarchy (spfd_hierarchy.cu).  Pc: the fine level's compact

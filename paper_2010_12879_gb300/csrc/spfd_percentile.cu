@@ -288,7 +288,7 @@ extern "C" spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev,
   // algorithmic bytes: the mask of every voxel, E and the label of each
   // conducting one (counted from the previous call; all voxels on the first)
   const double ncv = c->pct_nc > 0 ? (double)c->pct_nc : (double)nv;
-  SPFD_LAUNCH(c, "percentile", false, 1, nv + 12.0 * ncv, 0,
+  SPFD_LAUNCH(c, "percentile_count", false, 1, nv + 12.0 * ncv, 0,
               (k_pct_count<<<grid, PT, sm_count, st>>>(c->mask, E_dev, lab, nv, L, cnt,
                                                        status)));
   TRY(launch_check("percentile count"));
@@ -351,15 +351,15 @@ extern "C" spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev,
   }
   const size_t sm_scatter = (size_t)8 * ((G + 1) / 2) + (size_t)8 * G + 16;
   c->pct_nc = (long long)hc[L];
-  SPFD_LAUNCH(c, "percentile", false, 1, nv + 12.0 * hc[L] + 8.0 * total, 0,
+  SPFD_LAUNCH(c, "percentile_scatter", false, 1, nv + 12.0 * hc[L] + 8.0 * total, 0,
               (k_pct_scatter<<<grid, PT, sm_scatter, st>>>(c->mask, E_dev, lab, nv, L, off,
                                                            cnt, cur, c->pct_keys, status)));
   TRY(launch_check("percentile scatter"));
   for (int r = 0; r < PCT_ROUNDS && nch > 0; ++r) {
-    SPFD_LAUNCH(c, "percentile", false, 1, 8.0 * total, 0,
+    SPFD_LAUNCH(c, "percentile_hist", false, 1, 8.0 * total, 0,
                 (k_pct_hist<<<nch, PT, 0, st>>>(c->pct_keys, dcg, dcb, dce, pre, PCT_SHIFT[r],
                                                 PCT_WIDTH[r], c->pct_hist)));
-    SPFD_LAUNCH(c, "percentile", false, 1, 8.0 * G * (1 << PCT_WIDTH[r]), 0,
+    SPFD_LAUNCH(c, "percentile_select", false, 1, 8.0 * G * (1 << PCT_WIDTH[r]), 0,
                 (k_pct_select<<<G, PT, 0, st>>>(c->pct_hist, cnt, pre, rk, PCT_SHIFT[r],
                                                 PCT_WIDTH[r], status)));
   }

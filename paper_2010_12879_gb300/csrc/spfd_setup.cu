@@ -485,4 +485,56 @@ double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
   return a;
 }
 
+// ------------------------------------------------------------ brick tables
+// The neighbour, child and parent tables of the levels, from their brick maps
+// and brick coordinates: data-parallel lookups, one thread per entry.
+__global__ void k_brick_nbr(Grid g, int *__restrict__ nbr) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)g.nb * 27) return;
+  const int b = (int)(q / 27), e = (int)(q % 27);
+  const int4 bc = g.bco[b];
+  const int x = bc.x + e % 3 - 1, y = bc.y + (e / 3) % 3 - 1, z = bc.z + e / 9 - 1;
+  int v = -1;
+  if (x >= 0 && y >= 0 && z >= 0 && x < g.MX && y < g.MY && z < g.MZ)
+    v = g.bmap[((size_t)z * g.MY + y) * g.MX + x];
+  nbr[q] = v;
+}
+
+// kid[B][o]: the fine brick 2B + o - 1 (o in {0,1,2}^3) of coarse brick B.
+__global__ void k_brick_kid(Grid gf, Grid gc, int *__restrict__ kid) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)gc.nb * 27) return;
+  const int b = (int)(q / 27), o = (int)(q % 27);
+  const int4 bc = gc.bco[b];
+  const int x = 2 * bc.x + o % 3 - 1, y = 2 * bc.y + (o / 3) % 3 - 1, z = 2 * bc.z + o / 9 - 1;
+  int v = -1;
+  if (x >= 0 && y >= 0 && z >= 0 && x < gf.MX && y < gf.MY && z < gf.MZ)
+    v = gf.bmap[((size_t)z * gf.MY + y) * gf.MX + x];
+  kid[q] = v;
+}
+
+// par[b][o]: the coarse brick (b >> 1) + o (o in {0,1}^3) of fine brick b.
+__global__ void k_brick_par(Grid gf, Grid gc, int *__restrict__ par) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)gf.nb * 8) return;
+  const int b = (int)(q / 8), o = (int)(q % 8);
+  const int4 bc = gf.bco[b];
+  const int x = (bc.x >> 1) + (o & 1), y = (bc.y >> 1) + ((o >> 1) & 1), z = (bc.z >> 1) + (o >> 2);
+  int v = -1;
+  if (x < gc.MX && y < gc.MY && z < gc.MZ) v = gc.bmap[((size_t)z * gc.MY + y) * gc.MX + x];
+  par[q] = v;
+}
+
+static inline unsigned table_blocks(long long n) { return (unsigned)((n + 255) / 256); }
+
+void launch_brick_nbr(const Grid &g, int *nbr, cudaStream_t st) {
+  if (g.nb) k_brick_nbr<<<table_blocks((long long)g.nb * 27), 256, 0, st>>>(g, nbr);
+}
+void launch_brick_kid(const Grid &gf, const Grid &gc, int *kid, cudaStream_t st) {
+  if (gc.nb) k_brick_kid<<<table_blocks((long long)gc.nb * 27), 256, 0, st>>>(gf, gc, kid);
+}
+void launch_brick_par(const Grid &gf, const Grid &gc, int *par, cudaStream_t st) {
+  if (gf.nb) k_brick_par<<<table_blocks((long long)gf.nb * 8), 256, 0, st>>>(gf, gc, par);
+}
+
 }  // namespace spfd
