@@ -271,24 +271,19 @@ __global__ void __launch_bounds__(NT, 1) k_ap(LevelOp A, const double *__restric
 // prolongation.  Fine node 2I + d lies in cell I + (d == -1) of class |d|
 // and sees I as its parent (d == -1); its A P row starts at
 // base = I - 1 + (d == +1), so t = D + 1 - (d == +1).
-__global__ void __launch_bounds__(NT)
-k_ptap(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
-       const double *__restrict__ T, double *__restrict__ stc, double *__restrict__ P) {
-  __shared__ int kid[27];
-  const int b = blockIdx.x, t = threadIdx.x;
-  if (t < 27) kid[t] = gc.kid[(size_t)b * 27 + t];
-  __syncthreads();
-  const size_t Sc = (size_t)gc.nb * BV, s = (size_t)b * BV + t;
-  const int X = t & 7, Y = (t >> 3) & 7, Z = t >> 6;
-  const int4 bc = gc.bco[b];
-  const int I = bc.x * 8 + X, J = bc.y * 8 + Y, K = bc.z * 8 + Z;
-  const bool valid = I < gc.NX && J < gc.NY && K < gc.NZ;
-  double acc[14];
+// The 9 terms d = (dx, dy, DZ) of one coarse node: P[d] written, the
+// products with T accumulated into acc (offsets D with sidx(D) >= 13).
+template <int DZ>
+__device__ __forceinline__ void ptap_layer(const Grid &gf, const Grid &gc, size_t NCf,
+                                           const double *__restrict__ Pc,
+                                           const double *__restrict__ T, double *__restrict__ P,
+                                           const int *kid, size_t Sc, size_t s, int X, int Y,
+                                           int Z, int I, int J, int K, bool valid,
+                                           double (&acc)[14]) {
 #pragma unroll
-  for (int r = 0; r < 14; ++r) acc[r] = 0.0;
-#pragma unroll
-  for (int d = 0; d < 27; ++d) {
-    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+  for (int j = 0; j < 9; ++j) {
+    const int d = (DZ + 1) * 9 + j;
+    const int dx = j % 3 - 1, dy = j / 3 - 1, dz = DZ;
     const int ux = dx != 0, uy = dy != 0, uz = dz != 0;
     const int U = ux | (uy << 1) | (uz << 2);
     const int O = (dx < 0) | ((dy < 0) << 1) | ((dz < 0) << 2);
@@ -313,8 +308,64 @@ k_ptap(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(NT)
+k_ptap(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
+       const double *__restrict__ T, double *__restrict__ stc, double *__restrict__ P) {
+  __shared__ int kid[27];
+  const int b = blockIdx.x, t = threadIdx.x;
+  if (t < 27) kid[t] = gc.kid[(size_t)b * 27 + t];
+  __syncthreads();
+  const size_t Sc = (size_t)gc.nb * BV, s = (size_t)b * BV + t;
+  const int X = t & 7, Y = (t >> 3) & 7, Z = t >> 6;
+  const int4 bc = gc.bco[b];
+  const int I = bc.x * 8 + X, J = bc.y * 8 + Y, K = bc.z * 8 + Z;
+  const bool valid = I < gc.NX && J < gc.NY && K < gc.NZ;
+  double acc[14];
+#pragma unroll
+  for (int r = 0; r < 14; ++r) acc[r] = 0.0;
+  ptap_layer<-1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
+  ptap_layer<0>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
+  ptap_layer<1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
 #pragma unroll
   for (int r = 0; r < 14; ++r) stc[(size_t)(13 + r) * Sc + s] = acc[r];
+}
+
+// The same for small coarse levels, where one thread per coarse node leaves
+// most SMs idle: three threads per coarse node, one per fine z-layer of its
+// 27 points, in blocks of 3 x 128 threads over a quarter brick; the layers'
+// sums are added in a fixed order (dz = -1, 0, +1).
+constexpr int PT_Q = 128;
+__global__ void __launch_bounds__(3 * PT_Q)
+k_ptap3(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
+        const double *__restrict__ T, double *__restrict__ stc, double *__restrict__ P) {
+  __shared__ int kid[27];
+  __shared__ double red[2][PT_Q][15];
+  const int b = blockIdx.x >> 2;
+  const int part = threadIdx.x / PT_Q, nl = threadIdx.x % PT_Q;
+  const int t = (blockIdx.x & 3) * PT_Q + nl;
+  if (threadIdx.x < 27) kid[threadIdx.x] = gc.kid[(size_t)b * 27 + threadIdx.x];
+  __syncthreads();
+  const size_t Sc = (size_t)gc.nb * BV, s = (size_t)b * BV + t;
+  const int X = t & 7, Y = (t >> 3) & 7, Z = t >> 6;
+  const int4 bc = gc.bco[b];
+  const int I = bc.x * 8 + X, J = bc.y * 8 + Y, K = bc.z * 8 + Z;
+  const bool valid = I < gc.NX && J < gc.NY && K < gc.NZ;
+  double acc[14];
+#pragma unroll
+  for (int r = 0; r < 14; ++r) acc[r] = 0.0;
+  if (part == 0) ptap_layer<-1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
+  else if (part == 1) ptap_layer<0>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
+  else ptap_layer<1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
+  if (part > 0)
+#pragma unroll
+    for (int r = 0; r < 14; ++r) red[part - 1][nl][r] = acc[r];
+  __syncthreads();
+  if (part == 0)
+#pragma unroll
+    for (int r = 0; r < 14; ++r)
+      stc[(size_t)(13 + r) * Sc + s] = (acc[r] + red[0][nl][r]) + red[1][nl][r];
 }
 
 // A_c(I, I + D) = A_c(I + D, I) for the 13 offsets with sidx(D) < 13.
@@ -353,7 +404,9 @@ void launch_galerkin(const Grid &gf, const Grid &gc, const double *gx,
   const LevelOp A{gf, gx, st27f, diagf, (size_t)gf.nb * BV, (size_t)gf.nb * 64};
   if (st27f) k_ap<true><<<gf.nb, NT, 0, st>>>(A, Pc, T);
   else k_ap<false><<<gf.nb, NT, 0, st>>>(A, Pc, T);
-  k_ptap<<<gc.nb, NT, 0, st>>>(gf, gc, A.NC, Pc, T, stc, P);
+  // below a few waves of one-brick blocks, three threads per coarse node
+  if (gc.nb < 1024) k_ptap3<<<gc.nb * 4, 3 * PT_Q, 0, st>>>(gf, gc, A.NC, Pc, T, stc, P);
+  else k_ptap<<<gc.nb, NT, 0, st>>>(gf, gc, A.NC, Pc, T, stc, P);
   k_mirror<<<gc.nb, NT, 0, st>>>(gc, stc);
 }
 

@@ -439,35 +439,49 @@ k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, 
     __syncthreads();
   }
   const double(*Dinv)[GJ_B + 1] = D[GJ_B & 1];
-  // W = D^-1 M[K, tile columns]
-  for (int q = t; q < GJ_B * GJ_T; q += GJ_NT) {
-    const int l = q / GJ_T, jj = q % GJ_T;
-    double w = 0.0;
+  // W = D^-1 M[K, tile columns]: each thread forms the entries (l, jj) and
+  // (l + 8, jj) with their two sums interleaved (each in its own fixed order)
+  static_assert(GJ_B * GJ_T == 2 * GJ_NT && GJ_T * GJ_T == 4 * GJ_NT, "tile shape");
+  {
+    const int l = t / GJ_T, jj = t % GJ_T;
+    double w0 = 0.0, w1 = 0.0;
 #pragma unroll
-    for (int l2 = 0; l2 < GJ_B; ++l2) w += Dinv[l][l2] * C[l2][jj];
-    W[l][jj] = w;
+    for (int l2 = 0; l2 < GJ_B; ++l2) {
+      const double c = C[l2][jj];
+      w0 += Dinv[l][l2] * c;
+      w1 += Dinv[l + GJ_NT / GJ_T][l2] * c;
+    }
+    W[l][jj] = w0;
+    W[l + GJ_NT / GJ_T][jj] = w1;
   }
   __syncthreads();
-  for (int q = t; q < GJ_T * GJ_T; q += GJ_NT) {
-    const int ii = q / GJ_T, jj = q % GJ_T;
-    const int i = i0 + ii, j = j0 + jj;
-    if (i >= m || j >= m) continue;
-    const bool ki = i >= k0 && i < k0 + r, kj = j >= k0 && j < k0 + r;
-    double v;
-    if (ki && kj) {
-      v = Dinv[i - k0][j - k0];
-    } else if (ki) {
-      v = W[i - k0][jj];
-    } else if (kj) {
-      v = 0.0;
+  // the tile: each thread updates rows ii0 + 8k (k = 0..3) of column jj,
+  // four independent chains, each subtracting its terms in order l = 0..15
+  {
+    constexpr int RS = GJ_NT / GJ_T;  // row stride between a thread's entries
+    const int ii0 = t / GJ_T, jj = t % GJ_T, j = j0 + jj;
+    const bool kj = j >= k0 && j < k0 + r;
+    double v[4];
 #pragma unroll
-      for (int l = 0; l < GJ_B; ++l) v -= U[ii][l] * Dinv[l][j - k0];
-    } else {
-      v = A[(size_t)i * m + j];
-#pragma unroll
-      for (int l = 0; l < GJ_B; ++l) v -= U[ii][l] * W[l][jj];
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + ii0 + RS * k;
+      v[k] = (!kj && i < m && j < m) ? A[(size_t)i * m + j] : 0.0;
     }
-    B[(size_t)i * m + j] = v;
+#pragma unroll
+    for (int l = 0; l < GJ_B; ++l) {
+      const double mc = kj ? Dinv[l][j - k0] : W[l][jj];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] -= U[ii0 + RS * k][l] * mc;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int ii = ii0 + RS * k, i = i0 + ii;
+      if (i >= m || j >= m) continue;
+      const bool ki = i >= k0 && i < k0 + r;
+      double out = v[k];
+      if (ki) out = kj ? Dinv[i - k0][j - k0] : W[i - k0][jj];
+      B[(size_t)i * m + j] = out;
+    }
   }
 }
 
