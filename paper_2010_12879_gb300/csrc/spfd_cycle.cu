@@ -17,13 +17,13 @@ namespace spfd {
 // ------------------------------------------------------------ smoothers
 // Level 0 (7-point): r = b - A x, and the weighted-Jacobi sweep
 // x_out = x + omega D^-1 (b - A x), on the row mapping.
-template <typename T, typename C>
+template <typename T, typename C, int ORD>
 __global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r,
-            int order, int nk) {
+            int nk) {
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
   const size_t off = (size_t)rhs * S;
@@ -34,13 +34,13 @@ k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
   stq(r + s0, rv);
 }
 
-template <typename T, typename C>
+template <typename T, typename C, int ORD>
 __global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
-          const T *__restrict__ b, T *__restrict__ xout, int order, int nk) {
+          const T *__restrict__ b, T *__restrict__ xout, int nk) {
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
   const size_t off = (size_t)rhs * S;
@@ -53,14 +53,14 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
   stq(xout + s0, xc);
 }
 
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
-             const T *__restrict__ b, T *__restrict__ r, int order, int nk) {
+             const T *__restrict__ b, T *__restrict__ r, int nk) {
   __shared__ T tl[10][10][10];
   __shared__ int sn[27];
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const size_t off = (size_t)rhs * g.nb * BV;
   x += off; b += off; r += off;
   load_nbr(g, bk, sn);
@@ -71,15 +71,15 @@ k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
   r[s] = b[s] - apply27_tile<T>(tl, st, S, s);
 }
 
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
            const T *__restrict__ xin, const T *__restrict__ b,
-           T *__restrict__ xout, int order, int nk) {
+           T *__restrict__ xout, int nk) {
   __shared__ T tl[10][10][10];
   __shared__ int sn[27];
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const size_t off = (size_t)rhs * g.nb * BV;
   xin += off; b += off; xout += off;
   load_nbr(g, bk, sn);
@@ -94,13 +94,13 @@ k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
 
 // First sweep from a zero guess, x = omega D^-1 b: a streaming kernel, one
 // brick per block, 16 bytes per thread access.
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
-               T *__restrict__ x, int nb, int order, int nk) {
+               T *__restrict__ x, int nb, int nk) {
   constexpr int N = V16<T>::N;
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const size_t s0 = (size_t)bk * BV + threadIdx.x * N;
   const size_t off = (size_t)rhs * nb * BV;
   b += off; x += off;
@@ -113,13 +113,13 @@ k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
 
 // The same with the projection of b fused in: b <- b - mean(b) on the
 // unknowns (mean formed by the preceding reduction), in place.
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
-                    T *__restrict__ x, const Scalars *sc, int nb, int order, int nk) {
+                    T *__restrict__ x, const Scalars *sc, int nb, int nk) {
   constexpr int N = V16<T>::N;
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const size_t s0 = (size_t)bk * BV + threadIdx.x * N;
   const size_t off = (size_t)rhs * nb * BV;
   b += off; x += off; sc += rhs;
@@ -144,14 +144,14 @@ k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
 // Restriction r_c(I) = sum_d P[d][I] r_f(2I + d) (P^T, the adjoint of the
 // prolongation below).  A coarse brick B reads the 17^3 fine nodes
 // 16B-1 .. 16B+15 (per axis) from the 27 fine bricks 2B-1 .. 2B+1.
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf,
-           T *__restrict__ bcoarse, int order, int nk) {
+           T *__restrict__ bcoarse, int nk) {
   __shared__ T fs[17][17][17];
   __shared__ int sk[27];
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
   rf += (size_t)rhs * Sf;
   bcoarse += (size_t)rhs * gc.nb * BV;
@@ -183,12 +183,12 @@ k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf
 // c + o (o in {0,1}^3; coarse bricks from the brick's parent table) and its
 // 8 fine values as 2-vectors along x, then writes the 8 corrected values.
 // No shared memory and no barrier: every load is independent.
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(128)
 k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
-          T *__restrict__ ef, int order, int nk) {
+          T *__restrict__ ef, int nk) {
   int pair, rhs;
-  unit_rhs(order, nk, pair, rhs);
+  unit_rhs<ORD>(nk, pair, rhs);
   const int bk = pair * 2 + (threadIdx.x >> 6);
   if (bk >= gf.nb) return;
   ec += (size_t)rhs * gc.nb * BV;
@@ -258,19 +258,24 @@ template <typename T, typename C>
 void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
                       const T *b, T *r, cudaStream_t st, int nk, int order) {
   if (g.nb)
-    k_residual7<T, C><<<unit_grid(order, g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r, order, nk);
+    if (order) k_residual7<T, C, 1><<<unit_grid(1, g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r, nk);
+    else k_residual7<T, C, 0><<<unit_grid(0, g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r, nk);
 }
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
                        T *r, cudaStream_t st, int nk, int order) {
-  if (g.nb) k_residual27<T><<<unit_grid(order, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, order, nk);
+  if (!g.nb) return;
+  if (order) k_residual27<T, 1><<<unit_grid(1, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
+  else k_residual27<T, 0><<<unit_grid(0, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
 }
 template <typename T>
 void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
                          cudaStream_t st, int nk, int order) {
   if (g.nb)
-    k_jacobi_first<T><<<unit_grid(order, g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, g.nb,
-                                                                            order, nk);
+    if (order)
+      k_jacobi_first<T, 1><<<unit_grid(1, g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, g.nb, nk);
+    else
+      k_jacobi_first<T, 0><<<unit_grid(0, g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, g.nb, nk);
 }
 template <typename T>
 void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
@@ -278,36 +283,60 @@ void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
                               cudaStream_t st, int nk, int order) {
   (void)inv_ndof;  // the mean comes from each right-hand side's Scalars
   if (g.nb)
-    k_jacobi_first_proj<T><<<unit_grid(order, g.nb, nk), NT / V16<T>::N, 0, st>>>(
-        wdinv, b, x, sc, g.nb, order, nk);
+  {
+    if (order)
+      k_jacobi_first_proj<T, 1><<<unit_grid(1, g.nb, nk), NT / V16<T>::N, 0, st>>>(
+          wdinv, b, x, sc, g.nb, nk);
+    else
+      k_jacobi_first_proj<T, 0><<<unit_grid(0, g.nb, nk), NT / V16<T>::N, 0, st>>>(
+          wdinv, b, x, sc, g.nb, nk);
+  }
 }
 template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
                     const T *xin, const T *b, T *xout, cudaStream_t st, int nk, int order) {
   if (g.nb)
-    k_jacobi7<T, C><<<unit_grid(order, g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout,
-                                                               order, nk);
+  {
+    if (order)
+      k_jacobi7<T, C, 1><<<unit_grid(1, g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout, nk);
+    else
+      k_jacobi7<T, C, 0><<<unit_grid(0, g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout, nk);
+  }
 }
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
                      const T *b, T *xout, cudaStream_t st, int nk, int order) {
   if (g.nb)
-    k_jacobi27<T><<<unit_grid(order, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, order,
-                                                             nk);
+  {
+    if (order)
+      k_jacobi27<T, 1><<<unit_grid(1, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
+    else
+      k_jacobi27<T, 0><<<unit_grid(0, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
+  }
 }
 template <typename T>
 void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
                      T *bcoarse, cudaStream_t st, int nk, int order) {
   if (gc.nb)
-    k_restrict<T><<<unit_grid(order, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
-                                                              bcoarse, order, nk);
+  {
+    if (order)
+      k_restrict<T, 1><<<unit_grid(1, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
+                                                               bcoarse, nk);
+    else
+      k_restrict<T, 0><<<unit_grid(0, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
+                                                               bcoarse, nk);
+  }
 }
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
                     T *ef, cudaStream_t st, int nk, int order) {
   if (gf.nb)
-    k_prolong<T><<<unit_grid(order, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, order,
-                                                                        nk);
+  {
+    if (order)
+      k_prolong<T, 1><<<unit_grid(1, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
+    else
+      k_prolong<T, 0><<<unit_grid(0, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
+  }
 }
 template <typename T>
 void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,

@@ -49,8 +49,11 @@ __host__ __device__ __forceinline__ constexpr int crank(int u, int o) {
 // b % nk, so the nk blocks of one unit run side by side and share its
 // operator entries through L2.  The arithmetic of every block is the same
 // in both orders; the autotuner picks one per kernel family and level.
-__device__ __forceinline__ void unit_rhs(int order, int nk, int &unit, int &rhs) {
-  if (order) {
+// The order is a template parameter, so that the order-0 instances compile to
+// the same code as kernels without a batch order.
+template <int ORD>
+__device__ __forceinline__ void unit_rhs(int nk, int &unit, int &rhs) {
+  if constexpr (ORD == 1) {
     unit = (int)(blockIdx.x / (unsigned)nk);
     rhs = (int)(blockIdx.x % (unsigned)nk);
   } else {

@@ -101,13 +101,13 @@ constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SM
 // ------------------------------------------------------------ CG operator
 // q = A p on one brick per block (row mapping, four nodes per thread); each
 // warp writes its part of p.q, and k_finish_pq adds them.
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(RT, row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ p, T *__restrict__ q, double *partials,
-            size_t pstride, int order, int nk) {
+            size_t pstride, int nk) {
   int bk, rhs;
-  unit_rhs(order, nk, bk, rhs);
+  unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
   p += (size_t)rhs * S;
@@ -918,8 +918,12 @@ void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st, int nk,
                       size_t pstride, int order) {
   if (!g.nb) return;
-  k_apply_dot<T><<<unit_grid(order, g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride,
-                                                            order, nk);
+  if (order)
+    k_apply_dot<T, 1><<<unit_grid(1, g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride,
+                                                             nk);
+  else
+    k_apply_dot<T, 0><<<unit_grid(0, g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride,
+                                                             nk);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
                       cudaStream_t st, int nk, size_t pstride) {
