@@ -6,8 +6,8 @@
 // geometric operator-dependent V-cycle that replaces it.  All are
 // bandwidth-bound stencil or transfer sweeps (the FP64 forms approach the
 // FP64 pipe's rate); none is a dense contraction, so no tensor-core path is
-// used.  One block handles one 8x8x8 brick: four nodes per thread without
-// shared memory on level 0, one node per thread with a shared tile on the
+// used.  One block handles one 8x8x8 brick: two (FP64) or four (FP32) nodes
+// per thread without shared memory on level 0, one node per thread with a shared tile on the
 // 27-point levels (spfd_tile.cuh).
 #include "spfd_internal.cuh"
 #include "spfd_tile.cuh"
@@ -18,39 +18,41 @@ namespace spfd {
 // Level 0 (7-point): r = b - A x, and the weighted-Jacobi sweep
 // x_out = x + omega D^-1 (b - A x), on the row mapping.
 template <typename T, typename C, int ORD>
-__global__ void __launch_bounds__(RT, row_min_blocks<T>())
+__global__ void __launch_bounds__(row_threads<T>(), row_min_blocks<T>())
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r,
             int nk) {
+  constexpr int N = row_n<T>();
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
-  const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot<N>(bk, t);
   const size_t off = (size_t)rhs * S;
   x += off; b += off; r += off;
-  const Q4<T> bv = ldq<T>(b + s0);
-  Q4<T> xc, rv;
-  apply7_row<T, C, true>(g, gx, diag, x, S, bk, t, bv, xc, rv);
-  stq(r + s0, rv);
+  const Qv<T, N> bv = ldqn<T, T, N>(b + s0);
+  Qv<T, N> xc, rv;
+  apply7_row<T, C, true, N>(g, gx, diag, x, S, bk, t, bv, xc, rv);
+  stqn<T, N>(r + s0, rv);
 }
 
 template <typename T, typename C, int ORD>
-__global__ void __launch_bounds__(RT, row_min_blocks<T>())
+__global__ void __launch_bounds__(BV / row_n_jacobi<T>(), row_min_blocks<T>())
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
           const T *__restrict__ b, T *__restrict__ xout, int nk) {
+  constexpr int N = row_n_jacobi<T>();
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
-  const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot<N>(bk, t);
   const size_t off = (size_t)rhs * S;
   xin += off; b += off; xout += off;
-  const Q4<T> bv = ldq<T>(b + s0), wv = ldq<T>(wdinv + s0);
-  Q4<T> xc, rv;
-  apply7_row<T, C, true>(g, gx, diag, xin, S, bk, t, bv, xc, rv);
+  const Qv<T, N> bv = ldqn<T, T, N>(b + s0), wv = ldqn<T, T, N>(wdinv + s0);
+  Qv<T, N> xc, rv;
+  apply7_row<T, C, true, N>(g, gx, diag, xin, S, bk, t, bv, xc, rv);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) xc.v[i] += wv.v[i] * rv.v[i];
-  stq(xout + s0, xc);
+  for (int i = 0; i < N; ++i) xc.v[i] += wv.v[i] * rv.v[i];
+  stqn<T, N>(xout + s0, xc);
 }
 
 template <typename T, int ORD>
@@ -258,8 +260,12 @@ template <typename T, typename C>
 void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
                       const T *b, T *r, cudaStream_t st, int nk, int order) {
   if (g.nb)
-    if (order) k_residual7<T, C, 1><<<unit_grid(1, g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r, nk);
-    else k_residual7<T, C, 0><<<unit_grid(0, g.nb, nk), RT, 0, st>>>(g, gx, diag, x, b, r, nk);
+    if (order)
+      k_residual7<T, C, 1><<<unit_grid(1, g.nb, nk), row_threads<T>(), 0, st>>>(g, gx, diag, x, b,
+                                                                                r, nk);
+    else
+      k_residual7<T, C, 0><<<unit_grid(0, g.nb, nk), row_threads<T>(), 0, st>>>(g, gx, diag, x, b,
+                                                                                r, nk);
 }
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
@@ -298,9 +304,11 @@ void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
   if (g.nb)
   {
     if (order)
-      k_jacobi7<T, C, 1><<<unit_grid(1, g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout, nk);
+      k_jacobi7<T, C, 1><<<unit_grid(1, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
+          g, gx, diag, wdinv, xin, b, xout, nk);
     else
-      k_jacobi7<T, C, 0><<<unit_grid(0, g.nb, nk), RT, 0, st>>>(g, gx, diag, wdinv, xin, b, xout, nk);
+      k_jacobi7<T, C, 0><<<unit_grid(0, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
+          g, gx, diag, wdinv, xin, b, xout, nk);
   }
 }
 template <typename T>

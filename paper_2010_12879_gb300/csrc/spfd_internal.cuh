@@ -226,7 +226,7 @@ void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st, int nk = 1,
                       size_t pstride = 0, int order = 0);
 // Number of partial sums launch_apply_dot writes for nb bricks (one per warp,
-// 4 per brick); launch_finish_pq adds n of them (scratch: at least 152
+// 8 per brick in FP64, 4 in FP32); launch_finish_pq adds n of them (scratch: at least 152
 // doubles, not overlapping) and sets alpha = rz / pq.
 template <typename T> int apply_dot_partials(int nb);
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,

@@ -102,27 +102,28 @@ constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SM
 // q = A p on one brick per block (row mapping, four nodes per thread); each
 // warp writes its part of p.q, and k_finish_pq adds them.
 template <typename T, int ORD>
-__global__ void __launch_bounds__(RT, row_min_blocks<T>())
+__global__ void __launch_bounds__(row_threads<T>(), row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ p, T *__restrict__ q, double *partials,
             size_t pstride, int nk) {
+  constexpr int N = row_n<T>();
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
-  const size_t S = (size_t)g.nb * BV, s0 = row_slot(bk, t);
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot<N>(bk, t);
   p += (size_t)rhs * S;
   q += (size_t)rhs * S;
   partials += (size_t)rhs * pstride;
-  Q4<T> pc, qv;
-  apply7_row<T, T, false>(g, gx, diag, p, S, bk, t, zq<T>(), pc, qv);
-  stq(q + s0, qv);
+  Qv<T, N> pc, qv;
+  apply7_row<T, T, false, N>(g, gx, diag, p, S, bk, t, zqn<T, N>(), pc, qv);
+  stqn<T, N>(q + s0, qv);
   double part;
   if constexpr (sizeof(T) == 4) {
     // FP32 products, summed without rounding error in (hi, lo) pairs
     // (TwoSum) over the thread's four nodes and the warp; FP64 per warp
     float hi = pc.v[0] * qv.v[0], lo = 0.f;
 #pragma unroll
-    for (int i = 1; i < 4; ++i) {
+    for (int i = 1; i < N; ++i) {
       const float v = pc.v[i] * qv.v[i];
       const float sh = hi + v, bb = sh - hi;
       lo += (hi - (sh - bb)) + (v - bb);
@@ -141,17 +142,17 @@ k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
   } else {
     double a = pc.v[0] * qv.v[0];
 #pragma unroll
-    for (int i = 1; i < 4; ++i) a += pc.v[i] * qv.v[i];
+    for (int i = 1; i < N; ++i) a += pc.v[i] * qv.v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     part = a;
   }
-  if ((t & 31) == 0) partials[(size_t)bk * (RT / 32) + (t >> 5)] = part;
+  if ((t & 31) == 0) partials[(size_t)bk * (row_threads<T>() / 32) + (t >> 5)] = part;
 }
 
 // Number of partials k_apply_dot writes for nb bricks.
 template <typename T>
-int apply_dot_partials(int nb) { return nb * (RT / 32); }
+int apply_dot_partials(int nb) { return nb * (row_threads<T>() / 32); }
 
 // pq = sum of the n partials of k_apply_dot (blocks add contiguous chunks,
 // the last block adds the block sums, fixed order); alpha = rz / pq.
@@ -919,11 +920,11 @@ void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       size_t pstride, int order) {
   if (!g.nb) return;
   if (order)
-    k_apply_dot<T, 1><<<unit_grid(1, g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride,
-                                                             nk);
+    k_apply_dot<T, 1><<<unit_grid(1, g.nb, nk), row_threads<T>(), 0, st>>>(
+        g, gx, diag, p, q, partials, pstride, nk);
   else
-    k_apply_dot<T, 0><<<unit_grid(0, g.nb, nk), RT, 0, st>>>(g, gx, diag, p, q, partials, pstride,
-                                                             nk);
+    k_apply_dot<T, 0><<<unit_grid(0, g.nb, nk), row_threads<T>(), 0, st>>>(
+        g, gx, diag, p, q, partials, pstride, nk);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
                       cudaStream_t st, int nk, size_t pstride) {

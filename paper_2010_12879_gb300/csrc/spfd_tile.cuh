@@ -72,125 +72,165 @@ __device__ __forceinline__ void tile_full(T (*tl)[10][10], const T *__restrict__
 }
 
 // ----------------------------------------------- level-0 7-point operator
-// Row mapping: thread t of a 128-thread group covers the four nodes
-// x = 4h .. 4h+3 (h = t & 1) of row y = (t >> 1) & 7 of plane z = t >> 4 of
-// one brick.  Own values and conductances arrive as 16-byte vectors, the
-// +-y/+-z neighbours as the vectors of the rows beside it (L1/L2 hits inside
-// the brick), the +-x neighbours of the row ends from the other half-row by
-// shuffle or from the x-neighbour brick.  No shared memory, no barrier.
-constexpr int RT = 128;  // threads per brick in the row mapping
+// Row mapping: the N consecutive x nodes N h .. N h + N - 1 of row y of plane
+// z of one brick go to one thread (h < 8 / N; the 8 / N threads of a row are
+// consecutive lanes).  Own values and conductances arrive as vector loads,
+// the +-y/+-z neighbours as the vectors of the rows beside it (L1/L2 hits
+// inside the brick), the +-x neighbours of the row ends from the neighbouring
+// lanes by shuffle or from the x-neighbour brick.  No shared memory, no
+// barrier.
+// Nodes per thread along x: FP64 kernels take two (half the registers of
+// four, so twice the resident warps hide the memory latency behind the FP64
+// pipe), FP32 kernels four (16-byte vector accesses, memory-bound).
+template <typename T>
+constexpr int row_n() { return sizeof(T) == 8 ? 2 : 4; }
+// The weighted-Jacobi sweep keeps four nodes per thread in FP64 too: with
+// two it measured 4 % slower on the 2 mm body, the residual 11 % faster.
+template <typename T>
+constexpr int row_n_jacobi() { return 4; }
+// Threads per brick in the row mapping.
+template <typename T>
+constexpr int row_threads() { return BV / row_n<T>(); }
 // Resident blocks per SM asked of the compiler for row kernels: FP32 kernels
-// wait on memory and want many warps in flight (12 blocks = 48 warps caps
-// them at 40 registers); FP64 kernels are bound by the FP64 pipe and keep
-// their registers.
+// wait on memory and want many warps in flight (10 blocks of 128 threads);
+// FP64 kernels take 4 blocks (of 256 threads: 64 registers; of 128: 128).
 template <typename T>
 constexpr int row_min_blocks() { return sizeof(T) == 4 ? 10 : 4; }
 
-template <typename T>
-struct Q4 {
-  T v[4];
+template <typename T, int N>
+struct Qv {
+  T v[N];
 };
 
-// Four consecutive values at p (16-byte aligned for float/double, 8-byte for
-// BF16), widened to T.
-template <typename T, typename C>
-__device__ __forceinline__ Q4<T> ldq(const C *__restrict__ p) {
-  Q4<T> r;
-  if constexpr (sizeof(C) == 4) {
-    const float4 u = *reinterpret_cast<const float4 *>(p);
-    r.v[0] = (T)u.x; r.v[1] = (T)u.y; r.v[2] = (T)u.z; r.v[3] = (T)u.w;
-  } else if constexpr (sizeof(C) == 8) {
-    const double2 u = reinterpret_cast<const double2 *>(p)[0];
-    const double2 w = reinterpret_cast<const double2 *>(p)[1];
-    r.v[0] = (T)u.x; r.v[1] = (T)u.y; r.v[2] = (T)w.x; r.v[3] = (T)w.y;
+// N consecutive values at p (aligned to their total size, or to 4 bytes for
+// two BF16 values), widened to T.
+template <typename T, typename C, int N>
+__device__ __forceinline__ Qv<T, N> ldqn(const C *__restrict__ p) {
+  Qv<T, N> r;
+  if constexpr (N == 4) {
+    if constexpr (sizeof(C) == 4) {
+      const float4 u = *reinterpret_cast<const float4 *>(p);
+      r.v[0] = (T)u.x; r.v[1] = (T)u.y; r.v[2] = (T)u.z; r.v[3] = (T)u.w;
+    } else if constexpr (sizeof(C) == 8) {
+      const double2 u = reinterpret_cast<const double2 *>(p)[0];
+      const double2 w = reinterpret_cast<const double2 *>(p)[1];
+      r.v[0] = (T)u.x; r.v[1] = (T)u.y; r.v[2] = (T)w.x; r.v[3] = (T)w.y;
+    } else {
+      const uint2 u = *reinterpret_cast<const uint2 *>(p);
+      const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
+      const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+      const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+      r.v[0] = (T)fa.x; r.v[1] = (T)fa.y; r.v[2] = (T)fb.x; r.v[3] = (T)fb.y;
+    }
   } else {
-    const uint2 u = *reinterpret_cast<const uint2 *>(p);
-    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
-    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-    r.v[0] = (T)fa.x; r.v[1] = (T)fa.y; r.v[2] = (T)fb.x; r.v[3] = (T)fb.y;
+    static_assert(N == 2, "two or four nodes per thread");
+    if constexpr (sizeof(C) == 4) {
+      const float2 u = *reinterpret_cast<const float2 *>(p);
+      r.v[0] = (T)u.x; r.v[1] = (T)u.y;
+    } else if constexpr (sizeof(C) == 8) {
+      const double2 u = *reinterpret_cast<const double2 *>(p);
+      r.v[0] = (T)u.x; r.v[1] = (T)u.y;
+    } else {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+      r.v[0] = (T)f.x; r.v[1] = (T)f.y;
+    }
   }
   return r;
 }
-template <typename T>
-__device__ __forceinline__ Q4<T> zq() {
-  Q4<T> r;
+template <typename T, int N>
+__device__ __forceinline__ Qv<T, N> zqn() {
+  Qv<T, N> r;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) r.v[i] = T(0);
+  for (int i = 0; i < N; ++i) r.v[i] = T(0);
   return r;
 }
-template <typename T>
-__device__ __forceinline__ void stq(T *__restrict__ p, const Q4<T> &r) {
-  if constexpr (sizeof(T) == 4) {
-    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+template <typename T, int N>
+__device__ __forceinline__ void stqn(T *__restrict__ p, const Qv<T, N> &r) {
+  if constexpr (N == 4) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    } else {
+      reinterpret_cast<double2 *>(p)[0] = make_double2(r.v[0], r.v[1]);
+      reinterpret_cast<double2 *>(p)[1] = make_double2(r.v[2], r.v[3]);
+    }
   } else {
-    reinterpret_cast<double2 *>(p)[0] = make_double2(r.v[0], r.v[1]);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(r.v[2], r.v[3]);
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(p) = make_float2(r.v[0], r.v[1]);
+    else *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
   }
 }
 
-// First slot of this thread's four nodes in brick b.
+// First slot of this thread's N nodes in brick b: 8 / N threads per row,
+// rows in (z, y) order.
+template <int N>
 __device__ __forceinline__ size_t row_slot(int b, int t) {
-  return (size_t)b * BV + (t >> 4) * 64 + ((t >> 1) & 7) * 8 + 4 * (t & 1);
+  constexpr int TPR = 8 / N;
+  return (size_t)b * BV + (t / (8 * TPR)) * 64 + ((t / TPR) & 7) * 8 + N * (t % TPR);
 }
 
 // The vector beside the row at s0: at offset in_off when that stays in the
 // brick, else the row `across` of the neighbour brick e (zero if that brick
 // is not stored).
-template <typename T, typename C>
-__device__ __forceinline__ Q4<T> ldq_nb(const C *__restrict__ v, size_t s0, bool inside,
-                                        long long in_off, const Grid &g, int b, int e,
-                                        size_t across) {
-  if (inside) return ldq<T>(v + (long long)s0 + in_off);
+template <typename T, typename C, int N>
+__device__ __forceinline__ Qv<T, N> ldq_nb(const C *__restrict__ v, size_t s0, bool inside,
+                                           long long in_off, const Grid &g, int b, int e,
+                                           size_t across) {
+  if (inside) return ldqn<T, C, N>(v + (long long)s0 + in_off);
   const int nb = __ldg(&g.nbr[(size_t)b * 27 + e]);
-  return nb >= 0 ? ldq<T>(v + (size_t)nb * BV + across) : zq<T>();
+  return nb >= 0 ? ldqn<T, C, N>(v + (size_t)nb * BV + across) : zqn<T, N>();
 }
 
-// out = A x (RES = false) or base - A x (RES = true) at this thread's four
+// out = A x (RES = false) or base - A x (RES = true) at this thread's N
 // nodes of brick b, and xc = x there.  FP64: diag*x - sum g x_nbr, with base
 // folded into the first FMA (fewest FP64-pipe operations).  FP32: sum
 // g (x - x_nbr), exactly zero on constants, so rounded (BF16/FP32)
-// conductances keep the operator positive semidefinite.  All 32 lanes of
-// each warp must call it (row-end shuffles).
-template <typename T, typename C, bool RES>
+// conductances keep the operator positive semidefinite.  The x-neighbours
+// of the row ends come from the neighbouring lanes by shuffle (a row's
+// threads are consecutive lanes), else from the x-neighbour brick.  All 32
+// lanes of each warp must call it.
+template <typename T, typename C, bool RES, int N>
 __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ gx,
                                            const T *__restrict__ diag, const T *__restrict__ x,
-                                           size_t S, int b, int t, const Q4<T> &base,
-                                           Q4<T> &xc, Q4<T> &out) {
-  const int h = t & 1, y = (t >> 1) & 7, z = t >> 4;
-  const size_t s0 = row_slot(b, t);
-  const size_t rz = (size_t)z * 64 + 4 * h, ry = (size_t)y * 8 + 4 * h;
-  xc = ldq<T>(x + s0);
-  const Q4<T> gpx = ldq<T>(gx + s0), gpy = ldq<T>(gx + S + s0), gpz = ldq<T>(gx + 2 * S + s0);
-  const Q4<T> xym = ldq_nb<T>(x, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
-  const Q4<T> xyp = ldq_nb<T>(x, s0, y < 7, 8, g, b, sidx(0, 1, 0), rz);
-  const Q4<T> xzm = ldq_nb<T>(x, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
-  const Q4<T> xzp = ldq_nb<T>(x, s0, z < 7, 64, g, b, sidx(0, 0, 1), ry);
-  const Q4<T> gmy = ldq_nb<T>(gx + S, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
-  const Q4<T> gmz = ldq_nb<T>(gx + 2 * S, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
-  // row ends: the other half-row by shuffle, else the x-neighbour brick
-  const T o_first = __shfl_xor_sync(0xffffffffu, xc.v[0], 1);
-  const T o_last = __shfl_xor_sync(0xffffffffu, xc.v[3], 1);
-  const T og_last = __shfl_xor_sync(0xffffffffu, gpx.v[3], 1);
+                                           size_t S, int b, int t, const Qv<T, N> &base,
+                                           Qv<T, N> &xc, Qv<T, N> &out) {
+  constexpr int TPR = 8 / N;
+  const int h = t % TPR, y = (t / TPR) & 7, z = t / (8 * TPR);
+  const size_t s0 = row_slot<N>(b, t);
+  const size_t rz = (size_t)z * 64 + N * h, ry = (size_t)y * 8 + N * h;
+  xc = ldqn<T, T, N>(x + s0);
+  const Qv<T, N> gpx = ldqn<T, C, N>(gx + s0), gpy = ldqn<T, C, N>(gx + S + s0),
+                 gpz = ldqn<T, C, N>(gx + 2 * S + s0);
+  const Qv<T, N> xym = ldq_nb<T, T, N>(x, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
+  const Qv<T, N> xyp = ldq_nb<T, T, N>(x, s0, y < 7, 8, g, b, sidx(0, 1, 0), rz);
+  const Qv<T, N> xzm = ldq_nb<T, T, N>(x, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
+  const Qv<T, N> xzp = ldq_nb<T, T, N>(x, s0, z < 7, 64, g, b, sidx(0, 0, 1), ry);
+  const Qv<T, N> gmy = ldq_nb<T, C, N>(gx + S, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
+  const Qv<T, N> gmz = ldq_nb<T, C, N>(gx + 2 * S, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
+  // row ends: the neighbouring lanes' end values, else the x-neighbour brick
+  const T prev_last = __shfl_up_sync(0xffffffffu, xc.v[N - 1], 1);
+  const T prev_glast = __shfl_up_sync(0xffffffffu, gpx.v[N - 1], 1);
+  const T next_first = __shfl_down_sync(0xffffffffu, xc.v[0], 1);
   T xl, xr, gl;
   if (h == 0) {
-    xr = o_first;
     const int nb = __ldg(&g.nbr[(size_t)b * 27 + sidx(-1, 0, 0)]);
     const size_t m = (size_t)nb * BV + (size_t)z * 64 + (size_t)y * 8 + 7;
     xl = nb >= 0 ? x[m] : T(0);
     gl = nb >= 0 ? cvt<T>(gx[m]) : T(0);
   } else {
-    xl = o_last;
-    gl = og_last;
+    xl = prev_last;
+    gl = prev_glast;
+  }
+  if (h == TPR - 1) {
     const int nb = __ldg(&g.nbr[(size_t)b * 27 + sidx(1, 0, 0)]);
     xr = nb >= 0 ? x[(size_t)nb * BV + (size_t)z * 64 + (size_t)y * 8] : T(0);
+  } else {
+    xr = next_first;
   }
-  Q4<T> dg;
-  if constexpr (sizeof(T) == 8) dg = ldq<T>(diag + s0);
+  Qv<T, N> dg;
+  if constexpr (sizeof(T) == 8) dg = ldqn<T, T, N>(diag + s0);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < N; ++i) {
     const T c = xc.v[i];
-    const T left = i > 0 ? xc.v[i - 1] : xl, right = i < 3 ? xc.v[i + 1] : xr;
+    const T left = i > 0 ? xc.v[i - 1] : xl, right = i < N - 1 ? xc.v[i + 1] : xr;
     const T gmx = i > 0 ? gpx.v[i - 1] : gl;
     if constexpr (sizeof(T) == 4) {
       const T ax = gpx.v[i] * (c - right) + gmx * (c - left) + gpy.v[i] * (c - xyp.v[i]) +
