@@ -62,6 +62,26 @@ static void coarse_flags(const Level &f, int *CX, int *CY, int *CZ,
       }
 }
 
+// Host-to-device copy for the build.  A pinned block is read by the SMs over
+// the chip-to-chip link, which on GB300 reaches the copy engine's bandwidth,
+// so the build's uploads do not queue behind a large copy the caller may have
+// on the copy engine meanwhile (e.g. the next source field); any other host
+// memory goes through cudaMemcpyAsync.
+static spfd_status h2d(spfd_ctx *c, void *dst, const void *src, size_t bytes) {
+  if (bytes == 0) return SPFD_OK;
+  cudaPointerAttributes at{};
+  const bool mapped = cudaPointerGetAttributes(&at, src) == cudaSuccess &&
+                      at.type == cudaMemoryTypeHost && at.devicePointer != nullptr;
+  cudaGetLastError();  // an unregistered pointer is not an error here
+  if (mapped && (uintptr_t)dst % 16 == 0 && (uintptr_t)at.devicePointer % 16 == 0) {
+    launch_pull(dst, at.devicePointer, bytes, c->stream);
+    ++c->launch_count;
+    return launch_check("upload");
+  }
+  CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  return SPFD_OK;
+}
+
 // One asynchronous upload of host tables: each (host vector, device slot)
 // pair is packed into a pinned block, copied into one device block, and the
 // slot pointed at its part.  The pinned block stays with the context.
@@ -89,7 +109,7 @@ struct TableUpload {
       *it.dst = d + off;
       off += (it.bytes + 255) / 256 * 256;
     }
-    CU(cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, c->stream));
+    TRY(h2d(c, d, h, total));
     return SPFD_OK;
   }
 };
@@ -276,22 +296,26 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
   dmean /= m;
   for (int a = 0; a < m; ++a) A[(size_t)a * m + a] += 1e-8 * dmean;
   TRY(dalloc(c, &c->cidx, m));
-  CU(cudaMemcpyAsync(c->cidx, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice,
-                     c->stream));
+  int *hidx = nullptr;
+  TRY(halloc(c, &hidx, m));
+  memcpy(hidx, idx.data(), m * sizeof(int));
+  TRY(h2d(c, c->cidx, hidx, m * sizeof(int)));
+  double *hA = nullptr;  // pinned staging of the matrix (or its inverse)
+  TRY(halloc(c, &hA, (size_t)m * m));
   if (m <= 64) {  // small: invert on the host
     if (!invert_spd(A, m))
       return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
     TRY(dalloc(c, &c->Binv, (size_t)m * m));
-    CU(cudaMemcpyAsync(c->Binv, A.data(), (size_t)m * m * sizeof(double),
-                       cudaMemcpyHostToDevice, c->stream));
+    memcpy(hA, A.data(), (size_t)m * m * sizeof(double));
+    TRY(h2d(c, c->Binv, hA, (size_t)m * m * sizeof(double)));
     return sync_check(c, "coarsest upload");
   }
   // larger: Gauss-Jordan sweeps on the device (ping-pong between two buffers)
   double *b0 = nullptr, *b1 = nullptr;
   TRY(dalloc(c, &b0, (size_t)m * m));
   TRY(dalloc(c, &b1, (size_t)m * m));
-  CU(cudaMemcpyAsync(b0, A.data(), (size_t)m * m * sizeof(double),
-                     cudaMemcpyHostToDevice, c->stream));
+  memcpy(hA, A.data(), (size_t)m * m * sizeof(double));
+  TRY(h2d(c, b0, hA, (size_t)m * m * sizeof(double)));
   double *inv = nullptr;
   SPFD_LAUNCH(c, "setup_coarsest", false, (m + 15) / 16, 0, 2.0 * m * m * m,
               inv = launch_dense_inverse(b0, b1, m, &c->sc->status, c->stream));
@@ -511,7 +535,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     for (int b = 0; b < nb0; ++b) { hoff[b] = (int)tot; tot += hcnt[b]; }
     c->ncomp = (int)tot;
     if (nb0)
-      CU(cudaMemcpyAsync(offsets, hoff, nb0 * sizeof(int), cudaMemcpyHostToDevice, st));
+      TRY(h2d(c, offsets, hoff, nb0 * sizeof(int)));
     SPFD_LAUNCH(c, "setup_components", false, 2, 0, 0, launch_assign_comp(l0.g, parent, offsets, c->comp, st));
     TRY(dalloc(c, &c->csize, std::max(c->ncomp, 1)));
     CU(cudaMemsetAsync(c->csize, 0, std::max(c->ncomp, 1) * sizeof(int), st));
@@ -698,7 +722,8 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   CU(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
   CU(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
   const double inv_ndof = c->ndof ? 1.0 / (double)c->ndof : 0.0;
-  CU(cudaMemcpyAsync(&c->sc->inv_ndof, &inv_ndof, sizeof(double), cudaMemcpyHostToDevice, st));
+  launch_set_f64(&c->sc->inv_ndof, inv_ndof, st);
+  ++c->launch_count;
   CU(cudaEventRecord(c->ev1, st));
   TRY(sync_check(c, "build"));
   if (c->hsc->status & DEV_BAD_PIVOT)

@@ -148,6 +148,11 @@ void launch_root_counts(const Grid &g, const int *parent, int *counts,
                         cudaStream_t st);
 void launch_assign_comp(const Grid &g, const int *parent, const int *offsets,
                         int *comp, cudaStream_t st);
+// dst (device, 16-byte aligned) = bytes of src_mapped, pinned host memory
+// mapped into the device's address space (16-byte aligned), read by the SMs.
+void launch_pull(void *dst, const void *src_mapped, size_t bytes, cudaStream_t st);
+// *p = v on the device.
+void launch_set_f64(double *p, double v, cudaStream_t st);
 // Brick tables from the brick maps and coordinates already on the device:
 // nbr [nb][27] of level g; kid [gc.nb][27] of coarse level gc (fine bricks of
 // level gf); par [gf.nb][8] of fine level gf (coarse bricks of level gc).

@@ -551,4 +551,30 @@ void launch_brick_par(const Grid &gf, const Grid &gc, int *par, cudaStream_t st)
   if (gf.nb) k_brick_par<<<table_blocks((long long)gf.nb * 8), 256, 0, st>>>(gf, gc, par);
 }
 
+// ------------------------------------------------------------ uploads
+// dst = src for n16 16-byte words, src in pinned host memory read by the SMs
+// over the chip-to-chip link (both 16-byte aligned), then the tail bytes.
+__global__ void k_pull(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n16,
+                       const unsigned char *__restrict__ tsrc, unsigned char *__restrict__ tdst,
+                       int ntail) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+  if (blockIdx.x == 0 && (int)threadIdx.x < ntail) tdst[threadIdx.x] = tsrc[threadIdx.x];
+}
+
+void launch_pull(void *dst, const void *src_mapped, size_t bytes, cudaStream_t st) {
+  const size_t n16 = bytes / 16;
+  const int ntail = (int)(bytes % 16);
+  size_t blocks = (n16 + 255) / 256;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  if (blocks == 0) blocks = 1;
+  k_pull<<<(unsigned)blocks, 256, 0, st>>>(
+      (const uint4 *)src_mapped, (uint4 *)dst, n16,
+      (const unsigned char *)src_mapped + n16 * 16, (unsigned char *)dst + n16 * 16, ntail);
+}
+
+__global__ void k_set_f64(double *p, double v) { *p = v; }
+void launch_set_f64(double *p, double v, cudaStream_t st) { k_set_f64<<<1, 1, 0, st>>>(p, v); }
+
 }  // namespace spfd
