@@ -170,9 +170,12 @@ struct spfd_ctx {
   // scratch of spfd_percentile (allocated on first use, grown on demand):
   // per-group counters, digit histograms, the key segments, the chunk table
   // and its pinned host staging
-  unsigned long long *pct_small = nullptr, *pct_keys = nullptr;
-  unsigned *pct_hist = nullptr;
+  unsigned long long *pct_small = nullptr, *pct_keys = nullptr, *pct_cand = nullptr,
+                     *pct_boff = nullptr;
+  unsigned *pct_hist = nullptr, *pct_bcnt = nullptr;
+  int *pct_candg = nullptr;
   long long *pct_chunks = nullptr, *pct_hstage = nullptr;
+  long long pct_bcap = 0;
   int pct_gcap = 0, pct_chcap = 0;
   long long pct_keycap = 0, pct_nc = 0;  // pct_nc: conducting voxels seen last call
   size_t pct_hstage_n = 0;

@@ -66,16 +66,22 @@ __device__ __forceinline__ unsigned warp_group_add(unsigned *cnt, int g, unsigne
   return base + rank * v;
 }
 
-// 1. Voxels per group (groups 0..L-1 by label, L for the body).
+// Block b takes tiles b, b + grid, b + 2 grid, ... in both the count and the
+// scatter pass (same grid), so each block's keys of a group form one run
+// whose offset the scan fixes in advance.
+
+// 1. Voxels per group and block: bcount[block][g] (groups 0..L-1 by label,
+// L for the body).
 __global__ void __launch_bounds__(PT)
 k_pct_count(const unsigned char *__restrict__ mask, const double *__restrict__ E,
             const int *__restrict__ labels, long long nv, int L,
-            unsigned long long *__restrict__ count, int *status) {
+            unsigned *__restrict__ bcount, int *status) {
   extern __shared__ unsigned scnt[];  // L + 1
   for (int g = threadIdx.x; g <= L; g += PT) scnt[g] = 0;
   __syncthreads();
-  for (long long base = (long long)blockIdx.x * PCT_TILE; base < nv;
-       base += (long long)gridDim.x * PCT_TILE) {
+  const long long tiles = (nv + PCT_TILE - 1) / PCT_TILE;
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long base = tile * PCT_TILE;
     for (int q = 0; q < PCT_TILE / PT; ++q) {
       const long long v = base + q * PT + threadIdx.x;
       const bool cond = v < nv && mask[v];
@@ -89,26 +95,56 @@ k_pct_count(const unsigned char *__restrict__ mask, const double *__restrict__ E
     }
   }
   __syncthreads();
-  for (int g = threadIdx.x; g <= L; g += PT)
-    if (scnt[g]) atomicAdd(&count[g], (unsigned long long)scnt[g]);
+  for (int g = threadIdx.x; g <= L; g += PT) bcount[(size_t)blockIdx.x * (L + 1) + g] = scnt[g];
 }
 
-// 2. Keys into the segments: group g owns seg[off[g] .. off[g] + count[g]).
-// Each block reserves one contiguous run per group for its tile, so the
-// writes of a tile stay together.
+// 1b. One block per group: exclusive scan of the per-block counts over the
+// blocks (boff), and the group's total (count).
+__global__ void __launch_bounds__(PT)
+k_pct_scan(const unsigned *__restrict__ bcount, int nblk, int G,
+           unsigned long long *__restrict__ boff, unsigned long long *__restrict__ count) {
+  __shared__ unsigned long long part[PT];
+  const int g = blockIdx.x;
+  const int per = (nblk + PT - 1) / PT;
+  const int b0 = threadIdx.x * per, b1 = b0 + per < nblk ? b0 + per : nblk;
+  unsigned long long s = 0;
+  for (int b = b0; b < b1; ++b) s += bcount[(size_t)b * G + g];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < PT; o <<= 1) {
+    const unsigned long long add = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  unsigned long long run = part[threadIdx.x] - s;
+  for (int b = b0; b < b1; ++b) {
+    boff[(size_t)b * G + g] = run;
+    run += bcount[(size_t)b * G + g];
+  }
+  if (threadIdx.x == PT - 1) count[g] = part[PT - 1];
+}
+
+// 2. Keys into the segments: group g owns seg[off[g] .. off[g] + count[g]),
+// in which block b's keys of group g start at boff[b][g].  No global atomics:
+// a tile's keys take positions from shared-memory counters.
 __global__ void __launch_bounds__(PT)
 k_pct_scatter(const unsigned char *__restrict__ mask, const double *__restrict__ E,
               const int *__restrict__ labels, long long nv, int L,
-              const long long *__restrict__ off, const unsigned long long *__restrict__ count,
-              unsigned long long *__restrict__ cursor, unsigned long long *__restrict__ seg,
-              int *status) {
+              const long long *__restrict__ off, const unsigned long long *__restrict__ boff,
+              const unsigned long long *__restrict__ count,
+              unsigned long long *__restrict__ seg, int *status) {
   extern __shared__ unsigned char smem[];
-  unsigned *lc = (unsigned *)smem;                                   // L + 1
-  unsigned long long *gb = (unsigned long long *)(smem + 8 * ((L + 2) / 2));
+  const int G = L + 1;
+  unsigned *lc = (unsigned *)smem;   // this tile's counts
+  unsigned *run = lc + G;            // this block's keys so far, per group
   constexpr int Q = PCT_TILE / PT;
-  for (long long base = (long long)blockIdx.x * PCT_TILE; base < nv;
-       base += (long long)gridDim.x * PCT_TILE) {
-    for (int g = threadIdx.x; g <= L; g += PT) lc[g] = 0;
+  for (int g = threadIdx.x; g < G; g += PT) run[g] = 0;
+  const long long tiles = (nv + PCT_TILE - 1) / PCT_TILE;
+  const unsigned long long *bo = boff + (size_t)blockIdx.x * G;
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long base = tile * PCT_TILE;
+    for (int g = threadIdx.x; g < G; g += PT) lc[g] = 0;
     __syncthreads();
     unsigned long long key[Q];
     int grp[Q];
@@ -128,34 +164,36 @@ k_pct_scatter(const unsigned char *__restrict__ mask, const double *__restrict__
       lb[q] = warp_group_add(lc, L, 1u, active);
     }
     __syncthreads();
-    for (int g = threadIdx.x; g <= L; g += PT)
-      gb[g] = lc[g] ? atomicAdd(&cursor[g], (unsigned long long)lc[g]) : 0ull;
-    __syncthreads();
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       if (grp[q] == -2) continue;
       // positions stay inside the segments when count and scatter saw the
       // same inputs; anything else is flagged instead of written
       if (grp[q] >= 0) {
-        const unsigned long long pos = gb[grp[q]] + li[q];
-        if (pos < count[grp[q]]) seg[off[grp[q]] + pos] = key[q];
+        const int t = grp[q];
+        const unsigned long long pos = bo[t] + run[t] + li[q];
+        if (pos < count[t]) seg[off[t] + pos] = key[q];
         else atomicOr(status, PCT_BAD_RANK);
       }
-      const unsigned long long pos = gb[L] + lb[q];
+      const unsigned long long pos = bo[L] + run[L] + lb[q];
       if (pos < count[L]) seg[off[L] + pos] = key[q];
       else atomicOr(status, PCT_BAD_RANK);
     }
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += PT) run[g] += lc[g];
     __syncthreads();
   }
 }
 
 // 3a. Digit histogram of the keys of one chunk that match their group's
-// prefix above the digit.
+// prefix above the digit; with cand_key set, the matching keys are also
+// appended (with their group) to the candidate list.
 __global__ void __launch_bounds__(PT)
 k_pct_hist(const unsigned long long *__restrict__ seg, const int *__restrict__ chunk_group,
            const long long *__restrict__ chunk_begin, const long long *__restrict__ chunk_end,
            const unsigned long long *__restrict__ prefix, int shift, int width,
-           unsigned *__restrict__ ghist) {
+           unsigned *__restrict__ ghist, unsigned long long *__restrict__ cand_key,
+           int *__restrict__ cand_grp, unsigned long long *__restrict__ cand_n) {
   __shared__ unsigned hist[PCT_BINS];
   const int g = chunk_group[blockIdx.x];
   const long long b = chunk_begin[blockIdx.x], e = chunk_end[blockIdx.x];
@@ -169,12 +207,43 @@ k_pct_hist(const unsigned long long *__restrict__ seg, const int *__restrict__ c
     const unsigned long long k = in ? __ldg(&seg[i]) : 0ull;
     const bool match = in && (k >> hi) == want;
     const unsigned m = __ballot_sync(0xffffffffu, match);
-    if (match) warp_group_add(hist, (int)((k >> shift) & dmask), 1u, m);
+    if (match) {
+      warp_group_add(hist, (int)((k >> shift) & dmask), 1u, m);
+      if (cand_key) {  // keep the matching keys for the later rounds
+        const unsigned lane = threadIdx.x & 31;
+        const int leader = __ffs(m) - 1;
+        unsigned long long pos0 = 0;
+        if ((int)lane == leader) pos0 = atomicAdd(cand_n, (unsigned long long)__popc(m));
+        pos0 = __shfl_sync(m, pos0, leader);
+        const unsigned long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
+        cand_key[pos] = k;
+        cand_grp[pos] = g;
+      }
+    }
   }
   __syncthreads();
   unsigned *row = ghist + (size_t)g * PCT_BINS;
   for (int i = threadIdx.x; i <= (int)dmask; i += PT)
     if (hist[i]) atomicAdd(&row[i], hist[i]);
+}
+
+// 3c. The same over the compacted candidates (few keys): global-memory
+// histogram counters, grid-stride over the *cand_n candidates.
+__global__ void __launch_bounds__(PT)
+k_pct_hist_cand(const unsigned long long *__restrict__ cand_key, const int *__restrict__ cand_grp,
+                const unsigned long long *__restrict__ cand_n,
+                const unsigned long long *__restrict__ prefix, int shift, int width,
+                unsigned *__restrict__ ghist) {
+  const unsigned long long n = *cand_n;
+  const int hi = shift + width;
+  const unsigned dmask = (1u << width) - 1u;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * PT + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * PT) {
+    const unsigned long long k = cand_key[i];
+    const int g = cand_grp[i];
+    if ((k >> hi) == (prefix[g] >> hi))
+      atomicAdd(&ghist[(size_t)g * PCT_BINS + ((k >> shift) & dmask)], 1u);
+  }
 }
 
 // 3b. One block per group: the digit whose bucket holds the remaining rank;
@@ -278,19 +347,29 @@ extern "C" spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev,
     CU(cudaMemsetAsync(c->pct_hist, 0, (size_t)G * PCT_BINS * sizeof(unsigned), st));
     c->pct_gcap = G;
   }
-  unsigned long long *cnt = c->pct_small, *cur = cnt + G, *pre = cur + G, *rk = pre + G;
+  // cand_n (first entry of its slot): candidates kept after the first digit
+  unsigned long long *cnt = c->pct_small, *cand_n = cnt + G, *pre = cand_n + G, *rk = pre + G;
   long long *off = (long long *)(rk + G);
   int *status = (int *)(off + G);
   CU(cudaMemsetAsync(c->pct_small, 0, ((size_t)5 * G + 1) * 8, st));
   const long long tiles = (nv + PCT_TILE - 1) / PCT_TILE;
   const int grid = (int)std::max(1LL, std::min(tiles, (long long)c->nsm * 8));
+  if (c->pct_bcap < (long long)grid * G) {
+    dfree(c, c->pct_bcnt);
+    dfree(c, c->pct_boff);
+    TRY(dalloc(c, &c->pct_bcnt, (size_t)grid * G));
+    TRY(dalloc(c, &c->pct_boff, (size_t)grid * G));
+    c->pct_bcap = (long long)grid * G;
+  }
   const size_t sm_count = (size_t)G * sizeof(unsigned);
   // algorithmic bytes: the mask of every voxel, E and the label of each
   // conducting one (counted from the previous call; all voxels on the first)
   const double ncv = c->pct_nc > 0 ? (double)c->pct_nc : (double)nv;
   SPFD_LAUNCH(c, "percentile_count", false, 1, nv + 12.0 * ncv, 0,
-              (k_pct_count<<<grid, PT, sm_count, st>>>(c->mask, E_dev, lab, nv, L, cnt,
+              (k_pct_count<<<grid, PT, sm_count, st>>>(c->mask, E_dev, lab, nv, L, c->pct_bcnt,
                                                        status)));
+  SPFD_LAUNCH(c, "percentile_count", false, 1, 12.0 * grid * G, 0,
+              (k_pct_scan<<<G, PT, 0, st>>>(c->pct_bcnt, grid, G, c->pct_boff, cnt)));
   TRY(launch_check("percentile count"));
   std::vector<unsigned long long> hc(G);
   int hstatus = 0;
@@ -317,7 +396,11 @@ extern "C" spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev,
   const int nch = (int)cg.size();
   if (c->pct_keycap < total) {
     dfree(c, c->pct_keys);
+    dfree(c, c->pct_cand);
+    dfree(c, c->pct_candg);
     TRY(dalloc(c, &c->pct_keys, (size_t)total));
+    TRY(dalloc(c, &c->pct_cand, (size_t)total));
+    TRY(dalloc(c, &c->pct_candg, (size_t)total));
     c->pct_keycap = total;
   }
   if (c->pct_chcap < nch) {
@@ -349,16 +432,27 @@ extern "C" spfd_status spfd_percentile(spfd_ctx *ctx, const double *E_dev,
     CU(cudaMemcpyAsync(dcb, hch, (size_t)2 * nch * 8, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(dcg, hcg, (size_t)nch * sizeof(int), cudaMemcpyHostToDevice, st));
   }
-  const size_t sm_scatter = (size_t)8 * ((G + 1) / 2) + (size_t)8 * G + 16;
+  const size_t sm_scatter = (size_t)2 * G * sizeof(unsigned);
   c->pct_nc = (long long)hc[L];
   SPFD_LAUNCH(c, "percentile_scatter", false, 1, nv + 12.0 * hc[L] + 8.0 * total, 0,
               (k_pct_scatter<<<grid, PT, sm_scatter, st>>>(c->mask, E_dev, lab, nv, L, off,
-                                                           cnt, cur, c->pct_keys, status)));
+                                                           c->pct_boff, cnt, c->pct_keys,
+                                                           status)));
   TRY(launch_check("percentile scatter"));
+  // rounds 0 and 1 read every key (round 1 keeps those that match the first
+  // digit); rounds 2-4 read only those candidates
   for (int r = 0; r < PCT_ROUNDS && nch > 0; ++r) {
-    SPFD_LAUNCH(c, "percentile_hist", false, 1, 8.0 * total, 0,
-                (k_pct_hist<<<nch, PT, 0, st>>>(c->pct_keys, dcg, dcb, dce, pre, PCT_SHIFT[r],
-                                                PCT_WIDTH[r], c->pct_hist)));
+    if (r < 2) {
+      SPFD_LAUNCH(c, "percentile_hist", false, 1, 8.0 * total, 0,
+                  (k_pct_hist<<<nch, PT, 0, st>>>(
+                      c->pct_keys, dcg, dcb, dce, pre, PCT_SHIFT[r], PCT_WIDTH[r], c->pct_hist,
+                      r == 1 ? c->pct_cand : nullptr, c->pct_candg, cand_n)));
+    } else {
+      SPFD_LAUNCH(c, "percentile_hist", false, 1, 0, 0,
+                  (k_pct_hist_cand<<<c->nsm * 4, PT, 0, st>>>(c->pct_cand, c->pct_candg, cand_n,
+                                                              pre, PCT_SHIFT[r], PCT_WIDTH[r],
+                                                              c->pct_hist)));
+    }
     SPFD_LAUNCH(c, "percentile_select", false, 1, 8.0 * G * (1 << PCT_WIDTH[r]), 0,
                 (k_pct_select<<<G, PT, 0, st>>>(c->pct_hist, cnt, pre, rk, PCT_SHIFT[r],
                                                 PCT_WIDTH[r], status)));
