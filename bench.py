@@ -705,13 +705,17 @@ def bench_batch(spfd, torch, dev, stream, ph, sig, nrhs, K, W):
         rep = S.autotune_report()
         if rep:
             out["autotune"] = {
-                "decisions": len(rep), "order1_chosen": sum(r["order"] for r in rep),
+                "decisions": len(rep),
+                "orders_chosen": [sum(r["order"] == k for r in rep) for k in range(3)],
                 "tuned_launch_ms": {f"{r['family']}_l{r['level']}":
-                                    [round(r["ms_order0"], 3), round(r["ms_order1"], 3), r["order"]]
+                                    [round(r["ms_order0"], 3), round(r["ms_order1"], 3),
+                                     round(r["ms_order2"], 3), r["order"]]
                                     for r in rep},
                 "note": "per family and level: [ms per launch in order 0 (right-hand sides one "
                         "after the other), in order 1 (all right-hand sides of a brick side by "
-                        "side), order kept]"}
+                        "side), in order 2 (tiles of 4 right-hand sides per block, operator "
+                        "entries read once per tile; -1 where the family has none), order "
+                        "kept]; orders_chosen counts the decisions per order"}
         S.close()
         return out
 

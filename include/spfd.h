@@ -320,20 +320,25 @@ spfd_status spfd_energy_grad(spfd_ctx *ctx, const double *a_dev, const double *p
 
 /* One decision of the autotuner of batched solves (not in the paper: launch
  * tuning of this library).  A batched launch covers nk right-hand sides
- * over the bricks of a level in one of two block orders: 0 = the
+ * over the bricks of a level in one of three block orders: 0 = the
  * right-hand sides one after the other, 1 = the nk blocks of each brick side
- * by side, so that they share the brick's operator entries through L2.  The
- * first spfd_solve_batch of each batch size (with opts.autotune set) times
- * both orders of every batched kernel family on every level and keeps the
- * faster; results are unchanged either way. */
+ * by side, so that they share the brick's operator entries through L2,
+ * 2 = a tile of 4 right-hand sides per block, which reads the brick's
+ * operator entries (27-point stencils, interpolation weights) into registers
+ * once for the tile (the 27-point smoother and residual, restriction and
+ * prolongation, for batches of 4 or more).  The first spfd_solve_batch of
+ * each batch size (with opts.autotune set) times the orders of every batched
+ * kernel family on every level and keeps the fastest; results are unchanged
+ * whichever is kept. */
 typedef struct {
   const char *family;  /* "jacobi_first", "smooth", "residual", "restrict",
                           "prolong" (fine level) or "apply_dot" (static) */
   int level;           /* multigrid level (0 = finest) */
   int nrhs;            /* batch size tuned for */
-  int order;           /* the order kept (0 or 1) */
+  int order;           /* the order kept (0, 1 or 2) */
   double ms_order0;    /* mean time of one launch in order 0 */
   double ms_order1;    /* mean time of one launch in order 1 */
+  double ms_order2;    /* mean time of one launch in order 2, -1 if not timed */
 } spfd_tune_entry;
 
 /* The autotuner's decisions for this context, oldest first.

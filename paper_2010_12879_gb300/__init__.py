@@ -65,7 +65,7 @@ class SpfdKernelStat(ctypes.Structure):
 class SpfdTuneEntry(ctypes.Structure):
     _fields_ = [("family", ctypes.c_char_p), ("level", ctypes.c_int), ("nrhs", ctypes.c_int),
                 ("order", ctypes.c_int), ("ms_order0", ctypes.c_double),
-                ("ms_order1", ctypes.c_double)]
+                ("ms_order1", ctypes.c_double), ("ms_order2", ctypes.c_double)]
 
 
 class SpfdError(RuntimeError):
@@ -248,7 +248,8 @@ def spfd_autotune_report(ctx: int) -> list:
     arr = (SpfdTuneEntry * max(n.value, 1))()
     _check(lib().spfd_autotune_report(ctypes.c_void_p(ctx), arr, n.value, ctypes.byref(n)))
     return [{"family": e.family.decode(), "level": e.level, "nrhs": e.nrhs, "order": e.order,
-             "ms_order0": e.ms_order0, "ms_order1": e.ms_order1} for e in arr[:n.value]]
+             "ms_order0": e.ms_order0, "ms_order1": e.ms_order1, "ms_order2": e.ms_order2}
+            for e in arr[:n.value]]
 
 
 def spfd_release_cached_memory() -> int:

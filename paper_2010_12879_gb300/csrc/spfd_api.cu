@@ -339,14 +339,22 @@ static spfd_status autotune_orders(spfd_ctx *c, int nk, std::vector<signed char>
     *ms *= 0.5f;
     return launch_check("autotune");
   };
-  auto pick = [&](int fam, int l, int units, const auto &launch) -> spfd_status {
+  // SPFD_TUNE_FORCE=k keeps order k wherever it was timed (a test hook: all
+  // orders give the same results, so a test can run each one)
+  const char *force_env = getenv("SPFD_TUNE_FORCE");
+  const int force = force_env ? atoi(force_env) : -1;
+  // tile: whether the family has the right-hand-side tile (order 2)
+  auto pick = [&](int fam, int l, int units, bool tile, const auto &launch) -> spfd_status {
     if (units <= 0 || !order1_fits(units, nk)) return SPFD_OK;
-    float m0 = 0.f, m1 = 0.f;
-    TRY(timed(launch, 0, &m0));
-    TRY(timed(launch, 1, &m1));
-    const int best = m1 < m0 ? 1 : 0;
+    float m[3] = {0.f, 0.f, -1.f};
+    TRY(timed(launch, 0, &m[0]));
+    TRY(timed(launch, 1, &m[1]));
+    if (tile && nk >= RHS_TILE) TRY(timed(launch, 2, &m[2]));
+    int best = m[1] < m[0] ? 1 : 0;
+    if (m[2] >= 0.f && m[2] < m[best]) best = 2;
+    if (force >= 0 && force <= 2 && m[force] >= 0.f) best = force;
     tab[(size_t)fam * nl + l] = (signed char)best;
-    c->tune_log.push_back(TuneRecord{fam, l, nk, best, (double)m0, (double)m1});
+    c->tune_log.push_back(TuneRecord{fam, l, nk, best, (double)m[0], (double)m[1], (double)m[2]});
     return SPFD_OK;
   };
   for (int l = 0; l + 1 < nl; ++l) {
@@ -355,35 +363,35 @@ static spfd_status autotune_orders(spfd_ctx *c, int nk, std::vector<signed char>
     const T *wd = lv.WDINV<T>();
     T *x = lv.X<T>(), *t = lv.Tt<T>(), *b = lv.B<T>(), *r = lv.R<T>();
     if (l == 0 && c->ncomp == 1)
-      TRY(pick(TF_JFIRST, l, g.nb, [&](int o) {
+      TRY(pick(TF_JFIRST, l, g.nb, false, [&](int o) {
         launch_jacobi_first_proj<T>(g, wd, b, x, c->sc, 0.0, st, nk, o);
       }));
     else
-      TRY(pick(TF_JFIRST, l, g.nb, [&](int o) { launch_jacobi_first<T>(g, wd, b, x, st, nk, o); }));
+      TRY(pick(TF_JFIRST, l, g.nb, false, [&](int o) { launch_jacobi_first<T>(g, wd, b, x, st, nk, o); }));
     if (l == 0) {
-      TRY(pick(TF_SMOOTH, l, g.nb, [&](int o) {
+      TRY(pick(TF_SMOOTH, l, g.nb, false, [&](int o) {
         launch_jacobi7<T, C7>(g, Prec<T>::gx(lv), lv.DIAG<T>(), wd, x, b, t, st, nk, o);
       }));
-      TRY(pick(TF_RESID, l, g.nb, [&](int o) {
+      TRY(pick(TF_RESID, l, g.nb, false, [&](int o) {
         launch_residual7<T, C7>(g, Prec<T>::gx(lv), lv.DIAG<T>(), x, b, r, st, nk, o);
       }));
       const T *opgx = sizeof(T) == 4 ? (const T *)lv.gx32 : (const T *)lv.gx;
       const T *opdiag = sizeof(T) == 4 ? (const T *)lv.diag32 : (const T *)lv.diag;
-      TRY(pick(TF_APPLY, l, g.nb, [&](int o) {
+      TRY(pick(TF_APPLY, l, g.nb, false, [&](int o) {
         launch_apply_dot<T>(g, opgx, opdiag, x, r, c->sc, c->partials, st, nk, c->pstride, o);
       }));
     } else {
-      TRY(pick(TF_SMOOTH, l, g.nb, [&](int o) {
+      TRY(pick(TF_SMOOTH, l, g.nb, true, [&](int o) {
         launch_jacobi27<T>(g, lv.ST<T>(), wd, x, b, t, st, nk, o);
       }));
-      TRY(pick(TF_RESID, l, g.nb, [&](int o) {
+      TRY(pick(TF_RESID, l, g.nb, true, [&](int o) {
         launch_residual27<T>(g, lv.ST<T>(), x, b, r, st, nk, o);
       }));
     }
-    TRY(pick(TF_RESTRICT, l, cl.g.nb, [&](int o) {
+    TRY(pick(TF_RESTRICT, l, cl.g.nb, true, [&](int o) {
       launch_restrict<T>(g, cl.g, cl.PP<T>(), r, cl.B<T>(), st, nk, o);
     }));
-    TRY(pick(TF_PROLONG, l, (g.nb + 1) / 2, [&](int o) {
+    TRY(pick(TF_PROLONG, l, (g.nb + 1) / 2, true, [&](int o) {
       launch_prolong<T>(g, cl.g, lv.PC<T>(), cl.X<T>(), x, st, nk, o);
     }));
   }
@@ -1010,6 +1018,7 @@ extern "C" spfd_status spfd_autotune_report(const spfd_ctx *ctx, spfd_tune_entry
     entries[i].order = r.order;
     entries[i].ms_order0 = r.ms0;
     entries[i].ms_order1 = r.ms1;
+    entries[i].ms_order2 = r.ms2;
   }
   return SPFD_OK;
 }

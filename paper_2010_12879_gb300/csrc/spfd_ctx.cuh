@@ -99,7 +99,7 @@ enum TuneFam : int {
 };
 struct TuneRecord {
   int fam, level, nk, order;
-  double ms0, ms1;  // mean time per launch in order 0 and order 1
+  double ms0, ms1, ms2;  // mean time per launch in orders 0, 1, 2 (-1: not timed)
 };
 
 struct KernelStat {

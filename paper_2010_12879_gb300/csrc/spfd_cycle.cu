@@ -59,18 +59,33 @@ template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
              const T *__restrict__ b, T *__restrict__ r, int nk) {
-  __shared__ T tl[10][10][10];
+  __shared__ T tl[rhs_tile<ORD>()][10][10][10];
   __shared__ int sn[27];
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
-  const size_t off = (size_t)rhs * g.nb * BV;
-  x += off; b += off; r += off;
-  load_nbr(g, bk, sn);
-  __syncthreads();
-  tile_full<T>(tl, x, bk, sn);
-  __syncthreads();
   const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + threadIdx.x;
-  r[s] = b[s] - apply27_tile<T>(tl, st, S, s);
+  load_nbr(g, bk, sn);
+  if constexpr (rhs_tile<ORD>() == 1) {
+    const size_t off = (size_t)rhs * S;
+    x += off; b += off; r += off;
+    __syncthreads();
+    tile_full<T>(tl[0], x, bk, sn);
+    __syncthreads();
+    r[s] = b[s] - apply27_tile<T>(tl[0], st, S, s);
+  } else {
+    // the tile's right-hand sides side by side: all their halo tiles are
+    // loaded at once, then each uses the coefficients held in registers
+    T cf[27];
+    load27(st, S, s, cf);
+    const int nr = min(rhs_tile<ORD>(), nk - rhs);
+    __syncthreads();
+    for (int k = 0; k < nr; ++k) tile_full<T>(tl[k], x + (size_t)(rhs + k) * S, bk, sn);
+    __syncthreads();
+    for (int k = 0; k < nr; ++k) {
+      const size_t off = (size_t)(rhs + k) * S;
+      r[off + s] = b[off + s] - apply27_regs<T>(tl[k], cf);
+    }
+  }
 }
 
 template <typename T, int ORD>
@@ -78,20 +93,35 @@ __global__ void __launch_bounds__(NT)
 k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
            const T *__restrict__ xin, const T *__restrict__ b,
            T *__restrict__ xout, int nk) {
-  __shared__ T tl[10][10][10];
+  __shared__ T tl[rhs_tile<ORD>()][10][10][10];
   __shared__ int sn[27];
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
-  const size_t off = (size_t)rhs * g.nb * BV;
-  xin += off; b += off; xout += off;
-  load_nbr(g, bk, sn);
-  __syncthreads();
-  tile_full<T>(tl, xin, bk, sn);
-  __syncthreads();
   const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
-  const T r = b[s] - apply27_tile<T>(tl, st, S, s);
-  xout[s] = tl[(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wdinv[s] * r;
+  load_nbr(g, bk, sn);
+  if constexpr (rhs_tile<ORD>() == 1) {
+    const size_t off = (size_t)rhs * S;
+    xin += off; b += off; xout += off;
+    __syncthreads();
+    tile_full<T>(tl[0], xin, bk, sn);
+    __syncthreads();
+    const T r = b[s] - apply27_tile<T>(tl[0], st, S, s);
+    xout[s] = tl[0][(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wdinv[s] * r;
+  } else {
+    T cf[27];
+    load27(st, S, s, cf);
+    const T wd = wdinv[s];
+    const int nr = min(rhs_tile<ORD>(), nk - rhs);
+    __syncthreads();
+    for (int k = 0; k < nr; ++k) tile_full<T>(tl[k], xin + (size_t)(rhs + k) * S, bk, sn);
+    __syncthreads();
+    for (int k = 0; k < nr; ++k) {
+      const size_t off = (size_t)(rhs + k) * S;
+      const T r = b[off + s] - apply27_regs<T>(tl[k], cf);
+      xout[off + s] = tl[k][(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wd * r;
+    }
+  }
 }
 
 // First sweep from a zero guess, x = omega D^-1 b: a streaming kernel, one
@@ -155,27 +185,49 @@ k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
-  rf += (size_t)rhs * Sf;
-  bcoarse += (size_t)rhs * gc.nb * BV;
-  if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
-  __syncthreads();
-  for (int q = t; q < 17 * 17 * 17; q += NT) {
-    const int fz = q / 289, fy = (q / 17) % 17, fx = q % 17;
-    const int nb = sk[((fz + 7) >> 3) * 9 + ((fy + 7) >> 3) * 3 + ((fx + 7) >> 3)];
-    fs[fz][fy][fx] = nb >= 0
-        ? rf[(size_t)nb * BV + (((fz - 1) & 7) * 8 + ((fy - 1) & 7)) * 8 + ((fx - 1) & 7)]
-        : T(0);
-  }
-  __syncthreads();
   const size_t Sc = (size_t)gc.nb * BV, s = (size_t)bk * BV + t;
   const int cx = 2 * (t & 7) + 1, cy = 2 * ((t >> 3) & 7) + 1, cz = 2 * (t >> 6) + 1;
-  T acc = 0;
+  if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
+  // the 17^3 fine nodes of right-hand side j into fs
+  auto fill = [&](const T *__restrict__ src) {
+    for (int q = t; q < 17 * 17 * 17; q += NT) {
+      const int fz = q / 289, fy = (q / 17) % 17, fx = q % 17;
+      const int nb = sk[((fz + 7) >> 3) * 9 + ((fy + 7) >> 3) * 3 + ((fx + 7) >> 3)];
+      fs[fz][fy][fx] = nb >= 0
+          ? src[(size_t)nb * BV + (((fz - 1) & 7) * 8 + ((fy - 1) & 7)) * 8 + ((fx - 1) & 7)]
+          : T(0);
+    }
+  };
+  if constexpr (rhs_tile<ORD>() == 1) {
+    rf += (size_t)rhs * Sf;
+    bcoarse += (size_t)rhs * Sc;
+    __syncthreads();
+    fill(rf);
+    __syncthreads();
+    T acc = 0;
 #pragma unroll
-  for (int d = 0; d < 27; ++d) {
-    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-    acc += P[(size_t)d * Sc + s] * fs[cz + dz][cy + dy][cx + dx];
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      acc += P[(size_t)d * Sc + s] * fs[cz + dz][cy + dy][cx + dx];
+    }
+    bcoarse[s] = acc;
+  } else {
+    T w[27];
+    load27(P, Sc, s, w);
+    const int nr = min(rhs_tile<ORD>(), nk - rhs);
+    for (int k = 0; k < nr; ++k) {
+      __syncthreads();  // sk is loaded / the previous tile is consumed
+      fill(rf + (size_t)(rhs + k) * Sf);
+      __syncthreads();
+      T acc = 0;
+#pragma unroll
+      for (int d = 0; d < 27; ++d) {
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        acc += w[d] * fs[cz + dz][cy + dy][cx + dx];
+      }
+      bcoarse[(size_t)(rhs + k) * Sc + s] = acc;
+    }
   }
-  bcoarse[s] = acc;
 }
 
 // Prolongation + correction e_f(n) += sum over the <= 8 parents I of n of
@@ -193,8 +245,6 @@ k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
   unit_rhs<ORD>(nk, pair, rhs);
   const int bk = pair * 2 + (threadIdx.x >> 6);
   if (bk >= gf.nb) return;
-  ec += (size_t)rhs * gc.nb * BV;
-  ef += (size_t)rhs * gf.nb * BV;
   const int cell = threadIdx.x & 63;
   const int ccx = cell & 3, ccy = (cell >> 2) & 3, ccz = cell >> 4;
   const size_t NC = (size_t)gf.nb * 64, cid = (size_t)bk * 64 + cell;
@@ -202,6 +252,10 @@ k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
 #pragma unroll
   for (int j = 0; j < 27; ++j) w[j] = Pc[(size_t)j * NC + cid];
   const int4 bc = gf.bco[bk];
+  const int nr = rhs_tile<ORD>() == 1 ? 1 : min(rhs_tile<ORD>(), nk - rhs);
+  for (int k = 0; k < nr; ++k) {  // one pass unless ORD is the right-hand-side tile
+  const T *__restrict__ ecj = ec + (size_t)(rhs + k) * gc.nb * BV;
+  T *__restrict__ efj = ef + (size_t)(rhs + k) * gf.nb * BV;
   T e[8];
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
@@ -210,12 +264,12 @@ k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
     const int pb = (((gz_ >> 3) - (bc.z >> 1)) << 2) | (((gy_ >> 3) - (bc.y >> 1)) << 1) |
                    ((gx_ >> 3) - (bc.x >> 1));
     const int nb = __ldg(&gf.par[(size_t)bk * 8 + pb]);
-    e[o] = nb >= 0 ? ec[(size_t)nb * BV + ((gz_ & 7) * 8 + (gy_ & 7)) * 8 + (gx_ & 7)] : T(0);
+    e[o] = nb >= 0 ? ecj[(size_t)nb * BV + ((gz_ & 7) * 8 + (gy_ & 7)) * 8 + (gx_ & 7)] : T(0);
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) {  // r = uz*2 + uy: one 2-vector (ux = 0, 1) per row
     const int uy = r & 1, uz = r >> 1;
-    T *row = ef + (size_t)bk * BV + ((2 * ccz + uz) * 8 + 2 * ccy + uy) * 8 + 2 * ccx;
+    T *row = efj + (size_t)bk * BV + ((2 * ccz + uz) * 8 + 2 * ccy + uy) * 8 + 2 * ccx;
     T v[2];
     if constexpr (sizeof(T) == 4) {
       const float2 u = *reinterpret_cast<const float2 *>(row);
@@ -233,6 +287,7 @@ k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
     }
     if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(row) = make_float2(v[0], v[1]);
     else *reinterpret_cast<double2 *>(row) = make_double2(v[0], v[1]);
+  }
   }
 }
 
@@ -271,7 +326,8 @@ template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
                        T *r, cudaStream_t st, int nk, int order) {
   if (!g.nb) return;
-  if (order) k_residual27<T, 1><<<unit_grid(1, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
+  if (order == 2) k_residual27<T, 2><<<unit_grid(2, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
+  else if (order) k_residual27<T, 1><<<unit_grid(1, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
   else k_residual27<T, 0><<<unit_grid(0, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
 }
 template <typename T>
@@ -316,7 +372,9 @@ void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
                      const T *b, T *xout, cudaStream_t st, int nk, int order) {
   if (g.nb)
   {
-    if (order)
+    if (order == 2)
+      k_jacobi27<T, 2><<<unit_grid(2, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
+    else if (order)
       k_jacobi27<T, 1><<<unit_grid(1, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
     else
       k_jacobi27<T, 0><<<unit_grid(0, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
@@ -327,7 +385,10 @@ void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
                      T *bcoarse, cudaStream_t st, int nk, int order) {
   if (gc.nb)
   {
-    if (order)
+    if (order == 2)
+      k_restrict<T, 2><<<unit_grid(2, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
+                                                               bcoarse, nk);
+    else if (order)
       k_restrict<T, 1><<<unit_grid(1, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
                                                                bcoarse, nk);
     else
@@ -340,7 +401,9 @@ void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
                     T *ef, cudaStream_t st, int nk, int order) {
   if (gf.nb)
   {
-    if (order)
+    if (order == 2)
+      k_prolong<T, 2><<<unit_grid(2, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
+    else if (order)
       k_prolong<T, 1><<<unit_grid(1, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
     else
       k_prolong<T, 0><<<unit_grid(0, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);

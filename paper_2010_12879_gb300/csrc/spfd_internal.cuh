@@ -49,19 +49,31 @@ __host__ __device__ __forceinline__ constexpr int crank(int u, int o) {
 // b % nk, so the nk blocks of one unit run side by side and share its
 // operator entries through L2.  The arithmetic of every block is the same
 // in both orders; the autotuner picks one per kernel family and level.
+// Order 2 (the 27-point smoother and residual, restriction, prolongation): a
+// right-hand-side tile, blockIdx.y selects RHS_TILE consecutive right-hand
+// sides that one block handles in turn with the unit's operator entries held
+// in registers, so they are read from memory once per tile; rhs is then the
+// tile's first.  Per right-hand side the arithmetic is again the same.
 // The order is a template parameter, so that the order-0 instances compile to
 // the same code as kernels without a batch order.
+constexpr int RHS_TILE = 4;
+template <int ORD>
+constexpr int rhs_tile() { return ORD == 2 ? RHS_TILE : 1; }
 template <int ORD>
 __device__ __forceinline__ void unit_rhs(int nk, int &unit, int &rhs) {
   if constexpr (ORD == 1) {
     unit = (int)(blockIdx.x / (unsigned)nk);
     rhs = (int)(blockIdx.x % (unsigned)nk);
+  } else if constexpr (ORD == 2) {
+    unit = (int)blockIdx.x;
+    rhs = (int)blockIdx.y * RHS_TILE;
   } else {
     unit = (int)blockIdx.x;
     rhs = (int)blockIdx.y;
   }
 }
 inline dim3 unit_grid(int order, int units, int nk) {
+  if (order == 2) return dim3((unsigned)units, (unsigned)((nk + RHS_TILE - 1) / RHS_TILE));
   return order ? dim3((unsigned)units * (unsigned)nk) : dim3((unsigned)units, (unsigned)nk);
 }
 // Order 1 is available while units * nk fits a one-dimensional grid.

@@ -273,4 +273,25 @@ __device__ __forceinline__ T apply27_tile(const T (*tl)[10][10], const T *__rest
   return acc;
 }
 
+// The 27 entries e * S + s of a direction-major array (stencil coefficients
+// or interpolation weights of one node) into registers.
+template <typename T>
+__device__ __forceinline__ void load27(const T *__restrict__ a, size_t S, size_t s, T (&v)[27]) {
+#pragma unroll
+  for (int e = 0; e < 27; ++e) v[e] = a[(size_t)e * S + s];
+}
+
+// apply27_tile with the coefficients in registers (same order of terms).
+template <typename T>
+__device__ __forceinline__ T apply27_regs(const T (*tl)[10][10], const T (&cf)[27]) {
+  const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  T acc = 0;
+#pragma unroll
+  for (int e = 0; e < 27; ++e) {
+    const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
+    acc += cf[e] * tl[lz + 1 + dz][ly + 1 + dy][lx + 1 + dx];
+  }
+  return acc;
+}
+
 }  // namespace spfd

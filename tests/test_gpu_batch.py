@@ -143,14 +143,19 @@ def test_batch_mixed_random_and_zero(torch_cuda, spfd, oracle_mod, seed, air):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_autotuned_orders_keep_results(torch_cuda, spfd, precision):
-    """Both block orders run the same arithmetic per block: the batch solved
-    with the autotuner's orders equals, bit for bit, the same batch in the
-    fixed order 0; the autotuner records one decision per tuned family and
-    level, for this batch size only."""
+@pytest.mark.parametrize("force", [None, 1, 2])
+def test_batch_autotuned_orders_keep_results(torch_cuda, spfd, precision, force, monkeypatch):
+    """Every block order runs the same arithmetic per right-hand side: the
+    batch solved with the autotuner's orders (or with order 1 or the
+    right-hand-side tile forced wherever it exists) equals, bit for bit, the
+    same batch in the fixed order 0; the autotuner records one decision per
+    tuned family and level, for this batch size only.  Six right-hand sides
+    leave a ragged second tile of two."""
     torch = torch_cuda
+    if force is not None:
+        monkeypatch.setenv("SPFD_TUNE_FORCE", str(force))
     ph = body_phantom(64, 40, 224, h=8e-3)
-    loops = random_loops(4, np.random.default_rng(50))
+    loops = random_loops(6, np.random.default_rng(50))
     A = _dev(torch, np.stack([loop_potential(ph.dims, ph.h, ph.origin, center=c, normal=n)
                               for c, n in loops]))
     prec = spfd.SPFD_FP64 if precision == "fp64" else spfd.SPFD_MIXED
@@ -167,8 +172,16 @@ def test_batch_autotuned_orders_keep_results(torch_cuda, spfd, precision):
         # per non-coarsest level: first sweep, smooth, residual, restrict,
         # prolong; apply_dot on level 0
         assert len(rep) == 5 * (nl - 1) + 1
-        assert all(r["order"] in (0, 1) and r["nrhs"] == 4 for r in rep)
+        assert all(r["order"] in (0, 1, 2) and r["nrhs"] == 6 for r in rep)
         assert all(r["ms_order0"] > 0 and r["ms_order1"] > 0 for r in rep)
+        # the tile exists for the 27-point smoother and residual (levels >= 1)
+        # and for both transfers
+        for r in rep:
+            tile = r["family"] in ("restrict", "prolong") or (
+                r["family"] in ("smooth", "residual") and r["level"] >= 1)
+            assert (r["ms_order2"] > 0) if tile else (r["ms_order2"] == -1), r
+            if force is not None and (force == 1 or tile):
+                assert r["order"] == force, r
         assert S0.autotune_report() == []
         # a second batch of the same size reuses the decisions
         S1.solve_batch(A, 1e-10)
