@@ -237,7 +237,7 @@ spfd_status project(spfd_ctx *c, T *v, int nk, int j0) {
 // is fused into the first sweep, using sum(r) left in each right-hand side's
 // Scalars by the preceding x/r update.
 template <typename T>
-T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk) {
+T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
   Level &lv = c->L[l];
   cudaStream_t st = c->stream;
   const int nl = (int)c->L.size();
@@ -298,7 +298,16 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk) {
               (27.0 / 8.0 + 2.0) * w * S + w * Sc, 7 * S,
               launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st, nk,
                                 block_order(c, TF_PROLONG, l)));
-  for (int s = 0; s < c->opts.nu_post; ++s) { sweep(cur, oth); std::swap(cur, oth); }
+  for (int s = 0; s < c->opts.nu_post; ++s) {
+    if (rz && l == 0 && s + 1 == c->opts.nu_post)
+      SPFD_LAUNCH(c, "jacobi7_l0", f32, 1, (5 * w + 3 * wc) * S, 20 * S,
+                  (launch_jacobi7_rz<T, typename Prec<T>::C7>(
+                      lv.g, Prec<T>::gx(lv), lv.DIAG<T>(), wd, cur, bl, oth, c->partials,
+                      c->pstride, st, nk, block_order(c, TF_SMOOTH, l))));
+    else
+      sweep(cur, oth);
+    std::swap(cur, oth);
+  }
   return cur;
 }
 
@@ -470,10 +479,22 @@ spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
   const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
   const double *csum = c->ncomp > 1 ? c->csum : nullptr;
   cudaStream_t st = c->stream;
-  T *z = vcycle<T>(c, 0, r, true, nk);
-  SPFD_LAUNCH(c, "dot_rz", f32, 1, (2 * w + 4) * S, 3 * S,
-              launch_dot_rz<T>(nb, r, z, c->comp, c->sc, c->partials, first, st, nk,
-                               c->pstride));
+  // In FP32, r.z comes with the last level-0 sweep of the V-cycle when it
+  // has one: that sweep is HBM-bound, so the products and warp sums are free
+  // and a pass over r and z is saved.  The FP64 sweep is FP64-pipe-bound:
+  // its warp sums cost more than the separate pass (0.29 against 0.18 ms per
+  // sweep on the 2 mm body), so FP64 keeps k_dot_rz.
+  const bool fused = f32 && c->L.size() > 1 && c->opts.nu_post >= 1;
+  T *z = vcycle<T>(c, 0, r, true, nk, fused);
+  if (fused)
+    SPFD_LAUNCH(c, "finish_rz", false, 1, 16.0 * jacobi7_rz_partials<T>(nb) * nk, 0,
+                launch_finish_rz(jacobi7_rz_partials<T>(nb), c->partials,
+                                 c->partials + (size_t)16 * nb, c->sc, first, st, nk,
+                                 c->pstride));
+  else
+    SPFD_LAUNCH(c, "dot_rz", f32, 1, (2 * w + 4) * S, 3 * S,
+                launch_dot_rz<T>(nb, r, z, c->comp, c->sc, c->partials, first, st, nk,
+                                 c->pstride));
   if (c->ncomp > 1)
     SPFD_LAUNCH(c, "project", f32, 3, 2 * (w + 4) * S, 12 * S,
                 launch_comp_sum<T>(nb, z, c->comp, c->csum, c->ncomp, c->cstride, st, nk));
@@ -485,7 +506,7 @@ spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
 template spfd_status precondition_step<double>(spfd_ctx *, double *, double *, int, int);
 template spfd_status precondition_step<float>(spfd_ctx *, float *, float *, int, int);
 template spfd_status project<double>(spfd_ctx *, double *, int, int);
-template double *vcycle<double>(spfd_ctx *, int, double *, bool, int);
+template double *vcycle<double>(spfd_ctx *, int, double *, bool, int, bool);
 
 struct PcgResult {
   int iters = 0;

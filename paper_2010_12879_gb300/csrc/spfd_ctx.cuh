@@ -298,7 +298,7 @@ template <typename T>
 spfd_status project(spfd_ctx *c, T *v, int nk = 1, int j0 = 0);
 // V-cycle on level l for nk right-hand sides; returns the corrections.
 template <typename T>
-T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk);
+T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz = false);
 // z = M r, r.z, beta and p = z + beta p for the first nk right-hand sides.
 template <typename T>
 spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk);

@@ -35,11 +35,16 @@ k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
   stqn<T, N>(r + s0, rv);
 }
 
-template <typename T, typename C, int ORD>
+// RZ: the last sweep of the V-cycle on level 0, where b is the CG residual r
+// and xout the preconditioned z: each warp also writes its parts of r.z and
+// of the sum of z over the unknowns (w > 0) to partials[2 (brick warp) + {0,1}]
+// (right-hand side rhs at rhs * pstride), which launch_finish_rz adds.
+template <typename T, typename C, int ORD, bool RZ = false>
 __global__ void __launch_bounds__(BV / row_n_jacobi<T>(), row_min_blocks<T>())
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
-          const T *__restrict__ b, T *__restrict__ xout, int nk) {
+          const T *__restrict__ b, T *__restrict__ xout, int nk,
+          double *__restrict__ partials = nullptr, size_t pstride = 0) {
   constexpr int N = row_n_jacobi<T>();
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
@@ -53,6 +58,21 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
 #pragma unroll
   for (int i = 0; i < N; ++i) xc.v[i] += wv.v[i] * rv.v[i];
   stqn<T, N>(xout + s0, xc);
+  if constexpr (RZ) {
+    T rz[N], zs[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      rz[i] = bv.v[i] * xc.v[i];
+      zs[i] = wv.v[i] > (T)0 ? xc.v[i] : (T)0;
+    }
+    const double prz = warp_total<T, N>(rz), pzs = warp_total<T, N>(zs);
+    if ((t & 31) == 0) {
+      double *pp = partials + (size_t)rhs * pstride +
+                   2 * ((size_t)bk * (BV / N / 32) + (t >> 5));
+      pp[0] = prz;
+      pp[1] = pzs;
+    }
+  }
 }
 
 template <typename T, int ORD>
@@ -355,6 +375,22 @@ void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
   }
 }
 template <typename T, typename C>
+void launch_jacobi7_rz(const Grid &g, const C *gx, const T *diag, const T *wdinv,
+                       const T *xin, const T *b, T *xout, double *partials, size_t pstride,
+                       cudaStream_t st, int nk, int order) {
+  if (!g.nb) return;
+  if (order)
+    k_jacobi7<T, C, 1, true><<<unit_grid(1, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
+        g, gx, diag, wdinv, xin, b, xout, nk, partials, pstride);
+  else
+    k_jacobi7<T, C, 0, true><<<unit_grid(0, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
+        g, gx, diag, wdinv, xin, b, xout, nk, partials, pstride);
+}
+template <typename T>
+int jacobi7_rz_partials(int nb) { return nb * (BV / row_n_jacobi<T>() / 32); }
+template int jacobi7_rz_partials<double>(int);
+template int jacobi7_rz_partials<float>(int);
+template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
                     const T *xin, const T *b, T *xout, cudaStream_t st, int nk, int order) {
   if (g.nb)
@@ -439,6 +475,10 @@ void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
 INST_T(double)
 INST_T(float)
 #define INST_TC(T, C)                                                         \
+  template void launch_jacobi7_rz<T, C>(const Grid &, const C *, const T *,   \
+                                        const T *, const T *, const T *, T *, \
+                                        double *, size_t, cudaStream_t, int,  \
+                                        int);                                 \
   template void launch_residual7<T, C>(const Grid &, const C *, const T *,    \
                                        const T *, const T *, T *,             \
                                        cudaStream_t, int, int);               \

@@ -220,6 +220,18 @@ template <typename T, typename C>
 void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
                     const T *xin, const T *b, T *xout, cudaStream_t st, int nk = 1,
                     int order = 0);
+// The same sweep as the last one of the V-cycle on level 0 (b = r, xout =
+// z): also writes 2 partials (r.z, sum of z over the unknowns) per warp,
+// jacobi7_rz_partials(nb) pairs per right-hand side, for launch_finish_rz.
+template <typename T, typename C>
+void launch_jacobi7_rz(const Grid &g, const C *gx, const T *diag, const T *wdinv,
+                       const T *xin, const T *b, T *xout, double *partials, size_t pstride,
+                       cudaStream_t st, int nk = 1, int order = 0);
+template <typename T> int jacobi7_rz_partials(int nb);
+// Adds n pairs of partials (scratch: at least 304 doubles, not overlapping)
+// and sets rz, beta, zsum and zmean as launch_dot_rz does.
+void launch_finish_rz(int n, const double *partials, double *scratch, Scalars *sc, int first,
+                      cudaStream_t st, int nk = 1, size_t pstride = 0);
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
                      const T *b, T *xout, cudaStream_t st, int nk = 1, int order = 0);

@@ -222,6 +222,22 @@ k_update_xr(int nb, T *__restrict__ x, T *__restrict__ r,
 
 // rz = r.z (new), beta = rz / rz_old, zsum = sum of z over the unknowns and
 // zmean = zsum / n.
+// rz = r.z (tot[0]) and the sum of z over the unknowns (tot[1]) into the
+// Scalars: beta = rz / rz_old (0 on the first iteration or after a restart)
+// and the mean of z for its projection.
+__device__ __forceinline__ void set_rz(Scalars *sc, const double (&tot)[2], int first) {
+  const double old = sc->rz;
+  sc->rz_old = old;
+  sc->rz = tot[0];
+  const double beta = (first || sc->restart || old == 0.0) ? 0.0 : tot[0] / old;
+  sc->restart = 0;
+  sc->beta = beta;
+  sc->beta_f = (float)beta;
+  sc->zsum = tot[1];
+  sc->zmean = tot[1] * sc->inv_ndof;
+  sc->zmean_f = (float)sc->zmean;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT)
 k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
@@ -250,18 +266,24 @@ k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
   }
   double v[2] = {rz.get(), zsum.get()};
   double tot[2];
-  if (grid_sum<2>(v, partials, &sc->ticket[2], tot)) {
-    const double old = sc->rz;
-    sc->rz_old = old;
-    sc->rz = tot[0];
-    const double beta = (first || sc->restart || old == 0.0) ? 0.0 : tot[0] / old;
-    sc->restart = 0;
-    sc->beta = beta;
-    sc->beta_f = (float)beta;
-    sc->zsum = tot[1];
-    sc->zmean = tot[1] * sc->inv_ndof;
-    sc->zmean_f = (float)sc->zmean;
+  if (grid_sum<2>(v, partials, &sc->ticket[2], tot)) set_rz(sc, tot, first);
+}
+
+// The same scalars from the partial pairs the level-0 post-smoother wrote
+// (k_jacobi7 with RZ): grid-stride sums, then the ticketed block tree.
+__global__ void __launch_bounds__(NT)
+k_finish_rz(const double *__restrict__ partials, int n, double *scratch, Scalars *sc,
+            int first, size_t pstride) {
+  partials += (size_t)blockIdx.y * pstride;
+  scratch += (size_t)blockIdx.y * pstride;
+  sc += blockIdx.y;
+  double v[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    v[0] += partials[2 * (size_t)i];
+    v[1] += partials[2 * (size_t)i + 1];
   }
+  double tot[2];
+  if (grid_sum<2>(v, scratch, &sc->ticket[2], tot)) set_rz(sc, tot, first);
 }
 
 // Per-component sums of v over the unknowns (several components), exact and
@@ -925,6 +947,12 @@ void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
   else
     k_apply_dot<T, 0><<<unit_grid(0, g.nb, nk), row_threads<T>(), 0, st>>>(
         g, gx, diag, p, q, partials, pstride, nk);
+}
+void launch_finish_rz(int n, const double *partials, double *scratch, Scalars *sc, int first,
+                      cudaStream_t st, int nk, size_t pstride) {
+  if (n <= 0) return;
+  const int blocks = std::min(152, (n + NT - 1) / NT);
+  k_finish_rz<<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, first, pstride);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
                       cudaStream_t st, int nk, size_t pstride) {

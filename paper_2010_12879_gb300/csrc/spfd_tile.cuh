@@ -273,6 +273,40 @@ __device__ __forceinline__ T apply27_tile(const T (*tl)[10][10], const T *__rest
   return acc;
 }
 
+// Sum of the N values of every lane of the warp, returned in every lane:
+// FP64 adds for double; for float, error-free (TwoSum) FP32 pairs over the
+// thread's values and the warp, rounded once to FP64 (no FP64 arithmetic in
+// an FP32 kernel but that one conversion).
+template <typename T, int N>
+__device__ __forceinline__ double warp_total(const T (&v)[N]) {
+  if constexpr (sizeof(T) == 4) {
+    float hi = v[0], lo = 0.f;
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+      const float sh = hi + v[i], bb = sh - hi;
+      lo += (hi - (sh - bb)) + (v[i] - bb);
+      hi = sh;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      const float sh = hi + oh, bb = sh - hi;
+      const float e = (hi - (sh - bb)) + (oh - bb);
+      hi = sh;
+      lo = lo + ol + e;
+    }
+    return (double)hi + (double)lo;
+  } else {
+    double a = v[0];
+#pragma unroll
+    for (int i = 1; i < N; ++i) a += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+  }
+}
+
 // The 27 entries e * S + s of a direction-major array (stencil coefficients
 // or interpolation weights of one node) into registers.
 template <typename T>
