@@ -65,12 +65,12 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
       rz[i] = bv.v[i] * xc.v[i];
       zs[i] = wv.v[i] > (T)0 ? xc.v[i] : (T)0;
     }
-    const double prz = warp_total<T, N>(rz), pzs = warp_total<T, N>(zs);
+    const WarpSum<T> prz = warp_total<T, N>(rz), pzs = warp_total<T, N>(zs);
     if ((t & 31) == 0) {
       double *pp = partials + (size_t)rhs * pstride +
                    2 * ((size_t)bk * (BV / N / 32) + (t >> 5));
-      pp[0] = prz;
-      pp[1] = pzs;
+      pp[0] = prz.get();
+      pp[1] = pzs.get();
     }
   }
 }

@@ -117,37 +117,23 @@ k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
   Qv<T, N> pc, qv;
   apply7_row<T, T, false, N>(g, gx, diag, p, S, bk, t, zqn<T, N>(), pc, qv);
   stqn<T, N>(q + s0, qv);
-  double part;
   if constexpr (sizeof(T) == 4) {
-    // FP32 products, summed without rounding error in (hi, lo) pairs
-    // (TwoSum) over the thread's four nodes and the warp; FP64 per warp
-    float hi = pc.v[0] * qv.v[0], lo = 0.f;
+    // FP32 products summed without rounding error in (hi, lo) pairs
+    // (TwoSum) over the thread's nodes and the warp, rounded to FP64 in the
+    // storing lane only
+    float pq[N];
 #pragma unroll
-    for (int i = 1; i < N; ++i) {
-      const float v = pc.v[i] * qv.v[i];
-      const float sh = hi + v, bb = sh - hi;
-      lo += (hi - (sh - bb)) + (v - bb);
-      hi = sh;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
-      const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-      const float sh = hi + oh, bb = sh - hi;
-      const float e = (hi - (sh - bb)) + (oh - bb);
-      hi = sh;
-      lo = lo + ol + e;
-    }
-    part = (double)hi + (double)lo;
+    for (int i = 0; i < N; ++i) pq[i] = pc.v[i] * qv.v[i];
+    const WarpSum<float> part = warp_total<float, N>(pq);
+    if ((t & 31) == 0) partials[(size_t)bk * (row_threads<T>() / 32) + (t >> 5)] = part.get();
   } else {
     double a = pc.v[0] * qv.v[0];
 #pragma unroll
     for (int i = 1; i < N; ++i) a += pc.v[i] * qv.v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    part = a;
+    if ((t & 31) == 0) partials[(size_t)bk * (row_threads<T>() / 32) + (t >> 5)] = a;
   }
-  if ((t & 31) == 0) partials[(size_t)bk * (row_threads<T>() / 32) + (t >> 5)] = part;
 }
 
 // Number of partials k_apply_dot writes for nb bricks.

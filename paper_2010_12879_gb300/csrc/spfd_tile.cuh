@@ -16,8 +16,12 @@ namespace spfd {
 
 template <typename T> __device__ __forceinline__ T cvt(double v) { return (T)v; }
 template <typename T> __device__ __forceinline__ T cvt(float v) { return (T)v; }
+// BF16 is the upper half of an IEEE binary32: widening is exact and needs
+// only the bits moved into place (two integer operations for a pair).
+__device__ __forceinline__ float bf16_lo(unsigned u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned u) { return __uint_as_float(u & 0xffff0000u); }
 template <typename T> __device__ __forceinline__ T cvt(__nv_bfloat16 v) {
-  return (T)__bfloat162float(v);
+  return (T)bf16_lo((unsigned)__bfloat16_as_ushort(v));
 }
 
 // 16-byte vectors of T (4 floats or 2 doubles) for streaming kernels; slot
@@ -117,10 +121,8 @@ __device__ __forceinline__ Qv<T, N> ldqn(const C *__restrict__ p) {
       r.v[0] = (T)u.x; r.v[1] = (T)u.y; r.v[2] = (T)w.x; r.v[3] = (T)w.y;
     } else {
       const uint2 u = *reinterpret_cast<const uint2 *>(p);
-      const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
-      const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
-      const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-      r.v[0] = (T)fa.x; r.v[1] = (T)fa.y; r.v[2] = (T)fb.x; r.v[3] = (T)fb.y;
+      r.v[0] = (T)bf16_lo(u.x); r.v[1] = (T)bf16_hi(u.x);
+      r.v[2] = (T)bf16_lo(u.y); r.v[3] = (T)bf16_hi(u.y);
     }
   } else {
     static_assert(N == 2, "two or four nodes per thread");
@@ -131,8 +133,8 @@ __device__ __forceinline__ Qv<T, N> ldqn(const C *__restrict__ p) {
       const double2 u = *reinterpret_cast<const double2 *>(p);
       r.v[0] = (T)u.x; r.v[1] = (T)u.y;
     } else {
-      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-      r.v[0] = (T)f.x; r.v[1] = (T)f.y;
+      const unsigned u = *reinterpret_cast<const unsigned *>(p);
+      r.v[0] = (T)bf16_lo(u); r.v[1] = (T)bf16_hi(u);
     }
   }
   return r;
@@ -273,12 +275,22 @@ __device__ __forceinline__ T apply27_tile(const T (*tl)[10][10], const T *__rest
   return acc;
 }
 
-// Sum of the N values of every lane of the warp, returned in every lane:
-// FP64 adds for double; for float, error-free (TwoSum) FP32 pairs over the
-// thread's values and the warp, rounded once to FP64 (no FP64 arithmetic in
-// an FP32 kernel but that one conversion).
+// Sum of the N values of every lane of the warp, held by every lane: an
+// FP64 sum for double; for float, an error-free (TwoSum) FP32 pair over the
+// thread's values and the warp.  get() rounds it to FP64; kernels call it in
+// the one lane that stores the sum, so that an FP32 kernel spends no FP64
+// pipe cycles (conversions included) in the other 31.
+template <typename T> struct WarpSum;
+template <> struct WarpSum<double> {
+  double s;
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct WarpSum<float> {
+  float hi, lo;
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
 template <typename T, int N>
-__device__ __forceinline__ double warp_total(const T (&v)[N]) {
+__device__ __forceinline__ WarpSum<T> warp_total(const T (&v)[N]) {
   if constexpr (sizeof(T) == 4) {
     float hi = v[0], lo = 0.f;
 #pragma unroll
@@ -296,14 +308,14 @@ __device__ __forceinline__ double warp_total(const T (&v)[N]) {
       hi = sh;
       lo = lo + ol + e;
     }
-    return (double)hi + (double)lo;
+    return WarpSum<float>{hi, lo};
   } else {
     double a = v[0];
 #pragma unroll
     for (int i = 1; i < N; ++i) a += v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    return a;
+    return WarpSum<double>{a};
   }
 }
 
