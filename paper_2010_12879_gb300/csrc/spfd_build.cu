@@ -181,29 +181,45 @@ static bool invert_spd(std::vector<double> &A, int n) {
   return true;
 }
 
+// Wall-clock phase marks of the build (printed with opts.verbose >= 2).
+struct PhaseClock {
+  spfd_ctx *c;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double alloc0 = 0.0;
+  void mark(const char *what) {
+    if (c->opts.verbose < 2) return;
+    cudaStreamSynchronize(c->stream);
+    auto t1 = std::chrono::steady_clock::now();
+    fprintf(stderr, "[spfd]   build phase %-18s %8.3f ms (cudaMalloc %.3f ms)\n", what,
+            std::chrono::duration<double, std::milli>(t1 - t0).count(), c->alloc_ms - alloc0);
+    t0 = t1;
+    alloc0 = c->alloc_ms;
+  }
+};
+
 // Coarsest level: B = A + sum_c mu_c v_c v_c^T (v_c the normalised indicator
 // of a connected component of the coarsest graph, mu_c its mean diagonal) is
 // SPD, and B^-1 r = A^+ r for r with zero mean on every component.  The
 // symmetrised inverse is applied as a dense FP64 matrix-vector product.
-static spfd_status setup_coarsest(spfd_ctx *c) {
+static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
   Level &lv = c->L.back();
   const size_t S = lv.S;
   const bool single = c->L.size() == 1;
   c->m = 0;
   if (S == 0) return SPFD_OK;
-  std::vector<double> hst, hgx, hdiag(S);
-  CU(cudaMemcpyAsync(hdiag.data(), lv.diag, S * sizeof(double),
+  // read-backs and the matrix live in the context's pinned host blocks
+  // (reused across builds): fresh pageable buffers of this size cost more in
+  // first-touch page faults than the assembly itself
+  double *hdiag = nullptr, *hop = nullptr;
+  const size_t nop = (single ? 3 : 27) * S;
+  TRY(halloc(c, &hdiag, S));
+  TRY(halloc(c, &hop, nop));
+  CU(cudaMemcpyAsync(hdiag, lv.diag, S * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(hop, single ? lv.gx : lv.st, nop * sizeof(double),
                      cudaMemcpyDeviceToHost, c->stream));
-  if (single) {
-    hgx.resize(3 * S);
-    CU(cudaMemcpyAsync(hgx.data(), lv.gx, 3 * S * sizeof(double),
-                       cudaMemcpyDeviceToHost, c->stream));
-  } else {
-    hst.resize(27 * S);
-    CU(cudaMemcpyAsync(hst.data(), lv.st, 27 * S * sizeof(double),
-                       cudaMemcpyDeviceToHost, c->stream));
-  }
+  const double *hgx = hop, *hst = hop;
   TRY(sync_check(c, "coarsest copy"));
+  clk.mark("coarsest read-back");
   std::vector<int> row(S, -1), idx;
   for (size_t s = 0; s < S; ++s)
     if (hdiag[s] > 0.0) { row[s] = (int)idx.size(); idx.push_back((int)s); }
@@ -219,7 +235,9 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
     if (b < 0) return -1;
     return b * BV + ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
   };
-  std::vector<double> A((size_t)m * m, 0.0);
+  double *A = nullptr;  // pinned: staged for the device as it stands
+  TRY(halloc(c, &A, (size_t)m * m));
+  memset(A, 0, (size_t)m * m * sizeof(double));
   for (int a = 0; a < m; ++a) {
     const int s = idx[a];
     const int4 bc = lv.hbco[s / BV];
@@ -248,7 +266,7 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
   if (const char *dump = getenv("SPFD_DUMP_COARSEST")) {
     if (FILE *f = fopen(dump, "wb")) {
       fwrite(&m, sizeof(int), 1, f);
-      fwrite(A.data(), sizeof(double), (size_t)m * m, f);
+      fwrite(A, sizeof(double), (size_t)m * m, f);
       fclose(f);
     }
   }
@@ -272,12 +290,15 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
   std::vector<double> dsum(nc, 0.0);
   std::vector<int> cnt(nc, 0);
   for (int a = 0; a < m; ++a) { dsum[cc[a]] += A[(size_t)a * m + a]; cnt[cc[a]]++; }
-  for (int a = 0; a < m; ++a)
+  std::vector<double> mu(nc);  // mu_c / n_c, formed once per component
+  for (int q = 0; q < nc; ++q) mu[q] = (dsum[q] / cnt[q]) / cnt[q];
+  for (int a = 0; a < m; ++a) {
+    double *Ar = A + (size_t)a * m;
+    const int q = cc[a];
+    const double add = mu[q];
     for (int b2 = 0; b2 < m; ++b2)
-      if (cc[a] == cc[b2]) {
-        const int q = cc[a];
-        A[(size_t)a * m + b2] += (dsum[q] / cnt[q]) / cnt[q];
-      }
+      if (cc[b2] == q) Ar[b2] += add;
+  }
   // The coarsest Galerkin operator is numerically singular beyond the
   // component constants: coarse basis functions at the conducting boundary
   // can be nearly dependent (on the 2 mm body, 46 of 481 eigenvalues lie
@@ -300,22 +321,21 @@ static spfd_status setup_coarsest(spfd_ctx *c) {
   TRY(halloc(c, &hidx, m));
   memcpy(hidx, idx.data(), m * sizeof(int));
   TRY(h2d(c, c->cidx, hidx, m * sizeof(int)));
-  double *hA = nullptr;  // pinned staging of the matrix (or its inverse)
-  TRY(halloc(c, &hA, (size_t)m * m));
+  clk.mark("coarsest assembly");
   if (m <= 64) {  // small: invert on the host
-    if (!invert_spd(A, m))
+    std::vector<double> As(A, A + (size_t)m * m);
+    if (!invert_spd(As, m))
       return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
     TRY(dalloc(c, &c->Binv, (size_t)m * m));
-    memcpy(hA, A.data(), (size_t)m * m * sizeof(double));
-    TRY(h2d(c, c->Binv, hA, (size_t)m * m * sizeof(double)));
+    memcpy(A, As.data(), (size_t)m * m * sizeof(double));
+    TRY(h2d(c, c->Binv, A, (size_t)m * m * sizeof(double)));
     return sync_check(c, "coarsest upload");
   }
   // larger: Gauss-Jordan sweeps on the device (ping-pong between two buffers)
   double *b0 = nullptr, *b1 = nullptr;
   TRY(dalloc(c, &b0, (size_t)m * m));
   TRY(dalloc(c, &b1, (size_t)m * m));
-  memcpy(hA, A.data(), (size_t)m * m * sizeof(double));
-  TRY(h2d(c, b0, hA, (size_t)m * m * sizeof(double)));
+  TRY(h2d(c, b0, A, (size_t)m * m * sizeof(double)));
   double *inv = nullptr;
   SPFD_LAUNCH(c, "setup_coarsest", false, (m + 15) / 16, 0, 2.0 * m * m * m,
               inv = launch_dense_inverse(b0, b1, m, &c->sc->status, c->stream));
@@ -372,22 +392,6 @@ static spfd_status setup_mixed_krylov(spfd_ctx *c) {
   TRY(dalloc(c, &c->qk32, S0));
   return SPFD_OK;
 }
-
-// Wall-clock phase marks of the build (printed with opts.verbose >= 2).
-struct PhaseClock {
-  spfd_ctx *c;
-  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
-  double alloc0 = 0.0;
-  void mark(const char *what) {
-    if (c->opts.verbose < 2) return;
-    cudaStreamSynchronize(c->stream);
-    auto t1 = std::chrono::steady_clock::now();
-    fprintf(stderr, "[spfd]   build phase %-18s %8.3f ms (cudaMalloc %.3f ms)\n", what,
-            std::chrono::duration<double, std::milli>(t1 - t0).count(), c->alloc_ms - alloc0);
-    t0 = t1;
-    alloc0 = c->alloc_ms;
-  }
-};
 
 spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   cudaStream_t st = c->stream;
@@ -699,7 +703,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     TRY(setup_mixed_level(c, 0));
   }
   clk.mark("smoother weights");
-  TRY(setup_coarsest(c));
+  TRY(setup_coarsest(c, clk));
   clk.mark("coarsest inverse");
   if (mixed && c->L.size() > 1) TRY(setup_mixed_level(c, (int)c->L.size() - 1));
   for (int i = 0; i < ns; ++i) CU(cudaStreamWaitEvent(st, side.e[i], 0));
