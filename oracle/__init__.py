@@ -73,6 +73,7 @@ def lib():
         if _lib is None:
             L = ctypes.CDLL(build())
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_conductances.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
             L.orc_index_nodes.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, lp]
             L.orc_index_nodes.restype = i64
@@ -105,6 +106,11 @@ def lib():
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later parallel loops (timing only)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def _d(a):

@@ -61,6 +61,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following parallel loops (timing only; no result depends
+ * on it beyond the order of reduction sums). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* Edge conductances g (the diagonal of M_k, Eq. 3; averaging rule R1).
  * g has 3*(nx+1)*(ny+1)*(nz+1) entries; slots without an edge are 0. */
 void orc_conductances(const double *sigma, int nx_, int ny_, int nz_, double h,
