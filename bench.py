@@ -9,7 +9,7 @@ One step is one pass of the whole hot path over the full-size workload
 The headline line is the plain FP64 form; the mixed-precision form (FP64
 refinement around an FP32/BF16 V-cycle CG) is timed on the same inputs and
 reported beside it, and the adjoint gradient of J = mean |E|^2 (build +
-solve + gradient on the 128 x 96 x 448 config-5 body) in the "adjoint"
+solve + gradient on the 128 x 96 x 448 scaled body) in the "adjoint"
 sub-object.  Inputs (3.7 GB working set) exceed the 129 MB L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -272,7 +272,7 @@ def run_ours(args):
     roof64 = roofline(fam64, "fp64")
     roofmx = roofline(fammx, "mixed")
 
-    # adjoint gradient (config 5): 128 x 96 x 448 voxels at 2 mm, the C2
+    # adjoint gradient: 128 x 96 x 448 voxels at 2 mm, the body's
     # ellipsoids scaled to the box, loop source; build + solve + gradient of
     # J = mean |E|^2 over conducting voxels, both solves to TOL
     adjoint = None

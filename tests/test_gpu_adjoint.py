@@ -61,8 +61,8 @@ def _check(oracle, ph, a, J, dJda, dJds, tol_grad=1e-6):
 
 
 def test_energy_grad_scaled_body(torch_cuda, spfd, oracle_mod):
-    """The config-5 body shape (C2 ellipsoids scaled to the box) at 32 x 24 x
-    112 voxels, 40 tissues, loop source; per-tissue gradients."""
+    """The body's ellipsoids scaled to a 32 x 24 x 112 voxel box, 40
+    tissues, loop source; per-tissue gradients."""
     ph = scaled_body_phantom(32, 24, 112)
     a = loop_potential(ph.dims, ph.h, ph.origin)
     J, dJda, dJds, info = _gpu_grad(torch_cuda, spfd, ph.sigma, ph.h, a)
@@ -130,8 +130,8 @@ def test_field_energy_autograd_per_tissue(torch_cuda, spfd, oracle_mod):
     assert fd == pytest.approx(an, rel=1e-6)
 
 
-def test_energy_grad_config5_properties(torch_cuda, spfd, oracle_mod):
-    """The config-5 phantom itself (128 x 96 x 448 voxels, h = 2 mm): the
+def test_energy_grad_scaled_body_128_properties(torch_cuda, spfd, oracle_mod):
+    """The scaled body at full size (128 x 96 x 448 voxels, h = 2 mm): the
     oracle cannot solve it in seconds, so the GPU gradient is checked
     through what holds at any size.  J and dJ/du follow from the GPU's Psi
     by the oracle's own evaluation, and G^T dJ/da = G^T dJ/du - A lambda is

@@ -84,7 +84,7 @@ def _compare(oracle, ph, a, psi_g, E_g, tol_psi=PSI_TOL, tol_e=E_TOL):
 
 @pytest.mark.parametrize("gauge", ["symmetric", "landau"])
 def test_sphere_parity(torch_cuda, spfd, oracle_mod, gauge):
-    """Config 1: 32^3 sphere in a uniform 27 uT field, both gauges."""
+    """The 32^3 sphere (R = 28 mm, h = 2 mm) in a uniform 27 uT field, both gauges."""
     ph = sphere_phantom()
     f = uniform_b_symmetric if gauge == "symmetric" else uniform_b_landau
     a = f(ph.dims, ph.h, ph.origin, 27e-6)
@@ -96,7 +96,7 @@ def test_sphere_parity(torch_cuda, spfd, oracle_mod, gauge):
 
 @pytest.mark.parametrize("gauge", ["symmetric", "landau"])
 def test_sphere_mixed_precision(torch_cuda, spfd, oracle_mod, gauge):
-    """Config 3: the config-1 sphere and source through the mixed form (FP32
+    """The same sphere and source through the mixed form (FP32
     V-cycle with BF16 level-0 conductances and FP32 accumulation inside FP64
     refinement).  Solved to 1e-13 it meets the FP64 parity bars; solved to
     the 1e-8 target its errors against the FP64 oracle stay at the level of

@@ -214,7 +214,7 @@ def test_efield_of_uniform_edge_potential(oracle_mod):
     np.testing.assert_allclose(E, OMEGA / ph.h * 3e-9, rtol=1e-13)
 
 
-# ---------------------------------------------------------------- sphere (config 1)
+# ---------------------------------------------------------------- sphere (32^3, R = 28 mm)
 
 @pytest.fixture(scope="module")
 def sphere_solutions(oracle_mod):
