@@ -187,11 +187,20 @@ __device__ __forceinline__ void interp_node(const LevelOp &A, double *__restrict
 
 // Pass 1: classes 0 (coincident) and 1, 2, 4 (one odd axis); pass 2: classes
 // with two odd axes; pass 3: class 7.  Each pass reads only classes of
-// earlier passes, except class 0, whose weight a reader never loads.
-template <bool K27>
-__global__ void __launch_bounds__(NT) k_interp(LevelOp A, int pass, double *__restrict__ Pc) {
-  const int q = threadIdx.x >> 6, cell = threadIdx.x & 63, b = blockIdx.x;
-  if (__popc(q) != pass && !(pass == 1 && q == 0)) return;
+// earlier passes, except class 0, whose weight a reader never loads.  A
+// block holds only the pass's classes (64 threads each, one per cell) for
+// interp_bricks<PASS>() bricks, so every launched warp has work.
+template <int PASS>
+constexpr int interp_classes() { return PASS == 1 ? 4 : (PASS == 2 ? 3 : 1); }
+template <int PASS>
+constexpr int interp_bricks() { return PASS == 3 ? 8 : 2; }
+template <bool K27, int PASS>
+__global__ void __launch_bounds__(NT) k_interp(LevelOp A, double *__restrict__ Pc) {
+  constexpr int NCL = interp_classes<PASS>();
+  const int cell = threadIdx.x & 63, grp = threadIdx.x >> 6;
+  const int ci = grp % NCL, b = blockIdx.x * interp_bricks<PASS>() + grp / NCL;
+  if (b >= A.g.nb) return;
+  const int q = PASS == 1 ? (ci == 0 ? 0 : 1 << (ci - 1)) : (PASS == 2 ? 7 - (1 << ci) : 7);
   const int4 bc = A.g.bco[b];
   switch (q) {
     case 0: interp_node<0, K27>(A, Pc, b, bc, cell); break;
@@ -247,8 +256,10 @@ __device__ __forceinline__ void ap_node(const LevelOp &A, const double *__restri
   for (int r = 0; r < NTQ; ++r) T[(size_t)(toff(Q) + r) * A.NC + col] = acc[r];
 }
 
+// 7-point level: two resident blocks (at most 64 registers; 66 unbounded,
+// which allowed one); 27-point levels keep one (92 registers).
 template <bool K27>
-__global__ void __launch_bounds__(NT, 1) k_ap(LevelOp A, const double *__restrict__ Pc,
+__global__ void __launch_bounds__(NT, K27 ? 1 : 2) k_ap(LevelOp A, const double *__restrict__ Pc,
                                            double *__restrict__ T) {
   const int q = threadIdx.x >> 6, cell = threadIdx.x & 63, b = blockIdx.x;
   const int4 bc = A.g.bco[b];
@@ -391,9 +402,19 @@ void launch_interp_weights(const Grid &gf, const double *gx, const double *st27,
                            const double *diag, double *Pc, cudaStream_t st) {
   if (gf.nb == 0) return;
   const LevelOp A{gf, gx, st27, diag, (size_t)gf.nb * BV, (size_t)gf.nb * 64};
-  for (int pass = 1; pass <= 3; ++pass) {
-    if (st27) k_interp<true><<<gf.nb, NT, 0, st>>>(A, pass, Pc);
-    else k_interp<false><<<gf.nb, NT, 0, st>>>(A, pass, Pc);
+  auto grid = [&](int bricks) { return (unsigned)((gf.nb + bricks - 1) / bricks); };
+  constexpr int T1 = 64 * interp_classes<1>() * interp_bricks<1>();
+  constexpr int T2 = 64 * interp_classes<2>() * interp_bricks<2>();
+  constexpr int T3 = 64 * interp_classes<3>() * interp_bricks<3>();
+  static_assert(T1 <= NT && T2 <= NT && T3 <= NT, "interp blocks");
+  if (st27) {
+    k_interp<true, 1><<<grid(interp_bricks<1>()), T1, 0, st>>>(A, Pc);
+    k_interp<true, 2><<<grid(interp_bricks<2>()), T2, 0, st>>>(A, Pc);
+    k_interp<true, 3><<<grid(interp_bricks<3>()), T3, 0, st>>>(A, Pc);
+  } else {
+    k_interp<false, 1><<<grid(interp_bricks<1>()), T1, 0, st>>>(A, Pc);
+    k_interp<false, 2><<<grid(interp_bricks<2>()), T2, 0, st>>>(A, Pc);
+    k_interp<false, 3><<<grid(interp_bricks<3>()), T3, 0, st>>>(A, Pc);
   }
 }
 
