@@ -81,25 +81,58 @@ __device__ __forceinline__ double g_edge(const double *s, int d, int i, int j,
   }
 }
 
+// One brick per block.  The 9^3 voxels around the brick's nodes go to shared
+// memory once; each +edge conductance of the nodes -1 .. 7 (per axis) is
+// formed once there (the -edge of a node is the +edge of the node before
+// it), so a node costs about 13 FP64 operations for its six conductances
+// instead of 24.  Every conductance is summed in the same order as g_edge.
 __global__ void __launch_bounds__(NT)
 k_build_fine(Grid g, const double *__restrict__ sigma, int nx, int ny, int nz,
              double h, double *__restrict__ gx, double *__restrict__ diag,
              double *__restrict__ dinv) {
+  __shared__ double sv[9][9][9];  // voxels 8B - 1 .. 8B + 7 per axis (0 outside)
+  __shared__ double ex[8][8][9];  // +x edge of node (lx, ly, lz), lx = -1 .. 7 at [lz][ly][lx + 1]
+  __shared__ double ey[8][9][8];  // +y edge, ly = -1 .. 7 at [lz][ly + 1][lx]
+  __shared__ double ez[9][8][8];  // +z edge, lz = -1 .. 7 at [lz + 1][ly][lx]
   const size_t S = (size_t)g.nb * BV;
   const int b = blockIdx.x, t = threadIdx.x;
   const int4 bc = g.bco[b];
-  const int i = bc.x * 8 + (t & 7), j = bc.y * 8 + ((t >> 3) & 7),
-            k = bc.z * 8 + (t >> 6);
+  const int x0 = bc.x * 8 - 1, y0 = bc.y * 8 - 1, z0 = bc.z * 8 - 1;
+  for (int q = t; q < 729; q += NT) {
+    const int vz = q / 81, vy = (q / 9) % 9, vx = q % 9;
+    sv[vz][vy][vx] = sig_at(sigma, x0 + vx, y0 + vy, z0 + vz, nx, ny, nz);
+  }
+  __syncthreads();
+  const double hq = h * 0.25;
+  for (int q = t; q < 576; q += NT) {
+    {  // x: index (lz, ly, lx + 1)
+      const int lz = q / 72, ly = (q / 9) % 8, xp = q % 9;
+      ex[lz][ly][xp] = hq * (sv[lz][ly][xp] + sv[lz][ly + 1][xp] + sv[lz + 1][ly][xp] +
+                             sv[lz + 1][ly + 1][xp]);
+    }
+    {  // y: index (lz, ly + 1, lx)
+      const int lz = q / 72, yp = (q / 8) % 9, lx = q % 8;
+      ey[lz][yp][lx] = hq * (sv[lz][yp][lx] + sv[lz][yp][lx + 1] + sv[lz + 1][yp][lx] +
+                             sv[lz + 1][yp][lx + 1]);
+    }
+    {  // z: index (lz + 1, ly, lx)
+      const int zp = q / 64, ly = (q / 8) % 8, lx = q % 8;
+      ez[zp][ly][lx] = hq * (sv[zp][ly][lx] + sv[zp][ly][lx + 1] + sv[zp][ly + 1][lx] +
+                             sv[zp][ly + 1][lx + 1]);
+    }
+  }
+  __syncthreads();
+  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  const int i = bc.x * 8 + lx, j = bc.y * 8 + ly, k = bc.z * 8 + lz;
   const size_t s = (size_t)b * BV + t;
   double e[6] = {0, 0, 0, 0, 0, 0};
   if (i < g.NX && j < g.NY && k < g.NZ) {
-    const double hq = h * 0.25;
-    e[0] = g_edge(sigma, 0, i, j, k, nx, ny, nz, hq);      // +x
-    e[1] = g_edge(sigma, 1, i, j, k, nx, ny, nz, hq);      // +y
-    e[2] = g_edge(sigma, 2, i, j, k, nx, ny, nz, hq);      // +z
-    e[3] = g_edge(sigma, 0, i - 1, j, k, nx, ny, nz, hq);  // -x
-    e[4] = g_edge(sigma, 1, i, j - 1, k, nx, ny, nz, hq);  // -y
-    e[5] = g_edge(sigma, 2, i, j, k - 1, nx, ny, nz, hq);  // -z
+    e[0] = ex[lz][ly][lx + 1];  // +x
+    e[1] = ey[lz][ly + 1][lx];  // +y
+    e[2] = ez[lz + 1][ly][lx];  // +z
+    e[3] = ex[lz][ly][lx];      // -x
+    e[4] = ey[lz][ly][lx];      // -y
+    e[5] = ez[lz][ly][lx];      // -z
   }
   double d = ((e[3] + e[0]) + (e[4] + e[1])) + (e[5] + e[2]);
   gx[s] = e[0];
