@@ -451,6 +451,18 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   c->pstride = 16 * (size_t)std::max(nb0, 1) + 2048;
   TRY(dalloc(c, &c->partials, c->pstride));
   int *parent = nullptr, *counts = nullptr, *offsets = nullptr;
+  int *comp_hcnt = nullptr, *comp_hstat = nullptr;
+  struct CompStream {  // released on every exit (the context is then destroyed)
+    spfd_ctx *c;
+    cudaStream_t main, s = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    ~CompStream() {
+      c->stream = main;
+      if (s) cudaStreamDestroy(s);
+      if (fork) cudaEventDestroy(fork);
+      if (done) cudaEventDestroy(done);
+    }
+  } comp_side{c, st};
   {
     Level &l0 = c->L[0];
     TRY(dalloc(c, &l0.gx, 3 * S0));
@@ -461,15 +473,34 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
                 launch_build_fine(l0.g, sigma, c->nx, c->ny, c->nz, c->h, l0.gx,
                                   l0.diag, l0.dinv, st));
     TRY(launch_check("build fine"));
-    // connected components of the conducting nodes
+    // connected components of the conducting nodes: the union-find and the
+    // root counts run on a stream of their own, overlapping the coarse
+    // tables and the hierarchy (which do not need them); the numbering that
+    // follows runs on the main stream after it
     TRY(dalloc(c, &parent, S0));
     TRY(dalloc(c, &c->comp, S0));
-    SPFD_LAUNCH(c, "setup_components", false, 3, 0, 0,
-                launch_components(l0.g, l0.gx, parent, &c->sc->status, st));
-    TRY(launch_check("components"));
     TRY(dalloc(c, &counts, nb0));
     TRY(dalloc(c, &offsets, nb0));
-    SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0, launch_root_counts(l0.g, parent, counts, st));
+    TRY(halloc(c, &comp_hcnt, std::max(nb0, 1)));
+    TRY(halloc(c, &comp_hstat, 1));
+    CU(cudaStreamCreateWithFlags(&comp_side.s, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&comp_side.fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&comp_side.done, cudaEventDisableTiming));
+    CU(cudaEventRecord(comp_side.fork, st));
+    CU(cudaStreamWaitEvent(comp_side.s, comp_side.fork, 0));
+    c->stream = comp_side.s;
+    SPFD_LAUNCH(c, "setup_components", false, 3, 0, 0,
+                launch_components(l0.g, l0.gx, parent, &c->sc->status, comp_side.s));
+    SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0,
+                launch_root_counts(l0.g, parent, counts, comp_side.s));
+    c->stream = st;
+    TRY(launch_check("components"));
+    if (nb0)
+      CU(cudaMemcpyAsync(comp_hcnt, counts, nb0 * sizeof(int), cudaMemcpyDeviceToHost,
+                         comp_side.s));
+    CU(cudaMemcpyAsync(comp_hstat, &c->sc->status, sizeof(int), cudaMemcpyDeviceToHost,
+                       comp_side.s));
+    CU(cudaEventRecord(comp_side.done, comp_side.s));
   }
 
   // The brick structure of every coarser level follows from the brick maps
@@ -523,35 +554,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     TRY(launch_check("brick tables"));
   }
 
-  // component numbering (one read-back: the root count per brick)
-  {
-    Level &l0 = c->L[0];
-    int *hcnt = nullptr;
-    TRY(halloc(c, &hcnt, nb0));
-    if (nb0)
-      CU(cudaMemcpyAsync(hcnt, counts, nb0 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    TRY(read_scalars(c));
-    if (c->hsc->status & DEV_UF_CAP)
-      return fail(SPFD_EINTERNAL, "component labelling hit its iteration cap");
-    int *hoff = nullptr;
-    TRY(halloc(c, &hoff, nb0));
-    int64_t tot = 0;
-    for (int b = 0; b < nb0; ++b) { hoff[b] = (int)tot; tot += hcnt[b]; }
-    c->ncomp = (int)tot;
-    if (nb0)
-      TRY(h2d(c, offsets, hoff, nb0 * sizeof(int)));
-    SPFD_LAUNCH(c, "setup_components", false, 2, 0, 0, launch_assign_comp(l0.g, parent, offsets, c->comp, st));
-    TRY(dalloc(c, &c->csize, std::max(c->ncomp, 1)));
-    CU(cudaMemsetAsync(c->csize, 0, std::max(c->ncomp, 1) * sizeof(int), st));
-    SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0, launch_comp_sizes(l0.g, c->comp, c->csize, st));
-    TRY(launch_check("component sizes"));
-    dfree(c, parent);
-    dfree(c, counts);
-    dfree(c, offsets);
-    c->cstride = 3 * c->ncomp + 1;
-    if (c->ncomp > 1) TRY(dalloc(c, &c->csum, c->cstride));
-  }
-  clk.mark("fine+components");
+  clk.mark("brick tables");
 
   // Multigrid hierarchy, enqueued without host round trips.  lstat[4l..4l+3]:
   // level l's count and largest entry of the Galerkin diagonal, then the
@@ -605,6 +608,35 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     TRY(launch_check("coarse level"));
   }
   dfree(c, Ttmp);
+  // component numbering, once the side stream's root counts are in (the
+  // host waits for that stream alone; the main stream waits for it before
+  // the numbering kernels)
+  {
+    Level &l0 = c->L[0];
+    CU(cudaEventSynchronize(comp_side.done));
+    if (*comp_hstat & DEV_UF_CAP)
+      return fail(SPFD_EINTERNAL, "component labelling hit its iteration cap");
+    CU(cudaStreamWaitEvent(st, comp_side.done, 0));
+    const int *hcnt = comp_hcnt;
+    int *hoff = nullptr;
+    TRY(halloc(c, &hoff, nb0));
+    int64_t tot = 0;
+    for (int b = 0; b < nb0; ++b) { hoff[b] = (int)tot; tot += hcnt[b]; }
+    c->ncomp = (int)tot;
+    if (nb0)
+      TRY(h2d(c, offsets, hoff, nb0 * sizeof(int)));
+    SPFD_LAUNCH(c, "setup_components", false, 2, 0, 0, launch_assign_comp(l0.g, parent, offsets, c->comp, st));
+    TRY(dalloc(c, &c->csize, std::max(c->ncomp, 1)));
+    CU(cudaMemsetAsync(c->csize, 0, std::max(c->ncomp, 1) * sizeof(int), st));
+    SPFD_LAUNCH(c, "setup_components", false, 1, 0, 0, launch_comp_sizes(l0.g, c->comp, c->csize, st));
+    TRY(launch_check("component sizes"));
+    dfree(c, parent);
+    dfree(c, counts);
+    dfree(c, offsets);
+    c->cstride = 3 * c->ncomp + 1;
+    if (c->ncomp > 1) TRY(dalloc(c, &c->csum, c->cstride));
+  }
+  clk.mark("components");
   {
     // the one read-back of the hierarchy: component sizes and the unknowns
     // of every level
