@@ -63,6 +63,8 @@ typedef enum {
   SPFD_EINTERNAL = 5       /* a bounded device loop hit its iteration cap */
 } spfd_status;
 
+/* Smoother of the V-cycle.  Only weighted Jacobi is built; CHEBYSHEV is a
+ * reserved value that spfd_build rejects with SPFD_EINVAL. */
 enum { SPFD_SMOOTHER_JACOBI = 0, SPFD_SMOOTHER_CHEBYSHEV = 1 };
 
 /* Arithmetic of the solve.
@@ -78,8 +80,8 @@ typedef struct {
   int maxit;         /* PCG iteration cap (default 200) */
   int nu_pre;        /* pre-smoothing sweeps per level (default 1) */
   int nu_post;       /* post-smoothing sweeps per level (default 1) */
-  int smoother;      /* SPFD_SMOOTHER_* (default Jacobi) */
-  int cheb_degree;   /* Chebyshev polynomial degree (default 2) */
+  int smoother;      /* SPFD_SMOOTHER_JACOBI (the only one built; default) */
+  int cheb_degree;   /* reserved for a Chebyshev smoother (default 2, unused) */
   int precision;     /* SPFD_FP64 or SPFD_MIXED */
   int coarse_max;    /* stop coarsening at <= this many unknowns (default 512) */
   int max_levels;    /* hierarchy depth cap (default 12) */
@@ -87,9 +89,9 @@ typedef struct {
   int profile;       /* 1 = time every kernel launch with CUDA events (see
                         spfd_kernel_stats); adds ~2 us of host work per launch */
   int autotune;      /* 1 (default) = the first batched solve of each batch
-                        size times both block orders of each batched kernel
-                        family and level and keeps the faster (see
-                        spfd_autotune_report); 0 = fixed order */
+                        size times the block orders of each batched kernel
+                        family and level and keeps the fastest (see
+                        spfd_autotune_report); 0 = fixed order 0 */
 } spfd_opts;
 
 typedef struct {

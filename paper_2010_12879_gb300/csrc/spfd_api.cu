@@ -168,6 +168,9 @@ extern "C" spfd_status spfd_build(const double *sigma_dev, int nx, int ny,
       (o.precision != SPFD_FP64 && o.precision != SPFD_MIXED) ||
       (o.smoother != SPFD_SMOOTHER_JACOBI && o.smoother != SPFD_SMOOTHER_CHEBYSHEV))
     return fail(SPFD_EINVAL, "invalid options");
+  if (o.smoother != SPFD_SMOOTHER_JACOBI)
+    return fail(SPFD_EINVAL, "only the weighted-Jacobi smoother is built "
+                             "(SPFD_SMOOTHER_CHEBYSHEV is reserved)");
   spfd_ctx *c = new (std::nothrow) spfd_ctx();
   if (!c) return fail(SPFD_ENOMEM, "host allocation of the context failed");
   c->nx = nx; c->ny = ny; c->nz = nz; c->h = h; c->opts = o;

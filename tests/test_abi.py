@@ -91,6 +91,18 @@ def test_invalid_options_rejected(spfd):
     assert st == spfd.SPFD_EINVAL
 
 
+def test_reserved_chebyshev_smoother_rejected(spfd):
+    """Only weighted Jacobi is built: the reserved Chebyshev value is an
+    error (checked before any device work), not a silent fallback."""
+    L = spfd.lib()
+    o = spfd.spfd_opts_default()
+    o.smoother = spfd.SPFD_SMOOTHER_CHEBYSHEV
+    handle = ctypes.c_void_p()
+    st = L.spfd_build(ctypes.c_void_p(8), 4, 4, 4, 2e-3, ctypes.byref(o), None, ctypes.byref(handle))
+    assert st == spfd.SPFD_EINVAL and not handle.value
+    assert "Jacobi" in spfd.spfd_last_error()
+
+
 def test_without_gpu_build_reports_cuda_error(spfd):
     import torch
     if torch.cuda.is_available():
