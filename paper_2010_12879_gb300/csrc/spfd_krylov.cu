@@ -834,19 +834,18 @@ k_jacobi_weights(const double *__restrict__ dinv, const Scalars *sc, double marg
 
 // ------------------------------------------------ precision conversions
 // dst = (T) (f * src) elementwise over n values.
-template <typename T>
+// dst = (T)(f * src); with SCALE false (f = 1, every conversion of the
+// build) the FP64 multiply is skipped: the kernel then issues only the
+// conversion on the FP64 pipe, which is what bounds it on GB300.
+template <typename T, bool SCALE>
 __global__ void k_convert(size_t n, const double *__restrict__ src, double f,
                           T *__restrict__ dst) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = (T)(f * src[i]);
-}
-template <>
-__global__ void k_convert<__nv_bfloat16>(size_t n, const double *__restrict__ src,
-                                         double f, __nv_bfloat16 *__restrict__ dst) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = __double2bfloat16(f * src[i]);
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = SCALE ? f * src[i] : src[i];
+    if constexpr (sizeof(T) == 2) dst[i] = __double2bfloat16(v);
+    else dst[i] = (T)v;
+  }
 }
 
 // x += f * d (FP64 accumulation of an FP32 correction) on level-0 slots.
@@ -888,7 +887,8 @@ void launch_convert(size_t n, const double *src, double f, T *dst,
   size_t blocks = (n + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks == 0) return;
-  k_convert<T><<<(int)blocks, 256, 0, st>>>(n, src, f, dst);
+  if (f == 1.0) k_convert<T, false><<<(int)blocks, 256, 0, st>>>(n, src, f, dst);
+  else k_convert<T, true><<<(int)blocks, 256, 0, st>>>(n, src, f, dst);
 }
 template void launch_convert<float>(size_t, const double *, double, float *, cudaStream_t);
 template void launch_convert<__nv_bfloat16>(size_t, const double *, double,
