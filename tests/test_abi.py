@@ -109,3 +109,38 @@ def test_without_gpu_build_reports_cuda_error(spfd):
         pytest.skip("a GPU is present")
     st, h = _raw_build(spfd, 8, 4, 4, 4, 2e-3)
     assert st == spfd.SPFD_ECUDA and h is None
+
+
+def test_struct_layouts_match_header(spfd, tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    of the C structures in include/spfd.h, as a C compiler lays them out
+    (a field added on one side only would shift every later field)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"spfd_opts": spfd.SpfdOpts, "spfd_info": spfd.SpfdInfo,
+               "spfd_kernel_stat": spfd.SpfdKernelStat, "spfd_tune_entry": spfd.SpfdTuneEntry}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "spfd.h"',
+             "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for ln in out.split("\n"):
+        if ln:
+            cname, key, val = ln.split()
+            got[(cname, key)] = int(val)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
