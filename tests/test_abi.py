@@ -144,3 +144,13 @@ def test_struct_layouts_match_header(spfd, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def test_constants_match_header(spfd):
+    """Every SPFD_* enumerator of include/spfd.h has the binding's value."""
+    text = open(os.path.join(ROOT, "include", "spfd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    found = dict((k, int(v)) for k, v in re.findall(r"\b(SPFD_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert len(found) >= 10
+    for name, value in found.items():
+        assert getattr(spfd, name) == value, name
