@@ -270,22 +270,28 @@ spfd_status spfd_kernel_stats(spfd_ctx *ctx, spfd_kernel_stat *stats, int max,
  * nodes), computed directly from the voxel grid without a context and
  * without allocating any device memory.  The paper has no counterpart: this
  * is a service for callers that cannot allocate while they check a solution
- * -- code running during CUDA stream capture (cudaMalloc cannot be
- * captured), processes whose device memory an allocator has reserved up
- * front, real-time loops that must not enter the allocator.
+ * -- processes whose device memory an allocator has reserved up front (a
+ * framework's caching allocator, a fixed arena), real-time loops that must
+ * not enter the allocator, or code that must not trigger the implicit
+ * synchronisation a cudaMalloc or cudaFree can cause.
  *   sigma_dev, a_dev, psi_dev  as in spfd_build / spfd_solve (device, FP64).
  *   nx, ny, nz, h              the voxel grid; at most 134,217,728 nodes
  *                              ((nx+1)(ny+1)(nz+1)), else SPFD_EINVAL.
- *   stream                     cudaStream_t to run on (NULL = default stream).
+ *   stream                     cudaStream_t to run on (NULL = default stream);
+ *                              it must not be capturing into a CUDA graph:
+ *                              the call copies the result to host memory and
+ *                              synchronises the stream before it returns.
  *   rel_res                    host output; 0 when b = 0.
  * The partial sums live in one fixed 256 KB device array of the library,
  * which every device that loads the library holds until the process exits.
  * The first call on a device looks up that array's device address (with
- * that device current); make that first call before any stream capture.
- * Every call shares the array and it keeps the last call's contents: calls
- * that overlap on the GPU (other streams, other host threads) race and must
- * be serialised by the caller.  b is not projected, so the value matches
- * spfd_solve's rel_res_true to rounding.  Synchronises the stream. */
+ * that device current) and keeps it; a cudaDeviceReset on that device
+ * invalidates the kept address, so no call may follow one.  Every call
+ * shares the array and it keeps the last call's contents (the counter that
+ * must start at zero is cleared by each call): calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  b is not projected, so the value matches spfd_solve's
+ * rel_res_true to rounding. */
 spfd_status spfd_residual_noalloc(const double *sigma_dev, const double *a_dev,
                                   const double *psi_dev, int nx, int ny, int nz,
                                   double h, void *stream, double *rel_res);

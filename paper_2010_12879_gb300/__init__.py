@@ -263,8 +263,10 @@ def spfd_release_cached_memory() -> int:
 def spfd_residual_noalloc(sigma_ptr: int, a_ptr: int, psi_ptr: int, nx: int,
                           ny: int, nz: int, h: float, stream: int = 0) -> float:
     """Relative residual of psi computed without a context and without
-    allocating device memory (for callers that cannot allocate, e.g. during
-    stream capture); the first call on a device must precede any capture."""
+    allocating device memory, for callers whose device memory is reserved by
+    another allocator or that must stay out of the allocator.  The call
+    synchronises ``stream``, which therefore must not be capturing into a
+    CUDA graph."""
     out = ctypes.c_double(0.0)
     _check(lib().spfd_residual_noalloc(ctypes.c_void_p(sigma_ptr), ctypes.c_void_p(a_ptr),
                                        ctypes.c_void_p(psi_ptr), nx, ny, nz, float(h),

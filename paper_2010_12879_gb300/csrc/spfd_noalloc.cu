@@ -2,13 +2,16 @@
 // context and without allocating device memory.
 //
 // Some callers cannot allocate device memory when they want to check a
-// solution: code running while a stream is being captured into a CUDA graph
-// (cudaMalloc is not a capturable operation), processes whose device memory
-// is reserved up front by another allocator, or real-time loops that must not
-// enter the allocator.  This entry point serves them: the caller passes the
-// conductivities, edge potentials and node potentials it already holds, and
-// the reduction's partial sums live in one file-scope device array of fixed
-// size instead of in memory obtained from cudaMalloc.
+// solution: processes whose device memory is reserved up front by another
+// allocator (a framework's caching allocator, a fixed arena), real-time loops
+// that must not enter the allocator, or code that must not trigger the
+// implicit synchronisation of cudaMalloc / cudaFree.  This entry point serves
+// them: the caller passes the conductivities, edge potentials and node
+// potentials it already holds, and the reduction's partial sums live in one
+// file-scope device array of fixed size instead of in memory obtained from
+// cudaMalloc.  The call reads its result back into host memory and
+// synchronises the stream it is given, so that stream must not be capturing
+// into a CUDA graph.
 //
 // The computation is a fused, brick-free variant of the true-residual kernel
 // of the solver: for every node the six edge conductances are rebuilt from the
@@ -140,7 +143,8 @@ k_residual_noalloc(const double *__restrict__ sigma, const double *__restrict__ 
 
 // Device address of the scratch array on the current device, looked up once
 // per device (the host-side name of a __device__ variable is not a device
-// address).
+// address).  The kept address does not survive a cudaDeviceReset of that
+// device, after which the module is loaded again.
 spfd_status scratch_for_current_device(NoallocScratch **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -175,7 +179,7 @@ extern "C" spfd_status spfd_residual_noalloc(const double *sigma_dev,
   if (nx < 1 || ny < 1 || nz < 1)
     return fail(SPFD_EINVAL, "voxel counts must be >= 1 (got %d %d %d)", nx, ny, nz);
   if (!(h > 0.0) || !std::isfinite(h)) return fail(SPFD_EINVAL, "h must be > 0");
-  const long long NN = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  const long long NN = ((long long)nx + 1) * ((long long)ny + 1) * ((long long)nz + 1);
   if (NN > NA_MAX_NODES)
     return fail(SPFD_EINVAL,
                 "grid of %lld nodes exceeds the %lld nodes the fixed scratch of "

@@ -138,7 +138,11 @@ def test_components_match_26_connectivity(oracle_mod, seed):
 @pytest.mark.parametrize("seed,dims", [(10, (4, 4, 4)), (11, (5, 3, 4)), (12, (6, 5, 4))])
 def test_pcg_matches_dense_least_squares(oracle_mod, seed, dims):
     """Brute force: the minimum-norm least-squares solution of the assembled
-    system, projected per component, equals the oracle's Psi."""
+    system equals the oracle's Psi.  The minimum-norm solution is orthogonal
+    to the null space of A, which is spanned by the indicator vectors of the
+    conducting components, so it already has zero unweighted mean on every
+    component: it is compared as it comes, without re-projection, which pins
+    the projection convention (R4) as well as the solve."""
     rng = np.random.default_rng(seed)
     ph = random_phantom(*dims, rng, air_fraction=0.35)
     nx, ny, nz = dims
@@ -148,12 +152,36 @@ def test_pcg_matches_dense_least_squares(oracle_mod, seed, dims):
     A = _dense(sys)
     b = oracle_mod.rhs(sys, a)
     x = np.linalg.lstsq(A, b, rcond=None)[0]
-    x = oracle_mod.project(sys, x)
     got = sys.gather(psi)
     assert np.linalg.norm(got - x) <= 1e-11 * np.linalg.norm(x)
     # reported residual is the true one
     r = b - A @ sys.gather(psi)
     assert abs(np.linalg.norm(r) / np.linalg.norm(b) - info["rel_res"]) < 1e-13
+
+
+def test_project_removes_the_unweighted_component_mean(oracle_mod):
+    """R4: the projection subtracts each component's plain (unweighted) mean.
+    A unit vector at one node of a component with m nodes becomes 1 - 1/m
+    there and -1/m at the component's other nodes, and leaves every other
+    component untouched; a per-component constant is removed entirely."""
+    rng = np.random.default_rng(11)
+    sigma = np.zeros((5, 6, 9))
+    sigma[1:4, 1:5, 1:4] = rng.uniform(0.1, 1.0, size=(3, 4, 3))
+    sigma[1:3, 2:4, 6:8] = rng.uniform(0.1, 1.0, size=(2, 2, 2))
+    sys = oracle_mod.assemble(sigma, 2e-3)
+    assert sys.ncomp == 2
+    sizes = np.bincount(sys.comp, minlength=sys.ncomp)
+    c = int(np.argmax(sizes))
+    m = int(sizes[c])
+    i = int(np.flatnonzero(sys.comp == c)[m // 2])
+    x = np.zeros(sys.n)
+    x[i] = 1.0
+    y = oracle_mod.project(sys, x.copy())
+    want = np.where(sys.comp == c, -1.0 / m, 0.0)
+    want[i] += 1.0
+    assert np.max(np.abs(y - want)) <= 1e-15
+    k = rng.normal(size=sys.ncomp)
+    assert np.max(np.abs(oracle_mod.project(sys, k[sys.comp].copy()))) <= 1e-15 * np.abs(k).max() * 4
 
 
 def test_rhs_is_consistent(oracle_mod):
