@@ -24,7 +24,14 @@ function cites the paper passage it follows:
   dJ/da = dJ/du - M G lambda and dJ/dsigma from dJ/dg = -(G lambda) u (R1);
 * ``nearest_rank`` / ``percentile`` -- step 6 of the pipeline (Sec. II-A,
   Sec. III-E): the 99th percentile of the voxel-averaged |E| per tissue and
-  over the whole body, nearest-rank (reading R14).
+  over the whole body, nearest-rank (reading R14);
+* ``curl`` -- Eq. 2, b = C a: facet fluxes as the discrete curl of the edge
+  potentials (reading R15);
+* ``comb_tree`` / ``bfs_tree`` / ``tree_cotree`` -- step 3 of the pipeline
+  (Sec. II-A, Eq. 2): the edge potentials a with a = 0 on the edges of a
+  spanning tree of the node grid and C a = b, found from that definition by a
+  sparse least-squares solve over the cotree edges (reading R16; small grids
+  only).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 (closed forms, brute force on tiny grids, invariants); none is unpinned.
@@ -100,6 +107,7 @@ def lib():
             L.orc_percentile.argtypes = [dp, dp, ctypes.POINTER(ctypes.c_int32), i64,
                                          ctypes.c_int, ctypes.c_double, dp, lp]
             L.orc_percentile.restype = ctypes.c_int
+            L.orc_curl.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
             _lib = L
     return _lib
 
@@ -328,3 +336,134 @@ def percentile(sigma: np.ndarray, E: np.ndarray, labels: np.ndarray, n_labels: i
     if rc != 0:
         raise MemoryError("oracle percentile")
     return out, cnt
+
+
+# ------------------------------------------------------------ Eq. 2, step 3
+
+def curl(a: np.ndarray) -> np.ndarray:
+    """b = C a (Eq. 2): the flux through facet d at node (i, j, k), the
+    square spanned by the +d1 and +d2 edges of that node (d1, d2 the cyclic
+    successors of d), circulated right-handed about +d (R15).  Layout of a;
+    slots of facets that would leave the grid are 0."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    _, nzp, nyp, nxp = a.shape
+    b = np.empty_like(a)
+    lib().orc_curl(_d(a), nxp - 1, nyp - 1, nzp - 1, _d(b))
+    return b
+
+
+def _edge_exists(shape_nodes):
+    """[3][nz+1][ny+1][nx+1] mask of the slots that hold an edge."""
+    nzp, nyp, nxp = shape_nodes
+    m = np.zeros((3, nzp, nyp, nxp), dtype=bool)
+    m[0, :, :, :nxp - 1] = True
+    m[1, :, :nyp - 1, :] = True
+    m[2, :nzp - 1, :, :] = True
+    return m
+
+
+def _facet_exists(shape_nodes):
+    """[3][nz+1][ny+1][nx+1] mask of the slots that hold a facet: facet d at
+    a node exists when both of its spanning edges exist there."""
+    nzp, nyp, nxp = shape_nodes
+    m = np.zeros((3, nzp, nyp, nxp), dtype=bool)
+    m[0, :nzp - 1, :nyp - 1, :] = True   # spanned by y and z edges
+    m[1, :nzp - 1, :, :nxp - 1] = True   # spanned by z and x edges
+    m[2, :, :nyp - 1, :nxp - 1] = True   # spanned by x and y edges
+    return m
+
+
+def comb_tree(dims, j0: int, k0: int) -> np.ndarray:
+    """Edge mask [3][nz+1][ny+1][nx+1] of the comb spanning tree of the node
+    grid on the root line (j, k) = (j0, k0): every z edge, the y edges of the
+    plane k = k0 and the x edges of the root line.  Every node reaches the
+    root line through its z column, then the plane's y line; the tree has
+    (nodes - 1) edges (R16)."""
+    nx, ny, nz = dims
+    t = np.zeros((3, nz + 1, ny + 1, nx + 1), dtype=bool)
+    t[2, :nz, :, :] = True
+    t[1, k0, :ny, :] = True
+    t[0, k0, j0, :nx] = True
+    return t
+
+
+def bfs_tree(dims, root) -> np.ndarray:
+    """Edge mask of the breadth-first spanning tree of the node grid from
+    node root = (i0, j0, k0) (scipy's breadth-first order over the grid
+    graph; each node is joined to the node it was discovered from)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+    nx, ny, nz = dims
+    shp = (nz + 1, ny + 1, nx + 1)
+    nn = int(np.prod(shp))
+    ex = _edge_exists(shp)
+    ids = np.arange(nn).reshape(shp)
+    step = (1, nx + 1, (nx + 1) * (ny + 1))
+    rows, cols = [], []
+    for d in range(3):
+        tail = ids[ex[d]]
+        rows.append(tail)
+        cols.append(tail + step[d])
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    graph = sp.coo_matrix((np.ones(r.size), (r, c)), shape=(nn, nn)).tocsr()
+    i0, j0, k0 = root
+    _, pred = breadth_first_order(graph, int(ids[k0, j0, i0]), directed=False,
+                                  return_predecessors=True)
+    t = np.zeros((3,) + shp, dtype=bool)
+    for v in range(nn):
+        u = int(pred[v])
+        if u < 0:
+            continue
+        lo, hi = min(u, v), max(u, v)
+        d = step.index(hi - lo)
+        kk, jj, ii = np.unravel_index(lo, shp)
+        t[d, kk, jj, ii] = True
+    return t
+
+
+def curl_matrix(shape_nodes):
+    """Sparse C of Eq. 2 over every slot: row d*NN + n is facet d at node n
+    (zero rows where no facet exists), column d*NN + n the d edge of node n
+    (R15)."""
+    import scipy.sparse as sp
+    nzp, nyp, nxp = shape_nodes
+    nn = nxp * nyp * nzp
+    step = (1, nxp, nxp * nyp)
+    fx = _facet_exists(shape_nodes)
+    ids = np.arange(nn).reshape(shape_nodes)
+    rows, cols, vals = [], [], []
+    for d in range(3):
+        d1, d2 = (d + 1) % 3, (d + 2) % 3
+        n = ids[fx[d]]
+        row = d * nn + n
+        for col, v in ((d1 * nn + n, 1.0), (d2 * nn + n + step[d1], 1.0),
+                       (d1 * nn + n + step[d2], -1.0), (d2 * nn + n, -1.0)):
+            rows.append(row)
+            cols.append(col)
+            vals.append(np.full(n.size, v))
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(3 * nn, 3 * nn)).tocsr()
+
+
+def tree_cotree(b: np.ndarray, tree: np.ndarray) -> np.ndarray:
+    """Step 3 (Sec. II-A), tree-cotree gauging of Eq. 2: the edge potentials
+    a with a = 0 on the tree edges and C a = b.  For a spanning tree the
+    cotree columns of C are independent (a gradient that vanishes on a
+    spanning tree vanishes everywhere), so for a divergence-free b this is
+    the unique solution of the overdetermined system, found here by a sparse
+    direct solve of its normal equations (R16).  Small grids only."""
+    import scipy.sparse.linalg as spla
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    shp = b.shape[1:]
+    C = curl_matrix(shp)
+    ex = _edge_exists(shp).reshape(-1)
+    cot = np.flatnonzero(ex & ~tree.reshape(-1))
+    fx = np.flatnonzero(_facet_exists(shp).reshape(-1))
+    Cc = C[fx][:, cot]
+    rhs = b.reshape(-1)[fx]
+    N = (Cc.T @ Cc).tocsc()
+    x = spla.spsolve(N, Cc.T @ rhs)
+    a = np.zeros(b.size)
+    a[cot] = x
+    return a.reshape(b.shape)

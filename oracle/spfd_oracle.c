@@ -541,3 +541,36 @@ int orc_percentile(const double *sigma, const double *E, const int *labels, i64 
   free(buf);
   return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Eq. 2 (Sec. II): b = C a, the magnetic fluxes through the grid facets as
+ * the discrete curl of the edge vector potentials.
+ *
+ * Facet d at node (i,j,k) is the square spanned by the two edges that leave
+ * that node along d1 = (d+1) mod 3 and d2 = (d+2) mod 3; its normal is +d
+ * and its boundary is run right-handed about +d (along d1 first):
+ *   b_d(n) = a_d1(n) + a_d2(n + e_d1) - a_d1(n + e_d2) - a_d2(n).
+ * b has the edge layout [3][nz+1][ny+1][nx+1]; slots of facets that would
+ * leave the grid are 0.  Each facet sums its four terms in the order above.
+ * ------------------------------------------------------------------------- */
+void orc_curl(const double *a, int nx_, int ny_, int nz_, double *b) {
+  i64 n[3] = {(i64)nx_ + 1, (i64)ny_ + 1, (i64)nz_ + 1};
+  i64 nn = n[0] * n[1] * n[2];
+  i64 stride[3] = {1, n[0], n[0] * n[1]};
+#pragma omp parallel for schedule(static)
+  for (i64 k = 0; k < n[2]; k++)
+    for (i64 j = 0; j < n[1]; j++)
+      for (i64 i = 0; i < n[0]; i++) {
+        i64 idx[3] = {i, j, k};
+        i64 v = (k * n[1] + j) * n[0] + i;
+        for (int d = 0; d < 3; d++) {
+          int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+          if (idx[d1] + 1 >= n[d1] || idx[d2] + 1 >= n[d2]) {
+            b[d * nn + v] = 0.0;
+            continue;
+          }
+          const double *a1 = a + d1 * nn, *a2 = a + d2 * nn;
+          b[d * nn + v] = a1[v] + a2[v + stride[d1]] - a1[v + stride[d2]] - a2[v];
+        }
+      }
+}

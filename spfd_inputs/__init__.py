@@ -1,9 +1,10 @@
 """Seeded synthetic inputs shared by the CUDA path and the CPU oracle.
 
-This package only *generates inputs*: voxel conductivity phantoms and edge
-vector potentials of analytic magnetic sources.  It holds none of the
-arithmetic of the SPFD method itself (no conductance averaging, no gradient,
-no Poisson operator, no solver, no field evaluation).
+This package only *generates inputs*: voxel conductivity phantoms, edge
+vector potentials of analytic magnetic sources and facet fluxes of their
+closed-form flux densities (``flux.py``).  It holds none of the arithmetic of
+the SPFD method itself (no conductance averaging, no gradient or curl, no
+Poisson operator, no solver, no gauging, no field evaluation).
 
 Grid conventions (used by every consumer):
 
@@ -25,6 +26,7 @@ from .phantoms import (
     scaled_body_phantom,
     sphere_phantom,
 )
+from .flux import loop_flux, loop_flux_density, uniform_flux
 from .sources import (
     MU0,
     edge_potential,
@@ -44,6 +46,9 @@ __all__ = [
     "sphere_phantom",
     "MU0",
     "edge_potential",
+    "loop_flux",
+    "loop_flux_density",
+    "uniform_flux",
     "loop_potential",
     "loop_vector_potential",
     "random_loops",
