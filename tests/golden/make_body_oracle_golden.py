@@ -5,8 +5,11 @@ Solves the full-size body phantom (256 x 160 x 896 voxels, h = 2 mm,
 oracle's Jacobi-preconditioned CG twice -- to the 1e-8 relative residual of
 the benchmark and to the oracle's 1e-13 -- and records the iteration counts,
 residuals, wall times and thread count, plus Psi (zero mean per component)
-at 4096 seeded unknowns of the 1e-13 solve and its 2-norm.  Nothing here
-touches the CUDA path.  Run from the repository root:
+at 4096 seeded unknowns of the 1e-13 solve and its 2-norm, and the
+voxel-averaged |E| of Eq. 1 from that solve at 8192 seeded conducting voxels
+with its maximum over the body and the floor scale omega/h * max|a| of the
+|E| comparison.  Nothing here touches the CUDA path.  Run from the
+repository root:
 
     python tests/golden/make_body_oracle_golden.py
 """
@@ -53,6 +56,15 @@ def main():
     rec["psi_sample_nodes"] = sys_.nodes[pick].tolist()
     rec["psi_sample_values"] = x[pick].tolist()
     rec["psi_norm2"] = float(np.linalg.norm(x))
+    omega = 2 * np.pi * 85e3
+    E = oracle.efield(ph.sigma, a, sys_.scatter(x), ph.h, omega)
+    cond = np.flatnonzero(ph.sigma.reshape(-1) > 0)
+    vpick = np.sort(np.random.default_rng(12879).choice(cond.size, size=8192, replace=False))
+    rec["omega"] = omega
+    rec["E_sample_voxels"] = cond[vpick].tolist()
+    rec["E_sample_values"] = E.reshape(-1)[cond[vpick]].tolist()
+    rec["E_max"] = float(E.max())
+    rec["E_floor_scale"] = float(omega / ph.h * np.abs(a).max())
     with open(out, "w") as f:
         json.dump(rec, f, indent=1)
     print("wrote", out)
