@@ -177,6 +177,33 @@ spfd_status spfd_solve_batch(spfd_ctx *ctx, int nrhs, const double *a_dev, doubl
 spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host, double tol,
                             double *psi_host, spfd_info *info);
 
+/* Steps 4 and 5 of the pipeline (Sec. II-A) in one call with host arrays:
+ * builds the operator of Eq. 3 for sigma, solves it for a to tol, evaluates
+ * the voxel-averaged |E| of Eq. 1 and returns Psi and |E| in host memory
+ * (spfd_build + spfd_solve + spfd_efield + spfd_destroy, with the copies).
+ *   sigma_host  [nz][ny][nx] FP64 conductivities, host.
+ *   a_host      [3][nz+1][ny+1][nx+1] FP64 edge potentials, host.  Only the
+ *               rows (fixed edge direction, y and z node index) that hold an
+ *               edge of a conducting voxel are read; when the device can read
+ *               the memory directly (pinned memory, or any memory where
+ *               pageable-memory access is supported) they are pulled by the
+ *               GPU while the operator is built, else a is copied whole.
+ *   nx..h       as in spfd_build; tol as in spfd_solve; omega as in
+ *               spfd_efield; opts NULL for defaults.
+ *   stream      cudaStream_t (NULL = legacy default stream); a second stream
+ *               of the call's own carries the copy of a and of Psi.
+ *   psi_host    [nz+1][ny+1][nx+1] FP64 output, host.
+ *   E_host      [nz][ny][nx] FP64 output in V/m, host.
+ *   info        optional report of the solve; launches counts every kernel
+ *               of the call.
+ * Device buffers come from the library's block cache and are returned to it.
+ * Synchronises.  Returns SPFD_ENOTCONVERGED (Psi and |E| written) if tol was
+ * not reached.  Pinned host arrays give the fastest copies. */
+spfd_status spfd_pipeline_host(const double *sigma_host, const double *a_host, int nx,
+                               int ny, int nz, double h, double tol, double omega,
+                               const spfd_opts *opts, void *stream, double *psi_host,
+                               double *E_host, spfd_info *info);
+
 /* Voxel-averaged |E| of Eq. 1: for each conducting voxel,
  *   E_d = omega / (4 h) * sum over its four d-edges of (a_e + Psi_head - Psi_tail),
  *   |E| = sqrt(E_x^2 + E_y^2 + E_z^2); air voxels get 0.
@@ -185,6 +212,34 @@ spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host, double tol,
  * Asynchronous on the context's stream. */
 spfd_status spfd_efield(spfd_ctx *ctx, const double *a_dev,
                         const double *psi_dev, double omega, double *E_dev);
+
+/* Step 3 of the pipeline (Sec. II-A, step 3): the edge vector potentials a
+ * from the magnetic facet fluxes b of Eq. 2, b = C a, by tree-cotree
+ * gauging.  C (the discrete curl) annihilates every discrete gradient, so b
+ * fixes a only up to one; the gauge sets a = 0 on the edges of a spanning
+ * tree of the node grid, and the cotree edges then follow from b uniquely.
+ * The tree is the comb on the root line (j, k) = (j0, k0): every z edge, the
+ * y edges of the plane k = k0 and the x edges of the root line.  The result
+ * differs from any other potential of the same b by a discrete gradient, so
+ * spfd_solve and spfd_efield give the same |E| from it (gauge invariance of
+ * Eq. 1 and Eq. 3).
+ *   b_dev   [3][nz+1][ny+1][nx+1] FP64 facet fluxes in Wb, device: component
+ *           d at node (i,j,k) is the flux through the square spanned by the
+ *           two edges that leave that node along d1 = (d+1) mod 3 and
+ *           d2 = (d+2) mod 3, with normal +d (its boundary run along d1
+ *           first); slots of facets that would leave the grid are ignored.
+ *           b must be divergence-free (zero net flux out of every voxel) for
+ *           C a = b to hold on every facet; otherwise the facets z off the
+ *           plane k0 absorb the mismatch.
+ *   nx,ny,nz voxel counts (>= 1); j0 in 0..ny, k0 in 0..nz (a central root
+ *           line keeps |a| smallest).
+ *   stream  cudaStream_t to run on (NULL = the legacy default stream).
+ *   a_dev   [3][nz+1][ny+1][nx+1] FP64 output in V*s (the layout of
+ *           spfd_solve's a), device; every slot is written (0 on the tree
+ *           and past the last node).  Must not overlap b_dev.
+ * Needs no context and allocates nothing; asynchronous. */
+spfd_status spfd_tree_cotree(const double *b_dev, int nx, int ny, int nz, int j0, int k0,
+                             void *stream, double *a_dev);
 
 /* Step 6 of the pipeline (Sec. II-A, step 6; Sec. III-E): the p-quantile
  * (p = 0.99 for the 99th percentile) of the voxel-averaged |E| per tissue and

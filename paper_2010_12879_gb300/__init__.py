@@ -32,7 +32,7 @@ EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
            "spfd_energy_grad", "spfd_solve_batch", "spfd_percentile",
            "spfd_group_create", "spfd_group_solve", "spfd_group_destroy",
-           "spfd_autotune_report")
+           "spfd_autotune_report", "spfd_tree_cotree", "spfd_pipeline_host")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -115,6 +115,13 @@ def lib():
             L.spfd_residual_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, dp, vp, ctypes.POINTER(dp)]
             L.spfd_residual_noalloc.restype = ctypes.c_int
+            L.spfd_tree_cotree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, vp, vp]
+            L.spfd_tree_cotree.restype = ctypes.c_int
+            L.spfd_pipeline_host.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             dp, dp, dp, ctypes.POINTER(SpfdOpts), vp, vp, vp,
+                                             ctypes.POINTER(SpfdInfo)]
+            L.spfd_pipeline_host.restype = ctypes.c_int
             L.spfd_energy_grad.argtypes = [vp, vp, vp, dp, dp, ctypes.POINTER(dp), vp, vp,
                                            ctypes.POINTER(SpfdInfo)]
             L.spfd_energy_grad.restype = ctypes.c_int
@@ -272,6 +279,51 @@ def spfd_residual_noalloc(sigma_ptr: int, a_ptr: int, psi_ptr: int, nx: int,
                                        ctypes.c_void_p(psi_ptr), nx, ny, nz, float(h),
                                        ctypes.c_void_p(stream), ctypes.byref(out)))
     return out.value
+
+
+def spfd_tree_cotree(b_ptr: int, nx: int, ny: int, nz: int, j0: int, k0: int,
+                     stream: int, a_ptr: int) -> None:
+    """Step 3 (Sec. II-A): edge potentials from facet fluxes by tree-cotree
+    gauging on the comb tree of root line (j0, k0) (device pointers)."""
+    _check(lib().spfd_tree_cotree(ctypes.c_void_p(b_ptr), nx, ny, nz, j0, k0,
+                                  ctypes.c_void_p(stream), ctypes.c_void_p(a_ptr)))
+
+
+def tree_cotree(b, j0: int | None = None, k0: int | None = None, out=None):
+    """``torch.float64`` CUDA tensor b [3][nz+1][ny+1][nx+1] of facet fluxes
+    -> edge potentials a of the same shape (new tensor, or ``out``), on the
+    current stream; the root line defaults to the grid's centre."""
+    import torch
+    if not (b.is_cuda and b.dtype == torch.float64 and b.is_contiguous() and b.dim() == 4
+            and b.shape[0] == 3):
+        raise ValueError("b must be a contiguous float64 CUDA tensor [3][nz+1][ny+1][nx+1]")
+    nz, ny, nx = (int(v) - 1 for v in b.shape[1:])
+    j0 = ny // 2 if j0 is None else int(j0)
+    k0 = nz // 2 if k0 is None else int(k0)
+    a = torch.empty_like(b) if out is None else out
+    if not (a.shape == b.shape and a.dtype == torch.float64 and a.is_cuda and a.is_contiguous()):
+        raise ValueError("out must match b")
+    spfd_tree_cotree(b.data_ptr(), nx, ny, nz, j0, k0,
+                     torch.cuda.current_stream(b.device).cuda_stream, a.data_ptr())
+    return a
+
+
+def pipeline_host(sigma, a, h: float, tol: float, omega: float, psi_out, E_out,
+                  opts=None, stream: int = 0):
+    """Steps 4 and 5 (Sec. II-A) with host arrays: ``sigma`` [nz][ny][nx] and
+    ``a`` [3][nz+1][ny+1][nx+1] (float64, C-contiguous CPU tensors or numpy
+    arrays; pinned tensors give the fastest copies) in, Psi and |E| written
+    to ``psi_out`` / ``E_out`` (host, same kinds).  Returns (status, info)."""
+    def ptr(x):
+        return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+    nz, ny, nx = (int(v) for v in sigma.shape)
+    info = SpfdInfo()
+    st = _check(lib().spfd_pipeline_host(
+        ctypes.c_void_p(ptr(sigma)), ctypes.c_void_p(ptr(a)), nx, ny, nz, float(h), float(tol),
+        float(omega), ctypes.byref(opts) if opts is not None else None,
+        ctypes.c_void_p(stream), ctypes.c_void_p(ptr(psi_out)), ctypes.c_void_p(ptr(E_out)),
+        ctypes.byref(info)), allow=(SPFD_OK, SPFD_ENOTCONVERGED))
+    return st, info.as_dict()
 
 
 def spfd_group_create(ctxs, stream: int = 0) -> int:

@@ -82,6 +82,39 @@ def test_null_context_calls(spfd):
     L.spfd_destroy(None)  # no-op
 
 
+@pytest.mark.parametrize("args", [
+    (0, 8, 4, 4, 4, 2, 2),          # null b
+    (8, 0, 4, 4, 4, 2, 2),          # null a
+    (8, 1 << 20, 0, 4, 4, 2, 2),    # zero dims
+    (8, 1 << 20, 4, 4, 4, 5, 2),    # root line outside (j0 > ny)
+    (8, 1 << 20, 4, 4, 4, 2, -1),   # root line outside (k0 < 0)
+    (8, 16, 4, 4, 4, 2, 2),         # a overlaps b
+])
+def test_tree_cotree_rejects_invalid_arguments(spfd, args):
+    """Checked on the host before any launch (no GPU needed)."""
+    b, a, nx, ny, nz, j0, k0 = args
+    st = spfd.lib().spfd_tree_cotree(ctypes.c_void_p(b), nx, ny, nz, j0, k0, None,
+                                     ctypes.c_void_p(a))
+    assert st == spfd.SPFD_EINVAL
+    assert spfd.spfd_last_error()
+
+
+@pytest.mark.parametrize("args", [
+    (0, 8, 4, 4, 4, 2e-3, 1.0),          # null sigma
+    (8, 8, 0, 4, 4, 2e-3, 1.0),          # zero dims
+    (8, 8, 4000, 4000, 4000, 2e-3, 1.0), # > 2^31 nodes
+    (8, 8, 4, 4, 4, 2e-3, float("inf")), # omega not finite
+])
+def test_pipeline_host_rejects_invalid_arguments(spfd, args):
+    """Checked on the host before any device work (no GPU needed)."""
+    sig, a, nx, ny, nz, h, omega = args
+    st = spfd.lib().spfd_pipeline_host(ctypes.c_void_p(sig), ctypes.c_void_p(a), nx, ny, nz,
+                                       h, 1e-8, omega, None, None, ctypes.c_void_p(8),
+                                       ctypes.c_void_p(8), None)
+    assert st == spfd.SPFD_EINVAL
+    assert spfd.spfd_last_error()
+
+
 def test_invalid_options_rejected(spfd):
     L = spfd.lib()
     o = spfd.spfd_opts_default()
