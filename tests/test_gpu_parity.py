@@ -275,6 +275,37 @@ def test_host_array_entry_point(torch_cuda, spfd, oracle_mod):
     np.testing.assert_array_equal(psi_h.numpy(), psi_d.cpu().numpy())
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_pipeline_entry_point(torch_cuda, spfd, oracle_mod, pinned):
+    """spfd_pipeline_host (host sigma and a in, host Psi and |E| out, the
+    rows of a pulled selectively when the device can read the host memory,
+    else copied whole) gives the device path's results bit for bit and the
+    oracle's within the parity bar, on the 16 mm body (several bricks, air
+    rows of a that are never read) and the sphere."""
+    torch = torch_cuda
+    for ph in (body_phantom(32, 20, 112, h=16e-3), sphere_phantom()):
+        a = loop_potential(ph.dims, ph.h, ph.origin)
+        nz, ny, nx = ph.sigma.shape
+        if pinned:
+            sig_h = torch.from_numpy(ph.sigma).pin_memory()
+            a_h = torch.from_numpy(a).pin_memory()
+            psi_h = torch.empty((nz + 1, ny + 1, nx + 1), dtype=torch.float64).pin_memory()
+            E_h = torch.empty((nz, ny, nx), dtype=torch.float64).pin_memory()
+        else:
+            sig_h, a_h = ph.sigma.copy(), a.copy()
+            psi_h = np.full((nz + 1, ny + 1, nx + 1), np.nan)
+            E_h = np.full((nz, ny, nx), np.nan)
+        st, info = spfd.pipeline_host(sig_h, a_h, ph.h, 1e-13, OMEGA, psi_h, E_h)
+        assert st == spfd.SPFD_OK and info["rel_res_true"] <= 1e-13
+        psi_p = np.asarray(psi_h)
+        E_p = np.asarray(E_h)
+        psi_d, E_d, info_d, st_d = _gpu_solve(torch, spfd, ph, a, tol=1e-13)
+        np.testing.assert_array_equal(psi_p, psi_d)
+        np.testing.assert_array_equal(E_p, E_d)
+        assert info["iters"] == info_d["iters"]
+        _compare(oracle_mod, ph, a, psi_p, E_p)
+
+
 def test_cached_blocks_are_reused(torch_cuda, spfd):
     """A second build of the same model takes its device buffers from the
     library's cache: no net device memory is taken from the driver, and
@@ -388,3 +419,45 @@ def test_body_full_size_matches_oracle_samples(torch_cuda, spfd, body_2mm):
     got = psi.reshape(-1)[torch.from_numpy(nodes).cuda()].cpu().numpy()
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err <= 1e-9, f"sampled psi rel error {err:.3e}"
+
+
+@pytest.mark.parametrize("precision,tol,psi_bar,E_bar", [
+    ("fp64", 1e-12, 1e-9, 1e-7),
+    ("mixed", 1e-12, 1e-9, 1e-7),
+    ("fp64", 1e-8, 1e-5, 1e-5),
+    ("mixed", 1e-8, 1e-5, 1e-5),
+])
+def test_body_full_size_error_against_oracle(torch_cuda, spfd, body_2mm, precision, tol,
+                                             psi_bar, E_bar):
+    """The error of each form against the oracle's floor solution of the full
+    body (tests/golden/body_2mm_oracle.json): Psi at 4096 seeded unknowns
+    (relative L2) and |E| at 8192 seeded conducting voxels (largest relative
+    error, floor 1e-6 of the field scale, R9).  At the parity tolerance 1e-12
+    both forms meet the 1e-9 / 1e-7 bars; at the timing tolerance 1e-8 a
+    residual of 1e-8 bounds the error only through the conditioning of the
+    operator, so the bound asserted is the stated one the benchmark reports
+    against (1e-5)."""
+    import json
+    import os
+    torch = torch_cuda
+    ph, a = body_2mm
+    with open(os.path.join(os.path.dirname(__file__), "golden", "body_2mm_oracle.json")) as f:
+        gold = json.load(f)
+    prec = spfd.SPFD_FP64 if precision == "fp64" else spfd.SPFD_MIXED
+    ad = _dev(torch, a)
+    with spfd.Solver(_dev(torch, ph.sigma), ph.h, precision=prec) as S:
+        psi, info, st = S.solve(ad, tol)
+        E = S.efield(ad, psi, OMEGA).reshape(-1)
+    assert st == spfd.SPFD_OK and info["rel_res_true"] <= tol
+    nodes = torch.tensor(gold["psi_sample_nodes"], dtype=torch.int64, device="cuda")
+    vox = torch.tensor(gold["E_sample_voxels"], dtype=torch.int64, device="cuda")
+    pw = np.array(gold["psi_sample_values"])
+    ew = np.array(gold["E_sample_values"])
+    pg = psi.reshape(-1)[nodes].cpu().numpy()
+    eg = E[vox].cpu().numpy()
+    err_psi = np.linalg.norm(pg - pw) / np.linalg.norm(pw)
+    floor = 1e-6 * max(gold["E_max"], gold["E_floor_scale"])
+    err_E = np.max(np.abs(eg - ew) / np.maximum(ew, floor))
+    print(f"{precision} tol {tol:g}: psi {err_psi:.3e}, |E| {err_E:.3e}, "
+          f"iters {info['iters']}/{info['outer_iters']}")
+    assert err_psi <= psi_bar and err_E <= E_bar, (err_psi, err_E)
