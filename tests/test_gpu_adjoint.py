@@ -152,3 +152,65 @@ def test_energy_grad_scaled_body_128_properties(torch_cuda, spfd, oracle_mod):
     assert J == pytest.approx(J_ref, rel=1e-12)
     b = oracle_mod.div(gJ)
     assert np.linalg.norm(oracle_mod.div(dJda)) <= 2e-10 * np.linalg.norm(b)
+
+
+def test_energy_grad_scaled_body_128_finite_differences(torch_cuda, spfd):
+    """The adjoint gradient at the full size of the adjoint workload (the
+    body scaled to 128 x 96 x 448 voxels, 40 tissues, loop source) against
+    central differences of the GPU's own objective:
+    * dJ/dsigma summed per tissue, for a seeded subset of 8 tissues, against
+      (J(t_i (1 + d)) - J(t_i (1 - d))) / (2 d t_i) at relative step d = 1e-6
+      of the tissue's table entry, every solve to 1e-12;
+    * dJ/da along 3 seeded random directions w against the central
+      difference of J(a +- eps w): J is quadratic in a, so the difference is
+      exact up to rounding at any step.
+    Bar: 1e-6 relative, normwise over the 8 tissues (the largest error
+    against the largest gradient), per direction for dJ/da."""
+    torch = torch_cuda
+    ph = scaled_body_phantom(128, 96, 448)
+    a = _dev(torch, loop_potential(ph.dims, ph.h, ph.origin))
+    lab = ph.labels.astype(np.int64)
+    air = lab < 0
+    tol = 1e-12
+
+    def sigma_of(table):
+        s = np.asarray(table)[np.where(air, 0, lab)]
+        s[air] = 0.0
+        return s
+
+    def run(table, av, grads=False):
+        with spfd.Solver(_dev(torch, sigma_of(table)), ph.h) as S:
+            psi, _, st = S.solve(av, tol)
+            assert st == spfd.SPFD_OK
+            J, dJda, dJds, info, st = S.energy_grad(av, psi, OMEGA, tol)
+            assert st == spfd.SPFD_OK and info["converged"]
+            return (J, dJda, dJds) if grads else J
+
+    table = np.array(ph.tissue_sigma, dtype=np.float64)
+    J0, dJda, dJds = run(table, a, grads=True)
+    dJds = dJds.cpu().numpy()
+    rng = np.random.default_rng(128)
+    present = np.unique(lab[~air])
+    pick = np.sort(rng.choice(present, size=8, replace=False))
+    adj = np.array([dJds[lab == t].sum() for t in pick])
+    fd = []
+    d = 1e-6
+    for t in pick:
+        tp, tm = table.copy(), table.copy()
+        tp[t] *= 1 + d
+        tm[t] *= 1 - d
+        fd.append((run(tp, a) - run(tm, a)) / (2 * d * table[t]))
+    fd = np.array(fd)
+    err_sigma = np.abs(fd - adj).max() / np.abs(adj).max()
+    errs_a = []
+    for _ in range(3):
+        w = torch.from_numpy(rng.normal(size=tuple(a.shape))).cuda()
+        eps = 1e-3 * float(a.abs().max()) / float(w.abs().max())
+        Jp, Jm = run(table, a + eps * w), run(table, a - eps * w)
+        fd_a = (Jp - Jm) / (2 * eps)
+        an = float((dJda * w).sum())
+        errs_a.append(abs(fd_a - an) / abs(an))
+    print(f"128x96x448 adjoint vs central differences: dJ/dsigma {err_sigma:.2e}, "
+          f"dJ/da {max(errs_a):.2e}")
+    assert err_sigma <= 1e-6, (fd, adj)
+    assert max(errs_a) <= 1e-6, errs_a
