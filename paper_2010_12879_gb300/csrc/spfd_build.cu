@@ -337,8 +337,11 @@ static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
   TRY(dalloc(c, &b1, (size_t)m * m));
   TRY(h2d(c, b0, A, (size_t)m * m * sizeof(double)));
   double *inv = nullptr;
-  SPFD_LAUNCH(c, "setup_coarsest", false, (m + 15) / 16, 0, 2.0 * m * m * m,
-              inv = launch_dense_inverse(b0, b1, m, &c->sc->status, c->stream));
+  unsigned *bar = nullptr;
+  TRY(dalloc(c, &bar, 2));
+  CU(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), c->stream));
+  SPFD_LAUNCH(c, "setup_coarsest", false, dense_inverse_launches(m), 0, 2.0 * m * m * m,
+              inv = launch_dense_inverse(b0, b1, m, &c->sc->status, bar, c->stream));
   TRY(launch_check("coarsest inverse"));
   // a non-positive pivot raises DEV_BAD_PIVOT, read at the end of the build
   c->Binv = inv;
@@ -362,9 +365,9 @@ static spfd_status setup_mixed_level(spfd_ctx *c, int l) {
   TRY(dalloc(c, &lv.wdinv32, S));
   SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.wdinv, 1.0, lv.wdinv32, st));
   if (lv.Pc) {
-    TRY(dalloc(c, &lv.Pc32, 27 * (S / 8)));
+    TRY(dalloc(c, &lv.Pc16, 27 * (S / 8)));
     SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
-                launch_convert<float>(27 * (S / 8), lv.Pc, 1.0, lv.Pc32, st));
+                launch_convert<__half>(27 * (S / 8), lv.Pc, 1.0, lv.Pc16, st));
   }
   if (l == 0) {
     TRY(dalloc(c, &lv.gx32, 3 * S));
@@ -375,10 +378,12 @@ static spfd_status setup_mixed_level(spfd_ctx *c, int l) {
                 launch_convert<__nv_bfloat16>(3 * S, lv.gx, 1.0, lv.gxbf, st));
     SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
   } else {
-    TRY(dalloc(c, &lv.st32, 27 * S));
-    TRY(dalloc(c, &lv.P32, 27 * S));
-    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
-    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
+    // the symmetric half of the stencil: entries 13..26 (coef27)
+    TRY(dalloc(c, &lv.st32, 14 * S));
+    TRY(dalloc(c, &lv.P16, 27 * S));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
+                launch_convert<float>(14 * S, lv.st + 13 * S, 1.0, lv.st32, st));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<__half>(27 * S, lv.P, 1.0, lv.P16, st));
   }
   return launch_check("mixed-precision copies");
 }
@@ -764,6 +769,8 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   TRY(sync_check(c, "build"));
   if (c->hsc->status & DEV_BAD_PIVOT)
     return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
+  if (c->hsc->status & DEV_GRID_WAIT)
+    return fail(SPFD_EINTERNAL, "coarsest inverse: a grid-wide barrier hit its wait cap");
   for (size_t l = 1; l + 1 < c->L.size(); ++l) {
     c->L[l].lmax = hlam[l];
     c->L[l].omega = 4.0 / (3.0 * 1.05 * hlam[l]);

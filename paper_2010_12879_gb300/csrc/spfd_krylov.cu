@@ -521,74 +521,93 @@ k_gather(Grid g, const double *__restrict__ psi, const int *__restrict__ comp,
 // of an axis are added in the order (s, t) = (0,0), (0,1), (1,0), (1,1) of
 // the edge offsets, with no contracted multiply-add, so the result is the
 // correctly rounded evaluation of that fixed expression.
-// Thread i of row (j, k) loads node column i (nodes (i, j..j+1, k..k+1)):
-// its four Psi values, its two y-edge terms (at k and k+1) and its two
-// z-edge terms (at j and j+1).  Voxel i also needs column i+1, which comes
-// from the next lane (the last lane loads it itself).
-struct EfCol {
-  double p00, p10, p01, p11;  // Psi(i, j+s, k+t) as p_st
-  double y0, y1, z0, z1;      // y-edge terms at k, k+1; z-edge terms at j, j+1
-};
+//
+// Every edge term is formed once.  Warp w covers the node columns
+// 31w .. 31w + 31 of the plane j < ny (flattened as col = j * (nx+1) + i):
+// lane l < 31 owns voxel (i, j) of its column when i < nx, and lane 31 only
+// supplies its column's terms to lane 30.  A column forms, per node layer k,
+// its x-edge terms at rows j and j+1 (X0, X1, with Psi of column i+1 from the
+// next lane) and its y-edge term (Y), and per voxel layer its two z-edge terms
+// (Z0, Z1); voxel i takes the y and z terms of column i+1 from the next lane
+// too.  Block y walks EF_KCHUNK voxel layers and carries the terms of layer
+// k+1 into layer k+1's voxels, so a layer's terms are formed once.  Layers
+// with no conducting voxel in the warp form nothing (their voxels get 0).
+// Per voxel layer a column forms 5 terms (10 FP64 additions) against 16 when
+// every voxel forms its own.
+constexpr int EF_THREADS = 256;
+constexpr int EF_KCHUNK = 32;
 
-__device__ __forceinline__ EfCol ef_column(const double *__restrict__ a,
-                                           const double *__restrict__ psi, size_t n00,
-                                           size_t NX, size_t NXY, size_t NN) {
-  EfCol c;
-  c.p00 = psi[n00];
-  c.p10 = psi[n00 + NX];
-  c.p01 = psi[n00 + NXY];
-  c.p11 = psi[n00 + NXY + NX];
-  c.y0 = __dadd_rn(__dadd_rn(a[NN + n00], c.p10), -c.p00);
-  c.y1 = __dadd_rn(__dadd_rn(a[NN + n00 + NXY], c.p11), -c.p01);
-  c.z0 = __dadd_rn(__dadd_rn(a[2 * NN + n00], c.p01), -c.p00);
-  c.z1 = __dadd_rn(__dadd_rn(a[2 * NN + n00 + NX], c.p11), -c.p10);
-  return c;
-}
+struct EfTerms {
+  double p0, p1;  // Psi(i, j, k), Psi(i, j+1, k)
+  double x0, x1;  // x-edge terms at (i, j, k), (i, j+1, k)
+  double y;       // y-edge term at (i, j, k)
+};
 
 __device__ __forceinline__ double shfl_next(double v) {
   return __shfl_down_sync(0xffffffffu, v, 1);
 }
 
-__global__ void __launch_bounds__(128)
+// The terms of node layer k for the column at node offset nc (every lane of
+// the warp calls it; lanes without a column get zeros).
+__device__ __forceinline__ EfTerms ef_layer(const double *__restrict__ a,
+                                            const double *__restrict__ psi, bool live,
+                                            size_t n, size_t NX, size_t NN) {
+  EfTerms T;
+  T.p0 = live ? psi[n] : 0.0;
+  T.p1 = live ? psi[n + NX] : 0.0;
+  const double q0 = shfl_next(T.p0), q1 = shfl_next(T.p1);  // column i+1
+  T.x0 = live ? __dadd_rn(__dadd_rn(a[n], q0), -T.p0) : 0.0;
+  T.x1 = live ? __dadd_rn(__dadd_rn(a[n + NX], q1), -T.p1) : 0.0;
+  T.y = live ? __dadd_rn(__dadd_rn(a[NN + n], T.p1), -T.p0) : 0.0;
+  return T;
+}
+
+__global__ void __launch_bounds__(EF_THREADS)
 k_efield(const unsigned char *__restrict__ mask, const double *__restrict__ a,
          const double *__restrict__ psi, int nx, int ny, int nz, double c,
          double *__restrict__ E) {
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  const long long warp = ((long long)blockIdx.x * EF_THREADS + threadIdx.x) >> 5;
   const size_t NX = (size_t)nx + 1, NXY = NX * ((size_t)ny + 1);
   const size_t NN = NXY * ((size_t)nz + 1);
-  for (int k = blockIdx.z; k < nz; k += gridDim.z) {
-    const size_t n00 = (size_t)k * NXY + (size_t)j * NX + i;
+  const long long ncol = (long long)NX * ny;
+  if (warp * 31 >= ncol) return;  // the whole warp is past the plane
+  const long long col = warp * 31 + lane;
+  const bool live = col < ncol;
+  const int i = live ? (int)(col % (long long)NX) : 0, j = live ? (int)(col / (long long)NX) : 0;
+  const bool own = live && lane < 31 && i < nx;
+  const size_t nc = (size_t)j * NX + i;
+  const int kb = blockIdx.y * EF_KCHUNK, ke = min(kb + EF_KCHUNK, nz);
+  EfTerms T{};
+  bool have = false;  // T holds layer k's terms (warp-uniform)
+  for (int k = kb; k < ke; ++k) {
     const size_t v = ((size_t)k * ny + j) * nx + i;
-    // column i serves voxels i (own) and i-1 (through the shuffle)
-    const bool cond = i < nx && mask[v];
-    const bool need = cond || (i > 0 && i <= nx && mask[v - 1]);
-    EfCol h{0, 0, 0, 0, 0, 0, 0, 0};
-    if (need) h = ef_column(a, psi, n00, NX, NXY, NN);
-    EfCol n;
-    n.p00 = shfl_next(h.p00);
-    n.p10 = shfl_next(h.p10);
-    n.p01 = shfl_next(h.p01);
-    n.p11 = shfl_next(h.p11);
-    n.y0 = shfl_next(h.y0);
-    n.y1 = shfl_next(h.y1);
-    n.z0 = shfl_next(h.z0);
-    n.z1 = shfl_next(h.z1);
-    if (i >= nx) continue;
-    if (!cond) {
-      E[v] = 0.0;
+    const bool cond = own && mask[v];
+    if (!__any_sync(0xffffffffu, cond)) {
+      if (own) E[v] = 0.0;
+      have = false;
       continue;
     }
-    if (lane == 31) n = ef_column(a, psi, n00 + 1, NX, NXY, NN);
-    // x-edge terms at (i, j+s, k+t)
-    const double x00 = __dadd_rn(__dadd_rn(a[n00], n.p00), -h.p00);
-    const double x01 = __dadd_rn(__dadd_rn(a[n00 + NXY], n.p01), -h.p01);
-    const double x10 = __dadd_rn(__dadd_rn(a[n00 + NX], n.p10), -h.p10);
-    const double x11 = __dadd_rn(__dadd_rn(a[n00 + NXY + NX], n.p11), -h.p11);
-    const double ex = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(x00, x01), x10), x11), c);
-    const double ey = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(h.y0, h.y1), n.y0), n.y1), c);
-    const double ez = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(h.z0, h.z1), n.z0), n.z1), c);
-    E[v] = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+    const size_t n = (size_t)k * NXY + nc;
+    if (!have) T = ef_layer(a, psi, live, n, NX, NN);
+    const EfTerms Tn = ef_layer(a, psi, live, n + NXY, NX, NN);
+    const double z0 = live ? __dadd_rn(__dadd_rn(a[2 * NN + n], Tn.p0), -T.p0) : 0.0;
+    const double z1 = live ? __dadd_rn(__dadd_rn(a[2 * NN + n + NX], Tn.p1), -T.p1) : 0.0;
+    // the y and z terms of column i+1
+    const double y0n = shfl_next(T.y), y1n = shfl_next(Tn.y);
+    const double z0n = shfl_next(z0), z1n = shfl_next(z1);
+    if (own) {
+      double e = 0.0;
+      if (cond) {
+        const double ex = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(T.x0, Tn.x0), T.x1), Tn.x1), c);
+        const double ey = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(T.y, Tn.y), y0n), y1n), c);
+        const double ez = __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(z0, z1), z0n), z1n), c);
+        e = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+      }
+      E[v] = e;
+    }
+    T = Tn;
+    have = true;
   }
 }
 
@@ -1010,8 +1029,11 @@ void launch_efield(const unsigned char *mask, const double *a,
                    const double *psi, int nx, int ny, int nz, double h,
                    double omega, double *E, cudaStream_t st) {
   if ((size_t)nx * ny * nz == 0) return;
-  const dim3 grid((nx + 127) / 128, ny, nz < 65535 ? nz : 65535);
-  k_efield<<<grid, 128, 0, st>>>(mask, a, psi, nx, ny, nz, omega / (4.0 * h), E);
+  const long long ncol = (long long)(nx + 1) * ny;
+  const long long warps = (ncol + 30) / 31;
+  const dim3 grid((unsigned)((warps * 32 + EF_THREADS - 1) / EF_THREADS),
+                  (unsigned)((nz + EF_KCHUNK - 1) / EF_KCHUNK));
+  k_efield<<<grid, EF_THREADS, 0, st>>>(mask, a, psi, nx, ny, nz, omega / (4.0 * h), E);
 }
 
 static int grid_for(size_t n) {

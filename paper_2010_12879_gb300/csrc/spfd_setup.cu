@@ -429,18 +429,37 @@ constexpr int GJ_B = 16;   // pivots per launch
 constexpr int GJ_T = 32;   // tile edge
 constexpr int GJ_NT = 256; // threads per block (GJ_B * GJ_B)
 
-__global__ void __launch_bounds__(GJ_NT)
-k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, int r,
-           int *status) {
-  __shared__ double D[2][GJ_B][GJ_B + 1];
-  __shared__ double W[GJ_B][GJ_T];
-  __shared__ double U[GJ_T][GJ_B + 1];
-  __shared__ double C[GJ_B][GJ_T];
-  __shared__ double pinv[2];
+struct GjShared {
+  double D[2][GJ_B][GJ_B + 1];
+  double W[GJ_B][GJ_T];
+  double U[GJ_T][GJ_B + 1];
+  double C[GJ_B][GJ_T];
+  double pinv[2];
+};
+
+// One sweep of the pivot set k0 .. k0+r-1 by this block's tile.  COH: read
+// A through L2 only (ld.global.cg), as the single-launch form must: A was
+// written by other blocks in the same launch, and a line of it cached in
+// this SM's L1 by an earlier sweep would be stale.
+template <bool COH>
+__device__ __forceinline__ double gj_ld(const double *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
+template <bool COH>
+__device__ __forceinline__ void gj_sweep(GjShared &sh, const double *__restrict__ A,
+                                         double *__restrict__ B, int m, int k0, int r,
+                                         int *status) {
+  auto &D = sh.D;
+  auto &W = sh.W;
+  auto &U = sh.U;
+  auto &C = sh.C;
+  auto &pinv = sh.pinv;
   const int t = threadIdx.x;
   const int i0 = blockIdx.y * GJ_T, j0 = blockIdx.x * GJ_T;
   const int a = t / GJ_B, b = t % GJ_B;
-  const double d0 = (a < r && b < r) ? A[(size_t)(k0 + a) * m + k0 + b] : (a == b ? 1.0 : 0.0);
+  const double d0 = (a < r && b < r) ? gj_ld<COH>(&A[(size_t)(k0 + a) * m + k0 + b]) : (a == b ? 1.0 : 0.0);
   D[0][a][b] = d0;
   if (t == 0) {
     if (!(d0 > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
@@ -448,9 +467,9 @@ k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, 
   }
   for (int q = t; q < GJ_T * GJ_B; q += GJ_NT) {
     const int ii = q / GJ_B, l = q % GJ_B;
-    U[ii][l] = (l < r && i0 + ii < m) ? A[(size_t)(i0 + ii) * m + k0 + l] : 0.0;
+    U[ii][l] = (l < r && i0 + ii < m) ? gj_ld<COH>(&A[(size_t)(i0 + ii) * m + k0 + l]) : 0.0;
     const int l2 = q / GJ_T, jj = q % GJ_T;
-    C[l2][jj] = (l2 < r && j0 + jj < m) ? A[(size_t)(k0 + l2) * m + j0 + jj] : 0.0;
+    C[l2][jj] = (l2 < r && j0 + jj < m) ? gj_ld<COH>(&A[(size_t)(k0 + l2) * m + j0 + jj]) : 0.0;
   }
   __syncthreads();
   // D <- D^-1, one pivot per step, ping-pong between D[0] and D[1]: the
@@ -498,7 +517,7 @@ k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int i = i0 + ii0 + RS * k;
-      v[k] = (!kj && i < m && j < m) ? A[(size_t)i * m + j] : 0.0;
+      v[k] = (!kj && i < m && j < m) ? gj_ld<COH>(&A[(size_t)i * m + j]) : 0.0;
     }
 #pragma unroll
     for (int l = 0; l < GJ_B; ++l) {
@@ -518,12 +537,92 @@ k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, 
   }
 }
 
+__global__ void __launch_bounds__(GJ_NT)
+k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, int r,
+           int *status) {
+  __shared__ GjShared sh;
+  gj_sweep<false>(sh, A, B, m, k0, r, status);
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident): arrive
+// on a counter, the last block to arrive resets it and advances the
+// generation, the others wait for the generation to change.  The wait is
+// bounded: after GJ_SPIN_LIMIT polls it sets DEV_GRID_WAIT and goes on (the
+// build then fails with an error instead of hanging).
+constexpr long long GJ_SPIN_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks,
+                                             int *status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = atomicAdd(gen, 0u);
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long spins = 0;
+      while (atomicAdd(gen, 0u) == g) {
+        if (++spins > GJ_SPIN_LIMIT) {
+          atomicOr(status, DEV_GRID_WAIT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Every sweep of the blocked Gauss-Jordan inversion in one cooperative
+// launch: the same tiles and arithmetic as the per-sweep launches, with a
+// grid barrier between sweeps (sweep k reads what sweep k-1 wrote).
+// bar[0..1]: barrier counter and generation, zero at launch.
+__global__ void __launch_bounds__(GJ_NT)
+k_gj_all(double *buf0, double *buf1, int m, int *status, unsigned *bar) {
+  __shared__ GjShared sh;
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  double *a = buf0, *b = buf1;
+  for (int k0 = 0; k0 < m; k0 += GJ_B) {
+    gj_sweep<true>(sh, a, b, m, k0, m - k0 < GJ_B ? m - k0 : GJ_B, status);
+    grid_barrier(&bar[0], &bar[1], nblocks, status);
+    double *tmp = a; a = b; b = tmp;
+  }
+}
+
+// Kernel launches of launch_dense_inverse for an m x m matrix: one when its
+// tile grid fits on the device at once (a cooperative launch), else one per
+// pivot set.
+int dense_inverse_launches(int m) {
+  const int nt = (m + GJ_T - 1) / GJ_T;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_all, GJ_NT, 0) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return (m + GJ_B - 1) / GJ_B;
+  }
+  return (coop && (long long)nt * nt <= (long long)per_sm * nsm) ? 1 : (m + GJ_B - 1) / GJ_B;
+}
+
 // Inverts the SPD matrix in buf0 (m x m); returns the buffer holding A^-1
-// (buf0 or buf1, which serve as ping-pong buffers).
-double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
+// (buf0 or buf1, which serve as ping-pong buffers).  bar: two zeroed
+// unsigned ints of device scratch for the cooperative form.
+double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status, unsigned *bar,
                              cudaStream_t st) {
   double *a = buf0, *b = buf1;
   const int nt = (m + GJ_T - 1) / GJ_T;
+  if (dense_inverse_launches(m) == 1) {
+    void *args[] = {&buf0, &buf1, &m, &status, &bar};
+    if (cudaLaunchCooperativeKernel((const void *)k_gj_all, dim3(nt, nt), dim3(GJ_NT), args, 0,
+                                    st) == cudaSuccess)
+      return ((m + GJ_B - 1) / GJ_B) % 2 ? buf1 : buf0;
+    cudaGetLastError();  // not launched: sweep launch by launch instead
+  }
   for (int k0 = 0; k0 < m; k0 += GJ_B) {
     k_gj_block<<<dim3(nt, nt), GJ_NT, 0, st>>>(a, b, m, k0, m - k0 < GJ_B ? m - k0 : GJ_B,
                                               status);
