@@ -365,9 +365,9 @@ static spfd_status setup_mixed_level(spfd_ctx *c, int l) {
   TRY(dalloc(c, &lv.wdinv32, S));
   SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.wdinv, 1.0, lv.wdinv32, st));
   if (lv.Pc) {
-    TRY(dalloc(c, &lv.Pc16, 27 * (S / 8)));
+    TRY(dalloc(c, &lv.Pc32, 27 * (S / 8)));
     SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
-                launch_convert<__half>(27 * (S / 8), lv.Pc, 1.0, lv.Pc16, st));
+                launch_convert<float>(27 * (S / 8), lv.Pc, 1.0, lv.Pc32, st));
   }
   if (l == 0) {
     TRY(dalloc(c, &lv.gx32, 3 * S));
@@ -378,12 +378,10 @@ static spfd_status setup_mixed_level(spfd_ctx *c, int l) {
                 launch_convert<__nv_bfloat16>(3 * S, lv.gx, 1.0, lv.gxbf, st));
     SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
   } else {
-    // the symmetric half of the stencil: entries 13..26 (coef27)
-    TRY(dalloc(c, &lv.st32, 14 * S));
-    TRY(dalloc(c, &lv.P16, 27 * S));
-    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
-                launch_convert<float>(14 * S, lv.st + 13 * S, 1.0, lv.st32, st));
-    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<__half>(27 * S, lv.P, 1.0, lv.P16, st));
+    TRY(dalloc(c, &lv.st32, 27 * S));
+    TRY(dalloc(c, &lv.P32, 27 * S));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
+    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
   }
   return launch_check("mixed-precision copies");
 }

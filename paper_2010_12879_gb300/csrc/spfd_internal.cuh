@@ -144,6 +144,7 @@ enum : int {
   DEV_BAD_A = 2,         // non-finite edge potential on a conducting edge
   DEV_UF_CAP = 4,        // union-find loop hit its iteration cap
   DEV_BAD_PIVOT = 8,     // coarsest dense inverse met a non-positive pivot
+  DEV_GRID_WAIT = 16,    // a grid-wide barrier hit its wait cap
 };
 
 // ---------------------------------------------------------------- launchers
@@ -194,8 +195,9 @@ void launch_coarse_diag(const Grid &gc, const double *stc, const unsigned long l
                         double rel, double *diag, double *dinv, cudaStream_t st);
 // Inverse of the SPD matrix in buf0 (m x m, row-major) by blocked
 // Gauss-Jordan sweeps; returns buf0 or buf1, whichever holds the result.
-double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status,
+double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status, unsigned *bar,
                              cudaStream_t st);
+int dense_inverse_launches(int m);
 
 // V-cycle pieces (spfd_cycle.cu); T = vector type, C = 7-point coefficient type.
 // nk right-hand sides per launch (blockIdx.y): the vectors of a level with S

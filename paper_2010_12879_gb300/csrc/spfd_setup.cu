@@ -10,33 +10,64 @@
 namespace spfd {
 
 // ------------------------------------------------------------ sigma -> bricks
-__global__ void k_sigma_flags(const double *__restrict__ sigma, int nx, int ny,
-                              int nz, int MX, int MY,
-                              unsigned char *__restrict__ flags,
-                              unsigned char *__restrict__ mask, int *status) {
-  const long long n = (long long)nx * ny * nz;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+// One warp per voxel row (j, k): the row's conductivities are read as
+// 16-byte pairs and classified by their bit patterns with integer operations
+// (on this GPU an FP64 comparison costs a slot of the narrow FP64 pipe):
+// conducting iff the value is > 0 (sign clear, not zero, exponent not all
+// ones); invalid iff NaN or infinite (exponent all ones) or negative and not
+// -0.  mask gets 1 per conducting voxel, and the bricks of its 8 corner
+// nodes are flagged.
+__device__ __forceinline__ void flag_voxel(unsigned long long u, int i, int j, int k, int MX,
+                                           int MY, unsigned char *__restrict__ flags,
+                                           unsigned char &m, int &bad) {
+  const unsigned ex = (unsigned)(u >> 52) & 0x7ffu;
+  const bool neg = (u >> 63) != 0;
+  if (ex == 0x7ffu || (neg && (u << 1) != 0)) bad = 1;
+  m = (!neg && u != 0 && ex != 0x7ffu) ? 1 : 0;
+  if (m) {
+    const int i0 = i >> 3, i1 = (i + 1) >> 3, j0 = j >> 3, j1 = (j + 1) >> 3;
+    const int k0 = k >> 3, k1 = (k + 1) >> 3;
+    flags[(k0 * MY + j0) * MX + i0] = 1;
+    if (i1 != i0) flags[(k0 * MY + j0) * MX + i1] = 1;
+    if (j1 != j0) flags[(k0 * MY + j1) * MX + i0] = 1;
+    if (k1 != k0) flags[(k1 * MY + j0) * MX + i0] = 1;
+    if (i1 != i0 && j1 != j0) flags[(k0 * MY + j1) * MX + i1] = 1;
+    if (i1 != i0 && k1 != k0) flags[(k1 * MY + j0) * MX + i1] = 1;
+    if (j1 != j0 && k1 != k0) flags[(k1 * MY + j1) * MX + i0] = 1;
+    if (i1 != i0 && j1 != j0 && k1 != k0) flags[(k1 * MY + j1) * MX + i1] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_sigma_flags(const double *__restrict__ sigma, int nx, int ny, int nz, int MX, int MY,
+              bool pairs, unsigned char *__restrict__ flags, unsigned char *__restrict__ mask,
+              int *status) {
+  const int lane = threadIdx.x & 31;
+  const long long nrows = (long long)ny * nz;
   int bad = 0;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-       v += stride) {
-    double s = sigma[v];
-    mask[v] = s > 0.0;
-    if (!(s >= 0.0) || !isfinite(s)) { bad = 1; continue; }
-    if (s > 0.0) {
-      int i = (int)(v % nx);
-      int j = (int)((v / nx) % ny);
-      int k = (int)(v / ((long long)nx * ny));
-      // the voxel's 8 corner nodes are unknowns; mark their bricks
-      int i0 = i >> 3, i1 = (i + 1) >> 3, j0 = j >> 3, j1 = (j + 1) >> 3;
-      int k0 = k >> 3, k1 = (k + 1) >> 3;
-      flags[(k0 * MY + j0) * MX + i0] = 1;
-      if (i1 != i0) flags[(k0 * MY + j0) * MX + i1] = 1;
-      if (j1 != j0) flags[(k0 * MY + j1) * MX + i0] = 1;
-      if (k1 != k0) flags[(k1 * MY + j0) * MX + i0] = 1;
-      if (i1 != i0 && j1 != j0) flags[(k0 * MY + j1) * MX + i1] = 1;
-      if (i1 != i0 && k1 != k0) flags[(k1 * MY + j0) * MX + i1] = 1;
-      if (j1 != j0 && k1 != k0) flags[(k1 * MY + j1) * MX + i0] = 1;
-      if (i1 != i0 && j1 != j0 && k1 != k0) flags[(k1 * MY + j1) * MX + i1] = 1;
+  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows;
+       r += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const double *row = sigma + (size_t)r * nx;
+    unsigned char *mrow = mask + (size_t)r * nx;
+    // pairs when every row starts on a 16-byte boundary (nx even and sigma
+    // 16-byte aligned), else one value at a time
+    if (pairs) {
+      for (int i = 2 * lane; i < nx; i += 64) {
+        const double2 p = *reinterpret_cast<const double2 *>(row + i);
+        unsigned char m0, m1;
+        flag_voxel((unsigned long long)__double_as_longlong(p.x), i, j, k, MX, MY, flags, m0, bad);
+        flag_voxel((unsigned long long)__double_as_longlong(p.y), i + 1, j, k, MX, MY, flags, m1,
+                   bad);
+        *reinterpret_cast<uchar2 *>(mrow + i) = make_uchar2(m0, m1);
+      }
+    } else {
+      for (int i = lane; i < nx; i += 32) {
+        unsigned char m0;
+        flag_voxel((unsigned long long)__double_as_longlong(row[i]), i, j, k, MX, MY, flags, m0,
+                   bad);
+        mrow[i] = m0;
+      }
     }
   }
   if (bad) atomicOr(status, DEV_BAD_SIGMA);
@@ -45,12 +76,13 @@ __global__ void k_sigma_flags(const double *__restrict__ sigma, int nx, int ny,
 void launch_sigma_flags(const double *sigma, int nx, int ny, int nz, int MX,
                         int MY, unsigned char *flags, unsigned char *mask,
                         int *status, cudaStream_t st) {
-  long long n = (long long)nx * ny * nz;
-  long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  const long long rows = (long long)ny * nz;
+  long long blocks = (rows + 7) / 8;  // 8 warps (rows) per block
+  if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  k_sigma_flags<<<(int)blocks, 256, 0, st>>>(sigma, nx, ny, nz, MX, MY, flags,
-                                              mask, status);
+  const bool pairs = (nx & 1) == 0 && ((uintptr_t)sigma & 15) == 0;
+  k_sigma_flags<<<(int)blocks, 256, 0, st>>>(sigma, nx, ny, nz, MX, MY, pairs, flags, mask,
+                                              status);
 }
 
 // ------------------------------------------------- conductances (Eq. 3, M_k)

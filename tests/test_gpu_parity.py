@@ -306,6 +306,27 @@ def test_host_pipeline_entry_point(torch_cuda, spfd, oracle_mod, pinned):
         _compare(oracle_mod, ph, a, psi_p, E_p)
 
 
+def test_sigma_at_an_8_byte_offset(torch_cuda, spfd):
+    """A conductivity array that starts 8 bytes past a 16-byte boundary (a
+    view into a larger tensor) gives the same operator, unknowns and Psi
+    as an aligned copy: the classification falls back from paired loads."""
+    torch = torch_cuda
+    ph = body_phantom(32, 20, 112, h=16e-3)
+    a = _dev(torch, loop_potential(ph.dims, ph.h, ph.origin))
+    buf = torch.zeros(ph.sigma.size + 1, dtype=torch.float64, device="cuda")
+    buf[1:] = torch.from_numpy(ph.sigma.reshape(-1)).cuda()
+    sig_off = buf[1:].view(ph.sigma.shape)
+    assert sig_off.data_ptr() % 16 == 8
+    out = []
+    for sig in (_dev(torch, ph.sigma), sig_off):
+        with spfd.Solver(sig, ph.h) as S:
+            psi, info, st = S.solve(a, 1e-10)
+            assert st == spfd.SPFD_OK
+            out.append((psi.clone(), info["n_dof"], info["iters"]))
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert torch.equal(out[0][0], out[1][0])
+
+
 def test_cached_blocks_are_reused(torch_cuda, spfd):
     """A second build of the same model takes its device buffers from the
     library's cache: no net device memory is taken from the driver, and
