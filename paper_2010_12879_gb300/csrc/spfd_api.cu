@@ -277,7 +277,7 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
                                                            nk, block_order(c, TF_SMOOTH, l))));
     else
       SPFD_LAUNCH(c, l == 1 ? "jacobi27_l1" : "jacobi27_coarse", f32, 1,
-                  (f32 ? 18 : 32) * w * S, 57 * S,
+                  32 * w * S, 57 * S,
                   launch_jacobi27<T>(lv.g, lv.ST<T>(), wd, in, bl, out, st, nk,
                                      block_order(c, TF_SMOOTH, l)));
   };
@@ -289,19 +289,18 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
                                                            nk, block_order(c, TF_RESID, l))));
   else
     SPFD_LAUNCH(c, l == 1 ? "residual27_l1" : "residual27_coarse", f32, 1,
-                (f32 ? 17 : 30) * w * S, 55 * S,
+                30 * w * S, 55 * S,
                 launch_residual27<T>(lv.g, lv.ST<T>(), cur, bl, lv.R<T>(), st, nk,
                                      block_order(c, TF_RESID, l)));
   Level &cl = c->L[l + 1];
   const double Sc = (double)cl.S * nk;
-  const double wp = sizeof(Wt<T>);  // bytes per interpolation weight
   SPFD_LAUNCH(c, l == 0 ? "restrict_l0" : (l == 1 ? "restrict_l1" : "restrict_coarse"), f32, 1,
-              (27 * wp + w) * Sc + w * S, 54 * Sc,
+              28 * w * Sc + w * S, 54 * Sc,
               launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st, nk,
                                  block_order(c, TF_RESTRICT, l)));
   T *ec = vcycle<T>(c, l + 1, cl.B<T>(), false, nk);
   SPFD_LAUNCH(c, l == 0 ? "prolong_l0" : (l == 1 ? "prolong_l1" : "prolong_coarse"), f32, 1,
-              (27.0 / 8.0 * wp + 2.0 * w) * S + w * Sc, 7 * S,
+              (27.0 / 8.0 + 2.0) * w * S + w * Sc, 7 * S,
               launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st, nk,
                                 block_order(c, TF_PROLONG, l)));
   for (int s = 0; s < c->opts.nu_post; ++s) {
