@@ -71,9 +71,8 @@ enum { SPFD_SMOOTHER_JACOBI = 0, SPFD_SMOOTHER_CHEBYSHEV = 1 };
  *   SPFD_FP64:  every operation (operator, V-cycle, Krylov) in FP64.
  *   SPFD_MIXED: FP64 iterative refinement around an FP32 preconditioned CG
  *               whose V-cycle keeps the finest-level conductances in BF16
- *               and the interpolation weights in FP16 and accumulates in
- *               FP32; residuals, CG dot products and the coarsest-level
- *               solve stay FP64. */
+ *               and accumulates in FP32; residuals, CG dot products and the
+ *               coarsest-level solve stay FP64. */
 enum { SPFD_FP64 = 0, SPFD_MIXED = 1 };
 
 typedef struct {
