@@ -232,6 +232,15 @@ spfd_status project(spfd_ctx *c, T *v, int nk, int j0) {
   return launch_check("projection");
 }
 
+// Kernel-family name of a V-cycle kernel on level l: levels 0-4 by number
+// (level 0 is HBM-sized, levels >= 2 of the 2 mm body are L2-resident and
+// latency-bound), deeper levels together.
+static const char *lvl_name(const char *const (&names)[6], int l) {
+  return names[l < 5 ? l : 5];
+}
+#define LVL_NAMES(base)                                                          \
+  {base "_l0", base "_l1", base "_l2", base "_l3", base "_l4", base "_deep"}
+
 // V-cycle on level l for the right-hand sides bl (nk of them, S_l apart);
 // returns the buffer holding the corrections.  With proj (level 0) bl is
 // first projected onto the range of A in place (its per-component mean
@@ -266,7 +275,7 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
                 launch_jacobi_first_proj<T>(lv.g, wd, bl, cur, c->sc, inv, st, nk,
                                             block_order(c, TF_JFIRST, l)));
   else
-    SPFD_LAUNCH(c, l == 0 ? "jacobi_first_l0" : (l == 1 ? "jacobi_first_l1" : "jacobi_first_coarse"), f32, 1,
+    SPFD_LAUNCH(c, lvl_name(LVL_NAMES("jacobi_first"), l), f32, 1,
                 3 * w * S, S,
                 launch_jacobi_first<T>(lv.g, wd, bl, cur, st, nk, block_order(c, TF_JFIRST, l)));
   auto sweep = [&](T *in, T *out) {
@@ -276,7 +285,7 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
                                                            lv.DIAG<T>(), wd, in, bl, out, st,
                                                            nk, block_order(c, TF_SMOOTH, l))));
     else
-      SPFD_LAUNCH(c, l == 1 ? "jacobi27_l1" : "jacobi27_coarse", f32, 1,
+      SPFD_LAUNCH(c, lvl_name(LVL_NAMES("jacobi27"), l), f32, 1,
                   32 * w * S, 57 * S,
                   launch_jacobi27<T>(lv.g, lv.ST<T>(), wd, in, bl, out, st, nk,
                                      block_order(c, TF_SMOOTH, l)));
@@ -288,18 +297,18 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
                                                            lv.DIAG<T>(), cur, bl, lv.R<T>(), st,
                                                            nk, block_order(c, TF_RESID, l))));
   else
-    SPFD_LAUNCH(c, l == 1 ? "residual27_l1" : "residual27_coarse", f32, 1,
+    SPFD_LAUNCH(c, lvl_name(LVL_NAMES("residual27"), l), f32, 1,
                 30 * w * S, 55 * S,
                 launch_residual27<T>(lv.g, lv.ST<T>(), cur, bl, lv.R<T>(), st, nk,
                                      block_order(c, TF_RESID, l)));
   Level &cl = c->L[l + 1];
   const double Sc = (double)cl.S * nk;
-  SPFD_LAUNCH(c, l == 0 ? "restrict_l0" : (l == 1 ? "restrict_l1" : "restrict_coarse"), f32, 1,
+  SPFD_LAUNCH(c, lvl_name(LVL_NAMES("restrict"), l), f32, 1,
               28 * w * Sc + w * S, 54 * Sc,
               launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st, nk,
                                  block_order(c, TF_RESTRICT, l)));
   T *ec = vcycle<T>(c, l + 1, cl.B<T>(), false, nk);
-  SPFD_LAUNCH(c, l == 0 ? "prolong_l0" : (l == 1 ? "prolong_l1" : "prolong_coarse"), f32, 1,
+  SPFD_LAUNCH(c, lvl_name(LVL_NAMES("prolong"), l), f32, 1,
               (27.0 / 8.0 + 2.0) * w * S + w * Sc, 7 * S,
               launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st, nk,
                                 block_order(c, TF_PROLONG, l)));

@@ -670,6 +670,18 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   dfree(c, c->L.back().Pc);
   clk.mark("coarse levels");
 
+  // activity bits of the 27-point levels, from their interpolation columns
+  // (a superset of their nonzero rows)
+  for (size_t l = 1; l < c->L.size(); ++l) {
+    Level &lv = c->L[l];
+    unsigned *bits = nullptr;
+    TRY(dalloc(c, &bits, (size_t)std::max(lv.g.nb, 1) * 16));
+    SPFD_LAUNCH(c, "setup_pack", false, 1, 216.0 * lv.S, 0,
+                launch_act_bits(lv.g.nb, lv.P, 27, bits, st));
+    lv.g.act = bits;
+  }
+  TRY(launch_check("activity bits"));
+
   // smoother weights (weighted Jacobi): level 0 has D^-1 A the random-walk
   // Laplacian of a bipartite node graph, so lambda_max = 2 exactly and
   // omega = 2/3; coarser levels estimate it on the device by power

@@ -75,6 +75,23 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
   }
 }
 
+// r = b - A x on brick bk of a 27-point level: one node per thread, every
+// thread of the NT-thread block calls it; tl and sn are the caller's shared
+// tile and neighbour table.  A zero row (clear activity bit) contributes
+// exactly +0: its 27 coefficients are not read.
+template <typename T, bool COH>
+__device__ __forceinline__ void residual27_unit(const Grid &g, const T *__restrict__ st,
+                                                const T *x, const T *b, T *r, int bk,
+                                                T (*tl)[10][10], int *sn) {
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + threadIdx.x;
+  load_nbr(g, bk, sn);
+  const bool on = (act_word(g, bk) >> (threadIdx.x & 31)) & 1u;
+  __syncthreads();
+  tile_full<T, COH>(tl, x, bk, sn);
+  __syncthreads();
+  r[s] = ldv<COH>(b + s) - (on ? apply27_tile<T>(tl, st, S, s) : T(0));
+}
+
 template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
@@ -84,19 +101,19 @@ k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
   const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + threadIdx.x;
-  load_nbr(g, bk, sn);
   if constexpr (rhs_tile<ORD>() == 1) {
     const size_t off = (size_t)rhs * S;
-    x += off; b += off; r += off;
-    __syncthreads();
-    tile_full<T>(tl[0], x, bk, sn);
-    __syncthreads();
-    r[s] = b[s] - apply27_tile<T>(tl[0], st, S, s);
+    residual27_unit<T, false>(g, st, x + off, b + off, r + off, bk, tl[0], sn);
   } else {
+    load_nbr(g, bk, sn);
+    const bool on = (act_word(g, bk) >> (threadIdx.x & 31)) & 1u;
     // the tile's right-hand sides side by side: all their halo tiles are
     // loaded at once, then each uses the coefficients held in registers
     T cf[27];
-    load27(st, S, s, cf);
+    if (on) load27(st, S, s, cf);
+    else
+#pragma unroll
+      for (int e = 0; e < 27; ++e) cf[e] = T(0);
     const int nr = min(rhs_tile<ORD>(), nk - rhs);
     __syncthreads();
     for (int k = 0; k < nr; ++k) tile_full<T>(tl[k], x + (size_t)(rhs + k) * S, bk, sn);
@@ -106,6 +123,24 @@ k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
       r[off + s] = b[off + s] - apply27_regs<T>(tl[k], cf);
     }
   }
+}
+
+// One weighted-Jacobi sweep xout = xin + omega D^-1 (b - A xin) on brick bk
+// of a 27-point level (as residual27_unit).
+template <typename T, bool COH>
+__device__ __forceinline__ void jacobi27_unit(const Grid &g, const T *__restrict__ st,
+                                              const T *__restrict__ wdinv, const T *xin,
+                                              const T *b, T *xout, int bk, T (*tl)[10][10],
+                                              int *sn) {
+  const int t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  load_nbr(g, bk, sn);
+  const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
+  __syncthreads();
+  tile_full<T, COH>(tl, xin, bk, sn);
+  __syncthreads();
+  const T r = ldv<COH>(b + s) - (on ? apply27_tile<T>(tl, st, S, s) : T(0));
+  xout[s] = tl[(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wdinv[s] * r;
 }
 
 template <typename T, int ORD>
@@ -119,18 +154,17 @@ k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
-  load_nbr(g, bk, sn);
   if constexpr (rhs_tile<ORD>() == 1) {
     const size_t off = (size_t)rhs * S;
-    xin += off; b += off; xout += off;
-    __syncthreads();
-    tile_full<T>(tl[0], xin, bk, sn);
-    __syncthreads();
-    const T r = b[s] - apply27_tile<T>(tl[0], st, S, s);
-    xout[s] = tl[0][(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wdinv[s] * r;
+    jacobi27_unit<T, false>(g, st, wdinv, xin + off, b + off, xout + off, bk, tl[0], sn);
   } else {
+    load_nbr(g, bk, sn);
+    const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
     T cf[27];
-    load27(st, S, s, cf);
+    if (on) load27(st, S, s, cf);
+    else
+#pragma unroll
+      for (int e = 0; e < 27; ++e) cf[e] = T(0);
     const T wd = wdinv[s];
     const int nr = min(rhs_tile<ORD>(), nk - rhs);
     __syncthreads();
@@ -196,6 +230,45 @@ k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
 // Restriction r_c(I) = sum_d P[d][I] r_f(2I + d) (P^T, the adjoint of the
 // prolongation below).  A coarse brick B reads the 17^3 fine nodes
 // 16B-1 .. 16B+15 (per axis) from the 27 fine bricks 2B-1 .. 2B+1.
+// The 17^3 fine nodes of brick bk's children into fs (sk: the child table).
+template <typename T, bool COH>
+__device__ __forceinline__ void restrict_fill(T (*fs)[17][17], const T *src, const int *sk) {
+  for (int q = threadIdx.x; q < 17 * 17 * 17; q += NT) {
+    const int fz = q / 289, fy = (q / 17) % 17, fx = q % 17;
+    const int nb = sk[((fz + 7) >> 3) * 9 + ((fy + 7) >> 3) * 3 + ((fx + 7) >> 3)];
+    fs[fz][fy][fx] = nb >= 0
+        ? ldv<COH>(&src[(size_t)nb * BV + (((fz - 1) & 7) * 8 + ((fy - 1) & 7)) * 8 +
+                        ((fx - 1) & 7)])
+        : T(0);
+  }
+}
+
+// One coarse brick bk, one coarse node per thread (NT threads call it).  A
+// coarse node whose interpolation column is zero (clear activity bit)
+// restricts to exactly +0: its 27 weights are not read.
+template <typename T, bool COH>
+__device__ __forceinline__ void restrict_unit(const Grid &gc, size_t Sf, const T *__restrict__ P,
+                                              const T *rf, T *bcoarse, int bk,
+                                              T (*fs)[17][17], int *sk) {
+  const int t = threadIdx.x;
+  const size_t Sc = (size_t)gc.nb * BV, s = (size_t)bk * BV + t;
+  const int cx = 2 * (t & 7) + 1, cy = 2 * ((t >> 3) & 7) + 1, cz = 2 * (t >> 6) + 1;
+  if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
+  const bool on = (act_word(gc, bk) >> (t & 31)) & 1u;
+  __syncthreads();
+  restrict_fill<T, COH>(fs, rf, sk);
+  __syncthreads();
+  T acc = 0;
+  if (on) {
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      acc += P[(size_t)d * Sc + s] * fs[cz + dz][cy + dy][cx + dx];
+    }
+  }
+  bcoarse[s] = acc;
+}
+
 template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf,
@@ -206,38 +279,22 @@ k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
   const size_t Sc = (size_t)gc.nb * BV, s = (size_t)bk * BV + t;
-  const int cx = 2 * (t & 7) + 1, cy = 2 * ((t >> 3) & 7) + 1, cz = 2 * (t >> 6) + 1;
-  if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
-  // the 17^3 fine nodes of right-hand side j into fs
-  auto fill = [&](const T *__restrict__ src) {
-    for (int q = t; q < 17 * 17 * 17; q += NT) {
-      const int fz = q / 289, fy = (q / 17) % 17, fx = q % 17;
-      const int nb = sk[((fz + 7) >> 3) * 9 + ((fy + 7) >> 3) * 3 + ((fx + 7) >> 3)];
-      fs[fz][fy][fx] = nb >= 0
-          ? src[(size_t)nb * BV + (((fz - 1) & 7) * 8 + ((fy - 1) & 7)) * 8 + ((fx - 1) & 7)]
-          : T(0);
-    }
-  };
   if constexpr (rhs_tile<ORD>() == 1) {
-    rf += (size_t)rhs * Sf;
-    bcoarse += (size_t)rhs * Sc;
-    __syncthreads();
-    fill(rf);
-    __syncthreads();
-    T acc = 0;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-      acc += P[(size_t)d * Sc + s] * fs[cz + dz][cy + dy][cx + dx];
-    }
-    bcoarse[s] = acc;
+    restrict_unit<T, false>(gc, Sf, P, rf + (size_t)rhs * Sf, bcoarse + (size_t)rhs * Sc, bk,
+                            fs, sk);
   } else {
+    const int cx = 2 * (t & 7) + 1, cy = 2 * ((t >> 3) & 7) + 1, cz = 2 * (t >> 6) + 1;
+    if (t < 27) sk[t] = gc.kid[(size_t)bk * 27 + t];
+    const bool on = (act_word(gc, bk) >> (t & 31)) & 1u;
     T w[27];
-    load27(P, Sc, s, w);
+    if (on) load27(P, Sc, s, w);
+    else
+#pragma unroll
+      for (int e = 0; e < 27; ++e) w[e] = T(0);
     const int nr = min(rhs_tile<ORD>(), nk - rhs);
     for (int k = 0; k < nr; ++k) {
       __syncthreads();  // sk is loaded / the previous tile is consumed
-      fill(rf + (size_t)(rhs + k) * Sf);
+      restrict_fill<T, false>(fs, rf + (size_t)(rhs + k) * Sf, sk);
       __syncthreads();
       T acc = 0;
 #pragma unroll
@@ -252,63 +309,74 @@ k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf
 
 // Prolongation + correction e_f(n) += sum over the <= 8 parents I of n of
 // P(n, I) e_c(I).  One thread per 2x2x2 cell of a fine brick (two bricks per
-// 128-thread block): it loads the cell's 27 weights (row j of Pc at column
+// 128 threads): it loads the cell's 27 weights (row j of Pc at column
 // brick*64 + cell, coalesced across the warp), the 8 coarse corner values
 // c + o (o in {0,1}^3; coarse bricks from the brick's parent table) and its
 // 8 fine values as 2-vectors along x, then writes the 8 corrected values.
 // No shared memory and no barrier: every load is independent.
-template <typename T, int ORD>
-__global__ void __launch_bounds__(128)
-k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
-          T *__restrict__ ef, int nk) {
-  int pair, rhs;
-  unit_rhs<ORD>(nk, pair, rhs);
-  const int bk = pair * 2 + (threadIdx.x >> 6);
+// Pair `pair` of fine bricks, thread `tid` (0..127) of the pair's group;
+// nr right-hand sides from rhs on (S apart on each level).
+template <typename T, bool COH>
+__device__ __forceinline__ void prolong_unit(const Grid &gf, const Grid &gc,
+                                             const T *__restrict__ Pc, const T *ec, T *ef,
+                                             int pair, int tid, int rhs, int nr) {
+  const int bk = pair * 2 + (tid >> 6);
   if (bk >= gf.nb) return;
-  const int cell = threadIdx.x & 63;
+  const int cell = tid & 63;
   const int ccx = cell & 3, ccy = (cell >> 2) & 3, ccz = cell >> 4;
   const size_t NC = (size_t)gf.nb * 64, cid = (size_t)bk * 64 + cell;
   T w[27];
 #pragma unroll
   for (int j = 0; j < 27; ++j) w[j] = Pc[(size_t)j * NC + cid];
   const int4 bc = gf.bco[bk];
+  for (int k = 0; k < nr; ++k) {
+    const T *ecj = ec + (size_t)(rhs + k) * gc.nb * BV;
+    T *efj = ef + (size_t)(rhs + k) * gf.nb * BV;
+    T e[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int gx_ = 4 * bc.x + ccx + (o & 1), gy_ = 4 * bc.y + ccy + ((o >> 1) & 1),
+                gz_ = 4 * bc.z + ccz + (o >> 2);
+      const int pb = (((gz_ >> 3) - (bc.z >> 1)) << 2) | (((gy_ >> 3) - (bc.y >> 1)) << 1) |
+                     ((gx_ >> 3) - (bc.x >> 1));
+      const int nb = __ldg(&gf.par[(size_t)bk * 8 + pb]);
+      e[o] = nb >= 0 ? ldv<COH>(&ecj[(size_t)nb * BV + ((gz_ & 7) * 8 + (gy_ & 7)) * 8 +
+                                     (gx_ & 7)])
+                     : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {  // r = uz*2 + uy: one 2-vector (ux = 0, 1) per row
+      const int uy = r & 1, uz = r >> 1;
+      T *row = efj + (size_t)bk * BV + ((2 * ccz + uz) * 8 + 2 * ccy + uy) * 8 + 2 * ccx;
+      T v[2];
+      if constexpr (sizeof(T) == 4) {
+        const float2 u = ldv<COH>(reinterpret_cast<const float2 *>(row));
+        v[0] = u.x; v[1] = u.y;
+      } else {
+        const double2 u = ldv<COH>(reinterpret_cast<const double2 *>(row));
+        v[0] = u.x; v[1] = u.y;
+      }
+#pragma unroll
+      for (int ux = 0; ux < 2; ++ux) {
+        const int q = uz * 4 + uy * 2 + ux;
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+          if ((o & ~q) == 0) v[ux] += w[pc_off(q) + crank(q, o)] * e[o];
+      }
+      if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(row) = make_float2(v[0], v[1]);
+      else *reinterpret_cast<double2 *>(row) = make_double2(v[0], v[1]);
+    }
+  }
+}
+
+template <typename T, int ORD>
+__global__ void __launch_bounds__(128)
+k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
+          T *__restrict__ ef, int nk) {
+  int pair, rhs;
+  unit_rhs<ORD>(nk, pair, rhs);
   const int nr = rhs_tile<ORD>() == 1 ? 1 : min(rhs_tile<ORD>(), nk - rhs);
-  for (int k = 0; k < nr; ++k) {  // one pass unless ORD is the right-hand-side tile
-  const T *__restrict__ ecj = ec + (size_t)(rhs + k) * gc.nb * BV;
-  T *__restrict__ efj = ef + (size_t)(rhs + k) * gf.nb * BV;
-  T e[8];
-#pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    const int gx_ = 4 * bc.x + ccx + (o & 1), gy_ = 4 * bc.y + ccy + ((o >> 1) & 1),
-              gz_ = 4 * bc.z + ccz + (o >> 2);
-    const int pb = (((gz_ >> 3) - (bc.z >> 1)) << 2) | (((gy_ >> 3) - (bc.y >> 1)) << 1) |
-                   ((gx_ >> 3) - (bc.x >> 1));
-    const int nb = __ldg(&gf.par[(size_t)bk * 8 + pb]);
-    e[o] = nb >= 0 ? ecj[(size_t)nb * BV + ((gz_ & 7) * 8 + (gy_ & 7)) * 8 + (gx_ & 7)] : T(0);
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {  // r = uz*2 + uy: one 2-vector (ux = 0, 1) per row
-    const int uy = r & 1, uz = r >> 1;
-    T *row = efj + (size_t)bk * BV + ((2 * ccz + uz) * 8 + 2 * ccy + uy) * 8 + 2 * ccx;
-    T v[2];
-    if constexpr (sizeof(T) == 4) {
-      const float2 u = *reinterpret_cast<const float2 *>(row);
-      v[0] = u.x; v[1] = u.y;
-    } else {
-      const double2 u = *reinterpret_cast<const double2 *>(row);
-      v[0] = u.x; v[1] = u.y;
-    }
-#pragma unroll
-    for (int ux = 0; ux < 2; ++ux) {
-      const int q = uz * 4 + uy * 2 + ux;
-#pragma unroll
-      for (int o = 0; o < 8; ++o)
-        if ((o & ~q) == 0) v[ux] += w[pc_off(q) + crank(q, o)] * e[o];
-    }
-    if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(row) = make_float2(v[0], v[1]);
-    else *reinterpret_cast<double2 *>(row) = make_double2(v[0], v[1]);
-  }
-  }
+  prolong_unit<T, false>(gf, gc, Pc, ec, ef, pair, threadIdx.x, rhs, nr);
 }
 
 // Coarsest level: x = B^{-1} b on the m listed unknowns (dense, FP64); one

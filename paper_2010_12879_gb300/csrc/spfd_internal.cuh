@@ -92,7 +92,19 @@ struct Grid {
                         //   2B + (o - 1), o in {0,1,2}^3 (index o.z*9+o.y*3+o.x), or -1
   const int *par;       // levels with a coarser level: [nb][8] ids of the coarser
                         //   bricks (B >> 1) + o, o in {0,1}^3 (index o.z*4+o.y*2+o.x), or -1
+  const unsigned *act;  // levels >= 1: [nb][16], bit t of word w is set when slot
+                        //   b*512 + 32w + t has a nonzero column of the interpolation
+                        //   from the finer level, which every nonzero Galerkin row and
+                        //   every nonzero restricted value needs; a clear bit
+                        //   guarantees a zero 27-point row and a zero restriction
+                        //   weight column (level 0: unused)
 };
+
+// The activity bits (Grid::act) of this thread's warp on brick bk, one node
+// per thread: bit (thread & 31) is this thread's slot.
+__device__ __forceinline__ unsigned act_word(const Grid &g, int bk) {
+  return __ldg(&g.act[(size_t)bk * 16 + (threadIdx.x >> 5)]);
+}
 
 // Brick id of node (i, j, k) or -1 (outside the grid or brick not stored).
 __device__ __forceinline__ int brick_at(const Grid &g, int i, int j, int k) {
@@ -147,8 +159,45 @@ enum : int {
   DEV_GRID_WAIT = 16,    // a grid-wide barrier hit its wait cap
 };
 
+// Grid-wide barrier of a cooperative launch (all blocks resident): arrive
+// on a counter, the last block to arrive resets it and advances the
+// generation, the others wait for the generation to change.  count and gen
+// start at zero and are left so after every barrier, so one pair serves
+// every launch on a stream.  The wait is bounded: after GRID_SPIN_LIMIT
+// polls (far beyond any real wait) it sets DEV_GRID_WAIT and goes on, so the
+// caller fails with an error instead of hanging.
+constexpr long long GRID_SPIN_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks,
+                                             int *status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = atomicAdd(gen, 0u);
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long spins = 0;
+      while (atomicAdd(gen, 0u) == g) {
+        if (++spins > GRID_SPIN_LIMIT) {
+          atomicOr(status, DEV_GRID_WAIT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- launchers
 // Setup (spfd_setup.cu)
+// Activity bits of a level (Grid::act): bit of slot s = any of the n arrays
+// src[e * S + s] (e < n) is nonzero.
+void launch_act_bits(int nb, const double *src, int n, unsigned *bits, cudaStream_t st);
 void launch_sigma_flags(const double *sigma, int nx, int ny, int nz, int MX,
                         int MY, unsigned char *flags, unsigned char *mask,
                         int *status, cudaStream_t st);

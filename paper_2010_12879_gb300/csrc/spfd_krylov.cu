@@ -812,7 +812,9 @@ k_power27(Grid g, const double *__restrict__ st, const double *__restrict__ diag
     tile_full<double>(tl, v, bk, sn);
     __syncthreads();
     const size_t s = (size_t)bk * BV + t;
-    const double av = apply27_tile<double>(tl, st, S, s);
+    // a zero row (clear activity bit) gives exactly +0 without its loads
+    const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
+    const double av = on ? apply27_tile<double>(tl, st, S, s) : 0.0;
     const double vs = tl[lz + 1][ly + 1][lx + 1];
     w[s] = dinv[s] * av;
     vav += vs * av;

@@ -576,38 +576,6 @@ k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, 
   gj_sweep<false>(sh, A, B, m, k0, r, status);
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks resident): arrive
-// on a counter, the last block to arrive resets it and advances the
-// generation, the others wait for the generation to change.  The wait is
-// bounded: after GJ_SPIN_LIMIT polls it sets DEV_GRID_WAIT and goes on (the
-// build then fails with an error instead of hanging).
-constexpr long long GJ_SPIN_LIMIT = 1LL << 22;
-
-__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks,
-                                             int *status) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned g = atomicAdd(gen, 0u);
-    __threadfence();
-    if (atomicAdd(count, 1u) == nblocks - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      long long spins = 0;
-      while (atomicAdd(gen, 0u) == g) {
-        if (++spins > GJ_SPIN_LIMIT) {
-          atomicOr(status, DEV_GRID_WAIT);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
-
 // Every sweep of the blocked Gauss-Jordan inversion in one cooperative
 // launch: the same tiles and arithmetic as the per-sweep launches, with a
 // grid barrier between sweeps (sweep k reads what sweep k-1 wrote).
@@ -736,6 +704,20 @@ void launch_pull(void *dst, const void *src_mapped, size_t bytes, cudaStream_t s
   k_pull<<<(unsigned)blocks, 256, 0, st>>>(
       (const uint4 *)src_mapped, (uint4 *)dst, n16,
       (const unsigned char *)src_mapped + n16 * 16, (unsigned char *)dst + n16 * 16, ntail);
+}
+
+// ------------------------------------------------------------ activity bits
+__global__ void __launch_bounds__(NT)
+k_act_bits(const double *__restrict__ src, int n, size_t S, unsigned *__restrict__ bits) {
+  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
+  bool any = false;
+  for (int e = 0; e < n; ++e) any |= src[(size_t)e * S + s] != 0.0;
+  const unsigned w = __ballot_sync(0xffffffffu, any);
+  if ((threadIdx.x & 31) == 0) bits[(size_t)blockIdx.x * 16 + (threadIdx.x >> 5)] = w;
+}
+
+void launch_act_bits(int nb, const double *src, int n, unsigned *bits, cudaStream_t st) {
+  if (nb) k_act_bits<<<nb, NT, 0, st>>>(src, n, (size_t)nb * BV, bits);
 }
 
 __global__ void k_set_f64(double *p, double v) { *p = v; }

@@ -54,13 +54,24 @@ __device__ __forceinline__ void ld_ints(const int *p, int (&c)[N]) {
   }
 }
 
+// Vector loads.  COH = false: plain loads (standalone kernels: what they
+// read was written by earlier launches).  COH = true: L2-only loads
+// (ld.global.cg), for a vector written by other blocks earlier in the same
+// launch (the fused coarse cycle), of which this SM's L1 may hold a stale
+// line.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
 // Neighbour brick ids of brick bk into shared memory (threads 0..26).
 __device__ __forceinline__ void load_nbr(const Grid &g, int bk, int *sn) {
   if (threadIdx.x < 27) sn[threadIdx.x] = g.nbr[(size_t)bk * 27 + threadIdx.x];
 }
 
 // Brick + full halo of x (27-point stencils).
-template <typename T>
+template <typename T, bool COH = false>
 __device__ __forceinline__ void tile_full(T (*tl)[10][10], const T *__restrict__ x,
                                           int bk, const int *sn) {
   for (int q = threadIdx.x; q < 1000; q += NT) {
@@ -70,7 +81,7 @@ __device__ __forceinline__ void tile_full(T (*tl)[10][10], const T *__restrict__
     const int oz = tz == 0 ? -1 : (tz == 9 ? 1 : 0);
     const int nb = (ox | oy | oz) ? sn[sidx(ox, oy, oz)] : bk;
     tl[tz][ty][tx] = nb >= 0
-        ? x[(size_t)nb * BV + (((tz - 1) & 7) * 8 + ((ty - 1) & 7)) * 8 + ((tx - 1) & 7)]
+        ? ldv<COH>(&x[(size_t)nb * BV + (((tz - 1) & 7) * 8 + ((ty - 1) & 7)) * 8 + ((tx - 1) & 7)])
         : T(0);
   }
 }
