@@ -198,7 +198,10 @@ namespace spfd {
 
 // Allocation with optional injected failure: SPFD_FAIL_ALLOC_AT=N makes the
 // N-th device allocation of a context fail (counted from 1), so tests can
-// check that every failure path releases what was already allocated.
+// check that every failure path releases what was already allocated.  With
+// SPFD_POISON_ALLOC set, every block handed out is first filled with 0xff
+// bytes (NaN in FP64 and FP32, -1 in integers) on the context's stream, so a
+// test can show that no result depends on memory read before it is written.
 template <typename T>
 spfd_status dalloc(spfd_ctx *c, T **p, size_t count) {
   *p = nullptr;
@@ -229,6 +232,13 @@ spfd_status dalloc(spfd_ctx *c, T **p, size_t count) {
       cudaGetLastError();
       return fail(e == cudaErrorMemoryAllocation ? SPFD_ENOMEM : SPFD_ECUDA,
                   "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  if (getenv("SPFD_POISON_ALLOC")) {
+    cudaError_t e = cudaMemsetAsync(q, 0xff, block, c->stream);
+    if (e != cudaSuccess) {
+      c->spare.emplace_back(q, block);
+      return fail(SPFD_ECUDA, "poisoning a block failed: %s", cudaGetErrorString(e));
     }
   }
   c->allocs.push_back(q);

@@ -327,6 +327,35 @@ def test_sigma_at_an_8_byte_offset(torch_cuda, spfd):
     assert torch.equal(out[0][0], out[1][0])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_no_result_depends_on_unwritten_memory(torch_cuda, spfd, monkeypatch, precision):
+    """Every device block the library hands out is first filled with NaN
+    bytes (SPFD_POISON_ALLOC): build, solve to the rounding floor, |E| and the
+    adjoint gradient on the 8 mm body give the same bits as with ordinary
+    blocks, so nothing reads memory before writing it."""
+    torch = torch_cuda
+    ph = body_phantom(64, 40, 224, h=8e-3)
+    a = _dev(torch, loop_potential(ph.dims, ph.h, ph.origin))
+    sig = _dev(torch, ph.sigma)
+    prec = spfd.SPFD_FP64 if precision == "fp64" else spfd.SPFD_MIXED
+    out = []
+    for poison in (False, True):
+        if poison:
+            monkeypatch.setenv("SPFD_POISON_ALLOC", "1")
+        with spfd.Solver(sig, ph.h, precision=prec) as S:
+            psi, info, st = S.solve(a, 1e-12)
+            E = S.efield(a, psi, OMEGA)
+            J, dJda, dJds, infoa, sta = S.energy_grad(a, psi, OMEGA, 1e-10)
+            torch.cuda.synchronize()
+            out.append((st, info["iters"], info["outer_iters"], psi.clone(), E.clone(), J,
+                        dJds.clone()))
+        monkeypatch.delenv("SPFD_POISON_ALLOC", raising=False)
+    (s0, i0, o0, p0, e0, j0, d0), (s1, i1, o1, p1, e1, j1, d1) = out
+    assert s0 == s1 == spfd.SPFD_OK and (i0, o0) == (i1, o1)
+    assert torch.equal(p0, p1) and torch.equal(e0, e1) and j0 == j1
+    assert torch.equal(d0, d1)
+
+
 def test_cached_blocks_are_reused(torch_cuda, spfd):
     """A second build of the same model takes its device buffers from the
     library's cache: no net device memory is taken from the driver, and
@@ -469,7 +498,7 @@ def test_body_full_size_error_against_oracle(torch_cuda, spfd, body_2mm, precisi
     with spfd.Solver(_dev(torch, ph.sigma), ph.h, precision=prec) as S:
         psi, info, st = S.solve(ad, tol)
         E = S.efield(ad, psi, OMEGA).reshape(-1)
-    assert st == spfd.SPFD_OK and info["rel_res_true"] <= tol
+    assert st == spfd.SPFD_OK and info["rel_res_true"] <= tol, (st, info)
     nodes = torch.tensor(gold["psi_sample_nodes"], dtype=torch.int64, device="cuda")
     vox = torch.tensor(gold["E_sample_voxels"], dtype=torch.int64, device="cuda")
     pw = np.array(gold["psi_sample_values"])
