@@ -266,6 +266,12 @@ def run_ours(args):
 
     hbm_peak, peak_kind = _peaks()
     K, W = args.steps, args.warmup
+    # the FP64 pipe's rate on this GPU, measured by the library's probe
+    # (independent FMA chains on every resident warp), beside the derived one
+    try:
+        fp64_measured, _ = spfd.spfd_fp64_fma_rate(stream.cuda_stream)
+    except Exception:
+        fp64_measured = None
     # timed steps run without per-launch events; the kernel table and the
     # roofline come from separate profiled steps (events around every launch)
     rec64, wall64, clk64 = timed(spfd.SPFD_FP64, K, W, False)
@@ -320,6 +326,8 @@ def run_ours(args):
                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                     "frac": round(tfl / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                     "peak_kind": "FP64 pipe, derived from unit counts and clocks",
+                    "measured_fp64_fma_tflops": round(fp64_measured, 4) if fp64_measured else None,
+                    "frac_of_measured": round(tfl / fp64_measured, 4) if fp64_measured else None,
                     "algorithmic_GBs": round(gbs, 1), "avg_launch_ms": round(per, 4),
                     "launches": f["launches"], "share_of_solve_kernel_time": round(share, 3)}
         return {"kernel": name, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,

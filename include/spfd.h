@@ -417,6 +417,16 @@ spfd_status spfd_autotune_report(const spfd_ctx *ctx, spfd_tune_entry *entries, 
  * memory management of this library. */
 spfd_status spfd_release_cached_memory(size_t *released);
 
+/* This GPU's FP64 fused multiply-add rate, measured (not part of the paper's
+ * method: the denominator of the roofline of the library's FP64 kernels,
+ * which are bound by the FP64 pipe).  Runs a kernel of independent FMA chains
+ * on every resident warp six times and reports the fastest of the last five:
+ *   stream   cudaStream_t to run on (NULL = legacy default stream).
+ *   tflops   host output: 2 * FMAs / time, in TFLOP/s.
+ *   ms       optional host output: that kernel's CUDA-event time.
+ * Synchronises the stream. */
+spfd_status spfd_fp64_fma_rate(void *stream, double *tflops, double *ms);
+
 /* Thread-local message for the most recent failing call on this thread. */
 const char *spfd_last_error(void);
 

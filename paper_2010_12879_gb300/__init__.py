@@ -32,7 +32,8 @@ EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
            "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
            "spfd_energy_grad", "spfd_solve_batch", "spfd_percentile",
            "spfd_group_create", "spfd_group_solve", "spfd_group_destroy",
-           "spfd_autotune_report", "spfd_tree_cotree", "spfd_pipeline_host")
+           "spfd_autotune_report", "spfd_tree_cotree", "spfd_pipeline_host",
+           "spfd_fp64_fma_rate")
 
 
 class SpfdOpts(ctypes.Structure):
@@ -122,6 +123,9 @@ def lib():
                                              dp, dp, dp, ctypes.POINTER(SpfdOpts), vp, vp, vp,
                                              ctypes.POINTER(SpfdInfo)]
             L.spfd_pipeline_host.restype = ctypes.c_int
+            L.spfd_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]
+            L.spfd_fp64_fma_rate.restype = ctypes.c_int
             L.spfd_energy_grad.argtypes = [vp, vp, vp, dp, dp, ctypes.POINTER(dp), vp, vp,
                                            ctypes.POINTER(SpfdInfo)]
             L.spfd_energy_grad.restype = ctypes.c_int
@@ -324,6 +328,13 @@ def pipeline_host(sigma, a, h: float, tol: float, omega: float, psi_out, E_out,
         ctypes.c_void_p(stream), ctypes.c_void_p(ptr(psi_out)), ctypes.c_void_p(ptr(E_out)),
         ctypes.byref(info)), allow=(SPFD_OK, SPFD_ENOTCONVERGED))
     return st, info.as_dict()
+
+
+def spfd_fp64_fma_rate(stream: int = 0):
+    """This GPU's FP64 FMA rate: (TFLOP/s, ms of the timed kernel)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().spfd_fp64_fma_rate(ctypes.c_void_p(stream), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def spfd_group_create(ctxs, stream: int = 0) -> int:
