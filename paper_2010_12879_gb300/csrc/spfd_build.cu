@@ -447,8 +447,8 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   clk.mark("level-0 tables");
   const size_t S0 = c->L[0].S;
   const int nb0 = c->L[0].g.nb;
-  // reduction scratch: the level-0 CG operator writes 4 partials per brick
-  // (16 reserved), followed by the finishing reduction's block sums (152); the
+  // reduction scratch: the level-0 CG operator and the last smoothing sweep
+  // write at most 8 partials per brick (16 reserved), followed by the finishing reduction's block sums (152); the
   // grid-stride reductions of every level write 2 values per block, on at
   // most 608 blocks
   c->pstride = 16 * (size_t)std::max(nb0, 1) + 2048;

@@ -63,7 +63,7 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       rz[i] = bv.v[i] * xc.v[i];
-      zs[i] = wv.v[i] > (T)0 ? xc.v[i] : (T)0;
+      zs[i] = weight_pos(wv.v[i]) ? xc.v[i] : (T)0;
     }
     const WarpSum<T> prz = warp_total<T, N>(rz), pzs = warp_total<T, N>(zs);
     if ((t & 31) == 0) {
@@ -75,21 +75,60 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
   }
 }
 
-// r = b - A x on brick bk of a 27-point level: one node per thread, every
-// thread of the NT-thread block calls it; tl and sn are the caller's shared
-// tile and neighbour table.  A zero row (clear activity bit) contributes
-// exactly +0: its 27 coefficients are not read.
+// This thread's slot in a 27-point kernel over the staged brick: with
+// compaction (FP64) the brick's n-th active slot for thread n, else the
+// thread's own slot.  mine: the thread computes the stencil at ts; idle: its
+// own slot is inactive and gets the zero-row result.
+struct SlotMap {
+  int ts;
+  bool mine, idle;
+};
+template <typename T>
+__device__ __forceinline__ SlotMap slot_map(const ActList &al) {
+  const int t = threadIdx.x;
+  SlotMap m;
+  m.idle = !act_on(al, t);
+  if constexpr (compact27<T>()) {
+    m.mine = t < al.pre[16];
+    m.ts = m.mine ? act_slot(al, t) : 0;
+  } else {
+    m.mine = !m.idle;
+    m.ts = t;
+  }
+  return m;
+}
+
+// r = b - A x on brick bk of a 27-point level; every thread of the
+// NT-thread block calls it, and tl, sn and al are the caller's shared tile,
+// neighbour table and activity list.  A zero row (clear activity bit) gets
+// r = b - 0 = b without its 27 coefficients or any arithmetic.  FP64:
+// thread n computes the brick's n-th active slot (compaction).
 template <typename T, bool COH>
 __device__ __forceinline__ void residual27_unit(const Grid &g, const T *__restrict__ st,
                                                 const T *x, const T *b, T *r, int bk,
-                                                T (*tl)[10][10], int *sn) {
-  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + threadIdx.x;
+                                                T (*tl)[10][10], int *sn, ActList &al) {
+  const int t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, base = (size_t)bk * BV;
   load_nbr(g, bk, sn);
-  const bool on = (act_word(g, bk) >> (threadIdx.x & 31)) & 1u;
-  __syncthreads();
-  tile_full<T, COH>(tl, x, bk, sn);
-  __syncthreads();
-  r[s] = ldv<COH>(b + s) - (on ? apply27_tile<T>(tl, st, S, s) : T(0));
+  if constexpr (compact27<T>()) {
+    act_stage(g, bk, al);
+    __syncthreads();
+    tile_full<T, COH>(tl, x, bk, sn);
+    if (!act_on(al, t)) r[base + t] = ldv<COH>(b + base + t);
+    __syncthreads();
+    if (t < al.pre[16]) {
+      const int ts = act_slot(al, t);
+      const size_t s = base + ts;
+      r[s] = ldv<COH>(b + s) - apply27_tile<T>(tl, st, S, s, ts);
+    }
+  } else {
+    const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
+    __syncthreads();
+    tile_full<T, COH>(tl, x, bk, sn);
+    __syncthreads();
+    const size_t s = base + t;
+    r[s] = ldv<COH>(b + s) - (on ? apply27_tile<T>(tl, st, S, s, t) : T(0));
+  }
 }
 
 template <typename T, int ORD>
@@ -98,49 +137,67 @@ k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
              const T *__restrict__ b, T *__restrict__ r, int nk) {
   __shared__ T tl[rhs_tile<ORD>()][10][10][10];
   __shared__ int sn[27];
+  __shared__ ActList al;
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
-  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + threadIdx.x;
+  const int t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, base = (size_t)bk * BV;
   if constexpr (rhs_tile<ORD>() == 1) {
     const size_t off = (size_t)rhs * S;
-    residual27_unit<T, false>(g, st, x + off, b + off, r + off, bk, tl[0], sn);
+    residual27_unit<T, false>(g, st, x + off, b + off, r + off, bk, tl[0], sn, al);
   } else {
     load_nbr(g, bk, sn);
-    const bool on = (act_word(g, bk) >> (threadIdx.x & 31)) & 1u;
+    act_stage(g, bk, al);
+    __syncthreads();
     // the tile's right-hand sides side by side: all their halo tiles are
     // loaded at once, then each uses the coefficients held in registers
+    const SlotMap m = slot_map<T>(al);
+    const size_t sa = base + m.ts;
     T cf[27];
-    if (on) load27(st, S, s, cf);
-    else
-#pragma unroll
-      for (int e = 0; e < 27; ++e) cf[e] = T(0);
+    if (m.mine) load27(st, S, sa, cf);
     const int nr = min(rhs_tile<ORD>(), nk - rhs);
-    __syncthreads();
     for (int k = 0; k < nr; ++k) tile_full<T>(tl[k], x + (size_t)(rhs + k) * S, bk, sn);
     __syncthreads();
     for (int k = 0; k < nr; ++k) {
       const size_t off = (size_t)(rhs + k) * S;
-      r[off + s] = b[off + s] - apply27_regs<T>(tl[k], cf);
+      if (m.idle) r[off + base + t] = b[off + base + t];
+      if (m.mine) r[off + sa] = b[off + sa] - apply27_regs<T>(tl[k], cf, m.ts);
     }
   }
 }
 
 // One weighted-Jacobi sweep xout = xin + omega D^-1 (b - A xin) on brick bk
-// of a 27-point level (as residual27_unit).
+// of a 27-point level (as residual27_unit; a zero row gets xin + w b).
 template <typename T, bool COH>
 __device__ __forceinline__ void jacobi27_unit(const Grid &g, const T *__restrict__ st,
                                               const T *__restrict__ wdinv, const T *xin,
                                               const T *b, T *xout, int bk, T (*tl)[10][10],
-                                              int *sn) {
+                                              int *sn, ActList &al) {
   const int t = threadIdx.x;
-  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  const size_t S = (size_t)g.nb * BV, base = (size_t)bk * BV;
   load_nbr(g, bk, sn);
-  const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
-  __syncthreads();
-  tile_full<T, COH>(tl, xin, bk, sn);
-  __syncthreads();
-  const T r = ldv<COH>(b + s) - (on ? apply27_tile<T>(tl, st, S, s) : T(0));
-  xout[s] = tl[(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wdinv[s] * r;
+  if constexpr (compact27<T>()) {
+    act_stage(g, bk, al);
+    __syncthreads();
+    tile_full<T, COH>(tl, xin, bk, sn);
+    __syncthreads();
+    if (!act_on(al, t))
+      xout[base + t] = tile_at(tl, t) + wdinv[base + t] * ldv<COH>(b + base + t);
+    if (t < al.pre[16]) {
+      const int ts = act_slot(al, t);
+      const size_t s = base + ts;
+      const T r = ldv<COH>(b + s) - apply27_tile<T>(tl, st, S, s, ts);
+      xout[s] = tile_at(tl, ts) + wdinv[s] * r;
+    }
+  } else {
+    const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
+    __syncthreads();
+    tile_full<T, COH>(tl, xin, bk, sn);
+    __syncthreads();
+    const size_t s = base + t;
+    const T r = ldv<COH>(b + s) - (on ? apply27_tile<T>(tl, st, S, s, t) : T(0));
+    xout[s] = tile_at(tl, t) + wdinv[s] * r;
+  }
 }
 
 template <typename T, int ORD>
@@ -150,30 +207,33 @@ k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
            T *__restrict__ xout, int nk) {
   __shared__ T tl[rhs_tile<ORD>()][10][10][10];
   __shared__ int sn[27];
+  __shared__ ActList al;
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
-  const size_t S = (size_t)g.nb * BV, s = (size_t)bk * BV + t;
+  const size_t S = (size_t)g.nb * BV, base = (size_t)bk * BV;
   if constexpr (rhs_tile<ORD>() == 1) {
     const size_t off = (size_t)rhs * S;
-    jacobi27_unit<T, false>(g, st, wdinv, xin + off, b + off, xout + off, bk, tl[0], sn);
+    jacobi27_unit<T, false>(g, st, wdinv, xin + off, b + off, xout + off, bk, tl[0], sn, al);
   } else {
     load_nbr(g, bk, sn);
-    const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
-    T cf[27];
-    if (on) load27(st, S, s, cf);
-    else
-#pragma unroll
-      for (int e = 0; e < 27; ++e) cf[e] = T(0);
-    const T wd = wdinv[s];
-    const int nr = min(rhs_tile<ORD>(), nk - rhs);
+    act_stage(g, bk, al);
     __syncthreads();
+    const SlotMap m = slot_map<T>(al);
+    const size_t sa = base + m.ts;
+    T cf[27];
+    if (m.mine) load27(st, S, sa, cf);
+    const T wd = m.mine ? wdinv[sa] : T(0), wi = m.idle ? wdinv[base + t] : T(0);
+    const int nr = min(rhs_tile<ORD>(), nk - rhs);
     for (int k = 0; k < nr; ++k) tile_full<T>(tl[k], xin + (size_t)(rhs + k) * S, bk, sn);
     __syncthreads();
     for (int k = 0; k < nr; ++k) {
       const size_t off = (size_t)(rhs + k) * S;
-      const T r = b[off + s] - apply27_regs<T>(tl[k], cf);
-      xout[off + s] = tl[k][(t >> 6) + 1][((t >> 3) & 7) + 1][(t & 7) + 1] + wd * r;
+      if (m.idle) xout[off + base + t] = tile_at(tl[k], t) + wi * b[off + base + t];
+      if (m.mine) {
+        const T r = b[off + sa] - apply27_regs<T>(tl[k], cf, m.ts);
+        xout[off + sa] = tile_at(tl[k], m.ts) + wd * r;
+      }
     }
   }
 }
@@ -215,7 +275,7 @@ k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
   V16<T> bv = ld16(b + s0), xv;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    if (w.v[i] > (T)0) {  // an unknown of level 0
+    if (weight_pos(w.v[i])) {  // an unknown of level 0
       bv.v[i] -= mean;
       xv.v[i] = w.v[i] * bv.v[i];
     } else {

@@ -106,6 +106,90 @@ __device__ __forceinline__ unsigned act_word(const Grid &g, int bk) {
   return __ldg(&g.act[(size_t)bk * 16 + (threadIdx.x >> 5)]);
 }
 
+// The bit pattern of an FP64 value, through an opaque move: the compiler
+// would otherwise fold integer tests of the bits back into FP64 comparisons,
+// and on GB300 each of those takes a slot of the narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long f64_bits(double x) {
+  unsigned long long u;
+  asm("mov.b64 %0, %1;" : "=l"(u) : "d"(x));
+  return u;
+}
+// x is not +-0 (for x known to be +-0 or positive: x > 0), from its bits.
+__device__ __forceinline__ bool f64_nonzero(double x) { return (f64_bits(x) << 1) != 0ull; }
+// x is infinite or NaN, from its bits.
+__device__ __forceinline__ bool f64_nonfinite(double x) {
+  return ((f64_bits(x) >> 52) & 0x7ffull) == 0x7ffull;
+}
+// w > 0 for a non-negative weight w: a bit test in FP64, a comparison in FP32.
+template <typename T>
+__device__ __forceinline__ bool weight_pos(T w) {
+  if constexpr (sizeof(T) == 8) return f64_nonzero(w);
+  else return w > T(0);
+}
+
+// Active-slot compaction of one brick of a 27-point level.  The block that
+// handles brick bk gives its n-th thread the brick's n-th active slot (set
+// activity bit, in slot order), so warps past the brick's active count skip
+// the stencil arithmetic: a warp instruction occupies the FP64 pipe whatever
+// its lane mask, so only warps with no active slot save FP64 time.  FP64
+// kernels use it; FP32 ones, bound by memory, keep one slot per thread.
+template <typename T>
+constexpr bool compact27() { return sizeof(T) == 8; }
+
+struct ActList {
+  unsigned w[16];  // the brick's activity words
+  int pre[17];     // exclusive prefix counts of w; pre[16] = active slots
+};
+
+// Warp 0 stages brick bk's words and prefix counts (a barrier must follow
+// before any thread reads them).
+__device__ __forceinline__ void act_stage(const Grid &g, int bk, ActList &al) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned w = lane < 16 ? __ldg(&g.act[(size_t)bk * 16 + lane]) : 0u;
+    const int c = __popc(w);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane < 16) {
+      al.w[lane] = w;
+      al.pre[lane] = incl - c;
+    }
+    if (lane == 15) al.pre[16] = incl;
+  }
+}
+
+// Local slot (0..511) of the brick's n-th active slot, n < al.pre[16].
+__device__ __forceinline__ int act_slot(const ActList &al, int n) {
+  int j = 0;  // the last word whose prefix count is <= n (it holds slot n)
+#pragma unroll
+  for (int step = 8; step > 0; step >>= 1)
+    if (al.pre[j + step] <= n) j += step;
+  unsigned w = al.w[j];
+  int k = n - al.pre[j], pos = 0;  // the k-th set bit of w, by halving
+#pragma unroll
+  for (int width = 16; width > 0; width >>= 1) {
+    const unsigned lo = w & ((1u << width) - 1u);
+    const int c = __popc(lo);
+    if (k >= c) {
+      k -= c;
+      w >>= width;
+      pos += width;
+    } else {
+      w = lo;
+    }
+  }
+  return j * 32 + pos;
+}
+
+// Whether local slot t of the staged brick is active.
+__device__ __forceinline__ bool act_on(const ActList &al, int t) {
+  return (al.w[t >> 5] >> (t & 31)) & 1u;
+}
+
 // Brick id of node (i, j, k) or -1 (outside the grid or brick not stored).
 __device__ __forceinline__ int brick_at(const Grid &g, int i, int j, int k) {
   if ((unsigned)i >= (unsigned)g.NX || (unsigned)j >= (unsigned)g.NY ||

@@ -99,8 +99,8 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket,
 constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SMs
 
 // ------------------------------------------------------------ CG operator
-// q = A p on one brick per block (row mapping, four nodes per thread); each
-// warp writes its part of p.q, and k_finish_pq adds them.
+// q = A p on one brick per block (row mapping); each warp writes its part
+// of p.q, and k_finish_pq adds them.
 template <typename T, int ORD>
 __global__ void __launch_bounds__(row_threads<T>(), row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
@@ -441,7 +441,9 @@ k_dot(int nb, const T *__restrict__ x, const T *__restrict__ y,
 // ------------------------------------------------------------ Eq. 3 RHS
 // b_n = sum_{e leaving n} g_e a_e - sum_{e entering n} g_e a_e, from the
 // full-grid edge array a[3][NZ][NY][NX]; non-finite a on a conducting edge
-// raises DEV_BAD_A.
+// raises DEV_BAD_A.  The tests of g_e > 0 (g_e is +0, -0 or positive) and of
+// a finite a_e look at bit patterns, so each edge costs one FP64 multiply-add
+// on GB300's narrow FP64 pipe.
 __global__ void __launch_bounds__(NT)
 k_rhs(Grid g, const double *__restrict__ gx, const double *__restrict__ a,
       double *__restrict__ b, int *status) {
@@ -460,26 +462,27 @@ k_rhs(Grid g, const double *__restrict__ gx, const double *__restrict__ a,
   if (i < g.NX && j < g.NY && k < g.NZ) {
     const size_t NN = (size_t)g.NX * g.NY * g.NZ;
     const size_t n = ((size_t)k * g.NY + j) * g.NX + i;
-    auto term = [&](double ge, size_t idx, double sign) {
-      if (ge > 0.0) {
+    // ge: a conductance (+0, -0 or positive), subtracted for an entering edge
+    auto term = [&](double ge, size_t idx, bool entering) {
+      if (f64_nonzero(ge)) {
         const double av = a[idx];
-        if (!isfinite(av)) bad = true;
-        acc += sign * ge * av;
+        if (f64_nonfinite(av)) bad = true;
+        acc = fma(entering ? -ge : ge, av, acc);
       }
     };
-    term(gx[s], n, 1.0);
-    term(gx[S + s], NN + n, 1.0);
-    term(gx[2 * S + s], 2 * NN + n, 1.0);
+    term(gx[s], n, false);
+    term(gx[S + s], NN + n, false);
+    term(gx[2 * S + s], 2 * NN + n, false);
     // -edges: the +edge conductance of the neighbour node
     int nb;
-    if (lx > 0) term(gx[s - 1], n - 1, -1.0);
-    else if ((nb = sn[sidx(-1, 0, 0)]) >= 0) term(gx[(size_t)nb * BV + t + 7], n - 1, -1.0);
-    if (ly > 0) term(gx[S + s - 8], NN + n - g.NX, -1.0);
+    if (lx > 0) term(gx[s - 1], n - 1, true);
+    else if ((nb = sn[sidx(-1, 0, 0)]) >= 0) term(gx[(size_t)nb * BV + t + 7], n - 1, true);
+    if (ly > 0) term(gx[S + s - 8], NN + n - g.NX, true);
     else if ((nb = sn[sidx(0, -1, 0)]) >= 0)
-      term(gx[S + (size_t)nb * BV + t + 56], NN + n - g.NX, -1.0);
-    if (lz > 0) term(gx[2 * S + s - 64], 2 * NN + n - (size_t)g.NX * g.NY, -1.0);
+      term(gx[S + (size_t)nb * BV + t + 56], NN + n - g.NX, true);
+    if (lz > 0) term(gx[2 * S + s - 64], 2 * NN + n - (size_t)g.NX * g.NY, true);
     else if ((nb = sn[sidx(0, 0, -1)]) >= 0)
-      term(gx[2 * S + (size_t)nb * BV + t + 448], 2 * NN + n - (size_t)g.NX * g.NY, -1.0);
+      term(gx[2 * S + (size_t)nb * BV + t + 448], 2 * NN + n - (size_t)g.NX * g.NY, true);
   }
   b[s] = bad ? 0.0 : acc;
   if (bad) atomicOr(status, DEV_BAD_A);
@@ -535,7 +538,10 @@ k_gather(Grid g, const double *__restrict__ psi, const int *__restrict__ comp,
 // Per voxel layer a column forms 5 terms (10 FP64 additions) against 16 when
 // every voxel forms its own.
 constexpr int EF_THREADS = 256;
-constexpr int EF_KCHUNK = 32;
+constexpr int EF_KCHUNK = 16;
+// 4 resident blocks per SM (at most 64 registers a thread): the kernel waits
+// on memory between layers, and the FP64 pipe needs the warps to cover it.
+constexpr int EF_MIN_BLOCKS = 4;
 
 struct EfTerms {
   double p0, p1;  // Psi(i, j, k), Psi(i, j+1, k)
@@ -562,7 +568,7 @@ __device__ __forceinline__ EfTerms ef_layer(const double *__restrict__ a,
   return T;
 }
 
-__global__ void __launch_bounds__(EF_THREADS)
+__global__ void __launch_bounds__(EF_THREADS, EF_MIN_BLOCKS)
 k_efield(const unsigned char *__restrict__ mask, const double *__restrict__ a,
          const double *__restrict__ psi, int nx, int ny, int nz, double c,
          double *__restrict__ E) {
@@ -795,30 +801,36 @@ k_power_init(const double *__restrict__ diag, double *__restrict__ v) {
 // w = D^-1 A v, with the generalized Rayleigh quotient terms v.(A v) and
 // v.(D v) added into sc->aux[4] and sc->aux[5] (last-block reduction).
 // Bricks are grid-strided over at most RED_GRID blocks; v is staged in a
-// full-halo tile per brick.
+// full-halo tile per brick, and thread n handles the brick's n-th active
+// slot (a zero row has w = 0 and adds nothing: its v and diagonal are 0).
 __global__ void __launch_bounds__(NT)
 k_power27(Grid g, const double *__restrict__ st, const double *__restrict__ diag,
           const double *__restrict__ dinv, const double *__restrict__ v,
           double *__restrict__ w, Scalars *sc, double *partials) {
   __shared__ double tl[10][10][10];
   __shared__ int sn[27];
-  const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  __shared__ ActList al;
+  const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV;
   double vav = 0.0, vdv = 0.0;
   for (int bk = blockIdx.x; bk < g.nb; bk += gridDim.x) {
-    __syncthreads();  // the previous brick's tile is no longer read
+    __syncthreads();  // the previous brick's tile and list are no longer read
     load_nbr(g, bk, sn);
+    act_stage(g, bk, al);
     __syncthreads();
     tile_full<double>(tl, v, bk, sn);
     __syncthreads();
-    const size_t s = (size_t)bk * BV + t;
-    // a zero row (clear activity bit) gives exactly +0 without its loads
-    const bool on = (act_word(g, bk) >> (t & 31)) & 1u;
-    const double av = on ? apply27_tile<double>(tl, st, S, s) : 0.0;
-    const double vs = tl[lz + 1][ly + 1][lx + 1];
-    w[s] = dinv[s] * av;
-    vav += vs * av;
-    vdv += vs * vs * diag[s];
+    const size_t base = (size_t)bk * BV;
+    if (!act_on(al, t)) w[base + t] = 0.0;
+    if (t < al.pre[16]) {
+      const int ts = act_slot(al, t);
+      const size_t s = base + ts;
+      const double av = apply27_tile<double>(tl, st, S, s, ts);
+      const double vs = tile_at(tl, ts);
+      w[s] = dinv[s] * av;
+      vav += vs * av;
+      vdv += vs * vs * diag[s];
+    }
   }
   double vals[2] = {vav, vdv}, tot[2];
   if (grid_sum<2>(vals, partials, &sc->ticket[4], tot)) {

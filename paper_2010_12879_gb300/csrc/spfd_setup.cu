@@ -15,27 +15,16 @@ namespace spfd {
 // (on this GPU an FP64 comparison costs a slot of the narrow FP64 pipe):
 // conducting iff the value is > 0 (sign clear, not zero, exponent not all
 // ones); invalid iff NaN or infinite (exponent all ones) or negative and not
-// -0.  mask gets 1 per conducting voxel, and the bricks of its 8 corner
-// nodes are flagged.
-__device__ __forceinline__ void flag_voxel(unsigned long long u, int i, int j, int k, int MX,
-                                           int MY, unsigned char *__restrict__ flags,
-                                           unsigned char &m, int &bad) {
+// -0.  mask gets 1 per conducting voxel.  The bricks of the conducting
+// voxels' corner nodes are flagged once per warp step: the lanes OR the
+// x-bricks they touch into one word, and one lane per touched x-brick stores
+// its flags for the row's (at most 4) brick rows, so a flag byte is not
+// written once per voxel.
+__device__ __forceinline__ unsigned char classify_sigma(unsigned long long u, int &bad) {
   const unsigned ex = (unsigned)(u >> 52) & 0x7ffu;
   const bool neg = (u >> 63) != 0;
   if (ex == 0x7ffu || (neg && (u << 1) != 0)) bad = 1;
-  m = (!neg && u != 0 && ex != 0x7ffu) ? 1 : 0;
-  if (m) {
-    const int i0 = i >> 3, i1 = (i + 1) >> 3, j0 = j >> 3, j1 = (j + 1) >> 3;
-    const int k0 = k >> 3, k1 = (k + 1) >> 3;
-    flags[(k0 * MY + j0) * MX + i0] = 1;
-    if (i1 != i0) flags[(k0 * MY + j0) * MX + i1] = 1;
-    if (j1 != j0) flags[(k0 * MY + j1) * MX + i0] = 1;
-    if (k1 != k0) flags[(k1 * MY + j0) * MX + i0] = 1;
-    if (i1 != i0 && j1 != j0) flags[(k0 * MY + j1) * MX + i1] = 1;
-    if (i1 != i0 && k1 != k0) flags[(k1 * MY + j0) * MX + i1] = 1;
-    if (j1 != j0 && k1 != k0) flags[(k1 * MY + j1) * MX + i0] = 1;
-    if (i1 != i0 && j1 != j0 && k1 != k0) flags[(k1 * MY + j1) * MX + i1] = 1;
-  }
+  return (!neg && u != 0 && ex != 0x7ffu) ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(256)
@@ -48,25 +37,42 @@ k_sigma_flags(const double *__restrict__ sigma, int nx, int ny, int nz, int MX, 
   for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows;
        r += ((long long)gridDim.x * blockDim.x) >> 5) {
     const int j = (int)(r % ny), k = (int)(r / ny);
+    const int j0 = j >> 3, j1 = (j + 1) >> 3, k0 = k >> 3, k1 = (k + 1) >> 3;
     const double *row = sigma + (size_t)r * nx;
     unsigned char *mrow = mask + (size_t)r * nx;
     // pairs when every row starts on a 16-byte boundary (nx even and sigma
-    // 16-byte aligned), else one value at a time
-    if (pairs) {
-      for (int i = 2 * lane; i < nx; i += 64) {
-        const double2 p = *reinterpret_cast<const double2 *>(row + i);
-        unsigned char m0, m1;
-        flag_voxel((unsigned long long)__double_as_longlong(p.x), i, j, k, MX, MY, flags, m0, bad);
-        flag_voxel((unsigned long long)__double_as_longlong(p.y), i + 1, j, k, MX, MY, flags, m1,
-                   bad);
-        *reinterpret_cast<uchar2 *>(mrow + i) = make_uchar2(m0, m1);
+    // 16-byte aligned), else one value at a time; a step covers 64 (32)
+    // voxels, whose corner nodes lie in 9 (5) x-bricks from c0 / 8 on
+    const int step = pairs ? 64 : 32;
+    for (int c0 = 0; c0 < nx; c0 += step) {
+      const int base = c0 >> 3;
+      unsigned bits = 0;
+      if (pairs) {
+        const int i = c0 + 2 * lane;
+        if (i < nx) {  // nx is even, so i + 1 < nx
+          const double2 p = *reinterpret_cast<const double2 *>(row + i);
+          const unsigned char m0 = classify_sigma((unsigned long long)__double_as_longlong(p.x), bad);
+          const unsigned char m1 = classify_sigma((unsigned long long)__double_as_longlong(p.y), bad);
+          *reinterpret_cast<uchar2 *>(mrow + i) = make_uchar2(m0, m1);
+          if (m0) bits |= (1u << ((i >> 3) - base)) | (1u << (((i + 1) >> 3) - base));
+          if (m1) bits |= (1u << (((i + 1) >> 3) - base)) | (1u << (((i + 2) >> 3) - base));
+        }
+      } else {
+        const int i = c0 + lane;
+        if (i < nx) {
+          const unsigned char m0 =
+              classify_sigma((unsigned long long)__double_as_longlong(row[i]), bad);
+          mrow[i] = m0;
+          if (m0) bits |= (1u << ((i >> 3) - base)) | (1u << (((i + 1) >> 3) - base));
+        }
       }
-    } else {
-      for (int i = lane; i < nx; i += 32) {
-        unsigned char m0;
-        flag_voxel((unsigned long long)__double_as_longlong(row[i]), i, j, k, MX, MY, flags, m0,
-                   bad);
-        mrow[i] = m0;
+      bits = __reduce_or_sync(0xffffffffu, bits);
+      if (lane < 9 && ((bits >> lane) & 1u)) {
+        const int bx = base + lane;
+        flags[((size_t)k0 * MY + j0) * MX + bx] = 1;
+        if (j1 != j0) flags[((size_t)k0 * MY + j1) * MX + bx] = 1;
+        if (k1 != k0) flags[((size_t)k1 * MY + j0) * MX + bx] = 1;
+        if (j1 != j0 && k1 != k0) flags[((size_t)k1 * MY + j1) * MX + bx] = 1;
       }
     }
   }
@@ -114,15 +120,20 @@ __device__ __forceinline__ double g_edge(const double *s, int d, int i, int j,
 }
 
 // One brick per block.  The 9^3 voxels around the brick's nodes go to shared
-// memory once; each +edge conductance of the nodes -1 .. 7 (per axis) is
-// formed once there (the -edge of a node is the +edge of the node before
-// it), so a node costs about 13 FP64 operations for its six conductances
-// instead of 24.  Every conductance is summed in the same order as g_edge.
+// memory once; the sums of voxel pairs along y (py) and along x (px) are
+// formed once there, and each +edge conductance of the nodes -1 .. 7 (per
+// axis) is the sum of two such pairs times h/4 (the -edge of a node is the
+// +edge of the node before it): a node costs about 8 FP64 operations for its
+// six conductances, against 24 when each sums its own four voxels, which
+// matters on GB300's narrow FP64 pipe.  The four voxels of an edge are
+// added as (s00 + s01) + (s10 + s11).
 __global__ void __launch_bounds__(NT)
 k_build_fine(Grid g, const double *__restrict__ sigma, int nx, int ny, int nz,
              double h, double *__restrict__ gx, double *__restrict__ diag,
              double *__restrict__ dinv) {
   __shared__ double sv[9][9][9];  // voxels 8B - 1 .. 8B + 7 per axis (0 outside)
+  __shared__ double py[9][8][9];  // sv[z][y][x] + sv[z][y + 1][x]
+  __shared__ double px[9][9][8];  // sv[z][y][x] + sv[z][y][x + 1]
   __shared__ double ex[8][8][9];  // +x edge of node (lx, ly, lz), lx = -1 .. 7 at [lz][ly][lx + 1]
   __shared__ double ey[8][9][8];  // +y edge, ly = -1 .. 7 at [lz][ly + 1][lx]
   __shared__ double ez[9][8][8];  // +z edge, lz = -1 .. 7 at [lz + 1][ly][lx]
@@ -135,22 +146,30 @@ k_build_fine(Grid g, const double *__restrict__ sigma, int nx, int ny, int nz,
     sv[vz][vy][vx] = sig_at(sigma, x0 + vx, y0 + vy, z0 + vz, nx, ny, nz);
   }
   __syncthreads();
+  for (int q = t; q < 648; q += NT) {
+    {
+      const int vz = q / 72, vy = (q / 9) % 8, vx = q % 9;
+      py[vz][vy][vx] = sv[vz][vy][vx] + sv[vz][vy + 1][vx];
+    }
+    {
+      const int vz = q / 72, vy = (q / 8) % 9, vx = q % 8;
+      px[vz][vy][vx] = sv[vz][vy][vx] + sv[vz][vy][vx + 1];
+    }
+  }
+  __syncthreads();
   const double hq = h * 0.25;
   for (int q = t; q < 576; q += NT) {
-    {  // x: index (lz, ly, lx + 1)
+    {  // x: index (lz, ly, lx + 1), voxels (lz..lz+1, ly..ly+1, xp)
       const int lz = q / 72, ly = (q / 9) % 8, xp = q % 9;
-      ex[lz][ly][xp] = hq * (sv[lz][ly][xp] + sv[lz][ly + 1][xp] + sv[lz + 1][ly][xp] +
-                             sv[lz + 1][ly + 1][xp]);
+      ex[lz][ly][xp] = hq * (py[lz][ly][xp] + py[lz + 1][ly][xp]);
     }
-    {  // y: index (lz, ly + 1, lx)
+    {  // y: index (lz, ly + 1, lx), voxels (lz..lz+1, yp, lx..lx+1)
       const int lz = q / 72, yp = (q / 8) % 9, lx = q % 8;
-      ey[lz][yp][lx] = hq * (sv[lz][yp][lx] + sv[lz][yp][lx + 1] + sv[lz + 1][yp][lx] +
-                             sv[lz + 1][yp][lx + 1]);
+      ey[lz][yp][lx] = hq * (px[lz][yp][lx] + px[lz + 1][yp][lx]);
     }
-    {  // z: index (lz + 1, ly, lx)
+    {  // z: index (lz + 1, ly, lx), voxels (zp, ly..ly+1, lx..lx+1)
       const int zp = q / 64, ly = (q / 8) % 8, lx = q % 8;
-      ez[zp][ly][lx] = hq * (sv[zp][ly][lx] + sv[zp][ly][lx + 1] + sv[zp][ly + 1][lx] +
-                             sv[zp][ly + 1][lx + 1]);
+      ez[zp][ly][lx] = hq * (py[zp][ly][lx] + py[zp][ly][lx + 1]);
     }
   }
   __syncthreads();
@@ -166,12 +185,13 @@ k_build_fine(Grid g, const double *__restrict__ sigma, int nx, int ny, int nz,
     e[4] = ey[lz][ly][lx];      // -y
     e[5] = ez[lz][ly][lx];      // -z
   }
-  double d = ((e[3] + e[0]) + (e[4] + e[1])) + (e[5] + e[2]);
+  const double d = ((e[3] + e[0]) + (e[4] + e[1])) + (e[5] + e[2]);
   gx[s] = e[0];
   gx[S + s] = e[1];
   gx[2 * S + s] = e[2];
   diag[s] = d;
-  dinv[s] = d > 0.0 ? 1.0 / d : 0.0;
+  // d is +0, -0 or positive: a bit test replaces the FP64 comparison
+  dinv[s] = f64_nonzero(d) ? 1.0 / d : 0.0;
 }
 
 void launch_build_fine(const Grid &g, const double *sigma, int nx, int ny,

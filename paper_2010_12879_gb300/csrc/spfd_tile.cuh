@@ -272,11 +272,12 @@ __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ 
   }
 }
 
-// 27-point stencil at this thread's node, x in a full-halo tile.
+// 27-point stencil at local slot ts (global slot s) of the tiled brick, x
+// in a full-halo tile.
 template <typename T>
 __device__ __forceinline__ T apply27_tile(const T (*tl)[10][10], const T *__restrict__ st,
-                                          size_t S, size_t s) {
-  const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+                                          size_t S, size_t s, int ts) {
+  const int lx = ts & 7, ly = (ts >> 3) & 7, lz = ts >> 6;
   T acc = 0;
 #pragma unroll
   for (int e = 0; e < 27; ++e) {
@@ -284,6 +285,12 @@ __device__ __forceinline__ T apply27_tile(const T (*tl)[10][10], const T *__rest
     acc += st[(size_t)e * S + s] * tl[lz + 1 + dz][ly + 1 + dy][lx + 1 + dx];
   }
   return acc;
+}
+
+// The tile's value at local slot ts of its brick.
+template <typename T>
+__device__ __forceinline__ T tile_at(const T (*tl)[10][10], int ts) {
+  return tl[(ts >> 6) + 1][((ts >> 3) & 7) + 1][(ts & 7) + 1];
 }
 
 // Sum of the N values of every lane of the warp, held by every lane: an
@@ -340,8 +347,8 @@ __device__ __forceinline__ void load27(const T *__restrict__ a, size_t S, size_t
 
 // apply27_tile with the coefficients in registers (same order of terms).
 template <typename T>
-__device__ __forceinline__ T apply27_regs(const T (*tl)[10][10], const T (&cf)[27]) {
-  const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+__device__ __forceinline__ T apply27_regs(const T (*tl)[10][10], const T (&cf)[27], int ts) {
+  const int lx = ts & 7, ly = (ts >> 3) & 7, lz = ts >> 6;
   T acc = 0;
 #pragma unroll
   for (int e = 0; e < 27; ++e) {
