@@ -201,15 +201,18 @@ struct PhaseClock {
 // of a connected component of the coarsest graph, mu_c its mean diagonal) is
 // SPD, and B^-1 r = A^+ r for r with zero mean on every component.  The
 // symmetrised inverse is applied as a dense FP64 matrix-vector product.
+// The host reads the level back to number its unknowns and label the
+// components (a breadth-first search over the operator's couplings); the
+// dense matrix is assembled, regularised and inverted on the device.
 static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
   Level &lv = c->L.back();
   const size_t S = lv.S;
   const bool single = c->L.size() == 1;
   c->m = 0;
   if (S == 0) return SPFD_OK;
-  // read-backs and the matrix live in the context's pinned host blocks
-  // (reused across builds): fresh pageable buffers of this size cost more in
-  // first-touch page faults than the assembly itself
+  // read-backs live in the context's pinned host blocks (reused across
+  // builds): fresh pageable buffers cost more in first-touch page faults
+  // than the work on them
   double *hdiag = nullptr, *hop = nullptr;
   const size_t nop = (single ? 3 : 27) * S;
   TRY(halloc(c, &hdiag, S));
@@ -217,7 +220,6 @@ static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
   CU(cudaMemcpyAsync(hdiag, lv.diag, S * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaMemcpyAsync(hop, single ? lv.gx : lv.st, nop * sizeof(double),
                      cudaMemcpyDeviceToHost, c->stream));
-  const double *hgx = hop, *hst = hop;
   TRY(sync_check(c, "coarsest copy"));
   clk.mark("coarsest read-back");
   std::vector<int> row(S, -1), idx;
@@ -235,41 +237,31 @@ static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
     if (b < 0) return -1;
     return b * BV + ((k & 7) * 8 + (j & 7)) * 8 + (i & 7);
   };
-  double *A = nullptr;  // pinned: staged for the device as it stands
-  TRY(halloc(c, &A, (size_t)m * m));
-  memset(A, 0, (size_t)m * m * sizeof(double));
-  for (int a = 0; a < m; ++a) {
+  // the rows v != a that row a couples to (nonzero operator entry), in the
+  // order the dense matrix holds them
+  std::vector<int> nb;
+  auto couplings = [&](int a) {
+    nb.clear();
     const int s = idx[a];
     const int4 bc = lv.hbco[s / BV];
     const int t = s % BV;
     const int i = bc.x * 8 + (t & 7), j = bc.y * 8 + ((t >> 3) & 7), k = bc.z * 8 + (t >> 6);
-    if (single) {  // the 7-point level-0 operator (tiny problems)
-      A[(size_t)a * m + a] = hdiag[s];
-      const int dd[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
-      for (int q = 0; q < 6; ++q) {
-        int u = slot_of(i + dd[q][0], j + dd[q][1], k + dd[q][2]);
-        if (u < 0 || row[u] < 0) continue;
-        int ax = q / 2;
-        double ge = (q % 2 == 0) ? hgx[(size_t)ax * S + s] : hgx[(size_t)ax * S + u];
-        A[(size_t)a * m + row[u]] -= ge;
+    for (int e = 0; e < 27; ++e) {
+      if (e == 13) continue;
+      const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
+      if (single && (dx != 0) + (dy != 0) + (dz != 0) != 1) continue;
+      const int u = slot_of(i + dx, j + dy, k + dz);
+      if (u < 0 || row[u] < 0) continue;
+      double v;
+      if (single) {
+        const int ax = dx ? 0 : (dy ? 1 : 2);
+        v = hop[(size_t)ax * S + (dx + dy + dz > 0 ? s : u)];
+      } else {
+        v = hop[(size_t)e * S + s];
       }
-    } else {
-      for (int e = 0; e < 27; ++e) {
-        int u = slot_of(i + e % 3 - 1, j + (e / 3) % 3 - 1, k + e / 9 - 1);
-        if (u < 0 || row[u] < 0) continue;
-        A[(size_t)a * m + row[u]] += hst[(size_t)e * S + s];
-      }
+      if (v != 0.0) nb.push_back(row[u]);
     }
-  }
-  // diagnostics: SPFD_DUMP_COARSEST=<path> writes m (int32) and the
-  // assembled coarsest matrix (m x m FP64, row-major) before regularisation
-  if (const char *dump = getenv("SPFD_DUMP_COARSEST")) {
-    if (FILE *f = fopen(dump, "wb")) {
-      fwrite(&m, sizeof(int), 1, f);
-      fwrite(A, sizeof(double), (size_t)m * m, f);
-      fclose(f);
-    }
-  }
+  };
   // connected components of the coarsest graph
   std::vector<int> cc(m, -1), queue;
   int nc = 0;
@@ -278,27 +270,28 @@ static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
     queue.assign(1, a);
     cc[a] = nc;
     for (size_t hd = 0; hd < queue.size(); ++hd) {
-      const int u = queue[hd];
-      for (int v = 0; v < m; ++v)
-        if (v != u && cc[v] < 0 && A[(size_t)u * m + v] != 0.0) {
+      couplings(queue[hd]);
+      for (int v : nb)
+        if (cc[v] < 0) {
           cc[v] = nc;
           queue.push_back(v);
         }
     }
     ++nc;
   }
-  std::vector<double> dsum(nc, 0.0);
+  // mu_c / n_c per component from the dense diagonal (as the device
+  // assembles it), and the diagonal shift
+  std::vector<double> dsum(nc, 0.0), mu(nc);
   std::vector<int> cnt(nc, 0);
-  for (int a = 0; a < m; ++a) { dsum[cc[a]] += A[(size_t)a * m + a]; cnt[cc[a]]++; }
-  std::vector<double> mu(nc);  // mu_c / n_c, formed once per component
-  for (int q = 0; q < nc; ++q) mu[q] = (dsum[q] / cnt[q]) / cnt[q];
+  double dmean = 0.0;
   for (int a = 0; a < m; ++a) {
-    double *Ar = A + (size_t)a * m;
-    const int q = cc[a];
-    const double add = mu[q];
-    for (int b2 = 0; b2 < m; ++b2)
-      if (cc[b2] == q) Ar[b2] += add;
+    const int s = idx[a];
+    dsum[cc[a]] += single ? hdiag[s] : 0.0 + hop[(size_t)13 * S + s];
+    cnt[cc[a]]++;
+    dmean += hdiag[s];
   }
+  for (int q = 0; q < nc; ++q) mu[q] = (dsum[q] / cnt[q]) / cnt[q];
+  dmean /= m;
   // The coarsest Galerkin operator is numerically singular beyond the
   // component constants: coarse basis functions at the conducting boundary
   // can be nearly dependent (on the 2 mm body, 46 of 481 eigenvalues lie
@@ -312,30 +305,56 @@ static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
   // diagonal leaves the tiny ghost rows unregularised: on a 96x96x256 body
   // the condition number stayed at 2e11 and elimination met a negative
   // pivot.)
-  double dmean = 0.0;
-  for (int a = 0; a < m; ++a) dmean += hdiag[idx[a]];
-  dmean /= m;
-  for (int a = 0; a < m; ++a) A[(size_t)a * m + a] += 1e-8 * dmean;
-  TRY(dalloc(c, &c->cidx, m));
-  int *hidx = nullptr;
-  TRY(halloc(c, &hidx, m));
-  memcpy(hidx, idx.data(), m * sizeof(int));
-  TRY(h2d(c, c->cidx, hidx, m * sizeof(int)));
+  const double shift = 1e-8 * dmean;
+  TableUpload up;
+  const int *d_rowof = nullptr, *d_cc = nullptr, *d_idx = nullptr;
+  const double *d_mu = nullptr;
+  up.add(idx, &d_idx);
+  up.add(row, &d_rowof);
+  up.add(cc, &d_cc);
+  up.add(mu, &d_mu);
+  TRY(up.run(c));
+  c->cidx = const_cast<int *>(d_idx);
+  double *b0 = nullptr;
+  TRY(dalloc(c, &b0, (size_t)m * m));
+  CU(cudaMemsetAsync(b0, 0, (size_t)m * m * sizeof(double), c->stream));
+  // diagnostics: SPFD_DUMP_COARSEST=<path> writes m (int32) and the
+  // assembled coarsest matrix (m x m FP64, row-major) before regularisation
+  if (const char *dump = getenv("SPFD_DUMP_COARSEST")) {
+    launch_coarse_dense(g, single ? lv.gx : lv.st, !single, S,
+                        lv.diag, d_idx, d_rowof, m, nullptr, nullptr, 0.0, b0, c->stream);
+    std::vector<double> Ad((size_t)m * m);
+    CU(cudaMemcpyAsync(Ad.data(), b0, Ad.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    TRY(sync_check(c, "coarsest dump"));
+    if (FILE *f = fopen(dump, "wb")) {
+      fwrite(&m, sizeof(int), 1, f);
+      fwrite(Ad.data(), sizeof(double), Ad.size(), f);
+      fclose(f);
+    }
+  }
+  launch_coarse_dense(g, single ? lv.gx : lv.st, !single, S, lv.diag, d_idx, d_rowof, m, d_cc,
+                      d_mu, shift, b0, c->stream);
+  c->launch_count += 2;
+  TRY(launch_check("coarsest assembly"));
   clk.mark("coarsest assembly");
   if (m <= 64) {  // small: invert on the host
+    double *A = nullptr;
+    TRY(halloc(c, &A, (size_t)m * m));
+    CU(cudaMemcpyAsync(A, b0, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    TRY(sync_check(c, "coarsest matrix"));
     std::vector<double> As(A, A + (size_t)m * m);
     if (!invert_spd(As, m))
       return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
-    TRY(dalloc(c, &c->Binv, (size_t)m * m));
     memcpy(A, As.data(), (size_t)m * m * sizeof(double));
-    TRY(h2d(c, c->Binv, A, (size_t)m * m * sizeof(double)));
+    TRY(h2d(c, b0, A, (size_t)m * m * sizeof(double)));
+    c->Binv = b0;
     return sync_check(c, "coarsest upload");
   }
   // larger: Gauss-Jordan sweeps on the device (ping-pong between two buffers)
-  double *b0 = nullptr, *b1 = nullptr;
-  TRY(dalloc(c, &b0, (size_t)m * m));
+  double *b1 = nullptr;
   TRY(dalloc(c, &b1, (size_t)m * m));
-  TRY(h2d(c, b0, A, (size_t)m * m * sizeof(double)));
   double *inv = nullptr;
   unsigned *bar = nullptr;
   TRY(dalloc(c, &bar, 2));
@@ -597,8 +616,12 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     }
     SPFD_LAUNCH(c, "setup_interp", false, 3, 0, 0,
                 launch_interp_weights(f.g, f.gx, f.st, f.diag, f.Pc, st));
+    unsigned *bits = nullptr;  // the coarse level's activity bits, written with P
+    TRY(dalloc(c, &bits, (size_t)std::max(cl.g.nb, 1) * 16));
     SPFD_LAUNCH(c, "setup_galerkin", false, 3, 0, 0,
-                launch_galerkin(f.g, cl.g, f.gx, f.st, f.diag, f.Pc, Ttmp, cl.st, cl.P, st));
+                launch_galerkin(f.g, cl.g, f.gx, f.st, f.diag, f.Pc, Ttmp, cl.st, cl.P, bits,
+                                st));
+    cl.g.act = bits;
     // Rows below 1e-13 of the level's largest diagonal are not unknowns:
     // they come only from basis functions constant on a tiny component.
     unsigned long long *ls = lstat + 4 * (l + 1);
@@ -670,17 +693,6 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   dfree(c, c->L.back().Pc);
   clk.mark("coarse levels");
 
-  // activity bits of the 27-point levels, from their interpolation columns
-  // (a superset of their nonzero rows)
-  for (size_t l = 1; l < c->L.size(); ++l) {
-    Level &lv = c->L[l];
-    unsigned *bits = nullptr;
-    TRY(dalloc(c, &bits, (size_t)std::max(lv.g.nb, 1) * 16));
-    SPFD_LAUNCH(c, "setup_pack", false, 1, 216.0 * lv.S, 0,
-                launch_act_bits(lv.g.nb, lv.P, 27, bits, st));
-    lv.g.act = bits;
-  }
-  TRY(launch_check("activity bits"));
 
   // smoother weights (weighted Jacobi): level 0 has D^-1 A the random-walk
   // Laplacian of a bipartite node graph, so lambda_max = 2 exactly and

@@ -21,7 +21,10 @@
 // Every kernel maps thread t of a block to class t >> 6 and cell t & 63 and
 // dispatches on the class at compile time, so the stencil offsets, the
 // parents touched and the accumulator indices are constants and the
-// accumulators stay in registers.
+// accumulators stay in registers.  Zero tests
+// of coefficients and weights look at bit patterns (f64_nonzero): on GB300 an
+// FP64 comparison takes a slot of the narrow FP64 pipe, as a multiply-add
+// does.
 #include "spfd_internal.cuh"
 
 namespace spfd {
@@ -119,7 +122,7 @@ __device__ __forceinline__ void interp_node(const LevelOp &A, double *__restrict
   double w[NW];
 #pragma unroll
   for (int r = 0; r < NW; ++r) w[r] = 0.0;
-  if (dg > 0.0) {
+  if (f64_nonzero(dg)) {  // dg >= 0
     if (Q == 0) {
       w[0] = 1.0;
     } else {
@@ -141,7 +144,7 @@ __device__ __forceinline__ void interp_node(const LevelOp &A, double *__restrict
         const int px = p % 3 - 1, py = (p / 3) % 3 - 1, pz = p / 9 - 1;
         if (p == 13 || (!UX && px) || (!UY && py) || (!UZ && pz)) continue;
         const double a = ac[p];
-        if (a == 0.0) continue;
+        if (!f64_nonzero(a)) continue;
         if (i + px >= g.NX || j + py >= g.NY || k + pz >= g.NZ) continue;
         // the neighbour is even where p is non-zero; its cell is ours moved
         // by one on the axes where p = +1
@@ -154,7 +157,8 @@ __device__ __forceinline__ void interp_node(const LevelOp &A, double *__restrict
         } else {
           const long long mc = cell_col(g, b, cx + MX, cy + MY, cz + MZ);
           bool stored = false;
-          if (mc >= 0) stored = A.diag[cell_slot(mc, MQ & 1, (MQ >> 1) & 1, MQ >> 2)] > 0.0;
+          if (mc >= 0)
+            stored = f64_nonzero(A.diag[cell_slot(mc, MQ & 1, (MQ >> 1) & 1, MQ >> 2)]);
 #pragma unroll
           for (int r = 0; r < 8; ++r) wm[r] = 1.0 / NWM;
           if (stored) {
@@ -235,7 +239,7 @@ __device__ __forceinline__ void ap_node(const LevelOp &A, const double *__restri
       if (!in_stencil(K27, e)) continue;
       const int ex = e % 3 - 1, ey = (e / 3) % 3 - 1, ez = e / 9 - 1;
       const double a = coef<K27>(A, e, s, b, cx, cy, cz, UX, UY, UZ);
-      if (a == 0.0) continue;
+      if (!f64_nonzero(a)) continue;
       const int mux = (UX + ex) & 1, muy = (UY + ey) & 1, muz = (UZ + ez) & 1;
       const int dcx = (UX + ex) >> 1, dcy = (UY + ey) >> 1, dcz = (UZ + ez) >> 1;
       const int MQ = mux | (muy << 1) | (muz << 2);
@@ -290,7 +294,7 @@ __device__ __forceinline__ void ptap_layer(const Grid &gf, const Grid &gc, size_
                                            const double *__restrict__ T, double *__restrict__ P,
                                            const int *kid, size_t Sc, size_t s, int X, int Y,
                                            int Z, int I, int J, int K, bool valid,
-                                           double (&acc)[14]) {
+                                           double (&acc)[14], bool &any) {
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     const int d = (DZ + 1) * 9 + j;
@@ -308,7 +312,8 @@ __device__ __forceinline__ void ptap_layer(const Grid &gf, const Grid &gc, size_
       w = Pc[(size_t)(pc_off(U) + crank(U, O)) * NCf + col];
     }
     P[(size_t)d * Sc + s] = w;
-    if (w != 0.0) {
+    any |= f64_nonzero(w);
+    if (f64_nonzero(w)) {
 #pragma unroll
       for (int D = 13; D < 27; ++D) {
         const int Dx = D % 3 - 1, Dy = (D / 3) % 3 - 1, Dz = D / 9 - 1;
@@ -321,9 +326,12 @@ __device__ __forceinline__ void ptap_layer(const Grid &gf, const Grid &gc, size_
   }
 }
 
+// Each also writes the coarse level's activity bits (Grid::act): the bit of
+// a coarse node is set when one of its 27 weights P[d] is not zero.
 __global__ void __launch_bounds__(NT)
 k_ptap(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
-       const double *__restrict__ T, double *__restrict__ stc, double *__restrict__ P) {
+       const double *__restrict__ T, double *__restrict__ stc, double *__restrict__ P,
+       unsigned *__restrict__ act) {
   __shared__ int kid[27];
   const int b = blockIdx.x, t = threadIdx.x;
   if (t < 27) kid[t] = gc.kid[(size_t)b * 27 + t];
@@ -336,11 +344,14 @@ k_ptap(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
   double acc[14];
 #pragma unroll
   for (int r = 0; r < 14; ++r) acc[r] = 0.0;
-  ptap_layer<-1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
-  ptap_layer<0>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
-  ptap_layer<1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
+  bool any = false;
+  ptap_layer<-1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc, any);
+  ptap_layer<0>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc, any);
+  ptap_layer<1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc, any);
 #pragma unroll
   for (int r = 0; r < 14; ++r) stc[(size_t)(13 + r) * Sc + s] = acc[r];
+  const unsigned word = __ballot_sync(0xffffffffu, any);
+  if ((t & 31) == 0) act[(size_t)b * 16 + (t >> 5)] = word;
 }
 
 // The same for small coarse levels, where one thread per coarse node leaves
@@ -350,9 +361,11 @@ k_ptap(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
 constexpr int PT_Q = 128;
 __global__ void __launch_bounds__(3 * PT_Q)
 k_ptap3(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
-        const double *__restrict__ T, double *__restrict__ stc, double *__restrict__ P) {
+        const double *__restrict__ T, double *__restrict__ stc, double *__restrict__ P,
+        unsigned *__restrict__ act) {
   __shared__ int kid[27];
   __shared__ double red[2][PT_Q][15];
+  __shared__ bool anyp[2][PT_Q];
   const int b = blockIdx.x >> 2;
   const int part = threadIdx.x / PT_Q, nl = threadIdx.x % PT_Q;
   const int t = (blockIdx.x & 3) * PT_Q + nl;
@@ -366,17 +379,27 @@ k_ptap3(Grid gf, Grid gc, size_t NCf, const double *__restrict__ Pc,
   double acc[14];
 #pragma unroll
   for (int r = 0; r < 14; ++r) acc[r] = 0.0;
-  if (part == 0) ptap_layer<-1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
-  else if (part == 1) ptap_layer<0>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
-  else ptap_layer<1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc);
-  if (part > 0)
+  bool any = false;
+  if (part == 0)
+    ptap_layer<-1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc, any);
+  else if (part == 1)
+    ptap_layer<0>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc, any);
+  else
+    ptap_layer<1>(gf, gc, NCf, Pc, T, P, kid, Sc, s, X, Y, Z, I, J, K, valid, acc, any);
+  if (part > 0) {
 #pragma unroll
     for (int r = 0; r < 14; ++r) red[part - 1][nl][r] = acc[r];
+    anyp[part - 1][nl] = any;
+  }
   __syncthreads();
-  if (part == 0)
+  if (part == 0) {
 #pragma unroll
     for (int r = 0; r < 14; ++r)
       stc[(size_t)(13 + r) * Sc + s] = (acc[r] + red[0][nl][r]) + red[1][nl][r];
+    // part 0 is threads 0 .. PT_Q-1: whole warps, slots t in warp order
+    const unsigned word = __ballot_sync(0xffffffffu, any || anyp[0][nl] || anyp[1][nl]);
+    if ((nl & 31) == 0) act[(size_t)b * 16 + (t >> 5)] = word;
+  }
 }
 
 // A_c(I, I + D) = A_c(I + D, I) for the 13 offsets with sidx(D) < 13.
@@ -420,14 +443,14 @@ void launch_interp_weights(const Grid &gf, const double *gx, const double *st27,
 
 void launch_galerkin(const Grid &gf, const Grid &gc, const double *gx,
                      const double *st27f, const double *diagf, const double *Pc,
-                     double *T, double *stc, double *P, cudaStream_t st) {
+                     double *T, double *stc, double *P, unsigned *act, cudaStream_t st) {
   if (gf.nb == 0 || gc.nb == 0) return;
   const LevelOp A{gf, gx, st27f, diagf, (size_t)gf.nb * BV, (size_t)gf.nb * 64};
   if (st27f) k_ap<true><<<gf.nb, NT, 0, st>>>(A, Pc, T);
   else k_ap<false><<<gf.nb, NT, 0, st>>>(A, Pc, T);
   // below a few waves of one-brick blocks, three threads per coarse node
-  if (gc.nb < 1024) k_ptap3<<<gc.nb * 4, 3 * PT_Q, 0, st>>>(gf, gc, A.NC, Pc, T, stc, P);
-  else k_ptap<<<gc.nb, NT, 0, st>>>(gf, gc, A.NC, Pc, T, stc, P);
+  if (gc.nb < 1024) k_ptap3<<<gc.nb * 4, 3 * PT_Q, 0, st>>>(gf, gc, A.NC, Pc, T, stc, P, act);
+  else k_ptap<<<gc.nb, NT, 0, st>>>(gf, gc, A.NC, Pc, T, stc, P, act);
   k_mirror<<<gc.nb, NT, 0, st>>>(gc, stc);
 }
 

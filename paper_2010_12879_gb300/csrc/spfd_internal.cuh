@@ -127,6 +127,41 @@ __device__ __forceinline__ bool weight_pos(T w) {
   else return w > T(0);
 }
 
+// An FP64 value (bits u) rounded to nearest even to the format with 8
+// exponent bits and P stored significand bits: binary32 (P = 23) or bfloat16
+// (P = 7), returned as that format's bits.  Integer operations only, from
+// the IEEE 754 encodings: GB300 issues its hardware conversions from FP64 on
+// the narrow FP64 pipe, which the kernels running beside the build's
+// conversions need.  Overflow gives infinity, NaN stays a (quiet) NaN, and
+// results below the smallest normal are subnormal or zero, as the hardware
+// conversion gives them.
+template <int P>
+__host__ __device__ __forceinline__ unsigned narrow_f64_bits(unsigned long long u) {
+  constexpr int D = 52 - P;  // dropped significand bits of a normal result
+  const unsigned sign = (unsigned)(u >> 63) << (8 + P);
+  const int e = (int)((u >> 52) & 0x7ff);
+  const unsigned long long m = u & ((1ull << 52) - 1ull);
+  constexpr unsigned INF = 0xffu << P;
+  if (e == 0x7ff) return sign | INF | (m ? ((1u << (P - 1)) | (unsigned)(m >> D)) : 0u);
+  const int E = e - 896;  // the target's biased exponent (bias 127 against 1023)
+  if (E >= 0xff) return sign | INF;
+  unsigned long long sig, q;
+  int shift;
+  if (E > 0) {
+    sig = m;
+    shift = D;
+  } else {  // subnormal target: units of 2^(-126 - P)
+    sig = (e ? (1ull << 52) : 0ull) | m;
+    shift = 949 - P - (e ? e : 1);
+    if (shift >= 64) return sign;
+  }
+  q = sig >> shift;
+  const unsigned long long rem = sig & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;
+  // a carry out of the significand moves into the exponent field, as it should
+  return sign | ((E > 0 ? (unsigned)E << P : 0u) + (unsigned)q);
+}
+
 // Active-slot compaction of one brick of a 27-point level.  The block that
 // handles brick bk gives its n-th thread the brick's n-th active slot (set
 // activity bit, in slot order), so warps past the brick's active count skip
@@ -249,7 +284,9 @@ enum : int {
 // start at zero and are left so after every barrier, so one pair serves
 // every launch on a stream.  The wait is bounded: after GRID_SPIN_LIMIT
 // polls (far beyond any real wait) it sets DEV_GRID_WAIT and goes on, so the
-// caller fails with an error instead of hanging.
+// caller fails with an error instead of hanging.  (Polling gen with acquire
+// loads and a shorter sleep instead of atomics made the coarsest inverse
+// slower.)
 constexpr long long GRID_SPIN_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks,
@@ -279,9 +316,6 @@ __device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, uns
 
 // ---------------------------------------------------------------- launchers
 // Setup (spfd_setup.cu)
-// Activity bits of a level (Grid::act): bit of slot s = any of the n arrays
-// src[e * S + s] (e < n) is nonzero.
-void launch_act_bits(int nb, const double *src, int n, unsigned *bits, cudaStream_t st);
 void launch_sigma_flags(const double *sigma, int nx, int ny, int nz, int MX,
                         int MY, unsigned char *flags, unsigned char *mask,
                         int *status, cudaStream_t st);
@@ -315,9 +349,11 @@ void launch_comp_sizes(const Grid &g, const int *comp, int *sizes,
 int ap_rows_per_cell();
 void launch_interp_weights(const Grid &gf, const double *gx, const double *st27,
                            const double *diag, double *Pc, cudaStream_t st);
+// act: the coarse level's activity bits ([gc.nb][16], see Grid::act), written
+// with P.
 void launch_galerkin(const Grid &gf, const Grid &gc, const double *gx,
                      const double *st27f, const double *diagf, const double *Pc,
-                     double *T, double *stc, double *P, cudaStream_t st);
+                     double *T, double *stc, double *P, unsigned *act, cudaStream_t st);
 // ustat[0] += number of entries > 0 of d[0..n), ustat[1] = max(ustat[1], bits
 // of the largest entry) (non-negative doubles order like their bit patterns).
 void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
@@ -326,8 +362,16 @@ void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
 // bits are *maxbits, as written by launch_diag_stats), else 0; dinv = 1/diag.
 void launch_coarse_diag(const Grid &gc, const double *stc, const unsigned long long *maxbits,
                         double rel, double *diag, double *dinv, cudaStream_t st);
+// The coarsest level's dense matrix A (m x m, zeroed beforehand) from its
+// operator op (27-point stencil if k27, else 7-point conductances with
+// diag), then, if cc is given, the component shifts mu[cc] and the diagonal
+// shift (see setup_coarsest).
+void launch_coarse_dense(const Grid &g, const double *op, bool k27, size_t S, const double *diag,
+                         const int *idx, const int *rowof, int m, const int *cc,
+                         const double *mu, double shift, double *A, cudaStream_t st);
 // Inverse of the SPD matrix in buf0 (m x m, row-major) by blocked
 // Gauss-Jordan sweeps; returns buf0 or buf1, whichever holds the result.
+// bar: two zeroed unsigned ints.
 double *launch_dense_inverse(double *buf0, double *buf1, int m, int *status, unsigned *bar,
                              cudaStream_t st);
 int dense_inverse_launches(int m);

@@ -866,18 +866,44 @@ k_jacobi_weights(const double *__restrict__ dinv, const Scalars *sc, double marg
 }
 
 // ------------------------------------------------ precision conversions
-// dst = (T) (f * src) elementwise over n values.
-// dst = (T)(f * src); with SCALE false (f = 1, every conversion of the
-// build) the FP64 multiply is skipped: the kernel then issues only the
-// conversion on the FP64 pipe, which is what bounds it on GB300.
+// dst = (T)(f * src) elementwise over n values.  With SCALE false (f = 1,
+// every conversion of the build) the values are read as bit patterns and
+// rounded with integer operations (narrow_f64_bits): no FP64-pipe slot is
+// spent, so the kernel runs at memory speed beside the FP64 work of the
+// build (power iterations, coarsest inverse).
 template <typename T, bool SCALE>
 __global__ void k_convert(size_t n, const double *__restrict__ src, double f,
                           T *__restrict__ dst) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const double v = SCALE ? f * src[i] : src[i];
-    if constexpr (sizeof(T) == 2) dst[i] = __double2bfloat16(v);
-    else dst[i] = (T)v;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if constexpr (SCALE) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double v = f * src[i];
+      if constexpr (sizeof(T) == 2) dst[i] = __double2bfloat16(v);
+      else dst[i] = (T)v;
+    }
+  } else {
+    // pairs: 16-byte loads (src and dst come from the allocator, 256-byte
+    // aligned), then the odd last value
+    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
+    const size_t n2 = n / 2;
+#pragma unroll 4
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
+      const ulonglong2 u = __ldcs(&s2[i]);
+      if constexpr (sizeof(T) == 2) {
+        const unsigned lo = narrow_f64_bits<7>(u.x), hi = narrow_f64_bits<7>(u.y);
+        reinterpret_cast<unsigned *>(dst)[i] = lo | (hi << 16);
+      } else {
+        reinterpret_cast<float2 *>(dst)[i] = make_float2(__uint_as_float(narrow_f64_bits<23>(u.x)),
+                                                         __uint_as_float(narrow_f64_bits<23>(u.y)));
+      }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned long long u = reinterpret_cast<const unsigned long long *>(src)[n - 1];
+      if constexpr (sizeof(T) == 2)
+        dst[n - 1] = __ushort_as_bfloat16((unsigned short)narrow_f64_bits<7>(u));
+      else
+        dst[n - 1] = __uint_as_float(narrow_f64_bits<23>(u));
+    }
   }
 }
 

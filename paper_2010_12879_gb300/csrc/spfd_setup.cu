@@ -269,19 +269,20 @@ k_uf_local(Grid g, const double *__restrict__ gx, int *parent, int *status) {
   const size_t s = (size_t)b * BV + t;
   const int4 bc = g.bco[b];
   const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
-  const bool ex = gx[s] > 0, ey = gx[S + s] > 0, ez = gx[2 * S + s] > 0;
+  const bool ex = f64_nonzero(gx[s]), ey = f64_nonzero(gx[S + s]),
+             ez = f64_nonzero(gx[2 * S + s]);
   bool act = ex || ey || ez;
   if (!act) {
     const int m = slot_nb(g, b, bc, lx, ly, lz, -1, 0, 0);
-    act = m >= 0 && gx[m] > 0;
+    act = m >= 0 && f64_nonzero(gx[m]);
   }
   if (!act) {
     const int m = slot_nb(g, b, bc, lx, ly, lz, 0, -1, 0);
-    act = m >= 0 && gx[S + m] > 0;
+    act = m >= 0 && f64_nonzero(gx[S + m]);
   }
   if (!act) {
     const int m = slot_nb(g, b, bc, lx, ly, lz, 0, 0, -1);
-    act = m >= 0 && gx[2 * S + m] > 0;
+    act = m >= 0 && f64_nonzero(gx[2 * S + m]);
   }
   lp[t] = act ? t : -1;
   __syncthreads();
@@ -306,15 +307,15 @@ k_uf_union(Grid g, const double *__restrict__ gx, int *parent, int *status) {
   const int s = b * BV + t;
   const int4 bc = g.bco[b];
   int capped = 0;
-  if (lx == 7 && gx[s] > 0) {
+  if (lx == 7 && f64_nonzero(gx[s])) {
     const int m = slot_nb(g, b, bc, lx, ly, lz, 1, 0, 0);
     if (m >= 0) uf_unite(parent, s, m, &capped);
   }
-  if (ly == 7 && gx[S + s] > 0) {
+  if (ly == 7 && f64_nonzero(gx[S + s])) {
     const int m = slot_nb(g, b, bc, lx, ly, lz, 0, 1, 0);
     if (m >= 0) uf_unite(parent, s, m, &capped);
   }
-  if (lz == 7 && gx[2 * S + s] > 0) {
+  if (lz == 7 && f64_nonzero(gx[2 * S + s])) {
     const int m = slot_nb(g, b, bc, lx, ly, lz, 0, 0, 1);
     if (m >= 0) uf_unite(parent, s, m, &capped);
   }
@@ -466,18 +467,82 @@ void launch_diag_stats(const double *d, size_t n, unsigned long long *ustat,
   k_diag_stats<<<(int)blocks, NT, 0, st>>>(d, n, ustat);
 }
 
+// ------------------------------------------------ coarsest dense matrix
+// The dense matrix of the coarsest level's m unknowns (slots idx[a], row of
+// slot u rowof[u] or -1), into A (zeroed beforehand), entry by entry as the
+// operator stores it: 27-point levels A[a][rowof[u]] = 0 + st[e][idx[a]] for
+// the neighbour u at offset e; the 7-point level (a single-level hierarchy)
+// A[a][a] = diag and A[a][rowof[u]] = 0 - g for the six edges.
+template <bool K27>
+__global__ void k_coarse_scatter(Grid g, const double *__restrict__ op, size_t S,
+                                 const double *__restrict__ diag, const int *__restrict__ idx,
+                                 const int *__restrict__ rowof, int m, double *__restrict__ A) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 27LL * m) return;
+  const int a = (int)(q / 27), e = (int)(q % 27);
+  const int s = idx[a], b = s / BV, t = s % BV;
+  const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
+  if (!K27 && e == 13) {
+    A[(size_t)a * m + a] = diag[s];
+    return;
+  }
+  if (!K27 && (dx != 0) + (dy != 0) + (dz != 0) != 1) return;
+  const int4 bc = g.bco[b];
+  const int u = e == 13 ? s : slot_nb(g, b, bc, t & 7, (t >> 3) & 7, t >> 6, dx, dy, dz);
+  if (u < 0) return;
+  const int col = rowof[u];
+  if (col < 0) return;
+  if (K27) {
+    A[(size_t)a * m + col] = 0.0 + op[(size_t)e * S + s];
+  } else {
+    const int ax = dx ? 0 : (dy ? 1 : 2);
+    const double ge = dx + dy + dz > 0 ? op[(size_t)ax * S + s] : op[(size_t)ax * S + u];
+    A[(size_t)a * m + col] = 0.0 - ge;
+  }
+}
+
+// A[a][b] += mu[cc[a]] when a and b lie in one component of the coarsest
+// graph, then A[a][a] += shift.
+__global__ void k_coarse_regularise(double *__restrict__ A, int m, const int *__restrict__ cc,
+                                    const double *__restrict__ mu, double shift) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)m * m) return;
+  const int a = (int)(q / m), b = (int)(q % m);
+  double v = A[q];
+  if (cc[a] == cc[b]) v += mu[cc[a]];
+  if (a == b) v += shift;
+  A[q] = v;
+}
+
+void launch_coarse_dense(const Grid &g, const double *op, bool k27, size_t S, const double *diag,
+                         const int *idx, const int *rowof, int m, const int *cc,
+                         const double *mu, double shift, double *A, cudaStream_t st) {
+  if (m <= 0) return;
+  const unsigned nb1 = (unsigned)((27LL * m + 255) / 256);
+  if (k27) k_coarse_scatter<true><<<nb1, 256, 0, st>>>(g, op, S, diag, idx, rowof, m, A);
+  else k_coarse_scatter<false><<<nb1, 256, 0, st>>>(g, op, S, diag, idx, rowof, m, A);
+  if (cc)
+    k_coarse_regularise<<<(unsigned)(((long long)m * m + 255) / 256), 256, 0, st>>>(A, m, cc, mu,
+                                                                                    shift);
+}
+
 // ------------------------------------------------ coarsest dense inverse
-// Blocked Gauss-Jordan inversion of an SPD matrix (m x m, row-major).  One
-// launch sweeps the pivot set K = k0 .. k0+r-1 (r <= GJ_B) at once, reading
-// the current matrix M from A and writing B (a principal pivot transform):
+// Blocked Gauss-Jordan inversion of an SPD matrix (m x m, row-major).  A
+// sweep takes the pivot set K = k0 .. k0+r-1 (r <= GJ_B) at once, reading
+// the current matrix M and writing B (a principal pivot transform):
 //   B[K,K] = D^-1,  B[K,j] = D^-1 M[K,j],  B[i,K] = -M[i,K] D^-1,
 //   B[i,j] = M[i,j] - M[i,K] D^-1 M[K,j]   (i, j not in K),  D = M[K,K].
-// After every pivot set has been swept once, B = A^-1.  Every block inverts
-// D itself (scalar Gauss-Jordan in shared memory): its pivots are Schur
-// complements of the SPD matrix, hence positive; a non-positive one raises
-// DEV_BAD_PIVOT.  The block then forms D^-1 M[K, its columns] once and
-// updates its GJ_T x GJ_T tile.
-constexpr int GJ_B = 16;   // pivots per launch
+// After every pivot set has been swept once, B = A^-1.  D is inverted by
+// scalar Gauss-Jordan in shared memory: its pivots are Schur complements of
+// the SPD matrix, hence positive; a non-positive one raises DEV_BAD_PIVOT.
+// Every block inverts D itself, forms W = D^-1 M[K, its columns] and
+// updates its GJ_T x GJ_T tile; sweeps run one launch each (k_gj_block) or
+// all in one cooperative launch with a grid barrier between them (k_gj_all).
+// (Forming D^-1 and W once per column tile in a first phase of each sweep
+// halves the FP64 work, but its second grid barrier per sweep made the
+// inversion of the 2 mm body's 481 x 481 coarsest matrix slower: the sweeps
+// are bound by latency, not by the FP64 pipe.)
+constexpr int GJ_B = 16;   // pivots per sweep
 constexpr int GJ_T = 32;   // tile edge
 constexpr int GJ_NT = 256; // threads per block (GJ_B * GJ_B)
 
@@ -489,44 +554,57 @@ struct GjShared {
   double pinv[2];
 };
 
-// One sweep of the pivot set k0 .. k0+r-1 by this block's tile.  COH: read
-// A through L2 only (ld.global.cg), as the single-launch form must: A was
-// written by other blocks in the same launch, and a line of it cached in
-// this SM's L1 by an earlier sweep would be stale.
+// COH: read through L2 only (ld.global.cg), as the single-launch form must:
+// what it reads was written by other blocks in the same launch, and a line
+// cached in this SM's L1 by an earlier sweep would be stale.
 template <bool COH>
 __device__ __forceinline__ double gj_ld(const double *p) {
   if constexpr (COH) return __ldcg(p);
   else return *p;
 }
 
+// D = M[K,K] (identity-padded to GJ_B) into sh.D[0] and its first pivot's
+// reciprocal, and C = M[K, column tile j0] into sh.C.  A barrier follows.
 template <bool COH>
-__device__ __forceinline__ void gj_sweep(GjShared &sh, const double *__restrict__ A,
-                                         double *__restrict__ B, int m, int k0, int r,
-                                         int *status) {
-  auto &D = sh.D;
-  auto &W = sh.W;
-  auto &U = sh.U;
-  auto &C = sh.C;
-  auto &pinv = sh.pinv;
+__device__ __forceinline__ void gj_load_pivot_rows(GjShared &sh, const double *__restrict__ A,
+                                                   int m, int k0, int r, int j0, int *status) {
   const int t = threadIdx.x;
-  const int i0 = blockIdx.y * GJ_T, j0 = blockIdx.x * GJ_T;
   const int a = t / GJ_B, b = t % GJ_B;
-  const double d0 = (a < r && b < r) ? gj_ld<COH>(&A[(size_t)(k0 + a) * m + k0 + b]) : (a == b ? 1.0 : 0.0);
-  D[0][a][b] = d0;
+  const double d0 =
+      (a < r && b < r) ? gj_ld<COH>(&A[(size_t)(k0 + a) * m + k0 + b]) : (a == b ? 1.0 : 0.0);
+  sh.D[0][a][b] = d0;
   if (t == 0) {
     if (!(d0 > 0.0)) atomicOr(status, DEV_BAD_PIVOT);
-    pinv[0] = d0 > 0.0 ? 1.0 / d0 : 0.0;
+    sh.pinv[0] = d0 > 0.0 ? 1.0 / d0 : 0.0;
   }
   for (int q = t; q < GJ_T * GJ_B; q += GJ_NT) {
-    const int ii = q / GJ_B, l = q % GJ_B;
-    U[ii][l] = (l < r && i0 + ii < m) ? gj_ld<COH>(&A[(size_t)(i0 + ii) * m + k0 + l]) : 0.0;
     const int l2 = q / GJ_T, jj = q % GJ_T;
-    C[l2][jj] = (l2 < r && j0 + jj < m) ? gj_ld<COH>(&A[(size_t)(k0 + l2) * m + j0 + jj]) : 0.0;
+    sh.C[l2][jj] =
+        (l2 < r && j0 + jj < m) ? gj_ld<COH>(&A[(size_t)(k0 + l2) * m + j0 + jj]) : 0.0;
   }
-  __syncthreads();
-  // D <- D^-1, one pivot per step, ping-pong between D[0] and D[1]: the
-  // thread that forms the next pivot also writes its reciprocal, so a step
-  // needs a single barrier
+}
+
+// U = M[tile rows i0, K] into sh.U.  A barrier follows.
+template <bool COH>
+__device__ __forceinline__ void gj_load_pivot_cols(GjShared &sh, const double *__restrict__ A,
+                                                   int m, int k0, int r, int i0) {
+  for (int q = threadIdx.x; q < GJ_T * GJ_B; q += GJ_NT) {
+    const int ii = q / GJ_B, l = q % GJ_B;
+    sh.U[ii][l] = (l < r && i0 + ii < m) ? gj_ld<COH>(&A[(size_t)(i0 + ii) * m + k0 + l]) : 0.0;
+  }
+}
+
+// D <- D^-1 in shared memory (after a barrier), one pivot per step,
+// ping-pong between D[0] and D[1]: the thread that forms the next pivot also
+// writes its reciprocal, so a step needs a single barrier.  The inverse ends
+// in D[GJ_B & 1] = D[0]; W = D^-1 C then follows (each thread forms the
+// entries (l, jj) and (l + 8, jj), its two sums interleaved, each in its own
+// fixed order), and a barrier.
+__device__ __forceinline__ void gj_invert_pivots(GjShared &sh, int *status) {
+  auto &D = sh.D;
+  auto &pinv = sh.pinv;
+  const int t = threadIdx.x;
+  const int a = t / GJ_B, b = t % GJ_B;
   for (int p = 0; p < GJ_B; ++p) {
     const double(*Dc)[GJ_B + 1] = D[p & 1];
     const double iv = pinv[p & 1];
@@ -543,70 +621,88 @@ __device__ __forceinline__ void gj_sweep(GjShared &sh, const double *__restrict_
     __syncthreads();
   }
   const double(*Dinv)[GJ_B + 1] = D[GJ_B & 1];
-  // W = D^-1 M[K, tile columns]: each thread forms the entries (l, jj) and
-  // (l + 8, jj) with their two sums interleaved (each in its own fixed order)
   static_assert(GJ_B * GJ_T == 2 * GJ_NT && GJ_T * GJ_T == 4 * GJ_NT, "tile shape");
   {
     const int l = t / GJ_T, jj = t % GJ_T;
     double w0 = 0.0, w1 = 0.0;
 #pragma unroll
     for (int l2 = 0; l2 < GJ_B; ++l2) {
-      const double c = C[l2][jj];
+      const double c = sh.C[l2][jj];
       w0 += Dinv[l][l2] * c;
       w1 += Dinv[l + GJ_NT / GJ_T][l2] * c;
     }
-    W[l][jj] = w0;
-    W[l + GJ_NT / GJ_T][jj] = w1;
+    sh.W[l][jj] = w0;
+    sh.W[l + GJ_NT / GJ_T][jj] = w1;
   }
   __syncthreads();
-  // the tile: each thread updates rows ii0 + 8k (k = 0..3) of column jj,
-  // four independent chains, each subtracting its terms in order l = 0..15
-  {
-    constexpr int RS = GJ_NT / GJ_T;  // row stride between a thread's entries
-    const int ii0 = t / GJ_T, jj = t % GJ_T, j = j0 + jj;
-    const bool kj = j >= k0 && j < k0 + r;
-    double v[4];
+}
+
+// The tile (i0, j0) of B from M (A), with D^-1 in sh.D[0], W for the
+// tile's columns in sh.W and U in sh.U: each thread updates rows ii0 + 8k
+// (k = 0..3) of column jj, four independent chains, each subtracting its
+// terms in order l = 0..15.
+template <bool COH>
+__device__ __forceinline__ void gj_update_tile(const GjShared &sh, const double *__restrict__ A,
+                                               double *__restrict__ B, int m, int k0, int r,
+                                               int i0, int j0) {
+  const double(*Dinv)[GJ_B + 1] = sh.D[GJ_B & 1];
+  constexpr int RS = GJ_NT / GJ_T;  // row stride between a thread's entries
+  const int t = threadIdx.x;
+  const int ii0 = t / GJ_T, jj = t % GJ_T, j = j0 + jj;
+  const bool kj = j >= k0 && j < k0 + r;
+  double v[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = i0 + ii0 + RS * k;
-      v[k] = (!kj && i < m && j < m) ? gj_ld<COH>(&A[(size_t)i * m + j]) : 0.0;
-    }
+  for (int k = 0; k < 4; ++k) {
+    const int i = i0 + ii0 + RS * k;
+    v[k] = (!kj && i < m && j < m) ? gj_ld<COH>(&A[(size_t)i * m + j]) : 0.0;
+  }
 #pragma unroll
-    for (int l = 0; l < GJ_B; ++l) {
-      const double mc = kj ? Dinv[l][j - k0] : W[l][jj];
+  for (int l = 0; l < GJ_B; ++l) {
+    const double mc = kj ? Dinv[l][j - k0] : sh.W[l][jj];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) v[k] -= U[ii0 + RS * k][l] * mc;
-    }
+    for (int k = 0; k < 4; ++k) v[k] -= sh.U[ii0 + RS * k][l] * mc;
+  }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int ii = ii0 + RS * k, i = i0 + ii;
-      if (i >= m || j >= m) continue;
-      const bool ki = i >= k0 && i < k0 + r;
-      double out = v[k];
-      if (ki) out = kj ? Dinv[i - k0][j - k0] : W[i - k0][jj];
-      B[(size_t)i * m + j] = out;
-    }
+  for (int k = 0; k < 4; ++k) {
+    const int ii = ii0 + RS * k, i = i0 + ii;
+    if (i >= m || j >= m) continue;
+    const bool ki = i >= k0 && i < k0 + r;
+    double out = v[k];
+    if (ki) out = kj ? Dinv[i - k0][j - k0] : sh.W[i - k0][jj];
+    B[(size_t)i * m + j] = out;
   }
 }
 
+// One sweep per launch: every block forms D^-1 and its W itself.
 __global__ void __launch_bounds__(GJ_NT)
 k_gj_block(const double *__restrict__ A, double *__restrict__ B, int m, int k0, int r,
            int *status) {
   __shared__ GjShared sh;
-  gj_sweep<false>(sh, A, B, m, k0, r, status);
+  const int i0 = blockIdx.y * GJ_T, j0 = blockIdx.x * GJ_T;
+  gj_load_pivot_rows<false>(sh, A, m, k0, r, j0, status);
+  gj_load_pivot_cols<false>(sh, A, m, k0, r, i0);
+  __syncthreads();
+  gj_invert_pivots(sh, status);
+  gj_update_tile<false>(sh, A, B, m, k0, r, i0, j0);
 }
 
-// Every sweep of the blocked Gauss-Jordan inversion in one cooperative
-// launch: the same tiles and arithmetic as the per-sweep launches, with a
-// grid barrier between sweeps (sweep k reads what sweep k-1 wrote).
-// bar[0..1]: barrier counter and generation, zero at launch.
+// Every sweep in one cooperative launch: the same tiles and arithmetic as
+// the per-sweep launches, with a grid barrier between sweeps (sweep k reads
+// what sweep k-1 wrote).  bar[0..1]: barrier counter and generation, zero
+// at launch.
 __global__ void __launch_bounds__(GJ_NT)
 k_gj_all(double *buf0, double *buf1, int m, int *status, unsigned *bar) {
   __shared__ GjShared sh;
   const unsigned nblocks = gridDim.x * gridDim.y;
+  const int i0 = blockIdx.y * GJ_T, j0 = blockIdx.x * GJ_T;
   double *a = buf0, *b = buf1;
   for (int k0 = 0; k0 < m; k0 += GJ_B) {
-    gj_sweep<true>(sh, a, b, m, k0, m - k0 < GJ_B ? m - k0 : GJ_B, status);
+    const int r = m - k0 < GJ_B ? m - k0 : GJ_B;
+    gj_load_pivot_rows<true>(sh, a, m, k0, r, j0, status);
+    gj_load_pivot_cols<true>(sh, a, m, k0, r, i0);
+    __syncthreads();
+    gj_invert_pivots(sh, status);
+    gj_update_tile<true>(sh, a, b, m, k0, r, i0, j0);
     grid_barrier(&bar[0], &bar[1], nblocks, status);
     double *tmp = a; a = b; b = tmp;
   }
@@ -724,20 +820,6 @@ void launch_pull(void *dst, const void *src_mapped, size_t bytes, cudaStream_t s
   k_pull<<<(unsigned)blocks, 256, 0, st>>>(
       (const uint4 *)src_mapped, (uint4 *)dst, n16,
       (const unsigned char *)src_mapped + n16 * 16, (unsigned char *)dst + n16 * 16, ntail);
-}
-
-// ------------------------------------------------------------ activity bits
-__global__ void __launch_bounds__(NT)
-k_act_bits(const double *__restrict__ src, int n, size_t S, unsigned *__restrict__ bits) {
-  const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
-  bool any = false;
-  for (int e = 0; e < n; ++e) any |= src[(size_t)e * S + s] != 0.0;
-  const unsigned w = __ballot_sync(0xffffffffu, any);
-  if ((threadIdx.x & 31) == 0) bits[(size_t)blockIdx.x * 16 + (threadIdx.x >> 5)] = w;
-}
-
-void launch_act_bits(int nb, const double *src, int n, unsigned *bits, cudaStream_t st) {
-  if (nb) k_act_bits<<<nb, NT, 0, st>>>(src, n, (size_t)nb * BV, bits);
 }
 
 __global__ void k_set_f64(double *p, double v) { *p = v; }
