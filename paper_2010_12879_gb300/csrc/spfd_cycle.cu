@@ -16,7 +16,10 @@ namespace spfd {
 
 // ------------------------------------------------------------ smoothers
 // Level 0 (7-point): r = b - A x, and the weighted-Jacobi sweep
-// x_out = x + omega D^-1 (b - A x), on the row mapping.
+// x_out = x + omega D^-1 (b - A x), on the row mapping.  (The level-0 row
+// list that k_apply_dot uses in FP64 made these two slower: they issue
+// fewer FP64 instructions per row, and the extra dependent load of the list
+// entry and the looser brick locality cost more than the skipped rows.)
 template <typename T, typename C, int ORD>
 __global__ void __launch_bounds__(row_threads<T>(), row_min_blocks<T>())
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,

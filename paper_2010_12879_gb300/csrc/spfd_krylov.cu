@@ -99,8 +99,9 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket,
 constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SMs
 
 // ------------------------------------------------------------ CG operator
-// q = A p on one brick per block (row mapping); each warp writes its part
-// of p.q, and k_finish_pq adds them.
+// q = A p on one brick per block (row mapping; FP64: 64 rows of the level-0
+// row list per block); each warp writes its part of p.q, and k_finish_pq
+// adds them.
 template <typename T, int ORD>
 __global__ void __launch_bounds__(row_threads<T>(), row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
@@ -110,12 +111,20 @@ k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
   const int t = threadIdx.x;
-  const size_t S = (size_t)g.nb * BV, s0 = row_slot<N>(bk, t);
+  int br = bk, tl = t;
+  bool live = true;
+  if constexpr (sizeof(T) == 8) row_of_list<8 / N>(g, bk, t, br, tl, live);
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot<N>(br, tl);
   p += (size_t)rhs * S;
   q += (size_t)rhs * S;
   partials += (size_t)rhs * pstride;
   Qv<T, N> pc, qv;
-  apply7_row<T, T, false, N>(g, gx, diag, p, S, bk, t, zqn<T, N>(), pc, qv);
+  if (__any_sync(0xffffffffu, live)) {
+    apply7_row<T, T, false, N>(g, gx, diag, p, S, br, tl, zqn<T, N>(), pc, qv);
+  } else {  // rows without an unknown: A p = 0 there
+    pc = zqn<T, N>();
+    qv = zqn<T, N>();
+  }
   stqn<T, N>(q + s0, qv);
   if constexpr (sizeof(T) == 4) {
     // FP32 products summed without rounding error in (hi, lo) pairs
