@@ -204,7 +204,10 @@ struct PhaseClock {
 // The host reads the level back to number its unknowns and label the
 // components (a breadth-first search over the operator's couplings); the
 // dense matrix is assembled, regularised and inverted on the device.
-static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
+// *spare: a device block the inverse still uses when this returns (the
+// caller frees it once the build's streams are synchronised: kernels on the
+// side streams allocate after this, and must not be handed it meanwhile).
+static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk, double **spare) {
   Level &lv = c->L.back();
   const size_t S = lv.S;
   const bool single = c->L.size() == 1;
@@ -364,7 +367,7 @@ static spfd_status setup_coarsest(spfd_ctx *c, PhaseClock &clk) {
   TRY(launch_check("coarsest inverse"));
   // a non-positive pivot raises DEV_BAD_PIVOT, read at the end of the build
   c->Binv = inv;
-  if (inv == b0) dfree(c, b1); else dfree(c, b0);
+  *spare = inv == b0 ? b1 : b0;
   return SPFD_OK;
 }
 
@@ -714,7 +717,12 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   // omega = 2/3; coarser levels estimate it on the device by power
   // iterations.  Those are independent of one another and of the coarsest
   // inverse, so each runs on a stream of its own (with its own reduction
-  // scratch) while the main stream assembles and inverts the coarsest level.
+  // scratch) while the main stream inverts the coarsest level.  The side
+  // streams fork from the main stream before the coarsest level, but their
+  // kernels are enqueued after the inverse's cooperative launch: launched
+  // first, the inverse takes its SM slots (a quarter of each SM's threads),
+  // and the power iterations fill the rest beside it instead of holding
+  // every SM until they end.
   {
     Level &l0 = c->L[0];
     l0.lmax = 2.0;
@@ -755,6 +763,12 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
     }
     CU(cudaEventCreateWithFlags(&side.e[ns], cudaEventDisableTiming));
     CU(cudaEventRecord(side.e[ns], st));
+  }
+  clk.mark("smoother weights");
+  double *gj_spare = nullptr;
+  TRY(setup_coarsest(c, clk, &gj_spare));
+  clk.mark("coarsest inverse");
+  if (ns > 0) {
     for (int i = 0; i < ns; ++i) {
       CU(cudaStreamCreateWithFlags(&side.s[i], cudaStreamNonBlocking));
       CU(cudaEventCreateWithFlags(&side.e[i], cudaEventDisableTiming));
@@ -776,9 +790,6 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   } else if (mixed) {
     TRY(setup_mixed_level(c, 0));
   }
-  clk.mark("smoother weights");
-  TRY(setup_coarsest(c, clk));
-  clk.mark("coarsest inverse");
   if (mixed && c->L.size() > 1) TRY(setup_mixed_level(c, (int)c->L.size() - 1));
   for (int i = 0; i < ns; ++i) CU(cudaStreamWaitEvent(st, side.e[i], 0));
   dfree(c, psc);
@@ -804,6 +815,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   ++c->launch_count;
   CU(cudaEventRecord(c->ev1, st));
   TRY(sync_check(c, "build"));
+  dfree(c, gj_spare);
   if (c->hsc->status & DEV_BAD_PIVOT)
     return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
   if (c->hsc->status & DEV_GRID_WAIT)
