@@ -504,7 +504,7 @@ spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
     SPFD_LAUNCH(c, "finish_rz", false, 1, 16.0 * jacobi7_rz_partials<T>(nb) * nk, 0,
                 launch_finish_rz(jacobi7_rz_partials<T>(nb), c->partials,
                                  c->partials + (size_t)16 * nb, c->sc, first, st, nk,
-                                 c->pstride));
+                                 c->pstride, f32));
   else
     SPFD_LAUNCH(c, "dot_rz", f32, 1, (2 * w + 4) * S, 3 * S,
                 launch_dot_rz<T>(nb, r, z, c->comp, c->sc, c->partials, first, st, nk,
@@ -600,7 +600,8 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
                                     c->pstride, block_order(c, TF_APPLY, 0)));
     SPFD_LAUNCH(c, "finish_pq", false, 1, 8.0 * nb * na, nb * na,
                 launch_finish_pq(apply_dot_partials<T>(nb), c->partials,
-                                 c->partials + (size_t)16 * nb, c->sc, st, na, c->pstride));
+                                 c->partials + (size_t)16 * nb, c->sc, st, na, c->pstride,
+                                 f32));
     SPFD_LAUNCH(c, "update_xr", f32, 1, 6 * w * S, 7 * S,
                 launch_update_xr<T>(nb, x, r, p, q, c->sc, c->partials, st, na, c->pstride));
     TRY(launch_check("CG update"));

@@ -72,8 +72,8 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
     if ((t & 31) == 0) {
       double *pp = partials + (size_t)rhs * pstride +
                    2 * ((size_t)bk * (BV / N / 32) + (t >> 5));
-      pp[0] = prz.get();
-      pp[1] = pzs.get();
+      prz.put(pp);
+      pzs.put(pp + 1);
     }
   }
 }

@@ -488,7 +488,8 @@ spfd_status capture_solve_mixed(spfd_ctx *c, GraphCtl *ctl, const double *a, dou
                                             c->partials, s3, 1, c->pstride));
         SPFD_LAUNCH(c, "finish_pq", false, 1, 8.0 * nb, nb,
                     launch_finish_pq(apply_dot_partials<float>(nb), c->partials,
-                                     c->partials + (size_t)16 * nb, c->sc, s3, 1, c->pstride));
+                                     c->partials + (size_t)16 * nb, c->sc, s3, 1, c->pstride,
+                                     true));
         SPFD_LAUNCH(c, "update_xr", true, 1, 6 * 4 * S, 7 * S,
                     launch_update_xr<float>(nb, c->dk32, c->rk32, c->pk32, c->qk32, c->sc,
                                             c->partials, s3, 1, c->pstride));

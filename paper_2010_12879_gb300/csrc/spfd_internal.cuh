@@ -441,8 +441,9 @@ void launch_jacobi7_rz(const Grid &g, const C *gx, const T *diag, const T *wdinv
 template <typename T> int jacobi7_rz_partials(int nb);
 // Adds n pairs of partials (scratch: at least 304 doubles, not overlapping)
 // and sets rz, beta, zsum and zmean as launch_dot_rz does.
+// pairs: the partials are FP32 (hi, lo) pairs (FP32 producers).
 void launch_finish_rz(int n, const double *partials, double *scratch, Scalars *sc, int first,
-                      cudaStream_t st, int nk = 1, size_t pstride = 0);
+                      cudaStream_t st, int nk = 1, size_t pstride = 0, bool pairs = false);
 template <typename T>
 void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
                      const T *b, T *xout, cudaStream_t st, int nk = 1, int order = 0);
@@ -466,11 +467,12 @@ void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       T *q, Scalars *sc, double *partials, cudaStream_t st, int nk = 1,
                       size_t pstride = 0, int order = 0);
 // Number of partial sums launch_apply_dot writes for nb bricks (one per warp,
-// 8 per brick in FP64, 4 in FP32); launch_finish_pq adds n of them (scratch: at least 152
-// doubles, not overlapping) and sets alpha = rz / pq.
+// 8 per brick in FP64, 4 in FP32, where each is an FP32 (hi, lo) pair in its
+// 8-byte slot); launch_finish_pq adds n of them (scratch: at least 152
+// doubles, not overlapping; pairs for FP32 partials) and sets alpha = rz / pq.
 template <typename T> int apply_dot_partials(int nb);
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
-                      cudaStream_t st, int nk = 1, size_t pstride = 0);
+                      cudaStream_t st, int nk = 1, size_t pstride = 0, bool pairs = false);
 // x += alpha p, r -= alpha q, r.r, sum r; right-hand sides whose Scalars are
 // frozen are left as they are.
 template <typename T>

@@ -64,15 +64,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   __syncthreads();
 }
 
-// Returns true in thread 0 of the last block, with tot[] = grid totals.
+// The tail of the grid reductions, once thread 0 has written this block's NV
+// partials: a ticket finds the last block, which adds every block's partials
+// in a fixed order.  Returns true in thread 0 of the last block, with tot[] =
+// grid totals.
 template <int NV>
-__device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket,
-                         double (&tot)[NV]) {
+__device__ bool grid_finish(double *partials, unsigned *ticket, double (&tot)[NV]) {
   __shared__ bool last;
-  block_sum<NV>(v);
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) partials[(size_t)blockIdx.x * NV + k] = v[k];
     __threadfence();
     unsigned prev = atomicAdd(ticket, 1u);
     last = prev == gridDim.x - 1;
@@ -92,6 +91,83 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket,
   for (int k = 0; k < NV; ++k) tot[k] = a[k];
   *ticket = 0u;
   return true;
+}
+
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket,
+                         double (&tot)[NV]) {
+  block_sum<NV>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[(size_t)blockIdx.x * NV + k] = v[k];
+  return grid_finish<NV>(partials, ticket, tot);
+}
+
+// hi + lo += oh + ol with the rounding error of the high parts kept (TwoSum).
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float oh, float ol) {
+  const float s = hi + oh, bb = s - hi;
+  const float e = (hi - (s - bb)) + (oh - bb);
+  hi = s;
+  lo = lo + ol + e;
+}
+
+// grid_sum for per-thread FP32 pairs (value hi + lo): the warps and the block
+// add them as TwoSum pairs in FP32, and only the block's total is widened to
+// FP64 (in thread 0).  An FP64 conversion or addition takes a 16-clock slot
+// of GB300's narrow FP64 pipe for its warp whatever its lane mask, so
+// widening in every thread put an FP64 tail of several microseconds at the
+// end of the FP32 reduction kernels.
+template <int NV>
+__device__ bool grid_sum_f32(float (&hi)[NV], float (&lo)[NV], double *partials,
+                             unsigned *ticket, double (&tot)[NV]) {
+  __shared__ float sh[32][NV], sl[32][NV];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      two_sum_add(hi[k], lo[k], __shfl_xor_sync(0xffffffffu, hi[k], o),
+                  __shfl_xor_sync(0xffffffffu, lo[k], o));
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      sh[w][k] = hi[k];
+      sl[w][k] = lo[k];
+    }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float h = lane < nw ? sh[lane][k] : 0.f, l = lane < nw ? sl[lane][k] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        two_sum_add(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+      if (lane == 0) partials[(size_t)blockIdx.x * NV + k] = (double)h + (double)l;
+    }
+  }
+  return grid_finish<NV>(partials, ticket, tot);
+}
+
+// grid_sum of per-thread accumulators: FP64 sums directly, compensated FP32
+// sums (value s - c) as FP32 pairs.
+template <typename T, int NV>
+__device__ bool grid_sum_acc(const Acc<T> (&a)[NV], double *partials, unsigned *ticket,
+                             double (&tot)[NV]) {
+  if constexpr (sizeof(T) == 8) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = a[k].s;
+    return grid_sum<NV>(v, partials, ticket, tot);
+  } else {
+    float h[NV], l[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      h[k] = a[k].s;
+      l[k] = -a[k].c;
+    }
+    return grid_sum_f32<NV>(h, l, partials, ticket, tot);
+  }
 }
 
 // Grid-stride reduction kernels use at most RED_GRID blocks, so the ticket
@@ -134,7 +210,7 @@ k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
 #pragma unroll
     for (int i = 0; i < N; ++i) pq[i] = pc.v[i] * qv.v[i];
     const WarpSum<float> part = warp_total<float, N>(pq);
-    if ((t & 31) == 0) partials[(size_t)bk * (row_threads<T>() / 32) + (t >> 5)] = part.get();
+    if ((t & 31) == 0) part.put(&partials[(size_t)bk * (row_threads<T>() / 32) + (t >> 5)]);
   } else {
     double a = pc.v[0] * qv.v[0];
 #pragma unroll
@@ -152,6 +228,7 @@ int apply_dot_partials(int nb) { return nb * (row_threads<T>() / 32); }
 // pq = sum of the n partials of k_apply_dot (blocks add contiguous chunks,
 // the last block adds the block sums, fixed order); alpha = rz / pq.
 // scratch must not overlap the partials.
+template <bool PAIRS>
 __global__ void __launch_bounds__(NT)
 k_finish_pq(const double *__restrict__ partials, int n, double *scratch, Scalars *sc,
             size_t pstride) {
@@ -160,7 +237,7 @@ k_finish_pq(const double *__restrict__ partials, int n, double *scratch, Scalars
   sc += blockIdx.y;
   double a = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    a += partials[i];
+    a += pair_at<PAIRS>(partials, i);
   double v[1] = {a};
   double tot[1];
   if (grid_sum<1>(v, scratch, &sc->ticket[6], tot)) {
@@ -205,9 +282,9 @@ k_update_xr(int nb, T *__restrict__ x, T *__restrict__ r,
     st16(x + s0, xv);
     st16(r + s0, rv);
   }
-  double v[2] = {rr.get(), rs_sum.get()};
+  const Acc<T> v[2] = {rr, rs_sum};
   double tot[2];
-  if (grid_sum<2>(v, partials, &sc->ticket[1], tot)) {
+  if (grid_sum_acc<T, 2>(v, partials, &sc->ticket[1], tot)) {
     sc->rr = tot[0];
     sc->rsum = tot[1];
     sc->rmean = tot[1] * sc->inv_ndof;
@@ -259,13 +336,14 @@ k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
       if (c[i] >= 0) zsum.add(zv.v[i]);
     }
   }
-  double v[2] = {rz.get(), zsum.get()};
+  const Acc<T> v[2] = {rz, zsum};
   double tot[2];
-  if (grid_sum<2>(v, partials, &sc->ticket[2], tot)) set_rz(sc, tot, first);
+  if (grid_sum_acc<T, 2>(v, partials, &sc->ticket[2], tot)) set_rz(sc, tot, first);
 }
 
 // The same scalars from the partial pairs the level-0 post-smoother wrote
 // (k_jacobi7 with RZ): grid-stride sums, then the ticketed block tree.
+template <bool PAIRS>
 __global__ void __launch_bounds__(NT)
 k_finish_rz(const double *__restrict__ partials, int n, double *scratch, Scalars *sc,
             int first, size_t pstride) {
@@ -274,8 +352,8 @@ k_finish_rz(const double *__restrict__ partials, int n, double *scratch, Scalars
   sc += blockIdx.y;
   double v[2] = {0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    v[0] += partials[2 * (size_t)i];
-    v[1] += partials[2 * (size_t)i + 1];
+    v[0] += pair_at<PAIRS>(partials, 2 * (size_t)i);
+    v[1] += pair_at<PAIRS>(partials, 2 * (size_t)i + 1);
   }
   double tot[2];
   if (grid_sum<2>(v, scratch, &sc->ticket[2], tot)) set_rz(sc, tot, first);
@@ -442,9 +520,9 @@ k_dot(int nb, const T *__restrict__ x, const T *__restrict__ y,
     const size_t s = (size_t)bk * BV + threadIdx.x;
     if (comp[s] >= 0) acc.add(y ? x[s] * y[s] : x[s]);
   }
-  double v[1] = {acc.get()};
+  const Acc<T> v[1] = {acc};
   double tot[1];
-  if (grid_sum<1>(v, partials, &sc->ticket[3], tot)) sc->aux[slot] = tot[0];
+  if (grid_sum_acc<T, 1>(v, partials, &sc->ticket[3], tot)) sc->aux[slot] = tot[0];
 }
 
 // ------------------------------------------------------------ Eq. 3 RHS
@@ -939,9 +1017,9 @@ k_scale_to_f32(int nb, const double *__restrict__ r, double f,
     r32[s] = v;
     acc.add(v);
   }
-  double t[1] = {acc.get()};
+  const Acc<float> t[1] = {acc};
   double tot[1];
-  if (grid_sum<1>(t, partials, &sc->ticket[5], tot)) {
+  if (grid_sum_acc<float, 1>(t, partials, &sc->ticket[5], tot)) {
     sc->rsum = tot[0];
     sc->rmean = tot[0] * sc->inv_ndof;
     sc->rmean_f = (float)sc->rmean;
@@ -1003,16 +1081,22 @@ void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
         g, gx, diag, p, q, partials, pstride, nk);
 }
 void launch_finish_rz(int n, const double *partials, double *scratch, Scalars *sc, int first,
-                      cudaStream_t st, int nk, size_t pstride) {
+                      cudaStream_t st, int nk, size_t pstride, bool pairs) {
   if (n <= 0) return;
   const int blocks = std::min(152, (n + NT - 1) / NT);
-  k_finish_rz<<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, first, pstride);
+  if (pairs)
+    k_finish_rz<true><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, first, pstride);
+  else
+    k_finish_rz<false><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, first, pstride);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
-                      cudaStream_t st, int nk, size_t pstride) {
+                      cudaStream_t st, int nk, size_t pstride, bool pairs) {
   if (n <= 0) return;
   const int blocks = std::min(152, (n + NT - 1) / NT);
-  k_finish_pq<<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, pstride);
+  if (pairs)
+    k_finish_pq<true><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, pstride);
+  else
+    k_finish_pq<false><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, pstride);
 }
 template <typename T>
 void launch_update_xr(int nb, T *x, T *r, const T *p, const T *q, Scalars *sc,

@@ -295,18 +295,34 @@ __device__ __forceinline__ T tile_at(const T (*tl)[10][10], int ts) {
 
 // Sum of the N values of every lane of the warp, held by every lane: an
 // FP64 sum for double; for float, an error-free (TwoSum) FP32 pair over the
-// thread's values and the warp.  get() rounds it to FP64; kernels call it in
-// the one lane that stores the sum, so that an FP32 kernel spends no FP64
-// pipe cycles (conversions included) in the other 31.
+// thread's values and the warp.  get() rounds it to FP64.
 template <typename T> struct WarpSum;
+// put() stores the sum into one 8-byte partial slot: the FP64 value, or the
+// FP32 pair (hi, lo) as is, for a finishing kernel that widens it (pair_at)
+// so that the FP32 kernel itself issues no FP64 instruction.
 template <> struct WarpSum<double> {
   double s;
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ void put(double *slot) const { *slot = s; }
 };
 template <> struct WarpSum<float> {
   float hi, lo;
   __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ void put(double *slot) const {
+    *reinterpret_cast<float2 *>(slot) = make_float2(hi, lo);
+  }
 };
+// The value of partial slot i: an FP64 value, or (PAIRS) an FP32 pair
+// written by WarpSum<float>::put.
+template <bool PAIRS>
+__device__ __forceinline__ double pair_at(const double *p, size_t i) {
+  if constexpr (PAIRS) {
+    const float2 q = reinterpret_cast<const float2 *>(p)[i];
+    return (double)q.x + (double)q.y;
+  } else {
+    return p[i];
+  }
+}
 template <typename T, int N>
 __device__ __forceinline__ WarpSum<T> warp_total(const T (&v)[N]) {
   if constexpr (sizeof(T) == 4) {
