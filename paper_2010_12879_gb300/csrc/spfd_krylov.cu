@@ -39,26 +39,28 @@ template <> struct Acc<float> {
 };
 
 // ------------------------------------------------------------ reductions
+// Block sums of the threads' NV FP64 values, left in warp 0 (every lane),
+// for blocks of at most NT threads.  The values pass through shared memory
+// and warp 0 adds them (lane l the values of threads l, l + 32, ..., then a
+// butterfly): NV * (warps + 4) FP64 warp instructions per block, against
+// 5 NV per warp plus 5 NV for a butterfly in every warp, on GB300's narrow
+// FP64 pipe.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
-  __shared__ double sm[32][NV];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double sm[NV][NT];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sm[w][k] = v[k];
+  for (int k = 0; k < NV; ++k) sm[k][t] = v[k];
   __syncthreads();
   if (w == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      v[k] = lane < nw ? sm[lane][k] : 0.0;
+      double a = sm[k][lane];
+      for (int i = 1; i < nw; ++i) a += sm[k][lane + 32 * i];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      v[k] = a;
     }
   }
   __syncthreads();
