@@ -419,6 +419,8 @@ def run_ours(args):
         a_rows = pulled_rows_of_a(ph.sigma)
         nx1 = ph.sigma.shape[2] + 1
         e2e = {"value": round(statistics.mean(times) / world, 6), "unit": "s",
+               "value_kind": "host-to-host time of one body (s)" if world == 1 else
+                             f"seconds per body over {world} replicas (time / {world})",
                "h2d_bytes_per_step": int(sig_h.numel() * 8 + a_rows * nx1 * 8),
                "d2h_bytes_per_step": int(psi_h.numel() * 8 + E_h.numel() * 8),
                "std_s": round(statistics.pstdev(times), 6),
@@ -442,6 +444,10 @@ def run_ours(args):
             "ms_per_step": round(step_ms, 3), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": DATA, "config": _config(world),
+            "value_kind": ("step time of one body (s)" if world == 1 else
+                           f"seconds per body: {world} replicas, one body each, finish in the "
+                           f"slowest rank's step time; value = that time / {world} "
+                           "(an inverse throughput), ms_per_step = the step latency"),
             "breakdown_ms": {k: round(v, 3) for k, v in t64.items()},
             "solve_s": round(t64["solve_ms"] / 1000.0, 6),
             "iters": info64["iters"], "rel_res_true": info64["rel_res_true"],
