@@ -383,6 +383,10 @@ def run_ours(args):
         gauge = bench_tree_cotree(spfd, torch, dev, stream, ph, sig, ad, hbm_peak, peak_kind,
                                   K, W)
 
+    cheb = None
+    if not args.no_chebyshev:
+        cheb = bench_chebyshev(spfd, torch, dev, stream, ph, sig, ad, psi, max(3, min(K, 5)), W)
+
     group = None
     if not args.no_group:
         group = bench_group(spfd, torch, dev, stream, ph, sig, ad, max(1, min(K, 5)), W)
@@ -466,6 +470,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "percentile": pct,
             "tree_cotree": gauge,
+            "chebyshev": cheb,
             "group": group,
             "body_1mm": body1,
             "batch": batch,
@@ -575,6 +580,41 @@ def adjoint_fd_check(spfd, torch, dev, stream, ph, a, n_tissues=8, n_dirs=3, tol
             "max_rel_err_dJdsigma_per_tissue": err_s,
             "max_rel_err_dJda_directional": float(max(errs_a)),
             "directions": n_dirs}
+
+
+def bench_chebyshev(spfd, torch, dev, stream, ph, sig, ad, psi, K, W):
+    """The V-cycle's smoother: weighted Jacobi V(1,1) (the default) against
+    Chebyshev of degree 2 and 3 (fused residual-and-update sweeps) on the
+    2 mm body, FP64 and mixed, solve to TOL: median solve time over K solves
+    after W warm-up solves on one built context each (CUDA events on the
+    stream), iterations and the true residual."""
+    out = {"workload": "2 mm body, loop source, solve to 1e-8 (build excluded)", "runs": []}
+    for prec, pname in ((spfd.SPFD_FP64, "fp64"), (spfd.SPFD_MIXED, "mixed")):
+        for sm, deg in ((spfd.SPFD_SMOOTHER_JACOBI, 0), (spfd.SPFD_SMOOTHER_CHEBYSHEV, 2),
+                        (spfd.SPFD_SMOOTHER_CHEBYSHEV, 3)):
+            opts = spfd.spfd_opts_default()
+            opts.precision = prec
+            opts.smoother = sm
+            if deg:
+                opts.cheb_degree = deg
+            times = []
+            with spfd.Solver(sig, ph.h, opts, stream=stream) as S:
+                for i in range(W + K):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    _, info, st = S.solve(ad, TOL, psi)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    assert st == spfd.SPFD_OK, spfd.spfd_last_error()
+                    if i >= W:
+                        times.append(e0.elapsed_time(e1))
+            out["runs"].append({"precision": pname,
+                                "smoother": "jacobi V(1,1)" if not deg else f"chebyshev degree {deg}",
+                                "solve_ms": round(statistics.median(times), 3),
+                                "iters": info["iters"], "outer_iters": info["outer_iters"],
+                                "rel_res_true": info["rel_res_true"]})
+    return out
 
 
 def bench_tree_cotree(spfd, torch, dev, stream, ph, sig, ad, hbm_peak, peak_kind, K, W):
@@ -1061,6 +1101,7 @@ def main():
     ap.add_argument("--no-group", action="store_true")
     ap.add_argument("--no-1mm", action="store_true")
     ap.add_argument("--no-tree-cotree", action="store_true")
+    ap.add_argument("--no-chebyshev", action="store_true")
     ap.add_argument("--batch-rhs", type=int, default=64,
                     help="source fields of the batched-solve sub-object")
     ap.add_argument("--ncu-step", choices=["fp64", "mixed"], default=None,

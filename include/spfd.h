@@ -63,8 +63,15 @@ typedef enum {
   SPFD_EINTERNAL = 5       /* a bounded device loop hit its iteration cap */
 } spfd_status;
 
-/* Smoother of the V-cycle.  Only weighted Jacobi is built; CHEBYSHEV is a
- * reserved value that spfd_build rejects with SPFD_EINVAL. */
+/* Smoother of the V-cycle (both applied to D^-1 A, D the operator's
+ * diagonal, on every level but the coarsest).
+ *   SPFD_SMOOTHER_JACOBI:    weighted Jacobi, omega = 4 / (3 lambda_max),
+ *                            nu_pre / nu_post sweeps (the default).
+ *   SPFD_SMOOTHER_CHEBYSHEV: Chebyshev polynomial of degree cheb_degree
+ *                            before and after the coarse correction, on the
+ *                            eigenvalue interval [lambda_max / 8, lambda_max]
+ *                            (three-term recurrence; each step costs one
+ *                            residual); nu_pre / nu_post are not used. */
 enum { SPFD_SMOOTHER_JACOBI = 0, SPFD_SMOOTHER_CHEBYSHEV = 1 };
 
 /* Arithmetic of the solve.
@@ -80,8 +87,8 @@ typedef struct {
   int maxit;         /* PCG iteration cap (default 200) */
   int nu_pre;        /* pre-smoothing sweeps per level (default 1) */
   int nu_post;       /* post-smoothing sweeps per level (default 1) */
-  int smoother;      /* SPFD_SMOOTHER_JACOBI (the only one built; default) */
-  int cheb_degree;   /* reserved for a Chebyshev smoother (default 2, unused) */
+  int smoother;      /* SPFD_SMOOTHER_JACOBI (default) or SPFD_SMOOTHER_CHEBYSHEV */
+  int cheb_degree;   /* Chebyshev degree, 1 .. 8 (default 2; used with CHEBYSHEV only) */
   int precision;     /* SPFD_FP64 or SPFD_MIXED */
   int coarse_max;    /* stop coarsening at <= this many unknowns (default 512) */
   int max_levels;    /* hierarchy depth cap (default 12) */

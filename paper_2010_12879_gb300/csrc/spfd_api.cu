@@ -133,6 +133,16 @@ extern "C" spfd_status spfd_release_cached_memory(size_t *released) {
 
 extern "C" void spfd_destroy(spfd_ctx *ctx) { destroy_ctx(ctx); }
 
+// Chebyshev smoother: ratio of the eigenvalue bounds of D^-1 A it damps
+// (the upper part of the spectrum, which the coarse levels do not correct),
+// the margin on coarse levels' lambda_max estimates, and the largest degree
+// accepted.  Measured on the 2 mm body with degree 2: ratio 30 took 69
+// iterations (too little damping per step on the upper half), ratio 4 or 8
+// took 9; margin 1.3 costs no iteration against 1.05 there.
+constexpr double CHEB_RATIO = 8.0;
+constexpr double CHEB_MARGIN = 1.3;  // on the power-iteration estimate of coarse levels
+constexpr int CHEB_MAX_DEGREE = 8;
+
 extern "C" void spfd_opts_default(spfd_opts *o) {
   if (!o) return;
   o->tol = 1e-8;
@@ -168,9 +178,10 @@ extern "C" spfd_status spfd_build(const double *sigma_dev, int nx, int ny,
       (o.precision != SPFD_FP64 && o.precision != SPFD_MIXED) ||
       (o.smoother != SPFD_SMOOTHER_JACOBI && o.smoother != SPFD_SMOOTHER_CHEBYSHEV))
     return fail(SPFD_EINVAL, "invalid options");
-  if (o.smoother != SPFD_SMOOTHER_JACOBI)
-    return fail(SPFD_EINVAL, "only the weighted-Jacobi smoother is built "
-                             "(SPFD_SMOOTHER_CHEBYSHEV is reserved)");
+  if (o.smoother == SPFD_SMOOTHER_CHEBYSHEV &&
+      (o.cheb_degree < 1 || o.cheb_degree > CHEB_MAX_DEGREE))
+    return fail(SPFD_EINVAL, "cheb_degree must be in 1..%d (got %d)", CHEB_MAX_DEGREE,
+                o.cheb_degree);
   spfd_ctx *c = new (std::nothrow) spfd_ctx();
   if (!c) return fail(SPFD_ENOMEM, "host allocation of the context failed");
   c->nx = nx; c->ny = ny; c->nz = nz; c->h = h; c->opts = o;
@@ -241,6 +252,35 @@ static const char *lvl_name(const char *const (&names)[6], int l) {
 #define LVL_NAMES(base)                                                          \
   {base "_l0", base "_l1", base "_l2", base "_l3", base "_l4", base "_deep"}
 
+// Chebyshev smoothing of degree k on D^-1 A: eigenvalue bounds
+// [hi / CHEB_RATIO, hi] with hi the level's lambda_max (2 on level 0, the
+// power-iteration estimate times CHEB_MARGIN above: the polynomial grows
+// fast past hi, so an underestimate costs more than with Jacobi's 1.05
+// margin), theta and delta their centre
+// and half-width; the recurrence of the shifted and scaled Chebyshev
+// polynomials gives d_0 = D^-1 r_0 / theta and, for j >= 1,
+// rho_j = 1 / (2 theta / delta - rho_{j-1}) (rho_0 = delta / theta),
+// d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) D^-1 r_j, with
+// x_{j+1} = x_j + d_j.  c1[j], c2[j] are the two factors of step j.
+struct ChebCoef {
+  double c1[CHEB_MAX_DEGREE], c2[CHEB_MAX_DEGREE];
+};
+static ChebCoef cheb_coefficients(double hi, int k) {
+  ChebCoef cf{};
+  const double lo = hi / CHEB_RATIO;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  cf.c1[0] = 0.0;
+  cf.c2[0] = 1.0 / theta;
+  for (int j = 1; j < k && j < CHEB_MAX_DEGREE; ++j) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    cf.c1[j] = rn * rho;
+    cf.c2[j] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  return cf;
+}
+
 // V-cycle on level l for the right-hand sides bl (nk of them, S_l apart);
 // returns the buffer holding the corrections.  With proj (level 0) bl is
 // first projected onto the range of A in place (its per-component mean
@@ -257,7 +297,8 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
   const double w = sizeof(T), S = (double)lv.S * nk;
   const double wc = sizeof(typename Prec<T>::C7);
   const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
-  if (proj && (c->ncomp > 1 || l == nl - 1)) {
+  const bool cheb = c->opts.smoother == SPFD_SMOOTHER_CHEBYSHEV;
+  if (proj && (cheb || c->ncomp > 1 || l == nl - 1)) {
     project<T>(c, bl, nk);
     proj = false;
   }
@@ -268,8 +309,58 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
                 launch_coarse_solve<T>(c->m, lv.S, c->cidx, c->Binv, bl, lv.X<T>(), st, nk));
     return lv.X<T>();
   }
-  T *cur = lv.X<T>(), *oth = lv.Tt<T>();
   const T *wd = lv.WDINV<T>();
+  auto residual = [&](const T *xin, T *rout) {
+    if (l == 0)
+      SPFD_LAUNCH(c, "residual7_l0", f32, 1, (4 * w + 3 * wc) * S, 14 * S,
+                  (launch_residual7<T, typename Prec<T>::C7>(lv.g, Prec<T>::gx(lv),
+                                                             lv.DIAG<T>(), xin, bl, rout, st,
+                                                             nk, block_order(c, TF_RESID, l))));
+    else
+      SPFD_LAUNCH(c, lvl_name(LVL_NAMES("residual27"), l), f32, 1,
+                  30 * w * S, 55 * S,
+                  launch_residual27<T>(lv.g, lv.ST<T>(), xin, bl, rout, st, nk,
+                                       block_order(c, TF_RESID, l)));
+  };
+  if (cheb) {
+    // Chebyshev: x ping-pongs between the level's two vectors, d lives in
+    // its residual vector (free while smoothing; the residual for the
+    // restriction overwrites it once pre-smoothing is done)
+    const int k = c->opts.cheb_degree;
+    const ChebCoef cf = cheb_coefficients(l == 0 ? 2.0 : CHEB_MARGIN * lv.lmax, k);
+    const double iw = 1.0 / lv.omega;  // wdinv = omega D^-1
+    T *cur = lv.X<T>(), *oth = lv.Tt<T>(), *d = lv.R<T>();
+    auto step = [&](int j) {
+      if (l == 0)
+        SPFD_LAUNCH(c, "cheb7_l0", f32, 1, (7 * w + 3 * wc) * S, 18 * S,
+                    (launch_cheb7<T, typename Prec<T>::C7>(lv.g, Prec<T>::gx(lv), lv.DIAG<T>(),
+                                                           wd, cur, bl, oth, d, cf.c1[j],
+                                                           cf.c2[j] * iw, st, nk)));
+      else
+        SPFD_LAUNCH(c, lvl_name(LVL_NAMES("cheb27"), l), f32, 1, 34 * w * S, 59 * S,
+                    launch_cheb27<T>(lv.g, lv.ST<T>(), wd, cur, bl, oth, d, cf.c1[j],
+                                     cf.c2[j] * iw, st, nk));
+      std::swap(cur, oth);
+    };
+    SPFD_LAUNCH(c, lvl_name(LVL_NAMES("cheb_first"), l), f32, 1, 4 * w * S, 2 * S,
+                launch_cheb<T>(true, lv.S, wd, bl, d, cur, 0.0, cf.c2[0] * iw, st, nk));
+    for (int j = 1; j < k; ++j) step(j);
+    residual(cur, lv.R<T>());
+    Level &cl = c->L[l + 1];
+    const double Sc = (double)cl.S * nk;
+    SPFD_LAUNCH(c, lvl_name(LVL_NAMES("restrict"), l), f32, 1,
+                28 * w * Sc + w * S, 54 * Sc,
+                launch_restrict<T>(lv.g, cl.g, cl.PP<T>(), lv.R<T>(), cl.B<T>(), st, nk,
+                                   block_order(c, TF_RESTRICT, l)));
+    T *ec = vcycle<T>(c, l + 1, cl.B<T>(), false, nk);
+    SPFD_LAUNCH(c, lvl_name(LVL_NAMES("prolong"), l), f32, 1,
+                (27.0 / 8.0 + 2.0) * w * S + w * Sc, 7 * S,
+                launch_prolong<T>(lv.g, cl.g, lv.PC<T>(), ec, cur, st, nk,
+                                  block_order(c, TF_PROLONG, l)));
+    for (int j = 0; j < k; ++j) step(j);  // post-smoothing: the recurrence restarts
+    return cur;
+  }
+  T *cur = lv.X<T>(), *oth = lv.Tt<T>();
   if (proj)
     SPFD_LAUNCH(c, "jacobi_first_l0", f32, 1, 4 * w * S, 2 * S,
                 launch_jacobi_first_proj<T>(lv.g, wd, bl, cur, c->sc, inv, st, nk,
@@ -498,7 +589,8 @@ spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
   // and a pass over r and z is saved.  The FP64 sweep is FP64-pipe-bound:
   // its warp sums cost more than the separate pass (0.29 against 0.18 ms per
   // sweep on the 2 mm body), so FP64 keeps k_dot_rz.
-  const bool fused = f32 && c->L.size() > 1 && c->opts.nu_post >= 1;
+  const bool fused = f32 && c->L.size() > 1 && c->opts.nu_post >= 1 &&
+                     c->opts.smoother == SPFD_SMOOTHER_JACOBI;
   T *z = vcycle<T>(c, 0, r, true, nk, fused);
   if (fused)
     SPFD_LAUNCH(c, "finish_rz", false, 1, 16.0 * jacobi7_rz_partials<T>(nb) * nk, 0,

@@ -289,6 +289,103 @@ k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
   st16(x + s0, xv);
 }
 
+// ------------------------------------------------------------ Chebyshev sweeps
+// One Chebyshev step fused with its residual: with r = b - A xin,
+// d = c1 d + c2w wdinv r (in place: a thread reads and writes only its own
+// slots of d) and xout = xin + d.  Level 0 on the row mapping of k_jacobi7,
+// the 27-point levels as jacobi27_unit (FP64 with the active-slot
+// compaction; a zero row has r = b).
+template <typename T, typename C>
+__global__ void __launch_bounds__(BV / row_n_jacobi<T>(), row_min_blocks<T>())
+k_cheb7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
+        const T *__restrict__ wdinv, const T *__restrict__ xin, const T *__restrict__ b,
+        T *__restrict__ xout, T *__restrict__ d, T c1, T c2w) {
+  constexpr int N = row_n_jacobi<T>();
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, s0 = row_slot<N>(bk, t);
+  const size_t off = (size_t)blockIdx.y * S;
+  xin += off; b += off; xout += off; d += off;
+  const Qv<T, N> bv = ldqn<T, T, N>(b + s0), wv = ldqn<T, T, N>(wdinv + s0);
+  Qv<T, N> dv = ldqn<T, T, N>(d + s0), xc, rv;
+  apply7_row<T, C, true, N>(g, gx, diag, xin, S, bk, t, bv, xc, rv);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    dv.v[i] = c1 * dv.v[i] + c2w * wv.v[i] * rv.v[i];
+    xc.v[i] += dv.v[i];
+  }
+  stqn<T, N>(xout + s0, xc);
+  stqn<T, N>(d + s0, dv);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT)
+k_cheb27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
+         const T *__restrict__ xin, const T *__restrict__ b, T *__restrict__ xout,
+         T *__restrict__ d, T c1, T c2w) {
+  __shared__ T tl[10][10][10];
+  __shared__ int sn[27];
+  __shared__ ActList al;
+  const int bk = blockIdx.x, t = threadIdx.x;
+  const size_t S = (size_t)g.nb * BV, base = (size_t)bk * BV;
+  const size_t off = (size_t)blockIdx.y * S;
+  xin += off; b += off; xout += off; d += off;
+  load_nbr(g, bk, sn);
+  act_stage(g, bk, al);
+  __syncthreads();
+  tile_full<T>(tl, xin, bk, sn);
+  __syncthreads();
+  const SlotMap m = slot_map<T>(al);
+  auto update = [&](size_t s, int ts, T r) {
+    const T dn = c1 * d[s] + c2w * wdinv[s] * r;
+    d[s] = dn;
+    xout[s] = tile_at(tl, ts) + dn;
+  };
+  if (m.idle) update(base + t, t, b[base + t]);
+  if (m.mine) {
+    const size_t s = base + m.ts;
+    update(s, m.ts, b[s] - apply27_tile<T>(tl, st, S, s, m.ts));
+  }
+}
+
+// ------------------------------------------------------------ Chebyshev step
+// One step of the Chebyshev smoother (three-term recurrence on D^-1 A):
+// d = c1 d + c2w wdinv r, x += d, or (FIRST, from a zero guess, r = b)
+// d = c2w wdinv b, x = d.  wdinv = omega D^-1 holds the Jacobi weight, which
+// c2w absorbs; slots that are not unknowns (wdinv = 0) keep d = x = 0.  A
+// streaming kernel over the level's slots; the residual r comes from the
+// residual kernels above.
+template <typename T, bool FIRST>
+__global__ void __launch_bounds__(NT)
+k_cheb(size_t S, const T *__restrict__ wdinv, const T *__restrict__ r, T *__restrict__ d,
+       T *__restrict__ x, T c1, T c2w) {
+  constexpr int N = V16<T>::N;
+  const size_t off = (size_t)blockIdx.y * S;
+  r += off; d += off; x += off;
+  const size_t nv = S / N;
+  for (size_t vi = blockIdx.x * (size_t)blockDim.x + threadIdx.x; vi < nv;
+       vi += (size_t)gridDim.x * blockDim.x) {
+    const size_t s0 = vi * N;
+    const V16<T> w = ld16(wdinv + s0), rv = ld16(r + s0);
+    V16<T> dv, xv;
+    if constexpr (!FIRST) {
+      dv = ld16(d + s0);
+      xv = ld16(x + s0);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if constexpr (FIRST) {
+        dv.v[i] = c2w * w.v[i] * rv.v[i];
+        xv.v[i] = dv.v[i];
+      } else {
+        dv.v[i] = c1 * dv.v[i] + c2w * w.v[i] * rv.v[i];
+        xv.v[i] += dv.v[i];
+      }
+    }
+    st16(d + s0, dv);
+    st16(x + s0, xv);
+  }
+}
+
 // ------------------------------------------------------------ transfers
 // Restriction r_c(I) = sum_d P[d][I] r_f(2I + d) (P^T, the adjoint of the
 // prolongation below).  A coarse brick B reads the 17^3 fine nodes
@@ -576,6 +673,31 @@ void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
       k_prolong<T, 0><<<unit_grid(0, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
   }
 }
+template <typename T, typename C>
+void launch_cheb7(const Grid &g, const C *gx, const T *diag, const T *wdinv, const T *xin,
+                  const T *b, T *xout, T *d, double c1, double c2w, cudaStream_t st, int nk) {
+  if (g.nb)
+    k_cheb7<T, C><<<dim3(g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(g, gx, diag, wdinv, xin,
+                                                                    b, xout, d, (T)c1, (T)c2w);
+}
+template <typename T>
+void launch_cheb27(const Grid &g, const T *stc, const T *wdinv, const T *xin, const T *b,
+                   T *xout, T *d, double c1, double c2w, cudaStream_t st, int nk) {
+  if (g.nb)
+    k_cheb27<T><<<dim3(g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, d, (T)c1, (T)c2w);
+}
+template <typename T>
+void launch_cheb(bool first, size_t S, const T *wdinv, const T *r, T *d, T *x, double c1,
+                 double c2w, cudaStream_t st, int nk) {
+  if (S == 0) return;
+  const size_t nv = S / V16<T>::N;
+  const size_t want = (nv + NT - 1) / NT;
+  const unsigned blocks = (unsigned)(want < 152 * 8 ? want : 152 * 8);
+  if (first)
+    k_cheb<T, true><<<dim3(blocks, nk), NT, 0, st>>>(S, wdinv, r, d, x, (T)c1, (T)c2w);
+  else
+    k_cheb<T, false><<<dim3(blocks, nk), NT, 0, st>>>(S, wdinv, r, d, x, (T)c1, (T)c2w);
+}
 template <typename T>
 void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
                          const T *b, T *x, cudaStream_t st, int nk) {
@@ -602,7 +724,12 @@ void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
                                   const T *, T *, cudaStream_t, int, int);    \
   template void launch_coarse_solve<T>(int, size_t, const int *,              \
                                        const double *, const T *, T *,        \
-                                       cudaStream_t, int);
+                                       cudaStream_t, int);                    \
+  template void launch_cheb<T>(bool, size_t, const T *, const T *, T *, T *,  \
+                               double, double, cudaStream_t, int);            \
+  template void launch_cheb27<T>(const Grid &, const T *, const T *,          \
+                                 const T *, const T *, T *, T *, double,      \
+                                 double, cudaStream_t, int);
 INST_T(double)
 INST_T(float)
 #define INST_TC(T, C)                                                         \
@@ -618,6 +745,14 @@ INST_T(float)
                                      cudaStream_t, int, int);
 INST_TC(double, double)
 INST_TC(float, float)
+template void launch_cheb7<double, double>(const Grid &, const double *, const double *,
+                                           const double *, const double *, const double *,
+                                           double *, double *, double, double, cudaStream_t,
+                                           int);
+template void launch_cheb7<float, __nv_bfloat16>(const Grid &, const __nv_bfloat16 *,
+                                                 const float *, const float *, const float *,
+                                                 const float *, float *, float *, double, double,
+                                                 cudaStream_t, int);
 INST_TC(float, __nv_bfloat16)
 
 }  // namespace spfd

@@ -453,6 +453,22 @@ void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
 template <typename T>
 void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
                     T *ef, cudaStream_t st, int nk = 1, int order = 0);
+// One Chebyshev smoothing step on a level of S slots (nk right-hand sides,
+// S apart): d = c1 d + c2w wdinv r, x += d; first (from a zero guess, r = b):
+// d = c2w wdinv b, x = d.
+template <typename T>
+void launch_cheb(bool first, size_t S, const T *wdinv, const T *r, T *d, T *x, double c1,
+                 double c2w, cudaStream_t st, int nk = 1);
+// One Chebyshev step fused with its residual r = b - A xin:
+// d = c1 d + c2w wdinv r, xout = xin + d (level 0: 7-point, conductances C;
+// coarse levels: 27-point).
+template <typename T, typename C>
+void launch_cheb7(const Grid &g, const C *gx, const T *diag, const T *wdinv, const T *xin,
+                  const T *b, T *xout, T *d, double c1, double c2w, cudaStream_t st,
+                  int nk = 1);
+template <typename T>
+void launch_cheb27(const Grid &g, const T *stc, const T *wdinv, const T *xin, const T *b,
+                   T *xout, T *d, double c1, double c2w, cudaStream_t st, int nk = 1);
 // x[idx] = Binv b[idx] on the coarsest level (S slots per right-hand side).
 template <typename T>
 void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,

@@ -124,16 +124,27 @@ def test_invalid_options_rejected(spfd):
     assert st == spfd.SPFD_EINVAL
 
 
-def test_reserved_chebyshev_smoother_rejected(spfd):
-    """Only weighted Jacobi is built: the reserved Chebyshev value is an
-    error (checked before any device work), not a silent fallback."""
+@pytest.mark.parametrize("degree", [0, 9, -1])
+def test_chebyshev_degree_out_of_range_rejected(spfd, degree):
+    """The Chebyshev smoother takes degrees 1..8; others are an error
+    (checked before any device work)."""
     L = spfd.lib()
     o = spfd.spfd_opts_default()
     o.smoother = spfd.SPFD_SMOOTHER_CHEBYSHEV
+    o.cheb_degree = degree
     handle = ctypes.c_void_p()
     st = L.spfd_build(ctypes.c_void_p(8), 4, 4, 4, 2e-3, ctypes.byref(o), None, ctypes.byref(handle))
     assert st == spfd.SPFD_EINVAL and not handle.value
-    assert "Jacobi" in spfd.spfd_last_error()
+    assert "cheb_degree" in spfd.spfd_last_error()
+
+
+def test_unknown_smoother_rejected(spfd):
+    L = spfd.lib()
+    o = spfd.spfd_opts_default()
+    o.smoother = 7
+    handle = ctypes.c_void_p()
+    st = L.spfd_build(ctypes.c_void_p(8), 4, 4, 4, 2e-3, ctypes.byref(o), None, ctypes.byref(handle))
+    assert st == spfd.SPFD_EINVAL and not handle.value
 
 
 def test_without_gpu_build_reports_cuda_error(spfd):
