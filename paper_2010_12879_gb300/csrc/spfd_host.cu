@@ -5,11 +5,12 @@
 // host memory and receives Psi (Eq. 3) and the voxel-averaged |E| (Eq. 1) in
 // host memory.  On the device the call
 //   1. copies sigma in (copy engine),
-//   2. on a second stream, marks the voxel rows (j, k) that hold a conducting
-//      voxel and pulls from host memory only the rows of a that contain an
-//      edge of such a voxel (SM loads over the chip-to-chip link), zeroing
-//      the others: the operator and |E| never read the rest, and on a body
-//      phantom about half of the rows of a are skipped,
+//   2. on a second stream, finds in each voxel row (j, k) the span of its
+//      conducting voxels and pulls from host memory only the part of each
+//      row of a that holds an edge of such a voxel (SM loads over the
+//      chip-to-chip link), zeroing the rest: the operator and |E| never read
+//      it, and on a body phantom 54 % of the rows' nodes are pulled from 52 %
+//      of the rows,
 //   3. meanwhile builds the operator and hierarchy (spfd_build),
 //   4. solves Eq. 3 once the rows of a have arrived (spfd_solve),
 //   5. evaluates |E| (spfd_efield) while Psi goes back on the second stream,
@@ -25,44 +26,61 @@
 namespace spfd {
 namespace {
 
-// rowc[k * ny + j] = 1 iff voxel row (j, k) holds a voxel with sigma > 0; one
-// warp per row.
+// span[k * ny + j] = (first, last) x index of the conducting voxels
+// (sigma > 0) of voxel row (j, k), or (-1, -1); one warp per row.
 __global__ void __launch_bounds__(256)
-k_row_any(const double *__restrict__ sigma, int nx, int nrows, unsigned char *__restrict__ rowc) {
+k_row_span(const double *__restrict__ sigma, int nx, int nrows, int2 *__restrict__ span) {
   const int lane = threadIdx.x & 31;
   for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows;
        r += ((long long)gridDim.x * blockDim.x) >> 5) {
     const double *row = sigma + (size_t)r * nx;
-    bool any = false;
-    for (int i = lane; i < nx; i += 32) any |= row[i] > 0.0;
-    any = __any_sync(0xffffffffu, any);
-    if (lane == 0) rowc[r] = any ? 1 : 0;
+    int lo = nx, hi = -1;
+    for (int i = lane; i < nx; i += 32)
+      if (row[i] > 0.0) {
+        lo = min(lo, i);
+        hi = i;
+      }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) span[r] = hi >= 0 ? make_int2(lo, hi) : make_int2(-1, -1);
   }
 }
 
-// Row (d, k, j) of a (the d-edges of node row (j, k), nx+1 slots) is needed
-// iff one of its edges touches a conducting voxel:
+// The nodes lo .. hi of row (d, k, j) of a (the d-edges of node row (j, k),
+// nx+1 slots) that hold an edge of a conducting voxel: edges of nodes
+// imin .. imax + 1 of the voxel rows they touch,
 //   x edges of node row (j, k): voxel rows (j-1..j, k-1..k),
 //   y edges:                    voxel rows (j, k-1..k)   (none for j = ny),
-//   z edges:                    voxel rows (j-1..j, k)   (none for k = nz).
-__device__ __forceinline__ bool row_needed(const unsigned char *__restrict__ rowc, int ny,
-                                           int nz, int d, int j, int k) {
-  auto c = [&](int jj, int kk) {
-    return jj >= 0 && jj < ny && kk >= 0 && kk < nz && rowc[(size_t)kk * ny + jj];
+//   z edges:                    voxel rows (j-1..j, k)   (none for k = nz);
+// hi < lo when none does.
+__device__ __forceinline__ int2 row_nodes(const int2 *__restrict__ span, int ny, int nz, int d,
+                                          int j, int k) {
+  int lo = 1 << 30, hi = -1;
+  auto take = [&](int jj, int kk) {
+    if (jj < 0 || jj >= ny || kk < 0 || kk >= nz) return;
+    const int2 q = span[(size_t)kk * ny + jj];
+    if (q.y < 0) return;
+    lo = min(lo, q.x);
+    hi = max(hi, q.y + 1);
   };
-  if (d == 0) return c(j - 1, k - 1) || c(j, k - 1) || c(j - 1, k) || c(j, k);
-  if (d == 1) return c(j, k - 1) || c(j, k);
-  return c(j - 1, k) || c(j, k);
+  if (d == 0) {
+    take(j - 1, k - 1); take(j, k - 1); take(j - 1, k); take(j, k);
+  } else if (d == 1) {
+    take(j, k - 1); take(j, k);
+  } else {
+    take(j - 1, k); take(j, k);
+  }
+  return make_int2(lo, hi);
 }
 
 // loads each lane has in flight per pass along a row (one pass covers 288
 // slots, a whole row of the 2 mm body)
 constexpr int PULL_PER_LANE = 9;
 
-// One warp per row: the needed rows are loaded from host memory (every lane
+// One warp per row: the needed nodes are loaded from host memory (every lane
 // issues its loads before storing), the others zeroed.
 __global__ void __launch_bounds__(256)
-k_pull_rows(const double *__restrict__ a_host, const unsigned char *__restrict__ rowc, int nx,
+k_pull_rows(const double *__restrict__ a_host, const int2 *__restrict__ span, int nx,
             int ny, int nz, double *__restrict__ a_dev) {
   const int lane = threadIdx.x & 31;
   const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
@@ -73,17 +91,14 @@ k_pull_rows(const double *__restrict__ a_host, const unsigned char *__restrict__
     const int rem = (int)(r % ((long long)NZ * NY));
     const int k = rem / NY, j = rem % NY;
     double *dst = a_dev + (size_t)r * NX;
-    if (!row_needed(rowc, ny, nz, d, j, k)) {
-      for (int i = lane; i < NX; i += 32) dst[i] = 0.0;
-      continue;
-    }
+    const int2 nodes = row_nodes(span, ny, nz, d, j, k);
     const double *src = a_host + (size_t)r * NX;
     for (int i0 = 0; i0 < NX; i0 += 32 * PULL_PER_LANE) {
       double v[PULL_PER_LANE];
 #pragma unroll
       for (int u = 0; u < PULL_PER_LANE; ++u) {
         const int i = i0 + u * 32 + lane;
-        v[u] = i < NX ? src[i] : 0.0;
+        v[u] = (i >= nodes.x && i <= nodes.y) ? src[i] : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < PULL_PER_LANE; ++u) {
@@ -115,9 +130,15 @@ struct Staging {
 };
 
 // Streams and events of one call; synchronised and released on every exit.
+// With opts.verbose >= 2 the call also times its phases (tm[]: start, sigma
+// in, a in, built, solved, |E| done, end) and prints them.
 struct CallStreams {
   cudaStream_t main = nullptr, side = nullptr;
   cudaEvent_t ev_sig = nullptr, ev_a = nullptr, ev_solved = nullptr;
+  cudaEvent_t tm[7] = {};
+  void mark(int i, cudaStream_t st) {
+    if (tm[i]) cudaEventRecord(tm[i], st);
+  }
   ~CallStreams() {
     cudaStreamSynchronize(main);
     if (side) {
@@ -127,6 +148,8 @@ struct CallStreams {
     if (ev_sig) cudaEventDestroy(ev_sig);
     if (ev_a) cudaEventDestroy(ev_a);
     if (ev_solved) cudaEventDestroy(ev_solved);
+    for (cudaEvent_t e : tm)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -169,10 +192,10 @@ extern "C" spfd_status spfd_pipeline_host(const double *sigma_host, const double
   CallStreams cs;
   cs.main = (cudaStream_t)stream;
   double *sig_d = nullptr, *a_d = nullptr, *psi_d = nullptr, *E_d = nullptr;
-  unsigned char *rowc = nullptr;
+  int2 *span = nullptr;
   if (stg.get(&sig_d, nvox) != cudaSuccess || stg.get(&a_d, 3 * NN) != cudaSuccess ||
       stg.get(&psi_d, NN) != cudaSuccess || stg.get(&E_d, nvox) != cudaSuccess ||
-      stg.get(&rowc, (size_t)nrows) != cudaSuccess) {
+      stg.get(&span, (size_t)nrows) != cudaSuccess) {
     cudaGetLastError();
     return fail(SPFD_ENOMEM, "device staging buffers for the host pipeline");
   }
@@ -180,34 +203,52 @@ extern "C" spfd_status spfd_pipeline_host(const double *sigma_host, const double
   CU(cudaEventCreateWithFlags(&cs.ev_sig, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&cs.ev_a, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&cs.ev_solved, cudaEventDisableTiming));
+  const bool timed = opts && opts->verbose >= 2;
+  if (timed)
+    for (cudaEvent_t &e : cs.tm) CU(cudaEventCreate(&e));
+  cs.mark(0, cs.main);
   // 1. sigma in
   CU(cudaMemcpyAsync(sig_d, sigma_host, nvox * sizeof(double), cudaMemcpyHostToDevice,
                      cs.main));
   CU(cudaEventRecord(cs.ev_sig, cs.main));
+  cs.mark(1, cs.main);
   // 2. the rows of a the solve and |E| read, beside the build
   CU(cudaStreamWaitEvent(cs.side, cs.ev_sig, 0));
   const double *a_view = device_view(a_host, stg.device);
   if (a_view) {
-    k_row_any<<<(unsigned)std::min<long long>((nrows + 7) / 8, 152LL * 16), 256, 0, cs.side>>>(
-        sig_d, nx, nrows, rowc);
+    k_row_span<<<(unsigned)std::min<long long>((nrows + 7) / 8, 152LL * 16), 256, 0,
+                 cs.side>>>(sig_d, nx, nrows, span);
     CU(cudaGetLastError());
     const long long arows = 3LL * (nz + 1) * (ny + 1);
-    k_pull_rows<<<(unsigned)std::min<long long>((arows + 7) / 8, 152LL * 16), 256, 0,
-                  cs.side>>>(a_view, rowc, nx, ny, nz, a_d);
+    // one block per SM: the pull is bound by the chip-to-chip link, and
+    // more blocks only take SM slots from the build running beside it
+    k_pull_rows<<<(unsigned)std::min<long long>((arows + 7) / 8, 152LL), 256, 0, cs.side>>>(
+        a_view, span, nx, ny, nz, a_d);
     CU(cudaGetLastError());
   } else {
     CU(cudaMemcpyAsync(a_d, a_host, 3 * NN * sizeof(double), cudaMemcpyHostToDevice, cs.side));
   }
   CU(cudaEventRecord(cs.ev_a, cs.side));
+  cs.mark(2, cs.side);
   // 3. build
   spfd_ctx *ctx = nullptr;
-  spfd_status s = spfd_build(sig_d, nx, ny, nz, h, opts, cs.main, &ctx);
+  // the build's own phase marks (verbose >= 2) synchronise its stream, which
+  // would distort the call's phase times: the build gets verbose <= 1
+  spfd_opts bopts;
+  if (opts) {
+    bopts = *opts;
+    if (bopts.verbose > 1) bopts.verbose = 1;
+  } else {
+    spfd_opts_default(&bopts);
+  }
+  spfd_status s = spfd_build(sig_d, nx, ny, nz, h, &bopts, cs.main, &ctx);
   if (s != SPFD_OK) return s;
   struct CtxGuard {
     spfd_ctx *c;
     ~CtxGuard() { spfd_destroy(c); }
   } guard{ctx};
   const int64_t build_launches = ctx->info.launches;
+  cs.mark(3, cs.main);
   // 4. solve once a is in
   CU(cudaStreamWaitEvent(cs.main, cs.ev_a, 0));
   spfd_info inf{};
@@ -215,13 +256,25 @@ extern "C" spfd_status spfd_pipeline_host(const double *sigma_host, const double
   if (s != SPFD_OK && s != SPFD_ENOTCONVERGED) return s;
   const std::string msg = last_error_copy();
   // 5. Psi out beside |E|, then |E| out
+  cs.mark(4, cs.main);
   CU(cudaEventRecord(cs.ev_solved, cs.main));
   CU(cudaStreamWaitEvent(cs.side, cs.ev_solved, 0));
   CU(cudaMemcpyAsync(psi_host, psi_d, NN * sizeof(double), cudaMemcpyDeviceToHost, cs.side));
   TRY(spfd_efield(ctx, a_d, psi_d, omega, E_d));
+  cs.mark(5, cs.main);
   CU(cudaMemcpyAsync(E_host, E_d, nvox * sizeof(double), cudaMemcpyDeviceToHost, cs.main));
   CU(cudaStreamSynchronize(cs.side));
   CU(cudaStreamSynchronize(cs.main));
+  if (timed) {  // both streams are idle: the mark's time is the end of the call's work
+    cs.mark(6, cs.main);
+    CU(cudaStreamSynchronize(cs.main));
+    float t[7] = {};
+    for (int i = 1; i < 7; ++i) cudaEventElapsedTime(&t[i], cs.tm[0], cs.tm[i]);
+    fprintf(stderr,
+            "[spfd] pipeline: sigma in %.3f ms, a in %.3f, built %.3f, solved %.3f, "
+            "|E| %.3f, end %.3f (from the call's start)\n",
+            t[1], t[2], t[3], t[4], t[5], t[6]);
+  }
   if (info) {
     *info = inf;
     info->launches = build_launches + inf.launches + (a_view ? 2 : 0) + 1;
