@@ -190,11 +190,13 @@ spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host, double tol,
  * (spfd_build + spfd_solve + spfd_efield + spfd_destroy, with the copies).
  *   sigma_host  [nz][ny][nx] FP64 conductivities, host.
  *   a_host      [3][nz+1][ny+1][nx+1] FP64 edge potentials, host.  Only the
- *               rows (fixed edge direction, y and z node index) that hold an
- *               edge of a conducting voxel are read; when the device can read
- *               the memory directly (pinned memory, or any memory where
- *               pageable-memory access is supported) they are pulled by the
- *               GPU while the operator is built, else a is copied whole.
+ *               edges of conducting voxels are read: in each row (fixed edge
+ *               direction, y and z node index) the nodes from the first to
+ *               one past the last conducting voxel of the voxel rows it
+ *               touches; when the device can read the memory directly
+ *               (pinned memory, or any memory where pageable-memory access
+ *               is supported) they are pulled by the GPU while the operator
+ *               is built, else a is copied whole.
  *   nx..h       as in spfd_build; tol as in spfd_solve; omega as in
  *               spfd_efield; opts NULL for defaults.
  *   stream      cudaStream_t (NULL = legacy default stream); a second stream
@@ -203,6 +205,7 @@ spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host, double tol,
  *   E_host      [nz][ny][nx] FP64 output in V/m, host.
  *   info        optional report of the solve; launches counts every kernel
  *               of the call.
+ * With opts->verbose >= 2 the call prints its phase times to stderr.
  * Device buffers come from the library's block cache and are returned to it.
  * Synchronises.  Returns SPFD_ENOTCONVERGED (Psi and |E| written) if tol was
  * not reached.  Pinned host arrays give the fastest copies. */
