@@ -202,7 +202,11 @@ spfd_status spfd_solve_host(spfd_ctx *ctx, const double *a_host, double tol,
  *   stream      cudaStream_t (NULL = legacy default stream); a second stream
  *               of the call's own carries the copy of a and of Psi.
  *   psi_host    [nz+1][ny+1][nx+1] FP64 output, host.
- *   E_host      [nz][ny][nx] FP64 output in V/m, host.
+ *   E_host      [nz][ny][nx] FP64 output in V/m, host.  When the device can
+ *               write both directly, host threads of the call zero them
+ *               during the solve and the GPU writes only the spans of the
+ *               unknowns' node rows (Psi) and of the conducting voxels' rows
+ *               (|E|); else they are copied whole.
  *   info        optional report of the solve; launches counts every kernel
  *               of the call.
  * With opts->verbose >= 2 the call prints its phase times to stderr.

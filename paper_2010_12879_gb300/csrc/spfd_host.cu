@@ -14,13 +14,20 @@
 //   3. meanwhile builds the operator and hierarchy (spfd_build),
 //   4. solves Eq. 3 once the rows of a have arrived (spfd_solve),
 //   5. evaluates |E| (spfd_efield) while Psi goes back on the second stream,
-//      then copies |E| back.
+//      then copies |E| back.  Where the device can write the output arrays
+//      directly, host threads zero them while the GPU builds and solves, and
+//      the GPU then writes only the spans of nonzero values (the unknowns'
+//      node rows of Psi, the conducting voxels' rows of |E|): about a quarter
+//      of the bytes cross the link.
 // The device buffers come from the library's block cache and go back to it,
 // so repeated calls of one problem size do not call cudaMalloc.
 //
 // Host memory that the device can read directly (pinned, or any memory on a
 // system with pageable-memory access) is pulled row by row; otherwise a
 // is copied whole.
+#include <cstring>
+#include <thread>
+
 #include "spfd_ctx.cuh"
 
 namespace spfd {
@@ -108,6 +115,51 @@ k_pull_rows(const double *__restrict__ a_host, const int2 *__restrict__ span, in
     }
   }
 }
+
+// The spans of rows of the node grid (Psi: node row (j, k), the nodes of
+// its unknowns lie in row_nodes(..., 0, j, k)) or of the voxel grid (|E|:
+// span[r], the conducting voxels) from device rows to host rows; the rest of
+// each host row is left as it is (zeroed by the host beforehand).  One warp
+// per row.
+template <bool NODES>
+__global__ void __launch_bounds__(256)
+k_push_spans(const double *__restrict__ src, const int2 *__restrict__ span, int nx, int ny,
+             int nz, double *__restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  const size_t W = NODES ? (size_t)nx + 1 : (size_t)nx;
+  const long long nrows = NODES ? (long long)(nz + 1) * (ny + 1) : (long long)nz * ny;
+  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows;
+       r += ((long long)gridDim.x * blockDim.x) >> 5) {
+    int2 q;
+    if constexpr (NODES) q = row_nodes(span, ny, nz, 0, (int)(r % (ny + 1)), (int)(r / (ny + 1)));
+    else q = span[r];
+    // an empty row has q.y < 0 (voxel rows: (-1, -1); node rows: lo > hi)
+    if (q.y < 0 || q.x > q.y) continue;
+    const int lo = max(q.x, 0), hi = min(q.y, (int)W - 1);
+    const double *s = src + (size_t)r * W;
+    double *d = dst + (size_t)r * W;
+    for (int i = lo + lane; i <= hi; i += 32) d[i] = s[i];
+  }
+}
+
+// Host threads zeroing host arrays while the GPU works; joined before the
+// GPU writes into them, and on every exit.
+struct HostZero {
+  std::vector<std::thread> t;
+  void start(double *p, size_t n, int parts) {
+    const size_t chunk = (n + parts - 1) / parts;
+    for (size_t a = 0; a < n; a += chunk) {
+      const size_t b = std::min(n, a + chunk);
+      t.emplace_back([p, a, b] { std::memset(p + a, 0, (b - a) * sizeof(double)); });
+    }
+  }
+  void join() {
+    for (auto &x : t)
+      if (x.joinable()) x.join();
+    t.clear();
+  }
+  ~HostZero() { join(); }
+};
 
 // Device blocks from the library's cache, returned (after the streams have
 // been synchronised) when the call ends.
@@ -207,18 +259,27 @@ extern "C" spfd_status spfd_pipeline_host(const double *sigma_host, const double
   if (timed)
     for (cudaEvent_t &e : cs.tm) CU(cudaEventCreate(&e));
   cs.mark(0, cs.main);
+  // output arrays the device can write: host threads zero them now, the GPU
+  // writes the spans of nonzero values at the end
+  double *psi_view = const_cast<double *>(device_view(psi_host, stg.device));
+  double *E_view = const_cast<double *>(device_view(E_host, stg.device));
+  const bool push = psi_view && E_view;
+  HostZero zero;
   // 1. sigma in
   CU(cudaMemcpyAsync(sig_d, sigma_host, nvox * sizeof(double), cudaMemcpyHostToDevice,
                      cs.main));
   CU(cudaEventRecord(cs.ev_sig, cs.main));
   cs.mark(1, cs.main);
+
   // 2. the rows of a the solve and |E| read, beside the build
   CU(cudaStreamWaitEvent(cs.side, cs.ev_sig, 0));
   const double *a_view = device_view(a_host, stg.device);
-  if (a_view) {
+  if (a_view || push) {
     k_row_span<<<(unsigned)std::min<long long>((nrows + 7) / 8, 152LL * 16), 256, 0,
                  cs.side>>>(sig_d, nx, nrows, span);
     CU(cudaGetLastError());
+  }
+  if (a_view) {
     const long long arows = 3LL * (nz + 1) * (ny + 1);
     // one block per SM: the pull is bound by the chip-to-chip link, and
     // more blocks only take SM slots from the build running beside it
@@ -249,6 +310,14 @@ extern "C" spfd_status spfd_pipeline_host(const double *sigma_host, const double
   } guard{ctx};
   const int64_t build_launches = ctx->info.launches;
   cs.mark(3, cs.main);
+  if (push) {
+    // the host zeroes the outputs during the solve, which uses neither host
+    // memory nor the host's cores (beside the copies in and the build it
+    // took memory bandwidth and cycles from them); two threads per array
+    // finish well within the solve
+    zero.start(psi_host, NN, 2);
+    zero.start(E_host, nvox, 2);
+  }
   // 4. solve once a is in
   CU(cudaStreamWaitEvent(cs.main, cs.ev_a, 0));
   spfd_info inf{};
@@ -259,10 +328,24 @@ extern "C" spfd_status spfd_pipeline_host(const double *sigma_host, const double
   cs.mark(4, cs.main);
   CU(cudaEventRecord(cs.ev_solved, cs.main));
   CU(cudaStreamWaitEvent(cs.side, cs.ev_solved, 0));
-  CU(cudaMemcpyAsync(psi_host, psi_d, NN * sizeof(double), cudaMemcpyDeviceToHost, cs.side));
+  if (!push)
+    CU(cudaMemcpyAsync(psi_host, psi_d, NN * sizeof(double), cudaMemcpyDeviceToHost,
+                       cs.side));
   TRY(spfd_efield(ctx, a_d, psi_d, omega, E_d));
   cs.mark(5, cs.main);
-  CU(cudaMemcpyAsync(E_host, E_d, nvox * sizeof(double), cudaMemcpyDeviceToHost, cs.main));
+  if (push) {
+    // after |E| (beside it the SM writes over the link slowed it down), one
+    // block per SM (bound by the link)
+    zero.join();  // the host's zeros are in before the GPU writes the spans
+    const unsigned blocks =
+        (unsigned)std::min<long long>(((long long)(nz + 1) * (ny + 1) + 7) / 8, 152LL);
+    k_push_spans<true><<<blocks, 256, 0, cs.main>>>(psi_d, span, nx, ny, nz, psi_view);
+    CU(cudaGetLastError());
+    k_push_spans<false><<<blocks, 256, 0, cs.main>>>(E_d, span, nx, ny, nz, E_view);
+    CU(cudaGetLastError());
+  } else {
+    CU(cudaMemcpyAsync(E_host, E_d, nvox * sizeof(double), cudaMemcpyDeviceToHost, cs.main));
+  }
   CU(cudaStreamSynchronize(cs.side));
   CU(cudaStreamSynchronize(cs.main));
   if (timed) {  // both streams are idle: the mark's time is the end of the call's work
@@ -277,7 +360,8 @@ extern "C" spfd_status spfd_pipeline_host(const double *sigma_host, const double
   }
   if (info) {
     *info = inf;
-    info->launches = build_launches + inf.launches + (a_view ? 2 : 0) + 1;
+    info->launches = build_launches + inf.launches + (a_view || push ? 1 : 0) +
+                     (a_view ? 1 : 0) + (push ? 2 : 0) + 1;
   }
   set_error(msg);
   return s;
