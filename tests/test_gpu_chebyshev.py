@@ -127,3 +127,34 @@ def test_chebyshev_body_2mm_converges(torch_cuda, spfd):
             assert st == spfd.SPFD_OK and info["converged"], info
             assert info["rel_res_true"] <= 1e-8, info
             assert info["iters"] <= 40, info
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_chebyshev_group_equals_single_solves(torch_cuda, spfd, precision):
+    """The captured group graph records the same Chebyshev sweeps as the
+    host-driven solve: each body's Psi, iteration count and residual equal
+    its single solve's."""
+    torch = torch_cuda
+    rng = np.random.default_rng(45)
+    phs = [random_phantom(13, 9, 11, rng, air_fraction=0.55),
+           body_phantom(64, 40, 224, h=8e-3)]
+    srcs = [rng.normal(size=(3, 12, 10, 14)) * 1e-9,
+            loop_potential(phs[1].dims, phs[1].h, phs[1].origin)]
+    prec = spfd.SPFD_FP64 if precision == "fp64" else spfd.SPFD_MIXED
+    solvers = [spfd.Solver(_dev(torch, ph.sigma), ph.h, precision=prec,
+                           smoother=spfd.SPFD_SMOOTHER_CHEBYSHEV, cheb_degree=2) for ph in phs]
+    A = [_dev(torch, a) for a in srcs]
+    try:
+        with spfd.Group(solvers) as G:
+            psis, infos, st = G.solve(A, 1e-10)
+            assert st == spfd.SPFD_OK
+            psis = [p.clone() for p in psis]
+        for S, a, p, i in zip(solvers, A, psis, infos):
+            psi_s, info_s, st_s = S.solve(a, 1e-10)
+            assert st_s == spfd.SPFD_OK and i["converged"]
+            assert torch.equal(p, psi_s)
+            for k in ("iters", "outer_iters", "rel_res_true"):
+                assert i[k] == info_s[k], (k, i[k], info_s[k])
+    finally:
+        for S in solvers:
+            S.close()
