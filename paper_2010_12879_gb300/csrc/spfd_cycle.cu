@@ -390,11 +390,43 @@ k_cheb(size_t S, const T *__restrict__ wdinv, const T *__restrict__ r, T *__rest
 // Restriction r_c(I) = sum_d P[d][I] r_f(2I + d) (P^T, the adjoint of the
 // prolongation below).  A coarse brick B reads the 17^3 fine nodes
 // 16B-1 .. 16B+15 (per axis) from the 27 fine bricks 2B-1 .. 2B+1.
-// The 17^3 fine nodes of brick bk's children into fs (sk: the child table).
+// The 17^3 fine nodes of brick bk's children into fs (sk: the child table):
+// the 8 child bricks (16^3 nodes, fs[1..16]^3) as 16-byte vectors, then the
+// three planes fs[0][*][*], fs[1..16][0][*] and fs[1..16][1..16][0] from the
+// bricks before them, one value per thread.
 template <typename T, bool COH>
 __device__ __forceinline__ void restrict_fill(T (*fs)[17][17], const T *src, const int *sk) {
-  for (int q = threadIdx.x; q < 17 * 17 * 17; q += NT) {
-    const int fz = q / 289, fy = (q / 17) % 17, fx = q % 17;
+  constexpr int VN = 16 / (int)sizeof(T);  // values per vector
+  constexpr int VPB = BV / VN;             // vectors per brick
+  for (int q = threadIdx.x; q < 8 * VPB; q += NT) {
+    const int cb = q / VPB, e0 = (q % VPB) * VN;
+    const int ox = cb & 1, oy = (cb >> 1) & 1, oz = cb >> 2;
+    const int nb = sk[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    const int lx = e0 & 7, ly = (e0 >> 3) & 7, lz = e0 >> 6;
+    V16<T> v;
+    if (nb >= 0) {
+      const T *p = src + (size_t)nb * BV + e0;
+      if constexpr (COH) *reinterpret_cast<uint4 *>(&v) = __ldcg(reinterpret_cast<const uint4 *>(p));
+      else v = ld16(p);
+    } else {
+#pragma unroll
+      for (int i = 0; i < VN; ++i) v.v[i] = T(0);
+    }
+    T *row = &fs[1 + 8 * oz + lz][1 + 8 * oy + ly][1 + 8 * ox + lx];
+#pragma unroll
+    for (int i = 0; i < VN; ++i) row[i] = v.v[i];
+  }
+  for (int q = threadIdx.x; q < 289 + 272 + 256; q += NT) {
+    int fz, fy, fx;
+    if (q < 289) {
+      fz = 0; fy = q / 17; fx = q % 17;
+    } else if (q < 289 + 272) {
+      const int u = q - 289;
+      fz = 1 + u / 17; fy = 0; fx = u % 17;
+    } else {
+      const int u = q - 289 - 272;
+      fz = 1 + u / 16; fy = 1 + u % 16; fx = 0;
+    }
     const int nb = sk[((fz + 7) >> 3) * 9 + ((fy + 7) >> 3) * 3 + ((fx + 7) >> 3)];
     fs[fz][fy][fx] = nb >= 0
         ? ldv<COH>(&src[(size_t)nb * BV + (((fz - 1) & 7) * 8 + ((fy - 1) & 7)) * 8 +
