@@ -70,16 +70,41 @@ __device__ __forceinline__ void load_nbr(const Grid &g, int bk, int *sn) {
   if (threadIdx.x < 27) sn[threadIdx.x] = g.nbr[(size_t)bk * 27 + threadIdx.x];
 }
 
-// Brick + full halo of x (27-point stencils).
+// Brick + full halo of x (27-point stencils): the brick itself as 16-byte
+// vectors, the 488 halo values from the neighbour bricks one per thread
+// (planes tz = 0 and 9, then ty = 0 and 9, then tx = 0 and 9).
 template <typename T, bool COH = false>
 __device__ __forceinline__ void tile_full(T (*tl)[10][10], const T *__restrict__ x,
                                           int bk, const int *sn) {
-  for (int q = threadIdx.x; q < 1000; q += NT) {
-    const int tz = q / 100, ty = (q / 10) % 10, tx = q % 10;
+  constexpr int VN = 16 / (int)sizeof(T), VPB = BV / VN;
+  const int t = threadIdx.x;
+  if (t < VPB) {
+    const int e0 = t * VN, lx = e0 & 7, ly = (e0 >> 3) & 7, lz = e0 >> 6;
+    const T *p = x + (size_t)bk * BV + e0;
+    V16<T> v;
+    if constexpr (COH) *reinterpret_cast<uint4 *>(&v) = __ldcg(reinterpret_cast<const uint4 *>(p));
+    else v = ld16(p);
+    T *row = &tl[1 + lz][1 + ly][1 + lx];
+#pragma unroll
+    for (int i = 0; i < VN; ++i) row[i] = v.v[i];
+  }
+  for (int u = (t + NT - VPB) % NT; u < 488; u += NT) {
+    int tz, ty, tx;
+    if (u < 200) {
+      tz = u < 100 ? 0 : 9;
+      const int r = u % 100;
+      ty = r / 10; tx = r % 10;
+    } else if (u < 360) {
+      const int v = u - 200, w = v % 20;
+      tz = 1 + v / 20; ty = w < 10 ? 0 : 9; tx = w % 10;
+    } else {
+      const int v = u - 360, w = v % 16;
+      tz = 1 + v / 16; ty = 1 + (w >> 1); tx = (w & 1) ? 9 : 0;
+    }
     const int ox = tx == 0 ? -1 : (tx == 9 ? 1 : 0);
     const int oy = ty == 0 ? -1 : (ty == 9 ? 1 : 0);
     const int oz = tz == 0 ? -1 : (tz == 9 ? 1 : 0);
-    const int nb = (ox | oy | oz) ? sn[sidx(ox, oy, oz)] : bk;
+    const int nb = sn[sidx(ox, oy, oz)];
     tl[tz][ty][tx] = nb >= 0
         ? ldv<COH>(&x[(size_t)nb * BV + (((tz - 1) & 7) * 8 + ((ty - 1) & 7)) * 8 + ((tx - 1) & 7)])
         : T(0);
