@@ -76,6 +76,7 @@ void destroy_ctx(spfd_ctx *c) {
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->evsc) cudaEventDestroy(c->evsc);
   delete c;
 }
 
@@ -289,7 +290,7 @@ static ChebCoef cheb_coefficients(double hi, int k) {
 // is fused into the first sweep, using sum(r) left in each right-hand side's
 // Scalars by the preceding x/r update.
 template <typename T>
-T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
+T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz, bool head) {
   Level &lv = c->L[l];
   cudaStream_t st = c->stream;
   const int nl = (int)c->L.size();
@@ -361,7 +362,9 @@ T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz) {
     return cur;
   }
   T *cur = lv.X<T>(), *oth = lv.Tt<T>();
-  if (proj)
+  if (head)  // vcycle_head ran the projected first sweep already
+    ;
+  else if (proj)
     SPFD_LAUNCH(c, "jacobi_first_l0", f32, 1, 4 * w * S, 2 * S,
                 launch_jacobi_first_proj<T>(lv.g, wd, bl, cur, c->sc, inv, st, nk,
                                             block_order(c, TF_JFIRST, l)));
@@ -577,7 +580,7 @@ static spfd_status true_residual(spfd_ctx *c, const double *bb, double *rel, int
 // p = z + beta p, for the first nk right-hand sides; first = 1 on the first
 // iteration (beta = 0).
 template <typename T>
-spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
+spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk, bool head) {
   const int nb = c->L[0].g.nb;
   const bool f32 = sizeof(T) == 4;
   const double w = sizeof(T), S = (double)c->L[0].S * nk;
@@ -591,7 +594,7 @@ spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
   // sweep on the 2 mm body), so FP64 keeps k_dot_rz.
   const bool fused = f32 && c->L.size() > 1 && c->opts.nu_post >= 1 &&
                      c->opts.smoother == SPFD_SMOOTHER_JACOBI;
-  T *z = vcycle<T>(c, 0, r, true, nk, fused);
+  T *z = vcycle<T>(c, 0, r, true, nk, fused, head);
   if (fused)
     SPFD_LAUNCH(c, "finish_rz", false, 1, 16.0 * jacobi7_rz_partials<T>(nb) * nk, 0,
                 launch_finish_rz(jacobi7_rz_partials<T>(nb), c->partials,
@@ -609,10 +612,10 @@ spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk) {
                                 c->cstride));
   return launch_check("V-cycle");
 }
-template spfd_status precondition_step<double>(spfd_ctx *, double *, double *, int, int);
-template spfd_status precondition_step<float>(spfd_ctx *, float *, float *, int, int);
+template spfd_status precondition_step<double>(spfd_ctx *, double *, double *, int, int, bool);
+template spfd_status precondition_step<float>(spfd_ctx *, float *, float *, int, int, bool);
 template spfd_status project<double>(spfd_ctx *, double *, int, int);
-template double *vcycle<double>(spfd_ctx *, int, double *, bool, int, bool);
+template double *vcycle<double>(spfd_ctx *, int, double *, bool, int, bool, bool);
 
 struct PcgResult {
   int iters = 0;
@@ -627,6 +630,30 @@ struct PcgResult {
 // one that has stopped is frozen on the device (the x/r update skips it), so
 // each reaches the iterate it would reach alone.  Launches cover the
 // right-hand sides up to the last one still running.
+// The level-0 V-cycle's first kernel, when it depends on nothing but r and
+// the scalars update_xr left on the device (weighted Jacobi, one component,
+// a coarser level below): the projected first sweep from the zero guess.
+// The CG loop launches it right after the scalars' copy to the host, so the
+// GPU runs it while the host waits for the copy and takes its decisions,
+// instead of idling through that round trip; the V-cycle then starts with
+// its residual.  It is the same launch as the V-cycle's own, so results are
+// unchanged bit for bit; when the solve stops there, one sweep is spent.
+template <typename T>
+static bool vcycle_head_ok(const spfd_ctx *c) {
+  return c->opts.smoother == SPFD_SMOOTHER_JACOBI && c->ncomp == 1 && c->L.size() > 1;
+}
+template <typename T>
+static spfd_status vcycle_head(spfd_ctx *c, T *r, int nk) {
+  Level &lv = c->L[0];
+  const bool f32 = sizeof(T) == 4;
+  const double w = sizeof(T), S = (double)lv.S * nk;
+  const double inv = c->ndof ? 1.0 / (double)c->ndof : 0.0;
+  SPFD_LAUNCH(c, "jacobi_first_l0", f32, 1, 4 * w * S, 2 * S,
+              launch_jacobi_first_proj<T>(lv.g, lv.WDINV<T>(), r, lv.X<T>(), c->sc, inv,
+                                          c->stream, nk, block_order(c, TF_JFIRST, 0)));
+  return launch_check("first sweep");
+}
+
 // T = double: the operator is the FP64 one and the stopping rule recomputes
 // the true residual (restarting from it when the recursion has drifted).
 // T = float: the inner solve of the refinement, stopped on the recursive
@@ -660,11 +687,12 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
     }
   }
   int na = active_end();
-  auto precondition = [&](int first) -> spfd_status {
-    return precondition_step<T>(c, r, p, first, na);
+  auto precondition = [&](int first, bool head) -> spfd_status {
+    return precondition_step<T>(c, r, p, first, na, head);
   };
+  const bool ahead = vcycle_head_ok<T>(c);
   if (na == 0) return SPFD_OK;
-  TRY(precondition(1));
+  TRY(precondition(1, false));
   // FP64 stopping: the recursive residual triggers a recomputation of the
   // true one; if that is still above tol, CG restarts from it (beta = 0).
   // Three restarts that fail to halve the best true residual mean the
@@ -697,7 +725,17 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
     SPFD_LAUNCH(c, "update_xr", f32, 1, 6 * w * S, 7 * S,
                 launch_update_xr<T>(nb, x, r, p, q, c->sc, c->partials, st, na, c->pstride));
     TRY(launch_check("CG update"));
-    TRY(read_scalars(c, na));
+    CU(cudaMemcpyAsync(c->hsc, c->sc, (size_t)na * sizeof(Scalars), cudaMemcpyDeviceToHost,
+                       st));
+    CU(cudaEventRecord(c->evsc, st));
+    if (ahead) TRY(vcycle_head<T>(c, r, na));
+    bool head = ahead;  // false once the host replaces an r (restart)
+    {
+      cudaError_t e = cudaEventSynchronize(c->evsc);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess)
+        return fail(SPFD_ECUDA, "reading solver scalars: %s", cudaGetErrorString(e));
+    }
     check.clear();
     broke.clear();
     for (int j = 0; j < na; ++j) {
@@ -731,6 +769,13 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
                          cudaMemcpyDeviceToDevice, st));
       TRY(project<T>(c, r + (size_t)j * S0, 1, j));
       TRY(batch_flags(c, j, 1, 1, -1, 1));
+      if (head) {
+        // the V-cycle runs the first sweep again: the other right-hand
+        // sides' r were projected by the look-ahead sweep, so their means
+        // are cleared and the sweep gives them the same values again
+        TRY(batch_flags(c, 0, na, 1, -1, -1));
+        head = false;
+      }
     }
     for (int j = 0; j < na; ++j)
       if (done[j] == 1) {
@@ -738,7 +783,7 @@ static spfd_status pcg(spfd_ctx *c, T *x, T *r, T *p, T *q, const T *opgx,
         done[j] = 2;
       }
     na = active_end();
-    if (na > 0) TRY(precondition(0));
+    if (na > 0) TRY(precondition(0, head));
   }
   return SPFD_OK;
 }

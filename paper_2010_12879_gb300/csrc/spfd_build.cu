@@ -121,20 +121,34 @@ struct TableUpload {
 // twice as fast as the ratio of norms, so 8 steps match 16 of the latter.
 // The iterates are not normalised (they grow by at most 4^8), and nothing is
 // read back: the weights are formed on the device, lambda goes to *lam_dev.
+// The iteration runs in FP32 on FP32 copies of the coefficients and of the
+// inverse diagonal (an estimate taken with a margin needs no more), with v
+// and w in the level's FP64 vectors x and t, cleared afterwards.  The mixed
+// form keeps the coefficient copy as its level's FP32 operator; other copies
+// go to *tmp, released by the caller once the build's work has ended.
 static spfd_status smoother_weights(spfd_ctx *c, int l, double *lam_dev, Scalars *sc,
-                                   double *partials) {
+                                   double *partials, std::vector<float *> *tmp) {
   Level &lv = c->L[l];
   const int nb = lv.g.nb;
   cudaStream_t st = c->stream;
   if (nb == 0) return SPFD_OK;
   if (!partials || !lv.st)
     return fail(SPFD_EINTERNAL, "power iteration needs a 27-point level (%d)", l);
-  double *v = lv.x, *w = lv.t;
-  SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0, launch_power_init(nb, lv.diag, v, st));
+  const size_t S = lv.S;
+  float *st32 = nullptr, *dinv32 = nullptr;
+  TRY(dalloc(c, &st32, 27 * S));
+  if (c->opts.precision == SPFD_MIXED) lv.st32 = st32;
+  else tmp->push_back(st32);
+  TRY(dalloc(c, &dinv32, S));
+  tmp->push_back(dinv32);
+  SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, st32, st));
+  SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.dinv, 1.0, dinv32, st));
+  float *v = reinterpret_cast<float *>(lv.x), *w = reinterpret_cast<float *>(lv.t);
+  SPFD_LAUNCH(c, "setup_power", true, 1, 0, 0, launch_power_init_f32(nb, dinv32, v, st));
   const int iters = 8;
   for (int it = 0; it < iters; ++it) {
-    SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
-                launch_power27(lv.g, lv.st, lv.diag, lv.dinv, v, w, sc, partials, st));
+    SPFD_LAUNCH(c, "setup_power", true, 1, 0, 0,
+                launch_power27_f32(lv.g, st32, dinv32, v, w, sc, partials, st));
     std::swap(v, w);
   }
   SPFD_LAUNCH(c, "setup_power", false, 1, 0, 0,
@@ -400,9 +414,12 @@ static spfd_status setup_mixed_level(spfd_ctx *c, int l) {
                 launch_convert<__nv_bfloat16>(3 * S, lv.gx, 1.0, lv.gxbf, st));
     SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(S, lv.diag, 1.0, lv.diag32, st));
   } else {
-    TRY(dalloc(c, &lv.st32, 27 * S));
+    if (!lv.st32) {  // the coarsest level (no power iteration)
+      TRY(dalloc(c, &lv.st32, 27 * S));
+      SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0,
+                  launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
+    }
     TRY(dalloc(c, &lv.P32, 27 * S));
-    SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.st, 1.0, lv.st32, st));
     SPFD_LAUNCH(c, "setup_convert", false, 1, 0, 0, launch_convert<float>(27 * S, lv.P, 1.0, lv.P32, st));
   }
   return launch_check("mixed-precision copies");
@@ -427,6 +444,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   memset(c->hsc, 0, sizeof(Scalars));
   CU(cudaEventCreate(&c->ev0));
   CU(cudaEventCreate(&c->ev1));
+  CU(cudaEventCreateWithFlags(&c->evsc, cudaEventDisableTiming));
   CU(cudaEventRecord(c->ev0, st));
   const int64_t launches0 = c->launch_count;
 
@@ -766,6 +784,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   }
   clk.mark("smoother weights");
   double *gj_spare = nullptr;
+  std::vector<float *> tmp32;  // FP32 copies of the power iterations
   TRY(setup_coarsest(c, clk, &gj_spare));
   clk.mark("coarsest inverse");
   if (ns > 0) {
@@ -777,7 +796,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
       if (i < np) {
         const int l = i + 1;
         Level &lv = c->L[l];
-        TRY(smoother_weights(c, l, lam + l, psc + i, ppart + part_per_level * i));
+        TRY(smoother_weights(c, l, lam + l, psc + i, ppart + part_per_level * i, &tmp32));
         CU(cudaMemsetAsync(lv.x, 0, lv.S * sizeof(double), side.s[i]));
         CU(cudaMemsetAsync(lv.t, 0, lv.S * sizeof(double), side.s[i]));
         if (mixed) TRY(setup_mixed_level(c, l));
@@ -816,6 +835,7 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
   CU(cudaEventRecord(c->ev1, st));
   TRY(sync_check(c, "build"));
   dfree(c, gj_spare);
+  for (float *&p : tmp32) dfree(c, p);
   if (c->hsc->status & DEV_BAD_PIVOT)
     return fail(SPFD_EINTERNAL, "coarsest-level matrix is not positive definite after regularisation");
   if (c->hsc->status & DEV_GRID_WAIT)

@@ -186,6 +186,7 @@ struct spfd_ctx {
   const signed char *ord = nullptr;
   std::vector<spfd::TuneRecord> tune_log;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evsc = nullptr;  // the CG scalars' copy to the host
   spfd_info info{};
   // launch accounting and profiling
   int64_t launch_count = 0;
@@ -307,11 +308,12 @@ inline int block_order(const spfd_ctx *c, int fam, int l) {
 template <typename T>
 spfd_status project(spfd_ctx *c, T *v, int nk = 1, int j0 = 0);
 // V-cycle on level l for nk right-hand sides; returns the corrections.
+// head: the level-0 cycle's first sweep already ran (vcycle_head).
 template <typename T>
-T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz = false);
+T *vcycle(spfd_ctx *c, int l, T *bl, bool proj, int nk, bool rz = false, bool head = false);
 // z = M r, r.z, beta and p = z + beta p for the first nk right-hand sides.
 template <typename T>
-spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk);
+spfd_status precondition_step(spfd_ctx *c, T *r, T *p, int first, int nk, bool head = false);
 // Per-right-hand-side flags (clear_rsum: 1 clears the residual sums; frozen,
 // restart: >= 0 sets that flag) of the nk right-hand sides from j0.
 spfd_status batch_flags(spfd_ctx *c, int j0, int nk, int clear_rsum, int frozen, int restart);

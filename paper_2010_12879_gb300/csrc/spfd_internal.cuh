@@ -550,11 +550,12 @@ void launch_axpy_mixed(int nb, double *x, const float *d, double f,
 void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
                          Scalars *sc, double *partials, cudaStream_t st,
                          const double *fdev = nullptr);
-void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st);
-// w = D^-1 A v on a 27-point level; sc->aux[4] = v.(A v), sc->aux[5] = v.(D v).
-void launch_power27(const Grid &g, const double *st27, const double *diag,
-                    const double *dinv, const double *v, double *w, Scalars *sc,
-                    double *partials, cudaStream_t st);
+// One step w = D^-1 A v of the power iteration on a 27-point level, in FP32
+// on FP32 copies of the coefficients and the inverse diagonal; sc->aux[4] =
+// v.(A v), sc->aux[5] = v.(D v) (D from the centre coefficient), summed in FP64.
+void launch_power_init_f32(int nb, const float *dinv, float *v, cudaStream_t st);
+void launch_power27_f32(const Grid &g, const float *st27, const float *dinv, const float *v,
+                        float *w, Scalars *sc, double *partials, cudaStream_t st);
 void launch_scale(int nb, double *v, double f, cudaStream_t st);
 // Jacobi weights of a 27-point level from its power iteration: lambda =
 // sc->aux[4] / sc->aux[5] (2 if not a positive number), omega = 4 / (3 margin

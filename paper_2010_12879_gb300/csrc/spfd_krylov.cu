@@ -877,52 +877,52 @@ k_energy_grad_sigma(const unsigned char *__restrict__ mask, const double *__rest
 }
 
 // ------------------------------------------------ smoother eigenvalue estimate
-// Deterministic start vector on the unknowns for the power iteration.
+// Power iteration for the Jacobi weight of a 27-point level.  One step is
+// w = D^-1 A v, with the generalized Rayleigh quotient terms v.(A v) and
+// v.(D v) added into sc->aux[4] and sc->aux[5] (last-block reduction);
+// bricks are grid-strided over at most RED_GRID blocks, v is staged in a
+// full-halo tile per brick and every slot is handled by its thread.  The
+// steps run in FP32 on the level's FP32 copies (the 27 coefficients and the
+// inverse diagonal rounded from FP64): the weight is an estimate taken with a
+// 5 % margin, so FP32 rounding (relative 1e-7 per operation) does not move
+// it, and the iteration leaves GB300's narrow FP64 pipe to the kernels that
+// run beside it; only the block totals are widened to FP64.
+// Start vector: 0.5 + k / 65536 from a hash of the slot (exact in FP32), zero
+// where dinv is zero.
 __global__ void __launch_bounds__(NT)
-k_power_init(const double *__restrict__ diag, double *__restrict__ v) {
+k_power_init_f32(const float *__restrict__ dinv, float *__restrict__ v) {
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
   unsigned h = (unsigned)s * 2654435761u;
   h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
-  v[s] = diag[s] > 0.0 ? 0.5 + (double)(h & 0xffff) / 65536.0 : 0.0;
+  v[s] = dinv[s] != 0.f ? 0.5f + (float)(h & 0xffff) * (1.f / 65536.f) : 0.f;
 }
 
-// One power-iteration step for the Jacobi weight of a 27-point level:
-// w = D^-1 A v, with the generalized Rayleigh quotient terms v.(A v) and
-// v.(D v) added into sc->aux[4] and sc->aux[5] (last-block reduction).
-// Bricks are grid-strided over at most RED_GRID blocks; v is staged in a
-// full-halo tile per brick, and thread n handles the brick's n-th active
-// slot (a zero row has w = 0 and adds nothing: its v and diagonal are 0).
+// v.(D v) takes the centre coefficient for D: it equals the diagonal where
+// dinv is nonzero, and v is zero where dinv is zero.
 __global__ void __launch_bounds__(NT)
-k_power27(Grid g, const double *__restrict__ st, const double *__restrict__ diag,
-          const double *__restrict__ dinv, const double *__restrict__ v,
-          double *__restrict__ w, Scalars *sc, double *partials) {
-  __shared__ double tl[10][10][10];
+k_power27_f32(Grid g, const float *__restrict__ st, const float *__restrict__ dinv,
+              const float *__restrict__ v, float *__restrict__ w, Scalars *sc,
+              double *partials) {
+  __shared__ float tl[10][10][10];
   __shared__ int sn[27];
-  __shared__ ActList al;
   const int t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV;
-  double vav = 0.0, vdv = 0.0;
+  float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
   for (int bk = blockIdx.x; bk < g.nb; bk += gridDim.x) {
-    __syncthreads();  // the previous brick's tile and list are no longer read
+    __syncthreads();  // the previous brick's tile is no longer read
     load_nbr(g, bk, sn);
-    act_stage(g, bk, al);
     __syncthreads();
-    tile_full<double>(tl, v, bk, sn);
+    tile_full<float>(tl, v, bk, sn);
     __syncthreads();
-    const size_t base = (size_t)bk * BV;
-    if (!act_on(al, t)) w[base + t] = 0.0;
-    if (t < al.pre[16]) {
-      const int ts = act_slot(al, t);
-      const size_t s = base + ts;
-      const double av = apply27_tile<double>(tl, st, S, s, ts);
-      const double vs = tile_at(tl, ts);
-      w[s] = dinv[s] * av;
-      vav += vs * av;
-      vdv += vs * vs * diag[s];
-    }
+    const size_t s = (size_t)bk * BV + t;
+    const float av = apply27_tile<float>(tl, st, S, s, t);
+    const float vs = tile_at(tl, t);
+    w[s] = dinv[s] * av;
+    two_sum_add(hi[0], lo[0], vs * av, 0.f);
+    two_sum_add(hi[1], lo[1], vs * vs * st[13 * S + s], 0.f);
   }
-  double vals[2] = {vav, vdv}, tot[2];
-  if (grid_sum<2>(vals, partials, &sc->ticket[4], tot)) {
+  double tot[2];
+  if (grid_sum_f32<2>(hi, lo, partials, &sc->ticket[4], tot)) {
     sc->aux[4] = tot[0];
     sc->aux[5] = tot[1];
   }
@@ -1050,14 +1050,13 @@ void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
   if (nb)
     k_scale_to_f32<<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, f, fdev, r32, sc, partials);
 }
-void launch_power_init(int nb, const double *diag, double *v, cudaStream_t st) {
-  if (nb) k_power_init<<<nb, NT, 0, st>>>(diag, v);
+void launch_power_init_f32(int nb, const float *dinv, float *v, cudaStream_t st) {
+  if (nb) k_power_init_f32<<<nb, NT, 0, st>>>(dinv, v);
 }
-void launch_power27(const Grid &g, const double *st27, const double *diag,
-                    const double *dinv, const double *v, double *w, Scalars *sc,
-                    double *partials, cudaStream_t st) {
-  if (g.nb) k_power27<<<std::min(g.nb, RED_GRID), NT, 0, st>>>(g, st27, diag, dinv, v, w, sc,
-                                                                partials);
+void launch_power27_f32(const Grid &g, const float *st27, const float *dinv, const float *v,
+                        float *w, Scalars *sc, double *partials, cudaStream_t st) {
+  if (g.nb)
+    k_power27_f32<<<std::min(g.nb, RED_GRID), NT, 0, st>>>(g, st27, dinv, v, w, sc, partials);
 }
 void launch_scale(int nb, double *v, double f, cudaStream_t st) {
   if (nb) k_scale<<<nb, NT, 0, st>>>(v, f);
