@@ -26,6 +26,7 @@ using namespace spfd;
 static thread_local std::string g_err;
 
 namespace spfd {
+thread_local bool pdl_allowed = true;
 spfd_status fail(spfd_status s, const char *fmt, ...) {
   char buf[512];
   va_list ap;
@@ -534,6 +535,7 @@ static spfd_status batch_orders(spfd_ctx *c, int nk, const signed char **out) {
 // ------------------------------------------------------------------ Krylov
 // Per-right-hand-side flags and sums of the Scalars array, set on the device.
 __global__ void k_batch_flags(Scalars *sc, int nk, int clear_rsum, int frozen, int restart) {
+  pdl_entry();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nk) return;
   if (clear_rsum) {
@@ -548,7 +550,7 @@ spfd_status batch_flags(spfd_ctx *c, int j0, int nk, int clear_rsum, int frozen,
                         int restart) {
   if (nk <= 0) return SPFD_OK;
   SPFD_LAUNCH(c, "flags", false, 1, 0, 0,
-              (k_batch_flags<<<(nk + 127) / 128, 128, 0, c->stream>>>(c->sc + j0, nk, clear_rsum,
+              (pdl(k_batch_flags, (nk + 127) / 128, 128, c->stream)(c->sc + j0, nk, clear_rsum,
                                                                        frozen, restart)));
   return launch_check("batch flags");
 }

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(row_threads<T>(), row_min_blocks<T>())
 k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ r,
             int nk) {
+  pdl_entry();
   constexpr int N = row_n<T>();
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
@@ -48,6 +49,7 @@ k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
           const T *__restrict__ b, T *__restrict__ xout, int nk,
           double *__restrict__ partials = nullptr, size_t pstride = 0) {
+  pdl_entry();
   constexpr int N = row_n_jacobi<T>();
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
@@ -138,6 +140,7 @@ template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_residual27(Grid g, const T *__restrict__ st, const T *__restrict__ x,
              const T *__restrict__ b, T *__restrict__ r, int nk) {
+  pdl_entry();
   __shared__ T tl[rhs_tile<ORD>()][10][10][10];
   __shared__ int sn[27];
   __shared__ ActList al;
@@ -208,6 +211,7 @@ __global__ void __launch_bounds__(NT)
 k_jacobi27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
            const T *__restrict__ xin, const T *__restrict__ b,
            T *__restrict__ xout, int nk) {
+  pdl_entry();
   __shared__ T tl[rhs_tile<ORD>()][10][10][10];
   __shared__ int sn[27];
   __shared__ ActList al;
@@ -247,6 +251,7 @@ template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_jacobi_first(const T *__restrict__ wdinv, const T *__restrict__ b,
                T *__restrict__ x, int nb, int nk) {
+  pdl_entry();
   constexpr int N = V16<T>::N;
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
@@ -266,6 +271,7 @@ template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_jacobi_first_proj(const T *__restrict__ wdinv, T *__restrict__ b,
                     T *__restrict__ x, const Scalars *sc, int nb, int nk) {
+  pdl_entry();
   constexpr int N = V16<T>::N;
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
@@ -300,6 +306,7 @@ __global__ void __launch_bounds__(BV / row_n_jacobi<T>(), row_min_blocks<T>())
 k_cheb7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
         const T *__restrict__ wdinv, const T *__restrict__ xin, const T *__restrict__ b,
         T *__restrict__ xout, T *__restrict__ d, T c1, T c2w) {
+  pdl_entry();
   constexpr int N = row_n_jacobi<T>();
   const int bk = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)g.nb * BV, s0 = row_slot<N>(bk, t);
@@ -322,6 +329,7 @@ __global__ void __launch_bounds__(NT)
 k_cheb27(Grid g, const T *__restrict__ st, const T *__restrict__ wdinv,
          const T *__restrict__ xin, const T *__restrict__ b, T *__restrict__ xout,
          T *__restrict__ d, T c1, T c2w) {
+  pdl_entry();
   __shared__ T tl[10][10][10];
   __shared__ int sn[27];
   __shared__ ActList al;
@@ -358,6 +366,7 @@ template <typename T, bool FIRST>
 __global__ void __launch_bounds__(NT)
 k_cheb(size_t S, const T *__restrict__ wdinv, const T *__restrict__ r, T *__restrict__ d,
        T *__restrict__ x, T c1, T c2w) {
+  pdl_entry();
   constexpr int N = V16<T>::N;
   const size_t off = (size_t)blockIdx.y * S;
   r += off; d += off; x += off;
@@ -465,6 +474,7 @@ template <typename T, int ORD>
 __global__ void __launch_bounds__(NT)
 k_restrict(Grid gc, size_t Sf, const T *__restrict__ P, const T *__restrict__ rf,
            T *__restrict__ bcoarse, int nk) {
+  pdl_entry();
   __shared__ T fs[17][17][17];
   __shared__ int sk[27];
   int bk, rhs;
@@ -565,6 +575,7 @@ template <typename T, int ORD>
 __global__ void __launch_bounds__(128)
 k_prolong(Grid gf, Grid gc, const T *__restrict__ Pc, const T *__restrict__ ec,
           T *__restrict__ ef, int nk) {
+  pdl_entry();
   int pair, rhs;
   unit_rhs<ORD>(nk, pair, rhs);
   const int nr = rhs_tile<ORD>() == 1 ? 1 : min(rhs_tile<ORD>(), nk - rhs);
@@ -577,6 +588,7 @@ template <typename T>
 __global__ void k_coarse_solve(int m, size_t S, const int *__restrict__ idx,
                                const double *__restrict__ Binv,
                                const T *__restrict__ b, T *__restrict__ x) {
+  pdl_entry();
   b += (size_t)blockIdx.y * S;
   x += (size_t)blockIdx.y * S;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -596,28 +608,28 @@ void launch_residual7(const Grid &g, const C *gx, const T *diag, const T *x,
                       const T *b, T *r, cudaStream_t st, int nk, int order) {
   if (g.nb)
     if (order)
-      k_residual7<T, C, 1><<<unit_grid(1, g.nb, nk), row_threads<T>(), 0, st>>>(g, gx, diag, x, b,
+      pdl(k_residual7<T, C, 1>, unit_grid(1, g.nb, nk), row_threads<T>(), st)(g, gx, diag, x, b,
                                                                                 r, nk);
     else
-      k_residual7<T, C, 0><<<unit_grid(0, g.nb, nk), row_threads<T>(), 0, st>>>(g, gx, diag, x, b,
+      pdl(k_residual7<T, C, 0>, unit_grid(0, g.nb, nk), row_threads<T>(), st)(g, gx, diag, x, b,
                                                                                 r, nk);
 }
 template <typename T>
 void launch_residual27(const Grid &g, const T *stc, const T *x, const T *b,
                        T *r, cudaStream_t st, int nk, int order) {
   if (!g.nb) return;
-  if (order == 2) k_residual27<T, 2><<<unit_grid(2, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
-  else if (order) k_residual27<T, 1><<<unit_grid(1, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
-  else k_residual27<T, 0><<<unit_grid(0, g.nb, nk), NT, 0, st>>>(g, stc, x, b, r, nk);
+  if (order == 2) pdl(k_residual27<T, 2>, unit_grid(2, g.nb, nk), NT, st)(g, stc, x, b, r, nk);
+  else if (order) pdl(k_residual27<T, 1>, unit_grid(1, g.nb, nk), NT, st)(g, stc, x, b, r, nk);
+  else pdl(k_residual27<T, 0>, unit_grid(0, g.nb, nk), NT, st)(g, stc, x, b, r, nk);
 }
 template <typename T>
 void launch_jacobi_first(const Grid &g, const T *wdinv, const T *b, T *x,
                          cudaStream_t st, int nk, int order) {
   if (g.nb)
     if (order)
-      k_jacobi_first<T, 1><<<unit_grid(1, g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, g.nb, nk);
+      pdl(k_jacobi_first<T, 1>, unit_grid(1, g.nb, nk), NT / V16<T>::N, st)(wdinv, b, x, g.nb, nk);
     else
-      k_jacobi_first<T, 0><<<unit_grid(0, g.nb, nk), NT / V16<T>::N, 0, st>>>(wdinv, b, x, g.nb, nk);
+      pdl(k_jacobi_first<T, 0>, unit_grid(0, g.nb, nk), NT / V16<T>::N, st)(wdinv, b, x, g.nb, nk);
 }
 template <typename T>
 void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
@@ -627,10 +639,10 @@ void launch_jacobi_first_proj(const Grid &g, const T *wdinv, T *b, T *x,
   if (g.nb)
   {
     if (order)
-      k_jacobi_first_proj<T, 1><<<unit_grid(1, g.nb, nk), NT / V16<T>::N, 0, st>>>(
+      pdl(k_jacobi_first_proj<T, 1>, unit_grid(1, g.nb, nk), NT / V16<T>::N, st)(
           wdinv, b, x, sc, g.nb, nk);
     else
-      k_jacobi_first_proj<T, 0><<<unit_grid(0, g.nb, nk), NT / V16<T>::N, 0, st>>>(
+      pdl(k_jacobi_first_proj<T, 0>, unit_grid(0, g.nb, nk), NT / V16<T>::N, st)(
           wdinv, b, x, sc, g.nb, nk);
   }
 }
@@ -640,10 +652,10 @@ void launch_jacobi7_rz(const Grid &g, const C *gx, const T *diag, const T *wdinv
                        cudaStream_t st, int nk, int order) {
   if (!g.nb) return;
   if (order)
-    k_jacobi7<T, C, 1, true><<<unit_grid(1, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
+    pdl(k_jacobi7<T, C, 1, true>, unit_grid(1, g.nb, nk), BV / row_n_jacobi<T>(), st)(
         g, gx, diag, wdinv, xin, b, xout, nk, partials, pstride);
   else
-    k_jacobi7<T, C, 0, true><<<unit_grid(0, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
+    pdl(k_jacobi7<T, C, 0, true>, unit_grid(0, g.nb, nk), BV / row_n_jacobi<T>(), st)(
         g, gx, diag, wdinv, xin, b, xout, nk, partials, pstride);
 }
 template <typename T>
@@ -656,11 +668,11 @@ void launch_jacobi7(const Grid &g, const C *gx, const T *diag, const T *wdinv,
   if (g.nb)
   {
     if (order)
-      k_jacobi7<T, C, 1><<<unit_grid(1, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
-          g, gx, diag, wdinv, xin, b, xout, nk);
+      pdl(k_jacobi7<T, C, 1>, unit_grid(1, g.nb, nk), BV / row_n_jacobi<T>(), st)(
+          g, gx, diag, wdinv, xin, b, xout, nk, nullptr, (size_t)0);
     else
-      k_jacobi7<T, C, 0><<<unit_grid(0, g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(
-          g, gx, diag, wdinv, xin, b, xout, nk);
+      pdl(k_jacobi7<T, C, 0>, unit_grid(0, g.nb, nk), BV / row_n_jacobi<T>(), st)(
+          g, gx, diag, wdinv, xin, b, xout, nk, nullptr, (size_t)0);
   }
 }
 template <typename T>
@@ -669,11 +681,11 @@ void launch_jacobi27(const Grid &g, const T *stc, const T *wdinv, const T *xin,
   if (g.nb)
   {
     if (order == 2)
-      k_jacobi27<T, 2><<<unit_grid(2, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
+      pdl(k_jacobi27<T, 2>, unit_grid(2, g.nb, nk), NT, st)(g, stc, wdinv, xin, b, xout, nk);
     else if (order)
-      k_jacobi27<T, 1><<<unit_grid(1, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
+      pdl(k_jacobi27<T, 1>, unit_grid(1, g.nb, nk), NT, st)(g, stc, wdinv, xin, b, xout, nk);
     else
-      k_jacobi27<T, 0><<<unit_grid(0, g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, nk);
+      pdl(k_jacobi27<T, 0>, unit_grid(0, g.nb, nk), NT, st)(g, stc, wdinv, xin, b, xout, nk);
   }
 }
 template <typename T>
@@ -682,13 +694,13 @@ void launch_restrict(const Grid &gf, const Grid &gc, const T *P, const T *rf,
   if (gc.nb)
   {
     if (order == 2)
-      k_restrict<T, 2><<<unit_grid(2, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
+      pdl(k_restrict<T, 2>, unit_grid(2, gc.nb, nk), NT, st)(gc, (size_t)gf.nb * BV, P, rf,
                                                                bcoarse, nk);
     else if (order)
-      k_restrict<T, 1><<<unit_grid(1, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
+      pdl(k_restrict<T, 1>, unit_grid(1, gc.nb, nk), NT, st)(gc, (size_t)gf.nb * BV, P, rf,
                                                                bcoarse, nk);
     else
-      k_restrict<T, 0><<<unit_grid(0, gc.nb, nk), NT, 0, st>>>(gc, (size_t)gf.nb * BV, P, rf,
+      pdl(k_restrict<T, 0>, unit_grid(0, gc.nb, nk), NT, st)(gc, (size_t)gf.nb * BV, P, rf,
                                                                bcoarse, nk);
   }
 }
@@ -698,25 +710,25 @@ void launch_prolong(const Grid &gf, const Grid &gc, const T *P, const T *ec,
   if (gf.nb)
   {
     if (order == 2)
-      k_prolong<T, 2><<<unit_grid(2, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
+      pdl(k_prolong<T, 2>, unit_grid(2, (gf.nb + 1) / 2, nk), 128, st)(gf, gc, P, ec, ef, nk);
     else if (order)
-      k_prolong<T, 1><<<unit_grid(1, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
+      pdl(k_prolong<T, 1>, unit_grid(1, (gf.nb + 1) / 2, nk), 128, st)(gf, gc, P, ec, ef, nk);
     else
-      k_prolong<T, 0><<<unit_grid(0, (gf.nb + 1) / 2, nk), 128, 0, st>>>(gf, gc, P, ec, ef, nk);
+      pdl(k_prolong<T, 0>, unit_grid(0, (gf.nb + 1) / 2, nk), 128, st)(gf, gc, P, ec, ef, nk);
   }
 }
 template <typename T, typename C>
 void launch_cheb7(const Grid &g, const C *gx, const T *diag, const T *wdinv, const T *xin,
                   const T *b, T *xout, T *d, double c1, double c2w, cudaStream_t st, int nk) {
   if (g.nb)
-    k_cheb7<T, C><<<dim3(g.nb, nk), BV / row_n_jacobi<T>(), 0, st>>>(g, gx, diag, wdinv, xin,
+    pdl(k_cheb7<T, C>, dim3(g.nb, nk), BV / row_n_jacobi<T>(), st)(g, gx, diag, wdinv, xin,
                                                                     b, xout, d, (T)c1, (T)c2w);
 }
 template <typename T>
 void launch_cheb27(const Grid &g, const T *stc, const T *wdinv, const T *xin, const T *b,
                    T *xout, T *d, double c1, double c2w, cudaStream_t st, int nk) {
   if (g.nb)
-    k_cheb27<T><<<dim3(g.nb, nk), NT, 0, st>>>(g, stc, wdinv, xin, b, xout, d, (T)c1, (T)c2w);
+    pdl(k_cheb27<T>, dim3(g.nb, nk), NT, st)(g, stc, wdinv, xin, b, xout, d, (T)c1, (T)c2w);
 }
 template <typename T>
 void launch_cheb(bool first, size_t S, const T *wdinv, const T *r, T *d, T *x, double c1,
@@ -726,17 +738,16 @@ void launch_cheb(bool first, size_t S, const T *wdinv, const T *r, T *d, T *x, d
   const size_t want = (nv + NT - 1) / NT;
   const unsigned blocks = (unsigned)(want < 152 * 8 ? want : 152 * 8);
   if (first)
-    k_cheb<T, true><<<dim3(blocks, nk), NT, 0, st>>>(S, wdinv, r, d, x, (T)c1, (T)c2w);
+    pdl(k_cheb<T, true>, dim3(blocks, nk), NT, st)(S, wdinv, r, d, x, (T)c1, (T)c2w);
   else
-    k_cheb<T, false><<<dim3(blocks, nk), NT, 0, st>>>(S, wdinv, r, d, x, (T)c1, (T)c2w);
+    pdl(k_cheb<T, false>, dim3(blocks, nk), NT, st)(S, wdinv, r, d, x, (T)c1, (T)c2w);
 }
 template <typename T>
 void launch_coarse_solve(int m, size_t S, const int *idx, const double *Binv,
                          const T *b, T *x, cudaStream_t st, int nk) {
   if (m <= 0) return;
   const int warps_per_block = 8;
-  k_coarse_solve<T><<<dim3((m + warps_per_block - 1) / warps_per_block, nk),
-                      32 * warps_per_block, 0, st>>>(m, S, idx, Binv, b, x);
+  pdl(k_coarse_solve<T>, dim3((m + warps_per_block - 1) / warps_per_block, nk), 32 * warps_per_block, st)(m, S, idx, Binv, b, x);
 }
 
 #define INST_T(T)                                                             \

@@ -587,6 +587,13 @@ spfd_status capture_group(spfd_group *g, const double *const *a, double *const *
     prof[i] = g->ctx[i]->opts.profile;
     l0[i] = g->ctx[i]->launch_count;
   }
+  // the captured kernels are launched plainly (the graph has no host gaps
+  // to hide); restored on every exit
+  struct PdlOff {
+    bool was = pdl_allowed;
+    PdlOff() { pdl_allowed = false; }
+    ~PdlOff() { pdl_allowed = was; }
+  } pdl_off;
   CU(cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeThreadLocal));
   spfd_status s = SPFD_OK;
   cudaError_t e = cudaEventRecord(g->fork, g->origin);

@@ -15,11 +15,61 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace spfd {
 
 constexpr int BE = 8;     // brick edge in nodes
 constexpr int BV = 512;   // nodes per brick
 constexpr int NT = 512;   // threads per brick-kernel block (one node each)
+
+// Programmatic dependent launch.  The solve's kernels (the V-cycle, the
+// Krylov updates and reductions) are launched by pdl() with programmatic
+// stream serialization allowed: a kernel's blocks may be scheduled on the
+// SMs while its predecessor on the stream is still finishing, which hides
+// the launch gap between the solve's many short dependent kernels.  Every
+// kernel launched that way calls pdl_entry() before it touches global
+// memory: griddepcontrol.wait holds it until the predecessor grid has
+// completed and its writes are visible (it returns at once for a kernel
+// launched without the attribute), and griddepcontrol.launch_dependents
+// then lets the next kernel's blocks be scheduled as this grid's blocks
+// retire.  Every read and write thus happens in the order of plain stream
+// launches, and results are unchanged bit for bit.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Whether pdl() sets the attribute on this host thread (cleared while a
+// graph is captured: the captured solves launch from the graph, with no
+// host gaps to hide).
+extern thread_local bool pdl_allowed;
+// pdl(kernel, grid, block, stream)(args...) launches kernel<<<grid, block,
+// 0, stream>>>(args...) with programmatic stream serialization; the kernel
+// must begin with pdl_entry().
+template <typename... P>
+struct PdlLaunch {
+  void (*k)(P...);
+  dim3 grid, block;
+  cudaStream_t st;
+  template <typename... A>
+  cudaError_t operator()(A &&...args) const {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_allowed ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+  }
+};
+template <typename... P>
+inline PdlLaunch<P...> pdl(void (*k)(P...), dim3 grid, dim3 block, cudaStream_t st) {
+  return PdlLaunch<P...>{k, grid, block, st};
+}
 
 // Stencil offset index of (dx, dy, dz) in {-1,0,1}^3; 13 is the centre.
 __host__ __device__ __forceinline__ constexpr int sidx(int dx, int dy, int dz) {

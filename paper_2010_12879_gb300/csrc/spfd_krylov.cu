@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(row_threads<T>(), row_min_blocks<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ p, T *__restrict__ q, double *partials,
             size_t pstride, int nk) {
+  pdl_entry();
   constexpr int N = row_n<T>();
   int bk, rhs;
   unit_rhs<ORD>(nk, bk, rhs);
@@ -234,6 +235,7 @@ template <bool PAIRS>
 __global__ void __launch_bounds__(NT)
 k_finish_pq(const double *__restrict__ partials, int n, double *scratch, Scalars *sc,
             size_t pstride) {
+  pdl_entry();
   partials += (size_t)blockIdx.y * pstride;
   scratch += (size_t)blockIdx.y * pstride;
   sc += blockIdx.y;
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(NT)
 k_update_xr(int nb, T *__restrict__ x, T *__restrict__ r,
             const T *__restrict__ p, const T *__restrict__ q, Scalars *sc,
             double *partials, size_t pstride) {
+  pdl_entry();
   constexpr int N = V16<T>::N;
   sc += blockIdx.y;
   if (sc->frozen) return;  // this right-hand side has converged
@@ -317,6 +320,7 @@ __global__ void __launch_bounds__(NT)
 k_dot_rz(int nb, const T *__restrict__ r, const T *__restrict__ z,
          const int *__restrict__ comp, Scalars *sc, double *partials,
          int first, size_t pstride) {
+  pdl_entry();
   constexpr int N = V16<T>::N;
   {
     const size_t off = (size_t)blockIdx.y * nb * BV;
@@ -349,6 +353,7 @@ template <bool PAIRS>
 __global__ void __launch_bounds__(NT)
 k_finish_rz(const double *__restrict__ partials, int n, double *scratch, Scalars *sc,
             int first, size_t pstride) {
+  pdl_entry();
   partials += (size_t)blockIdx.y * pstride;
   scratch += (size_t)blockIdx.y * pstride;
   sc += blockIdx.y;
@@ -380,6 +385,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
 k_absmax(const T *__restrict__ v, const int *__restrict__ comp, double *ws, int cstride,
          int ncomp) {
+  pdl_entry();
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
   v += (size_t)blockIdx.y * gridDim.x * BV;
   ws += (size_t)blockIdx.y * cstride;
@@ -404,6 +410,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
 k_comp_sum(const T *__restrict__ v, const int *__restrict__ comp, double *ws, int cstride,
            int ncomp) {
+  pdl_entry();
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
   v += (size_t)blockIdx.y * gridDim.x * BV;
   ws += (size_t)blockIdx.y * cstride;
@@ -440,6 +447,7 @@ k_comp_sum(const T *__restrict__ v, const int *__restrict__ comp, double *ws, in
 }
 
 __global__ void k_comp_finish(double *ws, int cstride, int ncomp) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   ws += (size_t)blockIdx.y * cstride;
   if (c >= ncomp) return;
@@ -463,6 +471,7 @@ __global__ void __launch_bounds__(NT)
 k_pupdate(T *__restrict__ p, const T *__restrict__ z,
           const int *__restrict__ comp, const Scalars *sc,
           const double *__restrict__ csum, const int *__restrict__ csize, int cstride) {
+  pdl_entry();
   constexpr int N = V16<T>::N;
   const size_t s0 = (size_t)blockIdx.x * BV + threadIdx.x * N;
   {
@@ -493,6 +502,7 @@ __global__ void __launch_bounds__(NT)
 k_sub_mean(T *__restrict__ v, const int *__restrict__ comp, const Scalars *sc,
            int aux_slot, const double *__restrict__ csum,
            const int *__restrict__ csize, int cstride) {
+  pdl_entry();
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
   v += (size_t)blockIdx.y * gridDim.x * BV;
   sc += blockIdx.y;
@@ -510,6 +520,7 @@ __global__ void __launch_bounds__(NT)
 k_dot(int nb, const T *__restrict__ x, const T *__restrict__ y,
       const int *__restrict__ comp, Scalars *sc, double *partials, int slot,
       size_t pstride) {
+  pdl_entry();
   {
     const size_t off = (size_t)blockIdx.y * nb * BV;
     x += off;
@@ -581,6 +592,7 @@ k_rhs(Grid g, const double *__restrict__ gx, const double *__restrict__ a,
 template <typename T>
 __global__ void k_scatter(Grid g, const T *__restrict__ x,
                           const int *__restrict__ comp, double *__restrict__ psi) {
+  pdl_entry();
   const size_t NN = (size_t)g.NX * g.NY * g.NZ;
   x += (size_t)blockIdx.y * g.nb * BV;
   psi += (size_t)blockIdx.y * NN;
@@ -1000,6 +1012,7 @@ __global__ void k_convert(size_t n, const double *__restrict__ src, double f,
 __global__ void __launch_bounds__(NT)
 k_axpy_mixed(double *__restrict__ x, const float *__restrict__ d, double f,
              const double *__restrict__ fdev) {
+  pdl_entry();
   if (fdev) f = *fdev;
   const size_t s = (size_t)blockIdx.x * BV + threadIdx.x;
   x[s] += f * (double)d[s];
@@ -1011,6 +1024,7 @@ __global__ void __launch_bounds__(NT)
 k_scale_to_f32(int nb, const double *__restrict__ r, double f,
                const double *__restrict__ fdev, float *__restrict__ r32, Scalars *sc,
                double *partials) {
+  pdl_entry();
   if (fdev) f = *fdev;
   Acc<float> acc;
   for (int bk = blockIdx.x; bk < nb; bk += gridDim.x) {
@@ -1043,12 +1057,12 @@ template void launch_convert<__nv_bfloat16>(size_t, const double *, double,
                                             __nv_bfloat16 *, cudaStream_t);
 void launch_axpy_mixed(int nb, double *x, const float *d, double f,
                        cudaStream_t st, const double *fdev) {
-  if (nb) k_axpy_mixed<<<nb, NT, 0, st>>>(x, d, f, fdev);
+  if (nb) pdl(k_axpy_mixed, nb, NT, st)(x, d, f, fdev);
 }
 void launch_scale_to_f32(int nb, const double *r, double f, float *r32,
                          Scalars *sc, double *partials, cudaStream_t st, const double *fdev) {
   if (nb)
-    k_scale_to_f32<<<std::min(nb, RED_GRID), NT, 0, st>>>(nb, r, f, fdev, r32, sc, partials);
+    pdl(k_scale_to_f32, std::min(nb, RED_GRID), NT, st)(nb, r, f, fdev, r32, sc, partials);
 }
 void launch_power_init_f32(int nb, const float *dinv, float *v, cudaStream_t st) {
   if (nb) k_power_init_f32<<<nb, NT, 0, st>>>(dinv, v);
@@ -1075,10 +1089,10 @@ void launch_apply_dot(const Grid &g, const T *gx, const T *diag, const T *p,
                       size_t pstride, int order) {
   if (!g.nb) return;
   if (order)
-    k_apply_dot<T, 1><<<unit_grid(1, g.nb, nk), row_threads<T>(), 0, st>>>(
+    pdl(k_apply_dot<T, 1>, unit_grid(1, g.nb, nk), row_threads<T>(), st)(
         g, gx, diag, p, q, partials, pstride, nk);
   else
-    k_apply_dot<T, 0><<<unit_grid(0, g.nb, nk), row_threads<T>(), 0, st>>>(
+    pdl(k_apply_dot<T, 0>, unit_grid(0, g.nb, nk), row_threads<T>(), st)(
         g, gx, diag, p, q, partials, pstride, nk);
 }
 void launch_finish_rz(int n, const double *partials, double *scratch, Scalars *sc, int first,
@@ -1086,24 +1100,24 @@ void launch_finish_rz(int n, const double *partials, double *scratch, Scalars *s
   if (n <= 0) return;
   const int blocks = std::min(152, (n + NT - 1) / NT);
   if (pairs)
-    k_finish_rz<true><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, first, pstride);
+    pdl(k_finish_rz<true>, dim3(blocks, nk), NT, st)(partials, n, scratch, sc, first, pstride);
   else
-    k_finish_rz<false><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, first, pstride);
+    pdl(k_finish_rz<false>, dim3(blocks, nk), NT, st)(partials, n, scratch, sc, first, pstride);
 }
 void launch_finish_pq(int n, const double *partials, double *scratch, Scalars *sc,
                       cudaStream_t st, int nk, size_t pstride, bool pairs) {
   if (n <= 0) return;
   const int blocks = std::min(152, (n + NT - 1) / NT);
   if (pairs)
-    k_finish_pq<true><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, pstride);
+    pdl(k_finish_pq<true>, dim3(blocks, nk), NT, st)(partials, n, scratch, sc, pstride);
   else
-    k_finish_pq<false><<<dim3(blocks, nk), NT, 0, st>>>(partials, n, scratch, sc, pstride);
+    pdl(k_finish_pq<false>, dim3(blocks, nk), NT, st)(partials, n, scratch, sc, pstride);
 }
 template <typename T>
 void launch_update_xr(int nb, T *x, T *r, const T *p, const T *q, Scalars *sc,
                       double *partials, cudaStream_t st, int nk, size_t pstride) {
   if (nb)
-    k_update_xr<T><<<dim3(std::min(nb, RED_GRID), nk), NT, 0, st>>>(nb, x, r, p, q, sc,
+    pdl(k_update_xr<T>, dim3(std::min(nb, RED_GRID), nk), NT, st)(nb, x, r, p, q, sc,
                                                                     partials, pstride);
 }
 template <typename T>
@@ -1111,7 +1125,7 @@ void launch_dot_rz(int nb, const T *r, const T *z, const int *comp,
                    Scalars *sc, double *partials, int first, cudaStream_t st, int nk,
                    size_t pstride) {
   if (nb)
-    k_dot_rz<T><<<dim3(std::min(nb, RED_GRID), nk), NT, 0, st>>>(nb, r, z, comp, sc, partials,
+    pdl(k_dot_rz<T>, dim3(std::min(nb, RED_GRID), nk), NT, st)(nb, r, z, comp, sc, partials,
                                                                  first, pstride);
 }
 template <typename T>
@@ -1119,27 +1133,27 @@ void launch_comp_sum(int nb, const T *v, const int *comp, double *ws, int ncomp,
                      int cstride, cudaStream_t st, int nk) {
   cudaMemsetAsync(ws, 0, (size_t)nk * cstride * sizeof(double), st);
   if (!nb) return;
-  k_absmax<T><<<dim3(nb, nk), NT, 0, st>>>(v, comp, ws, cstride, ncomp);
-  k_comp_sum<T><<<dim3(nb, nk), NT, 0, st>>>(v, comp, ws, cstride, ncomp);
-  k_comp_finish<<<dim3((ncomp + 255) / 256, nk), 256, 0, st>>>(ws, cstride, ncomp);
+  pdl(k_absmax<T>, dim3(nb, nk), NT, st)(v, comp, ws, cstride, ncomp);
+  pdl(k_comp_sum<T>, dim3(nb, nk), NT, st)(v, comp, ws, cstride, ncomp);
+  pdl(k_comp_finish, dim3((ncomp + 255) / 256, nk), 256, st)(ws, cstride, ncomp);
 }
 template <typename T>
 void launch_pupdate(int nb, T *p, const T *z, const int *comp,
                     const Scalars *sc, const double *csum, const int *csize,
                     double, cudaStream_t st, int nk, int cstride) {
-  if (nb) k_pupdate<T><<<dim3(nb, nk), NT / V16<T>::N, 0, st>>>(p, z, comp, sc, csum, csize, cstride);
+  if (nb) pdl(k_pupdate<T>, dim3(nb, nk), NT / V16<T>::N, st)(p, z, comp, sc, csum, csize, cstride);
 }
 template <typename T>
 void launch_sub_mean(int nb, T *v, const int *comp, const Scalars *sc,
                      int aux_slot, const double *csum, const int *csize,
                      double, cudaStream_t st, int nk, int cstride) {
-  if (nb) k_sub_mean<T><<<dim3(nb, nk), NT, 0, st>>>(v, comp, sc, aux_slot, csum, csize, cstride);
+  if (nb) pdl(k_sub_mean<T>, dim3(nb, nk), NT, st)(v, comp, sc, aux_slot, csum, csize, cstride);
 }
 template <typename T>
 void launch_dot(int nb, const T *x, const T *y, const int *comp, Scalars *sc,
                 double *partials, int slot, cudaStream_t st, int nk, size_t pstride) {
   if (nb)
-    k_dot<T><<<dim3(std::min(nb, RED_GRID), nk), NT, 0, st>>>(nb, x, y, comp, sc, partials,
+    pdl(k_dot<T>, dim3(std::min(nb, RED_GRID), nk), NT, st)(nb, x, y, comp, sc, partials,
                                                               slot, pstride);
 }
 void launch_rhs(const Grid &g, const double *gx, const double *a, double *b,
@@ -1153,7 +1167,7 @@ void launch_scatter(const Grid &g, const T *x, const int *comp, double *psi,
   size_t blocks = (NN + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks == 0) blocks = 1;
-  k_scatter<T><<<dim3((int)blocks, nk), 256, 0, st>>>(g, x, comp, psi);
+  pdl(k_scatter<T>, dim3((int)blocks, nk), 256, st)(g, x, comp, psi);
 }
 void launch_gather(const Grid &g, const double *psi, const int *comp, double *x,
                    cudaStream_t st) {

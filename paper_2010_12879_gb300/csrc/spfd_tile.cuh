@@ -217,6 +217,14 @@ __device__ __forceinline__ Qv<T, N> ldq_nb(const C *__restrict__ v, size_t s0, b
   return nb >= 0 ? ldqn<T, C, N>(v + (size_t)nb * BV + across) : zqn<T, N>();
 }
 
+// The same with the neighbour brick's id already looked up (nb).
+template <typename T, typename C, int N>
+__device__ __forceinline__ Qv<T, N> ldq_nbi(const C *__restrict__ v, size_t s0, bool inside,
+                                            long long in_off, int nb, size_t across) {
+  if (inside) return ldqn<T, C, N>(v + (long long)s0 + in_off);
+  return nb >= 0 ? ldqn<T, C, N>(v + (size_t)nb * BV + across) : zqn<T, N>();
+}
+
 // out = A x (RES = false) or base - A x (RES = true) at this thread's N
 // nodes of brick b, and xc = x there.  FP64: diag*x - sum g x_nbr, with base
 // folded into the first FMA (fewest FP64-pipe operations).  FP32: sum
@@ -234,22 +242,43 @@ __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ 
   const int h = t % TPR, y = (t / TPR) & 7, z = t / (8 * TPR);
   const size_t s0 = row_slot<N>(b, t);
   const size_t rz = (size_t)z * 64 + N * h, ry = (size_t)y * 8 + N * h;
+  // sweeps and residuals: the (at most one per axis) neighbour bricks this
+  // thread reads from are looked up before any load that needs one (7 % and
+  // 6 % faster FP64 sweep and residual, 4-5 % in FP32); the CG operator
+  // measured 11 % slower that way in FP32 and keeps the lookups at its loads
+  int nx = -1, ny = -1, nz = -1;
+  if constexpr (RES) {
+    const int *nt = g.nbr + (size_t)b * 27;
+    nx = __ldg(nt + (h == 0 ? sidx(-1, 0, 0) : sidx(1, 0, 0)));
+    if (y == 0 || y == 7) ny = __ldg(nt + (y == 0 ? sidx(0, -1, 0) : sidx(0, 1, 0)));
+    if (z == 0 || z == 7) nz = __ldg(nt + (z == 0 ? sidx(0, 0, -1) : sidx(0, 0, 1)));
+  }
   xc = ldqn<T, T, N>(x + s0);
   const Qv<T, N> gpx = ldqn<T, C, N>(gx + s0), gpy = ldqn<T, C, N>(gx + S + s0),
                  gpz = ldqn<T, C, N>(gx + 2 * S + s0);
-  const Qv<T, N> xym = ldq_nb<T, T, N>(x, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
-  const Qv<T, N> xyp = ldq_nb<T, T, N>(x, s0, y < 7, 8, g, b, sidx(0, 1, 0), rz);
-  const Qv<T, N> xzm = ldq_nb<T, T, N>(x, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
-  const Qv<T, N> xzp = ldq_nb<T, T, N>(x, s0, z < 7, 64, g, b, sidx(0, 0, 1), ry);
-  const Qv<T, N> gmy = ldq_nb<T, C, N>(gx + S, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
-  const Qv<T, N> gmz = ldq_nb<T, C, N>(gx + 2 * S, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
+  Qv<T, N> xym, xyp, xzm, xzp, gmy, gmz;
+  if constexpr (RES) {
+    xym = ldq_nbi<T, T, N>(x, s0, y > 0, -8, ny, rz + 56);
+    xyp = ldq_nbi<T, T, N>(x, s0, y < 7, 8, ny, rz);
+    xzm = ldq_nbi<T, T, N>(x, s0, z > 0, -64, nz, 448 + ry);
+    xzp = ldq_nbi<T, T, N>(x, s0, z < 7, 64, nz, ry);
+    gmy = ldq_nbi<T, C, N>(gx + S, s0, y > 0, -8, ny, rz + 56);
+    gmz = ldq_nbi<T, C, N>(gx + 2 * S, s0, z > 0, -64, nz, 448 + ry);
+  } else {
+    xym = ldq_nb<T, T, N>(x, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
+    xyp = ldq_nb<T, T, N>(x, s0, y < 7, 8, g, b, sidx(0, 1, 0), rz);
+    xzm = ldq_nb<T, T, N>(x, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
+    xzp = ldq_nb<T, T, N>(x, s0, z < 7, 64, g, b, sidx(0, 0, 1), ry);
+    gmy = ldq_nb<T, C, N>(gx + S, s0, y > 0, -8, g, b, sidx(0, -1, 0), rz + 56);
+    gmz = ldq_nb<T, C, N>(gx + 2 * S, s0, z > 0, -64, g, b, sidx(0, 0, -1), 448 + ry);
+  }
   // row ends: the neighbouring lanes' end values, else the x-neighbour brick
   const T prev_last = __shfl_up_sync(0xffffffffu, xc.v[N - 1], 1);
   const T prev_glast = __shfl_up_sync(0xffffffffu, gpx.v[N - 1], 1);
   const T next_first = __shfl_down_sync(0xffffffffu, xc.v[0], 1);
   T xl, xr, gl;
   if (h == 0) {
-    const int nb = __ldg(&g.nbr[(size_t)b * 27 + sidx(-1, 0, 0)]);
+    const int nb = RES ? nx : __ldg(&g.nbr[(size_t)b * 27 + sidx(-1, 0, 0)]);
     const size_t m = (size_t)nb * BV + (size_t)z * 64 + (size_t)y * 8 + 7;
     xl = nb >= 0 ? x[m] : T(0);
     gl = nb >= 0 ? cvt<T>(gx[m]) : T(0);
@@ -258,7 +287,7 @@ __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ 
     gl = prev_glast;
   }
   if (h == TPR - 1) {
-    const int nb = __ldg(&g.nbr[(size_t)b * 27 + sidx(1, 0, 0)]);
+    const int nb = RES ? nx : __ldg(&g.nbr[(size_t)b * 27 + sidx(1, 0, 0)]);
     xr = nb >= 0 ? x[(size_t)nb * BV + (size_t)z * 64 + (size_t)y * 8] : T(0);
   } else {
     xr = next_first;
