@@ -466,6 +466,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(sig_h.numel() * 8 + a_nodes * 8),
                "d2h_bytes_per_step": int(8 * sum(pushed_values_of_outputs(ph.sigma))),
                "std_s": round(statistics.pstdev(times), 6),
+               "median_s": round(statistics.median(times) / world, 6),
                "a_read": f"{a_nodes} nodes in {a_rows} of {3 * psi.shape[0] * psi.shape[1]} rows "
                          "of a (each row's span of edges of conducting voxels)",
                "iters": pinfo["iters"], "rel_res_true": pinfo["rel_res_true"],
