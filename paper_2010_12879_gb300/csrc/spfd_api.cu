@@ -435,6 +435,9 @@ static spfd_status autotune_orders(spfd_ctx *c, int nk, std::vector<signed char>
   const int nl = (int)c->L.size();
   tab.assign((size_t)TF_COUNT * nl, 0);
   cudaStream_t st = c->stream;
+  // every right-hand side is live while the kernels are timed (the CG
+  // operator skips frozen ones); the solve sets the flags afresh
+  TRY(batch_flags(c, 0, nk, 0, 0, -1));
   cudaEvent_t e0 = take_event(c), e1 = take_event(c);
   struct Give {  // the events go back to the context's pool on every exit
     spfd_ctx *c;

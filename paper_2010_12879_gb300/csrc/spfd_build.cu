@@ -516,21 +516,6 @@ spfd_status build_impl(spfd_ctx *c, const double *sigma) {
                 launch_build_fine(l0.g, sigma, c->nx, c->ny, c->nz, c->h, l0.gx,
                                   l0.diag, l0.dinv, st));
     TRY(launch_check("build fine"));
-    {  // the level-0 row list of the FP64 CG operator
-      int *rows = nullptr, *nact = nullptr, *cnt = nullptr, *off = nullptr;
-      unsigned long long *mask = nullptr;
-      TRY(dalloc(c, &rows, (size_t)std::max(nb0, 1) * 64));
-      TRY(dalloc(c, &nact, 1));
-      TRY(dalloc(c, &cnt, std::max(nb0, 1)));
-      TRY(dalloc(c, &off, std::max(nb0, 1)));
-      TRY(dalloc(c, &mask, std::max(nb0, 1)));
-      CU(cudaMemsetAsync(nact, 0, sizeof(int), st));
-      SPFD_LAUNCH(c, "setup_pack", false, 3, 0, 0,
-                  launch_row_list(nb0, l0.diag, mask, cnt, off, nact, rows, st));
-      TRY(launch_check("row list"));
-      l0.g.rows = rows;
-      l0.g.nact = nact;
-    }
     // connected components of the conducting nodes: the union-find and the
     // root counts run on a stream of their own, overlapping the coarse
     // tables and the hierarchy (which do not need them); the numbering that

@@ -148,35 +148,8 @@ struct Grid {
                         //   every nonzero restricted value needs; a clear bit
                         //   guarantees a zero 27-point row and a zero restriction
                         //   weight column (level 0: unused)
-  const int *rows;      // level 0, FP64 CG operator: [64 nb] the brick rows b * 64 + z * 8 + y,
-                        //   those holding an unknown first (brick and row order), then
-                        //   the others; null: rows follow the bricks
-  const int *nact;      // level 0: device count of the rows holding an unknown
 };
 
-// The FP64 CG operator (k_apply_dot) gives block u the rows
-// rows[64 u .. 64 u + 63] of the level-0 row list: a row past *nact holds no
-// unknown, so a warp of such rows skips the FP64 arithmetic (on GB300 the
-// narrow FP64 pipe bounds the kernel; 11 % of the rows of the 2 mm body's
-// bricks hold no unknown).
-// Thread t of a block with TPR threads per row maps to brick b and the
-// brick-local row-mapping index tl = row * TPR + t % TPR; live tells whether
-// its row holds an unknown.
-template <int TPR>
-__device__ __forceinline__ void row_of_list(const Grid &g, int unit, int t, int &b, int &tl,
-                                            bool &live) {
-  if (!g.rows) {  // no list: block u takes brick u
-    b = unit;
-    tl = t;
-    live = true;
-    return;
-  }
-  const int li = unit * 64 + t / TPR;
-  const int e = __ldg(&g.rows[li]);
-  b = e >> 6;
-  tl = (e & 63) * TPR + t % TPR;
-  live = li < __ldg(g.nact);
-}
 
 // The activity bits (Grid::act) of this thread's warp on brick bk, one node
 // per thread: bit (thread & 31) is this thread's slot.
@@ -394,10 +367,6 @@ __device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, uns
 
 // ---------------------------------------------------------------- launchers
 // Setup (spfd_setup.cu)
-// The level-0 row list (Grid::rows, Grid::nact) from the diagonal; mask,
-// cnt, off: nb entries of scratch each.
-void launch_row_list(int nb, const double *diag, unsigned long long *mask, int *cnt, int *off,
-                     int *nact, int *rows, cudaStream_t st);
 void launch_sigma_flags(const double *sigma, int nx, int ny, int nz, int MX,
                         int MY, unsigned char *flags, unsigned char *mask,
                         int *status, cudaStream_t st);

@@ -201,79 +201,6 @@ void launch_build_fine(const Grid &g, const double *sigma, int nx, int ny,
   k_build_fine<<<g.nb, NT, 0, st>>>(g, sigma, nx, ny, nz, h, gx, diag, dinv);
 }
 
-// ------------------------------------------------ level-0 row list
-// Grid::rows / Grid::nact: the brick rows (8 nodes along x) holding an
-// unknown (diag > 0) first, in brick and row order, then the others.
-// k_row_mask: one 64-thread block per brick, thread = row; cnt[b] = the
-// brick's rows with an unknown, mask[b] their bits.
-__global__ void __launch_bounds__(64)
-k_row_mask(const double *__restrict__ diag, unsigned long long *__restrict__ mask,
-           int *__restrict__ cnt) {
-  const int b = blockIdx.x, r = threadIdx.x;
-  const double2 *d = reinterpret_cast<const double2 *>(diag + (size_t)b * BV + r * 8);
-  bool any = false;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const double2 v = d[q];
-    any |= f64_nonzero(v.x) || f64_nonzero(v.y);
-  }
-  __shared__ unsigned half[2];
-  const unsigned w = __ballot_sync(0xffffffffu, any);
-  if ((r & 31) == 0) half[r >> 5] = w;
-  __syncthreads();
-  if (r == 0) {
-    mask[b] = (unsigned long long)half[0] | ((unsigned long long)half[1] << 32);
-    cnt[b] = __popc(half[0]) + __popc(half[1]);
-  }
-}
-
-// off[b] = exclusive prefix sum of cnt over the bricks, *total = the sum: one
-// block of 1024 threads, each adding a contiguous chunk.
-__global__ void __launch_bounds__(1024)
-k_row_offsets(const int *__restrict__ cnt, int nb, int *__restrict__ off, int *total) {
-  __shared__ int part[1024];
-  const int t = threadIdx.x;
-  const int chunk = (nb + 1023) / 1024, lo = min(nb, t * chunk), hi = min(nb, lo + chunk);
-  int sum = 0;
-  for (int i = lo; i < hi; ++i) sum += cnt[i];
-  part[t] = sum;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the chunk sums
-    const int v = t >= o ? part[t - o] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  int run = part[t] - sum;
-  for (int i = lo; i < hi; ++i) {
-    off[i] = run;
-    run += cnt[i];
-  }
-  if (t == 1023) *total = part[1023];
-}
-
-// rows[]: brick b's rows with an unknown at off[b] + rank, the others after
-// all of those, at total + (64 b - off[b]) + rank.
-__global__ void __launch_bounds__(64)
-k_row_scatter(const unsigned long long *__restrict__ mask, const int *__restrict__ off,
-              const int *__restrict__ total, int *__restrict__ rows) {
-  const int b = blockIdx.x, r = threadIdx.x;
-  const unsigned long long m = mask[b];
-  const unsigned long long below = m & ((1ull << r) - 1ull);
-  const int rank = __popcll(below);
-  const int ob = off[b];
-  if ((m >> r) & 1ull) rows[ob + rank] = b * 64 + r;
-  else rows[*total + (b * 64 - ob) + (r - rank)] = b * 64 + r;
-}
-
-void launch_row_list(int nb, const double *diag, unsigned long long *mask, int *cnt, int *off,
-                     int *nact, int *rows, cudaStream_t st) {
-  if (nb == 0) return;
-  k_row_mask<<<nb, 64, 0, st>>>(diag, mask, cnt);
-  k_row_offsets<<<1, 1024, 0, st>>>(cnt, nb, off, nact);
-  k_row_scatter<<<nb, 64, 0, st>>>(mask, off, nact, rows);
-}
-
 // ------------------------------------------------ components (union-find)
 // Lock-free union-find: roots are linked with atomicCAS (larger index under
 // smaller), non-root pointers are only shortened.  Every loop is bounded and

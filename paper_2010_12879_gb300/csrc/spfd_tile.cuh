@@ -128,6 +128,12 @@ constexpr int row_n() { return sizeof(T) == 8 ? 2 : 4; }
 // two it measured 4 % slower on the 2 mm body, the residual 11 % faster.
 template <typename T>
 constexpr int row_n_jacobi() { return 4; }
+// The CG operator takes four nodes per thread in both precisions (in FP64
+// with its neighbour lookups first: 193.5 us per launch on the 2 mm body,
+// against 206.8 us with two nodes per thread over a list of the rows that
+// hold an unknown).
+template <typename T>
+constexpr int row_n_apply() { return 4; }
 // Threads per brick in the row mapping.
 template <typename T>
 constexpr int row_threads() { return BV / row_n<T>(); }
@@ -233,7 +239,7 @@ __device__ __forceinline__ Qv<T, N> ldq_nbi(const C *__restrict__ v, size_t s0, 
 // of the row ends come from the neighbouring lanes by shuffle (a row's
 // threads are consecutive lanes), else from the x-neighbour brick.  All 32
 // lanes of each warp must call it.
-template <typename T, typename C, bool RES, int N>
+template <typename T, typename C, bool RES, int N, bool NBF = RES>
 __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ gx,
                                            const T *__restrict__ diag, const T *__restrict__ x,
                                            size_t S, int b, int t, const Qv<T, N> &base,
@@ -242,12 +248,13 @@ __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ 
   const int h = t % TPR, y = (t / TPR) & 7, z = t / (8 * TPR);
   const size_t s0 = row_slot<N>(b, t);
   const size_t rz = (size_t)z * 64 + N * h, ry = (size_t)y * 8 + N * h;
-  // sweeps and residuals: the (at most one per axis) neighbour bricks this
-  // thread reads from are looked up before any load that needs one (7 % and
-  // 6 % faster FP64 sweep and residual, 4-5 % in FP32); the CG operator
-  // measured 11 % slower that way in FP32 and keeps the lookups at its loads
+  // NBF: the (at most one per axis) neighbour bricks this thread reads from
+  // are looked up before any load that needs one (7 % and 6 % faster FP64
+  // sweep and residual, 4-5 % in FP32, 6 % faster FP64 CG operator); the FP32
+  // CG operator measured 11 % slower that way and keeps the lookups at its
+  // loads
   int nx = -1, ny = -1, nz = -1;
-  if constexpr (RES) {
+  if constexpr (NBF) {
     const int *nt = g.nbr + (size_t)b * 27;
     nx = __ldg(nt + (h == 0 ? sidx(-1, 0, 0) : sidx(1, 0, 0)));
     if (y == 0 || y == 7) ny = __ldg(nt + (y == 0 ? sidx(0, -1, 0) : sidx(0, 1, 0)));
@@ -257,7 +264,7 @@ __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ 
   const Qv<T, N> gpx = ldqn<T, C, N>(gx + s0), gpy = ldqn<T, C, N>(gx + S + s0),
                  gpz = ldqn<T, C, N>(gx + 2 * S + s0);
   Qv<T, N> xym, xyp, xzm, xzp, gmy, gmz;
-  if constexpr (RES) {
+  if constexpr (NBF) {
     xym = ldq_nbi<T, T, N>(x, s0, y > 0, -8, ny, rz + 56);
     xyp = ldq_nbi<T, T, N>(x, s0, y < 7, 8, ny, rz);
     xzm = ldq_nbi<T, T, N>(x, s0, z > 0, -64, nz, 448 + ry);
@@ -278,7 +285,7 @@ __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ 
   const T next_first = __shfl_down_sync(0xffffffffu, xc.v[0], 1);
   T xl, xr, gl;
   if (h == 0) {
-    const int nb = RES ? nx : __ldg(&g.nbr[(size_t)b * 27 + sidx(-1, 0, 0)]);
+    const int nb = NBF ? nx : __ldg(&g.nbr[(size_t)b * 27 + sidx(-1, 0, 0)]);
     const size_t m = (size_t)nb * BV + (size_t)z * 64 + (size_t)y * 8 + 7;
     xl = nb >= 0 ? x[m] : T(0);
     gl = nb >= 0 ? cvt<T>(gx[m]) : T(0);
@@ -287,7 +294,7 @@ __device__ __forceinline__ void apply7_row(const Grid &g, const C *__restrict__ 
     gl = prev_glast;
   }
   if (h == TPR - 1) {
-    const int nb = RES ? nx : __ldg(&g.nbr[(size_t)b * 27 + sidx(1, 0, 0)]);
+    const int nb = NBF ? nx : __ldg(&g.nbr[(size_t)b * 27 + sidx(1, 0, 0)]);
     xr = nb >= 0 ? x[(size_t)nb * BV + (size_t)z * 64 + (size_t)y * 8] : T(0);
   } else {
     xr = next_first;
