@@ -44,7 +44,7 @@ k_residual7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
 // of the sum of z over the unknowns (w > 0) to partials[2 (brick warp) + {0,1}]
 // (right-hand side rhs at rhs * pstride), which launch_finish_rz adds.
 template <typename T, typename C, int ORD, bool RZ = false>
-__global__ void __launch_bounds__(BV / row_n_jacobi<T>(), row_min_blocks<T>())
+__global__ void __launch_bounds__(BV / row_n_jacobi<T>(), row_min_blocks_jacobi<T>())
 k_jacobi7(Grid g, const C *__restrict__ gx, const T *__restrict__ diag,
           const T *__restrict__ wdinv, const T *__restrict__ xin,
           const T *__restrict__ b, T *__restrict__ xout, int nk,

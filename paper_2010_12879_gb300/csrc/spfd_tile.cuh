@@ -142,6 +142,12 @@ constexpr int row_threads() { return BV / row_n<T>(); }
 // FP64 kernels take 4 blocks (of 256 threads: 64 registers; of 128: 128).
 template <typename T>
 constexpr int row_min_blocks() { return sizeof(T) == 4 ? 10 : 4; }
+// The weighted-Jacobi sweep asks for 9 resident FP32 blocks (56 registers,
+// no spills): 61.4 against 65.1 us per level-0 launch on the 2 mm body with
+// 10 (48 registers and spills); the residual and the CG operator measured
+// 2-3 % slower with 9 and keep 10.
+template <typename T>
+constexpr int row_min_blocks_jacobi() { return sizeof(T) == 4 ? 9 : 4; }
 
 template <typename T, int N>
 struct Qv {
