@@ -184,7 +184,7 @@ constexpr int RED_GRID = 608;  // 4 resident 512-thread blocks on each of 152 SM
 // measured 8 % faster than the unconditional form, 193 against 211 us per
 // launch on the 2 mm body.)
 template <typename T, int ORD>
-__global__ void __launch_bounds__(BV / row_n_apply<T>(), row_min_blocks<T>())
+__global__ void __launch_bounds__(BV / row_n_apply<T>(), row_min_blocks_apply<T>())
 k_apply_dot(Grid g, const T *__restrict__ gx, const T *__restrict__ diag,
             const T *__restrict__ p, T *__restrict__ q, const Scalars *sc,
             double *partials, size_t pstride, int nk) {

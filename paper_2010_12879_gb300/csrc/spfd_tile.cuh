@@ -148,6 +148,11 @@ constexpr int row_min_blocks() { return sizeof(T) == 4 ? 10 : 4; }
 // 2-3 % slower with 9 and keep 10.
 template <typename T>
 constexpr int row_min_blocks_jacobi() { return sizeof(T) == 4 ? 9 : 4; }
+// The FP64 CG operator (four nodes per thread) asks for 5 resident blocks (96
+// registers): 190 against 195 us per launch with 4 (108 registers); 6 (80
+// registers and spills) gave 193 us.
+template <typename T>
+constexpr int row_min_blocks_apply() { return sizeof(T) == 4 ? 10 : 5; }
 
 template <typename T, int N>
 struct Qv {
