@@ -242,6 +242,35 @@ def test_efield_of_uniform_edge_potential(oracle_mod):
     np.testing.assert_allclose(E, OMEGA / ph.h * 3e-9, rtol=1e-13)
 
 
+def test_efield_complex_closed_forms(oracle_mod):
+    """Complex source (R7): for Psi = 0 and a constant per axis with the
+    phasor a = (1 + 2j) a0, the field is (1 + 2j) E0, whose magnitude is
+    sqrt(5) (omega/h) ||a0||; a purely real source gives the real |E| bit for
+    bit; and a quadrature pair of linear potentials, Psi = c.r + j (d.r),
+    gives omega sqrt(|c|^2 + |d|^2) (the parts are not added before the
+    magnitude)."""
+    ph = random_phantom(3, 3, 3, np.random.default_rng(8), air_fraction=0.0)
+    a0 = np.zeros((3, 4, 4, 4))
+    a0[0], a0[1], a0[2] = 1e-9, -2e-9, 2e-9
+    z = np.zeros((4, 4, 4))
+    E = oracle_mod.efield_complex(ph.sigma, a0, z, 2 * a0, z, ph.h, OMEGA)
+    np.testing.assert_allclose(E, np.sqrt(5.0) * OMEGA / ph.h * 3e-9, rtol=1e-13)
+    E_re = oracle_mod.efield(ph.sigma, a0, z, ph.h, OMEGA)
+    np.testing.assert_array_equal(
+        oracle_mod.efield_complex(ph.sigma, a0, z, np.zeros_like(a0), z, ph.h, OMEGA), E_re)
+    rng = np.random.default_rng(11)
+    ph = random_phantom(5, 4, 3, rng, air_fraction=0.4)
+    X, Y, Z = _node_xyz(ph.dims, ph.h, ph.origin)
+    c = np.array([3.0, -2.0, 0.5]) * 1e-6
+    d = np.array([-1.0, 0.5, 2.0]) * 1e-6
+    zero_a = np.zeros((3,) + X.shape)
+    E = oracle_mod.efield_complex(ph.sigma, zero_a, c[0] * X + c[1] * Y + c[2] * Z,
+                                  zero_a, d[0] * X + d[1] * Y + d[2] * Z, ph.h, OMEGA)
+    m = ph.sigma > 0
+    np.testing.assert_allclose(E[m], OMEGA * np.sqrt(c @ c + d @ d), rtol=1e-12)
+    assert np.all(E[~m] == 0)
+
+
 # ---------------------------------------------------------------- sphere (32^3, R = 28 mm)
 
 @pytest.fixture(scope="module")
