@@ -227,6 +227,21 @@ spfd_status spfd_pipeline_host(const double *sigma_host, const double *a_host, i
 spfd_status spfd_efield(spfd_ctx *ctx, const double *a_dev,
                         const double *psi_dev, double omega, double *E_dev);
 
+/* |E| of a complex (phasor) source a = a_re + j a_im.  The operator of Eq. 3
+ * is real, so Psi = psi_re + j psi_im comes from two real solves (for
+ * instance one spfd_solve_batch of the two parts); the voxel-averaged field
+ * of Eq. 1 is then E_re + j E_im, and this writes its magnitude
+ *   |E| = sqrt(|E_re|^2 + |E_im|^2)
+ * (a peak-phasor magnitude; a_im = psi_im = 0 gives spfd_efield's result).
+ *   a_re, a_im       as a_dev of spfd_solve;  psi_re, psi_im as psi_dev.
+ *   E_dev            [nz][ny][nx] FP64 output in V/m, device, 16-byte
+ *                    aligned (SPFD_EINVAL otherwise).
+ * A scratch array of the voxel grid's size comes from the context's block
+ * cache.  Asynchronous on the context's stream. */
+spfd_status spfd_efield_complex(spfd_ctx *ctx, const double *a_re, const double *psi_re,
+                                const double *a_im, const double *psi_im, double omega,
+                                double *E_dev);
+
 /* Step 3 of the pipeline (Sec. II-A, step 3): the edge vector potentials a
  * from the magnetic facet fluxes b of Eq. 2, b = C a, by tree-cotree
  * gauging.  C (the discrete curl) annihilates every discrete gradient, so b

@@ -7,7 +7,8 @@ no fallback: if ``libspfd.so`` is missing or no GPU is present, the calls
 raise.
 
 Functions mirror the C entry points (``spfd_build``, ``spfd_solve``,
-``spfd_solve_host``, ``spfd_efield``, ``spfd_get_info``, ``spfd_destroy``,
+``spfd_solve_host``, ``spfd_efield``, ``spfd_efield_complex``, ``spfd_get_info``,
+``spfd_destroy``,
 ``spfd_last_error``, ``spfd_opts_default``); :class:`Solver` wraps them for
 ``torch.float64`` tensors.
 """
@@ -28,7 +29,7 @@ SPFD_FP64, SPFD_MIXED = 0, 1
 
 # Names declared in include/spfd.h (checked against the library by the tests).
 EXPORTS = ("spfd_opts_default", "spfd_build", "spfd_solve", "spfd_solve_host",
-           "spfd_efield", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
+           "spfd_efield", "spfd_efield_complex", "spfd_get_info", "spfd_kernel_stats", "spfd_destroy",
            "spfd_last_error", "spfd_residual_noalloc", "spfd_release_cached_memory",
            "spfd_energy_grad", "spfd_solve_batch", "spfd_percentile",
            "spfd_group_create", "spfd_group_solve", "spfd_group_destroy",
@@ -104,6 +105,8 @@ def lib():
             L.spfd_solve_host.restype = ctypes.c_int
             L.spfd_efield.argtypes = [vp, vp, vp, dp, vp]
             L.spfd_efield.restype = ctypes.c_int
+            L.spfd_efield_complex.argtypes = [vp, vp, vp, vp, vp, dp, vp]
+            L.spfd_efield_complex.restype = ctypes.c_int
             L.spfd_get_info.argtypes = [vp, ctypes.POINTER(SpfdInfo)]
             L.spfd_get_info.restype = ctypes.c_int
             L.spfd_kernel_stats.argtypes = [vp, ctypes.POINTER(SpfdKernelStat), ctypes.c_int,
@@ -204,6 +207,14 @@ def spfd_efield(ctx: int, a_ptr: int, psi_ptr: int, omega: float, E_ptr: int):
     _check(lib().spfd_efield(ctypes.c_void_p(ctx), ctypes.c_void_p(a_ptr),
                              ctypes.c_void_p(psi_ptr), float(omega),
                              ctypes.c_void_p(E_ptr)))
+
+
+def spfd_efield_complex(ctx: int, a_re_ptr: int, psi_re_ptr: int, a_im_ptr: int,
+                        psi_im_ptr: int, omega: float, E_ptr: int):
+    _check(lib().spfd_efield_complex(ctypes.c_void_p(ctx), ctypes.c_void_p(a_re_ptr),
+                                     ctypes.c_void_p(psi_re_ptr), ctypes.c_void_p(a_im_ptr),
+                                     ctypes.c_void_p(psi_im_ptr), float(omega),
+                                     ctypes.c_void_p(E_ptr)))
 
 
 def spfd_get_info(ctx: int) -> SpfdInfo:
@@ -482,6 +493,19 @@ class Solver:
         if E is None:
             E = torch.empty((nz, ny, nx), dtype=torch.float64, device=a.device)
         spfd_efield(self.ctx, a.data_ptr(), psi.data_ptr(), omega, E.data_ptr())
+        return E
+
+    def efield_complex(self, a_re, psi_re, a_im, psi_im, omega: float, E=None):
+        """|E| of the complex source a_re + j a_im from the solutions of its
+        two parts (include/spfd.h, spfd_efield_complex)."""
+        import torch
+        self._check_edges(a_re)
+        self._check_edges(a_im)
+        nx, ny, nz = self.dims
+        if E is None:
+            E = torch.empty((nz, ny, nx), dtype=torch.float64, device=a_re.device)
+        spfd_efield_complex(self.ctx, a_re.data_ptr(), psi_re.data_ptr(), a_im.data_ptr(),
+                            psi_im.data_ptr(), omega, E.data_ptr())
         return E
 
     def energy_grad(self, a, psi, omega: float, tol: float = 0.0):

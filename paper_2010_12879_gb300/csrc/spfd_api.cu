@@ -1182,6 +1182,33 @@ extern "C" spfd_status spfd_efield(spfd_ctx *ctx, const double *a_dev,
   return launch_check("efield");
 }
 
+extern "C" spfd_status spfd_efield_complex(spfd_ctx *ctx, const double *a_re,
+                                           const double *psi_re, const double *a_im,
+                                           const double *psi_im, double omega,
+                                           double *E_dev) {
+  if (!ctx) return fail(SPFD_EINVAL, "ctx is NULL");
+  if (!a_re || !psi_re || !a_im || !psi_im || !E_dev) return fail(SPFD_EINVAL, "null array");
+  if (!std::isfinite(omega)) return fail(SPFD_EINVAL, "omega must be finite");
+  if (reinterpret_cast<uintptr_t>(E_dev) % 16)
+    return fail(SPFD_EINVAL, "E_dev must be 16-byte aligned");
+  const size_t nvox = (size_t)ctx->nx * ctx->ny * ctx->nz;
+  const double nv = (double)nvox;
+  double *E_im = nullptr;
+  TRY(dalloc(ctx, &E_im, nvox));
+  SPFD_LAUNCH(ctx, "efield", false, 1, 41 * nv, 40 * nv,
+              launch_efield(ctx->mask, a_re, psi_re, ctx->nx, ctx->ny, ctx->nz, ctx->h, omega,
+                            E_dev, ctx->stream));
+  SPFD_LAUNCH(ctx, "efield", false, 1, 41 * nv, 40 * nv,
+              launch_efield(ctx->mask, a_im, psi_im, ctx->nx, ctx->ny, ctx->nz, ctx->h, omega,
+                            E_im, ctx->stream));
+  SPFD_LAUNCH(ctx, "efield", false, 1, 24 * nv, 4 * nv,
+              launch_efield_magnitude(nvox, E_dev, E_im, ctx->stream));
+  // the block goes back to the context's spare list; later work that takes it
+  // runs on the same stream, after the kernel above
+  dfree(ctx, E_im);
+  return launch_check("efield (complex)");
+}
+
 extern "C" spfd_status spfd_autotune_report(const spfd_ctx *ctx, spfd_tune_entry *entries,
                                             int max, int *n) {
   if (!ctx || !n || (max > 0 && !entries)) return fail(SPFD_EINVAL, "null argument");

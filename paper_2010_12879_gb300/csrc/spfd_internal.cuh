@@ -559,6 +559,8 @@ void launch_energy_grads(const Grid &g, const double *gx, const unsigned char *m
 void launch_efield(const unsigned char *mask, const double *a,
                    const double *psi, int nx, int ny, int nz, double h,
                    double omega, double *E, cudaStream_t st);
+// E = sqrt(E^2 + E_im^2) elementwise over n values (16-byte aligned arrays).
+void launch_efield_magnitude(size_t n, double *E, const double *E_im, cudaStream_t st);
 template <typename T>
 void launch_convert(size_t n, const double *src, double f, T *dst,
                     cudaStream_t st);

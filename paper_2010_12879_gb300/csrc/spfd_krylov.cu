@@ -1184,6 +1184,29 @@ void launch_efield(const unsigned char *mask, const double *a,
   k_efield<<<grid, EF_THREADS, 0, st>>>(mask, a, psi, nx, ny, nz, omega / (4.0 * h), E);
 }
 
+// |E| of a complex source from the magnitudes of its real and imaginary
+// parts: E = sqrt(E^2 + E_im^2) in place, each operation rounded on its own
+// (no contracted multiply-add), 16-byte loads.
+__global__ void __launch_bounds__(256)
+k_efield_magnitude(size_t n, double *__restrict__ E, const double *__restrict__ E_im) {
+  const size_t n2 = n / 2, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
+    double2 a = reinterpret_cast<const double2 *>(E)[i];
+    const double2 b = reinterpret_cast<const double2 *>(E_im)[i];
+    a.x = sqrt(__dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(b.x, b.x)));
+    a.y = sqrt(__dadd_rn(__dmul_rn(a.y, a.y), __dmul_rn(b.y, b.y)));
+    reinterpret_cast<double2 *>(E)[i] = a;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+    E[n - 1] = sqrt(__dadd_rn(__dmul_rn(E[n - 1], E[n - 1]), __dmul_rn(E_im[n - 1], E_im[n - 1])));
+}
+
+void launch_efield_magnitude(size_t n, double *E, const double *E_im, cudaStream_t st) {
+  if (n == 0) return;
+  const size_t blocks = std::min<size_t>((n / 2 + 255) / 256 + 1, 152 * 16);
+  k_efield_magnitude<<<(unsigned)blocks, 256, 0, st>>>(n, E, E_im);
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + NT - 1) / NT;
   return (int)std::max<size_t>(1, std::min<size_t>(b, RED_GRID));

@@ -511,3 +511,56 @@ def test_body_full_size_error_against_oracle(torch_cuda, spfd, body_2mm, precisi
     print(f"{precision} tol {tol:g}: psi {err_psi:.3e}, |E| {err_E:.3e}, "
           f"iters {info['iters']}/{info['outer_iters']}")
     assert err_psi <= psi_bar and err_E <= E_bar, (err_psi, err_E)
+
+
+@pytest.mark.parametrize("dims", [(19, 10, 12), (150, 6, 5)])
+def test_efield_complex_kernel_matches_oracle_on_given_psi(torch_cuda, spfd, oracle_mod, dims):
+    """|E| of a complex source (reading R7) from given real and imaginary
+    parts: the library's |E| of each part (bit-identical to the oracle's Eq. 1
+    evaluation), squared, added and rooted with no contracted multiply-add,
+    equals the oracle's definition bit for bit; a zero imaginary part gives
+    the real |E|."""
+    rng = np.random.default_rng(21)
+    ph = random_phantom(*dims, rng, air_fraction=0.4)
+    nx, ny, nz = ph.dims
+    a_re = rng.normal(size=(3, nz + 1, ny + 1, nx + 1))
+    a_im = rng.normal(size=(3, nz + 1, ny + 1, nx + 1))
+    p_re = rng.normal(size=(nz + 1, ny + 1, nx + 1))
+    p_im = rng.normal(size=(nz + 1, ny + 1, nx + 1))
+    torch = torch_cuda
+    with spfd.Solver(_dev(torch, ph.sigma), ph.h) as S:
+        E = S.efield_complex(_dev(torch, a_re), _dev(torch, p_re), _dev(torch, a_im),
+                             _dev(torch, p_im), OMEGA).cpu().numpy()
+        z_a, z_p = torch.zeros_like(_dev(torch, a_im)), torch.zeros_like(_dev(torch, p_im))
+        E0 = S.efield_complex(_dev(torch, a_re), _dev(torch, p_re), z_a, z_p, OMEGA).cpu().numpy()
+        E_real = S.efield(_dev(torch, a_re), _dev(torch, p_re), OMEGA).cpu().numpy()
+    E_r = oracle_mod.efield_complex(ph.sigma, a_re, p_re, a_im, p_im, ph.h, OMEGA)
+    np.testing.assert_array_equal(E, E_r)
+    np.testing.assert_array_equal(E0, E_real)
+
+
+def test_complex_source_solved_as_a_batch_of_two(torch_cuda, spfd, oracle_mod):
+    """A phasor source a = a_re + j a_im on the 8 mm body: its two parts
+    solved as one batch of two right-hand sides to 1e-12, then |E| of the
+    complex field, against the oracle's solves and its complex |E| at the
+    parity bars (1e-9 in each Psi part, 1e-7 in |E|)."""
+    torch = torch_cuda
+    ph = body_phantom(64, 40, 224, h=8e-3)
+    a_re = loop_potential(ph.dims, ph.h, ph.origin)
+    a_im = loop_potential(ph.dims, ph.h, ph.origin, center=(0.1, -0.05, -0.5))
+    A = torch.stack([_dev(torch, a_re), _dev(torch, a_im)])
+    with spfd.Solver(_dev(torch, ph.sigma), ph.h) as S:
+        psis, infos, st = S.solve_batch(A, 1e-12)
+        assert st == spfd.SPFD_OK
+        E = S.efield_complex(A[0], psis[0], A[1], psis[1], OMEGA).cpu().numpy()
+        psis = psis.cpu().numpy()
+    p_re, info_re, sys = oracle_mod.solve(ph.sigma, ph.h, a_re, tol=1e-13)
+    p_im, info_im, _ = oracle_mod.solve(ph.sigma, ph.h, a_im, tol=1e-13, sys=sys)
+    for g, r in ((psis[0], p_re), (psis[1], p_im)):
+        gg, rr = oracle_mod.project(sys, sys.gather(g)), sys.gather(r)
+        assert np.linalg.norm(gg - rr) <= 1e-9 * np.linalg.norm(rr)
+    E_r = oracle_mod.efield_complex(ph.sigma, a_re, p_re, a_im, p_im, ph.h, OMEGA)
+    m = ph.sigma > 0
+    floor = 1e-6 * E_r[m].max()
+    assert (np.abs(E - E_r)[m] / np.maximum(E_r[m], floor)).max() <= 1e-7
+    assert np.all(E[~m] == 0)
